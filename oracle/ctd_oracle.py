@@ -1,0 +1,478 @@
+"""FP64 CPU oracle for CTD (Lee, Choi, Sael: "CTD: Fast, Accurate, and
+Interpretable Method for Static and Dynamic Tensor Decompositions").
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke entry point and the
+benchmark's CPU-baseline leg may import this module.  It is a plain, slow,
+step-by-step restatement of the paper's method and shares no code with the
+CUDA library: no kernels, helpers, tables or constants are common to both.
+Inputs are plain arrays (the seeded generators produce them); nothing here
+reads a value computed by the GPU path.
+
+What each function follows:
+  matricize              Section 2.1 (mode-alpha matricization), reading A1
+  column_sqnorms, cdf    Algorithm 1 line 2, Eq. (1)
+  philox4x64_10          Salmon et al., SC'11 (counter-based RNG), reading A2
+  sample_columns         Algorithm 1 line 3 (with replacement), reading A2
+  unique_columns         Algorithm 1 line 4, reading A3
+  ctd_s                  Algorithm 1 lines 1-16, literally, FP64
+  ctd_d_step             Algorithm 2 lines 1-21, literally, FP64
+  c_columns              Algorithm 1 line 16 / Eq. (3), exact int64
+  relative_error_dense   Eq. (error), brute force on small inputs
+  projection_error       Lemma 3.2 (Eqs. 4-7): error = ||X - R R^+ X||^2/||X||^2
+  ddos_candidates        Section 5, detection rule on R's fibers
+
+Readings of points the paper leaves open (same letters everywhere):
+  A1 column order of X_(alpha): little-endian over the other modes
+     (alpha=1: f = j + J*k; alpha=2: f = i + I*k; alpha=3: f = i + I*j).
+  A2 draws: Philox4x64-10 with key (seed, 0) and counter (k, step, stream, 0);
+     u = first output word; target = floor(u * T / 2^64); the drawn column is
+     the smallest f with cdf[f] > target.
+  A3 I' is ascending.
+  A4 equality in the independence test counts as dependent (skip).
+  A5 Euclidean norms.
+  A6 the relative error is the squared ratio.
+  A9 a dynamic state may start empty; the first kept fiber then gives
+     U = 1/(x^T x), as in Algorithm 1 line 5.
+  A10 an all-zero input yields no draws and an empty factor.
+
+Parity pinned by tests/test_oracle_pins.py (brute force, numpy/scipy
+library routines, invariants, chi-square).  The DDoS rule is pinned only
+semantically (planted block), not against the paper's Table 4 numbers
+(parity unpinned for Table 4: the CAIDA data are not available).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+try:  # scipy is only used for sparse products (a library matmul)
+    import scipy.sparse as _sp
+except Exception:  # pragma: no cover
+    _sp = None
+
+_MASK64 = (1 << 64) - 1
+
+
+# ---------------------------------------------------------------------------
+# Section 2.1: mode-alpha matricization (reading A1)
+# ---------------------------------------------------------------------------
+
+def matricize(dims, i, j, k, alpha: int):
+    """Row index (the alpha index) and column index of each nonzero of X_(alpha).
+
+    Returns (rows int64, cols int64, I_alpha, N_alpha)."""
+    I, J, K = (int(d) for d in dims)
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    k = np.asarray(k, dtype=np.int64)
+    if alpha == 1:
+        return i, j + J * k, I, J * K
+    if alpha == 2:
+        return j, i + I * k, J, I * K
+    if alpha == 3:
+        return k, i + I * j, K, I * J
+    raise ValueError("alpha must be 1, 2 or 3")
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 line 2 / Eq. (1): squared column norms and their prefix sums
+# ---------------------------------------------------------------------------
+
+def column_sqnorms(cols, vals, n_cols: int) -> np.ndarray:
+    """|X_(alpha)(:, f)|^2 for every column f, exact in int64."""
+    v = np.asarray(vals, dtype=np.int64)
+    out = np.zeros(n_cols, dtype=np.int64)
+    np.add.at(out, np.asarray(cols, dtype=np.int64), v * v)
+    return out
+
+
+def column_counts(cols, n_cols: int) -> np.ndarray:
+    out = np.zeros(n_cols, dtype=np.int64)
+    np.add.at(out, np.asarray(cols, dtype=np.int64), 1)
+    return out
+
+
+def cdf(sqnorms: np.ndarray) -> np.ndarray:
+    """Inclusive prefix sum of the squared norms; the last entry is ||X||_F^2."""
+    out = np.cumsum(np.asarray(sqnorms, dtype=np.int64))
+    if out.size and (np.any(out < 0)):
+        raise OverflowError("||X||_F^2 does not fit in int64")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), reading A2
+# ---------------------------------------------------------------------------
+
+_PHILOX_M = (0xD2E7470EE14C6C93, 0xCA5A826395121157)
+_PHILOX_W = (0x9E3779B97F4A7C15, 0xBB67AE8584CAA73B)
+
+
+def philox4x64_10(counter: Sequence[int], key: Sequence[int]) -> List[int]:
+    """Ten rounds of the Philox S-P network on a 4x64-bit counter.
+
+    Each round multiplies words 0 and 2 by the two round multipliers, keeps
+    the 128-bit products' halves, XORs the high halves with the odd words and
+    the round key, and permutes; the key is bumped by the Weyl constants
+    before every round after the first."""
+    x = [int(c) & _MASK64 for c in counter]
+    kk = [int(c) & _MASK64 for c in key]
+    for r in range(10):
+        if r:
+            kk = [(kk[0] + _PHILOX_W[0]) & _MASK64, (kk[1] + _PHILOX_W[1]) & _MASK64]
+        p0 = _PHILOX_M[0] * x[0]
+        p1 = _PHILOX_M[1] * x[2]
+        hi0, lo0 = p0 >> 64, p0 & _MASK64
+        hi1, lo1 = p1 >> 64, p1 & _MASK64
+        x = [hi1 ^ x[1] ^ kk[0], lo1, hi0 ^ x[3] ^ kk[1], lo0]
+    return x
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 lines 3-4: sampling with replacement, then unique
+# ---------------------------------------------------------------------------
+
+def draw_target(k: int, total: int, seed: int, step: int = 0, stream: int = 0) -> int:
+    """Draw k's integer target in [0, total): floor(u * total / 2^64)."""
+    u = philox4x64_10((k, step, stream, 0), (seed, 0))[0]
+    return (u * int(total)) >> 64
+
+
+def sample_columns(cdf_arr: np.ndarray, s: int, seed: int, step: int = 0,
+                   stream: int = 0) -> np.ndarray:
+    """s column indices drawn with P(f) = |x_f|^2 / ||X||_F^2 (Alg. 1 line 3)."""
+    if cdf_arr.size == 0 or int(cdf_arr[-1]) == 0:
+        return np.zeros(0, dtype=np.int64)  # reading A10
+    total = int(cdf_arr[-1])
+    out = np.empty(s, dtype=np.int64)
+    for k in range(s):
+        t = draw_target(k, total, seed, step, stream)
+        # smallest f with cdf[f] > t
+        out[k] = int(np.searchsorted(cdf_arr, t, side="right"))
+    return out
+
+
+def unique_columns(I: np.ndarray) -> np.ndarray:
+    """I' = the distinct elements of I, ascending (Alg. 1 line 4, reading A3)."""
+    return np.unique(np.asarray(I, dtype=np.int64))
+
+
+# ---------------------------------------------------------------------------
+# Column access (CSC view of X_(alpha))
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Matricized:
+    """X_(alpha) as exact int64 CSC: column f holds rows[ptr[f]:ptr[f+1]]."""
+
+    n_rows: int
+    n_cols: int
+    ptr: np.ndarray
+    rows: np.ndarray
+    vals: np.ndarray
+
+    @staticmethod
+    def from_coo(dims, i, j, k, val, alpha: int) -> "Matricized":
+        rows, cols, n_rows, n_cols = matricize(dims, i, j, k, alpha)
+        order = np.lexsort((rows, cols))
+        rows = rows[order]
+        cols = cols[order]
+        vals = np.asarray(val, dtype=np.int64)[order]
+        ptr = np.zeros(n_cols + 1, dtype=np.int64)
+        np.add.at(ptr, cols + 1, 1)
+        ptr = np.cumsum(ptr)
+        return Matricized(n_rows, n_cols, ptr, rows, vals)
+
+    def column(self, f: int) -> np.ndarray:
+        """Dense int64 column X_(alpha)(:, f)."""
+        x = np.zeros(self.n_rows, dtype=np.int64)
+        a, b = int(self.ptr[f]), int(self.ptr[f + 1])
+        x[self.rows[a:b]] = self.vals[a:b]
+        return x
+
+    def sqnorm(self) -> int:
+        return int(np.sum(self.vals * self.vals))
+
+    def scipy(self):
+        return _sp.csc_matrix((self.vals, self.rows, self.ptr), shape=(self.n_rows, self.n_cols))
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 lines 5-15 / Algorithm 2 lines 6-16: the independence filter
+# ---------------------------------------------------------------------------
+
+def _filter(x_of, candidates, R_cols: List[np.ndarray], U: Optional[np.ndarray],
+            eps: float):
+    """Run the sequential independence test over `candidates` in order.
+
+    R_cols holds the current columns (dense float64, length I_alpha); U is
+    their (R^T R)^{-1} (None when R is empty).  For each candidate x the
+    residual res = x - R U R^T x is formed explicitly; the fiber is skipped
+    when ||res|| <= eps ||x|| (reading A4); otherwise delta = ||res||^2,
+    y = U R^T x, U grows by the block update of Alg. 1 line 12 and x is
+    appended to R.  Returns (kept candidate positions, R_cols, U, ratios)
+    where ratios[k] = ||res|| / ||x|| for every candidate (for tie margins).
+    """
+    kept: List[int] = []
+    ratios: List[float] = []
+    for pos, f in enumerate(candidates):
+        x = x_of(f).astype(np.float64)
+        xn = float(np.sqrt(x @ x))
+        if not R_cols:
+            # Alg. 1 line 5 (and reading A9): R <- [x], U <- 1/(x^T x)
+            if xn == 0.0:
+                ratios.append(0.0)
+                continue
+            R_cols.append(x)
+            U = np.array([[1.0 / (x @ x)]])
+            kept.append(pos)
+            ratios.append(1.0)
+            continue
+        R = np.stack(R_cols, axis=1)
+        Rtx = R.T @ x
+        y = U @ Rtx
+        res = x - R @ y
+        rn = float(np.sqrt(res @ res))
+        ratios.append(rn / xn if xn > 0 else 0.0)
+        if rn <= eps * xn:
+            continue
+        delta = rn * rn
+        n = U.shape[0]
+        Un = np.empty((n + 1, n + 1))
+        Un[:n, :n] = U + np.outer(y, y) / delta
+        Un[:n, n] = -y / delta
+        Un[n, :n] = -y / delta
+        Un[n, n] = 1.0 / delta
+        U = Un
+        R_cols.append(x)
+        kept.append(pos)
+    return kept, R_cols, U, ratios
+
+
+@dataclasses.dataclass
+class StaticResult:
+    T: int                   # ||X||_F^2, exact
+    sqnorms: np.ndarray      # |x_f|^2 for every column
+    cdf: np.ndarray
+    I: np.ndarray            # the s draws (Alg. 1 line 3)
+    I_unique: np.ndarray     # I' (Alg. 1 line 4)
+    kept: np.ndarray         # positions in I' of the columns of R
+    fibers: np.ndarray       # column ids of R's fibers (= I_unique[kept])
+    R: np.ndarray            # dense int64 I_alpha x s~
+    U: np.ndarray            # float64 s~ x s~
+    ratios: np.ndarray       # ||res|| / ||x|| per candidate in I' order
+    X: Matricized
+
+
+def ctd_s(dims, i, j, k, val, alpha: int, s: int, eps: float, seed: int,
+          step: int = 0, stream: int = 0) -> StaticResult:
+    """Algorithm 1 (CTD-S) lines 1-15.  C (line 16) is available through
+    `c_full` or `c_columns` because it can be far larger than R and U."""
+    X = Matricized.from_coo(dims, i, j, k, val, alpha)            # line 1
+    rows, cols, _, n_cols = matricize(dims, i, j, k, alpha)
+    sq = column_sqnorms(cols, val, n_cols)                          # line 2
+    c = cdf(sq)
+    T = int(c[-1]) if c.size else 0
+    I = sample_columns(c, s, seed, step, stream)                    # line 3
+    Iu = unique_columns(I)                                          # line 4
+    kept, R_cols, U, ratios = _filter(X.column, list(Iu), [], None, eps)  # 5-15
+    fibers = Iu[np.asarray(kept, dtype=np.int64)] if kept else np.zeros(0, np.int64)
+    if R_cols:
+        R = np.stack([X.column(int(f)) for f in fibers], axis=1)
+    else:
+        R = np.zeros((X.n_rows, 0), dtype=np.int64)
+        U = np.zeros((0, 0))
+    return StaticResult(T, sq, c, I, Iu, np.asarray(kept, dtype=np.int64), fibers,
+                        R, U, np.asarray(ratios), X)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 line 16 / Eq. (3): C_(alpha) = R^T X_(alpha), exact
+# ---------------------------------------------------------------------------
+
+def c_columns(X: Matricized, R: np.ndarray, cols) -> np.ndarray:
+    """Dense exact int64 columns C_(alpha)(:, cols) = R^T X_(alpha)(:, cols)."""
+    R = np.asarray(R, dtype=np.int64)
+    out = np.zeros((R.shape[1], len(cols)), dtype=np.int64)
+    for n, f in enumerate(cols):
+        a, b = int(X.ptr[f]), int(X.ptr[f + 1])
+        if b > a:
+            out[:, n] = R[X.rows[a:b], :].T @ X.vals[a:b]
+    return out
+
+
+def c_full(X: Matricized, R: np.ndarray):
+    """C_(alpha) = R^T X_(alpha) as an exact int64 scipy CSC matrix."""
+    Rs = _sp.csc_matrix(np.asarray(R, dtype=np.int64))
+    C = (Rs.T @ X.scipy()).tocsc()
+    C.eliminate_zeros()
+    C.sort_indices()
+    return C
+
+
+# ---------------------------------------------------------------------------
+# Eq. (error) and Lemma 3.2
+# ---------------------------------------------------------------------------
+
+def relative_error_dense(X: Matricized, R: np.ndarray, U: np.ndarray, C) -> float:
+    """||X~ - X||_F^2 / ||X||_F^2 with X~_(alpha) = R U C_(alpha) (Eq. error,
+    Eq. 3), computed densely.  Small inputs only."""
+    Xd = X.scipy().toarray().astype(np.float64)
+    Cd = C.toarray().astype(np.float64) if hasattr(C, "toarray") else np.asarray(C, np.float64)
+    Xt = np.asarray(R, np.float64) @ (U @ Cd) if R.shape[1] else np.zeros_like(Xd)
+    den = float(np.sum(Xd * Xd))
+    if den == 0.0:
+        return 0.0
+    return float(np.sum((Xt - Xd) ** 2)) / den
+
+
+def projection_error(X: Matricized, R: np.ndarray, chunk: int = 1 << 17) -> float:
+    """Lemma 3.2: the CTD-S error equals ||X - R R^+ X||_F^2 / ||X||_F^2.
+
+    Computed as 1 - ||Q^T X||_F^2 / ||X||_F^2 with Q an orthonormal basis of
+    range(R) from numpy's QR (a library routine), streaming over columns."""
+    T = X.sqnorm()
+    if T == 0:
+        return 0.0
+    if R.shape[1] == 0:
+        return 1.0
+    Q, _ = np.linalg.qr(np.asarray(R, np.float64))
+    Xs = X.scipy().astype(np.float64)
+    acc = 0.0
+    for a in range(0, X.n_cols, chunk):
+        blk = Xs[:, a:a + chunk]
+        if blk.nnz == 0:
+            continue
+        P = (blk.T @ Q)   # (cols x s~) dense
+        acc += float(np.sum(P * P))
+    return (T - acc) / T
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 2 (CTD-D): one time step
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class DynamicState:
+    """Factors after t steps: R^(t) (dense columns), U^(t), C^(t) (dense,
+    d~_t x N^(t), optional), plus bookkeeping for the error."""
+
+    n_rows: int
+    n_cols_slice: int
+    R_cols: List[np.ndarray] = dataclasses.field(default_factory=list)
+    fibers: List[tuple] = dataclasses.field(default_factory=list)   # (t, f)
+    U: Optional[np.ndarray] = None
+    C: Optional[np.ndarray] = None          # dense float64, kept when track_c
+    t: int = 0
+    track_c: bool = True
+    X_blocks: List = dataclasses.field(default_factory=list)   # for brute force
+    err_num: float = 0.0
+    err_den: int = 0
+
+
+@dataclasses.dataclass
+class StepResult:
+    I: np.ndarray
+    I_unique: np.ndarray
+    kept: np.ndarray            # positions in I' of the new columns (Delta R)
+    new_fibers: np.ndarray      # their fiber ids within the slice
+    M: Optional[np.ndarray]     # ((Delta R)^T R^(t)) U^(t), Delta d~ x d~_t
+    C_new: Optional[np.ndarray] # R^(t+1)^T Delta X, exact int64 (d~_{t+1} x J)
+    T_slice: int
+    ratios: np.ndarray
+
+
+def ctd_d_step(state: DynamicState, dims2, i, j, val, d: int, eps: float,
+               seed: int, stream: int = 0, keep_X: bool = False) -> StepResult:
+    """Algorithm 2 for one incoming slice Delta X (I x J x 1) with alpha = 1.
+
+    Lines 1-4 sample d columns of Delta X_(alpha) exactly as Algorithm 1;
+    line 5 warm-starts from R^(t), U^(t); lines 6-16 run the same sequential
+    test against the growing R^(t+1); lines 17-21 update C_(alpha) with the
+    block form of Eq. (C_t+1_final), whose lower-left block is evaluated
+    left to right as (((Delta R)^T R^(t)) U^(t)) C^(t) (the reordering)."""
+    I_, J_ = (int(dims2[0]), int(dims2[1]))
+    k = np.zeros_like(np.asarray(i))
+    dX = Matricized.from_coo((I_, J_, 1), i, j, k, val, 1)          # line 1
+    sq = column_sqnorms(matricize((I_, J_, 1), i, j, k, 1)[1], val, J_)  # line 2
+    c = cdf(sq)
+    Ts = int(c[-1]) if c.size else 0
+    Id = sample_columns(c, d, seed, state.t, stream)                 # line 3
+    Iu = unique_columns(Id)                                          # line 4
+    R_old = [col.copy() for col in state.R_cols]                     # line 5
+    U_old = None if state.U is None else state.U.copy()
+    d_t = len(R_old)
+    kept, R_cols, U, ratios = _filter(dX.column, list(Iu), list(R_old), U_old, eps)  # 6-16
+    new_f = Iu[np.asarray(kept, dtype=np.int64)] if kept else np.zeros(0, np.int64)
+    # lines 17-21
+    R_new_int = (np.stack([dX.column(int(f)) for f in new_f], axis=1)
+                 if len(new_f) else np.zeros((I_, 0), np.int64))
+    R_old_int = (np.stack([np.rint(col).astype(np.int64) for col in R_old], axis=1)
+                 if d_t else np.zeros((I_, 0), np.int64))
+    R_all_int = np.concatenate([R_old_int, R_new_int], axis=1)
+    C_new = c_columns(dX, R_all_int, range(J_))                      # [R^(t)T dX; dR^T dX]
+    M = None
+    if len(new_f) and d_t:
+        M = ((R_new_int.T.astype(np.float64) @ R_old_int.astype(np.float64)) @ U_old)
+    if state.track_c:
+        # C^(t) is d~_t x N^(t); before the first step it has no columns
+        top = state.C if state.C is not None else np.zeros((d_t, 0))
+        if len(new_f):
+            # line 18: lower-left block, parenthesized from the left
+            lower = M @ top if M is not None else np.zeros((len(new_f), top.shape[1]))
+            left = np.concatenate([top, lower], axis=0)
+        else:
+            left = top                                                # line 20
+        state.C = np.concatenate([left, C_new.astype(np.float64)], axis=1)
+    state.R_cols = R_cols
+    state.U = U if R_cols else None
+    state.fibers += [(state.t, int(f)) for f in new_f]
+    if keep_X:
+        state.X_blocks.append(dX)
+    # per-step error increment (the old columns' reconstruction is unchanged)
+    if Ts:
+        if R_cols:
+            R = R_all_int.astype(np.float64)
+            Q, _ = np.linalg.qr(R)
+            P = dX.scipy().astype(np.float64).T @ Q
+            state.err_num += Ts - float(np.sum(P * P))
+        else:
+            state.err_num += Ts
+    state.err_den += Ts
+    state.t += 1
+    return StepResult(Id, Iu, np.asarray(kept, np.int64), new_f, M, C_new, Ts, np.asarray(ratios))
+
+
+def dynamic_error_dense(state: DynamicState) -> float:
+    """Eq. (error) for X^(t) = [dX_0, ..., dX_{t-1}] with the literal dense C^(t)."""
+    if not state.X_blocks or state.C is None:
+        raise ValueError("needs keep_X=True and track_c=True")
+    Xd = np.concatenate([b.scipy().toarray().astype(np.float64) for b in state.X_blocks], axis=1)
+    den = float(np.sum(Xd * Xd))
+    if den == 0.0:
+        return 0.0
+    if not state.R_cols:
+        return 1.0
+    R = np.stack(state.R_cols, axis=1)
+    Xt = R @ (state.U @ state.C)
+    return float(np.sum((Xt - Xd) ** 2)) / den
+
+
+# ---------------------------------------------------------------------------
+# Section 5: DDoS candidates from CTD-D's R
+# ---------------------------------------------------------------------------
+
+def ddos_candidates(fibers: Sequence[tuple], R_cols: Sequence[np.ndarray]) -> List[int]:
+    """Group R's fibers (t, destination) by destination; the first fiber of
+    each group represents it; report the destinations whose representative's
+    norm exceeds the mean norm of all representatives."""
+    first = {}
+    for (t, dst), col in zip(fibers, R_cols):
+        if dst not in first:
+            first[dst] = float(np.sqrt(np.dot(col, col)))
+    if not first:
+        return []
+    mean = sum(first.values()) / len(first)
+    return sorted(dst for dst, nrm in first.items() if nrm > mean)

@@ -1,0 +1,305 @@
+"""Pins of the FP64 oracle against things other than itself: brute force on
+dense arrays, numpy/scipy library routines, closed forms, invariants and a
+chi-square test of the sampling law.  CPU only."""
+import numpy as np
+import pytest
+
+from oracle import ctd_oracle as O
+from paper_1710_03608_gb300 import synth
+
+
+def dense(coo):
+    X = np.zeros(coo.dims, dtype=np.int64)
+    X[coo.i, coo.j, coo.k] = coo.val
+    return X
+
+
+def unfold(X, alpha):
+    """Kolda-Bader mode-n unfolding: move mode n first, then Fortran-order reshape."""
+    Xm = np.moveaxis(X, alpha - 1, 0)
+    return Xm.reshape(Xm.shape[0], -1, order="F")
+
+
+# --- P1: matricization, squared norms, CDF ---------------------------------
+
+@pytest.mark.parametrize("alpha", [1, 2, 3])
+def test_norms_and_cdf_match_dense_unfolding(alpha):
+    coo = synth.tiny((7, 5, 4), 60, seed=3, signed=True)
+    Xa = unfold(dense(coo), alpha)
+    rows, cols, n_rows, n_cols = O.matricize(coo.dims, coo.i, coo.j, coo.k, alpha)
+    assert (n_rows, n_cols) == Xa.shape
+    # every nonzero lands at the unfolding's (row, col)
+    assert np.array_equal(Xa[rows, cols], coo.val.astype(np.int64))
+    sq = O.column_sqnorms(cols, coo.val, n_cols)
+    assert np.array_equal(sq, np.sum(Xa * Xa, axis=0))
+    c = O.cdf(sq)
+    assert int(c[-1]) == int(np.sum(Xa * Xa))
+    assert np.array_equal(np.diff(np.concatenate([[0], c])), sq)
+
+
+def test_matricized_columns_match_dense():
+    coo = synth.tiny((6, 5, 4), 40, seed=5)
+    Xa = unfold(dense(coo), 1)
+    M = O.Matricized.from_coo(coo.dims, coo.i, coo.j, coo.k, coo.val, 1)
+    for f in range(Xa.shape[1]):
+        assert np.array_equal(M.column(f), Xa[:, f])
+
+
+# --- P2: Philox4x64-10 against numpy's independent implementation ----------
+
+@pytest.mark.parametrize("key", [(0, 0), (5, 0), (2**64 - 1, 12345)])
+@pytest.mark.parametrize("ctr", [(0, 0, 0, 0), (7, 3, 1, 0), (2**63, 2**40, 9, 77)])
+def test_philox_matches_numpy(key, ctr):
+    bg = np.random.Philox(key=np.array(key, dtype=np.uint64),
+                          counter=np.array(ctr, dtype=np.uint64))
+    want = [int(v) for v in bg.random_raw(4)]
+    # numpy increments the counter before it generates a block
+    c = list(ctr)
+    c[0] += 1
+    for w in range(4):
+        if c[w] >= 2**64:
+            c[w] -= 2**64
+            if w + 1 < 4:
+                c[w + 1] += 1
+        else:
+            break
+    assert O.philox4x64_10(c, key) == want
+
+
+# --- P3: sampling law --------------------------------------------------------
+
+def test_sampling_chi_square():
+    scipy_stats = pytest.importorskip("scipy.stats")
+    rng = np.random.default_rng(11)
+    sq = rng.integers(0, 50, size=64).astype(np.int64)
+    sq[[3, 17, 40]] = 0
+    c = O.cdf(sq)
+    n = 200_000
+    draws = O.sample_columns(c, n, seed=1234)
+    counts = np.bincount(draws, minlength=64)
+    assert counts[[3, 17, 40]].sum() == 0          # P(f) = 0 => never drawn
+    p = sq / sq.sum()
+    nz = p > 0
+    stat, pval = scipy_stats.chisquare(counts[nz], n * p[nz])
+    assert pval > 1e-3, (stat, pval)
+
+
+def test_single_nonzero_column_is_always_drawn():
+    sq = np.zeros(100, dtype=np.int64)
+    sq[42] = 9
+    draws = O.sample_columns(O.cdf(sq), 500, seed=0)
+    assert np.all(draws == 42)
+
+
+def test_empty_tensor_draws_nothing():
+    assert O.sample_columns(O.cdf(np.zeros(10, np.int64)), 50, seed=0).size == 0
+
+
+def test_draw_target_is_floor_of_scaled_u():
+    # target = floor(u * T / 2^64) is always < T and monotone in u
+    for T in (1, 2, 3, 10**12, 2**62 + 7):
+        for k in range(20):
+            t = O.draw_target(k, T, seed=9)
+            assert 0 <= t < T
+
+
+# --- P4: unique ---------------------------------------------------------------
+
+def test_unique_is_the_distinct_sorted_draws():
+    sq = np.arange(1, 30, dtype=np.int64) ** 2
+    I = O.sample_columns(O.cdf(sq), 200, seed=3)
+    Iu = O.unique_columns(I)
+    assert list(Iu) == sorted(set(int(x) for x in I))
+
+
+# --- P5, P6: the independence filter and U ----------------------------------
+
+def _planted():
+    """Columns with planted dependencies: a scaled duplicate, a sum of two
+    kept columns, and parallel single-nonzero columns on the same row."""
+    I = 8
+    base = np.array([[3, 0, 1, 0, 0, 2, 0, 0],
+                     [0, 2, 0, 0, 1, 0, 0, 4],
+                     [1, 1, 1, 1, 0, 0, 0, 0]], dtype=np.int64).T
+    cols = [base[:, 0], base[:, 1], 2 * base[:, 0], base[:, 0] + base[:, 1], base[:, 2]]
+    e3 = np.zeros(I, np.int64); e3[3] = 5
+    e3b = np.zeros(I, np.int64); e3b[3] = 2
+    cols += [e3, e3b]
+    return np.stack(cols, axis=1)
+
+
+def test_filter_skips_planted_dependencies():
+    R0 = _planted()
+    kept, R_cols, U, ratios = O._filter(lambda f: R0[:, f], list(range(R0.shape[1])), [], None, 1e-6)
+    assert kept == [0, 1, 4, 5]
+    R = np.stack(R_cols, axis=1)
+    assert np.linalg.matrix_rank(R) == np.linalg.matrix_rank(R0.astype(float)) == len(kept)
+    # P6: U = (R^T R)^{-1}
+    G = R.T @ R
+    Ui = np.linalg.inv(G)
+    assert np.linalg.norm(U - Ui) <= 1e-12 * np.linalg.norm(Ui)
+    assert np.linalg.norm(U @ G - np.eye(len(kept))) < 1e-10
+
+
+def test_filter_tie_counts_as_dependent():
+    # eps = 1 makes ||res|| <= ||x|| always true after the first column
+    R0 = _planted()
+    kept, *_ = O._filter(lambda f: R0[:, f], list(range(R0.shape[1])), [], None, 1.0)
+    assert kept == [0]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_ctd_s_rank_and_U(seed):
+    coo = synth.tiny((12, 6, 5), 90, seed=seed)
+    res = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 40, 1e-6, seed)
+    Xa = unfold(dense(coo), 1)
+    R0 = Xa[:, res.I_unique].astype(float)
+    assert np.array_equal(res.R, Xa[:, res.fibers])
+    assert res.R.shape[1] == np.linalg.matrix_rank(R0)
+    G = res.R.T.astype(float) @ res.R.astype(float)
+    Ui = np.linalg.inv(G)
+    assert np.linalg.norm(res.U - Ui) <= 1e-10 * np.linalg.norm(Ui)
+
+
+# --- P7: C, the error, optimality (Lemma 3.2) --------------------------------
+
+@pytest.mark.parametrize("alpha", [1, 2, 3])
+def test_c_is_r_transpose_x(alpha):
+    coo = synth.tiny((6, 7, 5), 80, seed=4, signed=True)
+    res = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, alpha, 30, 1e-6, 0)
+    Xa = unfold(dense(coo), alpha)
+    C = O.c_full(res.X, res.R)
+    assert np.array_equal(C.toarray(), res.R.T @ Xa)
+    cols = [0, 3, Xa.shape[1] - 1]
+    assert np.array_equal(O.c_columns(res.X, res.R, cols), (res.R.T @ Xa)[:, cols])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_error_forms_agree_with_lstsq(seed):
+    coo = synth.tiny((10, 8, 6), 120, seed=seed + 10)
+    res = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 25, 1e-6, seed)
+    Xa = unfold(dense(coo), 1).astype(float)
+    C = O.c_full(res.X, res.R)
+    e_lit = O.relative_error_dense(res.X, res.R, res.U, C)
+    e_proj = O.projection_error(res.X, res.R)
+    # least squares against ALL sampled columns, duplicates and dependents included
+    R0 = Xa[:, res.I]
+    L, *_ = np.linalg.lstsq(R0, Xa, rcond=None)
+    e_ls = np.sum((R0 @ L - Xa) ** 2) / np.sum(Xa ** 2)
+    assert abs(e_lit - e_ls) <= 1e-10 * max(e_ls, 1e-3)
+    assert abs(e_proj - e_ls) <= 1e-10 * max(e_ls, 1e-3)
+    assert 0.0 <= e_ls <= 1.0
+
+
+def test_sampling_every_fiber_gives_exact_reconstruction():
+    coo = synth.tiny((6, 4, 3), 30, seed=2)
+    res = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 4000, 1e-6, 5)
+    nonempty = np.flatnonzero(res.sqnorms)
+    assert np.array_equal(res.I_unique, nonempty)
+    C = O.c_full(res.X, res.R)
+    assert abs(O.relative_error_dense(res.X, res.R, res.U, C)) <= 1e-12
+
+
+def test_error_identity_with_u_and_cct():
+    # Eq. (7): ||X - R U C||^2 = T - <U, C C^T> when U = (R^T R)^{-1}, C = R^T X
+    coo = synth.tiny((9, 7, 5), 100, seed=8)
+    res = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 20, 1e-6, 8)
+    C = O.c_full(res.X, res.R).toarray().astype(float)
+    e_lit = O.relative_error_dense(res.X, res.R, res.U, O.c_full(res.X, res.R))
+    e_gram = (res.T - float(np.sum(res.U * (C @ C.T)))) / res.T
+    assert abs(e_lit - e_gram) < 1e-12
+
+
+# --- P8, P9, P10: CTD-D ---------------------------------------------------------
+
+def _slices(n, dims2=(9, 7), nnz=25, seed=0):
+    out = []
+    for t in range(n):
+        c = synth.tiny((dims2[0], dims2[1], 1), nnz, seed=seed * 100 + t)
+        out.append(c)
+    return out
+
+
+def test_first_dynamic_step_equals_static():
+    sl = _slices(1, seed=3)[0]
+    st = O.DynamicState(9, 7)
+    step = O.ctd_d_step(st, (9, 7), sl.i, sl.j, sl.val, 20, 1e-6, seed=4)
+    ref = O.ctd_s((9, 7, 1), sl.i, sl.j, sl.k, sl.val, 1, 20, 1e-6, 4)
+    assert np.array_equal(step.I, ref.I)
+    assert np.array_equal(step.new_fibers, ref.fibers)
+    assert np.linalg.norm(st.U - ref.U) <= 1e-13 * np.linalg.norm(ref.U)
+    assert np.array_equal(step.C_new, ref.R.T @ unfold(dense(sl), 1))
+
+
+def test_dynamic_error_increment_matches_literal_c():
+    st = O.DynamicState(9, 7)
+    for t, sl in enumerate(_slices(6, seed=1)):
+        O.ctd_d_step(st, (9, 7), sl.i, sl.j, sl.val, 4, 1e-6, seed=2, keep_X=True)
+        e_inc = st.err_num / st.err_den
+        e_lit = O.dynamic_error_dense(st)
+        assert abs(e_inc - e_lit) <= 1e-10 * max(e_lit, 1e-6), (t, e_inc, e_lit)
+
+
+def test_dynamic_c_exact_when_history_is_spanned():
+    # if R^(t) spans every column of X^(t), C^(t+1) equals R^(t+1)^T X^(t+1)
+    st = O.DynamicState(6, 5)
+    sls = _slices(4, dims2=(6, 5), nnz=20, seed=2)
+    for sl in sls:
+        O.ctd_d_step(st, (6, 5), sl.i, sl.j, sl.val, 500, 1e-6, seed=1, keep_X=True)
+    Xd = np.concatenate([b.scipy().toarray() for b in st.X_blocks], axis=1).astype(float)
+    R = np.stack(st.R_cols, axis=1)
+    assert np.linalg.matrix_rank(R) == np.linalg.matrix_rank(Xd)
+    assert np.allclose(st.C, R.T @ Xd, rtol=1e-9, atol=1e-7)
+
+
+def test_reordering_parenthesizations_agree():
+    rng = np.random.default_rng(0)
+    dR = rng.integers(0, 4, size=(30, 3)).astype(float)
+    Rt = rng.integers(0, 4, size=(30, 6)).astype(float)
+    U = np.linalg.inv(Rt.T @ Rt + np.eye(6))
+    C = rng.integers(0, 9, size=(6, 40)).astype(float)
+    forms = [((dR.T @ Rt) @ U) @ C, (dR.T @ (Rt @ U)) @ C, dR.T @ ((Rt @ U) @ C),
+             dR.T @ (Rt @ (U @ C)), (dR.T @ Rt) @ (U @ C)]
+    for f in forms[1:]:
+        assert np.allclose(f, forms[0], rtol=1e-12, atol=1e-12)
+
+
+# --- Section 5: DDoS rule on a planted block ---------------------------------
+
+def test_ddos_rule_flags_planted_destinations():
+    # background traffic uses destinations 0..29; two victims (33, 37) first
+    # appear at steps 3-4, each hit by 12 sources with heavy counts
+    I, J = 60, 40
+    rng = np.random.default_rng(5)
+    victims = [33, 37]
+    st = O.DynamicState(I, J)
+    for t in range(6):
+        bg = synth.tiny((I, 30, 1), 150, seed=50 + t)
+        i, j, v = list(bg.i), list(bg.j), list(bg.val)
+        if t in (3, 4):
+            for dst in victims:
+                for s_ in rng.choice(I, size=12, replace=False):
+                    i.append(s_); j.append(dst); v.append(40)
+        O.ctd_d_step(st, (I, J), np.array(i), np.array(j), np.array(v), 10, 0.15, seed=3)
+    flagged = O.ddos_candidates(st.fibers, st.R_cols)
+    assert set(victims) <= set(flagged)
+    assert len(flagged) < 10
+
+
+# --- A10 / A12 edge cases ----------------------------------------------------------
+
+def test_all_zero_tensor():
+    coo = synth.tiny((4, 3, 2), 5, seed=1)
+    coo.val[:] = 0
+    res = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 10, 1e-6, 0)
+    assert res.T == 0 and res.I.size == 0 and res.R.shape[1] == 0
+
+
+def test_negative_values_allowed():
+    coo = synth.tiny((8, 6, 4), 70, seed=9, signed=True)
+    res = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 2, 30, 1e-6, 1)
+    Xa = unfold(dense(coo), 2).astype(float)
+    R0 = Xa[:, res.I]
+    L, *_ = np.linalg.lstsq(R0, Xa, rcond=None)
+    e_ls = np.sum((R0 @ L - Xa) ** 2) / np.sum(Xa ** 2)
+    assert abs(O.projection_error(res.X, res.R) - e_ls) < 1e-10
