@@ -1,0 +1,204 @@
+/*
+ * ctd.h -- C ABI of the GB300 CTD library (libctd.so).
+ *
+ * CTD (Lee, Choi, Sael) decomposes a sparse tensor X into C x_alpha (R U):
+ *   R  holds actual, linearly independent mode-alpha fibers of X,
+ *   U  = (R^T R)^{-1}  (the small pseudoinverse, Lemma 3.2),
+ *   C  = X x_alpha R^T, i.e. C_(alpha) = R^T X_(alpha)  (Algorithm 1 line 16, Eq. 3).
+ * CTD-S (Algorithm 1) does this for a static tensor; CTD-D (Algorithm 2)
+ * updates the factors when a new time slice arrives.
+ *
+ * Conventions for every entry point:
+ *  - Tensors are 3-way, in COO form (Section 2.1 "sparse-unordered"):
+ *    int32 index vectors i, j, k (0-based) and int32 values.  Coordinates
+ *    must be distinct; values may be zero or negative.
+ *  - Mode alpha is 1, 2 or 3 (the paper's 1-based notation).  Column f of
+ *    X_(alpha) is the little-endian index over the other two modes
+ *    (alpha=1: f = j + J*k; alpha=2: f = i + I*k; alpha=3: f = i + I*j).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    queued on it; entry points that must know a data-dependent size wait
+ *    for the stream before they return.  Inputs must stay valid until the
+ *    call returns.
+ *  - Outputs (ctd_factors) are owned by the library and live in device
+ *    memory until ctd_free.  Getters copy into caller-provided HOST buffers
+ *    and synchronize.
+ *  - No call throws.  Every call returns a ctd_status; on failure
+ *    ctd_last_error() gives a message (per thread).  Outputs are left
+ *    untouched on failure.
+ *  - Integer work (norms, CDF, draws, dedup, R, C) is exact.  U and the
+ *    relative error are computed in FP64; with CTD_FP32_BULK the stored C
+ *    values are float (each is an exactly rounded integer).
+ *  - Limits: N_alpha < 2^31, I_alpha < 2^31, nnz < 2^31, 1 <= s <= 8192,
+ *    1 <= d <= 8192, number of kept fibers <= 24576.  Larger inputs return
+ *    CTD_EINVAL.
+ */
+#ifndef CTD_H
+#define CTD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CTD_API __attribute__((visibility("default")))
+#else
+#define CTD_API
+#endif
+
+typedef enum {
+  CTD_OK = 0,
+  CTD_EINVAL = 1,     /* bad argument, index out of range, size over a limit */
+  CTD_ENOMEM = 2,     /* device allocation failed */
+  CTD_EOVERFLOW = 3,  /* ||X||_F^2 or an exact product does not fit 64 bits */
+  CTD_ECUDA = 4,      /* a CUDA runtime call failed */
+  CTD_ETIMEOUT = 5,   /* a bounded device wait gave up */
+  CTD_ENOTSUP = 6     /* valid request this build does not handle */
+} ctd_status;
+
+typedef enum {
+  CTD_FP64 = 0,       /* C stored as double */
+  CTD_FP32_BULK = 1   /* C stored as float; U, Gram and filter stay FP64 */
+} ctd_precision;
+
+typedef enum {
+  CTD_MEM_DEVICE = 0, /* i, j, k, val are device pointers */
+  CTD_MEM_HOST = 1    /* host pointers: the library copies them in */
+} ctd_memory;
+
+/* Flags for ctd_static. */
+#define CTD_SKIP_C 1u      /* do not materialize C (R, U and the error only) */
+#define CTD_SKIP_ERROR 2u  /* do not compute the relative error */
+
+typedef struct {
+  int64_t dims[3];     /* I, J, K */
+  int64_t nnz;
+  const int32_t* i;
+  const int32_t* j;
+  const int32_t* k;
+  const int32_t* val;
+  int32_t memory;      /* ctd_memory */
+} ctd_coo3;
+
+typedef struct ctd_factors ctd_factors;   /* opaque */
+
+typedef struct {
+  int64_t n_rows;      /* I_alpha */
+  int64_t n_cols;      /* N_alpha (CTD-D: columns of one slice) */
+  int64_t s_draws;     /* s (or d of the last step) */
+  int64_t s_unique;    /* s' (or d' of the last step) */
+  int64_t s_kept;      /* s~ (CTD-D: d~_t, all steps) */
+  int64_t nnz_R;
+  int64_t nnz_C;       /* CTD-S: nonzeros of C_(alpha); CTD-D: of all new-column blocks */
+  int64_t t_steps;     /* CTD-D: steps taken; CTD-S: 0 */
+  int64_t nnz_X;       /* nonzeros of X (CTD-D: all slices so far) */
+  double  sqnorm_X;    /* ||X||_F^2 (exact integer, as double) */
+} ctd_sizes;
+
+/*
+ * ctd_static -- CTD-S, Algorithm 1 (REQUIRE: tensor X, mode alpha, sample
+ * size s, tolerance eps; ENSURE: C, U, R).
+ *  X        tensor (device or host memory, see ctd_coo3.memory)
+ *  alpha    1..3
+ *  s        number of draws with replacement (line 3), 1..8192
+ *  eps      tolerance of the independence test (line 8), 0 <= eps < 1;
+ *           a fiber x is kept iff ||res|| > eps ||x||
+ *  seed     Philox4x64-10 key; draw k uses counter (k, 0, 0, 0)
+ *  precision ctd_precision
+ *  flags    CTD_SKIP_C | CTD_SKIP_ERROR
+ *  out      receives a new ctd_factors (free with ctd_free)
+ * Errors: CTD_EINVAL (arguments, index out of range), CTD_EOVERFLOW,
+ * CTD_ENOMEM, CTD_ECUDA.  An all-zero tensor gives empty factors and
+ * error 0 (no draws).
+ */
+CTD_API ctd_status ctd_static(const ctd_coo3* X, int alpha, int64_t s, double eps,
+                      uint64_t seed, int precision, unsigned flags,
+                      void* stream, ctd_factors** out);
+
+/*
+ * ctd_dynamic_create -- empty CTD-D state for slices of size
+ * dims2[0] x dims2[1] x 1 (Algorithm 2 with alpha in {1, 2}; the time mode
+ * is the third).  `stream_id` selects an independent Philox counter space
+ * (draw k of step t uses counter (k, t, stream_id, 0)).
+ */
+CTD_API ctd_status ctd_dynamic_create(const int64_t dims2[2], int alpha, int precision,
+                              uint64_t seed, uint64_t stream_id,
+                              ctd_factors** state);
+
+/*
+ * ctd_dynamic_step -- one step of CTD-D, Algorithm 2, in place:
+ * (C^(t), U^(t), R^(t)) -> (C^(t+1), U^(t+1), R^(t+1)).
+ *  dX   the new slice, dims = {dims2[0], dims2[1], 1}
+ *  d    draws for this step (line 3), 1..8192
+ *  eps  tolerance (line 9)
+ * The new columns' block R^(t+1)^T dX is stored exactly; the lower-left
+ * block of Eq. (C_t+1_final) is kept as M_{t+1} = ((dR)^T R^(t)) U^(t)
+ * (the paper's left-to-right order) and applied to old columns on request.
+ */
+CTD_API ctd_status ctd_dynamic_step(ctd_factors* state, const ctd_coo3* dX, int64_t d,
+                            double eps, void* stream);
+
+/* ctd_error -- relative error of Eq. (error), ||X~ - X||_F^2 / ||X||_F^2
+ * (the squared ratio), for the tensor the factors were computed from
+ * (CTD-D: all slices so far).  Waits for the work that produced it. */
+CTD_API ctd_status ctd_error(const ctd_factors* F, double* rel_err);
+
+/* Sizes; waits for outstanding work on the factors' stream. */
+CTD_API ctd_status ctd_get_sizes(const ctd_factors* F, ctd_sizes* out);
+
+/* The s draws I (line 3) and the s' unique ones I' ascending (line 4). */
+CTD_API ctd_status ctd_get_samples(const ctd_factors* F, int64_t* I, int64_t* I_unique);
+
+/* Column ids of R's fibers in column order (CTD-D: the slice-local fiber id
+ * of each fiber, and in `step` the time step it came from; step may be NULL). */
+CTD_API ctd_status ctd_get_fibers(const ctd_factors* F, int64_t* fiber, int64_t* step);
+
+/* R as CSC, I_alpha x s~: colptr[s~+1], row[nnz_R] (ascending within a
+ * column), val[nnz_R]. */
+CTD_API ctd_status ctd_get_R(const ctd_factors* F, int64_t* colptr, int32_t* row, int32_t* val);
+
+/* U, s~ x s~, row-major (symmetric). */
+CTD_API ctd_status ctd_get_U(const ctd_factors* F, double* U);
+
+/* Dense columns of C_(alpha): out is s~ x ncols, column-major.
+ * CTD-S: cols are column ids of X_(alpha).  CTD-D: column c of step t is
+ * t * N_slice + f; rows below the step's own block follow Eq. (C_t+1_final). */
+CTD_API ctd_status ctd_get_C_columns(const ctd_factors* F, int64_t ncols, const int64_t* cols,
+                             double* out);
+
+/* CTD-S only: C_(alpha) as CSC with rows ascending: colptr[N_alpha+1],
+ * row[nnz_C], val[nnz_C]. */
+CTD_API ctd_status ctd_get_C(const ctd_factors* F, int64_t* colptr, int32_t* row, double* val);
+
+/* CTD-D: per-step record.  info = {d', Delta d~, d~_t before the step,
+ * nnz of the slice}, sq = {||dX||^2, ||dX - P dX||^2}. */
+CTD_API ctd_status ctd_get_step(const ctd_factors* F, int64_t t, int64_t info[4], double sq[2]);
+
+/* CTD-D: M_{t+1} = ((dR)^T R^(t)) U^(t) of step t, row-major
+ * (Delta d~ x d~_t). */
+CTD_API ctd_status ctd_get_M(const ctd_factors* F, int64_t t, double* M);
+
+CTD_API void ctd_free(ctd_factors* F);
+
+/* Diagnostics (no counterpart in the paper).  ctd_profile(1) clears and
+ * starts per-phase device timing: each phase of a call is bracketed by a
+ * CUDA event pair on the call's stream.  ctd_profile_report waits for the
+ * recorded events and writes a JSON object
+ *   {"launches": L, "phases": {"name": {"ms": total, "calls": n}, ...}}
+ * into buf (NUL-terminated, truncated to len).  L counts every kernel the
+ * library launched since the last ctd_profile call. */
+CTD_API ctd_status ctd_profile(int enable);
+CTD_API ctd_status ctd_profile_report(char* buf, size_t len);
+
+/* Message of the last failing call on this thread ("" if none). */
+CTD_API const char* ctd_last_error(void);
+
+/* Library version string. */
+CTD_API const char* ctd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTD_H */

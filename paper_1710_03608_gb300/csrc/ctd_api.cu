@@ -1,0 +1,647 @@
+// C ABI: allocation, errors, CTD-S (Algorithm 1) orchestration and getters.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+
+#include "ctd_internal.cuh"
+
+namespace ctd {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+ctd_status fail(ctd_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+ctd_status status_from_device(unsigned w) {
+  if (w & DEV_BAD_INDEX) return fail(CTD_EINVAL, "a COO index lies outside its mode's extent");
+  if (w & DEV_OVERFLOW) return fail(CTD_EOVERFLOW, "||X||_F^2 does not fit in 63 bits");
+  if (w & DEV_CAPACITY) return fail(CTD_EINVAL, "a size exceeded its buffer bound");
+  if (w & DEV_TIMEOUT) return fail(CTD_ETIMEOUT, "a bounded device wait gave up");
+  return CTD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// diagnostics: launch counter and phase timers
+// ---------------------------------------------------------------------------
+static std::atomic<long long> g_launches{0};
+static std::mutex g_prof_mu;
+static bool g_prof = false;
+struct PhaseRec {
+  std::string name;
+  cudaEvent_t a, b;
+};
+static std::vector<PhaseRec> g_recs;
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+PhaseScope::PhaseScope(const char* n, cudaStream_t s) : name(n), st(s) {
+  if (!g_prof) return;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    a = b = nullptr;
+    return;
+  }
+  cudaEventRecord(a, st);
+}
+
+PhaseScope::~PhaseScope() {
+  if (!a) return;
+  cudaEventRecord(b, st);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_recs.push_back(PhaseRec{name, a, b});
+}
+
+static void init_pool_once() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;  // keep freed blocks cached in the pool
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  });
+}
+
+ctd_status dalloc(void** p, size_t bytes, cudaStream_t st) {
+  init_pool_once();
+  cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 1, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(CTD_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) +
+                                " bytes failed: " + cudaGetErrorString(e));
+  }
+  return CTD_OK;
+}
+
+void dfree(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+template <typename T>
+static ctd_status d2h(T* host, const T* dev, size_t n, cudaStream_t st) {
+  if (n == 0) return CTD_OK;
+  CTD_CUDA(cudaMemcpyAsync(host, dev, n * sizeof(T), cudaMemcpyDeviceToHost, st));
+  return CTD_OK;
+}
+
+static ctd_status sync(cudaStream_t st) {
+  CTD_CUDA(cudaStreamSynchronize(st));
+  return CTD_OK;
+}
+
+// Validate a COO descriptor; produce device views (copying host inputs in).
+ctd_status stage_coo(const ctd_coo3* X, int alpha, Arena& scratch, cudaStream_t st, CooDev* out) {
+  if (!X) return fail(CTD_EINVAL, "tensor descriptor is NULL");
+  if (alpha < 1 || alpha > 3) return fail(CTD_EINVAL, "alpha must be 1, 2 or 3");
+  for (int d = 0; d < 3; ++d)
+    if (X->dims[d] < 1 || X->dims[d] > INT32_MAX)
+      return fail(CTD_EINVAL, "each dimension must be in [1, 2^31)");
+  if (X->nnz < 0 || X->nnz > INT32_MAX) return fail(CTD_EINVAL, "nnz must be in [0, 2^31)");
+  if (X->nnz > 0 && (!X->i || !X->j || !X->k || !X->val))
+    return fail(CTD_EINVAL, "index or value pointer is NULL");
+  if (X->memory != CTD_MEM_DEVICE && X->memory != CTD_MEM_HOST)
+    return fail(CTD_EINVAL, "unknown memory kind");
+  int64_t n_rows, n_cols;
+  mode_extents(X->dims, alpha, &n_rows, &n_cols);
+  if (n_cols > INT32_MAX) return fail(CTD_EINVAL, "N_alpha must be < 2^31");
+  CooDev c;
+  c.nnz = X->nnz;
+  c.alpha = alpha;
+  for (int d = 0; d < 3; ++d) c.dims[d] = X->dims[d];
+  if (X->memory == CTD_MEM_HOST && X->nnz > 0) {
+    int32_t* buf;
+    CTD_TRY(scratch.get(&buf, 4 * (size_t)X->nnz));
+    const int32_t* src[4] = {X->i, X->j, X->k, X->val};
+    for (int a = 0; a < 4; ++a)
+      CTD_CUDA(cudaMemcpyAsync(buf + a * X->nnz, src[a], X->nnz * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, st));
+    c.i = buf;
+    c.j = buf + X->nnz;
+    c.k = buf + 2 * X->nnz;
+    c.v = buf + 3 * X->nnz;
+  } else {
+    c.i = X->i;
+    c.j = X->j;
+    c.k = X->k;
+    c.v = X->val;
+  }
+  *out = c;
+  return CTD_OK;
+}
+
+// X_(alpha) in both layouts plus its column distribution.
+struct Matricized {
+  int64_t n_rows = 0, n_cols = 0, nnz = 0;
+  uint64_t* cdf = nullptr;      // [n_cols] inclusive prefix of squared norms
+  uint64_t* colptr = nullptr;   // [n_cols+1]
+  uint64_t* rowptr = nullptr;   // [n_rows+1]
+  int32_t* csc_row = nullptr;
+  int32_t* csc_val = nullptr;
+  int32_t* csr_col = nullptr;
+  int32_t* csr_val = nullptr;
+  int* minval = nullptr;
+  unsigned* status = nullptr;
+  uint64_t* tmp = nullptr;
+  CscDev csc() const { return CscDev{colptr, csc_row, csc_val}; }
+  CsrX csr() const { return CsrX{rowptr, csr_col, csr_val}; }
+};
+
+// Algorithm 1 lines 1-2 (and the layouts the later lines read).
+ctd_status matricize(const CooDev& X, bool want_rows, Arena& A, cudaStream_t st, Matricized* M) {
+  mode_extents(X.dims, X.alpha, &M->n_rows, &M->n_cols);
+  M->nnz = X.nnz;
+  uint64_t* norm2;
+  uint32_t *colcnt, *rowcnt;
+  CTD_TRY(A.get(&norm2, M->n_cols));
+  CTD_TRY(A.get(&colcnt, M->n_cols));
+  CTD_TRY(A.get(&rowcnt, M->n_rows));
+  CTD_TRY(A.get(&M->cdf, M->n_cols));
+  CTD_TRY(A.get(&M->colptr, M->n_cols + 1));
+  CTD_TRY(A.get(&M->rowptr, M->n_rows + 1));
+  CTD_TRY(A.get(&M->csc_row, X.nnz));
+  CTD_TRY(A.get(&M->csc_val, X.nnz));
+  if (want_rows) {
+    CTD_TRY(A.get(&M->csr_col, X.nnz));
+    CTD_TRY(A.get(&M->csr_val, X.nnz));
+  }
+  CTD_TRY(A.get(&M->minval, 1));
+  CTD_TRY(A.get(&M->status, 1));
+  CTD_TRY(A.get(&M->tmp, scan_tmp_elems(std::max(M->n_cols, M->n_rows) + 1)));
+  CTD_CUDA(cudaMemsetAsync(norm2, 0, M->n_cols * 8, st));
+  CTD_CUDA(cudaMemsetAsync(colcnt, 0, M->n_cols * 4, st));
+  CTD_CUDA(cudaMemsetAsync(rowcnt, 0, M->n_rows * 4, st));
+  CTD_CUDA(cudaMemsetAsync(M->status, 0, 4, st));
+  const int big = INT32_MAX;
+  CTD_CUDA(cudaMemcpyAsync(M->minval, &big, 4, cudaMemcpyHostToDevice, st));
+  launch_fiber_norms(X, norm2, colcnt, rowcnt, M->minval, M->status, st);
+  launch_scan_u64(norm2, M->cdf, M->n_cols, true, M->tmp, M->status, st);
+  launch_scan_u32(colcnt, M->colptr, M->n_cols, false, M->tmp, M->status, st);
+  launch_scan_u32(rowcnt, M->rowptr, M->n_rows, false, M->tmp, M->status, st);
+  // cursors: reuse norm2 (n_cols u64) for columns; a fresh array for rows
+  uint64_t* rowcur = nullptr;
+  launch_copy_u64(M->colptr, norm2, M->n_cols, st);
+  if (want_rows) {
+    CTD_TRY(A.get(&rowcur, M->n_rows));
+    launch_copy_u64(M->rowptr, rowcur, M->n_rows, st);
+  }
+  launch_coo_scatter(X, norm2, rowcur, M->csc_row, M->csc_val, M->csr_col, M->csr_val, st);
+  CTD_CUDA(cudaGetLastError());
+  return CTD_OK;
+}
+
+
+}  // namespace ctd
+
+using namespace ctd;
+
+// ---------------------------------------------------------------------------
+// CTD-S
+// ---------------------------------------------------------------------------
+extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, double eps,
+                                 uint64_t seed, int precision, unsigned flags, void* stream,
+                                 ctd_factors** out) {
+  if (!out) return fail(CTD_EINVAL, "out is NULL");
+  if (s < 1 || s > 8192) return fail(CTD_EINVAL, "s must be in [1, 8192]");
+  if (!(eps >= 0.0 && eps < 1.0)) return fail(CTD_EINVAL, "eps must be in [0, 1)");
+  if (precision != CTD_FP64 && precision != CTD_FP32_BULK)
+    return fail(CTD_EINVAL, "unknown precision");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Arena scratch;
+  scratch.st = st;
+  CooDev X;
+  CTD_TRY(stage_coo(Xd, alpha, scratch, st, &X));
+
+  ctd_factors* F = new ctd_factors();
+  F->mem.st = st;
+  F->kind = 0;
+  F->alpha = alpha;
+  F->precision = precision;
+  F->stream = st;
+  F->seed = seed;
+  for (int d = 0; d < 3; ++d) F->dims[d] = Xd->dims[d];
+  F->nnz_X = X.nnz;
+  F->s = s;
+  auto bail = [&](ctd_status rc) {
+    cudaStreamSynchronize(st);
+    delete F;
+    return rc;
+  };
+#define STEP(expr)                     \
+  do {                                 \
+    ctd_status _r = (expr);            \
+    if (_r != CTD_OK) return bail(_r); \
+  } while (0)
+#define STEPC(call)                                                                   \
+  do {                                                                                \
+    cudaError_t _e = (call);                                                          \
+    if (_e != cudaSuccess)                                                            \
+      return bail(fail(CTD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e))); \
+  } while (0)
+
+  // lines 1-2
+  Matricized M;
+  {
+    PhaseScope ph("matricize", st);
+    STEP(matricize(X, !(flags & CTD_SKIP_ERROR), scratch, st, &M));
+  }
+  F->n_rows = M.n_rows;
+  F->n_cols = M.n_cols;
+  // line 3: draws; line 4: unique
+  STEP(F->mem.get(&F->I, s));
+  STEP(F->mem.get(&F->Iu, s));
+  int* d_count;
+  STEP(scratch.get(&d_count, 4));
+  {
+    PhaseScope ph("sample_unique", st);
+    launch_sample(M.cdf, M.n_cols, s, seed, 0, 0, F->I, st);
+    launch_sort_unique(F->I, s, F->Iu, d_count, st);
+  }
+  STEPC(cudaGetLastError());
+  unsigned status = 0;
+  int minval = 0, s_unique = 0;
+  uint64_t T = 0;
+  STEP(d2h(&status, M.status, 1, st));
+  STEP(d2h(&minval, M.minval, 1, st));
+  STEP(d2h(&s_unique, d_count, 1, st));
+  if (M.n_cols > 0) STEP(d2h(&T, M.cdf + (M.n_cols - 1), 1, st));
+  STEP(sync(st));
+  STEP(status_from_device(status));
+  F->T = T;
+  F->s_unique = s_unique;
+  if (T == 0) F->s = 0;  // nothing to draw from
+  const int su = s_unique;
+  const bool may_cancel = minval < 0;
+
+  // candidate columns R' (CSC) and their row-major copy
+  uint64_t *rc_ptr, *rc_sizes;
+  STEP(scratch.get(&rc_sizes, su + 1));
+  STEP(scratch.get(&rc_ptr, su + 1));
+  launch_column_sizes(M.colptr, F->Iu, d_count, su, rc_sizes, st);
+  launch_scan_u64(rc_sizes, rc_ptr, su, false, M.tmp, M.status, st);
+  uint64_t nnz_cand = 0;
+  STEP(d2h(&nnz_cand, rc_ptr + su, 1, st));
+  STEP(sync(st));
+  int32_t *rc_row, *rc_val, *rcr_col, *rcr_val;
+  uint64_t* rcr_ptr;
+  STEP(scratch.get(&rc_row, nnz_cand));
+  STEP(scratch.get(&rc_val, nnz_cand));
+  STEP(scratch.get(&rcr_col, nnz_cand));
+  STEP(scratch.get(&rcr_val, nnz_cand));
+  STEP(scratch.get(&rcr_ptr, M.n_rows + 1));
+  launch_gather_columns(M.colptr, M.csc_row, M.csc_val, F->Iu, d_count, su, rc_ptr, rc_row,
+                        rc_val, st);
+  STEP(build_csr_from_csc(rc_ptr, rc_row, rc_val, su, nnz_cand, M.n_rows, 0, rcr_ptr, rcr_col,
+                          rcr_val, scratch, st));
+
+  // lines 5-15: Gram matrix, in-order Cholesky with skip
+  double *G, *thr;
+  int *keep, *idx;
+  STEP(scratch.get(&G, (size_t)su * su));
+  STEP(scratch.get(&thr, su));
+  STEP(scratch.get(&keep, su));
+  STEP(scratch.get(&idx, su));
+  CsrDev Rc{rcr_ptr, rcr_col, rcr_val, su};
+  {
+    PhaseScope ph("gram", st);
+    STEP(launch_spmm_dense(M.csc(), F->Iu, d_count, su, Rc, G, su, st));
+  }
+  {
+    PhaseScope ph("filter_chol", st);
+    launch_thresholds(G, su, su, eps * eps, thr, st);
+    launch_chol_skip(G, su, su, thr, keep, st);
+    launch_compact_flags(keep, su, idx, d_count + 1, st);
+  }
+  int kept = 0;
+  STEP(d2h(&kept, d_count + 1, 1, st));
+  STEPC(cudaGetLastError());
+  STEP(sync(st));
+  F->s_kept = kept;
+
+  // U = (R^T R)^{-1} = L^{-T} L^{-1}
+  double *L, *Z;
+  STEP(scratch.get(&L, (size_t)kept * kept));
+  STEP(scratch.get(&Z, (size_t)kept * kept));
+  STEP(F->mem.get(&F->U, (size_t)kept * kept));
+  {
+    PhaseScope ph("u_inverse", st);
+    launch_gather_lower(G, su, idx, d_count + 1, kept, L, kept, st);
+    tri_inverse(L, kept, kept, Z, kept, st);
+    u_from_linv(Z, kept, kept, F->U, kept, st);
+  }
+
+  // R: kept columns of R', CSC and row-major
+  STEP(F->mem.get(&F->kept_pos, kept));
+  STEP(F->mem.get(&F->fibers, kept));
+  STEPC(cudaMemcpyAsync(F->kept_pos, idx, kept * sizeof(int), cudaMemcpyDeviceToDevice, st));
+  launch_gather_i64(F->Iu, idx, d_count + 1, kept, F->fibers, st);
+  uint64_t* r_sizes;
+  STEP(scratch.get(&r_sizes, kept + 1));
+  STEP(F->mem.get(&F->Rcolptr, kept + 1));
+  launch_column_sizes(M.colptr, F->fibers, d_count + 1, kept, r_sizes, st);
+  launch_scan_u64(r_sizes, F->Rcolptr, kept, false, M.tmp, M.status, st);
+  uint64_t nnzR = 0;
+  STEP(d2h(&nnzR, F->Rcolptr + kept, 1, st));
+  STEP(sync(st));
+  F->nnz_R = (int64_t)nnzR;
+  STEP(F->mem.get(&F->Rrow, nnzR));
+  STEP(F->mem.get(&F->Rval, nnzR));
+  STEP(F->mem.get(&F->Rrowptr, M.n_rows + 1));
+  STEP(F->mem.get(&F->Rcol, nnzR));
+  STEP(F->mem.get(&F->Rcval, nnzR));
+  launch_gather_columns(M.colptr, M.csc_row, M.csc_val, F->fibers, d_count + 1, kept, F->Rcolptr,
+                        F->Rrow, F->Rval, st);
+  STEP(build_csr_from_csc(F->Rcolptr, F->Rrow, F->Rval, kept, (int64_t)nnzR, M.n_rows, 0,
+                          F->Rrowptr, F->Rcol, F->Rcval, scratch, st));
+  CsrDev R{F->Rrowptr, F->Rcol, F->Rcval, kept};
+
+  // line 16: C = R^T X_(alpha)
+  if (!(flags & CTD_SKIP_C)) {
+    uint32_t* ub;
+    STEP(scratch.get(&ub, M.n_cols));
+    STEP(F->mem.get(&F->Coff, M.n_cols + 1));
+    STEP(F->mem.get(&F->Ccnt, M.n_cols));
+    {
+      PhaseScope ph("c_bounds", st);
+      launch_c_bounds(M.csc(), M.n_cols, R, ub, st);
+      launch_scan_u32(ub, F->Coff, M.n_cols, false, M.tmp, M.status, st);
+    }
+    uint64_t cap = 0;
+    STEP(d2h(&cap, F->Coff + M.n_cols, 1, st));
+    STEP(sync(st));
+    F->C_cap = cap;
+    STEP(F->mem.get(&F->Crow, cap));
+    const size_t vsz = precision == CTD_FP32_BULK ? 4 : 8;
+    void* cv = nullptr;
+    STEP(dalloc(&cv, (cap ? cap : 1) * vsz, st));
+    F->mem.ptrs.push_back(cv);
+    F->Cval = cv;
+    PhaseScope ph("c_fill", st);
+    STEP(launch_c_fill(M.csc(), M.n_cols, R, F->Coff, F->Ccnt, F->Crow, F->Cval,
+                       precision == CTD_FP32_BULK, may_cancel, st));
+  }
+
+  // Eq. (error): e = (T - <U, R^T X X^T R>) / T
+  double* d_pu = nullptr;
+  if (!(flags & CTD_SKIP_ERROR)) {
+    long long* CCt;
+    STEP(scratch.get(&CCt, (size_t)kept * kept));
+    STEP(scratch.get(&d_pu, 1));
+    STEPC(cudaMemsetAsync(CCt, 0, (size_t)kept * kept * 8, st));
+    STEPC(cudaMemsetAsync(d_pu, 0, 8, st));
+    PhaseScope ph("error_gram", st);
+    STEP(launch_gram_hform(M.csr(), M.csc(), M.n_rows, R, CCt, scratch, st));
+    if (kept > 0) launch_frob_dot(F->U, CCt, kept, d_pu, st);
+  }
+  uint64_t* d_nnzc;
+  STEP(scratch.get(&d_nnzc, 1));
+  if (F->Ccnt) launch_sum_u32(F->Ccnt, M.n_cols, d_nnzc, st);
+  uint64_t nnzC = 0;
+  double pu = 0.0;
+  if (F->Ccnt) STEP(d2h(&nnzC, d_nnzc, 1, st));
+  if (d_pu) STEP(d2h(&pu, d_pu, 1, st));
+  STEP(d2h(&status, M.status, 1, st));
+  STEPC(cudaGetLastError());
+  STEP(sync(st));
+  STEP(status_from_device(status));
+  F->nnz_C = (int64_t)nnzC;
+  if (d_pu) {
+    F->have_err = true;
+    F->err = T ? ((double)T - pu) / (double)T : 0.0;
+  }
+  *out = F;
+#undef STEP
+#undef STEPC
+  return CTD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// getters
+// ---------------------------------------------------------------------------
+extern "C" ctd_status ctd_error(const ctd_factors* F, double* rel_err) {
+  if (!F || !rel_err) return fail(CTD_EINVAL, "NULL argument");
+  if (!F->have_err) return fail(CTD_EINVAL, "the error was not computed (CTD_SKIP_ERROR)");
+  *rel_err = F->err;
+  return CTD_OK;
+}
+
+extern "C" ctd_status ctd_get_sizes(const ctd_factors* F, ctd_sizes* o) {
+  if (!F || !o) return fail(CTD_EINVAL, "NULL argument");
+  CTD_TRY(sync(F->stream));
+  o->n_rows = F->n_rows;
+  o->n_cols = F->n_cols;
+  o->s_draws = F->s;
+  o->s_unique = F->s_unique;
+  o->s_kept = F->s_kept;
+  o->nnz_R = F->nnz_R;
+  o->nnz_C = F->nnz_C;
+  o->t_steps = 0;
+  o->nnz_X = F->nnz_X;
+  o->sqnorm_X = (double)F->T;
+  return CTD_OK;
+}
+
+extern "C" ctd_status ctd_get_samples(const ctd_factors* F, int64_t* I, int64_t* Iu) {
+  if (!F) return fail(CTD_EINVAL, "NULL argument");
+  if (I) CTD_TRY(d2h(I, F->I, (size_t)F->s, F->stream));
+  if (Iu) CTD_TRY(d2h(Iu, F->Iu, (size_t)F->s_unique, F->stream));
+  return sync(F->stream);
+}
+
+extern "C" ctd_status ctd_get_fibers(const ctd_factors* F, int64_t* fiber, int64_t* step) {
+  if (!F) return fail(CTD_EINVAL, "NULL argument");
+  if (F->kind != 0) return fail(CTD_ENOTSUP, "use the dynamic getters");
+  if (fiber) CTD_TRY(d2h(fiber, F->fibers, (size_t)F->s_kept, F->stream));
+  CTD_TRY(sync(F->stream));
+  if (step)
+    for (int64_t c = 0; c < F->s_kept; ++c) step[c] = 0;
+  return CTD_OK;
+}
+
+// Copy a device CSC (s~ columns) to host and sort rows within columns.
+static ctd_status csc_to_host_sorted(const uint64_t* dptr, const int32_t* drow, const int32_t* dval,
+                                     int64_t ncols, int64_t nnz, cudaStream_t st,
+                                     int64_t* colptr, int32_t* row, int32_t* val) {
+  std::vector<uint64_t> p(ncols + 1);
+  std::vector<int32_t> r(nnz), v(nnz);
+  CTD_TRY(d2h(p.data(), dptr, ncols + 1, st));
+  CTD_TRY(d2h(r.data(), drow, nnz, st));
+  CTD_TRY(d2h(v.data(), dval, nnz, st));
+  CTD_TRY(sync(st));
+  std::vector<int64_t> ord;
+  for (int64_t c = 0; c < ncols; ++c) {
+    const int64_t a = (int64_t)p[c], b = (int64_t)p[c + 1];
+    ord.resize(b - a);
+    std::iota(ord.begin(), ord.end(), a);
+    std::sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return r[x] < r[y]; });
+    for (int64_t q = a; q < b; ++q) {
+      row[q] = r[ord[q - a]];
+      val[q] = v[ord[q - a]];
+    }
+    colptr[c] = a;
+  }
+  colptr[ncols] = (int64_t)p[ncols];
+  return CTD_OK;
+}
+
+extern "C" ctd_status ctd_get_R(const ctd_factors* F, int64_t* colptr, int32_t* row,
+                                int32_t* val) {
+  if (!F || !colptr || (F->nnz_R && (!row || !val))) return fail(CTD_EINVAL, "NULL argument");
+  if (F->kind != 0) return fail(CTD_ENOTSUP, "use the dynamic getters");
+  return csc_to_host_sorted(F->Rcolptr, F->Rrow, F->Rval, F->s_kept, F->nnz_R, F->stream, colptr,
+                            row, val);
+}
+
+extern "C" ctd_status ctd_get_U(const ctd_factors* F, double* U) {
+  if (!F || (!U && F->s_kept)) return fail(CTD_EINVAL, "NULL argument");
+  if (F->kind != 0) return fail(CTD_ENOTSUP, "use the dynamic getters");
+  CTD_TRY(d2h(U, F->U, (size_t)F->s_kept * F->s_kept, F->stream));
+  return sync(F->stream);
+}
+
+namespace ctd {
+template <typename V>
+__global__ void k_c_columns(const unsigned long long* __restrict__ coff,
+                            const unsigned* __restrict__ ccnt, const int32_t* __restrict__ crow,
+                            const V* __restrict__ cval, const int64_t* __restrict__ cols,
+                            int64_t ncols, int64_t height, double* __restrict__ out) {
+  for (int64_t c = blockIdx.x; c < ncols; c += gridDim.x) {
+    const int64_t f = cols[c];
+    const unsigned long long o = coff[f];
+    const unsigned n = ccnt[f];
+    for (unsigned q = threadIdx.x; q < n; q += blockDim.x)
+      out[c * height + crow[o + q]] = (double)cval[o + q];
+  }
+}
+}  // namespace ctd
+
+extern "C" ctd_status ctd_get_C_columns(const ctd_factors* F, int64_t ncols, const int64_t* cols,
+                                        double* out) {
+  if (!F || ncols < 0 || (ncols && (!cols || !out))) return fail(CTD_EINVAL, "NULL argument");
+  if (F->kind != 0) return fail(CTD_ENOTSUP, "use the dynamic getters");
+  if (!F->Coff) return fail(CTD_EINVAL, "C was not materialized (CTD_SKIP_C)");
+  for (int64_t c = 0; c < ncols; ++c)
+    if (cols[c] < 0 || cols[c] >= F->n_cols) return fail(CTD_EINVAL, "column out of range");
+  const int64_t h = F->s_kept;
+  if (ncols == 0 || h == 0) {
+    std::fill(out, out + ncols * h, 0.0);
+    return CTD_OK;
+  }
+  cudaStream_t st = F->stream;
+  Arena a;
+  a.st = st;
+  int64_t* dcols;
+  double* dout;
+  CTD_TRY(a.get(&dcols, ncols));
+  CTD_TRY(a.get(&dout, (size_t)ncols * h));
+  CTD_CUDA(cudaMemcpyAsync(dcols, cols, ncols * 8, cudaMemcpyHostToDevice, st));
+  CTD_CUDA(cudaMemsetAsync(dout, 0, (size_t)ncols * h * 8, st));
+  const unsigned g = grid_for(ncols, 1, 4096);
+  if (F->precision == CTD_FP32_BULK)
+    CTD_LAUNCH(k_c_columns<float>, (g), (128), 0, st, reinterpret_cast<const unsigned long long*>(F->Coff),
+                                          F->Ccnt, F->Crow, static_cast<const float*>(F->Cval),
+                                          dcols, ncols, h, dout);
+  else
+    CTD_LAUNCH(k_c_columns<double>, (g), (128), 0, st, reinterpret_cast<const unsigned long long*>(F->Coff),
+                                           F->Ccnt, F->Crow, static_cast<const double*>(F->Cval),
+                                           dcols, ncols, h, dout);
+  CTD_CUDA(cudaGetLastError());
+  CTD_TRY(d2h(out, dout, (size_t)ncols * h, st));
+  return sync(st);
+}
+
+extern "C" ctd_status ctd_get_C(const ctd_factors* F, int64_t* colptr, int32_t* row, double* val) {
+  if (!F || !colptr) return fail(CTD_EINVAL, "NULL argument");
+  if (F->kind != 0) return fail(CTD_ENOTSUP, "CTD-D keeps C implicit; use ctd_get_C_columns");
+  if (!F->Coff) return fail(CTD_EINVAL, "C was not materialized (CTD_SKIP_C)");
+  cudaStream_t st = F->stream;
+  const int64_t n = F->n_cols;
+  std::vector<uint64_t> off(n + 1);
+  std::vector<uint32_t> cnt(n);
+  std::vector<int32_t> r(F->C_cap);
+  CTD_TRY(d2h(off.data(), F->Coff, n + 1, st));
+  CTD_TRY(d2h(cnt.data(), F->Ccnt, n, st));
+  CTD_TRY(d2h(r.data(), F->Crow, F->C_cap, st));
+  std::vector<double> v(F->C_cap);
+  if (F->precision == CTD_FP32_BULK) {
+    std::vector<float> vf(F->C_cap);
+    CTD_TRY(d2h(vf.data(), static_cast<const float*>(F->Cval), F->C_cap, st));
+    CTD_TRY(sync(st));
+    for (size_t q = 0; q < vf.size(); ++q) v[q] = vf[q];
+  } else {
+    CTD_TRY(d2h(v.data(), static_cast<const double*>(F->Cval), F->C_cap, st));
+    CTD_TRY(sync(st));
+  }
+  int64_t pos = 0;
+  for (int64_t f = 0; f < n; ++f) {
+    colptr[f] = pos;
+    for (uint32_t q = 0; q < cnt[f]; ++q) {
+      if (row) row[pos] = r[off[f] + q];
+      if (val) val[pos] = v[off[f] + q];
+      ++pos;
+    }
+  }
+  colptr[n] = pos;
+  return CTD_OK;
+}
+
+extern "C" void ctd_free(ctd_factors* F) {
+  if (!F) return;
+  cudaStreamSynchronize(F->stream);
+  delete F;
+}
+
+extern "C" ctd_status ctd_profile(int enable) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& r : g_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_recs.clear();
+  g_launches.store(0);
+  g_prof = enable != 0;
+  return CTD_OK;
+}
+
+extern "C" ctd_status ctd_profile_report(char* buf, size_t len) {
+  if (!buf || len == 0) return fail(CTD_EINVAL, "NULL buffer");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  std::vector<std::string> names;
+  std::vector<double> ms;
+  std::vector<long long> calls;
+  for (auto& r : g_recs) {
+    CTD_CUDA(cudaEventSynchronize(r.b));
+    float t = 0.f;
+    CTD_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+    size_t q = 0;
+    while (q < names.size() && names[q] != r.name) ++q;
+    if (q == names.size()) {
+      names.push_back(r.name);
+      ms.push_back(0.0);
+      calls.push_back(0);
+    }
+    ms[q] += t;
+    calls[q] += 1;
+  }
+  std::string js = "{\"launches\": " + std::to_string(g_launches.load()) + ", \"phases\": {";
+  for (size_t q = 0; q < names.size(); ++q) {
+    char item[256];
+    snprintf(item, sizeof(item), "%s\"%s\": {\"ms\": %.6f, \"calls\": %lld}", q ? ", " : "",
+             names[q].c_str(), ms[q], calls[q]);
+    js += item;
+  }
+  js += "}}";
+  snprintf(buf, len, "%s", js.c_str());
+  return CTD_OK;
+}
+
+extern "C" const char* ctd_last_error(void) { return ctd::g_last_error.c_str(); }
+
+extern "C" const char* ctd_version(void) { return "ctd-gb300 0.1 (sm_103a)"; }

@@ -1,0 +1,297 @@
+// Internal declarations shared by the CTD CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "ctd.h"
+
+namespace ctd {
+
+// ---------------------------------------------------------------------------
+// status / errors
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+ctd_status fail(ctd_status st, const std::string& msg);
+
+#define CTD_CUDA(call)                                                        \
+  do {                                                                        \
+    cudaError_t _e = (call);                                                  \
+    if (_e != cudaSuccess) {                                                  \
+      return ::ctd::fail(_e == cudaErrorMemoryAllocation ? CTD_ENOMEM         \
+                                                         : CTD_ECUDA,         \
+                         std::string(#call) + ": " + cudaGetErrorString(_e)); \
+    }                                                                         \
+  } while (0)
+
+#define CTD_TRY(expr)                     \
+  do {                                    \
+    ctd_status _s = (expr);               \
+    if (_s != CTD_OK) return _s;          \
+  } while (0)
+
+// Every kernel launch goes through CTD_LAUNCH so the library can report how
+// many kernels it started (a diagnostic, see ctd_profile_report).
+void note_launch();
+#define CTD_LAUNCH(kern, grid, block, smem, st, ...) \
+  do {                                               \
+    ::ctd::note_launch();                            \
+    kern<<<grid, block, smem, st>>>(__VA_ARGS__);    \
+  } while (0)
+
+// Device-time phase timer: records a CUDA event pair on `st` around a scope
+// when profiling is on (ctd_profile(1)); no-op otherwise.
+struct PhaseScope {
+  PhaseScope(const char* name, cudaStream_t st);
+  ~PhaseScope();
+  const char* name;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+};
+
+// Bits of the device status word every pipeline carries.
+enum : unsigned {
+  DEV_BAD_INDEX = 1u,   // a COO index outside its mode's extent
+  DEV_OVERFLOW = 2u,    // an exact sum left its integer range
+  DEV_CAPACITY = 4u,    // a size exceeded a buffer bound
+  DEV_TIMEOUT = 8u      // a bounded wait gave up
+};
+ctd_status status_from_device(unsigned word);
+
+// ---------------------------------------------------------------------------
+// stream-ordered device memory
+// ---------------------------------------------------------------------------
+ctd_status dalloc(void** p, size_t bytes, cudaStream_t st);
+void dfree(void* p, cudaStream_t st);
+
+template <typename T>
+ctd_status dalloc_n(T** p, size_t n, cudaStream_t st) {
+  return dalloc(reinterpret_cast<void**>(p), n * sizeof(T), st);
+}
+
+// A list of device allocations freed together.
+struct Arena {
+  std::vector<void*> ptrs;
+  cudaStream_t st = nullptr;
+  template <typename T>
+  ctd_status get(T** p, size_t n) {
+    void* q = nullptr;
+    CTD_TRY(dalloc(&q, (n ? n : 1) * sizeof(T), st));
+    ptrs.push_back(q);
+    *p = static_cast<T*>(q);
+    return CTD_OK;
+  }
+  void release() {
+    for (void* q : ptrs) dfree(q, st);
+    ptrs.clear();
+  }
+  ~Arena() { release(); }
+};
+
+inline int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+inline unsigned grid_for(int64_t work, int per_block, int64_t cap) {
+  int64_t g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return static_cast<unsigned>(g);
+}
+
+// ---------------------------------------------------------------------------
+// kernel launchers (one translation unit each)
+// ---------------------------------------------------------------------------
+
+// ctd_stream.cu ------------------------------------------------------------
+struct CooDev {
+  const int32_t* i;
+  const int32_t* j;
+  const int32_t* k;
+  const int32_t* v;
+  int64_t nnz;
+  int64_t dims[3];
+  int alpha;  // 1..3
+};
+
+// Mode-alpha row extent and column count.
+void mode_extents(const int64_t dims[3], int alpha, int64_t* n_rows, int64_t* n_cols);
+
+// K1: squared column norms (exact u64), per-column and per-row counts.
+// norm2/colcnt/rowcnt must be zeroed.  Also reduces min(value) into
+// *minval (initialize to INT32_MAX).
+void launch_fiber_norms(const CooDev& X, uint64_t* norm2, uint32_t* colcnt,
+                        uint32_t* rowcnt, int* minval, unsigned* status,
+                        cudaStream_t st);
+
+// K2: prefix sums.  out[n] (inclusive) or out[n+1] (exclusive, out[0]=0).
+// `tmp` needs scan_tmp_elems(n) entries.  *overflow_flag gets DEV_OVERFLOW
+// when the running double sum passes 2^63.
+size_t scan_tmp_elems(int64_t n);
+void launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, bool inclusive,
+                     uint64_t* tmp, unsigned* status, cudaStream_t st);
+void launch_scan_u32(const uint32_t* in, uint64_t* out, int64_t n, bool inclusive,
+                     uint64_t* tmp, unsigned* status, cudaStream_t st);
+
+// K5a: counting-sort scatter of the COO into column-major (CSC: row, val)
+// and row-major (CSR: col, val) layouts.  colcur/rowcur start as copies of
+// the exclusive offsets and are consumed.
+void launch_coo_scatter(const CooDev& X, uint64_t* colcur, uint64_t* rowcur,
+                        int32_t* csc_row, int32_t* csc_val, int32_t* csr_col,
+                        int32_t* csr_val, cudaStream_t st);
+
+// Copy u64 -> u64 (cursor initialization) for n elements.
+void launch_copy_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t st);
+// out[0] = sum of n u32 values (as u64).
+void launch_sum_u32(const uint32_t* in, int64_t n, uint64_t* out, cudaStream_t st);
+// out[c] = in[idx[c]] for c < *count.
+void launch_gather_i64(const int64_t* in, const int* idx, const int* count, int nmax,
+                       int64_t* out, cudaStream_t st);
+
+// K5b: gather columns `fibers[0..nf)` of a CSC matrix into a compact CSC
+// (colptr_out[nf+1] must already hold the exclusive sizes).
+void launch_column_sizes(const uint64_t* colptr, const int64_t* fibers, const int* nf_dev,
+                         int nf_max, uint64_t* sizes, cudaStream_t st);
+void launch_gather_columns(const uint64_t* colptr, const int32_t* row, const int32_t* val,
+                           const int64_t* fibers, const int* nf_dev, int nf_max,
+                           const uint64_t* colptr_out, int32_t* row_out, int32_t* val_out,
+                           cudaStream_t st);
+
+// Build a row-major copy (rowptr over n_rows, col, val) of a small CSC with
+// ncols columns whose column c gets index col_base + c.  rowcnt must be
+// zeroed (n_rows entries), `tmp` as for scans.
+ctd_status build_csr_from_csc(const uint64_t* colptr, const int32_t* row, const int32_t* val,
+                              int64_t ncols, int64_t nnz, int64_t n_rows, int col_base,
+                              uint64_t* rowptr_out, int32_t* col_out, int32_t* val_out,
+                              Arena& scratch, cudaStream_t st);
+
+// ctd_sample.cu ------------------------------------------------------------
+// K3: s draws.  total = cdf[n-1] (read on device).
+void launch_sample(const uint64_t* cdf, int64_t n, int64_t s, uint64_t seed,
+                   uint64_t step, uint64_t stream_id, int64_t* out, cudaStream_t st);
+// K4: ascending unique of s values (s <= 8192); writes out[0..s') and *count.
+void launch_sort_unique(const int64_t* in, int64_t s, int64_t* out, int* count,
+                        cudaStream_t st);
+
+// ctd_spmm.cu --------------------------------------------------------------
+struct CscDev {        // X_(alpha) by column
+  const uint64_t* colptr;
+  const int32_t* row;
+  const int32_t* val;
+};
+struct CsrDev {        // a factor by row: row i holds (col, val) pairs
+  const uint64_t* rowptr;
+  const int32_t* col;
+  const int32_t* val;
+  int width;           // number of columns
+};
+
+// Dense products: out(:, c) = R^T x_{fibers[c]} for c < nf (column-major,
+// leading dimension ld), exact integer sums stored as double.
+ctd_status launch_spmm_dense(const CscDev& X, const int64_t* fibers, const int* nf_dev,
+                             int nf_max, const CsrDev& R, double* out, int64_t ld,
+                             cudaStream_t st);
+
+// Sparse product C = R^T X_(alpha) over all n_cols columns.
+// bounds: ub[f] = min(width, sum of R row lengths over column f).
+void launch_c_bounds(const CscDev& X, int64_t n_cols, const CsrDev& R, uint32_t* ub,
+                     cudaStream_t st);
+// fill: column f's entries go to [coff[f], coff[f] + ccnt[f]) with rows
+// ascending.  Values stored as float (fp32 != 0) or double.
+ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, const CsrDev& R,
+                         const uint64_t* coff, uint32_t* ccnt, int32_t* crow, void* cval,
+                         int fp32, int may_cancel, cudaStream_t st);
+
+// Relative-error numerator via Gram form: CCt = R^T (X X^T) R (exact int64,
+// width x width, column-major, must be zeroed).
+struct CsrX {          // X_(alpha) by row: row i holds (col, val)
+  const uint64_t* rowptr;
+  const int32_t* col;
+  const int32_t* val;
+};
+ctd_status launch_gram_hform(const CsrX& Xr, const CscDev& Xc, int64_t n_rows,
+                             const CsrDev& R, long long* CCt, Arena& scratch,
+                             cudaStream_t st);
+// out[0] = sum_{a,b} U[a,b] * CCt[a,b]  (FP64).
+void launch_frob_dot(const double* U, const long long* CCt, int64_t n, double* out,
+                     cudaStream_t st);
+
+// ctd_dense.cu -------------------------------------------------------------
+// C = alpha op(A) op(B) + beta C, column-major FP64.
+void dgemm(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+           int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+           cudaStream_t st);
+// In-order Cholesky with skip on the n x n SPD-or-singular matrix A
+// (column-major, lower triangle used).  Column k is kept iff its Schur
+// diagonal exceeds thr[k].  Kept columns hold L, skipped ones are zeroed.
+// keep[k] in {0,1}.
+void launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr, int* keep,
+                      cudaStream_t st);
+// idx[0..count) = positions k with keep[k] != 0 (ascending); *count on device.
+void launch_compact_flags(const int* keep, int n, int* idx, int* count, cudaStream_t st);
+// B (nk x nk) = A[idx, idx] for the lower triangle (upper zeroed).
+void launch_gather_lower(const double* A, int64_t lda, const int* idx, const int* count_dev,
+                         int nk_max, double* B, int64_t ldb, cudaStream_t st);
+// Z = L^{-1} for lower-triangular L (n x n), in place into Z (Z != L).
+void tri_inverse(const double* L, int64_t ldl, int64_t n, double* Z, int64_t ldz,
+                 cudaStream_t st);
+// U = Z^T Z (symmetric, full) for lower-triangular Z.
+void u_from_linv(const double* Z, int64_t n, int64_t ldz, double* U, int64_t ldu,
+                 cudaStream_t st);
+// Zero a column-major m x n matrix.
+void launch_zero_f64(double* A, int64_t m, int64_t n, int64_t lda, cudaStream_t st);
+// Copy lower triangle into upper (symmetrize).
+void launch_symmetrize(double* A, int64_t n, int64_t lda, cudaStream_t st);
+// thr[k] = eps^2 * diag[k] for the n diagonal entries of D (stride ldd+1).
+void launch_thresholds(const double* D, int64_t n, int64_t ldd, double eps2, double* thr,
+                       cudaStream_t st);
+
+}  // namespace ctd
+
+// The library-owned factors.
+struct ctd_factors {
+  int kind = 0;          // 0 = CTD-S, 1 = CTD-D
+  int alpha = 1;
+  int precision = 0;
+  cudaStream_t stream = nullptr;
+  int64_t dims[3] = {0, 0, 0};
+  int64_t n_rows = 0, n_cols = 0;
+  uint64_t seed = 0, stream_id = 0;
+  // sizes
+  int64_t s = 0, s_unique = 0, s_kept = 0, nnz_R = 0, nnz_C = 0, nnz_X = 0;
+  uint64_t T = 0;
+  double err = 0.0;
+  bool have_err = false;
+  // device arrays (owned)
+  ctd::Arena mem;
+  int64_t* I = nullptr;          // [s]
+  int64_t* Iu = nullptr;         // [s']
+  int64_t* fibers = nullptr;     // [s~]
+  int* kept_pos = nullptr;       // [s~] positions in I'
+  uint64_t* Rcolptr = nullptr;   // [s~+1]
+  int32_t* Rrow = nullptr;
+  int32_t* Rval = nullptr;
+  uint64_t* Rrowptr = nullptr;   // [n_rows+1]
+  int32_t* Rcol = nullptr;
+  int32_t* Rcval = nullptr;
+  double* U = nullptr;           // s~ x s~ column-major (symmetric)
+  uint64_t* Coff = nullptr;      // [n_cols+1]
+  uint32_t* Ccnt = nullptr;      // [n_cols]
+  int32_t* Crow = nullptr;
+  void* Cval = nullptr;          // float or double
+  uint64_t C_cap = 0;
+  // CTD-D extras live in ctd_dynamic.cu
+  struct Dyn;
+  Dyn* dyn = nullptr;
+};

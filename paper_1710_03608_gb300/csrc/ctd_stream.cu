@@ -1,0 +1,444 @@
+// Streaming passes over the COO input: squared column norms (Algorithm 1
+// line 2 / Eq. 1), prefix sums (the column distribution's CDF and the
+// counting-sort offsets), the counting-sort scatter into column- and
+// row-major layouts (the matricization of line 1), and column gathers.
+#include "ctd_internal.cuh"
+
+namespace ctd {
+
+void mode_extents(const int64_t dims[3], int alpha, int64_t* n_rows, int64_t* n_cols) {
+  if (alpha == 1) {
+    *n_rows = dims[0];
+    *n_cols = dims[1] * dims[2];
+  } else if (alpha == 2) {
+    *n_rows = dims[1];
+    *n_cols = dims[0] * dims[2];
+  } else {
+    *n_rows = dims[2];
+    *n_cols = dims[0] * dims[1];
+  }
+}
+
+// Row (mode-alpha index) and little-endian column of one nonzero.
+struct ModeMap {
+  int alpha;
+  int64_t I, J, K;
+  __device__ __forceinline__ bool map(int32_t a, int32_t b, int32_t c, int32_t* row,
+                                      int64_t* col) const {
+    if (a < 0 || b < 0 || c < 0 || a >= I || b >= J || c >= K) return false;
+    if (alpha == 1) {
+      *row = a;
+      *col = (int64_t)b + J * (int64_t)c;
+    } else if (alpha == 2) {
+      *row = b;
+      *col = (int64_t)a + I * (int64_t)c;
+    } else {
+      *row = c;
+      *col = (int64_t)a + I * (int64_t)b;
+    }
+    return true;
+  }
+};
+
+static ModeMap make_map(const CooDev& X) {
+  ModeMap m;
+  m.alpha = X.alpha;
+  m.I = X.dims[0];
+  m.J = X.dims[1];
+  m.K = X.dims[2];
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// K1: norms and counts
+// ---------------------------------------------------------------------------
+__global__ void k_fiber_norms(const int32_t* __restrict__ ii, const int32_t* __restrict__ jj,
+                              const int32_t* __restrict__ kk, const int32_t* __restrict__ vv,
+                              int64_t nnz, ModeMap mm, unsigned long long* __restrict__ norm2,
+                              unsigned* __restrict__ colcnt, unsigned* __restrict__ rowcnt,
+                              int* minval, unsigned* status) {
+  int local_min = INT32_MAX;
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    int32_t row;
+    int64_t col;
+    const int32_t v = __ldg(vv + e);
+    if (!mm.map(__ldg(ii + e), __ldg(jj + e), __ldg(kk + e), &row, &col)) {
+      bad = true;
+      continue;
+    }
+    const unsigned long long v2 = (unsigned long long)((long long)v * (long long)v);
+    atomicAdd(norm2 + col, v2);
+    atomicAdd(colcnt + col, 1u);
+    atomicAdd(rowcnt + row, 1u);
+    local_min = min(local_min, v);
+  }
+  // warp-reduce the minimum before one atomic
+  for (int o = 16; o; o >>= 1) local_min = min(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
+  if ((threadIdx.x & 31) == 0 && local_min != INT32_MAX) atomicMin(minval, local_min);
+  if (bad) atomicOr(status, DEV_BAD_INDEX);
+}
+
+void launch_fiber_norms(const CooDev& X, uint64_t* norm2, uint32_t* colcnt, uint32_t* rowcnt,
+                        int* minval, unsigned* status, cudaStream_t st) {
+  if (X.nnz == 0) return;
+  const int bs = 256;
+  unsigned g = grid_for(X.nnz, bs, (int64_t)num_sms() * 8);
+  CTD_LAUNCH(k_fiber_norms, (g), (bs), 0, st, X.i, X.j, X.k, X.v, X.nnz, make_map(X),
+                                  reinterpret_cast<unsigned long long*>(norm2), colcnt, rowcnt,
+                                  minval, status);
+}
+
+// ---------------------------------------------------------------------------
+// K2: reduce-then-scan prefix sums (no inter-block waits)
+// ---------------------------------------------------------------------------
+constexpr int SCAN_WARPS = 8;
+constexpr int SCAN_PER_WARP = 512;                       // 16 per lane
+constexpr int SCAN_TILE = SCAN_WARPS * SCAN_PER_WARP;    // 4096
+
+size_t scan_tmp_elems(int64_t n) { return 2 * (size_t)((n + SCAN_TILE - 1) / SCAN_TILE) + 4; }
+
+__device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+template <typename Tin>
+__global__ void k_scan_reduce(const Tin* __restrict__ in, int64_t n,
+                              unsigned long long* __restrict__ tile_sum, double* tile_dsum) {
+  __shared__ unsigned long long ws[SCAN_WARPS];
+  __shared__ double wd[SCAN_WARPS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)warp * SCAN_PER_WARP;
+  unsigned long long acc = 0;
+  double dacc = 0.0;
+  for (int it = 0; it < SCAN_PER_WARP / 32; ++it) {
+    int64_t e = base + it * 32 + lane;
+    if (e < n) {
+      unsigned long long x = (unsigned long long)in[e];
+      acc += x;
+      dacc += (double)x;
+    }
+  }
+  acc = warp_sum(acc);
+  for (int o = 16; o; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+  if (lane == 0) {
+    ws[warp] = acc;
+    wd[warp] = dacc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    double d = 0.0;
+    for (int w = 0; w < SCAN_WARPS; ++w) {
+      t += ws[w];
+      d += wd[w];
+    }
+    tile_sum[blockIdx.x] = t;
+    tile_dsum[blockIdx.x] = d;
+  }
+}
+
+// Exclusive scan of the tile sums in one block; detects overflow past 2^63.
+__global__ void k_scan_tiles(unsigned long long* tile_sum, const double* tile_dsum, int64_t ntiles,
+                             unsigned* status) {
+  __shared__ unsigned long long wsum[32];
+  __shared__ unsigned long long carry_s;
+  __shared__ double dcarry_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) {
+    carry_s = 0;
+    dcarry_s = 0.0;
+  }
+  __syncthreads();
+  for (int64_t base = 0; base < ntiles; base += blockDim.x) {
+    int64_t e = base + threadIdx.x;
+    unsigned long long x = e < ntiles ? tile_sum[e] : 0ull;
+    double dx = e < ntiles ? tile_dsum[e] : 0.0;
+    unsigned long long inc = warp_incl_scan(x);
+    if (lane == 31) wsum[warp] = inc;
+    for (int o = 16; o; o >>= 1) dx += __shfl_xor_sync(0xffffffffu, dx, o);
+    __syncthreads();
+    if (warp == 0) {
+      unsigned long long w = lane < nw ? wsum[lane] : 0ull;
+      unsigned long long wi = warp_incl_scan(w);
+      if (lane < nw) wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    unsigned long long excl = carry_s + wsum[warp] + inc - x;
+    if (e < ntiles) tile_sum[e] = excl;
+    __syncthreads();
+    if (lane == 0) atomicAdd(&dcarry_s, dx);
+    if (threadIdx.x == blockDim.x - 1) carry_s = excl + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    tile_sum[ntiles] = carry_s;
+    if (dcarry_s >= 9.2e18) atomicOr(status, DEV_OVERFLOW);
+  }
+}
+
+template <typename Tin>
+__global__ void k_scan_apply(const Tin* __restrict__ in, unsigned long long* __restrict__ out,
+                             int64_t n, const unsigned long long* __restrict__ tile_off,
+                             bool inclusive) {
+  __shared__ unsigned long long ws[SCAN_WARPS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)warp * SCAN_PER_WARP;
+  unsigned long long tot = 0;
+  for (int it = 0; it < SCAN_PER_WARP / 32; ++it) {
+    int64_t e = base + it * 32 + lane;
+    if (e < n) tot += (unsigned long long)in[e];
+  }
+  tot = warp_sum(tot);
+  if (lane == 0) ws[warp] = tot;
+  __syncthreads();
+  unsigned long long carry = tile_off[blockIdx.x];
+  for (int w = 0; w < warp; ++w) carry += ws[w];
+  const int shift = inclusive ? 0 : 1;
+  for (int it = 0; it < SCAN_PER_WARP / 32; ++it) {
+    int64_t e = base + it * 32 + lane;
+    unsigned long long x = e < n ? (unsigned long long)in[e] : 0ull;
+    unsigned long long inc = warp_incl_scan(x);
+    if (e < n) out[e + shift] = carry + inc;
+    carry += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  if (!inclusive && blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
+}
+
+template <typename Tin>
+static void scan_impl(const Tin* in, uint64_t* out, int64_t n, bool inclusive, uint64_t* tmp,
+                      unsigned* status, cudaStream_t st) {
+  const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (n == 0) {
+    if (!inclusive) cudaMemsetAsync(out, 0, sizeof(uint64_t), st);
+    return;
+  }
+  // tmp layout: [ntiles+1] u64 sums, then ntiles doubles (same byte size)
+  unsigned long long* ts = reinterpret_cast<unsigned long long*>(tmp);
+  double* td = reinterpret_cast<double*>(tmp + ntiles + 2);
+  CTD_LAUNCH(k_scan_reduce<Tin>, ((unsigned)ntiles), (SCAN_WARPS * 32), 0, st, in, n, ts, td);
+  CTD_LAUNCH(k_scan_tiles, (1), (1024), 0, st, ts, td, ntiles, status);
+  CTD_LAUNCH(k_scan_apply<Tin>, ((unsigned)ntiles), (SCAN_WARPS * 32), 0, st, 
+      in, reinterpret_cast<unsigned long long*>(out), n, ts, inclusive);
+}
+
+void launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, bool inclusive, uint64_t* tmp,
+                     unsigned* status, cudaStream_t st) {
+  scan_impl<unsigned long long>(reinterpret_cast<const unsigned long long*>(in), out, n,
+                                inclusive, tmp, status, st);
+}
+void launch_scan_u32(const uint32_t* in, uint64_t* out, int64_t n, bool inclusive, uint64_t* tmp,
+                     unsigned* status, cudaStream_t st) {
+  scan_impl<unsigned>(in, out, n, inclusive, tmp, status, st);
+}
+
+// ---------------------------------------------------------------------------
+// K5a: counting-sort scatter (CSC by column and CSR by row)
+// ---------------------------------------------------------------------------
+__global__ void k_coo_scatter(const int32_t* __restrict__ ii, const int32_t* __restrict__ jj,
+                              const int32_t* __restrict__ kk, const int32_t* __restrict__ vv,
+                              int64_t nnz, ModeMap mm, unsigned long long* colcur,
+                              unsigned long long* rowcur, int32_t* __restrict__ csc_row,
+                              int32_t* __restrict__ csc_val, int32_t* __restrict__ csr_col,
+                              int32_t* __restrict__ csr_val) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    int32_t row;
+    int64_t col;
+    const int32_t v = __ldg(vv + e);
+    if (!mm.map(__ldg(ii + e), __ldg(jj + e), __ldg(kk + e), &row, &col)) continue;
+    unsigned long long pc = atomicAdd(colcur + col, 1ull);
+    csc_row[pc] = row;
+    csc_val[pc] = v;
+    if (csr_col) {
+      unsigned long long pr = atomicAdd(rowcur + row, 1ull);
+      csr_col[pr] = (int32_t)col;
+      csr_val[pr] = v;
+    }
+  }
+}
+
+void launch_coo_scatter(const CooDev& X, uint64_t* colcur, uint64_t* rowcur, int32_t* csc_row,
+                        int32_t* csc_val, int32_t* csr_col, int32_t* csr_val, cudaStream_t st) {
+  if (X.nnz == 0) return;
+  const int bs = 256;
+  unsigned g = grid_for(X.nnz, bs, (int64_t)num_sms() * 8);
+  CTD_LAUNCH(k_coo_scatter, (g), (bs), 0, st, X.i, X.j, X.k, X.v, X.nnz, make_map(X),
+                                  reinterpret_cast<unsigned long long*>(colcur),
+                                  reinterpret_cast<unsigned long long*>(rowcur), csc_row, csc_val,
+                                  csr_col, csr_val);
+}
+
+__global__ void k_copy_u64(const unsigned long long* __restrict__ in, unsigned long long* out,
+                           int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride)
+    out[e] = in[e];
+}
+
+void launch_copy_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  CTD_LAUNCH(k_copy_u64, (grid_for(n, 256, (int64_t)num_sms() * 8)), (256), 0, st, 
+      reinterpret_cast<const unsigned long long*>(in), reinterpret_cast<unsigned long long*>(out),
+      n);
+}
+
+// ---------------------------------------------------------------------------
+// K5b: gather sampled columns
+// ---------------------------------------------------------------------------
+__global__ void k_column_sizes(const unsigned long long* __restrict__ colptr,
+                               const int64_t* __restrict__ fibers, const int* nf_dev, int nf_max,
+                               unsigned long long* sizes) {
+  const int nf = min(*nf_dev, nf_max);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nf_max; c += gridDim.x * blockDim.x) {
+    unsigned long long sz = 0;
+    if (c < nf) {
+      const int64_t f = fibers[c];
+      sz = colptr[f + 1] - colptr[f];
+    }
+    sizes[c] = sz;
+  }
+}
+
+void launch_column_sizes(const uint64_t* colptr, const int64_t* fibers, const int* nf_dev,
+                         int nf_max, uint64_t* sizes, cudaStream_t st) {
+  if (nf_max <= 0) return;
+  CTD_LAUNCH(k_column_sizes, (grid_for(nf_max, 256, 1024)), (256), 0, st, 
+      reinterpret_cast<const unsigned long long*>(colptr), fibers, nf_dev, nf_max,
+      reinterpret_cast<unsigned long long*>(sizes));
+}
+
+// one warp per column
+__global__ void k_gather_columns(const unsigned long long* __restrict__ colptr,
+                                 const int32_t* __restrict__ row, const int32_t* __restrict__ val,
+                                 const int64_t* __restrict__ fibers, const int* nf_dev, int nf_max,
+                                 const unsigned long long* __restrict__ colptr_out,
+                                 int32_t* __restrict__ row_out, int32_t* __restrict__ val_out) {
+  const int nf = min(*nf_dev, nf_max);
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int c = gw; c < nf; c += nwarps) {
+    const int64_t f = fibers[c];
+    const unsigned long long a = colptr[f], b = colptr[f + 1];
+    const unsigned long long o = colptr_out[c];
+    for (unsigned long long p = a + lane; p < b; p += 32) {
+      row_out[o + (p - a)] = row[p];
+      val_out[o + (p - a)] = val[p];
+    }
+  }
+}
+
+void launch_gather_columns(const uint64_t* colptr, const int32_t* row, const int32_t* val,
+                           const int64_t* fibers, const int* nf_dev, int nf_max,
+                           const uint64_t* colptr_out, int32_t* row_out, int32_t* val_out,
+                           cudaStream_t st) {
+  if (nf_max <= 0) return;
+  CTD_LAUNCH(k_gather_columns, (grid_for((int64_t)nf_max * 32, 256, 4096)), (256), 0, st, 
+      reinterpret_cast<const unsigned long long*>(colptr), row, val, fibers, nf_dev, nf_max,
+      reinterpret_cast<const unsigned long long*>(colptr_out), row_out, val_out);
+}
+
+// ---------------------------------------------------------------------------
+// small CSC -> CSR transposition (for the factor R)
+// ---------------------------------------------------------------------------
+__global__ void k_row_counts(const int32_t* __restrict__ row, int64_t nnz, unsigned* rowcnt) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(rowcnt + row[e], 1u);
+}
+
+// one warp per column: scatter its entries into their rows
+__global__ void k_csc_to_csr(const unsigned long long* __restrict__ colptr,
+                             const int32_t* __restrict__ row, const int32_t* __restrict__ val,
+                             int64_t ncols, int col_base, unsigned long long* rowcur,
+                             int32_t* __restrict__ col_out, int32_t* __restrict__ val_out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = gw; c < ncols; c += nwarps) {
+    for (unsigned long long p = colptr[c] + lane; p < colptr[c + 1]; p += 32) {
+      unsigned long long pos = atomicAdd(rowcur + row[p], 1ull);
+      col_out[pos] = (int32_t)(col_base + c);
+      val_out[pos] = val[p];
+    }
+  }
+}
+
+ctd_status build_csr_from_csc(const uint64_t* colptr, const int32_t* row, const int32_t* val,
+                              int64_t ncols, int64_t nnz, int64_t n_rows, int col_base,
+                              uint64_t* rowptr_out, int32_t* col_out, int32_t* val_out,
+                              Arena& scratch, cudaStream_t st) {
+  unsigned* rowcnt;
+  uint64_t* cur;
+  uint64_t* tmp;
+  unsigned* status;
+  CTD_TRY(scratch.get(&rowcnt, n_rows));
+  CTD_TRY(scratch.get(&cur, n_rows + 1));
+  CTD_TRY(scratch.get(&tmp, scan_tmp_elems(n_rows)));
+  CTD_TRY(scratch.get(&status, 1));
+  CTD_CUDA(cudaMemsetAsync(rowcnt, 0, n_rows * sizeof(unsigned), st));
+  CTD_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
+  if (nnz > 0)
+    CTD_LAUNCH(k_row_counts, (grid_for(nnz, 256, (int64_t)num_sms() * 8)), (256), 0, st, row, nnz, rowcnt);
+  launch_scan_u32(rowcnt, rowptr_out, n_rows, false, tmp, status, st);
+  launch_copy_u64(rowptr_out, cur, n_rows, st);
+  if (nnz > 0 && ncols > 0)
+    CTD_LAUNCH(k_csc_to_csr, (grid_for(ncols * 32, 256, 4096)), (256), 0, st, 
+        reinterpret_cast<const unsigned long long*>(colptr), row, val, ncols, col_base,
+        reinterpret_cast<unsigned long long*>(cur), col_out, val_out);
+  CTD_CUDA(cudaGetLastError());
+  return CTD_OK;
+}
+
+__global__ void k_sum_u32(const unsigned* __restrict__ in, int64_t n, unsigned long long* out) {
+  __shared__ unsigned long long part[32];
+  unsigned long long acc = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    acc += in[e];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    atomicAdd(out, t);
+  }
+}
+
+void launch_sum_u32(const uint32_t* in, int64_t n, uint64_t* out, cudaStream_t st) {
+  cudaMemsetAsync(out, 0, sizeof(uint64_t), st);
+  if (n <= 0) return;
+  CTD_LAUNCH(k_sum_u32, (grid_for(n, 1024, (int64_t)num_sms() * 2)), (1024), 0, st, 
+      in, n, reinterpret_cast<unsigned long long*>(out));
+}
+
+__global__ void k_gather_i64(const int64_t* __restrict__ in, const int* __restrict__ idx,
+                             const int* count, int nmax, int64_t* __restrict__ out) {
+  const int n = min(*count, nmax);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+    out[c] = in[idx[c]];
+}
+
+void launch_gather_i64(const int64_t* in, const int* idx, const int* count, int nmax,
+                       int64_t* out, cudaStream_t st) {
+  if (nmax <= 0) return;
+  CTD_LAUNCH(k_gather_i64, (grid_for(nmax, 256, 256)), (256), 0, st, in, idx, count, nmax, out);
+}
+
+}  // namespace ctd

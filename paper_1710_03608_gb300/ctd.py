@@ -1,0 +1,299 @@
+"""Python binding of libctd.so (argument marshalling only).
+
+Every function here forwards to the C ABI declared in include/ctd.h; all
+computation runs in the library's CUDA kernels.  Device memory and streams
+come from PyTorch.  If the library is missing or fails to load, every call
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libctd.so")
+
+CTD_FP64 = 0
+CTD_FP32_BULK = 1
+CTD_MEM_DEVICE = 0
+CTD_MEM_HOST = 1
+CTD_SKIP_C = 1
+CTD_SKIP_ERROR = 2
+
+STATUS = {0: "CTD_OK", 1: "CTD_EINVAL", 2: "CTD_ENOMEM", 3: "CTD_EOVERFLOW", 4: "CTD_ECUDA",
+          5: "CTD_ETIMEOUT", 6: "CTD_ENOTSUP"}
+
+EXPORTED = ["ctd_static", "ctd_dynamic_create", "ctd_dynamic_step", "ctd_error", "ctd_get_sizes",
+            "ctd_get_samples", "ctd_get_fibers", "ctd_get_R", "ctd_get_U", "ctd_get_C_columns",
+            "ctd_get_C", "ctd_get_step", "ctd_get_M", "ctd_free", "ctd_last_error",
+            "ctd_version", "ctd_profile", "ctd_profile_report"]
+
+
+class CtdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+
+
+class ctd_coo3(C.Structure):
+    _fields_ = [("dims", C.c_int64 * 3), ("nnz", C.c_int64), ("i", C.c_void_p),
+                ("j", C.c_void_p), ("k", C.c_void_p), ("val", C.c_void_p),
+                ("memory", C.c_int32)]
+
+
+class ctd_sizes(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("n_cols", C.c_int64), ("s_draws", C.c_int64),
+                ("s_unique", C.c_int64), ("s_kept", C.c_int64), ("nnz_R", C.c_int64),
+                ("nnz_C", C.c_int64), ("t_steps", C.c_int64), ("nnz_X", C.c_int64),
+                ("sqnorm_X", C.c_double)]
+
+
+_lib: Optional[C.CDLL] = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libctd.so (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
+                           "(run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    P, I64, I32, D, U64 = C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_uint64
+    sig = {
+        "ctd_static": [C.POINTER(ctd_coo3), I32, I64, D, U64, I32, C.c_uint, P, C.POINTER(P)],
+        "ctd_dynamic_create": [C.POINTER(C.c_int64 * 2), I32, I32, U64, U64, C.POINTER(P)],
+        "ctd_dynamic_step": [P, C.POINTER(ctd_coo3), I64, D, P],
+        "ctd_error": [P, C.POINTER(D)],
+        "ctd_get_sizes": [P, C.POINTER(ctd_sizes)],
+        "ctd_get_samples": [P, P, P],
+        "ctd_get_fibers": [P, P, P],
+        "ctd_get_R": [P, P, P, P],
+        "ctd_get_U": [P, P],
+        "ctd_get_C_columns": [P, I64, P, P],
+        "ctd_get_C": [P, P, P, P],
+        "ctd_get_step": [P, I64, P, P],
+        "ctd_get_M": [P, I64, P],
+        "ctd_profile": [I32],
+        "ctd_profile_report": [C.c_char_p, C.c_size_t],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.ctd_free.argtypes = [P]
+    lib.ctd_free.restype = None
+    lib.ctd_last_error.restype = C.c_char_p
+    lib.ctd_version.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != 0:
+        msg = load().ctd_last_error().decode(errors="replace")
+        raise CtdError(code, msg)
+
+
+def _ptr(a) -> int:
+    if a is None:
+        return 0
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Coo:
+    """A COO descriptor over torch CUDA int32 tensors or numpy int32 arrays
+    (host).  Keeps references so the buffers outlive the call."""
+
+    def __init__(self, dims, i, j, k, val):
+        self.dims = tuple(int(d) for d in dims)
+        self._keep = (i, j, k, val)
+        host = isinstance(val, np.ndarray)
+        if host:
+            for a in self._keep:
+                if a.dtype != np.int32 or not a.flags.c_contiguous:
+                    raise TypeError("host COO arrays must be contiguous int32")
+        else:
+            for a in self._keep:
+                if str(a.dtype) != "torch.int32" or not a.is_contiguous() or not a.is_cuda:
+                    raise TypeError("device COO tensors must be contiguous CUDA int32")
+        self.desc = ctd_coo3((C.c_int64 * 3)(*self.dims), int(val.shape[0]), _ptr(i), _ptr(j),
+                             _ptr(k), _ptr(val), CTD_MEM_HOST if host else CTD_MEM_DEVICE)
+
+    @staticmethod
+    def from_synth(x, device: bool = True) -> "Coo":
+        """From a paper_1710_03608_gb300.synth.Coo3 (copied to the GPU if device)."""
+        if device:
+            import torch
+            t = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+                 for a in (x.i, x.j, x.k, x.val)]
+            return Coo(x.dims, *t)
+        return Coo(x.dims, *(np.ascontiguousarray(a, dtype=np.int32)
+                             for a in (x.i, x.j, x.k, x.val)))
+
+
+class Factors:
+    """Owns a ctd_factors handle; getters copy to host numpy arrays."""
+
+    def __init__(self, handle: int):
+        self.h = C.c_void_p(handle)
+
+    def __del__(self):
+        try:
+            if self.h:
+                load().ctd_free(self.h)
+                self.h = C.c_void_p(0)
+        except Exception:
+            pass
+
+    def free(self):
+        self.__del__()
+
+    def sizes(self) -> ctd_sizes:
+        s = ctd_sizes()
+        _check(load().ctd_get_sizes(self.h, C.byref(s)))
+        return s
+
+    def error(self) -> float:
+        e = C.c_double()
+        _check(load().ctd_error(self.h, C.byref(e)))
+        return e.value
+
+    def samples(self):
+        s = self.sizes()
+        I = np.empty(s.s_draws, np.int64)
+        Iu = np.empty(s.s_unique, np.int64)
+        _check(load().ctd_get_samples(self.h, _ptr(I), _ptr(Iu)))
+        return I, Iu
+
+    def fibers(self):
+        s = self.sizes()
+        f = np.empty(s.s_kept, np.int64)
+        t = np.empty(s.s_kept, np.int64)
+        _check(load().ctd_get_fibers(self.h, _ptr(f), _ptr(t)))
+        return f, t
+
+    def R(self):
+        s = self.sizes()
+        p = np.empty(s.s_kept + 1, np.int64)
+        r = np.empty(s.nnz_R, np.int32)
+        v = np.empty(s.nnz_R, np.int32)
+        _check(load().ctd_get_R(self.h, _ptr(p), _ptr(r), _ptr(v)))
+        return p, r, v
+
+    def R_dense(self):
+        s = self.sizes()
+        p, r, v = self.R()
+        out = np.zeros((s.n_rows, s.s_kept), np.int64)
+        for c in range(s.s_kept):
+            out[r[p[c]:p[c + 1]], c] = v[p[c]:p[c + 1]]
+        return out
+
+    def U(self):
+        s = self.sizes()
+        u = np.empty((s.s_kept, s.s_kept), np.float64)
+        _check(load().ctd_get_U(self.h, _ptr(u)))
+        return u
+
+    def C_columns(self, cols):
+        s = self.sizes()
+        cols = np.ascontiguousarray(cols, dtype=np.int64)
+        out = np.empty((cols.shape[0], s.s_kept), np.float64)  # column-major s~ x n
+        _check(load().ctd_get_C_columns(self.h, cols.shape[0], _ptr(cols), _ptr(out)))
+        return out.T
+
+    def C(self):
+        s = self.sizes()
+        p = np.empty(s.n_cols + 1, np.int64)
+        r = np.empty(max(s.nnz_C, 1), np.int32)
+        v = np.empty(max(s.nnz_C, 1), np.float64)
+        _check(load().ctd_get_C(self.h, _ptr(p), _ptr(r), _ptr(v)))
+        return p, r[:s.nnz_C], v[:s.nnz_C]
+
+    def step(self, t: int):
+        info = np.empty(4, np.int64)
+        sq = np.empty(2, np.float64)
+        _check(load().ctd_get_step(self.h, int(t), _ptr(info), _ptr(sq)))
+        return info, sq
+
+    def M(self, t: int):
+        info, _ = self.step(t)
+        m = np.empty((info[1], info[2]), np.float64)
+        _check(load().ctd_get_M(self.h, int(t), _ptr(m)))
+        return m
+
+
+def ctd_static(X: Coo, alpha: int, s: int, eps: float, seed: int = 0,
+               precision: int = CTD_FP64, flags: int = 0, stream=None) -> Factors:
+    """CTD-S (Algorithm 1) through the C ABI."""
+    lib = load()
+    out = C.c_void_p()
+    st = _stream_handle(stream) if not _host(X) or stream is not None else _default_stream()
+    _check(lib.ctd_static(C.byref(X.desc), int(alpha), int(s), float(eps), int(seed),
+                          int(precision), int(flags), C.c_void_p(st), C.byref(out)))
+    return Factors(out.value)
+
+
+def _host(X: Coo) -> bool:
+    return X.desc.memory == CTD_MEM_HOST
+
+
+def _default_stream() -> int:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+class Dynamic(Factors):
+    """A CTD-D state (Algorithm 2)."""
+
+    def __init__(self, dims2, alpha: int = 1, precision: int = CTD_FP64, seed: int = 0,
+                 stream_id: int = 0):
+        lib = load()
+        out = C.c_void_p()
+        d2 = (C.c_int64 * 2)(int(dims2[0]), int(dims2[1]))
+        _check(lib.ctd_dynamic_create(C.byref(d2), int(alpha), int(precision), int(seed),
+                                      int(stream_id), C.byref(out)))
+        super().__init__(out.value)
+
+    def step_slice(self, dX: Coo, d: int, eps: float, stream=None):
+        st = _stream_handle(stream) if not _host(dX) or stream is not None else _default_stream()
+        _check(load().ctd_dynamic_step(self.h, C.byref(dX.desc), int(d), float(eps),
+                                       C.c_void_p(st)))
+
+
+def profile(enable: bool = True) -> None:
+    """Start (clear) or stop per-phase device timing and launch counting."""
+    _check(load().ctd_profile(1 if enable else 0))
+
+
+def profile_report() -> dict:
+    """{"launches": L, "phases": {name: {"ms": t, "calls": n}}} since profile()."""
+    import json
+    buf = C.create_string_buffer(1 << 16)
+    _check(load().ctd_profile_report(buf, len(buf)))
+    return json.loads(buf.value.decode())
+
+
+def version() -> str:
+    return load().ctd_version().decode()

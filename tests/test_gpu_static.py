@@ -1,0 +1,150 @@
+"""CTD-S parity: CUDA path (through the C ABI) vs the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import ctd_oracle as O
+from paper_1710_03608_gb300 import synth
+from tests.parity import error_tol, rel_fro, tie_margin, u_residual, u_tol
+
+pytestmark = pytest.mark.gpu
+
+
+def ctd():
+    from paper_1710_03608_gb300 import ctd as m
+    return m
+
+
+def run(coo, alpha, s, eps, seed, precision, host=False, flags=0):
+    m = ctd()
+    X = m.Coo.from_synth(coo, device=not host)
+    return m.ctd_static(X, alpha, s, eps, seed, precision, flags)
+
+
+def check(F, ref, eps, precision, full_c=True, c_cols=None, err_ref=None):
+    sz = F.sizes()
+    assert sz.sqnorm_X == float(ref.T)
+    I, Iu = F.samples()
+    assert np.array_equal(I, ref.I)
+    assert np.array_equal(Iu, ref.I_unique)
+    assert tie_margin(ref.ratios, eps) > 1e-7, "near-tie in the independence test"
+    fib, _ = F.fibers()
+    assert np.array_equal(fib, ref.fibers)
+    assert np.array_equal(F.R_dense(), ref.R)
+    if ref.R.shape[1]:
+        U = F.U()
+        assert rel_fro(U, ref.U) <= u_tol(ref.R)
+        # the GPU's U is at least as good an inverse as the oracle's
+        assert u_residual(U, ref.R) <= 2.0 * u_residual(ref.U, ref.R) + 1e-9
+    if full_c:
+        p, r, v = F.C()
+        Cref = O.c_full(ref.X, ref.R)
+        assert np.array_equal(p, Cref.indptr)
+        assert np.array_equal(r, Cref.indices)
+        assert np.array_equal(v, Cref.data.astype(np.float64))
+        assert sz.nnz_C == Cref.nnz
+    if c_cols is not None:
+        got = F.C_columns(c_cols)
+        want = O.c_columns(ref.X, ref.R, c_cols)
+        assert np.array_equal(got, want.astype(np.float64))
+    if err_ref is not None:
+        e = F.error()
+        assert abs(e - err_ref) <= error_tol(precision, err_ref), (e, err_ref)
+
+
+@pytest.mark.parametrize("alpha", [1, 2, 3])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_small_uniform_full(alpha, precision):
+    coo = synth.small_uniform()
+    s, eps, seed = 50, 1e-6, 0
+    F = run(coo, alpha, s, eps, seed, precision)
+    ref = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, alpha, s, eps, seed)
+    e_ref = O.relative_error_dense(ref.X, ref.R, ref.U, O.c_full(ref.X, ref.R))
+    check(F, ref, eps, precision, err_ref=e_ref)
+
+
+def test_host_input_matches_device_input():
+    coo = synth.small_uniform()
+    Fd = run(coo, 1, 50, 1e-6, 3, 0)
+    Fh = run(coo, 1, 50, 1e-6, 3, 0, host=True)
+    assert np.array_equal(Fd.samples()[0], Fh.samples()[0])
+    assert np.array_equal(Fd.R_dense(), Fh.R_dense())
+    assert np.array_equal(Fd.U(), Fh.U())
+    assert Fd.error() == Fh.error()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_signed_values(seed):
+    coo = synth.tiny((40, 30, 20), 2000, seed=seed + 20, vmax=7, signed=True)
+    F = run(coo, 1, 200, 1e-6, seed, 0)
+    ref = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 200, 1e-6, seed)
+    e_ref = O.relative_error_dense(ref.X, ref.R, ref.U, O.c_full(ref.X, ref.R))
+    check(F, ref, 1e-6, 0, err_ref=e_ref)
+
+
+def test_sample_every_fiber_exact():
+    coo = synth.tiny((30, 12, 6), 400, seed=4)
+    F = run(coo, 1, 8192, 1e-6, 1, 0)
+    ref = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 8192, 1e-6, 1)
+    check(F, ref, 1e-6, 0, err_ref=0.0)
+    assert abs(F.error()) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_traffic_scaled_full(precision):
+    """A 2,000 x 2,000 x 200 traffic tensor (8*10^4 nonzeros, Zipf(1.2),
+    Geometric(0.3)) with s = 500: many tiles, ragged tails, full C."""
+    coo = synth.traffic_10m(scale=0.2)
+    F = run(coo, 1, 500, 1e-6, 0, precision)
+    ref = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 500, 1e-6, 0)
+    check(F, ref, 1e-6, precision, err_ref=O.projection_error(ref.X, ref.R))
+
+
+def test_edge_all_zero():
+    coo = synth.tiny((5, 4, 3), 10, seed=1)
+    coo.val[:] = 0
+    F = run(coo, 1, 10, 1e-6, 0, 0)
+    sz = F.sizes()
+    assert sz.s_unique == 0 and sz.s_kept == 0 and sz.nnz_C == 0
+    assert F.error() == 0.0
+
+
+def test_edge_single_nonzero_and_s1():
+    coo = synth.tiny((5, 4, 3), 1, seed=2)
+    F = run(coo, 1, 1, 0.5, 7, 0)
+    ref = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 1, 0.5, 7)
+    check(F, ref, 0.5, 0, err_ref=0.0)
+
+
+def test_errors_are_reported():
+    m = ctd()
+    coo = synth.small_uniform()
+    with pytest.raises(m.CtdError) as e:
+        run(coo, 4, 50, 1e-6, 0, 0)
+    assert e.value.status == "CTD_EINVAL"
+    with pytest.raises(m.CtdError):
+        run(coo, 1, 0, 1e-6, 0, 0)
+    bad = synth.Coo3(coo.dims, coo.i.copy(), coo.j.copy(), coo.k.copy(), coo.val.copy())
+    bad.i[17] = 100  # outside I = 100: the kernels skip it and flag it
+    with pytest.raises(m.CtdError) as e:
+        run(bad, 1, 50, 1e-6, 0, 0)
+    assert e.value.status == "CTD_EINVAL"
+
+
+@pytest.fixture(scope="module")
+def traffic_full():
+    coo = synth.traffic_10m()
+    ref = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 500, 1e-6, 0)
+    return coo, ref
+
+
+def test_traffic_10m_full_size(traffic_full):
+    """The 10^4 x 10^4 x 10^3, 10^7-nonzero workload at full size, FP32 bulk:
+    integer stages and U element by element, C on sampled columns, the
+    error against Lemma 3.2's projection form."""
+    coo, ref = traffic_full
+    F = run(coo, 1, 500, 1e-6, 0, 1)
+    rng = np.random.default_rng(0)
+    nz = np.flatnonzero(np.diff(ref.X.ptr))
+    cols = np.concatenate([rng.choice(nz, 200, replace=False),
+                           nz[np.argsort(np.diff(ref.X.ptr)[nz])[-20:]], [0, ref.X.n_cols - 1]])
+    check(F, ref, 1e-6, 1, full_c=False, c_cols=cols, err_ref=O.projection_error(ref.X, ref.R))
