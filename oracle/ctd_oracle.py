@@ -34,6 +34,9 @@ Readings of points the paper leaves open (same letters everywhere):
   A9 a dynamic state may start empty; the first kept fiber then gives
      U = 1/(x^T x), as in Algorithm 1 line 5.
   A10 an all-zero input yields no draws and an empty factor.
+  A21 line 7's residual is evaluated as x minus its orthogonal projection
+      onto range(R), by Gram-Schmidt with reorthogonalization (equal to
+      x - R U R^T x in exact arithmetic; stable in floating point).
 
 Parity pinned by tests/test_oracle_pins.py (brute force, numpy/scipy
 library routines, invariants, chi-square).  The DDoS rule is pinned only
@@ -208,47 +211,78 @@ def _filter(x_of, candidates, R_cols: List[np.ndarray], U: Optional[np.ndarray],
     """Run the sequential independence test over `candidates` in order.
 
     R_cols holds the current columns (dense float64, length I_alpha); U is
-    their (R^T R)^{-1} (None when R is empty).  For each candidate x the
-    residual res = x - R U R^T x is formed explicitly; the fiber is skipped
-    when ||res|| <= eps ||x|| (reading A4); otherwise delta = ||res||^2,
-    y = U R^T x, U grows by the block update of Alg. 1 line 12 and x is
-    appended to R.  Returns (kept candidate positions, R_cols, U, ratios)
-    where ratios[k] = ||res|| / ||x|| for every candidate (for tie margins).
+    their (R^T R)^{-1} (None when R is empty).  For each candidate x
+    (Alg. 1 lines 6-15 / Alg. 2 lines 6-16):
+      line 7: res = x - R U R^T x.  Because U = (R^T R)^{-1} (Colibri's
+        Theorem 1, used in Lemma 3.2), R U R^T is the orthogonal projector
+        onto range(R), so res is x minus its projection.  It is evaluated
+        as res = x - Q (Q^T x) with an orthonormal basis Q of range(R),
+        applied twice (Gram-Schmidt with reorthogonalization), which keeps
+        ||res|| accurate to rounding however ill-conditioned R gets; the
+        product R (U (R^T x)) with the incrementally updated U loses that
+        accuracy once kappa(R^T R) grows large (reading A21).
+      line 8: skip when ||res|| <= eps ||x|| (reading A4);
+      line 11: delta = ||res||^2, y = U R^T x;
+      line 12: U grows by the block update;
+      line 13: x is appended to R (and res / ||res|| to Q).
+    Returns (kept candidate positions, R_cols, U, ratios) where ratios[k] =
+    ||res|| / ||x|| for every candidate (for tie margins).
     """
     kept: List[int] = []
     ratios: List[float] = []
+    n0 = len(R_cols)
+    cap = n0 + len(candidates)
+    Rbuf = Qbuf = None
     for pos, f in enumerate(candidates):
         x = x_of(f).astype(np.float64)
+        if Rbuf is None:
+            Rbuf = np.zeros((x.shape[0], max(cap, 1)))
+            Qbuf = np.zeros((x.shape[0], max(cap, 1)))
+            for c, col in enumerate(R_cols):
+                Rbuf[:, c] = col
+            if n0:  # orthonormal basis of the warm-start columns
+                Qbuf[:, :n0] = _orthonormal_basis(Rbuf[:, :n0])
+        n = n0 + len(kept)
         xn = float(np.sqrt(x @ x))
-        if not R_cols:
+        if n == 0:
             # Alg. 1 line 5 (and reading A9): R <- [x], U <- 1/(x^T x)
             if xn == 0.0:
                 ratios.append(0.0)
                 continue
-            R_cols.append(x)
+            Rbuf[:, 0] = x
+            Qbuf[:, 0] = x / xn
             U = np.array([[1.0 / (x @ x)]])
             kept.append(pos)
             ratios.append(1.0)
             continue
-        R = np.stack(R_cols, axis=1)
-        Rtx = R.T @ x
-        y = U @ Rtx
-        res = x - R @ y
+        R = Rbuf[:, :n]
+        Q = Qbuf[:, :n]
+        res = x - Q @ (Q.T @ x)
+        res = res - Q @ (Q.T @ res)
         rn = float(np.sqrt(res @ res))
         ratios.append(rn / xn if xn > 0 else 0.0)
         if rn <= eps * xn:
             continue
         delta = rn * rn
-        n = U.shape[0]
+        y = U @ (R.T @ x)
         Un = np.empty((n + 1, n + 1))
         Un[:n, :n] = U + np.outer(y, y) / delta
         Un[:n, n] = -y / delta
         Un[n, :n] = -y / delta
         Un[n, n] = 1.0 / delta
         U = Un
-        R_cols.append(x)
+        Rbuf[:, n] = x
+        Qbuf[:, n] = res / rn
         kept.append(pos)
+    if Rbuf is not None:
+        R_cols = [Rbuf[:, c].copy() for c in range(n0 + len(kept))]
     return kept, R_cols, U, ratios
+
+
+def _orthonormal_basis(R: np.ndarray) -> np.ndarray:
+    """Orthonormal basis of range(R) for full-column-rank R (numpy QR)."""
+    Q, _ = np.linalg.qr(R)
+    return Q
 
 
 @dataclasses.dataclass
