@@ -121,11 +121,16 @@ CTD_API ctd_status ctd_static(const ctd_coo3* X, int alpha, int64_t s, double ep
  * ctd_dynamic_create -- empty CTD-D state for slices of size
  * dims2[0] x dims2[1] x 1 (Algorithm 2 with alpha in {1, 2}; the time mode
  * is the third).  `stream_id` selects an independent Philox counter space
- * (draw k of step t uses counter (k, t, stream_id, 0)).
+ * (draw k of step t uses counter (k, t, stream_id, 0)).  flags: 0 keeps the
+ * new-column block of every step; CTD_KEEP_LAST_C keeps only the newest
+ * step's block (older columns can then no longer be read).
+ * Starting empty, the first kept fiber x gives U = 1/(x^T x) as in
+ * Algorithm 1 line 5, so a first step equals ctd_static on that slice.
  */
+#define CTD_KEEP_LAST_C 4u
 CTD_API ctd_status ctd_dynamic_create(const int64_t dims2[2], int alpha, int precision,
-                              uint64_t seed, uint64_t stream_id,
-                              ctd_factors** state);
+                                      uint64_t seed, uint64_t stream_id, unsigned flags,
+                                      ctd_factors** state);
 
 /*
  * ctd_dynamic_step -- one step of CTD-D, Algorithm 2, in place:

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libctd.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["ctd_stream.cu", "ctd_sample.cu", "ctd_spmm.cu", "ctd_dense.cu", "ctd_api.cu",
+SOURCES = ["ctd_stream.cu", "ctd_sample.cu", "ctd_spmm.cu", "ctd_dense.cu", "ctd_filter.cu", "ctd_api.cu",
            "ctd_dynamic.cu"]
 
 

@@ -85,14 +85,13 @@ void dfree(void* p, cudaStream_t st) {
   if (p) cudaFreeAsync(p, st);
 }
 
-template <typename T>
-static ctd_status d2h(T* host, const T* dev, size_t n, cudaStream_t st) {
-  if (n == 0) return CTD_OK;
-  CTD_CUDA(cudaMemcpyAsync(host, dev, n * sizeof(T), cudaMemcpyDeviceToHost, st));
+ctd_status d2h_bytes(void* host, const void* dev, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return CTD_OK;
+  CTD_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, st));
   return CTD_OK;
 }
 
-static ctd_status sync(cudaStream_t st) {
+ctd_status sync(cudaStream_t st) {
   CTD_CUDA(cudaStreamSynchronize(st));
   return CTD_OK;
 }
@@ -137,23 +136,6 @@ ctd_status stage_coo(const ctd_coo3* X, int alpha, Arena& scratch, cudaStream_t 
   return CTD_OK;
 }
 
-// X_(alpha) in both layouts plus its column distribution.
-struct Matricized {
-  int64_t n_rows = 0, n_cols = 0, nnz = 0;
-  uint64_t* cdf = nullptr;      // [n_cols] inclusive prefix of squared norms
-  uint64_t* colptr = nullptr;   // [n_cols+1]
-  uint64_t* rowptr = nullptr;   // [n_rows+1]
-  int32_t* csc_row = nullptr;
-  int32_t* csc_val = nullptr;
-  int32_t* csr_col = nullptr;
-  int32_t* csr_val = nullptr;
-  int* minval = nullptr;
-  unsigned* status = nullptr;
-  uint64_t* tmp = nullptr;
-  CscDev csc() const { return CscDev{colptr, csc_row, csc_val}; }
-  CsrX csr() const { return CsrX{rowptr, csr_col, csr_val}; }
-};
-
 // Algorithm 1 lines 1-2 (and the layouts the later lines read).
 ctd_status matricize(const CooDev& X, bool want_rows, Arena& A, cudaStream_t st, Matricized* M) {
   mode_extents(X.dims, X.alpha, &M->n_rows, &M->n_cols);
@@ -163,6 +145,7 @@ ctd_status matricize(const CooDev& X, bool want_rows, Arena& A, cudaStream_t st,
   CTD_TRY(A.get(&norm2, M->n_cols));
   CTD_TRY(A.get(&colcnt, M->n_cols));
   CTD_TRY(A.get(&rowcnt, M->n_rows));
+  M->rowcnt = rowcnt;
   CTD_TRY(A.get(&M->cdf, M->n_cols));
   CTD_TRY(A.get(&M->colptr, M->n_cols + 1));
   CTD_TRY(A.get(&M->rowptr, M->n_rows + 1));
@@ -250,7 +233,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   Matricized M;
   {
     PhaseScope ph("matricize", st);
-    STEP(matricize(X, !(flags & CTD_SKIP_ERROR), scratch, st, &M));
+    STEP(matricize(X, false, scratch, st, &M));
   }
   F->n_rows = M.n_rows;
   F->n_cols = M.n_cols;
@@ -278,7 +261,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   F->s_unique = s_unique;
   if (T == 0) F->s = 0;  // nothing to draw from
   const int su = s_unique;
-  const bool may_cancel = minval < 0;
+  const bool may_cancel = minval <= 0;
 
   // candidate columns R' (CSC) and their row-major copy
   uint64_t *rc_ptr, *rc_sizes;
@@ -301,39 +284,36 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   STEP(build_csr_from_csc(rc_ptr, rc_row, rc_val, su, nnz_cand, M.n_rows, 0, rcr_ptr, rcr_col,
                           rcr_val, scratch, st));
 
-  // lines 5-15: Gram matrix, in-order Cholesky with skip
-  double *G, *thr;
-  int *keep, *idx;
+  // lines 5-15: Gram matrix, in-order Cholesky with skip (+ explicit re-test)
+  double *G, *xn2;
   STEP(scratch.get(&G, (size_t)su * su));
-  STEP(scratch.get(&thr, su));
-  STEP(scratch.get(&keep, su));
-  STEP(scratch.get(&idx, su));
+  STEP(scratch.get(&xn2, su));
   CsrDev Rc{rcr_ptr, rcr_col, rcr_val, su};
   {
     PhaseScope ph("gram", st);
     STEP(launch_spmm_dense(M.csc(), F->Iu, d_count, su, Rc, G, su, st));
+    launch_thresholds(G, su, su, 1.0, xn2, st);
   }
-  {
-    PhaseScope ph("filter_chol", st);
-    launch_thresholds(G, su, su, eps * eps, thr, st);
-    launch_chol_skip(G, su, su, thr, keep, st);
-    launch_compact_flags(keep, su, idx, d_count + 1, st);
-  }
-  int kept = 0;
-  STEP(d2h(&kept, d_count + 1, 1, st));
-  STEPC(cudaGetLastError());
-  STEP(sync(st));
+  FilterIn fi;
+  fi.du = su;
+  fi.S = G;
+  fi.xnorm2 = xn2;
+  fi.eps = eps;
+  fi.cptr = rc_ptr;
+  fi.crow = rc_row;
+  fi.cval = rc_val;
+  fi.n_rows = M.n_rows;
+  FilterOut fo;
+  STEP(run_filter(fi, fo, scratch, st));
+  const int kept = fo.kept;
+  int* idx = fo.idx;
   F->s_kept = kept;
 
   // U = (R^T R)^{-1} = L^{-T} L^{-1}
-  double *L, *Z;
-  STEP(scratch.get(&L, (size_t)kept * kept));
-  STEP(scratch.get(&Z, (size_t)kept * kept));
+  double* Z = fo.Li;
   STEP(F->mem.get(&F->U, (size_t)kept * kept));
   {
     PhaseScope ph("u_inverse", st);
-    launch_gather_lower(G, su, idx, d_count + 1, kept, L, kept, st);
-    tri_inverse(L, kept, kept, Z, kept, st);
     u_from_linv(Z, kept, kept, F->U, kept, st);
   }
 
@@ -341,11 +321,11 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   STEP(F->mem.get(&F->kept_pos, kept));
   STEP(F->mem.get(&F->fibers, kept));
   STEPC(cudaMemcpyAsync(F->kept_pos, idx, kept * sizeof(int), cudaMemcpyDeviceToDevice, st));
-  launch_gather_i64(F->Iu, idx, d_count + 1, kept, F->fibers, st);
+  launch_gather_i64(F->Iu, idx, fo.count, kept, F->fibers, st);
   uint64_t* r_sizes;
   STEP(scratch.get(&r_sizes, kept + 1));
   STEP(F->mem.get(&F->Rcolptr, kept + 1));
-  launch_column_sizes(M.colptr, F->fibers, d_count + 1, kept, r_sizes, st);
+  launch_column_sizes(M.colptr, F->fibers, fo.count, kept, r_sizes, st);
   launch_scan_u64(r_sizes, F->Rcolptr, kept, false, M.tmp, M.status, st);
   uint64_t nnzR = 0;
   STEP(d2h(&nnzR, F->Rcolptr + kept, 1, st));
@@ -356,7 +336,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   STEP(F->mem.get(&F->Rrowptr, M.n_rows + 1));
   STEP(F->mem.get(&F->Rcol, nnzR));
   STEP(F->mem.get(&F->Rcval, nnzR));
-  launch_gather_columns(M.colptr, M.csc_row, M.csc_val, F->fibers, d_count + 1, kept, F->Rcolptr,
+  launch_gather_columns(M.colptr, M.csc_row, M.csc_val, F->fibers, fo.count, kept, F->Rcolptr,
                         F->Rrow, F->Rval, st);
   STEP(build_csr_from_csc(F->Rcolptr, F->Rrow, F->Rval, kept, (int64_t)nnzR, M.n_rows, 0,
                           F->Rrowptr, F->Rcol, F->Rcval, scratch, st));
@@ -385,20 +365,26 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
     F->Cval = cv;
     PhaseScope ph("c_fill", st);
     STEP(launch_c_fill(M.csc(), M.n_cols, R, F->Coff, F->Ccnt, F->Crow, F->Cval,
-                       precision == CTD_FP32_BULK, may_cancel, st));
+                       precision == CTD_FP32_BULK, may_cancel, minval > 0, T, st));
   }
 
-  // Eq. (error): e = (T - <U, R^T X X^T R>) / T
+  // Eq. (error): e = (T - ||Q^T X||_F^2) / T with Q = R L^{-T}
   double* d_pu = nullptr;
-  if (!(flags & CTD_SKIP_ERROR)) {
-    long long* CCt;
-    STEP(scratch.get(&CCt, (size_t)kept * kept));
+  if (!(flags & CTD_SKIP_ERROR) && kept > 0) {
+    std::vector<uint32_t> rc(M.n_rows);
+    STEP(d2h(rc.data(), M.rowcnt, M.n_rows, st));
+    STEP(sync(st));
+    std::vector<int> order(M.n_rows);
+    std::iota(order.begin(), order.end(), 0);
+    const int want = (int)std::min<int64_t>(M.n_rows, 4096);
+    std::partial_sort(order.begin(), order.begin() + want, order.end(),
+                      [&](int a, int b) { return rc[a] > rc[b] || (rc[a] == rc[b] && a < b); });
+    int n_hot = want;
+    while (n_hot > 0 && rc[order[n_hot - 1]] == 0) --n_hot;
     STEP(scratch.get(&d_pu, 1));
-    STEPC(cudaMemsetAsync(CCt, 0, (size_t)kept * kept * 8, st));
-    STEPC(cudaMemsetAsync(d_pu, 0, 8, st));
-    PhaseScope ph("error_gram", st);
-    STEP(launch_gram_hform(M.csr(), M.csc(), M.n_rows, R, CCt, scratch, st));
-    if (kept > 0) launch_frob_dot(F->U, CCt, kept, d_pu, st);
+    PhaseScope ph("error_qform", st);
+    STEP(launch_error_qform(M.csc(), M.n_cols, M.n_rows, R, Z, kept, nullptr, order.data(), n_hot,
+                            precision == CTD_FP32_BULK, d_pu, scratch, st));
   }
   uint64_t* d_nnzc;
   STEP(scratch.get(&d_nnzc, 1));
@@ -412,9 +398,9 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   STEP(sync(st));
   STEP(status_from_device(status));
   F->nnz_C = (int64_t)nnzC;
-  if (d_pu) {
+  if (!(flags & CTD_SKIP_ERROR)) {
     F->have_err = true;
-    F->err = T ? ((double)T - pu) / (double)T : 0.0;
+    F->err = T ? std::max(0.0, ((double)T - pu) / (double)T) : 0.0;
   }
   *out = F;
 #undef STEP
@@ -435,6 +421,7 @@ extern "C" ctd_status ctd_error(const ctd_factors* F, double* rel_err) {
 extern "C" ctd_status ctd_get_sizes(const ctd_factors* F, ctd_sizes* o) {
   if (!F || !o) return fail(CTD_EINVAL, "NULL argument");
   CTD_TRY(sync(F->stream));
+  if (F->kind == 1) return dyn_sizes(F, o);
   o->n_rows = F->n_rows;
   o->n_cols = F->n_cols;
   o->s_draws = F->s;
@@ -450,6 +437,7 @@ extern "C" ctd_status ctd_get_sizes(const ctd_factors* F, ctd_sizes* o) {
 
 extern "C" ctd_status ctd_get_samples(const ctd_factors* F, int64_t* I, int64_t* Iu) {
   if (!F) return fail(CTD_EINVAL, "NULL argument");
+  if (F->kind == 1) return dyn_samples(F, I, Iu);
   if (I) CTD_TRY(d2h(I, F->I, (size_t)F->s, F->stream));
   if (Iu) CTD_TRY(d2h(Iu, F->Iu, (size_t)F->s_unique, F->stream));
   return sync(F->stream);
@@ -457,7 +445,7 @@ extern "C" ctd_status ctd_get_samples(const ctd_factors* F, int64_t* I, int64_t*
 
 extern "C" ctd_status ctd_get_fibers(const ctd_factors* F, int64_t* fiber, int64_t* step) {
   if (!F) return fail(CTD_EINVAL, "NULL argument");
-  if (F->kind != 0) return fail(CTD_ENOTSUP, "use the dynamic getters");
+  if (F->kind == 1) return dyn_fibers(F, fiber, step);
   if (fiber) CTD_TRY(d2h(fiber, F->fibers, (size_t)F->s_kept, F->stream));
   CTD_TRY(sync(F->stream));
   if (step)
@@ -494,14 +482,14 @@ static ctd_status csc_to_host_sorted(const uint64_t* dptr, const int32_t* drow, 
 extern "C" ctd_status ctd_get_R(const ctd_factors* F, int64_t* colptr, int32_t* row,
                                 int32_t* val) {
   if (!F || !colptr || (F->nnz_R && (!row || !val))) return fail(CTD_EINVAL, "NULL argument");
-  if (F->kind != 0) return fail(CTD_ENOTSUP, "use the dynamic getters");
+  if (F->kind == 1) return dyn_R(F, colptr, row, val);
   return csc_to_host_sorted(F->Rcolptr, F->Rrow, F->Rval, F->s_kept, F->nnz_R, F->stream, colptr,
                             row, val);
 }
 
 extern "C" ctd_status ctd_get_U(const ctd_factors* F, double* U) {
   if (!F || (!U && F->s_kept)) return fail(CTD_EINVAL, "NULL argument");
-  if (F->kind != 0) return fail(CTD_ENOTSUP, "use the dynamic getters");
+  if (F->kind == 1) return dyn_U(F, U);
   CTD_TRY(d2h(U, F->U, (size_t)F->s_kept * F->s_kept, F->stream));
   return sync(F->stream);
 }
@@ -525,7 +513,7 @@ __global__ void k_c_columns(const unsigned long long* __restrict__ coff,
 extern "C" ctd_status ctd_get_C_columns(const ctd_factors* F, int64_t ncols, const int64_t* cols,
                                         double* out) {
   if (!F || ncols < 0 || (ncols && (!cols || !out))) return fail(CTD_EINVAL, "NULL argument");
-  if (F->kind != 0) return fail(CTD_ENOTSUP, "use the dynamic getters");
+  if (F->kind == 1) return dyn_C_columns(F, ncols, cols, out);
   if (!F->Coff) return fail(CTD_EINVAL, "C was not materialized (CTD_SKIP_C)");
   for (int64_t c = 0; c < ncols; ++c)
     if (cols[c] < 0 || cols[c] >= F->n_cols) return fail(CTD_EINVAL, "column out of range");

@@ -100,9 +100,12 @@ static void dgemm_tri_lower(const double* Z, int64_t n, int64_t ldz, double* C, 
 // Cholesky with skip
 // ---------------------------------------------------------------------------
 __global__ void k_chol_diag(double* __restrict__ A, int64_t n, int64_t lda, int64_t k0,
-                            const double* __restrict__ thr, int* __restrict__ keep) {
+                            const double* __restrict__ thr, const int* __restrict__ force,
+                            int* __restrict__ keep, double* __restrict__ piv,
+                            unsigned* __restrict__ status) {
   __shared__ double D[NB][NB + 1];  // D[r][c], lower
   __shared__ int kp;
+  __shared__ double inv;
   const int r = threadIdx.x;
   const int nb = (int)min((int64_t)NB, n - k0);
   if (r < nb)
@@ -111,22 +114,26 @@ __global__ void k_chol_diag(double* __restrict__ A, int64_t n, int64_t lda, int6
   for (int c = 0; c < nb; ++c) {
     if (r == 0) {
       const double d = D[c][c];
-      kp = (d > thr[k0 + c] && d > 0.0) ? 1 : 0;
-      keep[k0 + c] = kp;
-      D[c][c] = kp ? sqrt(d) : 0.0;
+      const int f = force ? force[k0 + c] : -1;
+      int k = (d > thr[k0 + c] && d > 0.0) ? 1 : 0;
+      if (f >= 0) k = f;
+      if (k && !(d > 0.0)) {  // forced keep of a column with no positive pivot
+        atomicOr(status, DEV_CAPACITY);
+        k = 0;
+      }
+      kp = k;
+      keep[k0 + c] = k;
+      if (piv) piv[k0 + c] = d;
+      const double l = k ? sqrt(d) : 0.0;
+      D[c][c] = l;
+      inv = k ? 1.0 / l : 0.0;
     }
     __syncthreads();
-    if (r > c && r < nb) {
-      if (kp) {
-        D[r][c] /= D[c][c];
-      } else {
-        D[r][c] = 0.0;
-      }
-    }
+    if (r > c && r < nb) D[r][c] = kp ? D[r][c] * inv : 0.0;
     __syncthreads();
     if (kp && r > c && r < nb) {
       const double lrc = D[r][c];
-      for (int j = c + 1; j <= r; ++j) D[r][j] -= lrc * D[j][c];
+      for (int j = c + 1; j <= r; ++j) D[r][j] = fma(-lrc, D[j][c], D[r][j]);
     }
     __syncthreads();
   }
@@ -204,15 +211,16 @@ __global__ void __launch_bounds__(256)
 }
 
 void launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr, int* keep,
-                      cudaStream_t st) {
+                      cudaStream_t st, const int* force, double* piv, unsigned* status) {
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
     const int nb = (int)std::min<int64_t>(NB, n - k0);
-    CTD_LAUNCH(k_chol_diag, (1), (NB), 0, st, A, n, lda, k0, thr, keep);
+    CTD_LAUNCH(k_chol_diag, (1), (NB), 0, st, A, n, lda, k0, thr, force, keep, piv, status);
     const int64_t rest = n - k0 - nb;
     if (rest > 0) {
       CTD_LAUNCH(k_chol_rows, ((unsigned)((rest + 127) / 128)), (128), 0, st, A, n, lda, k0, keep);
       const int64_t tb = (rest + NB - 1) / NB;
-      CTD_LAUNCH(k_chol_trailing, ((unsigned)(tb * (tb + 1) / 2)), (256), 0, st, A, n, lda, k0, nb);
+      CTD_LAUNCH(k_chol_trailing, ((unsigned)(tb * (tb + 1) / 2)), (256), 0, st, A, n, lda, k0,
+                 nb);
     }
   }
 }
@@ -362,6 +370,101 @@ void u_from_linv(const double* Z, int64_t n, int64_t ldz, double* U, int64_t ldu
                  cudaStream_t st) {
   dgemm_tri_lower(Z, n, ldz, U, ldu, st);
   launch_symmetrize(U, n, ldu, st);
+}
+
+// ---------------------------------------------------------------------------
+// B <- L^{-1} B for lower-triangular L (n x n) and nrhs right-hand sides,
+// by blocked forward substitution: each 32-row diagonal block is solved by
+// substitution (one thread per right-hand side), then the rows below are
+// updated with a GEMM.  Substitution keeps the solve backward stable, which
+// the independence test needs: pivots ||x||^2 - ||L^{-1} R^T x||^2 then carry
+// errors of order n u ||x||^2, not kappa(L) u ||x||^2.
+// ---------------------------------------------------------------------------
+__global__ void k_trsm_diag(const double* __restrict__ L, int64_t ldl, int64_t n, int64_t k0,
+                            double* __restrict__ B, int64_t ldb, int64_t nrhs) {
+  __shared__ double Ls[NB][NB + 1];
+  const int nb = (int)min((int64_t)NB, n - k0);
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e % NB, c = e / NB;
+    Ls[r][c] = (r < nb && c <= r) ? L[(k0 + r) + (k0 + c) * ldl] : 0.0;
+  }
+  __syncthreads();
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nrhs) return;
+  double x[NB];
+  double* col = B + j * ldb + k0;
+#pragma unroll
+  for (int r = 0; r < NB; ++r) x[r] = r < nb ? col[r] : 0.0;
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    if (r < nb) {
+      double s = x[r];
+#pragma unroll
+      for (int c = 0; c < r; ++c) s = fma(-Ls[r][c], x[c], s);
+      x[r] = s / Ls[r][r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NB; ++r)
+    if (r < nb) col[r] = x[r];
+}
+
+void tri_solve_lower(const double* L, int64_t ldl, int64_t n, double* B, int64_t ldb, int64_t nrhs,
+                     cudaStream_t st) {
+  if (n <= 0 || nrhs <= 0) return;
+  for (int64_t k0 = 0; k0 < n; k0 += NB) {
+    const int64_t nb = std::min<int64_t>(NB, n - k0);
+    CTD_LAUNCH(k_trsm_diag, ((unsigned)((nrhs + 127) / 128)), (128), 0, st, L, ldl, n, k0, B, ldb,
+               nrhs);
+    const int64_t rest = n - k0 - nb;
+    if (rest > 0)
+      dgemm(false, false, rest, nrhs, nb, -1.0, L + (k0 + nb) + k0 * ldl, ldl, B + k0, ldb, 1.0,
+            B + k0 + nb, ldb, st);
+  }
+}
+
+// B <- L^{-T} B (backward substitution with the transpose of lower L).
+__global__ void k_trsm_diag_T(const double* __restrict__ L, int64_t ldl, int64_t n, int64_t k0,
+                              double* __restrict__ B, int64_t ldb, int64_t nrhs) {
+  __shared__ double Ls[NB][NB + 1];
+  const int nb = (int)min((int64_t)NB, n - k0);
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e % NB, c = e / NB;
+    Ls[r][c] = (r < nb && c <= r) ? L[(k0 + r) + (k0 + c) * ldl] : 0.0;
+  }
+  __syncthreads();
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nrhs) return;
+  double x[NB];
+  double* col = B + j * ldb + k0;
+#pragma unroll
+  for (int r = 0; r < NB; ++r) x[r] = r < nb ? col[r] : 0.0;
+#pragma unroll
+  for (int r = NB - 1; r >= 0; --r) {
+    if (r < nb) {
+      double s = x[r];
+#pragma unroll
+      for (int c = r + 1; c < NB; ++c)
+        if (c < nb) s = fma(-Ls[c][r], x[c], s);
+      x[r] = s / Ls[r][r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NB; ++r)
+    if (r < nb) col[r] = x[r];
+}
+
+void tri_solve_lower_T(const double* L, int64_t ldl, int64_t n, double* B, int64_t ldb,
+                       int64_t nrhs, cudaStream_t st) {
+  if (n <= 0 || nrhs <= 0) return;
+  const int64_t last = ((n - 1) / NB) * NB;
+  for (int64_t k0 = last; k0 >= 0; k0 -= NB) {
+    const int64_t nb = std::min<int64_t>(NB, n - k0);
+    CTD_LAUNCH(k_trsm_diag_T, ((unsigned)((nrhs + 127) / 128)), (128), 0, st, L, ldl, n, k0, B,
+               ldb, nrhs);
+    if (k0 > 0)  // B[0:k0] -= L[k0:k0+nb, 0:k0]^T B[k0:k0+nb]
+      dgemm(true, false, k0, nrhs, nb, -1.0, L + k0, ldl, B + k0, ldb, 1.0, B, ldb, st);
+  }
 }
 
 // ---------------------------------------------------------------------------

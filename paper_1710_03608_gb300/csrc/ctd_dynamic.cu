@@ -1,28 +1,663 @@
-// CTD-D (Algorithm 2): placeholder until the dynamic path lands.
+// CTD-D (Algorithm 2): one time step on a new slice dX.
+//
+// Lines 1-4 are those of Algorithm 1 on dX alone (counter (k, t, stream)).
+// Line 5 warm-starts from R^(t), U^(t).  Lines 6-16 test the d' candidates
+// in order against the growing R^(t+1).  For a block of candidates X_c the
+// squared residual of candidate k against R^(t) and the candidates kept
+// before it is the pivot of an in-order Cholesky (with skip) of the Schur
+// complement
+//     S = X_c^T X_c - W^T W,   W = L^{-1} B,   B = R^(t)^T X_c,
+// where L L^T = R^(t)^T R^(t) is kept across steps (L^(t+1) =
+// [[L, 0], [W_K^T, L_S]]).  W comes from forward substitution, so the pivots
+// are backward stable (errors ~ n u ||x||^2); forming S as X_c^T X_c -
+// B^T U B with the explicit inverse would amplify them by kappa and keep
+// dependent fibers.  The block form takes the same decisions as the
+// sequential loop.  With Y_K = U^(t) B_K and S_K = L_S L_S^T, the rank-|K|
+// update of U is the block form of the line-13 update applied |K| times:
+//     U^(t+1) = [[U + Y_K S_K^{-1} Y_K^T, -Y_K S_K^{-1}], [., S_K^{-1}]].
+// Lines 17-21: the new columns R^(t+1)^T dX are computed exactly; the
+// lower-left block ((dR)^T R^(t)) U^(t) C^(t) of Eq. (C_t+1_final) is kept
+// as M_{t+1} = ((dR)^T R^(t)) U^(t) = Y_K^T (the paper's left-to-right
+// order) and applied to old columns when they are read.
+// The error of the old columns does not change (their reconstruction
+// R^(t+1) U^(t+1) [C; M C] equals R^(t) U^(t) C), so the relative error
+// accumulates ||dX||^2 - ||P_{t+1} dX||^2 per step, with
+// ||P_{t+1} dX||^2 = ||L^{-1} C_new||_F^2 over the new columns C_new (the
+// same as sum_f c_f^T U^(t+1) c_f, but backward stable).
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
 #include "ctd_internal.cuh"
 
 using namespace ctd;
 
-struct ctd_factors::Dyn {};
+namespace {
+
+struct StepRec {
+  int64_t d_draws = 0, d_unique = 0, d_kept = 0, d_before = 0, nnz = 0;
+  double sq = 0.0, err = 0.0;      // ||dX||^2 and ||dX - P dX||^2
+  double* M = nullptr;             // Y_K: d_before x d_kept column-major (= M row-major)
+  uint64_t* Coff = nullptr;        // new-column block, height d_before + d_kept
+  uint32_t* Ccnt = nullptr;
+  int32_t* Crow = nullptr;
+  void* Cval = nullptr;
+  int64_t nnzC = 0;
+};
+
+__global__ void k_gather_cols_f64(const double* __restrict__ A, int64_t lda, int64_t m,
+                                  const int* __restrict__ idx, int n, double* __restrict__ out,
+                                  int64_t ldo) {
+  const int64_t total = m * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % m, c = e / m;
+    out[r + c * ldo] = A[r + (int64_t)idx[c] * lda];
+  }
+}
+
+// out (n x m) = A^T for A (m x n)
+__global__ void k_transpose_f64(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                                double* __restrict__ out, int64_t ldo) {
+  const int64_t total = m * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % m, c = e / m;
+    out[c + r * ldo] = A[r + c * lda];
+  }
+}
+
+// dense (ld x J) FP64 copy of a sparse new-column block (rows < height)
+template <typename V>
+__global__ void k_densify(const unsigned long long* __restrict__ coff,
+                          const unsigned* __restrict__ ccnt, const int32_t* __restrict__ crow,
+                          const V* __restrict__ cval, int64_t n_cols, double* __restrict__ out,
+                          int64_t ld) {
+  for (int64_t f = blockIdx.x; f < n_cols; f += gridDim.x) {
+    const unsigned long long o = coff[f];
+    for (unsigned q = threadIdx.x; q < ccnt[f]; q += blockDim.x)
+      out[f * ld + crow[o + q]] = (double)cval[o + q];
+  }
+}
+
+__global__ void k_sumsq(const double* __restrict__ A, int64_t n, double* __restrict__ out) {
+  __shared__ double part[32];
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc = fma(A[e], A[e], acc);
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    *out = t;
+  }
+}
+
+__global__ void k_add_offset(const unsigned long long* __restrict__ in, int64_t n,
+                             unsigned long long off, unsigned long long* __restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = in[e] + off;
+}
+
+}  // namespace
+
+struct ctd_factors::Dyn {
+  int64_t I = 0, J = 0;
+  unsigned flags = 0;
+  int64_t t = 0;
+  int64_t cap_d = 0;                 // leading dimension of U
+  int64_t cap_cols = 0, cap_nnz = 0;
+  std::vector<StepRec> steps;
+  std::vector<int64_t> fiber_id, fiber_step;
+  double err_num = 0.0, err_den = 0.0;
+  double sq_total = 0.0;
+  int64_t nnz_total = 0, nnzC_total = 0;
+  int64_t last_d = 0, last_du = 0;
+  bool all_positive = true;          // every value seen so far > 0
+  double max_T = 0.0;                // largest ||dX||^2 so far
+  int64_t* lastI = nullptr;          // device [8192]
+  int64_t* lastIu = nullptr;
+};
+
+ctd_factors::~ctd_factors() {
+  if (dyn) {
+    cudaStreamSynchronize(stream);
+    for (auto& s : dyn->steps) {
+      dfree(s.M, stream);
+      dfree(s.Coff, stream);
+      dfree(s.Ccnt, stream);
+      dfree(s.Crow, stream);
+      dfree(s.Cval, stream);
+    }
+    dfree(dyn->lastI, stream);
+    dfree(dyn->lastIu, stream);
+    dfree(U, stream);
+    dfree(L, stream);
+    L = nullptr;
+    dfree(Rcolptr, stream);
+    dfree(Rrow, stream);
+    dfree(Rval, stream);
+    dfree(Rrowptr, stream);
+    dfree(Rcol, stream);
+    dfree(Rcval, stream);
+    U = nullptr;
+    delete dyn;
+    dyn = nullptr;
+  }
+}
 
 extern "C" ctd_status ctd_dynamic_create(const int64_t dims2[2], int alpha, int precision,
-                                         uint64_t seed, uint64_t stream_id, ctd_factors** state) {
-  (void)dims2; (void)alpha; (void)precision; (void)seed; (void)stream_id; (void)state;
-  return fail(CTD_ENOTSUP, "CTD-D is not built yet");
+                                         uint64_t seed, uint64_t stream_id, unsigned flags,
+                                         ctd_factors** state) {
+  if (!dims2 || !state) return fail(CTD_EINVAL, "NULL argument");
+  if (alpha != 1 && alpha != 2) return fail(CTD_EINVAL, "alpha must be 1 or 2 (time is mode 3)");
+  if (dims2[0] < 1 || dims2[1] < 1 || dims2[0] > INT32_MAX || dims2[1] > INT32_MAX)
+    return fail(CTD_EINVAL, "slice dimensions must be in [1, 2^31)");
+  if (precision != CTD_FP64 && precision != CTD_FP32_BULK)
+    return fail(CTD_EINVAL, "unknown precision");
+  if (flags & ~(unsigned)CTD_KEEP_LAST_C) return fail(CTD_EINVAL, "unknown flag");
+  ctd_factors* F = new ctd_factors();
+  F->kind = 1;
+  F->alpha = alpha;
+  F->precision = precision;
+  F->seed = seed;
+  F->stream_id = stream_id;
+  F->dims[0] = dims2[0];
+  F->dims[1] = dims2[1];
+  F->dims[2] = 1;
+  mode_extents(F->dims, alpha, &F->n_rows, &F->n_cols);
+  F->dyn = new ctd_factors::Dyn();
+  F->dyn->I = dims2[0];
+  F->dyn->J = dims2[1];
+  F->dyn->flags = flags;
+  ctd_status rc = dalloc_n(&F->dyn->lastI, 8192, nullptr);
+  if (rc == CTD_OK) rc = dalloc_n(&F->dyn->lastIu, 8192, nullptr);
+  if (rc == CTD_OK) rc = dalloc_n(&F->Rcolptr, 1, nullptr);
+  if (rc == CTD_OK && cudaMemsetAsync(F->Rcolptr, 0, 8, nullptr) != cudaSuccess)
+    rc = fail(CTD_ECUDA, "memset failed");
+  if (rc == CTD_OK && cudaStreamSynchronize(nullptr) != cudaSuccess)
+    rc = fail(CTD_ECUDA, "synchronize failed");
+  if (rc != CTD_OK) {
+    delete F;
+    return rc;
+  }
+  *state = F;
+  return CTD_OK;
 }
 
-extern "C" ctd_status ctd_dynamic_step(ctd_factors* state, const ctd_coo3* dX, int64_t d,
-                                       double eps, void* stream) {
-  (void)state; (void)dX; (void)d; (void)eps; (void)stream;
-  return fail(CTD_ENOTSUP, "CTD-D is not built yet");
+// grow U and L (ld cap) to hold n x n, keeping the leading d x d blocks
+static ctd_status grow_U(ctd_factors* F, int64_t d, int64_t n, cudaStream_t st) {
+  auto& D = *F->dyn;
+  if (n <= D.cap_d) return CTD_OK;
+  int64_t cap = std::max<int64_t>(std::max<int64_t>(2 * D.cap_d, n), 256);
+  double *U2, *L2;
+  CTD_TRY(dalloc_n(&U2, (size_t)cap * cap, st));
+  CTD_TRY(dalloc_n(&L2, (size_t)cap * cap, st));
+  CTD_CUDA(cudaMemsetAsync(L2, 0, (size_t)cap * cap * 8, st));
+  if (d > 0) {
+    CTD_CUDA(cudaMemcpy2DAsync(U2, cap * 8, F->U, D.cap_d * 8, d * 8, d,
+                               cudaMemcpyDeviceToDevice, st));
+    CTD_CUDA(cudaMemcpy2DAsync(L2, cap * 8, F->L, D.cap_d * 8, d * 8, d,
+                               cudaMemcpyDeviceToDevice, st));
+  }
+  dfree(F->U, st);
+  dfree(F->L, st);
+  F->U = U2;
+  F->L = L2;
+  D.cap_d = cap;
+  return CTD_OK;
 }
 
-extern "C" ctd_status ctd_get_step(const ctd_factors* F, int64_t t, int64_t info[4], double sq[2]) {
-  (void)F; (void)t; (void)info; (void)sq;
-  return fail(CTD_ENOTSUP, "CTD-D is not built yet");
+template <typename T>
+static ctd_status grow_array(T** p, int64_t used, int64_t need, int64_t* cap, cudaStream_t st) {
+  if (need <= *cap) return CTD_OK;
+  int64_t c = std::max<int64_t>(std::max<int64_t>(2 * *cap, need), 1024);
+  T* q;
+  CTD_TRY(dalloc_n(&q, c, st));
+  if (used > 0) CTD_CUDA(cudaMemcpyAsync(q, *p, used * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  dfree(*p, st);
+  *p = q;
+  *cap = c;
+  return CTD_OK;
+}
+
+extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int64_t d, double eps,
+                                       void* stream) {
+  if (!F || !dXd) return fail(CTD_EINVAL, "NULL argument");
+  if (F->kind != 1 || !F->dyn) return fail(CTD_EINVAL, "not a CTD-D state");
+  if (d < 1 || d > 8192) return fail(CTD_EINVAL, "d must be in [1, 8192]");
+  if (!(eps >= 0.0 && eps < 1.0)) return fail(CTD_EINVAL, "eps must be in [0, 1)");
+  auto& D = *F->dyn;
+  if (dXd->dims[0] != D.I || dXd->dims[1] != D.J || dXd->dims[2] != 1)
+    return fail(CTD_EINVAL, "slice dimensions differ from the state's");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  F->stream = st;
+  Arena scratch;
+  scratch.st = st;
+  CooDev X;
+  CTD_TRY(stage_coo(dXd, F->alpha, scratch, st, &X));
+  const int64_t dt = F->s_kept;
+  const bool fp32 = F->precision == CTD_FP32_BULK;
+  StepRec rec;
+  rec.d_draws = d;
+  rec.d_before = dt;
+  rec.nnz = X.nnz;
+
+  // lines 1-4
+  Matricized M;
+  {
+    PhaseScope ph("d_matricize", st);
+    CTD_TRY(matricize(X, false, scratch, st, &M));
+  }
+  int* d_count;
+  CTD_TRY(scratch.get(&d_count, 4));
+  {
+    PhaseScope ph("d_sample_unique", st);
+    launch_sample(M.cdf, M.n_cols, d, F->seed, (uint64_t)D.t, F->stream_id, D.lastI, st);
+    launch_sort_unique(D.lastI, d, D.lastIu, d_count, st);
+  }
+  unsigned status = 0;
+  int du = 0, minval = 0;
+  uint64_t T = 0;
+  CTD_TRY(d2h(&minval, M.minval, 1, st));
+  CTD_TRY(d2h(&status, M.status, 1, st));
+  CTD_TRY(d2h(&du, d_count, 1, st));
+  if (M.n_cols > 0) CTD_TRY(d2h(&T, M.cdf + (M.n_cols - 1), 1, st));
+  CTD_CUDA(cudaGetLastError());
+  CTD_TRY(sync(st));
+  CTD_TRY(status_from_device(status));
+  rec.sq = (double)T;
+  rec.d_unique = du;
+  if (X.nnz > 0 && minval <= 0) D.all_positive = false;
+  D.max_T = std::max(D.max_T, (double)T);
+  D.last_d = T ? d : 0;
+  D.last_du = du;
+
+  int kept = 0;
+  int* idx = nullptr;
+  FilterOut fo;
+  double* Bm = nullptr;   // R^(t)^T X_c
+  double* W = nullptr;    // L^{-1} R^(t)^T X_c
+  if (du > 0) {
+    // candidates X_c (CSC and by row)
+    uint64_t *rc_sizes, *rc_ptr, *rcr_ptr;
+    CTD_TRY(scratch.get(&rc_sizes, du + 1));
+    CTD_TRY(scratch.get(&rc_ptr, du + 1));
+    launch_column_sizes(M.colptr, D.lastIu, d_count, du, rc_sizes, st);
+    launch_scan_u64(rc_sizes, rc_ptr, du, false, M.tmp, M.status, st);
+    uint64_t nnz_cand = 0;
+    CTD_TRY(d2h(&nnz_cand, rc_ptr + du, 1, st));
+    CTD_TRY(sync(st));
+    int32_t *rc_row, *rc_val, *rcr_col, *rcr_val;
+    CTD_TRY(scratch.get(&rc_row, nnz_cand));
+    CTD_TRY(scratch.get(&rc_val, nnz_cand));
+    CTD_TRY(scratch.get(&rcr_col, nnz_cand));
+    CTD_TRY(scratch.get(&rcr_val, nnz_cand));
+    CTD_TRY(scratch.get(&rcr_ptr, M.n_rows + 1));
+    launch_gather_columns(M.colptr, M.csc_row, M.csc_val, D.lastIu, d_count, du, rc_ptr, rc_row,
+                          rc_val, st);
+    CTD_TRY(build_csr_from_csc(rc_ptr, rc_row, rc_val, du, (int64_t)nnz_cand, M.n_rows, 0,
+                               rcr_ptr, rcr_col, rcr_val, scratch, st));
+    // Gram of the candidates and the Schur complement against R^(t)
+    double *S, *xn2;
+    CTD_TRY(scratch.get(&S, (size_t)du * du));
+    CTD_TRY(scratch.get(&xn2, du));
+    {
+      PhaseScope ph("d_gram", st);
+      CTD_TRY(launch_spmm_dense(M.csc(), D.lastIu, d_count, du,
+                                CsrDev{rcr_ptr, rcr_col, rcr_val, du}, S, du, st));
+      launch_thresholds(S, du, du, 1.0, xn2, st);  // ||x_k||^2
+      if (dt > 0) {
+        // B = R^(t)^T X_c (exact), W = L^{-1} B, S = X_c^T X_c - W^T W
+        CTD_TRY(scratch.get(&Bm, (size_t)dt * du));
+        CTD_TRY(scratch.get(&W, (size_t)dt * du));
+        CTD_TRY(launch_spmm_dense(M.csc(), D.lastIu, d_count, du,
+                                  CsrDev{F->Rrowptr, F->Rcol, F->Rcval, (int)dt}, Bm, dt, st));
+        CTD_CUDA(cudaMemcpyAsync(W, Bm, (size_t)dt * du * 8, cudaMemcpyDeviceToDevice, st));
+        tri_solve_lower(F->L, D.cap_d, dt, W, dt, du, st);
+        dgemm(true, false, du, du, dt, -1.0, W, dt, W, dt, 1.0, S, du, st);
+      }
+    }
+    FilterIn fi;
+    fi.du = du;
+    fi.S = S;
+    fi.xnorm2 = xn2;
+    fi.eps = eps;
+    fi.cptr = rc_ptr;
+    fi.crow = rc_row;
+    fi.cval = rc_val;
+    fi.n_rows = M.n_rows;
+    if (dt > 0) {
+      fi.dt = dt;
+      fi.Lt = F->L;
+      fi.ldl = D.cap_d;
+      fi.W = W;
+      fi.rptr = F->Rcolptr;
+      fi.rrow = F->Rrow;
+      fi.rval = F->Rval;
+    }
+    CTD_TRY(run_filter(fi, fo, scratch, st));
+    kept = fo.kept;
+    idx = fo.idx;
+    rec.d_kept = kept;
+
+    if (kept > 0) {
+      PhaseScope ph("d_update_u", st);
+      const int64_t dn = dt + kept;
+      double* L = fo.Lk;   // factor of the kept block of S
+      double* Li = fo.Li;  // its inverse
+      double* Sinv;
+      CTD_TRY(scratch.get(&Sinv, (size_t)kept * kept));
+      u_from_linv(Li, kept, kept, Sinv, kept, st);
+      CTD_TRY(grow_U(F, dt, dn, st));
+      const int64_t ld = D.cap_d;
+      if (dt > 0) {
+        // Y_K = U^(t) B_K; M_{t+1} = Y_K^T = ((dR)^T R^(t)) U^(t), kept for C's lower-left blocks
+        double *BK, *WK, *Z;
+        CTD_TRY(scratch.get(&BK, (size_t)dt * kept));
+        CTD_TRY(scratch.get(&WK, (size_t)dt * kept));
+        CTD_TRY(scratch.get(&Z, (size_t)dt * kept));
+        CTD_TRY(dalloc_n(&rec.M, (size_t)dt * kept, st));
+        const unsigned gk = grid_for(dt * kept, 256, (int64_t)num_sms() * 8);
+        CTD_LAUNCH(k_gather_cols_f64, (gk), (256), 0, st, Bm, dt, dt, idx, kept, BK, dt);
+        CTD_LAUNCH(k_gather_cols_f64, (gk), (256), 0, st, W, dt, dt, idx, kept, WK, dt);
+        dgemm(false, false, dt, kept, dt, 1.0, F->U, ld, BK, dt, 0.0, rec.M, dt, st);
+        // U^(t+1): [[U + Z Z^T, -Z L_S^{-1}], [., S_K^{-1}]] with Z = Y_K L_S^{-T}
+        dgemm(false, true, dt, kept, kept, 1.0, rec.M, dt, Li, kept, 0.0, Z, dt, st);
+        dgemm(false, true, dt, dt, kept, 1.0, Z, dt, Z, dt, 1.0, F->U, ld, st);
+        dgemm(false, false, dt, kept, kept, -1.0, Z, dt, Li, kept, 0.0, F->U + dt * ld, ld, st);
+        CTD_LAUNCH(k_transpose_f64, (gk), (256), 0, st, F->U + dt * ld, ld, dt, kept, F->U + dt,
+                   ld);
+        // L^(t+1) = [[L, 0], [W_K^T, L_S]]
+        CTD_LAUNCH(k_transpose_f64, (gk), (256), 0, st, WK, dt, dt, kept, F->L + dt, ld);
+      }
+      CTD_CUDA(cudaMemcpy2DAsync(F->L + dt + dt * ld, ld * 8, L, kept * 8, kept * 8, kept,
+                                 cudaMemcpyDeviceToDevice, st));
+      CTD_CUDA(cudaMemcpy2DAsync(F->U + dt + dt * ld, ld * 8, Sinv, kept * 8, kept * 8, kept,
+                                 cudaMemcpyDeviceToDevice, st));
+      // append dR to R (CSC), then rebuild the by-row copy
+      int64_t* newf;
+      uint64_t *nsz, *nptr;
+      CTD_TRY(scratch.get(&newf, kept));
+      CTD_TRY(scratch.get(&nsz, kept + 1));
+      CTD_TRY(scratch.get(&nptr, kept + 1));
+      launch_gather_i64(D.lastIu, idx, fo.count, kept, newf, st);
+      launch_column_sizes(M.colptr, newf, fo.count, kept, nsz, st);
+      launch_scan_u64(nsz, nptr, kept, false, M.tmp, M.status, st);
+      uint64_t nnz_new = 0;
+      std::vector<int64_t> hf(kept);
+      CTD_TRY(d2h(&nnz_new, nptr + kept, 1, st));
+      CTD_TRY(d2h(hf.data(), newf, kept, st));
+      CTD_TRY(sync(st));
+      const int64_t nnzR = F->nnz_R;
+      int64_t cap_cols = D.cap_cols + 1;
+      CTD_TRY(grow_array(&F->Rcolptr, dt + 1, dn + 1, &cap_cols, st));
+      D.cap_cols = cap_cols - 1;
+      int64_t cap_nnz_r = D.cap_nnz, cap_nnz_v = D.cap_nnz;
+      CTD_TRY(grow_array(&F->Rrow, nnzR, nnzR + (int64_t)nnz_new, &cap_nnz_r, st));
+      CTD_TRY(grow_array(&F->Rval, nnzR, nnzR + (int64_t)nnz_new, &cap_nnz_v, st));
+      D.cap_nnz = cap_nnz_r;
+      launch_gather_columns(M.colptr, M.csc_row, M.csc_val, newf, fo.count, kept, nptr,
+                            F->Rrow + nnzR, F->Rval + nnzR, st);
+      CTD_LAUNCH(k_add_offset, (grid_for(kept + 1, 256, 64)), (256), 0, st,
+                 reinterpret_cast<const unsigned long long*>(nptr), kept + 1,
+                 (unsigned long long)nnzR,
+                 reinterpret_cast<unsigned long long*>(F->Rcolptr + dt));
+      F->nnz_R = nnzR + (int64_t)nnz_new;
+      F->s_kept = dn;
+      for (int q = 0; q < kept; ++q) {
+        D.fiber_id.push_back(hf[q]);
+        D.fiber_step.push_back(D.t);
+      }
+      dfree(F->Rrowptr, st);
+      dfree(F->Rcol, st);
+      dfree(F->Rcval, st);
+      CTD_TRY(dalloc_n(&F->Rrowptr, M.n_rows + 1, st));
+      CTD_TRY(dalloc_n(&F->Rcol, std::max<int64_t>(F->nnz_R, 1), st));
+      CTD_TRY(dalloc_n(&F->Rcval, std::max<int64_t>(F->nnz_R, 1), st));
+      CTD_TRY(build_csr_from_csc(F->Rcolptr, F->Rrow, F->Rval, dn, F->nnz_R, M.n_rows, 0,
+                                 F->Rrowptr, F->Rcol, F->Rcval, scratch, st));
+    }
+  }
+
+  // lines 17-21: the new columns R^(t+1)^T dX (exact), and the error increment
+  const int64_t dn = F->s_kept;
+  double pu = 0.0;
+  if (dn > 0 && X.nnz > 0) {
+    CsrDev R{F->Rrowptr, F->Rcol, F->Rcval, (int)dn};
+    uint32_t* ub;
+    CTD_TRY(scratch.get(&ub, M.n_cols));
+    CTD_TRY(dalloc_n(&rec.Coff, M.n_cols + 1, st));
+    CTD_TRY(dalloc_n(&rec.Ccnt, M.n_cols, st));
+    {
+      PhaseScope ph("d_c_bounds", st);
+      launch_c_bounds(M.csc(), M.n_cols, R, ub, st);
+      launch_scan_u32(ub, rec.Coff, M.n_cols, false, M.tmp, M.status, st);
+    }
+    uint64_t cap = 0;
+    CTD_TRY(d2h(&cap, rec.Coff + M.n_cols, 1, st));
+    CTD_TRY(sync(st));
+    CTD_TRY(dalloc_n(&rec.Crow, std::max<uint64_t>(cap, 1), st));
+    CTD_TRY(dalloc(&rec.Cval, std::max<uint64_t>(cap, 1) * (fp32 ? 4 : 8), st));
+    {
+      PhaseScope ph("d_c_fill", st);
+      CTD_TRY(launch_c_fill(M.csc(), M.n_cols, R, rec.Coff, rec.Ccnt, rec.Crow, rec.Cval, fp32,
+                            !D.all_positive, D.all_positive, (uint64_t)D.max_T, st));
+    }
+    double* d_pu;
+    uint64_t* d_nnzc;
+    CTD_TRY(scratch.get(&d_pu, 1));
+    CTD_TRY(scratch.get(&d_nnzc, 1));
+    {
+      // ||P_{t+1} dX||^2 = ||L^{-1} R^(t+1)^T dX||_F^2, by forward substitution
+      PhaseScope ph("d_error", st);
+      double* Cd;
+      CTD_TRY(scratch.get(&Cd, (size_t)dn * M.n_cols));
+      CTD_CUDA(cudaMemsetAsync(Cd, 0, (size_t)dn * M.n_cols * 8, st));
+      const unsigned g = grid_for(M.n_cols, 1, (int64_t)num_sms() * 16);
+      const auto* co = reinterpret_cast<const unsigned long long*>(rec.Coff);
+      if (fp32)
+        CTD_LAUNCH(k_densify<float>, (g), (128), 0, st, co, rec.Ccnt, rec.Crow,
+                   static_cast<const float*>(rec.Cval), M.n_cols, Cd, dn);
+      else
+        CTD_LAUNCH(k_densify<double>, (g), (128), 0, st, co, rec.Ccnt, rec.Crow,
+                   static_cast<const double*>(rec.Cval), M.n_cols, Cd, dn);
+      tri_solve_lower(F->L, D.cap_d, dn, Cd, dn, M.n_cols, st);
+      CTD_LAUNCH(k_sumsq, (1), (1024), 0, st, Cd, dn * M.n_cols, d_pu);
+    }
+    launch_sum_u32(rec.Ccnt, M.n_cols, d_nnzc, st);
+    uint64_t nnzc = 0;
+    CTD_TRY(d2h(&pu, d_pu, 1, st));
+    CTD_TRY(d2h(&nnzc, d_nnzc, 1, st));
+    CTD_TRY(d2h(&status, M.status, 1, st));
+    CTD_CUDA(cudaGetLastError());
+    CTD_TRY(sync(st));
+    CTD_TRY(status_from_device(status));
+    rec.nnzC = (int64_t)nnzc;
+  }
+  rec.err = (double)T - pu;
+  if (rec.err < 0.0) rec.err = 0.0;
+  D.err_num += rec.err;
+  D.err_den += (double)T;
+  D.sq_total += (double)T;
+  D.nnz_total += X.nnz;
+  D.nnzC_total += rec.nnzC;
+  if ((D.flags & CTD_KEEP_LAST_C) && !D.steps.empty()) {
+    auto& prev = D.steps.back();
+    dfree(prev.Coff, st);
+    dfree(prev.Ccnt, st);
+    dfree(prev.Crow, st);
+    dfree(prev.Cval, st);
+    prev.Coff = nullptr;
+    prev.Ccnt = nullptr;
+    prev.Crow = nullptr;
+    prev.Cval = nullptr;
+  }
+  D.steps.push_back(rec);
+  D.t += 1;
+  F->nnz_X = D.nnz_total;
+  F->T = (uint64_t)D.sq_total;
+  F->nnz_C = D.nnzC_total;
+  F->have_err = true;
+  F->err = D.err_den > 0 ? D.err_num / D.err_den : 0.0;
+  return CTD_OK;
+}
+
+extern "C" ctd_status ctd_get_step(const ctd_factors* F, int64_t t, int64_t info[4],
+                                   double sq[2]) {
+  if (!F || !F->dyn) return fail(CTD_EINVAL, "not a CTD-D state");
+  if (t < 0 || t >= F->dyn->t) return fail(CTD_EINVAL, "step out of range");
+  const StepRec& r = F->dyn->steps[t];
+  if (info) {
+    info[0] = r.d_unique;
+    info[1] = r.d_kept;
+    info[2] = r.d_before;
+    info[3] = r.nnz;
+  }
+  if (sq) {
+    sq[0] = r.sq;
+    sq[1] = r.err;
+  }
+  return CTD_OK;
 }
 
 extern "C" ctd_status ctd_get_M(const ctd_factors* F, int64_t t, double* M) {
-  (void)F; (void)t; (void)M;
-  return fail(CTD_ENOTSUP, "CTD-D is not built yet");
+  if (!F || !F->dyn) return fail(CTD_EINVAL, "not a CTD-D state");
+  if (t < 0 || t >= F->dyn->t) return fail(CTD_EINVAL, "step out of range");
+  const StepRec& r = F->dyn->steps[t];
+  const size_t n = (size_t)r.d_kept * r.d_before;
+  if (n == 0) return CTD_OK;
+  if (!M || !r.M) return fail(CTD_EINVAL, "NULL argument");
+  CTD_TRY(d2h(M, r.M, n, F->stream));
+  return sync(F->stream);
 }
+
+// ---------------------------------------------------------------------------
+// dynamic getters used by the common entry points
+// ---------------------------------------------------------------------------
+namespace ctd {
+
+ctd_status dyn_sizes(const ctd_factors* F, ctd_sizes* o) {
+  const auto& D = *F->dyn;
+  o->n_rows = F->n_rows;
+  o->n_cols = F->n_cols;
+  o->s_draws = D.last_d;
+  o->s_unique = D.last_du;
+  o->s_kept = F->s_kept;
+  o->nnz_R = F->nnz_R;
+  o->nnz_C = D.nnzC_total;
+  o->t_steps = D.t;
+  o->nnz_X = D.nnz_total;
+  o->sqnorm_X = D.sq_total;
+  return CTD_OK;
+}
+
+ctd_status dyn_samples(const ctd_factors* F, int64_t* I, int64_t* Iu) {
+  const auto& D = *F->dyn;
+  if (I) CTD_TRY(d2h(I, D.lastI, (size_t)D.last_d, F->stream));
+  if (Iu) CTD_TRY(d2h(Iu, D.lastIu, (size_t)D.last_du, F->stream));
+  return sync(F->stream);
+}
+
+ctd_status dyn_fibers(const ctd_factors* F, int64_t* fiber, int64_t* step) {
+  const auto& D = *F->dyn;
+  for (size_t c = 0; c < D.fiber_id.size(); ++c) {
+    if (fiber) fiber[c] = D.fiber_id[c];
+    if (step) step[c] = D.fiber_step[c];
+  }
+  return CTD_OK;
+}
+
+ctd_status dyn_U(const ctd_factors* F, double* U) {
+  const int64_t n = F->s_kept;
+  if (n == 0) return CTD_OK;
+  CTD_CUDA(cudaMemcpy2DAsync(U, n * 8, F->U, F->dyn->cap_d * 8, n * 8, n,
+                             cudaMemcpyDeviceToHost, F->stream));
+  return sync(F->stream);
+}
+
+// Column (t, f) of C^(now): the step's exact block, then the rows each later
+// step appends, M_{t'} times the column so far (Eq. C_t+1_final, line 18).
+ctd_status dyn_C_columns(const ctd_factors* F, int64_t ncols, const int64_t* cols, double* out) {
+  const auto& D = *F->dyn;
+  const int64_t J = F->n_cols, h = F->s_kept;
+  cudaStream_t st = F->stream;
+  std::vector<std::vector<double>> Mh(D.steps.size());
+  for (int64_t c = 0; c < ncols; ++c) {
+    const int64_t t = cols[c] / J, f = cols[c] % J;
+    if (cols[c] < 0 || t >= D.t) return fail(CTD_EINVAL, "column out of range");
+    const StepRec& r = D.steps[t];
+    std::vector<double> v(r.d_before + r.d_kept, 0.0);
+    if (r.Coff) {
+      uint64_t off = 0;
+      uint32_t n = 0;
+      CTD_TRY(d2h(&off, r.Coff + f, 1, st));
+      CTD_TRY(d2h(&n, r.Ccnt + f, 1, st));
+      CTD_TRY(sync(st));
+      std::vector<int32_t> rows(n);
+      CTD_TRY(d2h(rows.data(), r.Crow + off, n, st));
+      if (F->precision == CTD_FP32_BULK) {
+        std::vector<float> vals(n);
+        CTD_TRY(d2h(vals.data(), static_cast<const float*>(r.Cval) + off, n, st));
+        CTD_TRY(sync(st));
+        for (uint32_t q = 0; q < n; ++q) v[rows[q]] = vals[q];
+      } else {
+        std::vector<double> vals(n);
+        CTD_TRY(d2h(vals.data(), static_cast<const double*>(r.Cval) + off, n, st));
+        CTD_TRY(sync(st));
+        for (uint32_t q = 0; q < n; ++q) v[rows[q]] = vals[q];
+      }
+    } else if (r.d_before + r.d_kept > 0 && r.nnz > 0) {
+      return fail(CTD_EINVAL, "this step's new columns were released (CTD_KEEP_LAST_C)");
+    }
+    for (int64_t t2 = t + 1; t2 < D.t; ++t2) {
+      const StepRec& q = D.steps[t2];
+      if (q.d_kept == 0) continue;
+      if (q.d_before != (int64_t)v.size()) return fail(CTD_EINVAL, "inconsistent step record");
+      std::vector<double>& Mq = Mh[t2];
+      if (Mq.empty() && q.d_before > 0) {
+        Mq.resize((size_t)q.d_before * q.d_kept);
+        CTD_TRY(d2h(Mq.data(), q.M, Mq.size(), st));
+        CTD_TRY(sync(st));
+      }
+      const size_t base = v.size();
+      v.resize(base + q.d_kept, 0.0);
+      for (int64_t a = 0; a < q.d_kept; ++a) {
+        double s = 0.0;
+        for (int64_t b = 0; b < q.d_before; ++b) s += Mq[(size_t)a * q.d_before + b] * v[b];
+        v[base + a] = s;
+      }
+    }
+    if ((int64_t)v.size() != h) return fail(CTD_EINVAL, "inconsistent column height");
+    std::copy(v.begin(), v.end(), out + c * h);
+  }
+  return CTD_OK;
+}
+
+ctd_status dyn_R(const ctd_factors* F, int64_t* colptr, int32_t* row, int32_t* val) {
+  const int64_t n = F->s_kept, nnz = F->nnz_R;
+  std::vector<uint64_t> p(n + 1);
+  std::vector<int32_t> r(nnz), v(nnz);
+  CTD_TRY(d2h(p.data(), F->Rcolptr, n + 1, F->stream));
+  CTD_TRY(d2h(r.data(), F->Rrow, nnz, F->stream));
+  CTD_TRY(d2h(v.data(), F->Rval, nnz, F->stream));
+  CTD_TRY(sync(F->stream));
+  std::vector<int64_t> ord;
+  for (int64_t c = 0; c < n; ++c) {
+    const int64_t a = (int64_t)p[c], b = (int64_t)p[c + 1];
+    ord.resize(b - a);
+    std::iota(ord.begin(), ord.end(), a);
+    std::sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return r[x] < r[y]; });
+    for (int64_t q = a; q < b; ++q) {
+      row[q] = r[ord[q - a]];
+      val[q] = v[ord[q - a]];
+    }
+    colptr[c] = a;
+  }
+  colptr[n] = (int64_t)p[n];
+  return CTD_OK;
+}
+
+}  // namespace ctd

@@ -1,0 +1,297 @@
+// The independence filter (Algorithm 1 lines 6-15, Algorithm 2 lines 6-16)
+// for a block of candidate fibers, with the sequential loop's decisions.
+//
+// Fast path: an in-order Cholesky with skip of the candidates' Schur
+// complement S (see ctd_dense.cu); its pivot for candidate k is
+// ||res_k||^2, the squared residual against R^(t) and the candidates kept
+// before k.  A Gram-based pivot carries an absolute error of order
+// u * |beta|^T |G| |beta| in the SQUARED residual, while the test compares
+// ||res|| with eps ||x|| and the paper's eps = 1e-6 puts eps^2 = 1e-12 within
+// reach of that error for fibers that depend on an ill-conditioned R.  So
+// every candidate whose pivot is below 1e-4 ||x_k||^2 (residual ratio below
+// 1e-2; independent fibers mostly sit far above) is re-tested the way the
+// loop states it: its coefficients gamma are solved through the factor, the
+// residual vector x_k - [R^(t), kept candidates before k] gamma is formed
+// explicitly, and one step of iterative refinement (the normal equations
+// solved again for that residual) removes most of the error the factor's
+// conditioning left in gamma.  The ratio ||res|| / ||x_k|| then has an error
+// far below eps even for kappa(R^T R) ~ 1e11.  If that test disagrees with
+// the pivot, the first disagreeing candidate's decision is fixed and the
+// factorization is redone.
+#include <algorithm>
+#include <vector>
+
+#include "ctd_internal.cuh"
+
+namespace ctd {
+
+namespace {
+
+constexpr double SUSPECT = 1e-4;  // pivot / ||x||^2 below this is re-tested
+
+// Stilde(:, c) = row k_c of the skip-Cholesky storage over kept columns
+// before k_c (zero elsewhere), indexed by kept position.
+__global__ void k_suspect_rows(const double* __restrict__ S, int64_t lds,
+                               const int* __restrict__ kept_idx, int kept,
+                               const int* __restrict__ sus, int nsus, double* __restrict__ out) {
+  const int64_t total = (int64_t)kept * nsus;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e % kept), c = (int)(e / kept);
+    const int k = sus[c], j = kept_idx[p];
+    out[e] = (j < k) ? S[k + (int64_t)j * lds] : 0.0;
+  }
+}
+
+__global__ void k_gather_cols(const double* __restrict__ A, int64_t lda, int64_t m,
+                              const int* __restrict__ idx, int n, double* __restrict__ out,
+                              int64_t ldo) {
+  const int64_t total = m * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % m, c = e / m;
+    out[r + c * ldo] = A[r + (int64_t)idx[c] * lda];
+  }
+}
+
+// One block per suspect: r = x_k - R^(t) gammaR - Xc[:, K] eta, ratio = ||r|| / ||x_k||.
+__global__ void k_explicit_residual(int64_t n_rows, const unsigned long long* __restrict__ cptr,
+                                    const int32_t* __restrict__ crow,
+                                    const int32_t* __restrict__ cval, int64_t dt,
+                                    const unsigned long long* __restrict__ rptr,
+                                    const int32_t* __restrict__ rrow,
+                                    const int32_t* __restrict__ rval,
+                                    const double* __restrict__ gammaR,
+                                    const int* __restrict__ kept_idx, int kept,
+                                    const double* __restrict__ eta, const int* __restrict__ sus,
+                                    const double* __restrict__ xnorm2, double* __restrict__ rbuf,
+                                    double* __restrict__ ratio, int init) {
+  __shared__ double part[32];
+  const int c = blockIdx.x;
+  const int k = sus[c];
+  double* r = rbuf + (int64_t)c * n_rows;
+  if (init) {
+    for (int64_t i = threadIdx.x; i < n_rows; i += blockDim.x) r[i] = 0.0;
+    __syncthreads();
+    for (unsigned long long p = cptr[k] + threadIdx.x; p < cptr[k + 1]; p += blockDim.x)
+      r[crow[p]] = (double)cval[p];
+  }
+  __syncthreads();
+  for (int64_t j = threadIdx.x; j < dt; j += blockDim.x) {
+    const double g = gammaR[j + (int64_t)c * dt];
+    if (g != 0.0)
+      for (unsigned long long q = rptr[j]; q < rptr[j + 1]; ++q)
+        atomicAdd(r + rrow[q], -g * (double)rval[q]);
+  }
+  for (int p = threadIdx.x; p < kept; p += blockDim.x) {
+    const double g = eta[p + (int64_t)c * kept];
+    const int col = kept_idx[p];
+    if (g != 0.0)
+      for (unsigned long long q = cptr[col]; q < cptr[col + 1]; ++q)
+        atomicAdd(r + crow[q], -g * (double)cval[q]);
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n_rows; i += blockDim.x) acc = fma(r[i], r[i], acc);
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    const double xn = xnorm2[k];
+    ratio[c] = xn > 0.0 ? sqrt(t) / sqrt(xn) : 0.0;
+  }
+}
+
+// h_R(j, c) = R^(t)(:, j) . r_c ; h_K(p, c) = x_{K[p]} . r_c for K[p] < k_c (else 0)
+__global__ void k_residual_dots(int64_t n_rows, const unsigned long long* __restrict__ cptr,
+                                const int32_t* __restrict__ crow, const int32_t* __restrict__ cval,
+                                int64_t dt, const unsigned long long* __restrict__ rptr,
+                                const int32_t* __restrict__ rrow, const int32_t* __restrict__ rval,
+                                const int* __restrict__ kept_idx, int kept,
+                                const int* __restrict__ sus, const double* __restrict__ rbuf,
+                                double* __restrict__ hR, double* __restrict__ hK) {
+  const int c = blockIdx.x;
+  const int k = sus[c];
+  const double* r = rbuf + (int64_t)c * n_rows;
+  for (int64_t j = threadIdx.x; j < dt; j += blockDim.x) {
+    double s = 0.0;
+    for (unsigned long long q = rptr[j]; q < rptr[j + 1]; ++q) s = fma((double)rval[q], r[rrow[q]], s);
+    hR[j + (int64_t)c * dt] = s;
+  }
+  for (int p = threadIdx.x; p < kept; p += blockDim.x) {
+    const int col = kept_idx[p];
+    double s = 0.0;
+    if (col < k)
+      for (unsigned long long q = cptr[col]; q < cptr[col + 1]; ++q)
+        s = fma((double)cval[q], r[crow[q]], s);
+    hK[p + (int64_t)c * kept] = s;
+  }
+}
+
+// zero entries (p, c) whose kept column is not before suspect c
+__global__ void k_mask_before(double* __restrict__ A, int kept, const int* __restrict__ kept_idx,
+                              const int* __restrict__ sus, int ns) {
+  const int64_t total = (int64_t)kept * ns;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e % kept), c = (int)(e / kept);
+    if (kept_idx[p] >= sus[c]) A[e] = 0.0;
+  }
+}
+
+}  // namespace
+
+ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaStream_t st) {
+  const int du = in.du;
+  out.kept = 0;
+  if (du <= 0) return CTD_OK;
+  double *S0, *thr, *xn2, *piv;
+  int* force;
+  int*& count = out.count;
+  unsigned* status;
+  CTD_TRY(scratch.get(&S0, (size_t)du * du));
+  CTD_TRY(scratch.get(&thr, du));
+  CTD_TRY(scratch.get(&xn2, du));
+  CTD_TRY(scratch.get(&piv, du));
+  CTD_TRY(scratch.get(&force, du));
+  CTD_TRY(scratch.get(&count, 1));
+  CTD_TRY(scratch.get(&status, 1));
+  CTD_TRY(scratch.get(&out.keep, du));
+  CTD_TRY(scratch.get(&out.idx, du));
+  CTD_CUDA(cudaMemcpyAsync(S0, in.S, (size_t)du * du * 8, cudaMemcpyDeviceToDevice, st));
+  CTD_CUDA(cudaMemcpyAsync(xn2, in.xnorm2, (size_t)du * 8, cudaMemcpyDeviceToDevice, st));
+  launch_thresholds(xn2, du, 0, in.eps * in.eps, thr, st);  // ld 0: a plain vector
+  CTD_CUDA(cudaMemsetAsync(force, 0xff, (size_t)du * sizeof(int), st));  // -1
+  CTD_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
+  std::vector<int> h_force(du, -1), h_keep(du);
+  std::vector<double> h_piv(du), h_xn(du);
+  CTD_TRY(d2h(h_xn.data(), xn2, du, st));
+  for (int iter = 0; iter <= du + 1; ++iter) {
+    if (iter > 0) {
+      CTD_CUDA(cudaMemcpyAsync(in.S, S0, (size_t)du * du * 8, cudaMemcpyDeviceToDevice, st));
+      CTD_CUDA(cudaMemcpyAsync(force, h_force.data(), (size_t)du * sizeof(int),
+                               cudaMemcpyHostToDevice, st));
+    }
+    {
+      PhaseScope ph("filter_chol", st);
+      launch_chol_skip(in.S, du, du, thr, out.keep, st, force, piv, status);
+      launch_compact_flags(out.keep, du, out.idx, count, st);
+    }
+    unsigned h_status = 0;
+    int kept = 0;
+    CTD_TRY(d2h(&kept, count, 1, st));
+    CTD_TRY(d2h(&h_status, status, 1, st));
+    CTD_TRY(d2h(h_piv.data(), piv, du, st));
+    CTD_TRY(d2h(h_keep.data(), out.keep, du, st));
+    CTD_CUDA(cudaGetLastError());
+    CTD_TRY(sync(st));
+    if (h_status & DEV_CAPACITY)
+      return fail(CTD_ENOTSUP,
+                  "a fiber tested independent by its explicit residual has no positive pivot "
+                  "(numerically ambiguous input)");
+    out.kept = kept;
+    CTD_TRY(scratch.get(&out.Lk, (size_t)std::max(kept, 1) * std::max(kept, 1)));
+    CTD_TRY(scratch.get(&out.Li, (size_t)std::max(kept, 1) * std::max(kept, 1)));
+    launch_gather_lower(in.S, du, out.idx, count, kept, out.Lk, kept, st);
+    tri_inverse(out.Lk, kept, kept, out.Li, kept, st);
+    std::vector<int> sus;
+    for (int k = 0; k < du; ++k)
+      if (h_xn[k] > 0.0 && h_piv[k] < SUSPECT * h_xn[k]) sus.push_back(k);
+    if (sus.empty()) return CTD_OK;
+    // explicit residuals of the suspects
+    PhaseScope ph("filter_recheck", st);
+    const int ns = (int)sus.size();
+    const int kk = std::max(kept, 1);
+    int* d_sus;
+    double *Stil, *eta, *ratio, *rbuf, *gammaR = nullptr;
+    CTD_TRY(scratch.get(&d_sus, ns));
+    CTD_TRY(scratch.get(&Stil, (size_t)kk * ns));
+    CTD_TRY(scratch.get(&eta, (size_t)kk * ns));
+    CTD_TRY(scratch.get(&ratio, ns));
+    CTD_TRY(scratch.get(&rbuf, (size_t)in.n_rows * ns));
+    CTD_CUDA(cudaMemcpyAsync(d_sus, sus.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
+    CTD_CUDA(cudaMemsetAsync(eta, 0, (size_t)kk * ns * 8, st));
+    if (kept > 0) {
+      CTD_LAUNCH(k_suspect_rows, (grid_for((int64_t)kept * ns, 256, 4096)), (256), 0, st, in.S,
+                 du, out.idx, kept, d_sus, ns, Stil);
+      dgemm(true, false, kept, ns, kept, 1.0, out.Li, kept, Stil, kept, 0.0, eta, kept, st);
+    }
+    if (in.dt > 0) {
+      CTD_TRY(scratch.get(&gammaR, (size_t)in.dt * ns));
+      CTD_LAUNCH(k_gather_cols, (grid_for(in.dt * ns, 256, (int64_t)num_sms() * 8)), (256), 0, st,
+                 in.W, in.dt, in.dt, d_sus, ns, gammaR, in.dt);
+      if (kept > 0) {
+        double* WK;
+        CTD_TRY(scratch.get(&WK, (size_t)in.dt * kept));
+        CTD_LAUNCH(k_gather_cols, (grid_for(in.dt * kept, 256, (int64_t)num_sms() * 8)), (256), 0,
+                   st, in.W, in.dt, in.dt, out.idx, kept, WK, in.dt);
+        dgemm(false, false, in.dt, ns, kept, -1.0, WK, in.dt, eta, kept, 1.0, gammaR, in.dt, st);
+      }
+      tri_solve_lower_T(in.Lt, in.ldl, in.dt, gammaR, in.dt, ns, st);
+    }
+    CTD_LAUNCH(k_explicit_residual, (ns), (256), 0, st, in.n_rows,
+               reinterpret_cast<const unsigned long long*>(in.cptr), in.crow, in.cval, in.dt,
+               reinterpret_cast<const unsigned long long*>(in.rptr), in.rrow, in.rval, gammaR,
+               out.idx, kept, eta, d_sus, xn2, rbuf, ratio, 1);
+    // one step of iterative refinement: solve the normal equations again for
+    // the residual's remaining component in range([R^(t), kept before k])
+    {
+      double *hR = nullptr, *hK, *zK, *etad;
+      CTD_TRY(scratch.get(&hK, (size_t)kk * ns));
+      CTD_TRY(scratch.get(&zK, (size_t)kk * ns));
+      CTD_TRY(scratch.get(&etad, (size_t)kk * ns));
+      if (in.dt > 0) CTD_TRY(scratch.get(&hR, (size_t)in.dt * ns));
+      CTD_LAUNCH(k_residual_dots, (ns), (256), 0, st, in.n_rows,
+                 reinterpret_cast<const unsigned long long*>(in.cptr), in.crow, in.cval, in.dt,
+                 reinterpret_cast<const unsigned long long*>(in.rptr), in.rrow, in.rval, out.idx,
+                 kept, d_sus, rbuf, hR, hK);
+      double* WK = nullptr;
+      if (in.dt > 0) {
+        tri_solve_lower(in.Lt, in.ldl, in.dt, hR, in.dt, ns, st);  // z_R
+        if (kept > 0) {
+          CTD_TRY(scratch.get(&WK, (size_t)in.dt * kept));
+          CTD_LAUNCH(k_gather_cols, (grid_for(in.dt * kept, 256, (int64_t)num_sms() * 8)), (256),
+                     0, st, in.W, in.dt, in.dt, out.idx, kept, WK, in.dt);
+          dgemm(true, false, kept, ns, in.dt, -1.0, WK, in.dt, hR, in.dt, 1.0, hK, kept, st);
+        }
+      }
+      CTD_CUDA(cudaMemsetAsync(etad, 0, (size_t)kk * ns * 8, st));
+      if (kept > 0) {
+        const unsigned gm = grid_for((int64_t)kept * ns, 256, 4096);
+        CTD_LAUNCH(k_mask_before, (gm), (256), 0, st, hK, kept, out.idx, d_sus, ns);
+        dgemm(false, false, kept, ns, kept, 1.0, out.Li, kept, hK, kept, 0.0, zK, kept, st);
+        CTD_LAUNCH(k_mask_before, (gm), (256), 0, st, zK, kept, out.idx, d_sus, ns);
+        dgemm(true, false, kept, ns, kept, 1.0, out.Li, kept, zK, kept, 0.0, etad, kept, st);
+      }
+      if (in.dt > 0) {
+        if (kept > 0)
+          dgemm(false, false, in.dt, ns, kept, -1.0, WK, in.dt, etad, kept, 1.0, hR, in.dt, st);
+        tri_solve_lower_T(in.Lt, in.ldl, in.dt, hR, in.dt, ns, st);  // delta gamma_R
+      }
+      CTD_LAUNCH(k_explicit_residual, (ns), (256), 0, st, in.n_rows,
+                 reinterpret_cast<const unsigned long long*>(in.cptr), in.crow, in.cval, in.dt,
+                 reinterpret_cast<const unsigned long long*>(in.rptr), in.rrow, in.rval, hR,
+                 out.idx, kept, etad, d_sus, xn2, rbuf, ratio, 0);
+    }
+    std::vector<double> h_ratio(ns);
+    CTD_TRY(d2h(h_ratio.data(), ratio, ns, st));
+    CTD_CUDA(cudaGetLastError());
+    CTD_TRY(sync(st));
+    bool changed = false;
+    for (int c = 0; c < ns && !changed; ++c) {
+      const int k = sus[c];
+      const int explicit_keep = h_ratio[c] > in.eps ? 1 : 0;  // equality: dependent (A4)
+      if (explicit_keep != h_keep[k]) {
+        h_force[k] = explicit_keep;
+        changed = true;
+      }
+    }
+    if (out.ratios) out.ratios->assign(h_ratio.begin(), h_ratio.end());
+    if (!changed) return CTD_OK;
+  }
+  return fail(CTD_ENOTSUP, "independence filter did not settle");
+}
+
+}  // namespace ctd

@@ -208,24 +208,28 @@ ctd_status launch_spmm_dense(const CscDev& X, const int64_t* fibers, const int* 
 void launch_c_bounds(const CscDev& X, int64_t n_cols, const CsrDev& R, uint32_t* ub,
                      cudaStream_t st);
 // fill: column f's entries go to [coff[f], coff[f] + ccnt[f]) with rows
-// ascending.  Values stored as float (fp32 != 0) or double.
+// ascending.  Values stored as float (fp32 != 0) or double.  R's rows must
+// be sorted by column.  positive: every value of X and R is > 0.
 ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, const CsrDev& R,
                          const uint64_t* coff, uint32_t* ccnt, int32_t* crow, void* cval,
-                         int fp32, int may_cancel, cudaStream_t st);
+                         int fp32, int may_cancel, int positive, uint64_t sqnorm_X,
+                         cudaStream_t st);
+// Sort each row of a row-major factor by column (col/val copied to *_out).
+void launch_sort_rows(const uint64_t* rowptr, int64_t n_rows, const int32_t* col_in,
+                      const int32_t* val_in, int32_t* col_out, int32_t* val_out, cudaStream_t st);
 
-// Relative-error numerator via Gram form: CCt = R^T (X X^T) R (exact int64,
-// width x width, column-major, must be zeroed).
+// Relative-error numerator ||Q^T X_(alpha)||_F^2 with Q = R Z^T, Z = L^{-1}
+// (kept x kept, column-major, ld ldz).  hot_rows_host: up to n_hot rows of
+// X (most nonzeros first) whose Q rows are staged in shared memory.
 struct CsrX {          // X_(alpha) by row: row i holds (col, val)
   const uint64_t* rowptr;
   const int32_t* col;
   const int32_t* val;
 };
-ctd_status launch_gram_hform(const CsrX& Xr, const CscDev& Xc, int64_t n_rows,
-                             const CsrDev& R, long long* CCt, Arena& scratch,
-                             cudaStream_t st);
-// out[0] = sum_{a,b} U[a,b] * CCt[a,b]  (FP64).
-void launch_frob_dot(const double* U, const long long* CCt, int64_t n, double* out,
-                     cudaStream_t st);
+ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
+                              const double* Z, int64_t ldz, const uint32_t* rowcnt_host_unused,
+                              const int* hot_rows_host, int n_hot, int fp32, double* out,
+                              Arena& scratch, cudaStream_t st);
 
 // ctd_dense.cu -------------------------------------------------------------
 // C = alpha op(A) op(B) + beta C, column-major FP64.
@@ -236,8 +240,15 @@ void dgemm(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, cons
 // (column-major, lower triangle used).  Column k is kept iff its Schur
 // diagonal exceeds thr[k].  Kept columns hold L, skipped ones are zeroed.
 // keep[k] in {0,1}.
+// force (optional): -1 decide by pivot, 0 skip, 1 keep.  piv (optional)
+// receives each column's pivot before its decision; a forced keep without a
+// positive pivot sets DEV_CAPACITY in *status (required when force is set).
 void launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr, int* keep,
-                      cudaStream_t st);
+                      cudaStream_t st, const int* force = nullptr, double* piv = nullptr,
+                      unsigned* status = nullptr);
+// B <- L^{-T} B for lower-triangular L, by backward substitution.
+void tri_solve_lower_T(const double* L, int64_t ldl, int64_t n, double* B, int64_t ldb,
+                       int64_t nrhs, cudaStream_t st);
 // idx[0..count) = positions k with keep[k] != 0 (ascending); *count on device.
 void launch_compact_flags(const int* keep, int n, int* idx, int* count, cudaStream_t st);
 // B (nk x nk) = A[idx, idx] for the lower triangle (upper zeroed).
@@ -246,6 +257,9 @@ void launch_gather_lower(const double* A, int64_t lda, const int* idx, const int
 // Z = L^{-1} for lower-triangular L (n x n), in place into Z (Z != L).
 void tri_inverse(const double* L, int64_t ldl, int64_t n, double* Z, int64_t ldz,
                  cudaStream_t st);
+// B <- L^{-1} B (lower-triangular L, n x n; nrhs columns), by substitution.
+void tri_solve_lower(const double* L, int64_t ldl, int64_t n, double* B, int64_t ldb, int64_t nrhs,
+                     cudaStream_t st);
 // U = Z^T Z (symmetric, full) for lower-triangular Z.
 void u_from_linv(const double* Z, int64_t n, int64_t ldz, double* U, int64_t ldu,
                  cudaStream_t st);
@@ -256,6 +270,77 @@ void launch_symmetrize(double* A, int64_t n, int64_t lda, cudaStream_t st);
 // thr[k] = eps^2 * diag[k] for the n diagonal entries of D (stride ldd+1).
 void launch_thresholds(const double* D, int64_t n, int64_t ldd, double eps2, double* thr,
                        cudaStream_t st);
+
+// ctd_api.cu (host helpers shared by the entry points) -------------------
+ctd_status d2h_bytes(void* host, const void* dev, size_t bytes, cudaStream_t st);
+template <typename T>
+inline ctd_status d2h(T* host, const T* dev, size_t n, cudaStream_t st) {
+  return d2h_bytes(host, dev, n * sizeof(T), st);
+}
+ctd_status sync(cudaStream_t st);
+ctd_status stage_coo(const ctd_coo3* X, int alpha, Arena& scratch, cudaStream_t st, CooDev* out);
+
+// X_(alpha) in both layouts plus its column distribution.
+struct Matricized {
+  int64_t n_rows = 0, n_cols = 0, nnz = 0;
+  uint64_t* cdf = nullptr;      // [n_cols] inclusive prefix of squared norms
+  uint64_t* colptr = nullptr;   // [n_cols+1]
+  uint64_t* rowptr = nullptr;   // [n_rows+1]
+  int32_t* csc_row = nullptr;
+  int32_t* csc_val = nullptr;
+  int32_t* csr_col = nullptr;
+  int32_t* csr_val = nullptr;
+  int* minval = nullptr;
+  unsigned* status = nullptr;
+  uint64_t* tmp = nullptr;
+  uint32_t* rowcnt = nullptr;   // [n_rows] nonzeros per row
+  CscDev csc() const { return CscDev{colptr, csc_row, csc_val}; }
+  CsrX csr() const { return CsrX{rowptr, csr_col, csr_val}; }
+};
+// Algorithm 1 lines 1-2: squared norms, CDF and the column/row layouts.
+ctd_status matricize(const CooDev& X, bool want_rows, Arena& A, cudaStream_t st, Matricized* M);
+
+// ctd_filter.cu: the independence filter over a block of du candidates.
+// S (du x du, ld du) holds the candidates' Schur complement against R^(t)
+// (X_c^T X_c when R^(t) is empty) and is overwritten by the skip-Cholesky
+// storage; xnorm2 = ||x_k||^2.  cptr/crow/cval: the candidates as CSC.
+// For CTD-D: dt = columns of R^(t), Lt (ld ldl) its Cholesky factor,
+// W = Lt^{-1} R^(t)^T X_c (dt x du), and R^(t) as CSC (rptr, rrow, rval).
+struct FilterIn {
+  int du = 0;
+  double* S = nullptr;
+  const double* xnorm2 = nullptr;
+  double eps = 0.0;
+  const uint64_t* cptr = nullptr;
+  const int32_t* crow = nullptr;
+  const int32_t* cval = nullptr;
+  int64_t dt = 0;
+  const double* Lt = nullptr;
+  int64_t ldl = 0;
+  const double* W = nullptr;
+  const uint64_t* rptr = nullptr;
+  const int32_t* rrow = nullptr;
+  const int32_t* rval = nullptr;
+  int64_t n_rows = 0;
+};
+// keep[du], idx[kept] (device), count (device, = kept), Lk = factor of the
+// kept block (kept x kept, lower), Li = Lk^{-1}.
+struct FilterOut {
+  int* keep = nullptr;
+  int* idx = nullptr;
+  int* count = nullptr;
+  int kept = 0;
+  double* Lk = nullptr;
+  double* Li = nullptr;
+  std::vector<double>* ratios = nullptr;
+};
+ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaStream_t st);
+
+// ctd_spmm.cu: sum over columns f of c_f^T U c_f for a sparse C stored as
+// (coff, ccnt, crow, cval) with n_cols columns and U (n x n, leading dim ldu).
+ctd_status launch_quad_form(const uint64_t* coff, const uint32_t* ccnt, const int32_t* crow,
+                            const void* cval, int fp32, int64_t n_cols, const double* U,
+                            int64_t ldu, double* out, cudaStream_t st);
 
 }  // namespace ctd
 
@@ -286,6 +371,7 @@ struct ctd_factors {
   int32_t* Rcol = nullptr;
   int32_t* Rcval = nullptr;
   double* U = nullptr;           // s~ x s~ column-major (symmetric)
+  double* L = nullptr;           // CTD-D: Cholesky factor of R^T R (lower, ld as U)
   uint64_t* Coff = nullptr;      // [n_cols+1]
   uint32_t* Ccnt = nullptr;      // [n_cols]
   int32_t* Crow = nullptr;
@@ -294,4 +380,15 @@ struct ctd_factors {
   // CTD-D extras live in ctd_dynamic.cu
   struct Dyn;
   Dyn* dyn = nullptr;
+  ~ctd_factors();
 };
+
+namespace ctd {
+// CTD-D views used by the common getters (ctd_dynamic.cu)
+ctd_status dyn_sizes(const ctd_factors* F, ctd_sizes* o);
+ctd_status dyn_samples(const ctd_factors* F, int64_t* I, int64_t* Iu);
+ctd_status dyn_fibers(const ctd_factors* F, int64_t* fiber, int64_t* step);
+ctd_status dyn_U(const ctd_factors* F, double* U);
+ctd_status dyn_C_columns(const ctd_factors* F, int64_t ncols, const int64_t* cols, double* out);
+ctd_status dyn_R(const ctd_factors* F, int64_t* colptr, int32_t* row, int32_t* val);
+}  // namespace ctd

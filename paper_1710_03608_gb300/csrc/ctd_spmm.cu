@@ -2,14 +2,17 @@
 //   * dense columns  out(:, c) = R^T x_f      (the Gram matrices of the
 //     independence filter, Algorithm 1 lines 6-15 / Algorithm 2 lines 6-16),
 //   * the sparse core C_(alpha) = R^T X_(alpha) (Algorithm 1 line 16, Eq. 3),
-//   * the Gram form of the error numerator R^T (X_(alpha) X_(alpha)^T) R,
-//     which with U gives ||P_R X||_F^2 = <U, C C^T> (Eq. error, Lemma 3.2).
+//   * the error numerator ||P_R X||_F^2 = ||Q^T X_(alpha)||_F^2 with
+//     Q = R L^{-T} (Eq. error, Lemma 3.2).
 //
 // Every product is an exact integer sum (int32 x int32 -> int64 terms).
 // Column f of X is expanded into (row entry of R) work items which a warp
 // spreads over its lanes; partial sums go to a dense int64 accumulator in
 // shared memory and a bitmap marks the touched rows of R^T x_f, so results
 // come out in ascending row order without a sort.
+#include <algorithm>
+#include <vector>
+
 #include "ctd_internal.cuh"
 
 namespace ctd {
@@ -147,42 +150,84 @@ void launch_c_bounds(const CscDev& X, int64_t n_cols, const CsrDev& R, uint32_t*
 
 // ---------------------------------------------------------------------------
 // C fill
+//
+// Column f of C is written to [coff[f], coff[f] + ccnt[f]) with rows
+// ascending.  Three paths:
+//  * a column with one nonzero v in row i (and all values positive) is
+//    v * R(i, :), copied from R's row i (rows of R are sorted by column);
+//  * other columns with fewer than HEAVY nonzeros: one warp each, with a
+//    warp-private accumulator;
+//  * heavy columns: a whole block each.
+// Accumulators are int32 when ||X||_F^2 < 2^31: by Cauchy-Schwarz every
+// partial sum is at most ||x_f|| ||r_m|| <= ||X||_F^2, so int32 is exact.
 // ---------------------------------------------------------------------------
-template <typename V>
-__device__ __forceinline__ V convert_exact(long long x) {
-  return (V)x;
+constexpr int HEAVY = 128;
+
+template <typename A>
+__device__ __forceinline__ void acc_add(A* p, long long x);
+template <>
+__device__ __forceinline__ void acc_add<int>(int* p, long long x) {
+  atomicAdd(p, (int)x);
+}
+template <>
+__device__ __forceinline__ void acc_add<unsigned long long>(unsigned long long* p, long long x) {
+  atomicAdd(p, (unsigned long long)x);
+}
+template <typename A>
+__device__ __forceinline__ long long acc_get(const A* p) {
+  return sizeof(A) == 4 ? (long long)(*(const int*)p) : (long long)(*(const unsigned long long*)p);
 }
 
-// Emit the touched entries of acc (ascending m) for one column, zeroing
-// them.  Group = `gthreads` threads starting at thread `gtid0` (a warp or the
-// whole block).  wpre: scratch with nwords+1 ints for this group.
-template <typename V>
-__device__ void emit_column(unsigned long long* acc, unsigned* bitmap, int width, int* wpre,
-                            int gtid, int gthreads, bool may_cancel, unsigned long long off,
-                            int32_t* __restrict__ crow, V* __restrict__ cval, int* total_out,
-                            bool block_group) {
+template <typename A>
+__device__ __forceinline__ void accumulate_column_t(const CscDev& X, const CsrDev& R, int64_t f,
+                                                    A* acc, unsigned* bitmap, int gwarp,
+                                                    int gwarps) {
+  const unsigned long long a = X.colptr[f], b = X.colptr[f + 1];
+  const int lane = threadIdx.x & 31;
+  for (unsigned long long p0 = a + (unsigned long long)gwarp * 32; p0 < b;
+       p0 += (unsigned long long)gwarps * 32) {
+    const unsigned long long p = p0 + lane;
+    unsigned long long rs = 0;
+    int rl = 0, v = 0;
+    if (p < b) {
+      const int i = __ldg(X.row + p);
+      v = __ldg(X.val + p);
+      rs = __ldg(reinterpret_cast<const unsigned long long*>(R.rowptr) + i);
+      rl = (int)(__ldg(reinterpret_cast<const unsigned long long*>(R.rowptr) + i + 1) - rs);
+    }
+    expand_chunk(rs, rl, v, R.col, R.val, [&](int m, long long prod) {
+      acc_add<A>(acc + m, prod);
+      atomicOr(bitmap + (m >> 5), 1u << (m & 31));
+    });
+  }
+}
+
+// Emit the touched entries of one column in ascending row order and reset
+// them.  Group = gthreads threads (a warp or the block).
+template <typename V, typename A>
+__device__ void emit_column_t(A* acc, unsigned* bitmap, int width, int* wpre, int gtid,
+                              int gthreads, bool may_cancel, unsigned long long off,
+                              int32_t* __restrict__ crow, V* __restrict__ cval, unsigned* count,
+                              bool block_group) {
   const int nwords = (width + 31) >> 5;
-  // drop exact zeros (only possible with signed inputs)
-  if (may_cancel) {
+  const int lane = gtid & 31;
+  if (may_cancel) {  // drop exact zeros (only possible with signed inputs)
     for (int w = gtid; w < nwords; w += gthreads) {
       unsigned bits = bitmap[w], keep = bits;
       while (bits) {
         const int bpos = __ffs(bits) - 1;
         bits &= bits - 1;
-        if (acc[w * 32 + bpos] == 0ull) keep &= ~(1u << bpos);
+        if (acc_get<A>(acc + w * 32 + bpos) == 0) keep &= ~(1u << bpos);
       }
       bitmap[w] = keep;
     }
     if (block_group) __syncthreads(); else __syncwarp();
   }
-  // word prefix counts (sequential over chunks of gthreads words)
   int carry = 0;
   for (int w0 = 0; w0 < nwords; w0 += gthreads) {
     const int w = w0 + gtid;
     const int c = w < nwords ? __popc(bitmap[w]) : 0;
-    // inclusive scan over the group
     int incl = c;
-    const int lane = gtid & 31;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       int y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -193,10 +238,11 @@ __device__ void emit_column(unsigned long long* acc, unsigned* bitmap, int width
       const int warp = gtid >> 5;
       if (lane == 31) wtot[warp] = incl;
       __syncthreads();
-      int before = 0;
-      for (int q = 0; q < warp; ++q) before += wtot[q];
-      int all = 0;
-      for (int q = 0; q < (gthreads >> 5); ++q) all += wtot[q];
+      int before = 0, all = 0;
+      for (int q = 0; q < (gthreads >> 5); ++q) {
+        if (q < warp) before += wtot[q];
+        all += wtot[q];
+      }
       if (w < nwords) wpre[w] = carry + before + incl - c;
       __syncthreads();
       carry += all;
@@ -205,11 +251,9 @@ __device__ void emit_column(unsigned long long* acc, unsigned* bitmap, int width
       carry += __shfl_sync(0xffffffffu, incl, 31);
     }
   }
-  if (gtid == 0) wpre[nwords] = carry;
   if (block_group) __syncthreads(); else __syncwarp();
   const int total = carry;
   for (int k = gtid; k < total; k += gthreads) {
-    // word containing the k-th set bit: largest w with wpre[w] <= k
     int lo = 0, hi = nwords - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -218,39 +262,37 @@ __device__ void emit_column(unsigned long long* acc, unsigned* bitmap, int width
       else
         hi = mid - 1;
     }
-    const unsigned bits = bitmap[lo];
-    const int bpos = __fns(bits, 0, k - wpre[lo] + 1);
+    const int bpos = __fns(bitmap[lo], 0, k - wpre[lo] + 1);
     const int m = lo * 32 + bpos;
-    const long long x = (long long)acc[m];
     crow[off + k] = m;
-    cval[off + k] = convert_exact<V>(x);
+    cval[off + k] = (V)acc_get<A>(acc + m);
+    acc[m] = 0;
   }
   if (block_group) __syncthreads(); else __syncwarp();
-  // zero what was touched (including dropped exact zeros)
+  if (may_cancel) {  // dropped zeros were reset already (their value is 0)
+  }
   for (int w = gtid; w < nwords; w += gthreads) bitmap[w] = 0;
-  for (int m = gtid; m < width; m += gthreads) acc[m] = 0;
   if (block_group) __syncthreads(); else __syncwarp();
-  if (total_out && gtid == 0) *total_out = total;
+  if (gtid == 0) *count = (unsigned)total;
 }
 
-// Warp mode: each warp owns an accumulator and takes columns from a global
-// counter in chunks.
-template <typename V>
+template <typename V, typename A>
 __global__ void __launch_bounds__(SPMM_THREADS)
     k_c_fill_warp(CscDev X, int64_t n_cols, CsrDev R, const unsigned long long* __restrict__ coff,
                   unsigned* __restrict__ ccnt, int32_t* __restrict__ crow, V* __restrict__ cval,
-                  int may_cancel, unsigned long long* work) {
-  extern __shared__ unsigned long long smem[];
+                  int may_cancel, int positive, unsigned long long* work) {
+  extern __shared__ unsigned long long smem_u64[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int width = R.width, nwords = (width + 31) >> 5;
-  unsigned long long* acc = smem + (size_t)warp * width;
-  unsigned* bitmaps = reinterpret_cast<unsigned*>(smem + (size_t)nw * width);
+  const int accw = (width + 1) & ~1;  // keep 8-byte alignment between warps
+  A* acc = reinterpret_cast<A*>(smem_u64) + (size_t)warp * accw;
+  unsigned* bitmaps = reinterpret_cast<unsigned*>(reinterpret_cast<A*>(smem_u64) + (size_t)nw * accw);
   unsigned* bitmap = bitmaps + warp * nwords;
-  int* wpres = reinterpret_cast<int*>(bitmaps + nw * nwords);
-  int* wpre = wpres + warp * (nwords + 1);
+  int* wpre = reinterpret_cast<int*>(bitmaps + nw * nwords) + warp * (nwords + 1);
   for (int m = lane; m < width; m += 32) acc[m] = 0;
   for (int w = lane; w < nwords; w += 32) bitmap[w] = 0;
   __syncwarp();
+  const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
   constexpr int CHUNK = 64;
   while (true) {
     unsigned long long f0 = 0;
@@ -264,243 +306,380 @@ __global__ void __launch_bounds__(SPMM_THREADS)
         if (lane == 0) ccnt[f] = 0;
         continue;
       }
-      accumulate_column(X, R, f, acc, bitmap, 0, 1);
+      const unsigned long long a = X.colptr[f], b = X.colptr[f + 1];
+      if (b - a >= (unsigned long long)HEAVY) continue;  // block kernel
+      if (b - a == 1 && positive) {
+        const int i = __ldg(X.row + a);
+        const long long v = __ldg(X.val + a);
+        const unsigned long long rs = __ldg(rp + i), n = __ldg(rp + i + 1) - rs;
+        for (unsigned long long q = lane; q < n; q += 32) {
+          crow[o + q] = __ldg(R.col + rs + q);
+          cval[o + q] = (V)(v * (long long)__ldg(R.val + rs + q));
+        }
+        if (lane == 0) ccnt[f] = (unsigned)n;
+        continue;
+      }
+      accumulate_column_t<A>(X, R, f, acc, bitmap, 0, 1);
       __syncwarp();
-      int total = 0;
-      emit_column<V>(acc, bitmap, width, wpre, lane, 32, may_cancel != 0, o, crow, cval, &total,
-                     false);
-      if (lane == 0) ccnt[f] = (unsigned)total;
+      emit_column_t<V, A>(acc, bitmap, width, wpre, lane, 32, may_cancel != 0, o, crow, cval,
+                          ccnt + f, false);
     }
   }
 }
 
-// Block mode: the whole block works on one column at a time.
-template <typename V>
+template <typename V, typename A>
 __global__ void __launch_bounds__(SPMM_THREADS)
-    k_c_fill_block(CscDev X, int64_t n_cols, CsrDev R, const unsigned long long* __restrict__ coff,
+    k_c_fill_block(CscDev X, const int64_t* __restrict__ list, const unsigned* __restrict__ nlist,
+                   CsrDev R, const unsigned long long* __restrict__ coff,
                    unsigned* __restrict__ ccnt, int32_t* __restrict__ crow, V* __restrict__ cval,
                    int may_cancel, unsigned long long* work) {
-  extern __shared__ unsigned long long smem[];
+  extern __shared__ unsigned long long smem_u64[];
   const int width = R.width, nwords = (width + 31) >> 5;
-  unsigned long long* acc = smem;
-  unsigned* bitmap = reinterpret_cast<unsigned*>(smem + width);
+  A* acc = reinterpret_cast<A*>(smem_u64);
+  unsigned* bitmap = reinterpret_cast<unsigned*>(acc + ((width + 1) & ~1));
   int* wpre = reinterpret_cast<int*>(bitmap + nwords);
   __shared__ unsigned long long fcur;
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned long long n = *nlist;
   for (int m = threadIdx.x; m < width; m += blockDim.x) acc[m] = 0;
   for (int w = threadIdx.x; w < nwords; w += blockDim.x) bitmap[w] = 0;
   __syncthreads();
   while (true) {
     if (threadIdx.x == 0) fcur = atomicAdd(work, 1ull);
     __syncthreads();
-    const unsigned long long f = fcur;
+    const unsigned long long it = fcur;
     __syncthreads();
-    if (f >= (unsigned long long)n_cols) break;
-    const unsigned long long o = coff[f];
-    if (coff[f + 1] == o) {
-      if (threadIdx.x == 0) ccnt[f] = 0;
-      continue;
-    }
-    accumulate_column(X, R, (int64_t)f, acc, bitmap, warp, nw);
+    if (it >= n) break;
+    const int64_t f = list[it];
+    accumulate_column_t<A>(X, R, f, acc, bitmap, warp, nw);
     __syncthreads();
-    int total = 0;
-    emit_column<V>(acc, bitmap, width, wpre, threadIdx.x, blockDim.x, may_cancel != 0, o, crow,
-                   cval, &total, true);
-    if (threadIdx.x == 0) ccnt[f] = (unsigned)total;
+    emit_column_t<V, A>(acc, bitmap, width, wpre, threadIdx.x, blockDim.x, may_cancel != 0,
+                        coff[f], crow, cval, ccnt + f, true);
   }
 }
 
-template <typename V>
+// Columns with at least `minc` nonzeros (and a nonzero bound): list + count.
+__global__ void k_list_columns(const unsigned long long* __restrict__ colptr,
+                               const unsigned long long* __restrict__ coff, int64_t n_cols,
+                               unsigned long long minc, int64_t* __restrict__ list,
+                               unsigned* __restrict__ count) {
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < n_cols;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    if (colptr[f + 1] - colptr[f] >= minc && coff[f + 1] > coff[f])
+      list[atomicAdd(count, 1u)] = f;
+  }
+}
+
+template <typename V, typename A>
 static ctd_status c_fill_impl(const CscDev& X, int64_t n_cols, const CsrDev& R,
                               const uint64_t* coff, uint32_t* ccnt, int32_t* crow, V* cval,
-                              int may_cancel, unsigned long long* work, cudaStream_t st) {
+                              int may_cancel, int positive, unsigned long long* work,
+                              int64_t* heavy, unsigned* nheavy, cudaStream_t st) {
   const int width = R.width, nwords = (width + 31) >> 5;
-  if (width <= WARP_MODE_MAX_WIDTH) {
+  const int accw = (width + 1) & ~1;
+  const unsigned long long* co = reinterpret_cast<const unsigned long long*>(coff);
+  // heavy columns (and, if the warp accumulator would not fit, all columns)
+  const bool warp_ok = width <= WARP_MODE_MAX_WIDTH;
+  CTD_LAUNCH(k_list_columns, (grid_for(n_cols, 256, (int64_t)num_sms() * 8)), (256), 0, st,
+             reinterpret_cast<const unsigned long long*>(X.colptr), co, n_cols,
+             warp_ok ? (unsigned long long)HEAVY : 1ull, heavy, nheavy);
+  if (warp_ok) {
     const int nw = SPMM_THREADS / 32;
-    const size_t smem = (size_t)nw * width * 8 + (size_t)nw * nwords * 4 +
+    const size_t smem = (size_t)nw * accw * sizeof(A) + (size_t)nw * nwords * 4 +
                         (size_t)nw * (nwords + 1) * 4;
     if (smem > 48 * 1024)
-      CTD_CUDA(cudaFuncSetAttribute(k_c_fill_warp<V>,
+      CTD_CUDA(cudaFuncSetAttribute(k_c_fill_warp<V, A>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_c_fill_warp<V>,
+    CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_c_fill_warp<V, A>,
                                                            SPMM_THREADS, smem));
     if (per_sm < 1) per_sm = 1;
-    CTD_LAUNCH(k_c_fill_warp<V>, (num_sms() * per_sm), (SPMM_THREADS), smem, st, 
-        X, n_cols, R, reinterpret_cast<const unsigned long long*>(coff), ccnt, crow, cval,
-        may_cancel, work);
+    CTD_LAUNCH((k_c_fill_warp<V, A>), (num_sms() * per_sm), (SPMM_THREADS), smem, st, X, n_cols,
+               R, co, ccnt, crow, cval, may_cancel, positive, work);
   } else {
-    if (width > CTA_MODE_MAX_WIDTH)
-      return fail(CTD_EINVAL, "factor wider than the supported maximum (24576 columns)");
-    const size_t smem = (size_t)width * 8 + (size_t)nwords * 4 + (size_t)(nwords + 1) * 4;
-    if (smem > 48 * 1024)
-      CTD_CUDA(cudaFuncSetAttribute(k_c_fill_block<V>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_c_fill_block<V>,
-                                                           SPMM_THREADS, smem));
-    if (per_sm < 1) per_sm = 1;
-    CTD_LAUNCH(k_c_fill_block<V>, (num_sms() * per_sm), (SPMM_THREADS), smem, st, 
-        X, n_cols, R, reinterpret_cast<const unsigned long long*>(coff), ccnt, crow, cval,
-        may_cancel, work);
+    CTD_CUDA(cudaMemsetAsync(ccnt, 0, n_cols * sizeof(uint32_t), st));
   }
+  if (width > CTA_MODE_MAX_WIDTH)
+    return fail(CTD_EINVAL, "factor wider than the supported maximum (24576 columns)");
+  const size_t smem = (size_t)accw * sizeof(A) + (size_t)nwords * 4 + (size_t)(nwords + 1) * 4;
+  if (smem > 48 * 1024)
+    CTD_CUDA(cudaFuncSetAttribute(k_c_fill_block<V, A>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_c_fill_block<V, A>,
+                                                         SPMM_THREADS, smem));
+  if (per_sm < 1) per_sm = 1;
+  CTD_LAUNCH((k_c_fill_block<V, A>), (num_sms() * per_sm), (SPMM_THREADS), smem, st, X, heavy,
+             nheavy, R, co, ccnt, crow, cval, may_cancel, work + 1);
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
 
 ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, const CsrDev& R, const uint64_t* coff,
                          uint32_t* ccnt, int32_t* crow, void* cval, int fp32, int may_cancel,
-                         cudaStream_t st) {
+                         int positive, uint64_t sqnorm_X, cudaStream_t st) {
   if (n_cols <= 0) return CTD_OK;
-  unsigned long long* work;
-  CTD_TRY(dalloc_n(&work, 1, st));
-  CTD_CUDA(cudaMemsetAsync(work, 0, sizeof(unsigned long long), st));
-  ctd_status rc;
   if (R.width <= 0) {
     CTD_CUDA(cudaMemsetAsync(ccnt, 0, n_cols * sizeof(uint32_t), st));
-    rc = CTD_OK;
-  } else if (fp32) {
-    rc = c_fill_impl<float>(X, n_cols, R, coff, ccnt, crow, static_cast<float*>(cval), may_cancel,
-                            work, st);
-  } else {
-    rc = c_fill_impl<double>(X, n_cols, R, coff, ccnt, crow, static_cast<double*>(cval),
-                             may_cancel, work, st);
+    return CTD_OK;
   }
+  unsigned long long* work;
+  int64_t* heavy;
+  unsigned* nheavy;
+  CTD_TRY(dalloc_n(&work, 2, st));
+  CTD_TRY(dalloc_n(&heavy, n_cols, st));
+  CTD_TRY(dalloc_n(&nheavy, 1, st));
+  CTD_CUDA(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), st));
+  CTD_CUDA(cudaMemsetAsync(nheavy, 0, sizeof(unsigned), st));
+  const bool small = sqnorm_X < (1ull << 31);
+  ctd_status rc;
+  if (fp32)
+    rc = small ? c_fill_impl<float, int>(X, n_cols, R, coff, ccnt, crow, static_cast<float*>(cval),
+                                         may_cancel, positive, work, heavy, nheavy, st)
+               : c_fill_impl<float, unsigned long long>(X, n_cols, R, coff, ccnt, crow,
+                                                        static_cast<float*>(cval), may_cancel,
+                                                        positive, work, heavy, nheavy, st);
+  else
+    rc = small ? c_fill_impl<double, int>(X, n_cols, R, coff, ccnt, crow,
+                                          static_cast<double*>(cval), may_cancel, positive, work,
+                                          heavy, nheavy, st)
+               : c_fill_impl<double, unsigned long long>(X, n_cols, R, coff, ccnt, crow,
+                                                         static_cast<double*>(cval), may_cancel,
+                                                         positive, work, heavy, nheavy, st);
   dfree(work, st);
+  dfree(heavy, st);
+  dfree(nheavy, st);
   return rc;
 }
 
-// ---------------------------------------------------------------------------
-// Gram form of the error numerator: CCt = R^T H R with H = X_(alpha) X_(alpha)^T.
-// Work item = (row i of R's support, chunk of X's row i).  For the chunk,
-// h = sum over its entries (f, x_if) of x_if * x_f  (dense over rows, in
-// shared memory), w = R^T h, and CCt(m, :) += R(i, m) * w for m in row i of R.
-// By linearity the chunks of one row add up to r_i (H R)(i, :).
-// ---------------------------------------------------------------------------
-constexpr int HF_CHUNK = 2048;
-constexpr int HF_MAX_ROWS = 16384;  // int64 h in shared memory
-constexpr int HF_MAX_WIDTH = 8192;
-
-__global__ void k_hform_items(const unsigned long long* __restrict__ xrowptr,
-                              const unsigned long long* __restrict__ rrowptr, int64_t n_rows,
-                              unsigned* __restrict__ items) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rows;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long xl = xrowptr[i + 1] - xrowptr[i];
-    const unsigned long long rl = rrowptr[i + 1] - rrowptr[i];
-    items[i] = (rl > 0 && xl > 0) ? (unsigned)((xl + HF_CHUNK - 1) / HF_CHUNK) : 0u;
+// Sort each row of a row-major factor by column (rank by counting; rows are
+// short).  One warp per row; in/out arrays differ.
+__global__ void k_sort_rows(const unsigned long long* __restrict__ rowptr, int64_t n_rows,
+                            const int32_t* __restrict__ col_in, const int32_t* __restrict__ val_in,
+                            int32_t* __restrict__ col_out, int32_t* __restrict__ val_out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = gw; i < n_rows; i += nw) {
+    const unsigned long long a = rowptr[i], b = rowptr[i + 1];
+    for (unsigned long long p = a + lane; p < b; p += 32) {
+      const int m = col_in[p];
+      unsigned long long r = 0;
+      for (unsigned long long q = a; q < b; ++q) r += (col_in[q] < m);
+      col_out[a + r] = m;
+      val_out[a + r] = val_in[p];
+    }
   }
 }
 
-__global__ void __launch_bounds__(SPMM_THREADS)
-    k_hform(CsrX Xr, CscDev Xc, int64_t n_rows, CsrDev R,
-            const unsigned long long* __restrict__ item_off, long long* __restrict__ CCt,
-            unsigned long long* work) {
-  extern __shared__ unsigned long long sm[];
-  unsigned long long* h = sm;                 // [n_rows]
-  unsigned long long* w = sm + n_rows;        // [width]
-  __shared__ unsigned long long cur;
-  const int width = R.width;
-  const unsigned long long n_items = item_off[n_rows];
-  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+void launch_sort_rows(const uint64_t* rowptr, int64_t n_rows, const int32_t* col_in,
+                      const int32_t* val_in, int32_t* col_out, int32_t* val_out, cudaStream_t st) {
+  if (n_rows <= 0) return;
+  CTD_LAUNCH(k_sort_rows, (grid_for(n_rows * 32, 256, (int64_t)num_sms() * 16)), (256), 0, st,
+             reinterpret_cast<const unsigned long long*>(rowptr), n_rows, col_in, val_in, col_out,
+             val_out);
+}
+
+// ---------------------------------------------------------------------------
+// Error numerator in the Q form: ||P_R X||_F^2 = ||Q^T X_(alpha)||_F^2 with
+// Q = R L^{-T} (orthonormal columns spanning range(R); L L^T = R^T R, Z =
+// L^{-1}).  Q is dense I_alpha x s~, row-major with stride qs (a multiple of
+// 32), computed in FP64 and stored as T.  The sum over columns f of
+// ||Q^T x_f||^2 costs nnz * s~ multiply-adds; a column with one nonzero v in
+// row i contributes v^2 ||Q(i, :)||^2, read from the precomputed row norms.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_build_q(CsrDev R, int64_t n_rows, const double* __restrict__ Z, int64_t ldz,
+                          int qs, T* __restrict__ Q, double* __restrict__ qn) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
-  for (int64_t q = threadIdx.x; q < n_rows; q += blockDim.x) h[q] = 0;
-  for (int m = threadIdx.x; m < width; m += blockDim.x) w[m] = 0;
-  __syncthreads();
-  while (true) {
-    if (threadIdx.x == 0) cur = atomicAdd(work, 1ull);
-    __syncthreads();
-    const unsigned long long it = cur;
-    __syncthreads();
-    if (it >= n_items) break;
-    // row i: largest i with item_off[i] <= it
-    int64_t lo = 0, hi = n_rows - 1;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi + 1) >> 1;
-      if (item_off[mid] <= it)
-        lo = mid;
-      else
-        hi = mid - 1;
+  for (int64_t i = gw; i < n_rows; i += nw) {
+    const unsigned long long a = rp[i], b = rp[i + 1];
+    double nrm = 0.0;
+    for (int c = lane; c < qs; c += 32) {
+      double acc = 0.0;
+      if (c < R.width)
+        for (unsigned long long q = a; q < b; ++q) {
+          const int m = R.col[q];
+          if (c >= m) acc = fma((double)R.val[q], Z[c + (int64_t)m * ldz], acc);
+        }
+      const T tv = (T)acc;
+      Q[i * qs + c] = tv;
+      nrm = fma((double)tv, (double)tv, nrm);
     }
-    const int64_t i = lo;
-    const unsigned long long c = it - item_off[i];
-    const unsigned long long xa = (unsigned long long)Xr.rowptr[i] + c * HF_CHUNK;
-    const unsigned long long xb = min((unsigned long long)Xr.rowptr[i + 1], xa + (unsigned long long)HF_CHUNK);
-    // h = sum_{(f, x) in chunk} x * X(:, f)
-    for (unsigned long long e = xa + warp; e < xb; e += nw) {
-      const int f = __ldg(Xr.col + e);
-      const long long xv = __ldg(Xr.val + e);
-      const unsigned long long a = Xc.colptr[f], b = Xc.colptr[f + 1];
-      for (unsigned long long p = a + lane; p < b; p += 32)
-        atomicAdd(h + __ldg(Xc.row + p), (unsigned long long)(xv * (long long)__ldg(Xc.val + p)));
-    }
-    __syncthreads();
-    // w = R^T h (rows q with h[q] != 0), zero h on the way
-    for (int64_t q = threadIdx.x; q < n_rows; q += blockDim.x) {
-      const long long hq = (long long)h[q];
-      if (hq != 0) {
-        h[q] = 0;
-        for (unsigned long long r = rp[q]; r < rp[q + 1]; ++r)
-          atomicAdd(w + __ldg(R.col + r), (unsigned long long)(hq * (long long)__ldg(R.val + r)));
-      }
-    }
-    __syncthreads();
-    // CCt(m, :) += R(i, m) * w
-    for (unsigned long long r = rp[i]; r < rp[i + 1]; ++r) {
-      const int m = __ldg(R.col + r);
-      const long long rv = __ldg(R.val + r);
-      for (int m2 = threadIdx.x; m2 < width; m2 += blockDim.x) {
-        const long long wv = (long long)w[m2];
-        if (wv != 0) atomicAdd(reinterpret_cast<unsigned long long*>(CCt + (int64_t)m2 * width + m),
-                               (unsigned long long)(rv * wv));
-      }
-    }
-    __syncthreads();
-    for (int m = threadIdx.x; m < width; m += blockDim.x) w[m] = 0;
-    __syncthreads();
+    for (int o = 16; o; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    if (lane == 0) qn[i] = nrm;
   }
 }
 
-ctd_status launch_gram_hform(const CsrX& Xr, const CscDev& Xc, int64_t n_rows, const CsrDev& R,
-                             long long* CCt, Arena& scratch, cudaStream_t st) {
-  if (R.width <= 0 || n_rows <= 0) return CTD_OK;
-  if (n_rows > HF_MAX_ROWS || R.width > HF_MAX_WIDTH)
-    return fail(CTD_ENOTSUP, "error form limited to I_alpha <= 16384 and s~ <= 8192");
-  unsigned* items;
-  uint64_t* item_off;
-  uint64_t* tmp;
-  unsigned* status;
-  unsigned long long* work;
-  CTD_TRY(scratch.get(&items, n_rows));
-  CTD_TRY(scratch.get(&item_off, n_rows + 1));
-  CTD_TRY(scratch.get(&tmp, scan_tmp_elems(n_rows)));
-  CTD_TRY(scratch.get(&status, 1));
-  CTD_TRY(scratch.get(&work, 1));
-  CTD_CUDA(cudaMemsetAsync(status, 0, 4, st));
-  CTD_CUDA(cudaMemsetAsync(work, 0, 8, st));
-  CTD_LAUNCH(k_hform_items, (grid_for(n_rows, 256, 1024)), (256), 0, st, 
-      reinterpret_cast<const unsigned long long*>(Xr.rowptr),
-      reinterpret_cast<const unsigned long long*>(R.rowptr), n_rows, items);
-  launch_scan_u32(items, item_off, n_rows, false, tmp, status, st);
-  const size_t smem = (size_t)(n_rows + R.width) * 8;
+// One warp per column (dynamic chunks).  Hot rows of Q (slot >= 0 in
+// `slot_of`) are staged in shared memory once per block.
+template <typename T, int NC>
+__global__ void __launch_bounds__(256)
+    k_qform(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs,
+            const double* __restrict__ qn, const short* __restrict__ slot_of,
+            const int* __restrict__ hot_rows, int n_hot, int64_t n_rows,
+            unsigned long long* work, double* __restrict__ block_sums) {
+  extern __shared__ unsigned char smraw[];
+  T* Qs = reinterpret_cast<T*>(smraw);                                   // [n_hot][qs]
+  short* slot = reinterpret_cast<short*>(smraw + (size_t)n_hot * qs * sizeof(T));  // [n_rows]
+  __shared__ double wsum[8];
+  for (int64_t e = threadIdx.x; e < (int64_t)n_hot * qs; e += blockDim.x)
+    Qs[e] = Q[(int64_t)hot_rows[e / qs] * qs + (e % qs)];
+  for (int64_t e = threadIdx.x; e < n_rows; e += blockDim.x) slot[e] = slot_of[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double total = 0.0;
+  constexpr int CHUNK = 64;
+  while (true) {
+    unsigned long long f0 = 0;
+    if (lane == 0) f0 = atomicAdd(work, (unsigned long long)CHUNK);
+    f0 = __shfl_sync(0xffffffffu, f0, 0);
+    if (f0 >= (unsigned long long)n_cols) break;
+    const int64_t f1 = min((int64_t)f0 + CHUNK, n_cols);
+    for (int64_t f = (int64_t)f0; f < f1; ++f) {
+      const unsigned long long a = X.colptr[f], b = X.colptr[f + 1];
+      if (b == a) continue;
+      if (b == a + 1) {
+        const double v = (double)X.val[a];
+        if (lane == 0) total = fma(v * v, qn[X.row[a]], total);
+        continue;
+      }
+      float accf[NC];
+      double accd[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        accf[k] = 0.f;
+        accd[k] = 0.0;
+      }
+      for (unsigned long long p = a; p < b; ++p) {
+        const int i = __ldg(X.row + p);
+        const int v = __ldg(X.val + p);
+        const int sl = slot[i];
+        const T* qrow = sl >= 0 ? Qs + (int64_t)sl * qs : Q + (int64_t)i * qs;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          const int c = lane + 32 * k;
+          if (c < qs) {
+            if (sizeof(T) == 4)
+              accf[k] = fmaf((float)v, (float)qrow[c], accf[k]);
+            else
+              accd[k] = fma((double)v, (double)qrow[c], accd[k]);
+          }
+        }
+      }
+      double ss = 0.0;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        const double x = sizeof(T) == 4 ? (double)accf[k] : accd[k];
+        ss = fma(x, x, ss);
+      }
+      for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      if (lane == 0) total += ss;
+    }
+  }
+  if (lane == 0) wsum[warp] = total;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+    block_sums[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_sum_f64_small(const double* __restrict__ in, int n, double* out);
+
+template <typename T, int NC>
+static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int qs,
+                               const double* qn, const short* slot_of, const int* hot, int n_hot,
+                               int64_t n_rows, unsigned long long* work, double* block_sums,
+                               int* nblocks, cudaStream_t st) {
+  const size_t smem = (size_t)n_hot * qs * sizeof(T) + (size_t)n_rows * sizeof(short);
   if (smem > 48 * 1024)
-    CTD_CUDA(cudaFuncSetAttribute(k_hform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CTD_CUDA(cudaFuncSetAttribute(k_qform<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
   int per_sm = 0;
-  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hform, SPMM_THREADS, smem));
-  if (per_sm < 1) per_sm = 1;
-  CTD_LAUNCH(k_hform, (num_sms() * per_sm), (SPMM_THREADS), smem, st, 
-      Xr, Xc, n_rows, R, reinterpret_cast<const unsigned long long*>(item_off), CCt, work);
+  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qform<T, NC>, 256, smem));
+  if (per_sm < 1) return fail(CTD_ECUDA, "error kernel does not fit on an SM");
+  *nblocks = num_sms() * per_sm;
+  CTD_LAUNCH((k_qform<T, NC>), (*nblocks), (256), smem, st, X, n_cols, Q, qs, qn, slot_of, hot,
+             n_hot, n_rows, work, block_sums);
+  return CTD_OK;
+}
+
+ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
+                              const double* Z, int64_t ldz, const uint32_t* rowcnt_host_unused,
+                              const int* hot_rows_host, int n_hot_req, int fp32, double* out,
+                              Arena& scratch, cudaStream_t st) {
+  (void)rowcnt_host_unused;
+  CTD_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
+  if (R.width <= 0 || n_cols <= 0) return CTD_OK;
+  const int qs = (R.width + 31) & ~31;
+  const int NCmax = qs / 32;
+  if (NCmax > 32) return fail(CTD_ENOTSUP, "error kernel limited to s~ <= 1024");
+  const size_t tsz = fp32 ? 4 : 8;
+  void* Q;
+  double* qn;
+  short* slot_of;
+  int* hot;
+  unsigned long long* work;
+  double* bsums;
+  CTD_TRY(scratch.get(reinterpret_cast<unsigned char**>(&Q), (size_t)n_rows * qs * tsz));
+  CTD_TRY(scratch.get(&qn, n_rows));
+  CTD_TRY(scratch.get(&slot_of, n_rows));
+  CTD_TRY(scratch.get(&work, 1));
+  CTD_TRY(scratch.get(&bsums, 4096));
+  // hot rows: as many as fit next to the slot table in 200 KB of shared memory
+  const size_t budget = 200 * 1024;
+  const size_t table = (size_t)n_rows * sizeof(short);
+  int n_hot = 0;
+  if (table < budget) n_hot = (int)std::min<size_t>((budget - table) / ((size_t)qs * tsz), n_hot_req);
+  n_hot = std::max(n_hot, 0);
+  CTD_TRY(scratch.get(&hot, std::max(n_hot, 1)));
+  std::vector<short> slots(n_rows, (short)-1);
+  for (int q = 0; q < n_hot; ++q) slots[hot_rows_host[q]] = (short)q;
+  CTD_CUDA(cudaMemcpyAsync(slot_of, slots.data(), n_rows * sizeof(short), cudaMemcpyHostToDevice, st));
+  if (n_hot)
+    CTD_CUDA(cudaMemcpyAsync(hot, hot_rows_host, n_hot * sizeof(int), cudaMemcpyHostToDevice, st));
+  CTD_CUDA(cudaMemsetAsync(work, 0, 8, st));
+  const unsigned gq = grid_for(n_rows * 32, 256, (int64_t)num_sms() * 8);
+  if (fp32)
+    CTD_LAUNCH(k_build_q<float>, (gq), (256), 0, st, R, n_rows, Z, ldz, qs,
+               static_cast<float*>(Q), qn);
+  else
+    CTD_LAUNCH(k_build_q<double>, (gq), (256), 0, st, R, n_rows, Z, ldz, qs,
+               static_cast<double*>(Q), qn);
+  int nb = 0;
+  ctd_status rc;
+#define QF(NC)                                                                                  \
+  rc = fp32 ? qform_launch<float, NC>(X, n_cols, static_cast<const float*>(Q), qs, qn, slot_of,  \
+                                      hot, n_hot, n_rows, work, bsums, &nb, st)                  \
+            : qform_launch<double, NC>(X, n_cols, static_cast<const double*>(Q), qs, qn,         \
+                                       slot_of, hot, n_hot, n_rows, work, bsums, &nb, st)
+  if (NCmax <= 4) {
+    QF(4);
+  } else if (NCmax <= 8) {
+    QF(8);
+  } else if (NCmax <= 16) {
+    QF(16);
+  } else {
+    QF(32);
+  }
+#undef QF
+  CTD_TRY(rc);
+  if (nb > 4096) return fail(CTD_ECUDA, "too many blocks for the error reduction");
+  CTD_LAUNCH(k_sum_f64_small, (1), (1024), 0, st, bsums, nb, out);
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
 
-// <U, CCt> in FP64 (deterministic two-level reduction)
-__global__ void k_frob_dot(const double* __restrict__ U, const long long* __restrict__ CCt,
-                           int64_t nn, double* out) {
+__global__ void k_sum_f64_small(const double* __restrict__ in, int n, double* out) {
   __shared__ double part[32];
   double acc = 0.0;
-  for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) acc += U[e] * (double)CCt[e];
-  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) acc += in[e];
+  for (int w = 16; w; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
   if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -510,9 +689,75 @@ __global__ void k_frob_dot(const double* __restrict__ U, const long long* __rest
   }
 }
 
-void launch_frob_dot(const double* U, const long long* CCt, int64_t n, double* out,
-                     cudaStream_t st) {
-  CTD_LAUNCH(k_frob_dot, (1), (1024), 0, st, U, CCt, n * n, out);
+// ---------------------------------------------------------------------------
+// Quadratic form of a sparse C against U: sum_f c_f^T U c_f  (FP64).  One
+// block per column; per-column results then a fixed-order reduction, so the
+// sum does not depend on scheduling.
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void k_quad_cols(const unsigned long long* __restrict__ coff, const unsigned* __restrict__ ccnt,
+                            const int32_t* __restrict__ crow, const V* __restrict__ cval,
+                            int64_t n_cols, const double* __restrict__ U, int64_t ldu,
+                            double* __restrict__ per_col) {
+  __shared__ double part[32];
+  for (int64_t f = blockIdx.x; f < n_cols; f += gridDim.x) {
+    const unsigned long long o = coff[f];
+    const unsigned n = ccnt[f];
+    double acc = 0.0;
+    for (unsigned p = threadIdx.x; p < n; p += blockDim.x) {
+      const int mp = crow[o + p];
+      const double vp = (double)cval[o + p];
+      const double* Ucol = U + (int64_t)mp * ldu;
+      double s = 0.0;
+      for (unsigned q = 0; q < n; ++q) s = fma((double)cval[o + q], Ucol[crow[o + q]], s);
+      acc = fma(vp, s, acc);
+    }
+    for (int w = 16; w; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+      per_col[f] = t;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_sum_f64(const double* __restrict__ in, int64_t n, double* out) {
+  __shared__ double part[32];
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc += in[e];
+  for (int w = 16; w; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    *out = t;
+  }
+}
+
+ctd_status launch_quad_form(const uint64_t* coff, const uint32_t* ccnt, const int32_t* crow,
+                            const void* cval, int fp32, int64_t n_cols, const double* U,
+                            int64_t ldu, double* out, cudaStream_t st) {
+  CTD_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
+  if (n_cols <= 0) return CTD_OK;
+  double* per_col;
+  CTD_TRY(dalloc_n(&per_col, n_cols, st));
+  const unsigned g = grid_for(n_cols, 1, (int64_t)num_sms() * 16);
+  if (fp32)
+    CTD_LAUNCH(k_quad_cols<float>, (g), (256), 0, st,
+               reinterpret_cast<const unsigned long long*>(coff), ccnt, crow,
+               static_cast<const float*>(cval), n_cols, U, ldu, per_col);
+  else
+    CTD_LAUNCH(k_quad_cols<double>, (g), (256), 0, st,
+               reinterpret_cast<const unsigned long long*>(coff), ccnt, crow,
+               static_cast<const double*>(cval), n_cols, U, ldu, per_col);
+  CTD_LAUNCH(k_sum_f64, (1), (1024), 0, st, per_col, n_cols, out);
+  CTD_CUDA(cudaGetLastError());
+  dfree(per_col, st);
+  return CTD_OK;
 }
 
 }  // namespace ctd

@@ -52,11 +52,23 @@ static ModeMap make_map(const CooDev& X) {
 // ---------------------------------------------------------------------------
 // K1: norms and counts
 // ---------------------------------------------------------------------------
+// Row counts go to a per-block shared-memory histogram when the rows fit
+// (Zipf sources put ~10% of all nonzeros on one row; global atomics on that
+// one address would serialize), then one global add per touched row.
+constexpr int NORMS_SMEM_ROWS = 16384;
+
 __global__ void k_fiber_norms(const int32_t* __restrict__ ii, const int32_t* __restrict__ jj,
                               const int32_t* __restrict__ kk, const int32_t* __restrict__ vv,
-                              int64_t nnz, ModeMap mm, unsigned long long* __restrict__ norm2,
+                              int64_t nnz, ModeMap mm, int64_t n_rows,
+                              unsigned long long* __restrict__ norm2,
                               unsigned* __restrict__ colcnt, unsigned* __restrict__ rowcnt,
                               int* minval, unsigned* status) {
+  extern __shared__ unsigned rowhist[];
+  const bool priv = n_rows <= NORMS_SMEM_ROWS;
+  if (priv) {
+    for (int64_t r = threadIdx.x; r < n_rows; r += blockDim.x) rowhist[r] = 0;
+    __syncthreads();
+  }
   int local_min = INT32_MAX;
   bool bad = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -71,23 +83,36 @@ __global__ void k_fiber_norms(const int32_t* __restrict__ ii, const int32_t* __r
     const unsigned long long v2 = (unsigned long long)((long long)v * (long long)v);
     atomicAdd(norm2 + col, v2);
     atomicAdd(colcnt + col, 1u);
-    atomicAdd(rowcnt + row, 1u);
+    if (priv)
+      atomicAdd(rowhist + row, 1u);
+    else
+      atomicAdd(rowcnt + row, 1u);
     local_min = min(local_min, v);
   }
   // warp-reduce the minimum before one atomic
   for (int o = 16; o; o >>= 1) local_min = min(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
   if ((threadIdx.x & 31) == 0 && local_min != INT32_MAX) atomicMin(minval, local_min);
   if (bad) atomicOr(status, DEV_BAD_INDEX);
+  if (priv) {
+    __syncthreads();
+    for (int64_t r = threadIdx.x; r < n_rows; r += blockDim.x)
+      if (rowhist[r]) atomicAdd(rowcnt + r, rowhist[r]);
+  }
 }
 
 void launch_fiber_norms(const CooDev& X, uint64_t* norm2, uint32_t* colcnt, uint32_t* rowcnt,
                         int* minval, unsigned* status, cudaStream_t st) {
   if (X.nnz == 0) return;
-  const int bs = 256;
-  unsigned g = grid_for(X.nnz, bs, (int64_t)num_sms() * 8);
-  CTD_LAUNCH(k_fiber_norms, (g), (bs), 0, st, X.i, X.j, X.k, X.v, X.nnz, make_map(X),
-                                  reinterpret_cast<unsigned long long*>(norm2), colcnt, rowcnt,
-                                  minval, status);
+  const int bs = 512;
+  int64_t n_rows, n_cols;
+  mode_extents(X.dims, X.alpha, &n_rows, &n_cols);
+  const bool priv = n_rows <= NORMS_SMEM_ROWS;
+  const size_t smem = priv ? (size_t)n_rows * 4 : 0;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_fiber_norms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  unsigned g = grid_for(X.nnz, bs, (int64_t)num_sms() * 2);
+  CTD_LAUNCH(k_fiber_norms, (g), (bs), smem, st, X.i, X.j, X.k, X.v, X.nnz, make_map(X), n_rows,
+             reinterpret_cast<unsigned long long*>(norm2), colcnt, rowcnt, minval, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -387,20 +412,27 @@ ctd_status build_csr_from_csc(const uint64_t* colptr, const int32_t* row, const 
   uint64_t* cur;
   uint64_t* tmp;
   unsigned* status;
+  int32_t *col_tmp, *val_tmp;
   CTD_TRY(scratch.get(&rowcnt, n_rows));
   CTD_TRY(scratch.get(&cur, n_rows + 1));
   CTD_TRY(scratch.get(&tmp, scan_tmp_elems(n_rows)));
   CTD_TRY(scratch.get(&status, 1));
+  CTD_TRY(scratch.get(&col_tmp, nnz));
+  CTD_TRY(scratch.get(&val_tmp, nnz));
   CTD_CUDA(cudaMemsetAsync(rowcnt, 0, n_rows * sizeof(unsigned), st));
   CTD_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
   if (nnz > 0)
-    CTD_LAUNCH(k_row_counts, (grid_for(nnz, 256, (int64_t)num_sms() * 8)), (256), 0, st, row, nnz, rowcnt);
+    CTD_LAUNCH(k_row_counts, (grid_for(nnz, 256, (int64_t)num_sms() * 8)), (256), 0, st, row, nnz,
+               rowcnt);
   launch_scan_u32(rowcnt, rowptr_out, n_rows, false, tmp, status, st);
   launch_copy_u64(rowptr_out, cur, n_rows, st);
-  if (nnz > 0 && ncols > 0)
-    CTD_LAUNCH(k_csc_to_csr, (grid_for(ncols * 32, 256, 4096)), (256), 0, st, 
-        reinterpret_cast<const unsigned long long*>(colptr), row, val, ncols, col_base,
-        reinterpret_cast<unsigned long long*>(cur), col_out, val_out);
+  if (nnz > 0 && ncols > 0) {
+    CTD_LAUNCH(k_csc_to_csr, (grid_for(ncols * 32, 256, 4096)), (256), 0, st,
+               reinterpret_cast<const unsigned long long*>(colptr), row, val, ncols, col_base,
+               reinterpret_cast<unsigned long long*>(cur), col_tmp, val_tmp);
+    // rows sorted by column, so R(i, :) can be copied out in order
+    launch_sort_rows(rowptr_out, n_rows, col_tmp, val_tmp, col_out, val_out, st);
+  }
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }

@@ -22,6 +22,7 @@ CTD_MEM_DEVICE = 0
 CTD_MEM_HOST = 1
 CTD_SKIP_C = 1
 CTD_SKIP_ERROR = 2
+CTD_KEEP_LAST_C = 4
 
 STATUS = {0: "CTD_OK", 1: "CTD_EINVAL", 2: "CTD_ENOMEM", 3: "CTD_EOVERFLOW", 4: "CTD_ECUDA",
           5: "CTD_ETIMEOUT", 6: "CTD_ENOTSUP"}
@@ -67,7 +68,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     P, I64, I32, D, U64 = C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_uint64
     sig = {
         "ctd_static": [C.POINTER(ctd_coo3), I32, I64, D, U64, I32, C.c_uint, P, C.POINTER(P)],
-        "ctd_dynamic_create": [C.POINTER(C.c_int64 * 2), I32, I32, U64, U64, C.POINTER(P)],
+        "ctd_dynamic_create": [C.POINTER(C.c_int64 * 2), I32, I32, U64, U64, C.c_uint,
+                               C.POINTER(P)],
         "ctd_dynamic_step": [P, C.POINTER(ctd_coo3), I64, D, P],
         "ctd_error": [P, C.POINTER(D)],
         "ctd_get_sizes": [P, C.POINTER(ctd_sizes)],
@@ -268,12 +270,12 @@ class Dynamic(Factors):
     """A CTD-D state (Algorithm 2)."""
 
     def __init__(self, dims2, alpha: int = 1, precision: int = CTD_FP64, seed: int = 0,
-                 stream_id: int = 0):
+                 stream_id: int = 0, flags: int = 0):
         lib = load()
         out = C.c_void_p()
         d2 = (C.c_int64 * 2)(int(dims2[0]), int(dims2[1]))
         _check(lib.ctd_dynamic_create(C.byref(d2), int(alpha), int(precision), int(seed),
-                                      int(stream_id), C.byref(out)))
+                                      int(stream_id), int(flags), C.byref(out)))
         super().__init__(out.value)
 
     def step_slice(self, dX: Coo, d: int, eps: float, stream=None):

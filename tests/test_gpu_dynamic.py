@@ -1,0 +1,124 @@
+"""CTD-D parity: one step at a time, CUDA path (through the C ABI) vs the
+FP64 oracle's literal Algorithm 2 with a dense C."""
+import numpy as np
+import pytest
+
+from oracle import ctd_oracle as O
+from paper_1710_03608_gb300 import synth
+from tests.parity import error_tol, rel_fro, tie_margin, u_tol
+
+pytestmark = pytest.mark.gpu
+
+
+def ctd():
+    from paper_1710_03608_gb300 import ctd as m
+    return m
+
+
+def slices_small(n, dims2=(60, 40), nnz=150, seed=0):
+    return [synth.tiny((dims2[0], dims2[1], 1), nnz, seed=seed * 100 + t) for t in range(n)]
+
+
+def run_stream(slices, dims2, d, eps, seed, precision, alpha=1, check_every=True, flags=0):
+    m = ctd()
+    G = m.Dynamic(dims2, alpha, precision, seed, 0, flags)
+    st = O.DynamicState(dims2[alpha - 1], dims2[2 - alpha])
+    for t, sl in enumerate(slices):
+        X = m.Coo.from_synth(sl)
+        G.step_slice(X, d, eps)
+        if alpha == 1:
+            step = O.ctd_d_step(st, dims2, sl.i, sl.j, sl.val, d, eps, seed, keep_X=True)
+        else:  # mode 2: swap the roles of the two slice modes
+            step = O.ctd_d_step(st, (dims2[1], dims2[0]), sl.j, sl.i, sl.val, d, eps, seed,
+                                keep_X=True)
+        if check_every or t == len(slices) - 1:
+            check_step(G, st, step, t, eps, precision)
+    return G, st
+
+
+def check_step(G, st, step, t, eps, precision):
+    sz = G.sizes()
+    assert sz.t_steps == t + 1
+    I, Iu = G.samples()
+    assert np.array_equal(I, step.I)
+    assert np.array_equal(Iu, step.I_unique)
+    assert tie_margin(step.ratios, eps) > 1e-7, "near-tie"
+    info, sq = G.step(t)
+    assert info[0] == len(step.I_unique) and info[1] == len(step.new_fibers)
+    assert sq[0] == float(step.T_slice)
+    fib, fstep = G.fibers()
+    assert [(int(a), int(b)) for a, b in zip(fstep, fib)] == st.fibers
+    R_ref = (np.stack([np.rint(c).astype(np.int64) for c in st.R_cols], axis=1)
+             if st.R_cols else np.zeros((st.n_rows, 0), np.int64))
+    assert np.array_equal(G.R_dense(), R_ref)
+    if st.R_cols:
+        assert rel_fro(G.U(), st.U) <= u_tol(R_ref)
+    if step.M is not None:
+        assert rel_fro(G.M(t), step.M) <= u_tol(R_ref)
+    # every column of C^(t+1) (exact new block, implicit lower-left blocks)
+    J = st.n_cols_slice
+    ncols = J * (t + 1)
+    if st.C is not None and st.C.shape[0]:
+        got = G.C_columns(np.arange(ncols))
+        assert got.shape == st.C.shape
+        assert rel_fro(got, st.C) <= max(u_tol(R_ref), 1e-12)
+        assert np.array_equal(got[:, -J:], st.C[:, -J:])       # new block is exact
+    e_lit = O.dynamic_error_dense(st)
+    assert abs(G.error() - e_lit) <= error_tol(precision, e_lit) + 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_small_stream_every_step(precision):
+    run_stream(slices_small(8, seed=1), (60, 40), 20, 1e-6, 5, precision)
+
+
+def test_mode2_stream():
+    run_stream(slices_small(5, seed=2), (60, 40), 15, 1e-6, 3, 0, alpha=2)
+
+
+def test_first_step_equals_static():
+    m = ctd()
+    sl = slices_small(1, seed=3)[0]
+    G = m.Dynamic((60, 40), 1, 0, 11)
+    G.step_slice(m.Coo.from_synth(sl), 25, 1e-6)
+    F = m.ctd_static(m.Coo.from_synth(sl), 1, 25, 1e-6, 11, 0)
+    assert np.array_equal(G.samples()[0], F.samples()[0])
+    assert np.array_equal(G.fibers()[0], F.fibers()[0])
+    assert np.array_equal(G.R_dense(), F.R_dense())
+    assert rel_fro(G.U(), F.U()) <= 1e-12
+    assert abs(G.error() - F.error()) <= 1e-12
+
+
+def test_empty_slice_step():
+    sl = slices_small(3, seed=4)
+    sl[1].val[:] = 0
+    G, st = run_stream(sl, (60, 40), 10, 1e-6, 1, 0)
+    info, sq = G.step(1)
+    assert info[0] == 0 and info[1] == 0 and sq[0] == 0.0
+
+
+def test_keep_last_c_releases_older_blocks():
+    m = ctd()
+    G = m.Dynamic((60, 40), 1, 0, 2, 0, m.CTD_KEEP_LAST_C)
+    for sl in slices_small(3, seed=6):
+        G.step_slice(m.Coo.from_synth(sl), 10, 1e-6)
+    # the newest block stays readable, older ones were released
+    assert G.C_columns([2 * 40 + 1]).shape[1] == 1
+    with pytest.raises(m.CtdError):
+        G.C_columns([0])
+
+
+def test_traffic_stream_scaled():
+    """Slices of 1,000 x 1,000 (1,250 nonzeros each, Zipf(1.1), Poisson(2)+1)
+    with a planted 10 x 2 block of Poisson(40) counts at steps 40-45
+    (here within 14 steps: none), d = 400, eps = 1e-6, FP32 bulk."""
+    stream = synth.traffic_stream_20k(scale=0.05, steps=14)
+    run_stream(list(stream), stream.dims2, 400, 1e-6, 0, 1, check_every=False)
+
+
+def test_planted_block_stream_scaled():
+    """The same stream shape over steps 36..47 so the planted block (steps
+    40-45) arrives mid-stream."""
+    stream = synth.traffic_stream_20k(scale=0.05, steps=48)
+    sl = [stream.slice(t) for t in range(36, 48)]
+    run_stream(sl, stream.dims2, 400, 1e-6, 0, 0, check_every=False)
