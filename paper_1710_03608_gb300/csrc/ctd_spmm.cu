@@ -515,7 +515,24 @@ __global__ void k_build_q(CsrDev R, int64_t n_rows, const double* __restrict__ Z
 }
 
 // One warp per column (dynamic chunks).  Hot rows of Q (slot >= 0 in
-// `slot_of`) are staged in shared memory once per block.
+// `slot_of`) are staged in shared memory once per block.  A column's
+// entries are loaded 32 at a time (one per lane) and broadcast by shuffles;
+// two Q rows are in flight per step.
+template <typename T, int NC>
+__device__ __forceinline__ void qrow_fma(const T* __restrict__ qrow, float v, float* acc,
+                                         double* accd, int lane, int qs) {
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const int c = lane + 32 * k;
+    if (c < qs) {
+      if (sizeof(T) == 4)
+        acc[k] = fmaf(v, (float)qrow[c], acc[k]);
+      else
+        accd[k] = fma((double)v, (double)qrow[c], accd[k]);
+    }
+  }
+}
+
 template <typename T, int NC>
 __global__ void __launch_bounds__(256)
     k_qform(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs,
@@ -547,33 +564,57 @@ __global__ void __launch_bounds__(256)
         if (lane == 0) total = fma(v * v, qn[X.row[a]], total);
         continue;
       }
-      float accf[NC];
+      float acc[NC];
       double accd[NC];
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
-        accf[k] = 0.f;
+        acc[k] = 0.f;
         accd[k] = 0.0;
       }
-      for (unsigned long long p = a; p < b; ++p) {
-        const int i = __ldg(X.row + p);
-        const int v = __ldg(X.val + p);
-        const int sl = slot[i];
-        const T* qrow = sl >= 0 ? Qs + (int64_t)sl * qs : Q + (int64_t)i * qs;
+      for (unsigned long long base = a; base < b; base += 32) {
+        const int cnt = (int)min((unsigned long long)32, b - base);
+        const T* myrow = nullptr;
+        int myv = 0;
+        if (lane < cnt) {
+          const int i = __ldg(X.row + base + lane);
+          myv = __ldg(X.val + base + lane);
+          const int sl = slot[i];
+          myrow = sl >= 0 ? Qs + (int64_t)sl * qs : Q + (int64_t)i * qs;
+        }
+        int e = 0;
+        for (; e + 1 < cnt; e += 2) {
+          const T* r0 = (const T*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, e);
+          const T* r1 = (const T*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, e + 1);
+          const float v0 = (float)__shfl_sync(0xffffffffu, myv, e);
+          const float v1 = (float)__shfl_sync(0xffffffffu, myv, e + 1);
+          T q0[NC], q1[NC];
 #pragma unroll
-        for (int k = 0; k < NC; ++k) {
-          const int c = lane + 32 * k;
-          if (c < qs) {
-            if (sizeof(T) == 4)
-              accf[k] = fmaf((float)v, (float)qrow[c], accf[k]);
-            else
-              accd[k] = fma((double)v, (double)qrow[c], accd[k]);
+          for (int k = 0; k < NC; ++k) {
+            const int c = lane + 32 * k;
+            q0[k] = c < qs ? r0[c] : (T)0;
+            q1[k] = c < qs ? r1[c] : (T)0;
           }
+#pragma unroll
+          for (int k = 0; k < NC; ++k) {
+            if (sizeof(T) == 4) {
+              acc[k] = fmaf(v0, (float)q0[k], acc[k]);
+              acc[k] = fmaf(v1, (float)q1[k], acc[k]);
+            } else {
+              accd[k] = fma((double)v0, (double)q0[k], accd[k]);
+              accd[k] = fma((double)v1, (double)q1[k], accd[k]);
+            }
+          }
+        }
+        if (e < cnt) {
+          const T* r0 = (const T*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, e);
+          const float v0 = (float)__shfl_sync(0xffffffffu, myv, e);
+          qrow_fma<T, NC>(r0, v0, acc, accd, lane, qs);
         }
       }
       double ss = 0.0;
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
-        const double x = sizeof(T) == 4 ? (double)accf[k] : accd[k];
+        const double x = sizeof(T) == 4 ? (double)acc[k] : accd[k];
         ss = fma(x, x, ss);
       }
       for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
@@ -631,8 +672,9 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
   CTD_TRY(scratch.get(&slot_of, n_rows));
   CTD_TRY(scratch.get(&work, 1));
   CTD_TRY(scratch.get(&bsums, 4096));
-  // hot rows: as many as fit next to the slot table in 200 KB of shared memory
-  const size_t budget = 200 * 1024;
+  // hot rows: as many as fit next to the slot table in ~100 KB of shared
+  // memory, so two blocks (16 warps) stay resident per SM
+  const size_t budget = 100 * 1024;
   const size_t table = (size_t)n_rows * sizeof(short);
   int n_hot = 0;
   if (table < budget) n_hot = (int)std::min<size_t>((budget - table) / ((size_t)qs * tsz), n_hot_req);
