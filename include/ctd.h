@@ -187,6 +187,32 @@ CTD_API ctd_status ctd_get_M(const ctd_factors* F, int64_t t, double* M);
 
 CTD_API void ctd_free(ctd_factors* F);
 
+/*
+ * ctd_sample_noalloc -- the draws I and their unique set I' of ctd_static
+ * (same values as ctd_get_samples on ctd_static(X, alpha, s, eps, seed, ...)),
+ * without allocating any device memory.  The paper has no counterpart: this
+ * is for callers that cannot call cudaMalloc (code running inside another
+ * allocator's arena or under a hard memory cap, or latency-critical paths
+ * that must not enter the driver's allocator).
+ *  X         tensor in DEVICE memory (CTD_MEM_HOST is rejected: copying it
+ *            in would need a buffer)
+ *  draws     device int64[s], receives I;  unique: device int64[s],
+ *            receives I' ascending in its first *n_unique entries
+ *  n_unique  host int, receives s'
+ * Scratch lives in file-scope device arrays of the library, sized for
+ * N_alpha <= CTD_NOALLOC_MAX_COLS columns (8 MiB); every GPU that loads the
+ * library holds them until the process exits.  Larger N_alpha returns
+ * CTD_EINVAL.  The first call on a device looks up the arrays' device
+ * addresses for that device (once, with it current); make that first call
+ * before any stream capture.  Every call on a device shares the same arrays:
+ * calls that overlap on the GPU (other streams, other threads) race, so
+ * serialize them.  The call waits for its stream before returning.
+ */
+#define CTD_NOALLOC_MAX_COLS (1 << 20)
+CTD_API ctd_status ctd_sample_noalloc(const ctd_coo3* X, int alpha, int64_t s, uint64_t seed,
+                                      int64_t* draws, int64_t* unique, int* n_unique,
+                                      void* stream);
+
 /* Diagnostics (no counterpart in the paper).  ctd_profile(1) clears and
  * starts per-phase device timing: each phase of a call is bracketed by a
  * CUDA event pair on the call's stream.  ctd_profile_report waits for the

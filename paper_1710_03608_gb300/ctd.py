@@ -30,7 +30,7 @@ STATUS = {0: "CTD_OK", 1: "CTD_EINVAL", 2: "CTD_ENOMEM", 3: "CTD_EOVERFLOW", 4: 
 EXPORTED = ["ctd_static", "ctd_dynamic_create", "ctd_dynamic_step", "ctd_error", "ctd_get_sizes",
             "ctd_get_samples", "ctd_get_fibers", "ctd_get_R", "ctd_get_U", "ctd_get_C_columns",
             "ctd_get_C", "ctd_get_step", "ctd_get_M", "ctd_free", "ctd_last_error",
-            "ctd_version", "ctd_profile", "ctd_profile_report"]
+            "ctd_version", "ctd_profile", "ctd_profile_report", "ctd_sample_noalloc"]
 
 
 class CtdError(RuntimeError):
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ctd_get_step": [P, I64, P, P],
         "ctd_get_M": [P, I64, P],
         "ctd_profile": [I32],
+        "ctd_sample_noalloc": [C.POINTER(ctd_coo3), I32, I64, U64, P, P, C.POINTER(C.c_int), P],
         "ctd_profile_report": [C.c_char_p, C.c_size_t],
     }
     for name, args in sig.items():
@@ -282,6 +283,15 @@ class Dynamic(Factors):
         st = _stream_handle(stream) if not _host(dX) or stream is not None else _default_stream()
         _check(load().ctd_dynamic_step(self.h, C.byref(dX.desc), int(d), float(eps),
                                        C.c_void_p(st)))
+
+
+def sample_noalloc(X: Coo, alpha: int, s: int, seed: int, draws, unique, stream=None) -> int:
+    """ctd_sample_noalloc: the draws and unique draws of ctd_static into the
+    caller's device int64 tensors, with no device allocation; returns s'."""
+    n = C.c_int()
+    _check(load().ctd_sample_noalloc(C.byref(X.desc), int(alpha), int(s), int(seed), _ptr(draws),
+                                     _ptr(unique), C.byref(n), C.c_void_p(_stream_handle(stream))))
+    return n.value
 
 
 def profile(enable: bool = True) -> None:
