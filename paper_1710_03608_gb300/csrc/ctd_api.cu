@@ -261,7 +261,6 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   F->s_unique = s_unique;
   if (T == 0) F->s = 0;  // nothing to draw from
   const int su = s_unique;
-  const bool may_cancel = minval <= 0;
 
   // candidate columns R' (CSC) and their row-major copy
   uint64_t *rc_ptr, *rc_sizes;
@@ -365,7 +364,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
     F->Cval = cv;
     PhaseScope ph("c_fill", st);
     STEP(launch_c_fill(M.csc(), M.n_cols, R, F->Coff, F->Ccnt, F->Crow, F->Cval,
-                       precision == CTD_FP32_BULK, may_cancel, minval > 0, T, st));
+                       precision == CTD_FP32_BULK, minval > 0, T, st));
   }
 
   // Eq. (error): e = (T - ||Q^T X||_F^2) / T with Q = R L^{-T}
@@ -497,7 +496,7 @@ extern "C" ctd_status ctd_get_U(const ctd_factors* F, double* U) {
 namespace ctd {
 template <typename V>
 __global__ void k_c_columns(const unsigned long long* __restrict__ coff,
-                            const unsigned* __restrict__ ccnt, const int32_t* __restrict__ crow,
+                            const unsigned* __restrict__ ccnt, const uint16_t* __restrict__ crow,
                             const V* __restrict__ cval, const int64_t* __restrict__ cols,
                             int64_t ncols, int64_t height, double* __restrict__ out) {
   for (int64_t c = blockIdx.x; c < ncols; c += gridDim.x) {
@@ -553,7 +552,7 @@ extern "C" ctd_status ctd_get_C(const ctd_factors* F, int64_t* colptr, int32_t* 
   const int64_t n = F->n_cols;
   std::vector<uint64_t> off(n + 1);
   std::vector<uint32_t> cnt(n);
-  std::vector<int32_t> r(F->C_cap);
+  std::vector<uint16_t> r(F->C_cap);
   CTD_TRY(d2h(off.data(), F->Coff, n + 1, st));
   CTD_TRY(d2h(cnt.data(), F->Ccnt, n, st));
   CTD_TRY(d2h(r.data(), F->Crow, F->C_cap, st));

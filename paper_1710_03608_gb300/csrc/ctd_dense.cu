@@ -80,149 +80,321 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// 32 x 32 tile, 256 threads with 2 x 2 outputs each; blockIdx.z splits k
+// into chunks of kchunk.  With splits > 1 each split writes its partial
+// product to part + z * m * n (column-major, ld m) and k_splitk_reduce adds
+// them in split order (deterministic).
+constexpr int GS = 32;
+
+__global__ void __launch_bounds__(256)
+    k_dgemm32(int ta, int tb, int64_t m, int64_t n, int64_t k, double alpha,
+              const double* __restrict__ A, int64_t lda, const double* __restrict__ B,
+              int64_t ldb, double beta, double* __restrict__ C, int64_t ldc, int tri,
+              int64_t kchunk, double* __restrict__ part) {
+  __shared__ double As[GK][GS + 1];
+  __shared__ double Bs[GK][GS + 1];
+  const int64_t bm = (int64_t)blockIdx.x * GS, bn = (int64_t)blockIdx.y * GS;
+  if (tri && bn > bm) return;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[2][2] = {};
+  int64_t kb = (int64_t)blockIdx.z * kchunk, ke = min(k, kb + kchunk);
+  if (tri) kb = max(kb, bm);  // lower-triangular operand: terms need k >= max(row, col)
+  for (int64_t kk = kb; kk < ke; kk += GK) {
+    for (int e = threadIdx.x; e < GS * GK; e += 256) {
+      const int r = e % GS, q = e / GS;
+      const int64_t gr = bm + r, gq = kk + q;
+      double av = 0.0;
+      if (gr < m && gq < ke) av = ta ? A[gq + gr * lda] : A[gr + gq * lda];
+      As[q][r] = av;
+      const int64_t gc = bn + r;
+      double bv = 0.0;
+      if (gc < n && gq < ke) bv = tb ? B[gc + gq * ldb] : B[gq + gc * ldb];
+      Bs[q][r] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < GK; ++q) {
+      const double a0 = As[q][tx], a1 = As[q][tx + 16];
+      const double b0 = Bs[q][ty], b1 = Bs[q][ty + 16];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int64_t r = bm + tx + 16 * u, c = bn + ty + 16 * v;
+      if (r < m && c < n) {
+        if (part) {
+          part[(int64_t)blockIdx.z * m * n + r + c * m] = acc[u][v];
+        } else {
+          double* p = C + r + c * ldc;
+          *p = alpha * acc[u][v] + (beta == 0.0 ? 0.0 : beta * *p);
+        }
+      }
+    }
+}
+
+__global__ void k_splitk_reduce(const double* __restrict__ part, int splits, int64_t m, int64_t n,
+                                double alpha, double beta, double* __restrict__ C, int64_t ldc,
+                                int tri) {
+  const int64_t total = m * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % m, c = e / m;
+    if (tri && (c / GS) > (r / GS)) continue;
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += part[(int64_t)z * total + e];
+    double* p = C + r + c * ldc;
+    *p = alpha * s + (beta == 0.0 ? 0.0 : beta * *p);
+  }
+}
+
+static void dgemm_impl(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
+                       const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                       double* C, int64_t ldc, int tri, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return;
+  const int64_t sms = num_sms();
+  const int64_t t64 = ((m + GT - 1) / GT) * ((n + GT - 1) / GT);
+  if (!tri && t64 >= 2 * sms) {
+    dim3 g((unsigned)((m + GT - 1) / GT), (unsigned)((n + GT - 1) / GT));
+    CTD_LAUNCH(k_dgemm, (g), (256), 0, st, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+               0);
+    return;
+  }
+  const int64_t t32 = ((m + GS - 1) / GS) * ((n + GS - 1) / GS) / (tri ? 2 : 1) + 1;
+  // split k so that about four blocks per SM have work, in chunks of >= 64
+  int64_t splits = std::max<int64_t>(1, (4 * sms) / std::max<int64_t>(t32, 1));
+  splits = std::min<int64_t>(splits, std::max<int64_t>(1, k / 64));
+  splits = std::min<int64_t>(splits, 16);
+  int64_t kchunk = (k + splits - 1) / splits;
+  kchunk = ((kchunk + GK - 1) / GK) * GK;
+  splits = std::max<int64_t>(1, (k + kchunk - 1) / std::max<int64_t>(kchunk, 1));
+  dim3 g((unsigned)((m + GS - 1) / GS), (unsigned)((n + GS - 1) / GS), (unsigned)splits);
+  double* part = nullptr;
+  if (splits > 1 && dalloc_n(&part, (size_t)splits * m * n, st) != CTD_OK) {
+    part = nullptr;
+    splits = 1;
+    kchunk = std::max<int64_t>(k, 1);
+    g.z = 1;
+  }
+  CTD_LAUNCH(k_dgemm32, (g), (256), 0, st, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+             tri, std::max<int64_t>(kchunk, 1), splits > 1 ? part : nullptr);
+  if (splits > 1) {
+    CTD_LAUNCH(k_splitk_reduce, (grid_for(m * n, 256, sms * 8)), (256), 0, st, part, (int)splits,
+               m, n, alpha, beta, C, ldc, tri);
+    dfree(part, st);
+  }
+}
+
 void dgemm(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
            int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
            cudaStream_t st) {
-  if (m <= 0 || n <= 0) return;
-  dim3 g((unsigned)((m + GT - 1) / GT), (unsigned)((n + GT - 1) / GT));
-  CTD_LAUNCH(k_dgemm, (g), (256), 0, st, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 0);
+  dgemm_impl(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 0, st);
 }
 
-// Lower triangle (tile granularity) of C = Z^T Z for lower-triangular Z.
+// Lower tiles of C = Z^T Z for lower-triangular Z.
 static void dgemm_tri_lower(const double* Z, int64_t n, int64_t ldz, double* C, int64_t ldc,
                             cudaStream_t st) {
-  if (n <= 0) return;
-  dim3 g((unsigned)((n + GT - 1) / GT), (unsigned)((n + GT - 1) / GT));
-  CTD_LAUNCH(k_dgemm, (g), (256), 0, st, 1, 0, n, n, n, 1.0, Z, ldz, Z, ldz, 0.0, C, ldc, 1);
+  dgemm_impl(true, false, n, n, n, 1.0, Z, ldz, Z, ldz, 0.0, C, ldc, 1, st);
 }
 
 // ---------------------------------------------------------------------------
 // Cholesky with skip
 // ---------------------------------------------------------------------------
-__global__ void k_chol_diag(double* __restrict__ A, int64_t n, int64_t lda, int64_t k0,
-                            const double* __restrict__ thr, const int* __restrict__ force,
-                            int* __restrict__ keep, double* __restrict__ piv,
-                            unsigned* __restrict__ status) {
-  __shared__ double D[NB][NB + 1];  // D[r][c], lower
-  __shared__ int kp;
-  __shared__ double inv;
-  const int r = threadIdx.x;
-  const int nb = (int)min((int64_t)NB, n - k0);
-  if (r < nb)
-    for (int c = 0; c <= r; ++c) D[r][c] = A[(k0 + r) + (k0 + c) * lda];
-  __syncthreads();
-  for (int c = 0; c < nb; ++c) {
-    if (r == 0) {
-      const double d = D[c][c];
-      const int f = force ? force[k0 + c] : -1;
-      int k = (d > thr[k0 + c] && d > 0.0) ? 1 : 0;
-      if (f >= 0) k = f;
-      if (k && !(d > 0.0)) {  // forced keep of a column with no positive pivot
-        atomicOr(status, DEV_CAPACITY);
-        k = 0;
-      }
-      kp = k;
-      keep[k0 + c] = k;
-      if (piv) piv[k0 + c] = d;
-      const double l = k ? sqrt(d) : 0.0;
-      D[c][c] = l;
-      inv = k ? 1.0 / l : 0.0;
-    }
-    __syncthreads();
-    if (r > c && r < nb) D[r][c] = kp ? D[r][c] * inv : 0.0;
-    __syncthreads();
-    if (kp && r > c && r < nb) {
-      const double lrc = D[r][c];
-      for (int j = c + 1; j <= r; ++j) D[r][j] = fma(-lrc, D[j][c], D[r][j]);
-    }
-    __syncthreads();
-  }
-  if (r < nb)
-    for (int c = 0; c <= r; ++c) A[(k0 + r) + (k0 + c) * lda] = D[r][c];
-}
+// ---------------------------------------------------------------------------
+// The whole skip-Cholesky in one cooperative launch (one block per SM): per
+// 32-column panel, block 0 factors the diagonal block (in order, with the
+// keep/skip decisions), every block then forms its share of the panel rows
+// below and of the trailing update, separated by grid barriers.  The grid
+// barrier spins a bounded number of times; if it gives up it records
+// DEV_TIMEOUT and every block leaves, so the host reports CTD_ETIMEOUT.
+// ---------------------------------------------------------------------------
+constexpr long long BARRIER_SPIN_LIMIT = 1ll << 26;  // ~2 s of 32 ns naps
 
-// rows i >= k0 + nb: L21(i, :) = A21(i, :) L11^{-T} on kept columns
-__global__ void k_chol_rows(double* __restrict__ A, int64_t n, int64_t lda, int64_t k0,
-                            const int* __restrict__ keep) {
-  __shared__ double L[NB][NB + 1];
-  __shared__ int kp[NB];
-  const int nb = (int)min((int64_t)NB, n - k0);
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e % NB, c = e / NB;
-    L[r][c] = (r < nb && c <= r) ? A[(k0 + r) + (k0 + c) * lda] : 0.0;
-  }
-  if (threadIdx.x < NB) kp[threadIdx.x] = threadIdx.x < nb ? keep[k0 + threadIdx.x] : 0;
+struct GridBar {
+  unsigned* count;
+  unsigned* gen;
+  unsigned* status;
+};
+
+// returns false if the barrier timed out (or an earlier one did)
+__device__ bool grid_sync(const GridBar& gb) {
+  __shared__ int ok;
   __syncthreads();
-  const int64_t i = k0 + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double x[NB];
-#pragma unroll
-  for (int c = 0; c < NB; ++c) x[c] = c < nb ? A[i + (k0 + c) * lda] : 0.0;
-#pragma unroll
-  for (int c = 0; c < NB; ++c) {
-    if (c < nb) {
-      if (kp[c]) {
-        double s = x[c];
-#pragma unroll
-        for (int j = 0; j < c; ++j) s -= x[j] * L[c][j];
-        x[c] = s / L[c][c];
-      } else {
-        x[c] = 0.0;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = gb.gen;
+    volatile unsigned* vstat = gb.status;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(gb.count, 1u);
+    if (arrived == gridDim.x - 1) {
+      *gb.count = 0;
+      __threadfence();
+      atomicAdd(gb.gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g) {
+        if ((*vstat & DEV_TIMEOUT) || ++spins > BARRIER_SPIN_LIMIT) {
+          atomicOr(gb.status, DEV_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
       }
     }
+    __threadfence();
   }
-#pragma unroll
-  for (int c = 0; c < NB; ++c)
-    if (c < nb) A[i + (k0 + c) * lda] = x[c];
+  __syncthreads();
+  return ok != 0;
 }
 
-// trailing update of the lower triangle: A(r, c) -= sum_k L(r, k) L(c, k)
-// over the panel columns, for r >= c >= k1.  One 32 x 32 tile per block.
 __global__ void __launch_bounds__(256)
-    k_chol_trailing(double* __restrict__ A, int64_t n, int64_t lda, int64_t k0, int nb) {
-  __shared__ double Pr[NB][NB + 1];
+    k_chol_coop(double* __restrict__ A, int64_t n, int64_t lda, const double* __restrict__ thr,
+                const int* __restrict__ force, int* __restrict__ keep, double* __restrict__ piv,
+                unsigned* __restrict__ status, GridBar gb) {
+  __shared__ double D[NB][NB + 1];
   __shared__ double Pc[NB][NB + 1];
-  const int64_t k1 = k0 + nb;
-  const int64_t t = blockIdx.x;
-  // tile (bi, bj) with bi >= bj from the linear index
-  int64_t bi = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-  while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
-  while (bi * (bi + 1) / 2 > t) --bi;
-  const int64_t bj = t - bi * (bi + 1) / 2;
-  const int64_t r0 = k1 + bi * NB, c0 = k1 + bj * NB;
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int rr = e % NB, q = e / NB;
-    Pr[rr][q] = (r0 + rr < n && q < nb) ? A[(r0 + rr) + (k0 + q) * lda] : 0.0;
-    Pc[rr][q] = (c0 + rr < n && q < nb) ? A[(c0 + rr) + (k0 + q) * lda] : 0.0;
-  }
-  __syncthreads();
-  const int rr = threadIdx.x & 31, cq = threadIdx.x >> 5;  // 8 column groups
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int cc = cq + 8 * v;
-    const int64_t r = r0 + rr, c = c0 + cc;
-    if (r < n && c < n && r >= c) {
-      double s = 0.0;
-#pragma unroll
-      for (int q = 0; q < NB; ++q) s = fma(Pr[rr][q], Pc[cc][q], s);
-      A[r + c * lda] -= s;
+  __shared__ double invd[NB];
+  __shared__ int kp[NB];
+  __shared__ double thr_s[NB], piv_s[NB];
+  __shared__ int force_s[NB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int64_t k0 = 0; k0 < n; k0 += NB) {
+    const int nb = (int)min((int64_t)NB, n - k0);
+    // --- A: the diagonal block, in order, by block 0.  Decisions and
+    // pivots use shared memory only; they are stored after the loop.
+    if (blockIdx.x == 0) {
+      for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int r = e % NB, c = e / NB;
+        D[r][c] = (r < nb && c <= r) ? A[(k0 + r) + (k0 + c) * lda] : 0.0;
+      }
+      if (tid < nb) {
+        thr_s[tid] = thr[k0 + tid];
+        force_s[tid] = force ? force[k0 + tid] : -1;
+      }
+      __syncthreads();
+      for (int c = 0; c < nb; ++c) {
+        if (tid == 0) {
+          const double d = D[c][c];
+          int k = (d > thr_s[c] && d > 0.0) ? 1 : 0;
+          if (force_s[c] >= 0) k = force_s[c];
+          if (k && !(d > 0.0)) {
+            atomicOr(status, DEV_CAPACITY);
+            k = 0;
+          }
+          kp[c] = k;
+          piv_s[c] = d;
+          const double l = k ? sqrt(d) : 0.0;
+          D[c][c] = l;
+          invd[c] = k ? 1.0 / l : 0.0;
+        }
+        __syncthreads();
+        const int k = kp[c];
+        if (tid > c && tid < nb) D[tid][c] = k ? D[tid][c] * invd[c] : 0.0;
+        __syncthreads();
+        if (k) {  // trailing update inside the block: pairs c < j <= r < nb
+          for (int e = tid; e < NB * NB; e += blockDim.x) {
+            const int r = e % NB, j = e / NB;
+            if (j > c && j <= r && r < nb) D[r][j] = fma(-D[r][c], D[j][c], D[r][j]);
+          }
+          __syncthreads();
+        }
+      }
+      for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int r = e % NB, c = e / NB;
+        if (r < nb && c <= r) A[(k0 + r) + (k0 + c) * lda] = D[r][c];
+      }
+      if (tid < nb) {
+        keep[k0 + tid] = kp[tid];
+        if (piv) piv[k0 + tid] = piv_s[tid];
+      }
+      __threadfence();
     }
+    if (!grid_sync(gb)) return;
+    const int64_t k1 = k0 + nb;
+    const int64_t rest = n - k1;
+    if (rest <= 0) break;
+    // --- B: panel rows, L21(i, :) = A21(i, :) L11^{-T} on kept columns.
+    // One warp per row: lane c holds column c's value; each step's dot
+    // product over earlier columns is a warp reduction.
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      const int r = e % NB, c = e / NB;
+      D[r][c] = (r < nb && c <= r) ? A[(k0 + r) + (k0 + c) * lda] : 0.0;
+    }
+    if (tid < NB) {
+      kp[tid] = tid < nb ? keep[k0 + tid] : 0;
+      invd[tid] = (tid < nb && kp[tid]) ? 1.0 / D[tid][tid] : 0.0;
+    }
+    __syncthreads();
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = k1 + gw; i < n; i += nwarps) {
+      const double a = lane < nb ? A[i + (k0 + lane) * lda] : 0.0;
+      double x = 0.0;
+      for (int c = 0; c < nb; ++c) {
+        double part = (lane < c) ? x * D[c][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == c) x = kp[c] ? (a - part) * invd[c] : 0.0;
+      }
+      if (lane < nb) A[i + (k0 + lane) * lda] = x;
+    }
+    __threadfence();
+    if (!grid_sync(gb)) return;
+    // --- C: trailing update of the lower triangle, 32 x 32 tiles over blocks
+    const int64_t tb = (rest + NB - 1) / NB;
+    const int64_t ntiles = tb * (tb + 1) / 2;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      int64_t bi = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+      while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+      while (bi * (bi + 1) / 2 > t) --bi;
+      const int64_t bj = t - bi * (bi + 1) / 2;
+      const int64_t r0 = k1 + bi * NB, c0 = k1 + bj * NB;
+      __syncthreads();
+      for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int rr = e % NB, q = e / NB;
+        D[rr][q] = (r0 + rr < n && q < nb) ? A[(r0 + rr) + (k0 + q) * lda] : 0.0;
+        Pc[rr][q] = (c0 + rr < n && q < nb) ? A[(c0 + rr) + (k0 + q) * lda] : 0.0;
+      }
+      __syncthreads();
+      const int rr = tid & 31, cq = tid >> 5;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int cc = cq + 8 * v;
+        const int64_t r = r0 + rr, c = c0 + cc;
+        if (r < n && c < n && r >= c) {
+          double s2 = 0.0;
+#pragma unroll
+          for (int q = 0; q < NB; ++q) s2 = fma(D[rr][q], Pc[cc][q], s2);
+          A[r + c * lda] -= s2;
+        }
+      }
+    }
+    __threadfence();
+    if (!grid_sync(gb)) return;
   }
 }
 
 void launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr, int* keep,
                       cudaStream_t st, const int* force, double* piv, unsigned* status) {
-  for (int64_t k0 = 0; k0 < n; k0 += NB) {
-    const int nb = (int)std::min<int64_t>(NB, n - k0);
-    CTD_LAUNCH(k_chol_diag, (1), (NB), 0, st, A, n, lda, k0, thr, force, keep, piv, status);
-    const int64_t rest = n - k0 - nb;
-    if (rest > 0) {
-      CTD_LAUNCH(k_chol_rows, ((unsigned)((rest + 127) / 128)), (128), 0, st, A, n, lda, k0, keep);
-      const int64_t tb = (rest + NB - 1) / NB;
-      CTD_LAUNCH(k_chol_trailing, ((unsigned)(tb * (tb + 1) / 2)), (256), 0, st, A, n, lda, k0,
-                 nb);
-    }
-  }
+  if (n <= 0) return;
+  // barrier words live in the status array's tail: status[1] count, status[2] generation
+  GridBar gb{status + 1, status + 2, status};
+  cudaMemsetAsync(status + 1, 0, 2 * sizeof(unsigned), st);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_coop, 256, 0);
+  const int nblocks = num_sms() * (per_sm > 0 ? 1 : 0);
+  if (nblocks <= 0) return;
+  void* args[] = {&A, &n, &lda, const_cast<double**>(&thr), const_cast<int**>(&force), &keep,
+                  &piv, &status, &gb};
+  note_launch();
+  cudaLaunchCooperativeKernel((const void*)k_chol_coop, dim3(nblocks), dim3(256), args, 0, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -278,91 +450,24 @@ void launch_gather_lower(const double* A, int64_t lda, const int* idx, const int
 }
 
 // ---------------------------------------------------------------------------
-// Z = L^{-1} (blocked by 32)
+// Z = L^{-1}
 // ---------------------------------------------------------------------------
-__global__ void k_trinv_diag(const double* __restrict__ L, int64_t ldl, int64_t n,
-                             double* __restrict__ Z, int64_t ldz) {
-  __shared__ double Lb[NB][NB + 1];
-  __shared__ double Zb[NB][NB + 1];
-  const int64_t b0 = (int64_t)blockIdx.x * NB;
-  const int nb = (int)min((int64_t)NB, n - b0);
-  const int j = threadIdx.x;
-  for (int r = 0; r < NB; ++r) {
-    Lb[r][j] = (r < nb && j < nb && j <= r) ? L[(b0 + r) + (b0 + j) * ldl] : 0.0;
-    Zb[r][j] = 0.0;
-  }
-  __syncthreads();
-  if (j < nb) {
-    Zb[j][j] = 1.0 / Lb[j][j];
-    for (int i = j + 1; i < nb; ++i) {
-      double s = 0.0;
-      for (int q = j; q < i; ++q) s = fma(Lb[i][q], Zb[q][j], s);
-      Zb[i][j] = -s / Lb[i][i];
-    }
-  }
-  __syncthreads();
-  for (int r = 0; r < nb; ++r)
-    if (j < nb) Z[(b0 + r) + (b0 + j) * ldz] = Zb[r][j];
-}
-
-// block row I: Z[I, J] = -Z[I, I] * sum_{K=J}^{I-1} L[I, K] Z[K, J], one block per J
-__global__ void __launch_bounds__(256)
-    k_trinv_row(const double* __restrict__ L, int64_t ldl, int64_t n, double* __restrict__ Z,
-                int64_t ldz, int64_t bI) {
-  __shared__ double Ls[NB][NB + 1];
-  __shared__ double Zs[NB][NB + 1];
-  __shared__ double Ts[NB][NB + 1];
-  const int64_t bJ = blockIdx.x;
-  const int64_t r0 = bI * NB;
-  const int rr = threadIdx.x & 31, cq = threadIdx.x >> 5;
-  double t[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int64_t bK = bJ; bK < bI; ++bK) {
-    for (int e = threadIdx.x; e < NB * NB; e += 256) {
-      const int a = e % NB, b = e / NB;
-      const int64_t lr = r0 + a, lc = bK * NB + b;
-      Ls[a][b] = (lr < n && lc < n) ? L[lr + lc * ldl] : 0.0;
-      const int64_t zr = bK * NB + a, zc = bJ * NB + b;
-      Zs[a][b] = (zr < n && zc < n) ? Z[zr + zc * ldz] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int cc = cq + 8 * v;
-      double s = t[v];
-#pragma unroll
-      for (int q = 0; q < NB; ++q) s = fma(Ls[rr][q], Zs[q][cc], s);
-      t[v] = s;
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int v = 0; v < 4; ++v) Ts[rr][cq + 8 * v] = t[v];
-  // diagonal block of Z
-  for (int e = threadIdx.x; e < NB * NB; e += 256) {
-    const int a = e % NB, b = e / NB;
-    const int64_t zr = r0 + a, zc = r0 + b;
-    Zs[a][b] = (zr < n && zc < n) ? Z[zr + zc * ldz] : 0.0;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int cc = cq + 8 * v;
-    double s = 0.0;
-#pragma unroll
-    for (int q = 0; q < NB; ++q) s = fma(Zs[rr][q], Ts[q][cc], s);
-    const int64_t zr = r0 + rr, zc = bJ * NB + cc;
-    if (zr < n && zc < n) Z[zr + zc * ldz] = -s;
+__global__ void k_identity(double* Z, int64_t n, int64_t ldz) {
+  const int64_t total = n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % n, c = e / n;
+    Z[r + c * ldz] = r == c ? 1.0 : 0.0;
   }
 }
 
+// Z = L^{-1}: forward substitution with the identity as right-hand sides
+// (blocked: substitution on 32-row diagonal blocks, GEMM updates below).
 void tri_inverse(const double* L, int64_t ldl, int64_t n, double* Z, int64_t ldz,
                  cudaStream_t st) {
   if (n <= 0) return;
-  const int64_t nbk = (n + NB - 1) / NB;
-  launch_zero_f64(Z, n, n, ldz, st);
-  CTD_LAUNCH(k_trinv_diag, ((unsigned)nbk), (NB), 0, st, L, ldl, n, Z, ldz);
-  for (int64_t bI = 1; bI < nbk; ++bI)
-    CTD_LAUNCH(k_trinv_row, ((unsigned)bI), (256), 0, st, L, ldl, n, Z, ldz, bI);
+  CTD_LAUNCH(k_identity, (grid_for(n * n, 256, (int64_t)num_sms() * 8)), (256), 0, st, Z, n, ldz);
+  tri_solve_lower(L, ldl, n, Z, ldz, n, st);
 }
 
 // U = Z^T Z for Z = L^{-1}: lower tiles then mirror.

@@ -40,7 +40,7 @@ struct StepRec {
   double* M = nullptr;             // Y_K: d_before x d_kept column-major (= M row-major)
   uint64_t* Coff = nullptr;        // new-column block, height d_before + d_kept
   uint32_t* Ccnt = nullptr;
-  int32_t* Crow = nullptr;
+  uint16_t* Crow = nullptr;
   void* Cval = nullptr;
   int64_t nnzC = 0;
 };
@@ -70,7 +70,7 @@ __global__ void k_transpose_f64(const double* __restrict__ A, int64_t lda, int64
 // dense (ld x J) FP64 copy of a sparse new-column block (rows < height)
 template <typename V>
 __global__ void k_densify(const unsigned long long* __restrict__ coff,
-                          const unsigned* __restrict__ ccnt, const int32_t* __restrict__ crow,
+                          const unsigned* __restrict__ ccnt, const uint16_t* __restrict__ crow,
                           const V* __restrict__ cval, int64_t n_cols, double* __restrict__ out,
                           int64_t ld) {
   for (int64_t f = blockIdx.x; f < n_cols; f += gridDim.x) {
@@ -444,7 +444,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
     {
       PhaseScope ph("d_c_fill", st);
       CTD_TRY(launch_c_fill(M.csc(), M.n_cols, R, rec.Coff, rec.Ccnt, rec.Crow, rec.Cval, fp32,
-                            !D.all_positive, D.all_positive, (uint64_t)D.max_T, st));
+                            D.all_positive, (uint64_t)D.max_T, st));
     }
     double* d_pu;
     uint64_t* d_nnzc;
@@ -596,7 +596,7 @@ ctd_status dyn_C_columns(const ctd_factors* F, int64_t ncols, const int64_t* col
       CTD_TRY(d2h(&off, r.Coff + f, 1, st));
       CTD_TRY(d2h(&n, r.Ccnt + f, 1, st));
       CTD_TRY(sync(st));
-      std::vector<int32_t> rows(n);
+      std::vector<uint16_t> rows(n);
       CTD_TRY(d2h(rows.data(), r.Crow + off, n, st));
       if (F->precision == CTD_FP32_BULK) {
         std::vector<float> vals(n);

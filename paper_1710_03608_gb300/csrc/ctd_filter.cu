@@ -157,7 +157,7 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
   CTD_TRY(scratch.get(&piv, du));
   CTD_TRY(scratch.get(&force, du));
   CTD_TRY(scratch.get(&count, 1));
-  CTD_TRY(scratch.get(&status, 1));
+  CTD_TRY(scratch.get(&status, 4));
   CTD_TRY(scratch.get(&out.keep, du));
   CTD_TRY(scratch.get(&out.idx, du));
   CTD_CUDA(cudaMemcpyAsync(S0, in.S, (size_t)du * du * 8, cudaMemcpyDeviceToDevice, st));
@@ -187,6 +187,7 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
     CTD_TRY(d2h(h_keep.data(), out.keep, du, st));
     CTD_CUDA(cudaGetLastError());
     CTD_TRY(sync(st));
+    if (h_status & DEV_TIMEOUT) return fail(CTD_ETIMEOUT, "skip-Cholesky grid barrier gave up");
     if (h_status & DEV_CAPACITY)
       return fail(CTD_ENOTSUP,
                   "a fiber tested independent by its explicit residual has no positive pivot "

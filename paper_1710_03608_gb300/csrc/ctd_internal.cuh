@@ -208,12 +208,12 @@ ctd_status launch_spmm_dense(const CscDev& X, const int64_t* fibers, const int* 
 void launch_c_bounds(const CscDev& X, int64_t n_cols, const CsrDev& R, uint32_t* ub,
                      cudaStream_t st);
 // fill: column f's entries go to [coff[f], coff[f] + ccnt[f]) with rows
-// ascending.  Values stored as float (fp32 != 0) or double.  R's rows must
-// be sorted by column.  positive: every value of X and R is > 0.
+// ascending (16-bit row indices).  Values stored as float (fp32 != 0) or
+// double.  R's rows must be sorted by column.  positive: every value of X
+// and R is > 0 (enables the one-nonzero copy path).
 ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, const CsrDev& R,
-                         const uint64_t* coff, uint32_t* ccnt, int32_t* crow, void* cval,
-                         int fp32, int may_cancel, int positive, uint64_t sqnorm_X,
-                         cudaStream_t st);
+                         const uint64_t* coff, uint32_t* ccnt, uint16_t* crow, void* cval,
+                         int fp32, int positive, uint64_t sqnorm_X, cudaStream_t st);
 // Sort each row of a row-major factor by column (col/val copied to *_out).
 void launch_sort_rows(const uint64_t* rowptr, int64_t n_rows, const int32_t* col_in,
                       const int32_t* val_in, int32_t* col_out, int32_t* val_out, cudaStream_t st);
@@ -242,10 +242,11 @@ void dgemm(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, cons
 // keep[k] in {0,1}.
 // force (optional): -1 decide by pivot, 0 skip, 1 keep.  piv (optional)
 // receives each column's pivot before its decision; a forced keep without a
-// positive pivot sets DEV_CAPACITY in *status (required when force is set).
+// positive pivot sets DEV_CAPACITY in status[0]; a grid barrier that gives
+// up sets DEV_TIMEOUT.  status must hold 3 words (status[1..2] are the grid
+// barrier's counter and generation).
 void launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr, int* keep,
-                      cudaStream_t st, const int* force = nullptr, double* piv = nullptr,
-                      unsigned* status = nullptr);
+                      cudaStream_t st, const int* force, double* piv, unsigned* status);
 // B <- L^{-T} B for lower-triangular L, by backward substitution.
 void tri_solve_lower_T(const double* L, int64_t ldl, int64_t n, double* B, int64_t ldb,
                        int64_t nrhs, cudaStream_t st);
@@ -336,12 +337,6 @@ struct FilterOut {
 };
 ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaStream_t st);
 
-// ctd_spmm.cu: sum over columns f of c_f^T U c_f for a sparse C stored as
-// (coff, ccnt, crow, cval) with n_cols columns and U (n x n, leading dim ldu).
-ctd_status launch_quad_form(const uint64_t* coff, const uint32_t* ccnt, const int32_t* crow,
-                            const void* cval, int fp32, int64_t n_cols, const double* U,
-                            int64_t ldu, double* out, cudaStream_t st);
-
 }  // namespace ctd
 
 // The library-owned factors.
@@ -374,7 +369,7 @@ struct ctd_factors {
   double* L = nullptr;           // CTD-D: Cholesky factor of R^T R (lower, ld as U)
   uint64_t* Coff = nullptr;      // [n_cols+1]
   uint32_t* Ccnt = nullptr;      // [n_cols]
-  int32_t* Crow = nullptr;
+  uint16_t* Crow = nullptr;
   void* Cval = nullptr;          // float or double
   uint64_t C_cap = 0;
   // CTD-D extras live in ctd_dynamic.cu

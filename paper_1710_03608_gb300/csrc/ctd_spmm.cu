@@ -152,14 +152,17 @@ void launch_c_bounds(const CscDev& X, int64_t n_cols, const CsrDev& R, uint32_t*
 // C fill
 //
 // Column f of C is written to [coff[f], coff[f] + ccnt[f]) with rows
-// ascending.  Three paths:
-//  * a column with one nonzero v in row i (and all values positive) is
+// ascending (uint16 row index: s~ <= 24576).  Three paths:
+//  * a column with one nonzero v in row i (all values positive) is
 //    v * R(i, :), copied from R's row i (rows of R are sorted by column);
 //  * other columns with fewer than HEAVY nonzeros: one warp each, with a
-//    warp-private accumulator;
+//    warp-private accumulator in shared memory;
 //  * heavy columns: a whole block each.
-// Accumulators are int32 when ||X||_F^2 < 2^31: by Cauchy-Schwarz every
-// partial sum is at most ||x_f|| ||r_m|| <= ||X||_F^2, so int32 is exact.
+// An output entry exists exactly where the accumulator is nonzero, so the
+// emission is a sweep over the accumulator, 32 rows at a time, compacted
+// with a ballot (ascending order, exact zeros dropped) -- no touched-set
+// bookkeeping.  Accumulators are int32 when ||X||_F^2 < 2^31: by
+// Cauchy-Schwarz every partial sum is at most ||x_f|| ||r_m|| <= ||X||_F^2.
 // ---------------------------------------------------------------------------
 constexpr int HEAVY = 128;
 
@@ -174,14 +177,18 @@ __device__ __forceinline__ void acc_add<unsigned long long>(unsigned long long* 
   atomicAdd(p, (unsigned long long)x);
 }
 template <typename A>
-__device__ __forceinline__ long long acc_get(const A* p) {
-  return sizeof(A) == 4 ? (long long)(*(const int*)p) : (long long)(*(const unsigned long long*)p);
+__device__ __forceinline__ long long acc_val(A x) {
+  return sizeof(A) == 4 ? (long long)(int)x : (long long)x;
 }
+
+// R rows with at least LONG_ROW entries are walked by the whole warp (one
+// product per lane per step); shorter rows go through expand_chunk, which
+// spreads the products of 32 short rows over the lanes.
+constexpr int LONG_ROW = 16;
 
 template <typename A>
 __device__ __forceinline__ void accumulate_column_t(const CscDev& X, const CsrDev& R, int64_t f,
-                                                    A* acc, unsigned* bitmap, int gwarp,
-                                                    int gwarps) {
+                                                    A* acc, int gwarp, int gwarps) {
   const unsigned long long a = X.colptr[f], b = X.colptr[f + 1];
   const int lane = threadIdx.x & 31;
   for (unsigned long long p0 = a + (unsigned long long)gwarp * 32; p0 < b;
@@ -195,134 +202,107 @@ __device__ __forceinline__ void accumulate_column_t(const CscDev& X, const CsrDe
       rs = __ldg(reinterpret_cast<const unsigned long long*>(R.rowptr) + i);
       rl = (int)(__ldg(reinterpret_cast<const unsigned long long*>(R.rowptr) + i + 1) - rs);
     }
-    expand_chunk(rs, rl, v, R.col, R.val, [&](int m, long long prod) {
-      acc_add<A>(acc + m, prod);
-      atomicOr(bitmap + (m >> 5), 1u << (m & 31));
-    });
+    unsigned longs = __ballot_sync(0xffffffffu, rl >= LONG_ROW);
+    while (longs) {
+      const int src = __ffs(longs) - 1;
+      longs &= longs - 1;
+      const unsigned long long s0 = __shfl_sync(0xffffffffu, rs, src);
+      const int n = __shfl_sync(0xffffffffu, rl, src);
+      const long long vs = __shfl_sync(0xffffffffu, v, src);
+      for (int q = lane; q < n; q += 32)
+        acc_add<A>(acc + __ldg(R.col + s0 + q), vs * (long long)__ldg(R.val + s0 + q));
+    }
+    if (rl >= LONG_ROW) rl = 0;
+    if (__any_sync(0xffffffffu, rl > 0))
+      expand_chunk(rs, rl, v, R.col, R.val,
+                   [&](int m, long long prod) { acc_add<A>(acc + m, prod); });
   }
 }
 
-// Emit the touched entries of one column in ascending row order and reset
-// them.  Group = gthreads threads (a warp or the block).
+// Warp-level emission of one column: sweep acc 32 rows at a time.
 template <typename V, typename A>
-__device__ void emit_column_t(A* acc, unsigned* bitmap, int width, int* wpre, int gtid,
-                              int gthreads, bool may_cancel, unsigned long long off,
-                              int32_t* __restrict__ crow, V* __restrict__ cval, unsigned* count,
-                              bool block_group) {
-  const int nwords = (width + 31) >> 5;
-  const int lane = gtid & 31;
-  if (may_cancel) {  // drop exact zeros (only possible with signed inputs)
-    for (int w = gtid; w < nwords; w += gthreads) {
-      unsigned bits = bitmap[w], keep = bits;
-      while (bits) {
-        const int bpos = __ffs(bits) - 1;
-        bits &= bits - 1;
-        if (acc_get<A>(acc + w * 32 + bpos) == 0) keep &= ~(1u << bpos);
-      }
-      bitmap[w] = keep;
+__device__ __forceinline__ unsigned emit_warp(A* acc, int width, unsigned long long off,
+                                              uint16_t* __restrict__ crow, V* __restrict__ cval) {
+  const int lane = threadIdx.x & 31;
+  unsigned pos = 0;
+  for (int m0 = 0; m0 < width; m0 += 32) {
+    const int m = m0 + lane;
+    long long x = 0;
+    if (m < width) {
+      x = acc_val<A>(acc[m]);
+      acc[m] = 0;
     }
-    if (block_group) __syncthreads(); else __syncwarp();
-  }
-  int carry = 0;
-  for (int w0 = 0; w0 < nwords; w0 += gthreads) {
-    const int w = w0 + gtid;
-    const int c = w < nwords ? __popc(bitmap[w]) : 0;
-    int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+    const unsigned ball = __ballot_sync(0xffffffffu, x != 0);
+    if (x != 0) {
+      const unsigned q = pos + __popc(ball & ((1u << lane) - 1));
+      crow[off + q] = (uint16_t)m;
+      cval[off + q] = (V)x;
     }
-    if (block_group) {
-      __shared__ int wtot[32];
-      const int warp = gtid >> 5;
-      if (lane == 31) wtot[warp] = incl;
-      __syncthreads();
-      int before = 0, all = 0;
-      for (int q = 0; q < (gthreads >> 5); ++q) {
-        if (q < warp) before += wtot[q];
-        all += wtot[q];
-      }
-      if (w < nwords) wpre[w] = carry + before + incl - c;
-      __syncthreads();
-      carry += all;
-    } else {
-      if (w < nwords) wpre[w] = carry + incl - c;
-      carry += __shfl_sync(0xffffffffu, incl, 31);
-    }
+    pos += __popc(ball);
   }
-  if (block_group) __syncthreads(); else __syncwarp();
-  const int total = carry;
-  for (int k = gtid; k < total; k += gthreads) {
-    int lo = 0, hi = nwords - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (wpre[mid] <= k)
-        lo = mid;
-      else
-        hi = mid - 1;
-    }
-    const int bpos = __fns(bitmap[lo], 0, k - wpre[lo] + 1);
-    const int m = lo * 32 + bpos;
-    crow[off + k] = m;
-    cval[off + k] = (V)acc_get<A>(acc + m);
-    acc[m] = 0;
-  }
-  if (block_group) __syncthreads(); else __syncwarp();
-  if (may_cancel) {  // dropped zeros were reset already (their value is 0)
-  }
-  for (int w = gtid; w < nwords; w += gthreads) bitmap[w] = 0;
-  if (block_group) __syncthreads(); else __syncwarp();
-  if (gtid == 0) *count = (unsigned)total;
+  return pos;
 }
 
 template <typename V, typename A>
 __global__ void __launch_bounds__(SPMM_THREADS)
     k_c_fill_warp(CscDev X, int64_t n_cols, CsrDev R, const unsigned long long* __restrict__ coff,
-                  unsigned* __restrict__ ccnt, int32_t* __restrict__ crow, V* __restrict__ cval,
-                  int may_cancel, int positive, unsigned long long* work) {
+                  unsigned* __restrict__ ccnt, uint16_t* __restrict__ crow, V* __restrict__ cval,
+                  int positive, unsigned long long* work) {
   extern __shared__ unsigned long long smem_u64[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int width = R.width, nwords = (width + 31) >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int width = R.width;
   const int accw = (width + 1) & ~1;  // keep 8-byte alignment between warps
   A* acc = reinterpret_cast<A*>(smem_u64) + (size_t)warp * accw;
-  unsigned* bitmaps = reinterpret_cast<unsigned*>(reinterpret_cast<A*>(smem_u64) + (size_t)nw * accw);
-  unsigned* bitmap = bitmaps + warp * nwords;
-  int* wpre = reinterpret_cast<int*>(bitmaps + nw * nwords) + warp * (nwords + 1);
   for (int m = lane; m < width; m += 32) acc[m] = 0;
-  for (int w = lane; w < nwords; w += 32) bitmap[w] = 0;
   __syncwarp();
   const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
-  constexpr int CHUNK = 64;
+  const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(X.colptr);
+  // 32 columns per grab; lane l prefetches column f0 + l's offsets and, for a
+  // one-nonzero column, its entry and R-row range, so empty and one-nonzero
+  // columns cost no dependent loads inside the walk below
   while (true) {
     unsigned long long f0 = 0;
-    if (lane == 0) f0 = atomicAdd(work, (unsigned long long)CHUNK);
+    if (lane == 0) f0 = atomicAdd(work, 32ull);
     f0 = __shfl_sync(0xffffffffu, f0, 0);
     if (f0 >= (unsigned long long)n_cols) break;
-    const int64_t f1 = min((int64_t)f0 + CHUNK, n_cols);
-    for (int64_t f = (int64_t)f0; f < f1; ++f) {
-      const unsigned long long o = coff[f];
-      if (coff[f + 1] == o) {
-        if (lane == 0) ccnt[f] = 0;
-        continue;
+    const int64_t f = (int64_t)f0 + lane;
+    unsigned long long o = 0, xa = 0, rs = 0;
+    int ub = 0, nx = 0, vv = 0, rl = 0;
+    if (f < n_cols) {
+      o = coff[f];
+      ub = (int)(coff[f + 1] - o);
+      xa = xp[f];
+      nx = (int)min(xp[f + 1] - xa, (unsigned long long)0x7fffffff);
+      if (ub > 0 && nx == 1 && positive) {
+        const int i = __ldg(X.row + xa);
+        vv = __ldg(X.val + xa);
+        rs = __ldg(rp + i);
+        rl = (int)(__ldg(rp + i + 1) - rs);
       }
-      const unsigned long long a = X.colptr[f], b = X.colptr[f + 1];
-      if (b - a >= (unsigned long long)HEAVY) continue;  // block kernel
-      if (b - a == 1 && positive) {
-        const int i = __ldg(X.row + a);
-        const long long v = __ldg(X.val + a);
-        const unsigned long long rs = __ldg(rp + i), n = __ldg(rp + i + 1) - rs;
-        for (unsigned long long q = lane; q < n; q += 32) {
-          crow[o + q] = __ldg(R.col + rs + q);
-          cval[o + q] = (V)(v * (long long)__ldg(R.val + rs + q));
+      if (ub == 0) ccnt[f] = 0;
+    }
+    const int nf = (int)min((int64_t)32, n_cols - (int64_t)f0);
+    for (int e = 0; e < nf; ++e) {
+      const int ube = __shfl_sync(0xffffffffu, ub, e);
+      const int nxe = __shfl_sync(0xffffffffu, nx, e);
+      if (ube == 0 || nxe >= HEAVY) continue;  // empty here; heavy: block kernel
+      const unsigned long long oe = __shfl_sync(0xffffffffu, o, e);
+      if (nxe == 1 && positive) {
+        const unsigned long long rse = __shfl_sync(0xffffffffu, rs, e);
+        const int rle = __shfl_sync(0xffffffffu, rl, e);
+        const long long ve = __shfl_sync(0xffffffffu, vv, e);
+        for (int q = lane; q < rle; q += 32) {
+          crow[oe + q] = (uint16_t)__ldg(R.col + rse + q);
+          cval[oe + q] = (V)(ve * (long long)__ldg(R.val + rse + q));
         }
-        if (lane == 0) ccnt[f] = (unsigned)n;
+        if (lane == 0) ccnt[f0 + e] = (unsigned)rle;
         continue;
       }
-      accumulate_column_t<A>(X, R, f, acc, bitmap, 0, 1);
+      accumulate_column_t<A>(X, R, (int64_t)f0 + e, acc, 0, 1);
       __syncwarp();
-      emit_column_t<V, A>(acc, bitmap, width, wpre, lane, 32, may_cancel != 0, o, crow, cval,
-                          ccnt + f, false);
+      const unsigned n = emit_warp<V, A>(acc, width, oe, crow, cval);
+      __syncwarp();
+      if (lane == 0) ccnt[f0 + e] = n;
     }
   }
 }
@@ -331,18 +311,16 @@ template <typename V, typename A>
 __global__ void __launch_bounds__(SPMM_THREADS)
     k_c_fill_block(CscDev X, const int64_t* __restrict__ list, const unsigned* __restrict__ nlist,
                    CsrDev R, const unsigned long long* __restrict__ coff,
-                   unsigned* __restrict__ ccnt, int32_t* __restrict__ crow, V* __restrict__ cval,
-                   int may_cancel, unsigned long long* work) {
+                   unsigned* __restrict__ ccnt, uint16_t* __restrict__ crow, V* __restrict__ cval,
+                   unsigned long long* work) {
   extern __shared__ unsigned long long smem_u64[];
-  const int width = R.width, nwords = (width + 31) >> 5;
+  const int width = R.width;
   A* acc = reinterpret_cast<A*>(smem_u64);
-  unsigned* bitmap = reinterpret_cast<unsigned*>(acc + ((width + 1) & ~1));
-  int* wpre = reinterpret_cast<int*>(bitmap + nwords);
   __shared__ unsigned long long fcur;
-  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ unsigned wcount[SPMM_THREADS / 32];
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
   const unsigned long long n = *nlist;
   for (int m = threadIdx.x; m < width; m += blockDim.x) acc[m] = 0;
-  for (int w = threadIdx.x; w < nwords; w += blockDim.x) bitmap[w] = 0;
   __syncthreads();
   while (true) {
     if (threadIdx.x == 0) fcur = atomicAdd(work, 1ull);
@@ -351,10 +329,42 @@ __global__ void __launch_bounds__(SPMM_THREADS)
     __syncthreads();
     if (it >= n) break;
     const int64_t f = list[it];
-    accumulate_column_t<A>(X, R, f, acc, bitmap, warp, nw);
+    accumulate_column_t<A>(X, R, f, acc, warp, nw);
     __syncthreads();
-    emit_column_t<V, A>(acc, bitmap, width, wpre, threadIdx.x, blockDim.x, may_cancel != 0,
-                        coff[f], crow, cval, ccnt + f, true);
+    // emission: warp w sweeps rows [w * span, (w + 1) * span) after counting
+    const int span = (((width + nw - 1) / nw) + 31) & ~31;
+    const int m_lo = min(width, warp * span), m_hi = min(width, m_lo + span);
+    unsigned cnt = 0;
+    for (int m0 = m_lo; m0 < m_hi; m0 += 32) {
+      const int m = m0 + lane;
+      const bool nz = m < m_hi && acc[m] != 0;
+      cnt += __popc(__ballot_sync(0xffffffffu, nz));
+    }
+    if (lane == 0) wcount[warp] = cnt;
+    __syncthreads();
+    unsigned pos = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) pos += wcount[w];
+      total += wcount[w];
+    }
+    const unsigned long long off = coff[f];
+    for (int m0 = m_lo; m0 < m_hi; m0 += 32) {
+      const int m = m0 + lane;
+      long long x = 0;
+      if (m < m_hi) {
+        x = acc_val<A>(acc[m]);
+        acc[m] = 0;
+      }
+      const unsigned ball = __ballot_sync(0xffffffffu, x != 0);
+      if (x != 0) {
+        const unsigned q = pos + __popc(ball & ((1u << lane) - 1));
+        crow[off + q] = (uint16_t)m;
+        cval[off + q] = (V)x;
+      }
+      pos += __popc(ball);
+    }
+    if (threadIdx.x == 0) ccnt[f] = total;
+    __syncthreads();
   }
 }
 
@@ -372,10 +382,10 @@ __global__ void k_list_columns(const unsigned long long* __restrict__ colptr,
 
 template <typename V, typename A>
 static ctd_status c_fill_impl(const CscDev& X, int64_t n_cols, const CsrDev& R,
-                              const uint64_t* coff, uint32_t* ccnt, int32_t* crow, V* cval,
-                              int may_cancel, int positive, unsigned long long* work,
-                              int64_t* heavy, unsigned* nheavy, cudaStream_t st) {
-  const int width = R.width, nwords = (width + 31) >> 5;
+                              const uint64_t* coff, uint32_t* ccnt, uint16_t* crow, V* cval,
+                              int positive, unsigned long long* work, int64_t* heavy,
+                              unsigned* nheavy, cudaStream_t st) {
+  const int width = R.width;
   const int accw = (width + 1) & ~1;
   const unsigned long long* co = reinterpret_cast<const unsigned long long*>(coff);
   // heavy columns (and, if the warp accumulator would not fit, all columns)
@@ -385,8 +395,7 @@ static ctd_status c_fill_impl(const CscDev& X, int64_t n_cols, const CsrDev& R,
              warp_ok ? (unsigned long long)HEAVY : 1ull, heavy, nheavy);
   if (warp_ok) {
     const int nw = SPMM_THREADS / 32;
-    const size_t smem = (size_t)nw * accw * sizeof(A) + (size_t)nw * nwords * 4 +
-                        (size_t)nw * (nwords + 1) * 4;
+    const size_t smem = (size_t)nw * accw * sizeof(A);
     if (smem > 48 * 1024)
       CTD_CUDA(cudaFuncSetAttribute(k_c_fill_warp<V, A>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -395,13 +404,13 @@ static ctd_status c_fill_impl(const CscDev& X, int64_t n_cols, const CsrDev& R,
                                                            SPMM_THREADS, smem));
     if (per_sm < 1) per_sm = 1;
     CTD_LAUNCH((k_c_fill_warp<V, A>), (num_sms() * per_sm), (SPMM_THREADS), smem, st, X, n_cols,
-               R, co, ccnt, crow, cval, may_cancel, positive, work);
+               R, co, ccnt, crow, cval, positive, work);
   } else {
     CTD_CUDA(cudaMemsetAsync(ccnt, 0, n_cols * sizeof(uint32_t), st));
   }
   if (width > CTA_MODE_MAX_WIDTH)
     return fail(CTD_EINVAL, "factor wider than the supported maximum (24576 columns)");
-  const size_t smem = (size_t)accw * sizeof(A) + (size_t)nwords * 4 + (size_t)(nwords + 1) * 4;
+  const size_t smem = (size_t)accw * sizeof(A);
   if (smem > 48 * 1024)
     CTD_CUDA(cudaFuncSetAttribute(k_c_fill_block<V, A>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -410,19 +419,20 @@ static ctd_status c_fill_impl(const CscDev& X, int64_t n_cols, const CsrDev& R,
                                                          SPMM_THREADS, smem));
   if (per_sm < 1) per_sm = 1;
   CTD_LAUNCH((k_c_fill_block<V, A>), (num_sms() * per_sm), (SPMM_THREADS), smem, st, X, heavy,
-             nheavy, R, co, ccnt, crow, cval, may_cancel, work + 1);
+             nheavy, R, co, ccnt, crow, cval, work + 1);
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
 
 ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, const CsrDev& R, const uint64_t* coff,
-                         uint32_t* ccnt, int32_t* crow, void* cval, int fp32, int may_cancel,
-                         int positive, uint64_t sqnorm_X, cudaStream_t st) {
+                         uint32_t* ccnt, uint16_t* crow, void* cval, int fp32, int positive,
+                         uint64_t sqnorm_X, cudaStream_t st) {
   if (n_cols <= 0) return CTD_OK;
   if (R.width <= 0) {
     CTD_CUDA(cudaMemsetAsync(ccnt, 0, n_cols * sizeof(uint32_t), st));
     return CTD_OK;
   }
+  if (R.width > 65535) return fail(CTD_EINVAL, "too many kept fibers for 16-bit row indices");
   unsigned long long* work;
   int64_t* heavy;
   unsigned* nheavy;
@@ -435,17 +445,17 @@ ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, const CsrDev& R, const
   ctd_status rc;
   if (fp32)
     rc = small ? c_fill_impl<float, int>(X, n_cols, R, coff, ccnt, crow, static_cast<float*>(cval),
-                                         may_cancel, positive, work, heavy, nheavy, st)
+                                         positive, work, heavy, nheavy, st)
                : c_fill_impl<float, unsigned long long>(X, n_cols, R, coff, ccnt, crow,
-                                                        static_cast<float*>(cval), may_cancel,
-                                                        positive, work, heavy, nheavy, st);
+                                                        static_cast<float*>(cval), positive, work,
+                                                        heavy, nheavy, st);
   else
     rc = small ? c_fill_impl<double, int>(X, n_cols, R, coff, ccnt, crow,
-                                          static_cast<double*>(cval), may_cancel, positive, work,
-                                          heavy, nheavy, st)
+                                          static_cast<double*>(cval), positive, work, heavy,
+                                          nheavy, st)
                : c_fill_impl<double, unsigned long long>(X, n_cols, R, coff, ccnt, crow,
-                                                         static_cast<double*>(cval), may_cancel,
-                                                         positive, work, heavy, nheavy, st);
+                                                         static_cast<double*>(cval), positive,
+                                                         work, heavy, nheavy, st);
   dfree(work, st);
   dfree(heavy, st);
   dfree(nheavy, st);
@@ -488,89 +498,110 @@ void launch_sort_rows(const uint64_t* rowptr, int64_t n_rows, const int32_t* col
 // ||Q^T x_f||^2 costs nnz * s~ multiply-adds; a column with one nonzero v in
 // row i contributes v^2 ||Q(i, :)||^2, read from the precomputed row norms.
 // ---------------------------------------------------------------------------
+// One warp per (row i, 32-column chunk of Q): lane c accumulates
+// Q(i, c) = sum over row i of R of R(i, m) Z(c, m) (Z lower triangular).
 template <typename T>
 __global__ void k_build_q(CsrDev R, int64_t n_rows, const double* __restrict__ Z, int64_t ldz,
-                          int qs, T* __restrict__ Q, double* __restrict__ qn) {
+                          int qs, T* __restrict__ Q) {
   const int lane = threadIdx.x & 31;
+  const int nchunk = qs / 32;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
-  for (int64_t i = gw; i < n_rows; i += nw) {
+  for (int64_t w = gw; w < n_rows * nchunk; w += nw) {
+    const int64_t i = w / nchunk;
+    const int c = (int)(w % nchunk) * 32 + lane;
     const unsigned long long a = rp[i], b = rp[i + 1];
+    double acc = 0.0;
+    if (c < R.width)
+      for (unsigned long long q = a; q < b; ++q) {
+        const int m = R.col[q];
+        if (c >= m) acc = fma((double)R.val[q], Z[c + (int64_t)m * ldz], acc);
+      }
+    Q[i * qs + c] = (T)acc;
+  }
+}
+
+// qn[i] = ||Q(i, :)||^2 of the stored (rounded) rows
+template <typename T>
+__global__ void k_q_rownorms(const T* __restrict__ Q, int64_t n_rows, int qs,
+                             double* __restrict__ qn) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = gw; i < n_rows; i += nw) {
     double nrm = 0.0;
     for (int c = lane; c < qs; c += 32) {
-      double acc = 0.0;
-      if (c < R.width)
-        for (unsigned long long q = a; q < b; ++q) {
-          const int m = R.col[q];
-          if (c >= m) acc = fma((double)R.val[q], Z[c + (int64_t)m * ldz], acc);
-        }
-      const T tv = (T)acc;
-      Q[i * qs + c] = tv;
-      nrm = fma((double)tv, (double)tv, nrm);
+      const double v = (double)Q[i * qs + c];
+      nrm = fma(v, v, nrm);
     }
     for (int o = 16; o; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
     if (lane == 0) qn[i] = nrm;
   }
 }
 
-// One warp per column (dynamic chunks).  Hot rows of Q (slot >= 0 in
-// `slot_of`) are staged in shared memory once per block.  A column's
-// entries are loaded 32 at a time (one per lane) and broadcast by shuffles;
-// two Q rows are in flight per step.
-template <typename T, int NC>
-__device__ __forceinline__ void qrow_fma(const T* __restrict__ qrow, float v, float* acc,
-                                         double* accd, int lane, int qs) {
-#pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    const int c = lane + 32 * k;
-    if (c < qs) {
-      if (sizeof(T) == 4)
-        acc[k] = fmaf(v, (float)qrow[c], acc[k]);
-      else
-        accd[k] = fma((double)v, (double)qrow[c], accd[k]);
-    }
-  }
-}
+// One warp per column, 32 columns per grab.  Hot rows of Q (slot >= 0 in
+// `slot_of`) are staged in shared memory once per block.  Lane l owns the
+// VEC consecutive Q columns at (l + 32 k) * VEC, read with 16-byte loads;
+// a column's entries are loaded 32 at a time and broadcast by shuffles.
+// Each 32-column chunk's sum goes to partial[chunk] (fixed order inside
+// the warp), so the total does not depend on scheduling.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
 
-template <typename T, int NC>
+template <typename T, int NK>
 __global__ void __launch_bounds__(256)
     k_qform(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs,
             const double* __restrict__ qn, const short* __restrict__ slot_of,
             const int* __restrict__ hot_rows, int n_hot, int64_t n_rows,
-            unsigned long long* work, double* __restrict__ block_sums) {
-  extern __shared__ unsigned char smraw[];
+            unsigned long long* work, double* __restrict__ partial) {
+  using VT = typename Vec16<T>::type;
+  constexpr int VEC = Vec16<T>::n;
+  extern __shared__ __align__(16) unsigned char smraw[];
   T* Qs = reinterpret_cast<T*>(smraw);                                   // [n_hot][qs]
   short* slot = reinterpret_cast<short*>(smraw + (size_t)n_hot * qs * sizeof(T));  // [n_rows]
-  __shared__ double wsum[8];
   for (int64_t e = threadIdx.x; e < (int64_t)n_hot * qs; e += blockDim.x)
     Qs[e] = Q[(int64_t)hot_rows[e / qs] * qs + (e % qs)];
   for (int64_t e = threadIdx.x; e < n_rows; e += blockDim.x) slot[e] = slot_of[e];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double total = 0.0;
-  constexpr int CHUNK = 64;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(X.colptr);
   while (true) {
     unsigned long long f0 = 0;
-    if (lane == 0) f0 = atomicAdd(work, (unsigned long long)CHUNK);
+    if (lane == 0) f0 = atomicAdd(work, 32ull);
     f0 = __shfl_sync(0xffffffffu, f0, 0);
     if (f0 >= (unsigned long long)n_cols) break;
-    const int64_t f1 = min((int64_t)f0 + CHUNK, n_cols);
-    for (int64_t f = (int64_t)f0; f < f1; ++f) {
-      const unsigned long long a = X.colptr[f], b = X.colptr[f + 1];
-      if (b == a) continue;
-      if (b == a + 1) {
-        const double v = (double)X.val[a];
-        if (lane == 0) total = fma(v * v, qn[X.row[a]], total);
-        continue;
+    // lane l: column f0 + l's range; a one-nonzero column is settled here
+    const int64_t fl = (int64_t)f0 + lane;
+    unsigned long long la = 0, lb = 0;
+    double total = 0.0;
+    if (fl < n_cols) {
+      la = xp[fl];
+      lb = xp[fl + 1];
+      if (lb == la + 1) {
+        const double v = (double)X.val[la];
+        total = v * v * qn[X.row[la]];
+        lb = la;  // done
       }
-      float acc[NC];
-      double accd[NC];
+    }
+    const int nf = (int)min((int64_t)32, n_cols - (int64_t)f0);
+    for (int e = 0; e < nf; ++e) {
+      const unsigned long long a = __shfl_sync(0xffffffffu, la, e);
+      const unsigned long long b = __shfl_sync(0xffffffffu, lb, e);
+      if (b <= a) continue;
+      T acc[NK * VEC];
 #pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        acc[k] = 0.f;
-        accd[k] = 0.0;
-      }
+      for (int k = 0; k < NK * VEC; ++k) acc[k] = (T)0;
       for (unsigned long long base = a; base < b; base += 32) {
         const int cnt = (int)min((unsigned long long)32, b - base);
         const T* myrow = nullptr;
@@ -581,192 +612,54 @@ __global__ void __launch_bounds__(256)
           const int sl = slot[i];
           myrow = sl >= 0 ? Qs + (int64_t)sl * qs : Q + (int64_t)i * qs;
         }
-        int e = 0;
-        for (; e + 1 < cnt; e += 2) {
-          const T* r0 = (const T*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, e);
-          const T* r1 = (const T*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, e + 1);
-          const float v0 = (float)__shfl_sync(0xffffffffu, myv, e);
-          const float v1 = (float)__shfl_sync(0xffffffffu, myv, e + 1);
-          T q0[NC], q1[NC];
+        int q = 0;
+        for (; q + 1 < cnt; q += 2) {
+          const VT* r0 = (const VT*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, q);
+          const VT* r1 = (const VT*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, q + 1);
+          const T v0 = (T)__shfl_sync(0xffffffffu, myv, q);
+          const T v1 = (T)__shfl_sync(0xffffffffu, myv, q + 1);
+          VT a0[NK], a1[NK];
 #pragma unroll
-          for (int k = 0; k < NC; ++k) {
-            const int c = lane + 32 * k;
-            q0[k] = c < qs ? r0[c] : (T)0;
-            q1[k] = c < qs ? r1[c] : (T)0;
+          for (int k = 0; k < NK; ++k) {
+            a0[k] = r0[lane + 32 * k];
+            a1[k] = r1[lane + 32 * k];
           }
 #pragma unroll
-          for (int k = 0; k < NC; ++k) {
-            if (sizeof(T) == 4) {
-              acc[k] = fmaf(v0, (float)q0[k], acc[k]);
-              acc[k] = fmaf(v1, (float)q1[k], acc[k]);
-            } else {
-              accd[k] = fma((double)v0, (double)q0[k], accd[k]);
-              accd[k] = fma((double)v1, (double)q1[k], accd[k]);
+          for (int k = 0; k < NK; ++k) {
+            const T* x0 = reinterpret_cast<const T*>(&a0[k]);
+            const T* x1 = reinterpret_cast<const T*>(&a1[k]);
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) {
+              acc[k * VEC + u] = fma(v0, x0[u], acc[k * VEC + u]);
+              acc[k * VEC + u] = fma(v1, x1[u], acc[k * VEC + u]);
             }
           }
         }
-        if (e < cnt) {
-          const T* r0 = (const T*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, e);
-          const float v0 = (float)__shfl_sync(0xffffffffu, myv, e);
-          qrow_fma<T, NC>(r0, v0, acc, accd, lane, qs);
+        if (q < cnt) {
+          const VT* r0 = (const VT*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, q);
+          const T v0 = (T)__shfl_sync(0xffffffffu, myv, q);
+#pragma unroll
+          for (int k = 0; k < NK; ++k) {
+            const VT a0 = r0[lane + 32 * k];
+            const T* x0 = reinterpret_cast<const T*>(&a0);
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) acc[k * VEC + u] = fma(v0, x0[u], acc[k * VEC + u]);
+          }
         }
       }
       double ss = 0.0;
 #pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        const double x = sizeof(T) == 4 ? (double)acc[k] : accd[k];
-        ss = fma(x, x, ss);
-      }
+      for (int k = 0; k < NK * VEC; ++k) ss = fma((double)acc[k], (double)acc[k], ss);
       for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-      if (lane == 0) total += ss;
+      if (lane == e) total += ss;  // lane e owns column f0 + e
     }
-  }
-  if (lane == 0) wsum[warp] = total;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
-    block_sums[blockIdx.x] = t;
+    for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+    if (lane == 0) partial[f0 / 32] = total;
   }
 }
 
-__global__ void k_sum_f64_small(const double* __restrict__ in, int n, double* out);
-
-template <typename T, int NC>
-static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int qs,
-                               const double* qn, const short* slot_of, const int* hot, int n_hot,
-                               int64_t n_rows, unsigned long long* work, double* block_sums,
-                               int* nblocks, cudaStream_t st) {
-  const size_t smem = (size_t)n_hot * qs * sizeof(T) + (size_t)n_rows * sizeof(short);
-  if (smem > 48 * 1024)
-    CTD_CUDA(cudaFuncSetAttribute(k_qform<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
-  int per_sm = 0;
-  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qform<T, NC>, 256, smem));
-  if (per_sm < 1) return fail(CTD_ECUDA, "error kernel does not fit on an SM");
-  *nblocks = num_sms() * per_sm;
-  CTD_LAUNCH((k_qform<T, NC>), (*nblocks), (256), smem, st, X, n_cols, Q, qs, qn, slot_of, hot,
-             n_hot, n_rows, work, block_sums);
-  return CTD_OK;
-}
-
-ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
-                              const double* Z, int64_t ldz, const uint32_t* rowcnt_host_unused,
-                              const int* hot_rows_host, int n_hot_req, int fp32, double* out,
-                              Arena& scratch, cudaStream_t st) {
-  (void)rowcnt_host_unused;
-  CTD_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
-  if (R.width <= 0 || n_cols <= 0) return CTD_OK;
-  const int qs = (R.width + 31) & ~31;
-  const int NCmax = qs / 32;
-  if (NCmax > 32) return fail(CTD_ENOTSUP, "error kernel limited to s~ <= 1024");
-  const size_t tsz = fp32 ? 4 : 8;
-  void* Q;
-  double* qn;
-  short* slot_of;
-  int* hot;
-  unsigned long long* work;
-  double* bsums;
-  CTD_TRY(scratch.get(reinterpret_cast<unsigned char**>(&Q), (size_t)n_rows * qs * tsz));
-  CTD_TRY(scratch.get(&qn, n_rows));
-  CTD_TRY(scratch.get(&slot_of, n_rows));
-  CTD_TRY(scratch.get(&work, 1));
-  CTD_TRY(scratch.get(&bsums, 4096));
-  // hot rows: as many as fit next to the slot table in ~100 KB of shared
-  // memory, so two blocks (16 warps) stay resident per SM
-  const size_t budget = 100 * 1024;
-  const size_t table = (size_t)n_rows * sizeof(short);
-  int n_hot = 0;
-  if (table < budget) n_hot = (int)std::min<size_t>((budget - table) / ((size_t)qs * tsz), n_hot_req);
-  n_hot = std::max(n_hot, 0);
-  CTD_TRY(scratch.get(&hot, std::max(n_hot, 1)));
-  std::vector<short> slots(n_rows, (short)-1);
-  for (int q = 0; q < n_hot; ++q) slots[hot_rows_host[q]] = (short)q;
-  CTD_CUDA(cudaMemcpyAsync(slot_of, slots.data(), n_rows * sizeof(short), cudaMemcpyHostToDevice, st));
-  if (n_hot)
-    CTD_CUDA(cudaMemcpyAsync(hot, hot_rows_host, n_hot * sizeof(int), cudaMemcpyHostToDevice, st));
-  CTD_CUDA(cudaMemsetAsync(work, 0, 8, st));
-  const unsigned gq = grid_for(n_rows * 32, 256, (int64_t)num_sms() * 8);
-  if (fp32)
-    CTD_LAUNCH(k_build_q<float>, (gq), (256), 0, st, R, n_rows, Z, ldz, qs,
-               static_cast<float*>(Q), qn);
-  else
-    CTD_LAUNCH(k_build_q<double>, (gq), (256), 0, st, R, n_rows, Z, ldz, qs,
-               static_cast<double*>(Q), qn);
-  int nb = 0;
-  ctd_status rc;
-#define QF(NC)                                                                                  \
-  rc = fp32 ? qform_launch<float, NC>(X, n_cols, static_cast<const float*>(Q), qs, qn, slot_of,  \
-                                      hot, n_hot, n_rows, work, bsums, &nb, st)                  \
-            : qform_launch<double, NC>(X, n_cols, static_cast<const double*>(Q), qs, qn,         \
-                                       slot_of, hot, n_hot, n_rows, work, bsums, &nb, st)
-  if (NCmax <= 4) {
-    QF(4);
-  } else if (NCmax <= 8) {
-    QF(8);
-  } else if (NCmax <= 16) {
-    QF(16);
-  } else {
-    QF(32);
-  }
-#undef QF
-  CTD_TRY(rc);
-  if (nb > 4096) return fail(CTD_ECUDA, "too many blocks for the error reduction");
-  CTD_LAUNCH(k_sum_f64_small, (1), (1024), 0, st, bsums, nb, out);
-  CTD_CUDA(cudaGetLastError());
-  return CTD_OK;
-}
-
-__global__ void k_sum_f64_small(const double* __restrict__ in, int n, double* out) {
-  __shared__ double part[32];
-  double acc = 0.0;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) acc += in[e];
-  for (int w = 16; w; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
-    *out = t;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Quadratic form of a sparse C against U: sum_f c_f^T U c_f  (FP64).  One
-// block per column; per-column results then a fixed-order reduction, so the
-// sum does not depend on scheduling.
-// ---------------------------------------------------------------------------
-template <typename V>
-__global__ void k_quad_cols(const unsigned long long* __restrict__ coff, const unsigned* __restrict__ ccnt,
-                            const int32_t* __restrict__ crow, const V* __restrict__ cval,
-                            int64_t n_cols, const double* __restrict__ U, int64_t ldu,
-                            double* __restrict__ per_col) {
-  __shared__ double part[32];
-  for (int64_t f = blockIdx.x; f < n_cols; f += gridDim.x) {
-    const unsigned long long o = coff[f];
-    const unsigned n = ccnt[f];
-    double acc = 0.0;
-    for (unsigned p = threadIdx.x; p < n; p += blockDim.x) {
-      const int mp = crow[o + p];
-      const double vp = (double)cval[o + p];
-      const double* Ucol = U + (int64_t)mp * ldu;
-      double s = 0.0;
-      for (unsigned q = 0; q < n; ++q) s = fma((double)cval[o + q], Ucol[crow[o + q]], s);
-      acc = fma(vp, s, acc);
-    }
-    for (int w = 16; w; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
-      per_col[f] = t;
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void k_sum_f64(const double* __restrict__ in, int64_t n, double* out) {
+// fixed-order sum of n doubles (one block)
+__global__ void k_sum_f64_fixed(const double* __restrict__ in, int64_t n, double* out) {
   __shared__ double part[32];
   double acc = 0.0;
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc += in[e];
@@ -780,26 +673,96 @@ __global__ void k_sum_f64(const double* __restrict__ in, int64_t n, double* out)
   }
 }
 
-ctd_status launch_quad_form(const uint64_t* coff, const uint32_t* ccnt, const int32_t* crow,
-                            const void* cval, int fp32, int64_t n_cols, const double* U,
-                            int64_t ldu, double* out, cudaStream_t st) {
-  CTD_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
-  if (n_cols <= 0) return CTD_OK;
-  double* per_col;
-  CTD_TRY(dalloc_n(&per_col, n_cols, st));
-  const unsigned g = grid_for(n_cols, 1, (int64_t)num_sms() * 16);
-  if (fp32)
-    CTD_LAUNCH(k_quad_cols<float>, (g), (256), 0, st,
-               reinterpret_cast<const unsigned long long*>(coff), ccnt, crow,
-               static_cast<const float*>(cval), n_cols, U, ldu, per_col);
-  else
-    CTD_LAUNCH(k_quad_cols<double>, (g), (256), 0, st,
-               reinterpret_cast<const unsigned long long*>(coff), ccnt, crow,
-               static_cast<const double*>(cval), n_cols, U, ldu, per_col);
-  CTD_LAUNCH(k_sum_f64, (1), (1024), 0, st, per_col, n_cols, out);
-  CTD_CUDA(cudaGetLastError());
-  dfree(per_col, st);
+template <typename T, int NK>
+static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int qs,
+                               const double* qn, const short* slot_of, const int* hot, int n_hot,
+                               int64_t n_rows, unsigned long long* work, double* partial,
+                               cudaStream_t st) {
+  const size_t smem = (size_t)n_hot * qs * sizeof(T) + (size_t)n_rows * sizeof(short);
+  if (smem > 48 * 1024)
+    CTD_CUDA(cudaFuncSetAttribute(k_qform<T, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  int per_sm = 0;
+  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qform<T, NK>, 256, smem));
+  if (per_sm < 1) return fail(CTD_ECUDA, "error kernel does not fit on an SM");
+  CTD_LAUNCH((k_qform<T, NK>), (num_sms() * per_sm), (256), smem, st, X, n_cols, Q, qs, qn,
+             slot_of, hot, n_hot, n_rows, work, partial);
   return CTD_OK;
 }
+
+ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
+                              const double* Z, int64_t ldz, const uint32_t* rowcnt_host_unused,
+                              const int* hot_rows_host, int n_hot_req, int fp32, double* out,
+                              Arena& scratch, cudaStream_t st) {
+  (void)rowcnt_host_unused;
+  CTD_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
+  if (R.width <= 0 || n_cols <= 0) return CTD_OK;
+  const size_t tsz = fp32 ? 4 : 8;
+  const int span = 32 * (16 / (int)tsz);        // columns per 16-byte load across a warp
+  int NK = (R.width + span - 1) / span;
+  if (NK > 8) return fail(CTD_ENOTSUP, "error kernel limited to s~ <= 1024 (FP32) / 512 (FP64)");
+  NK = NK <= 1 ? 1 : NK <= 2 ? 2 : NK <= 4 ? 4 : 8;  // the kernel's compiled widths
+  const int qs = NK * span;                     // each Q row holds exactly NK loads per lane
+  void* Q;
+  double *qn, *partial;
+  short* slot_of;
+  int* hot;
+  unsigned long long* work;
+  const int64_t nchunks = (n_cols + 31) / 32;
+  CTD_TRY(scratch.get(reinterpret_cast<unsigned char**>(&Q), (size_t)n_rows * qs * tsz));
+  CTD_TRY(scratch.get(&qn, n_rows));
+  CTD_TRY(scratch.get(&slot_of, n_rows));
+  CTD_TRY(scratch.get(&work, 1));
+  CTD_TRY(scratch.get(&partial, nchunks));
+  // hot rows: as many as fit next to the slot table in ~48 KB of shared
+  // memory, so four blocks (32 warps) stay resident per SM
+  const size_t budget = 48 * 1024;
+  const size_t table = (size_t)n_rows * sizeof(short);
+  int n_hot = 0;
+  if (table < budget) n_hot = (int)std::min<size_t>((budget - table) / ((size_t)qs * tsz), n_hot_req);
+  n_hot = std::max(n_hot, 0);
+  CTD_TRY(scratch.get(&hot, std::max(n_hot, 1)));
+  std::vector<short> slots(n_rows, (short)-1);
+  for (int q = 0; q < n_hot; ++q) slots[hot_rows_host[q]] = (short)q;
+  CTD_CUDA(cudaMemcpyAsync(slot_of, slots.data(), n_rows * sizeof(short), cudaMemcpyHostToDevice, st));
+  if (n_hot)
+    CTD_CUDA(cudaMemcpyAsync(hot, hot_rows_host, n_hot * sizeof(int), cudaMemcpyHostToDevice, st));
+  CTD_CUDA(cudaMemsetAsync(work, 0, 8, st));
+  CTD_CUDA(cudaMemsetAsync(partial, 0, nchunks * sizeof(double), st));
+  const unsigned gq = grid_for(n_rows * qs, 256, (int64_t)num_sms() * 16);
+  const unsigned gn = grid_for(n_rows * 32, 256, (int64_t)num_sms() * 8);
+  if (fp32) {
+    CTD_LAUNCH(k_build_q<float>, (gq), (256), 0, st, R, n_rows, Z, ldz, qs,
+               static_cast<float*>(Q));
+    CTD_LAUNCH(k_q_rownorms<float>, (gn), (256), 0, st, static_cast<const float*>(Q), n_rows, qs,
+               qn);
+  } else {
+    CTD_LAUNCH(k_build_q<double>, (gq), (256), 0, st, R, n_rows, Z, ldz, qs,
+               static_cast<double*>(Q));
+    CTD_LAUNCH(k_q_rownorms<double>, (gn), (256), 0, st, static_cast<const double*>(Q), n_rows,
+               qs, qn);
+  }
+  ctd_status rc;
+#define QF(NKV)                                                                                  \
+  rc = fp32 ? qform_launch<float, NKV>(X, n_cols, static_cast<const float*>(Q), qs, qn, slot_of, \
+                                       hot, n_hot, n_rows, work, partial, st)                    \
+            : qform_launch<double, NKV>(X, n_cols, static_cast<const double*>(Q), qs, qn,        \
+                                        slot_of, hot, n_hot, n_rows, work, partial, st)
+  if (NK <= 1) {
+    QF(1);
+  } else if (NK <= 2) {
+    QF(2);
+  } else if (NK <= 4) {
+    QF(4);
+  } else {
+    QF(8);
+  }
+#undef QF
+  CTD_TRY(rc);
+  CTD_LAUNCH(k_sum_f64_fixed, (1), (1024), 0, st, partial, nchunks, out);
+  CTD_CUDA(cudaGetLastError());
+  return CTD_OK;
+}
+
 
 }  // namespace ctd
