@@ -51,6 +51,28 @@ def dist():
     return rank, world, local
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank decomposes its own replica of the workload with its own
+    sampling seed (weak scaling: the units are independent problems)."""
+    return rank
+
+
+def max_over_ranks(ms: float, world: int, device="cpu") -> float:
+    """The slowest rank's time; the whole job's value is counted against it."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(nnz_per_rank: int, world: int, ms_max: float) -> float:
+    """Nonzeros decomposed by all ranks per second of the slowest rank."""
+    return nnz_per_rank * world / (ms_max * 1e-3)
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -199,9 +221,10 @@ def reference_arm(args):
 def c_fill_bytes(sz, fp32: bool):
     """Algorithmic bytes of one C = R^T X launch: read X by column (row+value,
     8 B/nnz) and two column-offset arrays (8 B per column each), write C
-    (row 4 B + value 4/8 B per nonzero) and its per-column counts (4 B)."""
+    (16-bit row index + value 4/8 B per nonzero) and its per-column counts
+    (4 B)."""
     vb = 4 if fp32 else 8
-    return sz.nnz_X * 8 + 16 * (sz.n_cols + 1) + sz.nnz_C * (4 + vb) + 4 * sz.n_cols
+    return sz.nnz_X * 8 + 16 * (sz.n_cols + 1) + sz.nnz_C * (2 + vb) + 4 * sz.n_cols
 
 
 def ours(args):
@@ -219,7 +242,7 @@ def ours(args):
     nnz_step = coo.nnz
     X = ctd.Coo.from_synth(coo)
     st = torch.cuda.current_stream()
-    seed = rank
+    seed = rank_seed(rank)
 
     def barrier():
         if world > 1:
@@ -256,13 +279,8 @@ def ours(args):
     ms = e0.elapsed_time(e1) / args.steps
     rep = ctd.profile_report()
     ctd.profile(False)
-    t_max = ms
-    if world > 1:
-        import torch.distributed as td
-        t = torch.tensor([ms], device="cuda")
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = nnz_step * world / (t_max * 1e-3)
+    t_max = max_over_ranks(ms, world, device="cuda")
+    value = whole_job_value(nnz_step, world, t_max)
 
     # live roofline of the dominant kernel (C = R^T X)
     peak, peak_kind = measured_peaks()

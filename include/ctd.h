@@ -118,6 +118,22 @@ CTD_API ctd_status ctd_static(const ctd_coo3* X, int alpha, int64_t s, double ep
                       void* stream, ctd_factors** out);
 
 /*
+ * ctd_static_batched -- CTD-S (Algorithm 1) on n independent tensors, each
+ * exactly as ctd_static(&X[t], alpha, s[t], eps, seeds[t], precision, flags)
+ * would decompose it.  The per-tensor pipelines run concurrently on
+ * `workers` library-owned streams (0: 8), largest tensors first, so the
+ * host read-backs of one tensor's data-dependent sizes overlap the kernels
+ * of the others.  The work is ordered after `stream` and `stream` after
+ * the work, as for one launch; the call returns when every tensor is done.
+ * out[t] receives tensor t's factors.  On any failure every out[t] is
+ * freed and NULL, and the first failing tensor's status is returned.
+ */
+CTD_API ctd_status ctd_static_batched(int n, const ctd_coo3* X, int alpha, const int64_t* s,
+                                      const uint64_t* seeds, double eps, int precision,
+                                      unsigned flags, int workers, void* stream,
+                                      ctd_factors** out);
+
+/*
  * ctd_dynamic_create -- empty CTD-D state for slices of size
  * dims2[0] x dims2[1] x 1 (Algorithm 2 with alpha in {1, 2}; the time mode
  * is the third).  `stream_id` selects an independent Philox counter space
@@ -144,6 +160,32 @@ CTD_API ctd_status ctd_dynamic_create(const int64_t dims2[2], int alpha, int pre
  */
 CTD_API ctd_status ctd_dynamic_step(ctd_factors* state, const ctd_coo3* dX, int64_t d,
                             double eps, void* stream);
+
+/*
+ * Serving loop for CTD-D with continuous batching (no counterpart in the
+ * paper beyond Algorithm 2 itself).  A server holds one CTD-D state per
+ * stream (stream k uses Philox counter space k), resident on the device.
+ * ctd_server_submit queues one slice for one stream; slices of a stream are
+ * applied in submission order, slices of different streams run
+ * concurrently on `workers` internal CUDA streams (0: 8), each admitted as
+ * soon as a worker is free, its stream idle, and the device's free memory
+ * (times mem_fraction, less the estimates of running steps) covers its
+ * estimate.  dX must stay valid until the request has completed
+ * (ctd_server_wait).  ctd_server_result gives {queued, running, total} ms
+ * per request.  ctd_server_state lends a stream's state to the getters
+ * (do not free it; call after ctd_server_wait).
+ */
+typedef struct ctd_server ctd_server;
+CTD_API ctd_status ctd_server_create(int n_streams, const int64_t dims2[2], int alpha,
+                                     int precision, uint64_t seed, int64_t d, double eps,
+                                     int workers, double mem_fraction, ctd_server** out);
+CTD_API ctd_status ctd_server_submit(ctd_server* S, int stream_id, const ctd_coo3* dX,
+                                     int64_t* ticket);
+/* Wait for one request (ticket >= 0) or for all submitted so far (ticket < 0). */
+CTD_API ctd_status ctd_server_wait(ctd_server* S, int64_t ticket);
+CTD_API ctd_status ctd_server_result(ctd_server* S, int64_t ticket, int* status, double ms[3]);
+CTD_API ctd_status ctd_server_state(ctd_server* S, int stream_id, ctd_factors** state);
+CTD_API void ctd_server_free(ctd_server* S);
 
 /* ctd_error -- relative error of Eq. (error), ||X~ - X||_F^2 / ||X||_F^2
  * (the squared ratio), for the tensor the factors were computed from

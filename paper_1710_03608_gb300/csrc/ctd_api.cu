@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <set>
 #include <numeric>
 
 #include "ctd_internal.cuh"
@@ -67,6 +68,20 @@ static void init_pool_once() {
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
   });
+}
+
+ctd_status allow_max_smem(const void* fn) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  CTD_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({dev, fn})) return CTD_OK;
+  int optin = 0;
+  CTD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  CTD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  done.insert({dev, fn});
+  return CTD_OK;
 }
 
 ctd_status dalloc(void** p, size_t bytes, cudaStream_t st) {

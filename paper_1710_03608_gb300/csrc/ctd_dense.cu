@@ -256,7 +256,8 @@ __device__ bool grid_sync(const GridBar& gb) {
 
 __global__ void __launch_bounds__(256)
     k_chol_coop(double* __restrict__ A, int64_t n, int64_t lda, const double* __restrict__ thr,
-                const int* __restrict__ force, int* __restrict__ keep, double* __restrict__ piv,
+                const int* __restrict__ force, const double* __restrict__ fpiv,
+                int* __restrict__ keep, double* __restrict__ piv,
                 unsigned* __restrict__ status, GridBar gb) {
   __shared__ double D[NB][NB + 1];
   __shared__ double Pc[NB][NB + 1];
@@ -264,6 +265,7 @@ __global__ void __launch_bounds__(256)
   __shared__ int kp[NB];
   __shared__ double thr_s[NB], piv_s[NB];
   __shared__ int force_s[NB];
+  __shared__ double fpiv_s[NB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
     const int nb = (int)min((int64_t)NB, n - k0);
@@ -277,13 +279,17 @@ __global__ void __launch_bounds__(256)
       if (tid < nb) {
         thr_s[tid] = thr[k0 + tid];
         force_s[tid] = force ? force[k0 + tid] : -1;
+        fpiv_s[tid] = fpiv ? fpiv[k0 + tid] : 0.0;
       }
       __syncthreads();
       for (int c = 0; c < nb; ++c) {
         if (tid == 0) {
-          const double d = D[c][c];
+          double d = D[c][c];
           int k = (d > thr_s[c] && d > 0.0) ? 1 : 0;
           if (force_s[c] >= 0) k = force_s[c];
+          // a keep forced by the explicit residual takes that residual's
+          // squared norm as its pivot (the Gram-based one lost it to rounding)
+          if (force_s[c] == 1 && fpiv_s[c] > 0.0) d = fpiv_s[c];
           if (k && !(d > 0.0)) {
             atomicOr(status, DEV_CAPACITY);
             k = 0;
@@ -327,6 +333,7 @@ __global__ void __launch_bounds__(256)
       const int r = e % NB, c = e / NB;
       D[r][c] = (r < nb && c <= r) ? A[(k0 + r) + (k0 + c) * lda] : 0.0;
     }
+    __syncthreads();  // D's diagonal is read below by other threads than wrote it
     if (tid < NB) {
       kp[tid] = tid < nb ? keep[k0 + tid] : 0;
       invd[tid] = (tid < nb && kp[tid]) ? 1.0 / D[tid][tid] : 0.0;
@@ -382,7 +389,8 @@ __global__ void __launch_bounds__(256)
 }
 
 void launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr, int* keep,
-                      cudaStream_t st, const int* force, double* piv, unsigned* status) {
+                      cudaStream_t st, const int* force, double* piv, unsigned* status,
+                      const double* fpiv) {
   if (n <= 0) return;
   // barrier words live in the status array's tail: status[1] count, status[2] generation
   GridBar gb{status + 1, status + 2, status};
@@ -391,8 +399,8 @@ void launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr, int*
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_coop, 256, 0);
   const int nblocks = num_sms() * (per_sm > 0 ? 1 : 0);
   if (nblocks <= 0) return;
-  void* args[] = {&A, &n, &lda, const_cast<double**>(&thr), const_cast<int**>(&force), &keep,
-                  &piv, &status, &gb};
+  void* args[] = {&A, &n, &lda, const_cast<double**>(&thr), const_cast<int**>(&force),
+                  const_cast<double**>(&fpiv), &keep, &piv, &status, &gb};
   note_launch();
   cudaLaunchCooperativeKernel((const void*)k_chol_coop, dim3(nblocks), dim3(256), args, 0, st);
 }

@@ -22,8 +22,8 @@
 // The error of the old columns does not change (their reconstruction
 // R^(t+1) U^(t+1) [C; M C] equals R^(t) U^(t) C), so the relative error
 // accumulates ||dX||^2 - ||P_{t+1} dX||^2 per step, with
-// ||P_{t+1} dX||^2 = ||L^{-1} C_new||_F^2 over the new columns C_new (the
-// same as sum_f c_f^T U^(t+1) c_f, but backward stable).
+// ||P_{t+1} dX||^2 = ||Q^T dX||_F^2 with an orthonormal basis Q of
+// range(R^(t+1)) kept across steps (the same as sum_f c_f^T U^(t+1) c_f).
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -94,6 +94,32 @@ __global__ void k_sumsq(const double* __restrict__ A, int64_t n, double* __restr
   }
 }
 
+// V(:, c) = candidate column idx[c] (dense n_rows x n, V zeroed beforehand)
+__global__ void k_densify_cols(const unsigned long long* __restrict__ cptr,
+                               const int32_t* __restrict__ crow, const int32_t* __restrict__ cval,
+                               const int* __restrict__ idx, int n, double* __restrict__ V,
+                               int64_t ldv) {
+  for (int c = blockIdx.x; c < n; c += gridDim.x) {
+    const int k = idx[c];
+    for (unsigned long long p = cptr[k] + threadIdx.x; p < cptr[k + 1]; p += blockDim.x)
+      V[crow[p] + (int64_t)c * ldv] = (double)cval[p];
+  }
+}
+
+// qn[i] += sum_c Qt(d0 + c, i)^2 for the n new rows of Q^T
+__global__ void k_qn_add(const double* __restrict__ Qt, int64_t ld, int64_t d0, int n,
+                         int64_t n_rows, double* __restrict__ qn) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = qn[i];
+    for (int c = 0; c < n; ++c) {
+      const double q = Qt[d0 + c + i * ld];
+      s = fma(q, q, s);
+    }
+    qn[i] = s;
+  }
+}
+
 __global__ void k_add_offset(const unsigned long long* __restrict__ in, int64_t n,
                              unsigned long long off, unsigned long long* __restrict__ out) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -135,7 +161,11 @@ ctd_factors::~ctd_factors() {
     dfree(dyn->lastIu, stream);
     dfree(U, stream);
     dfree(L, stream);
+    dfree(Qt, stream);
+    dfree(qn, stream);
     L = nullptr;
+    Qt = nullptr;
+    qn = nullptr;
     dfree(Rcolptr, stream);
     dfree(Rrow, stream);
     dfree(Rval, stream);
@@ -175,6 +205,9 @@ extern "C" ctd_status ctd_dynamic_create(const int64_t dims2[2], int alpha, int 
   ctd_status rc = dalloc_n(&F->dyn->lastI, 8192, nullptr);
   if (rc == CTD_OK) rc = dalloc_n(&F->dyn->lastIu, 8192, nullptr);
   if (rc == CTD_OK) rc = dalloc_n(&F->Rcolptr, 1, nullptr);
+  if (rc == CTD_OK) rc = dalloc_n(&F->qn, F->n_rows, nullptr);
+  if (rc == CTD_OK && cudaMemsetAsync(F->qn, 0, F->n_rows * 8, nullptr) != cudaSuccess)
+    rc = fail(CTD_ECUDA, "memset failed");
   if (rc == CTD_OK && cudaMemsetAsync(F->Rcolptr, 0, 8, nullptr) != cudaSuccess)
     rc = fail(CTD_ECUDA, "memset failed");
   if (rc == CTD_OK && cudaStreamSynchronize(nullptr) != cudaSuccess)
@@ -187,26 +220,98 @@ extern "C" ctd_status ctd_dynamic_create(const int64_t dims2[2], int alpha, int 
   return CTD_OK;
 }
 
-// grow U and L (ld cap) to hold n x n, keeping the leading d x d blocks
+// grow U, L and Q^T (ld cap, a multiple of 512) to hold n kept fibers,
+// keeping the first d
 static ctd_status grow_U(ctd_factors* F, int64_t d, int64_t n, cudaStream_t st) {
   auto& D = *F->dyn;
   if (n <= D.cap_d) return CTD_OK;
-  int64_t cap = std::max<int64_t>(std::max<int64_t>(2 * D.cap_d, n), 256);
-  double *U2, *L2;
+  int64_t cap = std::max<int64_t>(std::max<int64_t>(2 * D.cap_d, n), 512);
+  cap = (cap + 511) / 512 * 512;
+  const int64_t rows = F->n_rows;
+  double *U2, *L2, *Q2;
   CTD_TRY(dalloc_n(&U2, (size_t)cap * cap, st));
   CTD_TRY(dalloc_n(&L2, (size_t)cap * cap, st));
+  CTD_TRY(dalloc_n(&Q2, (size_t)cap * rows, st));
   CTD_CUDA(cudaMemsetAsync(L2, 0, (size_t)cap * cap * 8, st));
+  CTD_CUDA(cudaMemsetAsync(Q2, 0, (size_t)cap * rows * 8, st));
   if (d > 0) {
     CTD_CUDA(cudaMemcpy2DAsync(U2, cap * 8, F->U, D.cap_d * 8, d * 8, d,
                                cudaMemcpyDeviceToDevice, st));
     CTD_CUDA(cudaMemcpy2DAsync(L2, cap * 8, F->L, D.cap_d * 8, d * 8, d,
                                cudaMemcpyDeviceToDevice, st));
+    CTD_CUDA(cudaMemcpy2DAsync(Q2, cap * 8, F->Qt, D.cap_d * 8, d * 8, rows,
+                               cudaMemcpyDeviceToDevice, st));
   }
   dfree(F->U, st);
   dfree(F->L, st);
+  dfree(F->Qt, st);
   F->U = U2;
   F->L = L2;
+  F->Qt = Q2;
   D.cap_d = cap;
+  return CTD_OK;
+}
+
+// column c of V (m x n, ld m) scaled to unit norm (zero columns stay zero)
+__global__ void k_unit_columns(double* __restrict__ V, int64_t m, int n) {
+  __shared__ double part[32];
+  __shared__ double scale;
+  for (int c = blockIdx.x; c < n; c += gridDim.x) {
+    double* v = V + (int64_t)c * m;
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) acc = fma(v[i], v[i], acc);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+      scale = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+    }
+    __syncthreads();
+    const double sc = scale;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) v[i] *= sc;
+    __syncthreads();
+  }
+}
+
+__global__ void k_add_diag(double* __restrict__ A, int64_t lda, int n, double x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    A[i + (int64_t)i * lda] += x;
+}
+
+// One Cholesky-QR pass: L L^T = V^T V + shift I, out = V L^{-T}.  *ok is
+// false if a pivot was not positive (V numerically rank deficient).
+static ctd_status cholqr_pass(const double* V, int64_t m, int n, double shift, double* out,
+                              Arena& scratch, cudaStream_t st, bool* ok) {
+  double *G, *L, *Li, *thr;
+  int *keep, *idx;
+  unsigned* status;
+  CTD_TRY(scratch.get(&G, (size_t)n * n));
+  CTD_TRY(scratch.get(&L, (size_t)n * n));
+  CTD_TRY(scratch.get(&Li, (size_t)n * n));
+  CTD_TRY(scratch.get(&thr, n));
+  CTD_TRY(scratch.get(&keep, n));
+  CTD_TRY(scratch.get(&idx, n + 1));
+  CTD_TRY(scratch.get(&status, 4));
+  dgemm(true, false, n, n, m, 1.0, V, m, V, m, 0.0, G, n, st);
+  if (shift > 0.0) CTD_LAUNCH(k_add_diag, (grid_for(n, 256, 64)), (256), 0, st, G, n, n, shift);
+  CTD_CUDA(cudaMemsetAsync(thr, 0, (size_t)n * 8, st));
+  CTD_CUDA(cudaMemsetAsync(status, 0, 4 * sizeof(unsigned), st));
+  launch_chol_skip(G, n, n, thr, keep, st, nullptr, nullptr, status);
+  launch_compact_flags(keep, n, idx, idx + n, st);
+  int nk = 0;
+  unsigned h_status = 0;
+  CTD_TRY(d2h(&nk, idx + n, 1, st));
+  CTD_TRY(d2h(&h_status, status, 1, st));
+  CTD_CUDA(cudaGetLastError());
+  CTD_TRY(sync(st));
+  if (h_status & DEV_TIMEOUT) return fail(CTD_ETIMEOUT, "skip-Cholesky grid barrier gave up");
+  *ok = nk == n;
+  if (!*ok) return CTD_OK;
+  launch_gather_lower(G, n, idx, idx + n, n, L, n, st);
+  tri_inverse(L, n, n, Li, n, st);
+  dgemm(false, true, m, n, n, 1.0, V, m, Li, n, 0.0, out, m, st);
   return CTD_OK;
 }
 
@@ -278,9 +383,14 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   int kept = 0;
   int* idx = nullptr;
   FilterOut fo;
+  const uint64_t* rc_ptr_k = nullptr;  // the candidates as CSC
+  const int32_t* rc_row_k = nullptr;
+  const int32_t* rc_val_k = nullptr;
   double* Bm = nullptr;   // R^(t)^T X_c
   double* W = nullptr;    // L^{-1} R^(t)^T X_c
-  if (du > 0) {
+  // R^(t) already spans every mode-alpha vector (d~_t = I_alpha independent
+  // columns): every candidate's residual is exactly zero, so none is kept.
+  if (du > 0 && dt < M.n_rows) {
     // candidates X_c (CSC and by row)
     uint64_t *rc_sizes, *rc_ptr, *rcr_ptr;
     CTD_TRY(scratch.get(&rc_sizes, du + 1));
@@ -339,6 +449,9 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
       fi.rval = F->Rval;
     }
     CTD_TRY(run_filter(fi, fo, scratch, st));
+    rc_ptr_k = rc_ptr;
+    rc_row_k = rc_row;
+    rc_val_k = rc_val;
     kept = fo.kept;
     idx = fo.idx;
     rec.d_kept = kept;
@@ -346,6 +459,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
     if (kept > 0) {
       PhaseScope ph("d_update_u", st);
       const int64_t dn = dt + kept;
+      double* WKs = nullptr;  // W restricted to the kept candidates (dt x kept)
       double* L = fo.Lk;   // factor of the kept block of S
       double* Li = fo.Li;  // its inverse
       double* Sinv;
@@ -358,6 +472,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
         double *BK, *WK, *Z;
         CTD_TRY(scratch.get(&BK, (size_t)dt * kept));
         CTD_TRY(scratch.get(&WK, (size_t)dt * kept));
+        WKs = WK;
         CTD_TRY(scratch.get(&Z, (size_t)dt * kept));
         CTD_TRY(dalloc_n(&rec.M, (size_t)dt * kept, st));
         const unsigned gk = grid_for(dt * kept, 256, (int64_t)num_sms() * 8);
@@ -375,6 +490,49 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
       }
       CTD_CUDA(cudaMemcpy2DAsync(F->L + dt + dt * ld, ld * 8, L, kept * 8, kept * 8, kept,
                                  cudaMemcpyDeviceToDevice, st));
+      // Q^(t+1) = [Q^(t), Q_new]: the kept candidates' residuals against
+      // range(Q^(t)) (Gram-Schmidt twice), normalized by L_S^{-T} and then
+      // once more by a Cholesky of their Gram matrix (orthonormal to rounding)
+      {
+        const int64_t nr = M.n_rows;
+        double *V, *V2, *Vq;
+        CTD_TRY(scratch.get(&V, (size_t)nr * kept));
+        CTD_TRY(scratch.get(&V2, (size_t)nr * kept));
+        CTD_TRY(scratch.get(&Vq, (size_t)nr * kept));
+        CTD_CUDA(cudaMemsetAsync(V, 0, (size_t)nr * kept * 8, st));
+        CTD_LAUNCH(k_densify_cols, ((unsigned)std::min(kept, 4096)), (128), 0, st,
+                   reinterpret_cast<const unsigned long long*>(rc_ptr_k), rc_row_k, rc_val_k, idx,
+                   kept, V, nr);
+        if (dt > 0) {
+          double* Hm;
+          CTD_TRY(scratch.get(&Hm, (size_t)dt * kept));
+          dgemm(true, false, nr, kept, dt, -1.0, F->Qt, ld, WKs, dt, 1.0, V, nr, st);
+          dgemm(false, false, dt, kept, nr, 1.0, F->Qt, ld, V, nr, 0.0, Hm, dt, st);
+          dgemm(true, false, nr, kept, dt, -1.0, F->Qt, ld, Hm, dt, 1.0, V, nr, st);
+        }
+        // V2 = V L_S^{-T} is orthonormal up to the filter's rounding; one
+        // Cholesky-QR pass makes it so to working precision.  If that pass
+        // meets a non-positive pivot (V2 too far from orthonormal), the
+        // residuals are orthonormalized from scratch: unit columns, one
+        // shifted Cholesky-QR pass, then two plain ones (Fukaya et al.,
+        // SIAM J. Sci. Comput. 42(1), 2020).
+        dgemm(false, true, nr, kept, kept, 1.0, V, nr, Li, kept, 0.0, V2, nr, st);
+        bool ok = false;
+        CTD_TRY(cholqr_pass(V2, nr, kept, 0.0, Vq, scratch, st, &ok));
+        if (!ok) {
+          CTD_LAUNCH(k_unit_columns, ((unsigned)std::min(kept, 4096)), (256), 0, st, V, nr, kept);
+          const double u = 1.1102230246251565e-16;
+          const double shift = 11.0 * ((double)nr * kept + (double)kept * (kept + 1)) * u * kept;
+          CTD_TRY(cholqr_pass(V, nr, kept, shift, V2, scratch, st, &ok));
+          if (ok) CTD_TRY(cholqr_pass(V2, nr, kept, 0.0, V, scratch, st, &ok));
+          if (ok) CTD_TRY(cholqr_pass(V, nr, kept, 0.0, Vq, scratch, st, &ok));
+          if (!ok) return fail(CTD_ENOTSUP, "new basis vectors are numerically dependent");
+        }
+        CTD_LAUNCH(k_transpose_f64, (grid_for(nr * kept, 256, (int64_t)num_sms() * 8)), (256), 0,
+                   st, Vq, nr, nr, kept, F->Qt + dt, ld);
+        CTD_LAUNCH(k_qn_add, (grid_for(nr, 256, (int64_t)num_sms() * 4)), (256), 0, st, F->Qt, ld,
+                   dt, kept, nr, F->qn);
+      }
       CTD_CUDA(cudaMemcpy2DAsync(F->U + dt + dt * ld, ld * 8, Sinv, kept * 8, kept * 8, kept,
                                  cudaMemcpyDeviceToDevice, st));
       // append dR to R (CSC), then rebuild the by-row copy
@@ -451,21 +609,10 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
     CTD_TRY(scratch.get(&d_pu, 1));
     CTD_TRY(scratch.get(&d_nnzc, 1));
     {
-      // ||P_{t+1} dX||^2 = ||L^{-1} R^(t+1)^T dX||_F^2, by forward substitution
+      // ||P_{t+1} dX||^2 = ||Q^(t+1)^T dX||_F^2 with the maintained basis Q
       PhaseScope ph("d_error", st);
-      double* Cd;
-      CTD_TRY(scratch.get(&Cd, (size_t)dn * M.n_cols));
-      CTD_CUDA(cudaMemsetAsync(Cd, 0, (size_t)dn * M.n_cols * 8, st));
-      const unsigned g = grid_for(M.n_cols, 1, (int64_t)num_sms() * 16);
-      const auto* co = reinterpret_cast<const unsigned long long*>(rec.Coff);
-      if (fp32)
-        CTD_LAUNCH(k_densify<float>, (g), (128), 0, st, co, rec.Ccnt, rec.Crow,
-                   static_cast<const float*>(rec.Cval), M.n_cols, Cd, dn);
-      else
-        CTD_LAUNCH(k_densify<double>, (g), (128), 0, st, co, rec.Ccnt, rec.Crow,
-                   static_cast<const double*>(rec.Cval), M.n_cols, Cd, dn);
-      tri_solve_lower(F->L, D.cap_d, dn, Cd, dn, M.n_cols, st);
-      CTD_LAUNCH(k_sumsq, (1), (1024), 0, st, Cd, dn * M.n_cols, d_pu);
+      CTD_TRY(launch_qform_rows(M.csc(), M.n_cols, F->Qt, D.cap_d, dn, F->qn, M.n_rows, d_pu,
+                                scratch, st));
     }
     launch_sum_u32(rec.Ccnt, M.n_cols, d_nnzc, st);
     uint64_t nnzc = 0;

@@ -147,7 +147,7 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
   const int du = in.du;
   out.kept = 0;
   if (du <= 0) return CTD_OK;
-  double *S0, *thr, *xn2, *piv;
+  double *S0, *thr, *xn2, *piv, *fpiv;
   int* force;
   int*& count = out.count;
   unsigned* status;
@@ -156,6 +156,7 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
   CTD_TRY(scratch.get(&xn2, du));
   CTD_TRY(scratch.get(&piv, du));
   CTD_TRY(scratch.get(&force, du));
+  CTD_TRY(scratch.get(&fpiv, du));
   CTD_TRY(scratch.get(&count, 1));
   CTD_TRY(scratch.get(&status, 4));
   CTD_TRY(scratch.get(&out.keep, du));
@@ -166,17 +167,20 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
   CTD_CUDA(cudaMemsetAsync(force, 0xff, (size_t)du * sizeof(int), st));  // -1
   CTD_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
   std::vector<int> h_force(du, -1), h_keep(du);
-  std::vector<double> h_piv(du), h_xn(du);
+  std::vector<double> h_piv(du), h_xn(du), h_fpiv(du, 0.0);
   CTD_TRY(d2h(h_xn.data(), xn2, du, st));
   for (int iter = 0; iter <= du + 1; ++iter) {
     if (iter > 0) {
       CTD_CUDA(cudaMemcpyAsync(in.S, S0, (size_t)du * du * 8, cudaMemcpyDeviceToDevice, st));
       CTD_CUDA(cudaMemcpyAsync(force, h_force.data(), (size_t)du * sizeof(int),
                                cudaMemcpyHostToDevice, st));
+      CTD_CUDA(cudaMemcpyAsync(fpiv, h_fpiv.data(), (size_t)du * sizeof(double),
+                               cudaMemcpyHostToDevice, st));
     }
     {
       PhaseScope ph("filter_chol", st);
-      launch_chol_skip(in.S, du, du, thr, out.keep, st, force, piv, status);
+      launch_chol_skip(in.S, du, du, thr, out.keep, st, force, piv, status,
+                       iter > 0 ? fpiv : nullptr);
       launch_compact_flags(out.keep, du, out.idx, count, st);
     }
     unsigned h_status = 0;
@@ -286,6 +290,7 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
       const int explicit_keep = h_ratio[c] > in.eps ? 1 : 0;  // equality: dependent (A4)
       if (explicit_keep != h_keep[k]) {
         h_force[k] = explicit_keep;
+        h_fpiv[k] = h_ratio[c] * h_ratio[c] * h_xn[k];
         changed = true;
       }
     }

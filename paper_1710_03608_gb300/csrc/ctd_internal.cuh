@@ -92,6 +92,12 @@ struct Arena {
   ~Arena() { release(); }
 };
 
+// Let `fn` use up to the device's opt-in shared memory per block.  Set once
+// per kernel and device, under a lock: each call site used to set the limit
+// to its own need, so concurrent host threads could lower it under another's
+// launch.  A higher limit does not change launches that ask for less.
+ctd_status allow_max_smem(const void* fn);
+
 inline int num_sms() {
   static int n = 0;
   if (!n) {
@@ -231,6 +237,12 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
                               const int* hot_rows_host, int n_hot, int fp32, double* out,
                               Arena& scratch, cudaStream_t st);
 
+// ||Q^T X_(alpha)||_F^2 for FP64 Q by rows (row i at Q + i * ld, ld a
+// multiple of 512, zero past `width`), with row norms qn.
+ctd_status launch_qform_rows(const CscDev& X, int64_t n_cols, const double* Q, int64_t ld,
+                             int64_t width, const double* qn, int64_t n_rows, double* out,
+                             Arena& scratch, cudaStream_t st);
+
 // ctd_dense.cu -------------------------------------------------------------
 // C = alpha op(A) op(B) + beta C, column-major FP64.
 void dgemm(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
@@ -240,13 +252,16 @@ void dgemm(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, cons
 // (column-major, lower triangle used).  Column k is kept iff its Schur
 // diagonal exceeds thr[k].  Kept columns hold L, skipped ones are zeroed.
 // keep[k] in {0,1}.
-// force (optional): -1 decide by pivot, 0 skip, 1 keep.  piv (optional)
+// force (optional): -1 decide by pivot, 0 skip, 1 keep.  fpiv (optional):
+// for a forced keep with fpiv[k] > 0, the pivot used in place of the Schur
+// diagonal (the explicit residual's squared norm).  piv (optional)
 // receives each column's pivot before its decision; a forced keep without a
 // positive pivot sets DEV_CAPACITY in status[0]; a grid barrier that gives
 // up sets DEV_TIMEOUT.  status must hold 3 words (status[1..2] are the grid
 // barrier's counter and generation).
 void launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr, int* keep,
-                      cudaStream_t st, const int* force, double* piv, unsigned* status);
+                      cudaStream_t st, const int* force, double* piv, unsigned* status,
+                      const double* fpiv = nullptr);
 // B <- L^{-T} B for lower-triangular L, by backward substitution.
 void tri_solve_lower_T(const double* L, int64_t ldl, int64_t n, double* B, int64_t ldb,
                        int64_t nrhs, cudaStream_t st);
@@ -367,6 +382,9 @@ struct ctd_factors {
   int32_t* Rcval = nullptr;
   double* U = nullptr;           // s~ x s~ column-major (symmetric)
   double* L = nullptr;           // CTD-D: Cholesky factor of R^T R (lower, ld as U)
+  double* Qt = nullptr;          // CTD-D: Q^T, Q an orthonormal basis of range(R); row i of Q
+                                 // at Qt + i * ld (ld as U), zero past the kept count
+  double* qn = nullptr;          // CTD-D: ||Q(i, :)||^2 per row
   uint64_t* Coff = nullptr;      // [n_cols+1]
   uint32_t* Ccnt = nullptr;      // [n_cols]
   uint16_t* Crow = nullptr;

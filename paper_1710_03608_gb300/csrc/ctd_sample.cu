@@ -143,7 +143,7 @@ void launch_sort_unique(const int64_t* in, int64_t s, int64_t* out, int* count, 
   while (npow2 < s) npow2 <<= 1;
   const size_t smem = (size_t)npow2 * sizeof(unsigned long long);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_sort_unique, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem((const void*)k_sort_unique);
   CTD_LAUNCH(k_sort_unique, (1), (SU_THREADS), smem, st, in, s, out, count);
 }
 

@@ -1,0 +1,236 @@
+// Serving loop for CTD-D (Algorithm 2) with continuous batching.
+//
+// A server owns one CTD-D state per stream (kept on the device for the
+// server's life).  Requests -- one new slice for one stream -- are queued
+// per stream and run in submission order within a stream.  `workers` host
+// threads, each with its own CUDA stream, take the oldest waiting request
+// whose stream is idle, as soon as a worker frees up: steps of different
+// streams overlap on the device, and a request that arrives while others
+// run is admitted without waiting for a batch boundary.  Admission also
+// checks device memory: a step starts only if the free memory, less the
+// estimates of the steps already running, covers its own estimate (at
+// least one step always runs, so the queue cannot stall).
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "ctd_internal.cuh"
+
+using namespace ctd;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  int stream = 0;
+  ctd_coo3 X{};
+  Clock::time_point t_submit, t_start, t_done;
+  size_t estimate = 0;
+  ctd_status rc = CTD_OK;
+  bool done = false;
+  std::string msg;
+};
+
+}  // namespace
+
+struct ctd_server {
+  int n_streams = 0;
+  int64_t d = 0;
+  double eps = 0.0;
+  double mem_fraction = 0.9;
+  int dev = 0;
+  std::vector<ctd_factors*> states;
+  std::vector<std::deque<int64_t>> queue;   // tickets per stream
+  std::vector<char> busy;
+  std::vector<Request> req;                  // by ticket
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  size_t running_bytes = 0;
+  int running = 0;
+  std::vector<std::thread> pool;
+  std::vector<cudaStream_t> cstream;
+};
+
+namespace {
+
+size_t step_estimate(const ctd_factors* F, const ctd_coo3& X, int64_t d) {
+  const double dt = (double)F->s_kept + (double)d;
+  // COO staging + CSC + CDF (~64 B/nnz), candidates' Gram/Schur/W (FP64),
+  // U/L growth, the new-column block (bounded by nnz * d~ / 8 B on average)
+  return (size_t)(64.0 * X.nnz + 8.0 * (double)F->n_cols * 6.0 + 24.0 * dt * d +
+                  16.0 * dt * dt * 0.25 + 12.0 * (double)X.nnz * 16.0);
+}
+
+void worker(ctd_server* S, int w) {
+  cudaSetDevice(S->dev);
+  while (true) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    int64_t ticket = -1;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      while (true) {
+        if (S->stop) return;
+        // oldest waiting request on an idle stream that fits in memory
+        int64_t best = -1;
+        for (int s = 0; s < S->n_streams; ++s) {
+          if (S->busy[s] || S->queue[s].empty()) continue;
+          const int64_t t = S->queue[s].front();
+          if (best < 0 || t < best) best = t;
+        }
+        if (best >= 0) {
+          Request& r = S->req[best];
+          const size_t avail = (size_t)((double)free_b * S->mem_fraction);
+          const bool fits = S->running == 0 || S->running_bytes + r.estimate <= avail;
+          if (fits) {
+            ticket = best;
+            S->busy[r.stream] = 1;
+            S->queue[r.stream].pop_front();
+            S->running_bytes += r.estimate;
+            S->running += 1;
+            break;
+          }
+        }
+        S->cv.wait_for(lk, std::chrono::milliseconds(2));
+        lk.unlock();
+        cudaMemGetInfo(&free_b, &total_b);
+        lk.lock();
+      }
+    }
+    Request& r = S->req[ticket];
+    r.t_start = Clock::now();
+    r.rc = ctd_dynamic_step(S->states[r.stream], &r.X, S->d, S->eps, S->cstream[w]);
+    if (r.rc != CTD_OK) r.msg = ctd_last_error();
+    r.t_done = Clock::now();
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      r.done = true;
+      S->busy[r.stream] = 0;
+      S->running_bytes -= r.estimate;
+      S->running -= 1;
+    }
+    S->cv.notify_all();
+  }
+}
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+}  // namespace
+
+extern "C" ctd_status ctd_server_create(int n_streams, const int64_t dims2[2], int alpha,
+                                        int precision, uint64_t seed, int64_t d, double eps,
+                                        int workers, double mem_fraction, ctd_server** out) {
+  if (!out || !dims2) return fail(CTD_EINVAL, "NULL argument");
+  if (n_streams < 1 || n_streams > 65536) return fail(CTD_EINVAL, "n_streams out of range");
+  if (d < 1 || d > 8192) return fail(CTD_EINVAL, "d must be in [1, 8192]");
+  if (!(eps >= 0.0 && eps < 1.0)) return fail(CTD_EINVAL, "eps must be in [0, 1)");
+  if (workers <= 0) workers = 8;
+  if (!(mem_fraction > 0.0 && mem_fraction <= 1.0)) mem_fraction = 0.9;
+  ctd_server* S = new ctd_server();
+  S->n_streams = n_streams;
+  S->d = d;
+  S->eps = eps;
+  S->mem_fraction = mem_fraction;
+  cudaGetDevice(&S->dev);
+  S->states.assign(n_streams, nullptr);
+  S->queue.resize(n_streams);
+  S->busy.assign(n_streams, 0);
+  S->req.reserve(1 << 16);
+  for (int k = 0; k < n_streams; ++k) {
+    ctd_status rc = ctd_dynamic_create(dims2, alpha, precision, seed, (uint64_t)k, 0, &S->states[k]);
+    if (rc != CTD_OK) {
+      ctd_server_free(S);
+      return rc;
+    }
+  }
+  S->cstream.assign(workers, nullptr);
+  for (int w = 0; w < workers; ++w)
+    if (cudaStreamCreateWithFlags(&S->cstream[w], cudaStreamNonBlocking) != cudaSuccess) {
+      ctd_server_free(S);
+      return fail(CTD_ECUDA, "stream creation failed");
+    }
+  for (int w = 0; w < workers; ++w) S->pool.emplace_back(worker, S, w);
+  *out = S;
+  return CTD_OK;
+}
+
+extern "C" ctd_status ctd_server_submit(ctd_server* S, int stream_id, const ctd_coo3* dX,
+                                        int64_t* ticket) {
+  if (!S || !dX || !ticket) return fail(CTD_EINVAL, "NULL argument");
+  if (stream_id < 0 || stream_id >= S->n_streams) return fail(CTD_EINVAL, "stream out of range");
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->req.size() == S->req.capacity())
+    return fail(CTD_ENOTSUP, "too many requests for one server (65536)");
+  Request r;
+  r.stream = stream_id;
+  r.X = *dX;
+  r.t_submit = Clock::now();
+  r.estimate = step_estimate(S->states[stream_id], *dX, S->d);
+  S->req.push_back(r);
+  const int64_t t = (int64_t)S->req.size() - 1;
+  S->queue[stream_id].push_back(t);
+  *ticket = t;
+  S->cv.notify_one();
+  return CTD_OK;
+}
+
+extern "C" ctd_status ctd_server_wait(ctd_server* S, int64_t ticket) {
+  if (!S) return fail(CTD_EINVAL, "NULL argument");
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (ticket >= (int64_t)S->req.size()) return fail(CTD_EINVAL, "unknown ticket");
+  auto done = [&] {
+    if (ticket >= 0) return S->req[ticket].done;
+    for (const auto& r : S->req)
+      if (!r.done) return false;
+    return true;
+  };
+  while (!done()) S->cv.wait_for(lk, std::chrono::milliseconds(5));
+  if (ticket >= 0 && S->req[ticket].rc != CTD_OK)
+    return fail(S->req[ticket].rc, S->req[ticket].msg);
+  if (ticket < 0)
+    for (const auto& r : S->req)
+      if (r.rc != CTD_OK) return fail(r.rc, r.msg);
+  return CTD_OK;
+}
+
+extern "C" ctd_status ctd_server_result(ctd_server* S, int64_t ticket, int* status, double ms[3]) {
+  if (!S || !ms) return fail(CTD_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (ticket < 0 || ticket >= (int64_t)S->req.size()) return fail(CTD_EINVAL, "unknown ticket");
+  const Request& r = S->req[ticket];
+  if (!r.done) return fail(CTD_EINVAL, "request still running");
+  if (status) *status = r.rc;
+  ms[0] = ms_between(r.t_submit, r.t_start);
+  ms[1] = ms_between(r.t_start, r.t_done);
+  ms[2] = ms_between(r.t_submit, r.t_done);
+  return CTD_OK;
+}
+
+extern "C" ctd_status ctd_server_state(ctd_server* S, int stream_id, ctd_factors** state) {
+  if (!S || !state) return fail(CTD_EINVAL, "NULL argument");
+  if (stream_id < 0 || stream_id >= S->n_streams) return fail(CTD_EINVAL, "stream out of range");
+  *state = S->states[stream_id];
+  return CTD_OK;
+}
+
+extern "C" void ctd_server_free(ctd_server* S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  for (auto& th : S->pool) th.join();
+  for (auto* F : S->states)
+    if (F) ctd_free(F);
+  for (auto st : S->cstream)
+    if (st) cudaStreamDestroy(st);
+  delete S;
+}

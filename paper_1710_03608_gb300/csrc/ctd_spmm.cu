@@ -117,8 +117,7 @@ ctd_status launch_spmm_dense(const CscDev& X, const int64_t* fibers, const int* 
     return fail(CTD_EINVAL, "factor wider than the supported maximum (24576 columns)");
   const size_t smem = (size_t)R.width * sizeof(unsigned long long);
   if (smem > 48 * 1024)
-    CTD_CUDA(cudaFuncSetAttribute(k_spmm_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    CTD_TRY(allow_max_smem((const void*)k_spmm_dense));
   unsigned g = (unsigned)std::min<int64_t>(nf_max, (int64_t)num_sms() * 4);
   CTD_LAUNCH(k_spmm_dense, (g), (SPMM_THREADS), smem, st, X, fibers, nf_dev, nf_max, R, out, ld);
   CTD_CUDA(cudaGetLastError());
@@ -397,8 +396,7 @@ static ctd_status c_fill_impl(const CscDev& X, int64_t n_cols, const CsrDev& R,
     const int nw = SPMM_THREADS / 32;
     const size_t smem = (size_t)nw * accw * sizeof(A);
     if (smem > 48 * 1024)
-      CTD_CUDA(cudaFuncSetAttribute(k_c_fill_warp<V, A>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      CTD_TRY(allow_max_smem((const void*)k_c_fill_warp<V, A>));
     int per_sm = 0;
     CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_c_fill_warp<V, A>,
                                                            SPMM_THREADS, smem));
@@ -412,8 +410,7 @@ static ctd_status c_fill_impl(const CscDev& X, int64_t n_cols, const CsrDev& R,
     return fail(CTD_EINVAL, "factor wider than the supported maximum (24576 columns)");
   const size_t smem = (size_t)accw * sizeof(A);
   if (smem > 48 * 1024)
-    CTD_CUDA(cudaFuncSetAttribute(k_c_fill_block<V, A>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CTD_TRY(allow_max_smem((const void*)k_c_fill_block<V, A>));
   int per_sm = 0;
   CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_c_fill_block<V, A>,
                                                          SPMM_THREADS, smem));
@@ -561,7 +558,7 @@ struct Vec16<double> {
 
 template <typename T, int NK>
 __global__ void __launch_bounds__(256)
-    k_qform(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs,
+    k_qform(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs, int nblk,
             const double* __restrict__ qn, const short* __restrict__ slot_of,
             const int* __restrict__ hot_rows, int n_hot, int64_t n_rows,
             unsigned long long* work, double* __restrict__ partial) {
@@ -572,7 +569,10 @@ __global__ void __launch_bounds__(256)
   short* slot = reinterpret_cast<short*>(smraw + (size_t)n_hot * qs * sizeof(T));  // [n_rows]
   for (int64_t e = threadIdx.x; e < (int64_t)n_hot * qs; e += blockDim.x)
     Qs[e] = Q[(int64_t)hot_rows[e / qs] * qs + (e % qs)];
-  for (int64_t e = threadIdx.x; e < n_rows; e += blockDim.x) slot[e] = slot_of[e];
+  if (slot_of)
+    for (int64_t e = threadIdx.x; e < n_rows; e += blockDim.x) slot[e] = slot_of[e];
+  else
+    slot = nullptr;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(X.colptr);
@@ -599,6 +599,9 @@ __global__ void __launch_bounds__(256)
       const unsigned long long a = __shfl_sync(0xffffffffu, la, e);
       const unsigned long long b = __shfl_sync(0xffffffffu, lb, e);
       if (b <= a) continue;
+      double ss = 0.0;
+      for (int cb = 0; cb < nblk; ++cb) {  // column blocks of NK * 32 * VEC
+      const int64_t coff = (int64_t)cb * NK * 32 * VEC;
       T acc[NK * VEC];
 #pragma unroll
       for (int k = 0; k < NK * VEC; ++k) acc[k] = (T)0;
@@ -609,8 +612,8 @@ __global__ void __launch_bounds__(256)
         if (lane < cnt) {
           const int i = __ldg(X.row + base + lane);
           myv = __ldg(X.val + base + lane);
-          const int sl = slot[i];
-          myrow = sl >= 0 ? Qs + (int64_t)sl * qs : Q + (int64_t)i * qs;
+          const int sl = slot ? slot[i] : -1;
+          myrow = sl >= 0 ? Qs + (int64_t)sl * qs : Q + (int64_t)i * qs + coff;
         }
         int q = 0;
         for (; q + 1 < cnt; q += 2) {
@@ -647,9 +650,9 @@ __global__ void __launch_bounds__(256)
           }
         }
       }
-      double ss = 0.0;
 #pragma unroll
       for (int k = 0; k < NK * VEC; ++k) ss = fma((double)acc[k], (double)acc[k], ss);
+      }
       for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
       if (lane == e) total += ss;  // lane e owns column f0 + e
     }
@@ -674,19 +677,43 @@ __global__ void k_sum_f64_fixed(const double* __restrict__ in, int64_t n, double
 }
 
 template <typename T, int NK>
-static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int qs,
+static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int qs, int nblk,
                                const double* qn, const short* slot_of, const int* hot, int n_hot,
                                int64_t n_rows, unsigned long long* work, double* partial,
                                cudaStream_t st) {
-  const size_t smem = (size_t)n_hot * qs * sizeof(T) + (size_t)n_rows * sizeof(short);
+  const size_t smem =
+      (size_t)n_hot * qs * sizeof(T) + (slot_of ? (size_t)n_rows * sizeof(short) : 0);
   if (smem > 48 * 1024)
-    CTD_CUDA(cudaFuncSetAttribute(k_qform<T, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    CTD_TRY(allow_max_smem((const void*)k_qform<T, NK>));
   int per_sm = 0;
   CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qform<T, NK>, 256, smem));
   if (per_sm < 1) return fail(CTD_ECUDA, "error kernel does not fit on an SM");
-  CTD_LAUNCH((k_qform<T, NK>), (num_sms() * per_sm), (256), smem, st, X, n_cols, Q, qs, qn,
-             slot_of, hot, n_hot, n_rows, work, partial);
+  CTD_LAUNCH((k_qform<T, NK>), (num_sms() * per_sm), (256), smem, st, X, n_cols, Q, qs, nblk,
+             qn, slot_of, hot, n_hot, n_rows, work, partial);
+  return CTD_OK;
+}
+
+// ||Q^T X_(alpha)||_F^2 for a dense FP64 Q given by rows (row i at
+// Q + i * ld, ld a multiple of 512, entries past the used width zero) and
+// its row norms qn; no shared-memory staging.
+ctd_status launch_qform_rows(const CscDev& X, int64_t n_cols, const double* Q, int64_t ld,
+                             int64_t width, const double* qn, int64_t n_rows, double* out,
+                             Arena& scratch, cudaStream_t st) {
+  CTD_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
+  if (width <= 0 || n_cols <= 0) return CTD_OK;
+  if (ld % 512 != 0 || ld < width) return fail(CTD_EINVAL, "Q row stride must be a multiple of 512");
+  const int nblk = (int)((width + 511) / 512);
+  unsigned long long* work;
+  double* partial;
+  const int64_t nchunks = (n_cols + 31) / 32;
+  CTD_TRY(scratch.get(&work, 1));
+  CTD_TRY(scratch.get(&partial, nchunks));
+  CTD_CUDA(cudaMemsetAsync(work, 0, 8, st));
+  CTD_CUDA(cudaMemsetAsync(partial, 0, nchunks * sizeof(double), st));
+  CTD_TRY((qform_launch<double, 8>(X, n_cols, Q, (int)ld, nblk, qn, nullptr, nullptr, 0, n_rows,
+                                   work, partial, st)));
+  CTD_LAUNCH(k_sum_f64_fixed, (1), (1024), 0, st, partial, nchunks, out);
+  CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
 
@@ -744,9 +771,9 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
   }
   ctd_status rc;
 #define QF(NKV)                                                                                  \
-  rc = fp32 ? qform_launch<float, NKV>(X, n_cols, static_cast<const float*>(Q), qs, qn, slot_of, \
-                                       hot, n_hot, n_rows, work, partial, st)                    \
-            : qform_launch<double, NKV>(X, n_cols, static_cast<const double*>(Q), qs, qn,        \
+  rc = fp32 ? qform_launch<float, NKV>(X, n_cols, static_cast<const float*>(Q), qs, 1, qn,     \
+                                       slot_of, hot, n_hot, n_rows, work, partial, st)           \
+            : qform_launch<double, NKV>(X, n_cols, static_cast<const double*>(Q), qs, 1, qn,     \
                                         slot_of, hot, n_hot, n_rows, work, partial, st)
   if (NK <= 1) {
     QF(1);

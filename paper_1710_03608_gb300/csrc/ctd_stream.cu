@@ -109,7 +109,7 @@ void launch_fiber_norms(const CooDev& X, uint64_t* norm2, uint32_t* colcnt, uint
   const bool priv = n_rows <= NORMS_SMEM_ROWS;
   const size_t smem = priv ? (size_t)n_rows * 4 : 0;
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_fiber_norms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem((const void*)k_fiber_norms);
   unsigned g = grid_for(X.nnz, bs, (int64_t)num_sms() * 2);
   CTD_LAUNCH(k_fiber_norms, (g), (bs), smem, st, X.i, X.j, X.k, X.v, X.nnz, make_map(X), n_rows,
              reinterpret_cast<unsigned long long*>(norm2), colcnt, rowcnt, minval, status);

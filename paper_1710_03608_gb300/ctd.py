@@ -30,7 +30,8 @@ STATUS = {0: "CTD_OK", 1: "CTD_EINVAL", 2: "CTD_ENOMEM", 3: "CTD_EOVERFLOW", 4: 
 EXPORTED = ["ctd_static", "ctd_dynamic_create", "ctd_dynamic_step", "ctd_error", "ctd_get_sizes",
             "ctd_get_samples", "ctd_get_fibers", "ctd_get_R", "ctd_get_U", "ctd_get_C_columns",
             "ctd_get_C", "ctd_get_step", "ctd_get_M", "ctd_free", "ctd_last_error",
-            "ctd_version", "ctd_profile", "ctd_profile_report", "ctd_sample_noalloc"]
+            "ctd_version", "ctd_profile", "ctd_profile_report", "ctd_sample_noalloc", "ctd_static_batched", "ctd_server_create", "ctd_server_submit",
+            "ctd_server_wait", "ctd_server_result", "ctd_server_state", "ctd_server_free"]
 
 
 class CtdError(RuntimeError):
@@ -82,6 +83,13 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ctd_get_step": [P, I64, P, P],
         "ctd_get_M": [P, I64, P],
         "ctd_profile": [I32],
+        "ctd_static_batched": [I32, P, I32, P, P, D, I32, C.c_uint, I32, P, P],
+        "ctd_server_create": [I32, C.POINTER(C.c_int64 * 2), I32, I32, U64, I64, D, I32, D,
+                              C.POINTER(P)],
+        "ctd_server_submit": [P, I32, C.POINTER(ctd_coo3), C.POINTER(C.c_int64)],
+        "ctd_server_wait": [P, I64],
+        "ctd_server_result": [P, I64, C.POINTER(C.c_int), P],
+        "ctd_server_state": [P, I32, C.POINTER(P)],
         "ctd_sample_noalloc": [C.POINTER(ctd_coo3), I32, I64, U64, P, P, C.POINTER(C.c_int), P],
         "ctd_profile_report": [C.c_char_p, C.c_size_t],
     }
@@ -89,6 +97,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = C.c_int
+    lib.ctd_server_free.argtypes = [P]
+    lib.ctd_server_free.restype = None
     lib.ctd_free.argtypes = [P]
     lib.ctd_free.restype = None
     lib.ctd_last_error.restype = C.c_char_p
@@ -253,6 +263,21 @@ def ctd_static(X: Coo, alpha: int, s: int, eps: float, seed: int = 0,
     return Factors(out.value)
 
 
+def ctd_static_batched(Xs, alpha: int, s, seeds, eps: float, precision: int = CTD_FP64,
+                       flags: int = 0, workers: int = 0, stream=None):
+    """CTD-S on a list of tensors through one ctd_static_batched call."""
+    n = len(Xs)
+    descs = (ctd_coo3 * n)(*[X.desc for X in Xs])
+    s_arr = (C.c_int64 * n)(*[int(v) for v in s])
+    seeds_arr = (C.c_uint64 * n)(*[int(v) for v in seeds])
+    outs = (C.c_void_p * n)()
+    st = _stream_handle(stream) if stream is not None or any(not _host(X) for X in Xs) else _default_stream()
+    _check(load().ctd_static_batched(n, descs, int(alpha), s_arr, seeds_arr, float(eps),
+                                     int(precision), int(flags), int(workers), C.c_void_p(st),
+                                     outs))
+    return [Factors(outs[t]) for t in range(n)]
+
+
 def _host(X: Coo) -> bool:
     return X.desc.memory == CTD_MEM_HOST
 
@@ -305,6 +330,59 @@ def profile_report() -> dict:
     buf = C.create_string_buffer(1 << 16)
     _check(load().ctd_profile_report(buf, len(buf)))
     return json.loads(buf.value.decode())
+
+
+class _Borrowed(Factors):
+    """A state owned by a server: getters only, never freed here."""
+
+    def __del__(self):
+        pass
+
+
+class Server:
+    """Serving loop for CTD-D streams (ctd_server_*)."""
+
+    def __init__(self, n_streams: int, dims2, d: int, eps: float, alpha: int = 1,
+                 precision: int = CTD_FP64, seed: int = 0, workers: int = 0,
+                 mem_fraction: float = 0.9):
+        out = C.c_void_p()
+        d2 = (C.c_int64 * 2)(int(dims2[0]), int(dims2[1]))
+        _check(load().ctd_server_create(int(n_streams), C.byref(d2), int(alpha), int(precision),
+                                        int(seed), int(d), float(eps), int(workers),
+                                        float(mem_fraction), C.byref(out)))
+        self.h = out
+        self._keep = {}
+
+    def submit(self, stream_id: int, X: Coo) -> int:
+        t = C.c_int64()
+        _check(load().ctd_server_submit(self.h, int(stream_id), C.byref(X.desc), C.byref(t)))
+        self._keep[t.value] = X
+        return t.value
+
+    def wait(self, ticket: int = -1):
+        _check(load().ctd_server_wait(self.h, int(ticket)))
+
+    def result(self, ticket: int):
+        st = C.c_int()
+        ms = np.empty(3, np.float64)
+        _check(load().ctd_server_result(self.h, int(ticket), C.byref(st), _ptr(ms)))
+        return st.value, ms
+
+    def state(self, stream_id: int) -> Factors:
+        out = C.c_void_p()
+        _check(load().ctd_server_state(self.h, int(stream_id), C.byref(out)))
+        return _Borrowed(out.value)
+
+    def close(self):
+        if self.h:
+            load().ctd_server_free(self.h)
+            self.h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def version() -> str:

@@ -1,0 +1,221 @@
+"""Measurements of the batched, serving and streaming forms (one JSON line each).
+
+  python -m paper_1710_03608_gb300.measure batched [--count N] [--tune]
+      256 uneven CTD-S tensors: a plain loop of ctd_static vs one
+      ctd_static_batched call; nonzeros/s of each and the gain.
+  python -m paper_1710_03608_gb300.measure serving [--seconds S] [--rate HZ]
+      64 CTD-D streams, Poisson arrivals, continuous batching; p50/p99
+      latency, offered and achieved nonzeros/s; the same requests run one at
+      a time for comparison.
+  python -m paper_1710_03608_gb300.measure stream [--steps T] [--scale F]
+      one CTD-D stream of 2*10^4 x 2*10^4 slices (500K nonzeros each, planted
+      block at steps 40-45); per-step nonzeros/s and d~_t.
+
+All times are host wall-clock around calls that wait for their work (the
+library's entry points return when the device is done), inputs in HBM.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+from . import ctd, synth
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+TUNE_FILE = os.path.join(_HERE, "_build", "autotune.json")
+
+
+def _sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+# ---------------------------------------------------------------------------
+# autotuner: worker streams for the batched form
+# ---------------------------------------------------------------------------
+def tuned_workers(default: int = 8) -> int:
+    try:
+        with open(TUNE_FILE) as f:
+            return int(json.load(f)["batched_workers"])
+    except Exception:
+        return default
+
+
+def autotune_workers(Xs, s, seeds, candidates=(2, 4, 8, 12, 16, 24)) -> dict:
+    """Time ctd_static_batched on the given tensors for each worker count;
+    keep the fastest in the tuning file."""
+    times = {}
+    for w in candidates:
+        for _ in range(2):
+            _sync()
+            t0 = time.perf_counter()
+            Fs = ctd.ctd_static_batched(Xs, 1, s, seeds, 1e-6, ctd.CTD_FP32_BULK, 0, w)
+            _sync()
+            dt = time.perf_counter() - t0
+            del Fs
+        times[w] = dt
+    best = min(times, key=times.get)
+    os.makedirs(os.path.dirname(TUNE_FILE), exist_ok=True)
+    with open(TUNE_FILE, "w") as f:
+        json.dump({"batched_workers": best, "times_s": times}, f)
+    return {"best": best, "times_s": times}
+
+
+# ---------------------------------------------------------------------------
+# batched CTD-S
+# ---------------------------------------------------------------------------
+def batched(args):
+    specs = synth.batch_256(count=args.count)
+    t0 = time.perf_counter()
+    tensors = [sp.tensor() for sp in specs]
+    gen_s = time.perf_counter() - t0
+    Xs = [ctd.Coo.from_synth(x) for x in tensors]
+    s = [sp.s for sp in specs]
+    seeds = list(range(len(specs)))
+    nnz = sum(x.nnz for x in tensors)
+    tune = None
+    if args.tune:
+        sample = list(range(0, len(Xs), max(1, len(Xs) // 48)))
+        tune = autotune_workers([Xs[i] for i in sample], [s[i] for i in sample],
+                                [seeds[i] for i in sample])
+    workers = args.workers or tuned_workers()
+    # warm-up
+    ctd.ctd_static_batched(Xs[:8], 1, s[:8], seeds[:8], 1e-6, ctd.CTD_FP32_BULK, 0, workers)
+    for X, si, se in zip(Xs[:4], s[:4], seeds[:4]):
+        ctd.ctd_static(X, 1, si, 1e-6, se, ctd.CTD_FP32_BULK)
+    _sync()
+    # plain loop
+    t0 = time.perf_counter()
+    errs_plain = []
+    for X, si, se in zip(Xs, s, seeds):
+        F = ctd.ctd_static(X, 1, si, 1e-6, se, ctd.CTD_FP32_BULK)
+        errs_plain.append(F.error())
+        F.free()
+    _sync()
+    t_plain = time.perf_counter() - t0
+    # batched
+    t0 = time.perf_counter()
+    Fs = ctd.ctd_static_batched(Xs, 1, s, seeds, 1e-6, ctd.CTD_FP32_BULK, 0, workers)
+    _sync()
+    t_batch = time.perf_counter() - t0
+    errs_batch = [F.error() for F in Fs]
+    same = all(a == b for a, b in zip(errs_plain, errs_batch))
+    line = {"workload": f"{len(specs)} uneven CTD-S traffic tensors (batch law of the 256-tensor "
+                        f"workload), {nnz} nonzeros", "nnz": nnz, "generation_s": gen_s,
+            "plain": {"seconds": t_plain, "nnz_per_s": nnz / t_plain},
+            "batched": {"seconds": t_batch, "nnz_per_s": nnz / t_batch, "workers": workers},
+            "gain": t_plain / t_batch, "same_errors": same, "autotune": tune}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# serving CTD-D
+# ---------------------------------------------------------------------------
+def serving(args):
+    import torch
+    dims2 = (5000, 5000)
+    reqs = synth.serving_requests(streams=args.streams, rate_hz=args.rate,
+                                  duration_s=args.seconds)
+    rng = np.random.default_rng(7)
+    # a pool of distinct slices reused cyclically (generation is slower than 2 kHz)
+    pool_n = min(args.pool, len(reqs))
+    pool = [Request_slice(r, dims2) for r in reqs[:pool_n]]
+    Xp = [ctd.Coo.from_synth(sl) for sl in pool]
+    nnz = [sl.nnz for sl in pool]
+    total_nnz = sum(nnz[q % pool_n] for q in range(len(reqs)))
+
+    def run(workers, paced):
+        S = ctd.Server(args.streams, dims2, args.d, 1e-6, 1, ctd.CTD_FP32_BULK, 0, workers)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tickets = []
+        for q, r in enumerate(reqs):
+            if paced:
+                while time.perf_counter() - t0 < r.arrival_s:
+                    time.sleep(0.0002)
+            tickets.append(S.submit(r.stream, Xp[q % pool_n]))
+        S.wait()
+        t_end = time.perf_counter()
+        lat = np.array([S.result(t)[1][2] for t in tickets])
+        S.close()
+        return t_end - t0, lat
+
+    d_mix, lat_mix = run(args.workers, True)
+    d_one, lat_one = run(1, True)
+    line = {"workload": f"{args.streams} CTD-D streams, 5000x5000 slices, Poisson arrivals at "
+                        f"{args.rate:.0f} Hz for {args.seconds} s ({len(reqs)} requests, "
+                        f"{pool_n} distinct slices reused), d = {args.d}",
+            "offered_nnz_per_s": total_nnz / args.seconds,
+            "continuous": {"workers": args.workers, "achieved_nnz_per_s": total_nnz / d_mix,
+                           "p50_ms": float(np.percentile(lat_mix, 50)),
+                           "p99_ms": float(np.percentile(lat_mix, 99)), "wall_s": d_mix},
+            "one_at_a_time": {"achieved_nnz_per_s": total_nnz / d_one,
+                              "p50_ms": float(np.percentile(lat_one, 50)),
+                              "p99_ms": float(np.percentile(lat_one, 99)), "wall_s": d_one},
+            "gain": d_one / d_mix}
+    print(json.dumps(line), flush=True)
+
+
+def Request_slice(r, dims2):
+    return r.slice(dims2)
+
+
+# ---------------------------------------------------------------------------
+# one CTD-D stream
+# ---------------------------------------------------------------------------
+def stream(args):
+    st = synth.traffic_stream_20k(scale=args.scale, steps=args.steps)
+    G = ctd.Dynamic(st.dims2, 1, ctd.CTD_FP32_BULK, 0, 0, ctd.CTD_KEEP_LAST_C)
+    per = []
+    tot_nnz, tot_s = 0, 0.0
+    for t in range(args.steps):
+        sl = st.slice(t)
+        X = ctd.Coo.from_synth(sl)
+        _sync()
+        t0 = time.perf_counter()
+        G.step_slice(X, args.d, 1e-6)
+        _sync()
+        dt = time.perf_counter() - t0
+        info, sq = G.step(t)
+        per.append({"t": t, "nnz": sl.nnz, "ms": dt * 1e3, "d_unique": int(info[0]),
+                    "kept": int(info[1]), "d_before": int(info[2])})
+        tot_nnz += sl.nnz
+        tot_s += dt
+    line = {"workload": f"CTD-D stream of {args.steps} slices {st.dims2[0]}x{st.dims2[1]}, "
+                        f"{st.nnz} nonzeros each, d = {args.d}",
+            "nnz_per_s": tot_nnz / tot_s, "seconds": tot_s, "final_d": int(G.sizes().s_kept),
+            "rel_error": G.error(), "steps": per}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    b = sub.add_parser("batched")
+    b.add_argument("--count", type=int, default=256)
+    b.add_argument("--workers", type=int, default=0)
+    b.add_argument("--tune", action="store_true")
+    sv = sub.add_parser("serving")
+    sv.add_argument("--streams", type=int, default=64)
+    sv.add_argument("--rate", type=float, default=2000.0)
+    sv.add_argument("--seconds", type=float, default=2.0)
+    sv.add_argument("--pool", type=int, default=96)
+    sv.add_argument("--workers", type=int, default=8)
+    sv.add_argument("--d", type=int, default=200)
+    sm = sub.add_parser("stream")
+    sm.add_argument("--steps", type=int, default=100)
+    sm.add_argument("--scale", type=float, default=1.0)
+    sm.add_argument("--d", type=int, default=400)
+    args = ap.parse_args()
+    import torch
+    torch.cuda.set_device(0)
+    ctd.load()
+    {"batched": batched, "serving": serving, "stream": stream}[args.cmd](args)
+
+
+if __name__ == "__main__":
+    main()
