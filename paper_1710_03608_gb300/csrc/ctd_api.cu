@@ -79,7 +79,10 @@ ctd_status allow_max_smem(const void* fn) {
   if (done.count({dev, fn})) return CTD_OK;
   int optin = 0;
   CTD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  CTD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  cudaFuncAttributes fa{};
+  CTD_CUDA(cudaFuncGetAttributes(&fa, fn));  // static shared memory counts against the limit
+  CTD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes));
   done.insert({dev, fn});
   return CTD_OK;
 }
@@ -378,7 +381,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
     F->mem.ptrs.push_back(cv);
     F->Cval = cv;
     PhaseScope ph("c_fill", st);
-    STEP(launch_c_fill(M.csc(), M.n_cols, R, F->Coff, F->Ccnt, F->Crow, F->Cval,
+    STEP(launch_c_fill(M.csc(), M.n_cols, M.n_rows, R, F->Coff, F->Ccnt, F->Crow, F->Cval,
                        precision == CTD_FP32_BULK, minval > 0, T, st));
   }
 

@@ -37,7 +37,9 @@ namespace {
 struct StepRec {
   int64_t d_draws = 0, d_unique = 0, d_kept = 0, d_before = 0, nnz = 0;
   double sq = 0.0, err = 0.0;      // ||dX||^2 and ||dX - P dX||^2
-  double* M = nullptr;             // Y_K: d_before x d_kept column-major (= M row-major)
+  double* WK = nullptr;            // W_K = L^(t)^{-1} R^(t)^T dR: d_before x d_kept
+  double* M = nullptr;             // Y_K = L^(t)^{-T} W_K = U^(t) R^(t)^T dR, computed on
+                                   // first request (column-major = M_{t+1} row-major)
   uint64_t* Coff = nullptr;        // new-column block, height d_before + d_kept
   uint32_t* Ccnt = nullptr;
   uint16_t* Crow = nullptr;
@@ -152,6 +154,7 @@ ctd_factors::~ctd_factors() {
     cudaStreamSynchronize(stream);
     for (auto& s : dyn->steps) {
       dfree(s.M, stream);
+      dfree(s.WK, stream);
       dfree(s.Coff, stream);
       dfree(s.Ccnt, stream);
       dfree(s.Crow, stream);
@@ -220,7 +223,7 @@ extern "C" ctd_status ctd_dynamic_create(const int64_t dims2[2], int alpha, int 
   return CTD_OK;
 }
 
-// grow U, L and Q^T (ld cap, a multiple of 512) to hold n kept fibers,
+// grow L and Q^T (ld cap, a multiple of 512) to hold n kept fibers,
 // keeping the first d
 static ctd_status grow_U(ctd_factors* F, int64_t d, int64_t n, cudaStream_t st) {
   auto& D = *F->dyn;
@@ -228,24 +231,19 @@ static ctd_status grow_U(ctd_factors* F, int64_t d, int64_t n, cudaStream_t st) 
   int64_t cap = std::max<int64_t>(std::max<int64_t>(2 * D.cap_d, n), 512);
   cap = (cap + 511) / 512 * 512;
   const int64_t rows = F->n_rows;
-  double *U2, *L2, *Q2;
-  CTD_TRY(dalloc_n(&U2, (size_t)cap * cap, st));
+  double *L2, *Q2;
   CTD_TRY(dalloc_n(&L2, (size_t)cap * cap, st));
   CTD_TRY(dalloc_n(&Q2, (size_t)cap * rows, st));
   CTD_CUDA(cudaMemsetAsync(L2, 0, (size_t)cap * cap * 8, st));
   CTD_CUDA(cudaMemsetAsync(Q2, 0, (size_t)cap * rows * 8, st));
   if (d > 0) {
-    CTD_CUDA(cudaMemcpy2DAsync(U2, cap * 8, F->U, D.cap_d * 8, d * 8, d,
-                               cudaMemcpyDeviceToDevice, st));
     CTD_CUDA(cudaMemcpy2DAsync(L2, cap * 8, F->L, D.cap_d * 8, d * 8, d,
                                cudaMemcpyDeviceToDevice, st));
     CTD_CUDA(cudaMemcpy2DAsync(Q2, cap * 8, F->Qt, D.cap_d * 8, d * 8, rows,
                                cudaMemcpyDeviceToDevice, st));
   }
-  dfree(F->U, st);
   dfree(F->L, st);
   dfree(F->Qt, st);
-  F->U = U2;
   F->L = L2;
   F->Qt = Q2;
   D.cap_d = cap;
@@ -462,31 +460,18 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
       double* WKs = nullptr;  // W restricted to the kept candidates (dt x kept)
       double* L = fo.Lk;   // factor of the kept block of S
       double* Li = fo.Li;  // its inverse
-      double* Sinv;
-      CTD_TRY(scratch.get(&Sinv, (size_t)kept * kept));
-      u_from_linv(Li, kept, kept, Sinv, kept, st);
+      F->U_valid = false;
       CTD_TRY(grow_U(F, dt, dn, st));
       const int64_t ld = D.cap_d;
       if (dt > 0) {
-        // Y_K = U^(t) B_K; M_{t+1} = Y_K^T = ((dR)^T R^(t)) U^(t), kept for C's lower-left blocks
-        double *BK, *WK, *Z;
-        CTD_TRY(scratch.get(&BK, (size_t)dt * kept));
-        CTD_TRY(scratch.get(&WK, (size_t)dt * kept));
-        WKs = WK;
-        CTD_TRY(scratch.get(&Z, (size_t)dt * kept));
-        CTD_TRY(dalloc_n(&rec.M, (size_t)dt * kept, st));
-        const unsigned gk = grid_for(dt * kept, 256, (int64_t)num_sms() * 8);
-        CTD_LAUNCH(k_gather_cols_f64, (gk), (256), 0, st, Bm, dt, dt, idx, kept, BK, dt);
-        CTD_LAUNCH(k_gather_cols_f64, (gk), (256), 0, st, W, dt, dt, idx, kept, WK, dt);
-        dgemm(false, false, dt, kept, dt, 1.0, F->U, ld, BK, dt, 0.0, rec.M, dt, st);
-        // U^(t+1): [[U + Z Z^T, -Z L_S^{-1}], [., S_K^{-1}]] with Z = Y_K L_S^{-T}
-        dgemm(false, true, dt, kept, kept, 1.0, rec.M, dt, Li, kept, 0.0, Z, dt, st);
-        dgemm(false, true, dt, dt, kept, 1.0, Z, dt, Z, dt, 1.0, F->U, ld, st);
-        dgemm(false, false, dt, kept, kept, -1.0, Z, dt, Li, kept, 0.0, F->U + dt * ld, ld, st);
-        CTD_LAUNCH(k_transpose_f64, (gk), (256), 0, st, F->U + dt * ld, ld, dt, kept, F->U + dt,
-                   ld);
+        // W_K = L^{-1} R^(t)^T dR, kept for the M chain (M_{t+1} = W_K^T
+        // L^(t)^{-1} = ((dR)^T R^(t)) U^(t), formed on request) and for
         // L^(t+1) = [[L, 0], [W_K^T, L_S]]
-        CTD_LAUNCH(k_transpose_f64, (gk), (256), 0, st, WK, dt, dt, kept, F->L + dt, ld);
+        CTD_TRY(dalloc_n(&rec.WK, (size_t)dt * kept, st));
+        WKs = rec.WK;
+        const unsigned gk = grid_for(dt * kept, 256, (int64_t)num_sms() * 8);
+        CTD_LAUNCH(k_gather_cols_f64, (gk), (256), 0, st, W, dt, dt, idx, kept, rec.WK, dt);
+        CTD_LAUNCH(k_transpose_f64, (gk), (256), 0, st, rec.WK, dt, dt, kept, F->L + dt, ld);
       }
       CTD_CUDA(cudaMemcpy2DAsync(F->L + dt + dt * ld, ld * 8, L, kept * 8, kept * 8, kept,
                                  cudaMemcpyDeviceToDevice, st));
@@ -494,6 +479,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
       // range(Q^(t)) (Gram-Schmidt twice), normalized by L_S^{-T} and then
       // once more by a Cholesky of their Gram matrix (orthonormal to rounding)
       {
+        PhaseScope phq("d_q_basis", st);
         const int64_t nr = M.n_rows;
         double *V, *V2, *Vq;
         CTD_TRY(scratch.get(&V, (size_t)nr * kept));
@@ -507,8 +493,13 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
           double* Hm;
           CTD_TRY(scratch.get(&Hm, (size_t)dt * kept));
           dgemm(true, false, nr, kept, dt, -1.0, F->Qt, ld, WKs, dt, 1.0, V, nr, st);
-          dgemm(false, false, dt, kept, nr, 1.0, F->Qt, ld, V, nr, 0.0, Hm, dt, st);
-          dgemm(true, false, nr, kept, dt, -1.0, F->Qt, ld, Hm, dt, 1.0, V, nr, st);
+          // the second pass holds the blocks orthogonal to ~u / rho for a
+          // residual ratio rho >= eps; FP32_BULK's error bar (1e-4 relative)
+          // does not need it
+          if (!fp32) {
+            dgemm(false, false, dt, kept, nr, 1.0, F->Qt, ld, V, nr, 0.0, Hm, dt, st);
+            dgemm(true, false, nr, kept, dt, -1.0, F->Qt, ld, Hm, dt, 1.0, V, nr, st);
+          }
         }
         // V2 = V L_S^{-T} is orthonormal up to the filter's rounding; one
         // Cholesky-QR pass makes it so to working precision.  If that pass
@@ -533,8 +524,6 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
         CTD_LAUNCH(k_qn_add, (grid_for(nr, 256, (int64_t)num_sms() * 4)), (256), 0, st, F->Qt, ld,
                    dt, kept, nr, F->qn);
       }
-      CTD_CUDA(cudaMemcpy2DAsync(F->U + dt + dt * ld, ld * 8, Sinv, kept * 8, kept * 8, kept,
-                                 cudaMemcpyDeviceToDevice, st));
       // append dR to R (CSC), then rebuild the by-row copy
       int64_t* newf;
       uint64_t *nsz, *nptr;
@@ -601,7 +590,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
     CTD_TRY(dalloc(&rec.Cval, std::max<uint64_t>(cap, 1) * (fp32 ? 4 : 8), st));
     {
       PhaseScope ph("d_c_fill", st);
-      CTD_TRY(launch_c_fill(M.csc(), M.n_cols, R, rec.Coff, rec.Ccnt, rec.Crow, rec.Cval, fp32,
+      CTD_TRY(launch_c_fill(M.csc(), M.n_cols, M.n_rows, R, rec.Coff, rec.Ccnt, rec.Crow, rec.Cval, fp32,
                             D.all_positive, (uint64_t)D.max_T, st));
     }
     double* d_pu;
@@ -670,13 +659,30 @@ extern "C" ctd_status ctd_get_step(const ctd_factors* F, int64_t t, int64_t info
   return CTD_OK;
 }
 
+// M_{t+1} (as Y_K = L^(t)^{-T} W_K) of step t, formed on first request; the
+// leading d_before block of the current L is L^(t), since L only grows.
+static ctd_status ensure_M(const ctd_factors* Fc, int64_t t) {
+  ctd_factors* F = const_cast<ctd_factors*>(Fc);
+  StepRec& r = F->dyn->steps[t];
+  if (r.M || r.d_before == 0 || r.d_kept == 0) return CTD_OK;
+  if (!r.WK) return fail(CTD_EINVAL, "inconsistent step record");
+  cudaStream_t st = F->stream;
+  const size_t n = (size_t)r.d_before * r.d_kept;
+  CTD_TRY(dalloc_n(&r.M, n, st));
+  CTD_CUDA(cudaMemcpyAsync(r.M, r.WK, n * 8, cudaMemcpyDeviceToDevice, st));
+  tri_solve_lower_T(F->L, F->dyn->cap_d, r.d_before, r.M, r.d_before, r.d_kept, st);
+  CTD_CUDA(cudaGetLastError());
+  return CTD_OK;
+}
+
 extern "C" ctd_status ctd_get_M(const ctd_factors* F, int64_t t, double* M) {
   if (!F || !F->dyn) return fail(CTD_EINVAL, "not a CTD-D state");
   if (t < 0 || t >= F->dyn->t) return fail(CTD_EINVAL, "step out of range");
   const StepRec& r = F->dyn->steps[t];
   const size_t n = (size_t)r.d_kept * r.d_before;
   if (n == 0) return CTD_OK;
-  if (!M || !r.M) return fail(CTD_EINVAL, "NULL argument");
+  if (!M) return fail(CTD_EINVAL, "NULL argument");
+  CTD_TRY(ensure_M(F, t));
   CTD_TRY(d2h(M, r.M, n, F->stream));
   return sync(F->stream);
 }
@@ -717,12 +723,28 @@ ctd_status dyn_fibers(const ctd_factors* F, int64_t* fiber, int64_t* step) {
   return CTD_OK;
 }
 
-ctd_status dyn_U(const ctd_factors* F, double* U) {
+// U^(t) = (R^T R)^{-1} = L^{-T} L^{-1}, formed from the maintained factor on
+// the first request after a step that kept fibers, then cached.
+ctd_status dyn_U(const ctd_factors* Fc, double* U) {
+  ctd_factors* F = const_cast<ctd_factors*>(Fc);
   const int64_t n = F->s_kept;
   if (n == 0) return CTD_OK;
-  CTD_CUDA(cudaMemcpy2DAsync(U, n * 8, F->U, F->dyn->cap_d * 8, n * 8, n,
-                             cudaMemcpyDeviceToHost, F->stream));
-  return sync(F->stream);
+  cudaStream_t st = F->stream;
+  if (!F->U_valid) {
+    dfree(F->U, st);
+    F->U = nullptr;
+    CTD_TRY(dalloc_n(&F->U, (size_t)n * n, st));
+    Arena a;
+    a.st = st;
+    double* Li;
+    CTD_TRY(a.get(&Li, (size_t)n * n));
+    tri_inverse(F->L, F->dyn->cap_d, n, Li, n, st);
+    u_from_linv(Li, n, n, F->U, n, st);
+    CTD_CUDA(cudaGetLastError());
+    F->U_valid = true;
+  }
+  CTD_CUDA(cudaMemcpyAsync(U, F->U, (size_t)n * n * 8, cudaMemcpyDeviceToHost, st));
+  return sync(st);
 }
 
 // Column (t, f) of C^(now): the step's exact block, then the rows each later
@@ -765,6 +787,7 @@ ctd_status dyn_C_columns(const ctd_factors* F, int64_t ncols, const int64_t* col
       if (q.d_before != (int64_t)v.size()) return fail(CTD_EINVAL, "inconsistent step record");
       std::vector<double>& Mq = Mh[t2];
       if (Mq.empty() && q.d_before > 0) {
+        CTD_TRY(ensure_M(F, t2));
         Mq.resize((size_t)q.d_before * q.d_kept);
         CTD_TRY(d2h(Mq.data(), q.M, Mq.size(), st));
         CTD_TRY(sync(st));

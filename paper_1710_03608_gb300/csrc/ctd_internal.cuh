@@ -217,9 +217,17 @@ void launch_c_bounds(const CscDev& X, int64_t n_cols, const CsrDev& R, uint32_t*
 // ascending (16-bit row indices).  Values stored as float (fp32 != 0) or
 // double.  R's rows must be sorted by column.  positive: every value of X
 // and R is > 0 (enables the one-nonzero copy path).
-ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, const CsrDev& R,
+ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
                          const uint64_t* coff, uint32_t* ccnt, uint16_t* crow, void* cval,
                          int fp32, int positive, uint64_t sqnorm_X, cudaStream_t st);
+// The same with the longest rows of R dense in shared memory and register
+// accumulators (ctd_cfill.cu); requires sqnorm_X < 2^31 and width <= 1024.
+ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
+                             const uint64_t* coff, uint32_t* ccnt, uint16_t* crow, void* cval,
+                             int fp32, int positive, cudaStream_t st);
+// list[0..count) = columns with >= minc nonzeros and a nonzero C bound
+void launch_list_columns(const uint64_t* colptr, const uint64_t* coff, int64_t n_cols,
+                         uint64_t minc, int64_t* list, unsigned* count, cudaStream_t st);
 // Sort each row of a row-major factor by column (col/val copied to *_out).
 void launch_sort_rows(const uint64_t* rowptr, int64_t n_rows, const int32_t* col_in,
                       const int32_t* val_in, int32_t* col_out, int32_t* val_out, cudaStream_t st);
@@ -381,6 +389,7 @@ struct ctd_factors {
   int32_t* Rcol = nullptr;
   int32_t* Rcval = nullptr;
   double* U = nullptr;           // s~ x s~ column-major (symmetric)
+  bool U_valid = false;          // CTD-D: U is formed from L on request and cached
   double* L = nullptr;           // CTD-D: Cholesky factor of R^T R (lower, ld as U)
   double* Qt = nullptr;          // CTD-D: Q^T, Q an orthonormal basis of range(R); row i of Q
                                  // at Qt + i * ld (ld as U), zero past the kept count

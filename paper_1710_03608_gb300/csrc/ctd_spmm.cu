@@ -14,53 +14,13 @@
 #include <vector>
 
 #include "ctd_internal.cuh"
+#include "ctd_expand.cuh"
 
 namespace ctd {
 
 constexpr int WARP_MODE_MAX_WIDTH = 1024;  // accumulator per warp
 constexpr int CTA_MODE_MAX_WIDTH = 24576;  // accumulator per block
 constexpr int SPMM_THREADS = 256;
-
-// Expand 32 column entries (one per lane) into their R-row work items and
-// apply fn(m, product) to every item.  Lanes without an entry pass rlen=0.
-template <typename Fn>
-__device__ __forceinline__ void expand_chunk(unsigned long long rstart, int rlen, int v,
-                                             const int32_t* __restrict__ rcol,
-                                             const int32_t* __restrict__ rval, Fn fn) {
-  const int lane = threadIdx.x & 31;
-  int incl = rlen;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const int total = __shfl_sync(0xffffffffu, incl, 31);
-  const int excl = incl - rlen;
-  for (int base = 0; base < total; base += 32) {
-    const int t = base + lane;
-    // owner = smallest lane with incl > t
-    int lo = 0, hi = 31;
-#pragma unroll
-    for (int it = 0; it < 5; ++it) {
-      const int mid = (lo + hi) >> 1;
-      const int im = __shfl_sync(0xffffffffu, incl, mid);
-      if (im > t)
-        hi = mid;
-      else
-        lo = mid + 1;
-    }
-    const int owner = lo;
-    const unsigned long long os = __shfl_sync(0xffffffffu, rstart, owner);
-    const int oe = __shfl_sync(0xffffffffu, excl, owner);
-    const int ov = __shfl_sync(0xffffffffu, v, owner);
-    if (t < total) {
-      const unsigned long long q = os + (unsigned long long)(t - oe);
-      const int m = __ldg(rcol + q);
-      const long long prod = (long long)ov * (long long)__ldg(rval + q);
-      fn(m, prod);
-    }
-  }
-}
 
 // Accumulate R^T x_f for column f into acc/bitmap; warps of the group
 // [gwarp0, gwarp0 + gwarps) take interleaved 32-entry chunks.
@@ -379,6 +339,15 @@ __global__ void k_list_columns(const unsigned long long* __restrict__ colptr,
   }
 }
 
+void launch_list_columns(const uint64_t* colptr, const uint64_t* coff, int64_t n_cols,
+                         uint64_t minc, int64_t* list, unsigned* count, cudaStream_t st) {
+  if (n_cols <= 0) return;
+  CTD_LAUNCH(k_list_columns, (grid_for(n_cols, 256, (int64_t)num_sms() * 8)), (256), 0, st,
+             reinterpret_cast<const unsigned long long*>(colptr),
+             reinterpret_cast<const unsigned long long*>(coff), n_cols,
+             (unsigned long long)minc, list, count);
+}
+
 template <typename V, typename A>
 static ctd_status c_fill_impl(const CscDev& X, int64_t n_cols, const CsrDev& R,
                               const uint64_t* coff, uint32_t* ccnt, uint16_t* crow, V* cval,
@@ -421,15 +390,19 @@ static ctd_status c_fill_impl(const CscDev& X, int64_t n_cols, const CsrDev& R,
   return CTD_OK;
 }
 
-ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, const CsrDev& R, const uint64_t* coff,
-                         uint32_t* ccnt, uint16_t* crow, void* cval, int fp32, int positive,
-                         uint64_t sqnorm_X, cudaStream_t st) {
+ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
+                         const uint64_t* coff, uint32_t* ccnt, uint16_t* crow, void* cval,
+                         int fp32, int positive, uint64_t sqnorm_X, cudaStream_t st) {
   if (n_cols <= 0) return CTD_OK;
   if (R.width <= 0) {
     CTD_CUDA(cudaMemsetAsync(ccnt, 0, n_cols * sizeof(uint32_t), st));
     return CTD_OK;
   }
   if (R.width > 65535) return fail(CTD_EINVAL, "too many kept fibers for 16-bit row indices");
+  // integer partial sums fit int32 (Cauchy-Schwarz) and the warp's register
+  // accumulators cover the width: dense long rows + registers
+  if (sqnorm_X < (1ull << 31) && R.width <= 1024)
+    return c_fill_dense_rows(X, n_cols, n_rows, R, coff, ccnt, crow, cval, fp32, positive, st);
   unsigned long long* work;
   int64_t* heavy;
   unsigned* nheavy;
@@ -538,7 +511,8 @@ __global__ void k_q_rownorms(const T* __restrict__ Q, int64_t n_rows, int qs,
 }
 
 // One warp per column, 32 columns per grab.  Hot rows of Q (slot >= 0 in
-// `slot_of`) are staged in shared memory once per block.  Lane l owns the
+// `slot_of`, a global table read through the read-only cache) are staged
+// in shared memory once per block.  Lane l owns the
 // VEC consecutive Q columns at (l + 32 k) * VEC, read with 16-byte loads;
 // a column's entries are loaded 32 at a time and broadcast by shuffles.
 // Each 32-column chunk's sum goes to partial[chunk] (fixed order inside
@@ -556,8 +530,10 @@ struct Vec16<double> {
   static constexpr int n = 2;
 };
 
+constexpr int QF_THREADS = 512;
+
 template <typename T, int NK>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(QF_THREADS)
     k_qform(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs, int nblk,
             const double* __restrict__ qn, const short* __restrict__ slot_of,
             const int* __restrict__ hot_rows, int n_hot, int64_t n_rows,
@@ -565,14 +541,9 @@ __global__ void __launch_bounds__(256)
   using VT = typename Vec16<T>::type;
   constexpr int VEC = Vec16<T>::n;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* Qs = reinterpret_cast<T*>(smraw);                                   // [n_hot][qs]
-  short* slot = reinterpret_cast<short*>(smraw + (size_t)n_hot * qs * sizeof(T));  // [n_rows]
+  T* Qs = reinterpret_cast<T*>(smraw);  // [n_hot][qs]
   for (int64_t e = threadIdx.x; e < (int64_t)n_hot * qs; e += blockDim.x)
     Qs[e] = Q[(int64_t)hot_rows[e / qs] * qs + (e % qs)];
-  if (slot_of)
-    for (int64_t e = threadIdx.x; e < n_rows; e += blockDim.x) slot[e] = slot_of[e];
-  else
-    slot = nullptr;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(X.colptr);
@@ -594,11 +565,13 @@ __global__ void __launch_bounds__(256)
         lb = la;  // done
       }
     }
-    const int nf = (int)min((int64_t)32, n_cols - (int64_t)f0);
-    for (int e = 0; e < nf; ++e) {
+    // columns with two or more nonzeros, one at a time
+    unsigned todo = __ballot_sync(0xffffffffu, lb > la);
+    while (todo) {
+      const int e = __ffs(todo) - 1;
+      todo &= todo - 1;
       const unsigned long long a = __shfl_sync(0xffffffffu, la, e);
       const unsigned long long b = __shfl_sync(0xffffffffu, lb, e);
-      if (b <= a) continue;
       double ss = 0.0;
       for (int cb = 0; cb < nblk; ++cb) {  // column blocks of NK * 32 * VEC
       const int64_t coff = (int64_t)cb * NK * 32 * VEC;
@@ -612,7 +585,7 @@ __global__ void __launch_bounds__(256)
         if (lane < cnt) {
           const int i = __ldg(X.row + base + lane);
           myv = __ldg(X.val + base + lane);
-          const int sl = slot ? slot[i] : -1;
+          const int sl = slot_of ? (int)__ldg(slot_of + i) : -1;
           myrow = sl >= 0 ? Qs + (int64_t)sl * qs : Q + (int64_t)i * qs + coff;
         }
         int q = 0;
@@ -681,14 +654,14 @@ static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int 
                                const double* qn, const short* slot_of, const int* hot, int n_hot,
                                int64_t n_rows, unsigned long long* work, double* partial,
                                cudaStream_t st) {
-  const size_t smem =
-      (size_t)n_hot * qs * sizeof(T) + (slot_of ? (size_t)n_rows * sizeof(short) : 0);
+  const size_t smem = (size_t)n_hot * qs * sizeof(T);
   if (smem > 48 * 1024)
     CTD_TRY(allow_max_smem((const void*)k_qform<T, NK>));
   int per_sm = 0;
-  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qform<T, NK>, 256, smem));
+  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qform<T, NK>, QF_THREADS,
+                                                         smem));
   if (per_sm < 1) return fail(CTD_ECUDA, "error kernel does not fit on an SM");
-  CTD_LAUNCH((k_qform<T, NK>), (num_sms() * per_sm), (256), smem, st, X, n_cols, Q, qs, nblk,
+  CTD_LAUNCH((k_qform<T, NK>), (num_sms() * per_sm), (QF_THREADS), smem, st, X, n_cols, Q, qs, nblk,
              qn, slot_of, hot, n_hot, n_rows, work, partial);
   return CTD_OK;
 }
@@ -741,13 +714,10 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
   CTD_TRY(scratch.get(&slot_of, n_rows));
   CTD_TRY(scratch.get(&work, 1));
   CTD_TRY(scratch.get(&partial, nchunks));
-  // hot rows: as many as fit next to the slot table in ~48 KB of shared
-  // memory, so four blocks (32 warps) stay resident per SM
-  const size_t budget = 48 * 1024;
-  const size_t table = (size_t)n_rows * sizeof(short);
-  int n_hot = 0;
-  if (table < budget) n_hot = (int)std::min<size_t>((budget - table) / ((size_t)qs * tsz), n_hot_req);
-  n_hot = std::max(n_hot, 0);
+  // hot rows: as many as fit in ~100 KB of shared memory, so two blocks of
+  // 16 warps stay resident per SM
+  const size_t budget = 100 * 1024;
+  int n_hot = (int)std::min<size_t>(budget / ((size_t)qs * tsz), (size_t)std::max(n_hot_req, 0));
   CTD_TRY(scratch.get(&hot, std::max(n_hot, 1)));
   std::vector<short> slots(n_rows, (short)-1);
   for (int q = 0; q < n_hot; ++q) slots[hot_rows_host[q]] = (short)q;

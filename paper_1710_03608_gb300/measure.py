@@ -103,7 +103,8 @@ def batched(args):
     _sync()
     t_batch = time.perf_counter() - t0
     errs_batch = [F.error() for F in Fs]
-    same = all(a == b for a, b in zip(errs_plain, errs_batch))
+    # integer stages are bit-exact; the FP32 error sum may differ in its last bits
+    same = all(abs(a - b) <= 1e-6 * max(abs(b), 1e-6) for a, b in zip(errs_plain, errs_batch))
     line = {"workload": f"{len(specs)} uneven CTD-S traffic tensors (batch law of the 256-tensor "
                         f"workload), {nnz} nonzeros", "nnz": nnz, "generation_s": gen_s,
             "plain": {"seconds": t_plain, "nnz_per_s": nnz / t_plain},
@@ -170,6 +171,7 @@ def Request_slice(r, dims2):
 def stream(args):
     st = synth.traffic_stream_20k(scale=args.scale, steps=args.steps)
     G = ctd.Dynamic(st.dims2, 1, ctd.CTD_FP32_BULK, 0, 0, ctd.CTD_KEEP_LAST_C)
+    ctd.profile(True)
     per = []
     tot_nnz, tot_s = 0, 0.0
     for t in range(args.steps):
@@ -188,7 +190,7 @@ def stream(args):
     line = {"workload": f"CTD-D stream of {args.steps} slices {st.dims2[0]}x{st.dims2[1]}, "
                         f"{st.nnz} nonzeros each, d = {args.d}",
             "nnz_per_s": tot_nnz / tot_s, "seconds": tot_s, "final_d": int(G.sizes().s_kept),
-            "rel_error": G.error(), "steps": per}
+            "rel_error": G.error(), "phases_ms": ctd.profile_report()["phases"], "steps": per}
     print(json.dumps(line), flush=True)
 
 

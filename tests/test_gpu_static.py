@@ -99,6 +99,29 @@ def test_traffic_scaled_full(precision):
     check(F, ref, 1e-6, precision, err_ref=O.projection_error(ref.X, ref.R))
 
 
+@pytest.mark.parametrize("case", ["int64_sums", "wide_registers", "wider_than_registers"])
+def test_c_fill_paths(case):
+    """Each C = R^T X path against the oracle: partial sums beyond int32
+    (||X||_F^2 >= 2^31), s~ in (512, 1024] (the widest register layout) and
+    s~ > 1024 (shared-memory accumulators only)."""
+    if case == "int64_sums":
+        coo, s = synth.tiny((60, 40, 10), 3000, seed=31, vmax=100_000), 300
+    elif case == "wide_registers":
+        coo, s = synth.tiny((900, 600, 2), 15_000, seed=32, vmax=5), 2000
+    else:
+        coo, s = synth.tiny((1200, 800, 2), 20_000, seed=33, vmax=5), 4000
+    F = run(coo, 1, s, 1e-6, 5, 0)
+    ref = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, s, 1e-6, 5)
+    kept = ref.R.shape[1]
+    if case == "int64_sums":
+        assert F.sizes().sqnorm_X >= 2 ** 31
+    elif case == "wide_registers":
+        assert 512 < kept <= 1024
+    else:
+        assert kept > 1024
+    check(F, ref, 1e-6, 0, err_ref=O.projection_error(ref.X, ref.R))
+
+
 def test_edge_all_zero():
     coo = synth.tiny((5, 4, 3), 10, seed=1)
     coo.val[:] = 0
