@@ -26,7 +26,7 @@ namespace ctd {
 
 namespace {
 
-constexpr int CF_THREADS = 256;
+constexpr int CF_THREADS = 1024;  // one block per SM shares one copy of the dense rows
 constexpr int CF_HEAVY_COL = 128;  // columns with at least this many nonzeros: one block each
 constexpr int CF_LONG_ROW = 16;    // sparse rows at least this long: walked by the whole warp
 constexpr int CF_MAX_DENSE = 64;   // dense rows at most
@@ -148,8 +148,19 @@ __device__ __forceinline__ void accumulate_reg(const CscDev& X, const CsrDev& R,
       const unsigned long long s0 = __shfl_sync(0xffffffffu, rs, src);
       const int n = __shfl_sync(0xffffffffu, rl, src);
       const int vs = __shfl_sync(0xffffffffu, v, src);
-      for (int q = lane; q < n; q += 32)
-        atomicAdd(acc + __ldg(R.col + s0 + q), vs * __ldg(R.val + s0 + q));
+      // four loads in flight per lane before the atomics
+      int q = lane;
+      for (; q + 96 < n; q += 128) {
+        int c4[4], v4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          c4[u] = __ldg(R.col + s0 + q + 32 * u);
+          v4[u] = __ldg(R.val + s0 + q + 32 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) atomicAdd(acc + c4[u], vs * v4[u]);
+      }
+      for (; q < n; q += 32) atomicAdd(acc + __ldg(R.col + s0 + q), vs * __ldg(R.val + s0 + q));
     }
     if (rl >= CF_LONG_ROW) rl = 0;
     if (__any_sync(0xffffffffu, rl > 0))
@@ -198,7 +209,7 @@ __device__ __forceinline__ unsigned emit_reg(int* acc, int (&regs)[4 * NQ], unsi
 // copied.  Columns are taken 32 at a time from a global counter; lane l
 // prefetches column f0 + l's metadata.
 template <typename V, int NQ>
-__global__ void __launch_bounds__(CF_THREADS)
+__global__ void __launch_bounds__(CF_THREADS, 1)
     k_cf_warp(CscDev X, int64_t n_cols, CsrDev R, Dense dn,
               const unsigned long long* __restrict__ coff, unsigned* __restrict__ ccnt,
               uint16_t* __restrict__ crow, V* __restrict__ cval, int positive,
@@ -249,7 +260,22 @@ __global__ void __launch_bounds__(CF_THREADS)
         const unsigned long long rse = __shfl_sync(0xffffffffu, rs, e);
         const int rle = __shfl_sync(0xffffffffu, rl, e);
         const int ve = __shfl_sync(0xffffffffu, vv, e);
-        for (int q = lane; q < rle; q += 32) {
+        // a copy of R's row: four loads in flight per lane before the stores
+        int q = lane;
+        for (; q + 96 < rle; q += 128) {
+          int c4[4], v4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            c4[u] = __ldg(R.col + rse + q + 32 * u);
+            v4[u] = __ldg(R.val + rse + q + 32 * u);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            crow[oe + q + 32 * u] = (uint16_t)c4[u];
+            cval[oe + q + 32 * u] = (V)(ve * v4[u]);
+          }
+        }
+        for (; q < rle; q += 32) {
           crow[oe + q] = (uint16_t)__ldg(R.col + rse + q);
           cval[oe + q] = (V)(ve * __ldg(R.val + rse + q));
         }
@@ -267,7 +293,7 @@ __global__ void __launch_bounds__(CF_THREADS)
 
 // One block per column with at least CF_HEAVY_COL nonzeros (from `list`).
 template <typename V, int NQ>
-__global__ void __launch_bounds__(CF_THREADS)
+__global__ void __launch_bounds__(CF_THREADS, 1)
     k_cf_block(CscDev X, const int64_t* __restrict__ list, const unsigned* __restrict__ nlist,
                CsrDev R, Dense dn, const unsigned long long* __restrict__ coff,
                unsigned* __restrict__ ccnt, uint16_t* __restrict__ crow, V* __restrict__ cval,
@@ -390,8 +416,8 @@ ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, co
   const int nq = nq0 <= 1 ? 1 : nq0 <= 2 ? 2 : nq0 <= 4 ? 4 : 8;
   const int W = nq * 128;
   const size_t row_b = (size_t)W * sizeof(int);
-  // two blocks of 8 warps per SM: dense rows + 8 warp accumulators in ~113 KB
-  const int budget = 113 * 1024;
+  // one block of 32 warps per SM: dense rows + 32 warp accumulators in ~220 KB
+  const int budget = 220 * 1024;
   int hmax = (int)(budget / (int64_t)row_b) - CF_THREADS / 32;
   hmax = std::max(0, std::min(hmax, CF_MAX_DENSE));
   const int minlen = std::max(16, 16 * nq);  // shorter rows are cheaper walked sparsely

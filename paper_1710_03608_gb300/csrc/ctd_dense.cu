@@ -269,56 +269,59 @@ __global__ void __launch_bounds__(256)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
     const int nb = (int)min((int64_t)NB, n - k0);
-    // --- A: the diagonal block, in order, by block 0.  Decisions and
-    // pivots use shared memory only; they are stored after the loop.
+    // --- A: the diagonal block, in order, by warp 0 of block 0.  Lane r
+    // holds row r in registers; column c is finished left-looking (its
+    // entries reduced by the earlier columns, row c's values broadcast by
+    // shuffles), then decided and scaled.  No block barriers inside.
     if (blockIdx.x == 0) {
-      for (int e = tid; e < NB * NB; e += blockDim.x) {
-        const int r = e % NB, c = e / NB;
-        D[r][c] = (r < nb && c <= r) ? A[(k0 + r) + (k0 + c) * lda] : 0.0;
-      }
       if (tid < nb) {
         thr_s[tid] = thr[k0 + tid];
         force_s[tid] = force ? force[k0 + tid] : -1;
         fpiv_s[tid] = fpiv ? fpiv[k0 + tid] : 0.0;
       }
       __syncthreads();
-      for (int c = 0; c < nb; ++c) {
-        if (tid == 0) {
-          double d = D[c][c];
-          int k = (d > thr_s[c] && d > 0.0) ? 1 : 0;
-          if (force_s[c] >= 0) k = force_s[c];
-          // a keep forced by the explicit residual takes that residual's
-          // squared norm as its pivot (the Gram-based one lost it to rounding)
-          if (force_s[c] == 1 && fpiv_s[c] > 0.0) d = fpiv_s[c];
-          if (k && !(d > 0.0)) {
-            atomicOr(status, DEV_CAPACITY);
-            k = 0;
+      if (warp == 0) {
+        double row[NB];
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+          row[c] = (lane < nb && c <= lane) ? A[(k0 + lane) + (k0 + c) * lda] : 0.0;
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          if (c < nb) {
+            double sred = row[c];
+#pragma unroll
+            for (int q = 0; q < c; ++q)
+              sred = fma(-row[q], __shfl_sync(0xffffffffu, row[q], c), sred);
+            double d = __shfl_sync(0xffffffffu, sred, c);
+            int k = (d > thr_s[c] && d > 0.0) ? 1 : 0;
+            if (force_s[c] >= 0) k = force_s[c];
+            // a keep forced by the explicit residual takes that residual's
+            // squared norm as its pivot (the Gram-based one lost it to rounding)
+            if (force_s[c] == 1 && fpiv_s[c] > 0.0) d = fpiv_s[c];
+            if (k && !(d > 0.0)) {
+              if (lane == 0) atomicOr(status, DEV_CAPACITY);
+              k = 0;
+            }
+            const double l = k ? sqrt(d) : 0.0;
+            const double inv = k ? 1.0 / l : 0.0;
+            if (lane == c)
+              row[c] = l;
+            else if (lane > c)
+              row[c] = sred * inv;
+            if (lane == 0) {
+              kp[c] = k;
+              piv_s[c] = d;
+            }
           }
-          kp[c] = k;
-          piv_s[c] = d;
-          const double l = k ? sqrt(d) : 0.0;
-          D[c][c] = l;
-          invd[c] = k ? 1.0 / l : 0.0;
         }
-        __syncthreads();
-        const int k = kp[c];
-        if (tid > c && tid < nb) D[tid][c] = k ? D[tid][c] * invd[c] : 0.0;
-        __syncthreads();
-        if (k) {  // trailing update inside the block: pairs c < j <= r < nb
-          for (int e = tid; e < NB * NB; e += blockDim.x) {
-            const int r = e % NB, j = e / NB;
-            if (j > c && j <= r && r < nb) D[r][j] = fma(-D[r][c], D[j][c], D[r][j]);
-          }
-          __syncthreads();
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+          if (lane < nb && c <= lane) A[(k0 + lane) + (k0 + c) * lda] = row[c];
+        __syncwarp();
+        if (lane < nb) {
+          keep[k0 + lane] = kp[lane];
+          if (piv) piv[k0 + lane] = piv_s[lane];
         }
-      }
-      for (int e = tid; e < NB * NB; e += blockDim.x) {
-        const int r = e % NB, c = e / NB;
-        if (r < nb && c <= r) A[(k0 + r) + (k0 + c) * lda] = D[r][c];
-      }
-      if (tid < nb) {
-        keep[k0 + tid] = kp[tid];
-        if (piv) piv[k0 + tid] = piv_s[tid];
       }
       __threadfence();
     }
@@ -493,33 +496,37 @@ void u_from_linv(const double* Z, int64_t n, int64_t ldz, double* U, int64_t ldu
 // the independence test needs: pivots ||x||^2 - ||L^{-1} R^T x||^2 then carry
 // errors of order n u ||x||^2, not kappa(L) u ||x||^2.
 // ---------------------------------------------------------------------------
+// One warp per right-hand side: lane r holds x_r of the 32-row block; once
+// x_r is known (lane r), it is broadcast and every lane below subtracts its
+// share (right-looking), so a column costs 32 FP64 multiply-adds per lane and
+// the reciprocal diagonal is formed once per block.  (A thread per column
+// left most SMs idle: GB300's FP64 pipe is narrow, so the work must spread.)
 __global__ void k_trsm_diag(const double* __restrict__ L, int64_t ldl, int64_t n, int64_t k0,
                             double* __restrict__ B, int64_t ldb, int64_t nrhs) {
   __shared__ double Ls[NB][NB + 1];
+  __shared__ double inv[NB];
   const int nb = (int)min((int64_t)NB, n - k0);
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int r = e % NB, c = e / NB;
     Ls[r][c] = (r < nb && c <= r) ? L[(k0 + r) + (k0 + c) * ldl] : 0.0;
   }
   __syncthreads();
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (threadIdx.x < NB) inv[threadIdx.x] = threadIdx.x < nb ? 1.0 / Ls[threadIdx.x][threadIdx.x] : 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (j >= nrhs) return;
-  double x[NB];
   double* col = B + j * ldb + k0;
-#pragma unroll
-  for (int r = 0; r < NB; ++r) x[r] = r < nb ? col[r] : 0.0;
+  double x = lane < nb ? col[lane] : 0.0;
 #pragma unroll
   for (int r = 0; r < NB; ++r) {
     if (r < nb) {
-      double s = x[r];
-#pragma unroll
-      for (int c = 0; c < r; ++c) s = fma(-Ls[r][c], x[c], s);
-      x[r] = s / Ls[r][r];
+      const double xr = __shfl_sync(0xffffffffu, x * inv[r], r);
+      if (lane == r) x = xr;
+      else if (lane > r) x = fma(-Ls[lane][r], xr, x);
     }
   }
-#pragma unroll
-  for (int r = 0; r < NB; ++r)
-    if (r < nb) col[r] = x[r];
+  if (lane < nb) col[lane] = x;
 }
 
 void tri_solve_lower(const double* L, int64_t ldl, int64_t n, double* B, int64_t ldb, int64_t nrhs,
@@ -527,7 +534,7 @@ void tri_solve_lower(const double* L, int64_t ldl, int64_t n, double* B, int64_t
   if (n <= 0 || nrhs <= 0) return;
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
     const int64_t nb = std::min<int64_t>(NB, n - k0);
-    CTD_LAUNCH(k_trsm_diag, ((unsigned)((nrhs + 127) / 128)), (128), 0, st, L, ldl, n, k0, B, ldb,
+    CTD_LAUNCH(k_trsm_diag, ((unsigned)((nrhs + 7) / 8)), (256), 0, st, L, ldl, n, k0, B, ldb,
                nrhs);
     const int64_t rest = n - k0 - nb;
     if (rest > 0)
@@ -537,34 +544,34 @@ void tri_solve_lower(const double* L, int64_t ldl, int64_t n, double* B, int64_t
 }
 
 // B <- L^{-T} B (backward substitution with the transpose of lower L).
+// Backward substitution on one 32-row block with L^T, a warp per right-hand
+// side (lane r holds x_r; rows are finished from the bottom up).
 __global__ void k_trsm_diag_T(const double* __restrict__ L, int64_t ldl, int64_t n, int64_t k0,
                               double* __restrict__ B, int64_t ldb, int64_t nrhs) {
   __shared__ double Ls[NB][NB + 1];
+  __shared__ double inv[NB];
   const int nb = (int)min((int64_t)NB, n - k0);
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int r = e % NB, c = e / NB;
     Ls[r][c] = (r < nb && c <= r) ? L[(k0 + r) + (k0 + c) * ldl] : 0.0;
   }
   __syncthreads();
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (threadIdx.x < NB) inv[threadIdx.x] = threadIdx.x < nb ? 1.0 / Ls[threadIdx.x][threadIdx.x] : 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (j >= nrhs) return;
-  double x[NB];
   double* col = B + j * ldb + k0;
-#pragma unroll
-  for (int r = 0; r < NB; ++r) x[r] = r < nb ? col[r] : 0.0;
+  double x = lane < nb ? col[lane] : 0.0;
 #pragma unroll
   for (int r = NB - 1; r >= 0; --r) {
     if (r < nb) {
-      double s = x[r];
-#pragma unroll
-      for (int c = r + 1; c < NB; ++c)
-        if (c < nb) s = fma(-Ls[c][r], x[c], s);
-      x[r] = s / Ls[r][r];
+      const double xr = __shfl_sync(0xffffffffu, x * inv[r], r);
+      if (lane == r) x = xr;
+      else if (lane < r) x = fma(-Ls[r][lane], xr, x);
     }
   }
-#pragma unroll
-  for (int r = 0; r < NB; ++r)
-    if (r < nb) col[r] = x[r];
+  if (lane < nb) col[lane] = x;
 }
 
 void tri_solve_lower_T(const double* L, int64_t ldl, int64_t n, double* B, int64_t ldb,
@@ -573,7 +580,7 @@ void tri_solve_lower_T(const double* L, int64_t ldl, int64_t n, double* B, int64
   const int64_t last = ((n - 1) / NB) * NB;
   for (int64_t k0 = last; k0 >= 0; k0 -= NB) {
     const int64_t nb = std::min<int64_t>(NB, n - k0);
-    CTD_LAUNCH(k_trsm_diag_T, ((unsigned)((nrhs + 127) / 128)), (128), 0, st, L, ldl, n, k0, B,
+    CTD_LAUNCH(k_trsm_diag_T, ((unsigned)((nrhs + 7) / 8)), (256), 0, st, L, ldl, n, k0, B,
                ldb, nrhs);
     if (k0 > 0)  // B[0:k0] -= L[k0:k0+nb, 0:k0]^T B[k0:k0+nb]
       dgemm(true, false, k0, nrhs, nb, -1.0, L + k0, ldl, B + k0, ldb, 1.0, B, ldb, st);

@@ -495,7 +495,7 @@ __global__ void k_build_q(CsrDev R, int64_t n_rows, const double* __restrict__ Z
 // qn[i] = ||Q(i, :)||^2 of the stored (rounded) rows
 template <typename T>
 __global__ void k_q_rownorms(const T* __restrict__ Q, int64_t n_rows, int qs,
-                             double* __restrict__ qn) {
+                             T* __restrict__ qn) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -506,7 +506,7 @@ __global__ void k_q_rownorms(const T* __restrict__ Q, int64_t n_rows, int qs,
       nrm = fma(v, v, nrm);
     }
     for (int o = 16; o; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-    if (lane == 0) qn[i] = nrm;
+    if (lane == 0) qn[i] = (T)nrm;
   }
 }
 
@@ -533,9 +533,9 @@ struct Vec16<double> {
 constexpr int QF_THREADS = 512;
 
 template <typename T, int NK>
-__global__ void __launch_bounds__(QF_THREADS)
+__global__ void __launch_bounds__(QF_THREADS, (NK * Vec16<T>::n >= 16 ? 1 : 2))
     k_qform(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs, int nblk,
-            const double* __restrict__ qn, const short* __restrict__ slot_of,
+            const T* __restrict__ qn, const short* __restrict__ slot_of,
             const int* __restrict__ hot_rows, int n_hot, int64_t n_rows,
             unsigned long long* work, double* __restrict__ partial) {
   using VT = typename Vec16<T>::type;
@@ -555,12 +555,12 @@ __global__ void __launch_bounds__(QF_THREADS)
     // lane l: column f0 + l's range; a one-nonzero column is settled here
     const int64_t fl = (int64_t)f0 + lane;
     unsigned long long la = 0, lb = 0;
-    double total = 0.0;
+    T total = (T)0;  // this lane's column; FP32 sums on the FP32 path (GB300's FP64 pipe is narrow)
     if (fl < n_cols) {
       la = xp[fl];
       lb = xp[fl + 1];
       if (lb == la + 1) {
-        const double v = (double)X.val[la];
+        const T v = (T)X.val[la];
         total = v * v * qn[X.row[la]];
         lb = la;  // done
       }
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(QF_THREADS)
       todo &= todo - 1;
       const unsigned long long a = __shfl_sync(0xffffffffu, la, e);
       const unsigned long long b = __shfl_sync(0xffffffffu, lb, e);
-      double ss = 0.0;
+      T ss = (T)0;
       for (int cb = 0; cb < nblk; ++cb) {  // column blocks of NK * 32 * VEC
       const int64_t coff = (int64_t)cb * NK * 32 * VEC;
       T acc[NK * VEC];
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(QF_THREADS)
           const int i = __ldg(X.row + base + lane);
           myv = __ldg(X.val + base + lane);
           const int sl = slot_of ? (int)__ldg(slot_of + i) : -1;
-          myrow = sl >= 0 ? Qs + (int64_t)sl * qs : Q + (int64_t)i * qs + coff;
+          myrow = (sl >= 0 ? Qs + (int64_t)sl * qs : Q + (int64_t)i * qs) + coff;
         }
         int q = 0;
         for (; q + 1 < cnt; q += 2) {
@@ -624,13 +624,31 @@ __global__ void __launch_bounds__(QF_THREADS)
         }
       }
 #pragma unroll
-      for (int k = 0; k < NK * VEC; ++k) ss = fma((double)acc[k], (double)acc[k], ss);
+      for (int k = 0; k < NK * VEC; ++k) ss = fma(acc[k], acc[k], ss);
       }
       for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
       if (lane == e) total += ss;  // lane e owns column f0 + e
     }
     for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
-    if (lane == 0) partial[f0 / 32] = total;
+    if (lane == 0) partial[f0 / 32] = (double)total;
+  }
+}
+
+// fixed-order two-level sum: block b adds its contiguous range of `in`
+// (FP64 adds spread over many SMs: GB300's FP64 pipe is narrow)
+__global__ void k_sum_f64_ranges(const double* __restrict__ in, int64_t n, int64_t per,
+                                 double* __restrict__ out) {
+  __shared__ double part[32];
+  const int64_t a = (int64_t)blockIdx.x * per, b = min(n, a + per);
+  double acc = 0.0;
+  for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) acc += in[e];
+  for (int w = 16; w; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    out[blockIdx.x] = t;
   }
 }
 
@@ -649,9 +667,25 @@ __global__ void k_sum_f64_fixed(const double* __restrict__ in, int64_t n, double
   }
 }
 
+// *out = sum of n doubles, in an order fixed by n alone
+static ctd_status sum_f64(const double* in, int64_t n, double* out, Arena& scratch,
+                          cudaStream_t st) {
+  if (n <= 8192) {
+    CTD_LAUNCH(k_sum_f64_fixed, (1), (1024), 0, st, in, n, out);
+    return CTD_OK;
+  }
+  const int64_t nb = std::min<int64_t>(num_sms() * 2, (n + 1023) / 1024);
+  const int64_t per = (n + nb - 1) / nb;
+  double* mid;
+  CTD_TRY(scratch.get(&mid, nb));
+  CTD_LAUNCH(k_sum_f64_ranges, ((unsigned)nb), (256), 0, st, in, n, per, mid);
+  CTD_LAUNCH(k_sum_f64_fixed, (1), (1024), 0, st, mid, nb, out);
+  return CTD_OK;
+}
+
 template <typename T, int NK>
 static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int qs, int nblk,
-                               const double* qn, const short* slot_of, const int* hot, int n_hot,
+                               const T* qn, const short* slot_of, const int* hot, int n_hot,
                                int64_t n_rows, unsigned long long* work, double* partial,
                                cudaStream_t st) {
   const size_t smem = (size_t)n_hot * qs * sizeof(T);
@@ -675,7 +709,7 @@ ctd_status launch_qform_rows(const CscDev& X, int64_t n_cols, const double* Q, i
   CTD_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
   if (width <= 0 || n_cols <= 0) return CTD_OK;
   if (ld % 512 != 0 || ld < width) return fail(CTD_EINVAL, "Q row stride must be a multiple of 512");
-  const int nblk = (int)((width + 511) / 512);
+  const int nblk = (int)((width + 255) / 256);  // 256 columns (4 loads per lane) per block
   unsigned long long* work;
   double* partial;
   const int64_t nchunks = (n_cols + 31) / 32;
@@ -683,9 +717,9 @@ ctd_status launch_qform_rows(const CscDev& X, int64_t n_cols, const double* Q, i
   CTD_TRY(scratch.get(&partial, nchunks));
   CTD_CUDA(cudaMemsetAsync(work, 0, 8, st));
   CTD_CUDA(cudaMemsetAsync(partial, 0, nchunks * sizeof(double), st));
-  CTD_TRY((qform_launch<double, 8>(X, n_cols, Q, (int)ld, nblk, qn, nullptr, nullptr, 0, n_rows,
+  CTD_TRY((qform_launch<double, 4>(X, n_cols, Q, (int)ld, nblk, qn, nullptr, nullptr, 0, n_rows,
                                    work, partial, st)));
-  CTD_LAUNCH(k_sum_f64_fixed, (1), (1024), 0, st, partial, nchunks, out);
+  CTD_TRY(sum_f64(partial, nchunks, out, scratch, st));
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
@@ -700,24 +734,30 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
   const size_t tsz = fp32 ? 4 : 8;
   const int span = 32 * (16 / (int)tsz);        // columns per 16-byte load across a warp
   int NK = (R.width + span - 1) / span;
-  if (NK > 8) return fail(CTD_ENOTSUP, "error kernel limited to s~ <= 1024 (FP32) / 512 (FP64)");
+  int nblk = 1;
+  if (NK > 8) {  // wider than one register block: column blocks of 8 loads per lane
+    nblk = (NK + 7) / 8;
+    NK = 8;
+  }
   NK = NK <= 1 ? 1 : NK <= 2 ? 2 : NK <= 4 ? 4 : 8;  // the kernel's compiled widths
-  const int qs = NK * span;                     // each Q row holds exactly NK loads per lane
-  void* Q;
-  double *qn, *partial;
+  const int qs = nblk * NK * span;              // each Q row holds exactly NK loads per lane per block
+  void *Q, *qn;
+  double* partial;
   short* slot_of;
   int* hot;
   unsigned long long* work;
   const int64_t nchunks = (n_cols + 31) / 32;
   CTD_TRY(scratch.get(reinterpret_cast<unsigned char**>(&Q), (size_t)n_rows * qs * tsz));
-  CTD_TRY(scratch.get(&qn, n_rows));
+  CTD_TRY(scratch.get(reinterpret_cast<unsigned char**>(&qn), (size_t)n_rows * tsz));
   CTD_TRY(scratch.get(&slot_of, n_rows));
   CTD_TRY(scratch.get(&work, 1));
   CTD_TRY(scratch.get(&partial, nchunks));
-  // hot rows: as many as fit in ~100 KB of shared memory, so two blocks of
-  // 16 warps stay resident per SM
+  // hot rows (one register block wide only): as many as fit in ~100 KB of
+  // shared memory, so two blocks of 16 warps stay resident per SM
   const size_t budget = 100 * 1024;
-  int n_hot = (int)std::min<size_t>(budget / ((size_t)qs * tsz), (size_t)std::max(n_hot_req, 0));
+  int n_hot = nblk == 1 ? (int)std::min<size_t>(budget / ((size_t)qs * tsz),
+                                                (size_t)std::max(n_hot_req, 0))
+                        : 0;
   CTD_TRY(scratch.get(&hot, std::max(n_hot, 1)));
   std::vector<short> slots(n_rows, (short)-1);
   for (int q = 0; q < n_hot; ++q) slots[hot_rows_host[q]] = (short)q;
@@ -732,19 +772,21 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
     CTD_LAUNCH(k_build_q<float>, (gq), (256), 0, st, R, n_rows, Z, ldz, qs,
                static_cast<float*>(Q));
     CTD_LAUNCH(k_q_rownorms<float>, (gn), (256), 0, st, static_cast<const float*>(Q), n_rows, qs,
-               qn);
+               static_cast<float*>(qn));
   } else {
     CTD_LAUNCH(k_build_q<double>, (gq), (256), 0, st, R, n_rows, Z, ldz, qs,
                static_cast<double*>(Q));
     CTD_LAUNCH(k_q_rownorms<double>, (gn), (256), 0, st, static_cast<const double*>(Q), n_rows,
-               qs, qn);
+               qs, static_cast<double*>(qn));
   }
   ctd_status rc;
-#define QF(NKV)                                                                                  \
-  rc = fp32 ? qform_launch<float, NKV>(X, n_cols, static_cast<const float*>(Q), qs, 1, qn,     \
-                                       slot_of, hot, n_hot, n_rows, work, partial, st)           \
-            : qform_launch<double, NKV>(X, n_cols, static_cast<const double*>(Q), qs, 1, qn,     \
-                                        slot_of, hot, n_hot, n_rows, work, partial, st)
+#define QF(NKV)                                                                                 \
+  rc = fp32 ? qform_launch<float, NKV>(X, n_cols, static_cast<const float*>(Q), qs, nblk,     \
+                                       static_cast<const float*>(qn), slot_of, hot, n_hot,     \
+                                       n_rows, work, partial, st)                              \
+            : qform_launch<double, NKV>(X, n_cols, static_cast<const double*>(Q), qs, nblk,    \
+                                        static_cast<const double*>(qn), slot_of, hot, n_hot,   \
+                                        n_rows, work, partial, st)
   if (NK <= 1) {
     QF(1);
   } else if (NK <= 2) {
@@ -756,7 +798,7 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
   }
 #undef QF
   CTD_TRY(rc);
-  CTD_LAUNCH(k_sum_f64_fixed, (1), (1024), 0, st, partial, nchunks, out);
+  CTD_TRY(sum_f64(partial, nchunks, out, scratch, st));
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
