@@ -296,6 +296,12 @@ def ours(args):
             "traffic": (tr["bytes_per_launch"] if tr else None)}
     phases = {k: {"ms_per_step": round(v["ms"] / args.steps, 4),
                   "calls_per_step": round(v["calls"] / args.steps, 2)} for k, v in ph.items()}
+    if "call" in ph:
+        # device time of a call not covered by a named phase (mostly idle
+        # gaps while the host reads back sizes and issues the next kernels)
+        inner = sum(v["ms"] for k, v in ph.items() if k != "call")
+        phases["between_phases"] = {"ms_per_step": round((ph["call"]["ms"] - inner) / args.steps, 4),
+                                    "calls_per_step": 1.0}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None

@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <set>
 #include <numeric>
@@ -215,10 +216,14 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   if (precision != CTD_FP64 && precision != CTD_FP32_BULK)
     return fail(CTD_EINVAL, "unknown precision");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PhaseScope ph_call("call", st);  // the whole call; the named phases below sit inside it
   Arena scratch;
   scratch.st = st;
   CooDev X;
-  CTD_TRY(stage_coo(Xd, alpha, scratch, st, &X));
+  {
+    PhaseScope ph("stage", st);
+    CTD_TRY(stage_coo(Xd, alpha, scratch, st, &X));
+  }
 
   ctd_factors* F = new ctd_factors();
   F->mem.st = st;
@@ -281,6 +286,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   const int su = s_unique;
 
   // candidate columns R' (CSC) and their row-major copy
+  std::unique_ptr<PhaseScope> ph_cand(new PhaseScope("candidates", st));
   uint64_t *rc_ptr, *rc_sizes;
   STEP(scratch.get(&rc_sizes, su + 1));
   STEP(scratch.get(&rc_ptr, su + 1));
@@ -301,6 +307,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   STEP(build_csr_from_csc(rc_ptr, rc_row, rc_val, su, nnz_cand, M.n_rows, 0, rcr_ptr, rcr_col,
                           rcr_val, scratch, st));
 
+  ph_cand.reset();
   // lines 5-15: Gram matrix, in-order Cholesky with skip (+ explicit re-test)
   double *G, *xn2;
   STEP(scratch.get(&G, (size_t)su * su));
@@ -335,6 +342,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   }
 
   // R: kept columns of R', CSC and row-major
+  std::unique_ptr<PhaseScope> ph_r(new PhaseScope("r_build", st));
   STEP(F->mem.get(&F->kept_pos, kept));
   STEP(F->mem.get(&F->fibers, kept));
   STEPC(cudaMemcpyAsync(F->kept_pos, idx, kept * sizeof(int), cudaMemcpyDeviceToDevice, st));
@@ -358,6 +366,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   STEP(build_csr_from_csc(F->Rcolptr, F->Rrow, F->Rval, kept, (int64_t)nnzR, M.n_rows, 0,
                           F->Rrowptr, F->Rcol, F->Rcval, scratch, st));
   CsrDev R{F->Rrowptr, F->Rcol, F->Rcval, kept};
+  ph_r.reset();
 
   // line 16: C = R^T X_(alpha)
   if (!(flags & CTD_SKIP_C)) {

@@ -204,27 +204,89 @@ __device__ __forceinline__ unsigned emit_reg(int* acc, int (&regs)[4 * NQ], unsi
   return pos;
 }
 
-// One warp per column (columns with fewer than CF_HEAVY_COL nonzeros); a
-// column with a single nonzero v in row i and positive values is v R(i, :),
-// copied.  Columns are taken 32 at a time from a global counter; lane l
-// prefetches column f0 + l's metadata.
+// One persistent kernel, one 32-warp block per SM.  First the columns with
+// at least CF_HEAVY_COL nonzeros (from `list`), a whole block each, the
+// largest work items first; then every other column, a warp each, 32 at a
+// time from a global counter (lane l prefetches column f0 + l's metadata).
+// A column with a single nonzero v in row i and positive values is v R(i, :),
+// copied.  The block accumulator of the first part is warp 0's accumulator
+// of the second; emission leaves both zero.
 template <typename V, int NQ>
 __global__ void __launch_bounds__(CF_THREADS, 1)
-    k_cf_warp(CscDev X, int64_t n_cols, CsrDev R, Dense dn,
-              const unsigned long long* __restrict__ coff, unsigned* __restrict__ ccnt,
-              uint16_t* __restrict__ crow, V* __restrict__ cval, int positive,
-              unsigned long long* work) {
+    k_cf(CscDev X, int64_t n_cols, CsrDev R, Dense dn, const int64_t* __restrict__ list,
+         const unsigned* __restrict__ nlist, const unsigned long long* __restrict__ coff,
+         unsigned* __restrict__ ccnt, uint16_t* __restrict__ crow, V* __restrict__ cval,
+         int positive, unsigned long long* work) {
   extern __shared__ int4 smem4[];
   constexpr int W = NQ * 128;
   int* dense = reinterpret_cast<int*>(smem4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   int* accs = dense + (size_t)dn.hmax * W;
   load_dense(R, dn, dense, W, accs, nw * W);
-  int* acc = accs + warp * W;
   const int4* dense4 = reinterpret_cast<const int4*>(dense);
   int regs[4 * NQ];
 #pragma unroll
   for (int k = 0; k < 4 * NQ; ++k) regs[k] = 0;
+  __shared__ unsigned long long fcur;
+  __shared__ unsigned wcount[CF_THREADS / 32];
+  const int width = R.width;
+  {
+    int* acc = accs;
+    const unsigned long long n = *nlist;
+    while (true) {
+      if (threadIdx.x == 0) fcur = atomicAdd(work + 1, 1ull);
+      __syncthreads();
+      const unsigned long long it = fcur;
+      __syncthreads();
+      if (it >= n) break;
+      const int64_t f = list[it];
+      accumulate_reg<NQ>(X, R, dn, dense4, f, acc, regs, warp, nw);
+      // fold each warp's registers into the block accumulator
+  #pragma unroll
+      for (int q = 0; q < NQ; ++q)
+  #pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (regs[4 * q + k] != 0) atomicAdd(acc + q * 128 + 4 * lane + k, regs[4 * q + k]);
+          regs[4 * q + k] = 0;
+        }
+      __syncthreads();
+      // emission: warp w sweeps rows [w * span, (w + 1) * span) after counting
+      const int span = (((width + nw - 1) / nw) + 31) & ~31;
+      const int m_lo = min(width, warp * span), m_hi = min(width, m_lo + span);
+      unsigned cnt = 0;
+      for (int m0 = m_lo; m0 < m_hi; m0 += 32) {
+        const int m = m0 + lane;
+        cnt += __popc(__ballot_sync(0xffffffffu, m < m_hi && acc[m] != 0));
+      }
+      if (lane == 0) wcount[warp] = cnt;
+      __syncthreads();
+      unsigned pos = 0, total = 0;
+      for (int w = 0; w < nw; ++w) {
+        if (w < warp) pos += wcount[w];
+        total += wcount[w];
+      }
+      const unsigned long long off = coff[f];
+      for (int m0 = m_lo; m0 < m_hi; m0 += 32) {
+        const int m = m0 + lane;
+        int x = 0;
+        if (m < m_hi) {
+          x = acc[m];
+          acc[m] = 0;
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, x != 0);
+        if (x != 0) {
+          const unsigned q = pos + __popc(ball & ((1u << lane) - 1));
+          crow[off + q] = (uint16_t)m;
+          cval[off + q] = (V)x;
+        }
+        pos += __popc(ball);
+      }
+      if (threadIdx.x == 0) ccnt[f] = total;
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  int* acc = accs + warp * W;
   const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
   const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(X.colptr);
   while (true) {
@@ -248,8 +310,7 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
       }
       if (ub == 0) ccnt[f] = 0;
     }
-    // columns with work for this kernel (empty ones are done, heavy ones go
-    // to the block kernel)
+    // columns with work here (empty ones are done, heavy ones were done first)
     unsigned todo = __ballot_sync(0xffffffffu, ub > 0 && nx < CF_HEAVY_COL);
     while (todo) {
       const int e = __ffs(todo) - 1;
@@ -291,102 +352,19 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
   }
 }
 
-// One block per column with at least CF_HEAVY_COL nonzeros (from `list`).
-template <typename V, int NQ>
-__global__ void __launch_bounds__(CF_THREADS, 1)
-    k_cf_block(CscDev X, const int64_t* __restrict__ list, const unsigned* __restrict__ nlist,
-               CsrDev R, Dense dn, const unsigned long long* __restrict__ coff,
-               unsigned* __restrict__ ccnt, uint16_t* __restrict__ crow, V* __restrict__ cval,
-               unsigned long long* work) {
-  extern __shared__ int4 smem4[];
-  constexpr int W = NQ * 128;
-  int* dense = reinterpret_cast<int*>(smem4);
-  int* acc = dense + (size_t)dn.hmax * W;
-  __shared__ unsigned long long fcur;
-  __shared__ unsigned wcount[CF_THREADS / 32];
-  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
-  const int width = R.width;
-  load_dense(R, dn, dense, W, acc, W);
-  const int4* dense4 = reinterpret_cast<const int4*>(dense);
-  int regs[4 * NQ];
-#pragma unroll
-  for (int k = 0; k < 4 * NQ; ++k) regs[k] = 0;
-  const unsigned long long n = *nlist;
-  while (true) {
-    if (threadIdx.x == 0) fcur = atomicAdd(work, 1ull);
-    __syncthreads();
-    const unsigned long long it = fcur;
-    __syncthreads();
-    if (it >= n) break;
-    const int64_t f = list[it];
-    accumulate_reg<NQ>(X, R, dn, dense4, f, acc, regs, warp, nw);
-    // fold each warp's registers into the block accumulator
-#pragma unroll
-    for (int q = 0; q < NQ; ++q)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (regs[4 * q + k] != 0) atomicAdd(acc + q * 128 + 4 * lane + k, regs[4 * q + k]);
-        regs[4 * q + k] = 0;
-      }
-    __syncthreads();
-    // emission: warp w sweeps rows [w * span, (w + 1) * span) after counting
-    const int span = (((width + nw - 1) / nw) + 31) & ~31;
-    const int m_lo = min(width, warp * span), m_hi = min(width, m_lo + span);
-    unsigned cnt = 0;
-    for (int m0 = m_lo; m0 < m_hi; m0 += 32) {
-      const int m = m0 + lane;
-      cnt += __popc(__ballot_sync(0xffffffffu, m < m_hi && acc[m] != 0));
-    }
-    if (lane == 0) wcount[warp] = cnt;
-    __syncthreads();
-    unsigned pos = 0, total = 0;
-    for (int w = 0; w < nw; ++w) {
-      if (w < warp) pos += wcount[w];
-      total += wcount[w];
-    }
-    const unsigned long long off = coff[f];
-    for (int m0 = m_lo; m0 < m_hi; m0 += 32) {
-      const int m = m0 + lane;
-      int x = 0;
-      if (m < m_hi) {
-        x = acc[m];
-        acc[m] = 0;
-      }
-      const unsigned ball = __ballot_sync(0xffffffffu, x != 0);
-      if (x != 0) {
-        const unsigned q = pos + __popc(ball & ((1u << lane) - 1));
-        crow[off + q] = (uint16_t)m;
-        cval[off + q] = (V)x;
-      }
-      pos += __popc(ball);
-    }
-    if (threadIdx.x == 0) ccnt[f] = total;
-    __syncthreads();
-  }
-}
-
 template <typename V, int NQ>
 ctd_status cf_launch(const CscDev& X, int64_t n_cols, const CsrDev& R, const Dense& dn,
                      const unsigned long long* coff, uint32_t* ccnt, uint16_t* crow, V* cval,
                      int positive, unsigned long long* work, const int64_t* heavy,
                      const unsigned* nheavy, cudaStream_t st) {
   constexpr int W = NQ * 128;
-  const size_t row_b = (size_t)W * sizeof(int);
-  const size_t smem_w = ((size_t)dn.hmax + CF_THREADS / 32) * row_b;
-  const size_t smem_b = ((size_t)dn.hmax + 1) * row_b;
-  CTD_TRY(allow_max_smem((const void*)k_cf_warp<V, NQ>));
-  CTD_TRY(allow_max_smem((const void*)k_cf_block<V, NQ>));
+  const size_t smem = ((size_t)dn.hmax + CF_THREADS / 32) * (size_t)W * sizeof(int);
+  CTD_TRY(allow_max_smem((const void*)k_cf<V, NQ>));
   int per_sm = 0;
-  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cf_warp<V, NQ>, CF_THREADS,
-                                                         smem_w));
+  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cf<V, NQ>, CF_THREADS, smem));
   if (per_sm < 1) return fail(CTD_ENOTSUP, "C fill: shared memory for the dense rows too large");
-  CTD_LAUNCH((k_cf_warp<V, NQ>), (num_sms() * per_sm), (CF_THREADS), smem_w, st, X, n_cols, R, dn,
-             coff, ccnt, crow, cval, positive, work);
-  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cf_block<V, NQ>, CF_THREADS,
-                                                         smem_b));
-  if (per_sm < 1) per_sm = 1;
-  CTD_LAUNCH((k_cf_block<V, NQ>), (num_sms() * per_sm), (CF_THREADS), smem_b, st, X, heavy,
-             nheavy, R, dn, coff, ccnt, crow, cval, work + 1);
+  CTD_LAUNCH((k_cf<V, NQ>), (num_sms() * per_sm), (CF_THREADS), smem, st, X, n_cols, R, dn, heavy,
+             nheavy, coff, ccnt, crow, cval, positive, work);
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }

@@ -533,7 +533,7 @@ struct Vec16<double> {
 constexpr int QF_THREADS = 512;
 
 template <typename T, int NK>
-__global__ void __launch_bounds__(QF_THREADS, (NK * Vec16<T>::n >= 16 ? 1 : 2))
+__global__ void __launch_bounds__(QF_THREADS, (NK >= 8 ? 1 : 2))
     k_qform(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs, int nblk,
             const T* __restrict__ qn, const short* __restrict__ slot_of,
             const int* __restrict__ hot_rows, int n_hot, int64_t n_rows,
