@@ -390,7 +390,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
     F->mem.ptrs.push_back(cv);
     F->Cval = cv;
     PhaseScope ph("c_fill", st);
-    STEP(launch_c_fill(M.csc(), M.n_cols, M.n_rows, R, F->Coff, F->Ccnt, F->Crow, F->Cval,
+    STEP(launch_c_fill(M.csc(), M.n_cols, M.n_rows, M.nnz, R, F->Coff, F->Ccnt, F->Crow, F->Cval,
                        precision == CTD_FP32_BULK, minval > 0, T, st));
   }
 

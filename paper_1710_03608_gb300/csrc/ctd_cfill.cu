@@ -99,6 +99,92 @@ __device__ __forceinline__ void load_dense(const CsrDev& R, const Dense& dn, int
 }
 
 
+// Sort the columns by how C's column is formed (from the column bounds ub =
+// coff[f+1] - coff[f] and the nonzero counts): ub = 0, the column is empty
+// (count 0); one nonzero with positive values: a scaled copy of one row of
+// R (`single`, count = ub); at least CF_HEAVY_COL nonzeros: `heavy`; else
+// `multi`.  Appends are warp-aggregated; the order inside a list does not
+// matter (every column writes its own output range).
+__global__ void k_classify(const unsigned long long* __restrict__ xp,
+                           const unsigned long long* __restrict__ coff, int64_t n_cols,
+                           int positive, unsigned* __restrict__ ccnt,
+                           int64_t* __restrict__ single, unsigned* __restrict__ n_single,
+                           int64_t* __restrict__ heavy, unsigned* __restrict__ n_heavy,
+                           int64_t* __restrict__ multi, unsigned* __restrict__ n_multi) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t f0 = (int64_t)blockIdx.x * blockDim.x; f0 < n_cols; f0 += stride) {
+    const int64_t f = f0 + threadIdx.x;
+    int kind = -1;  // -1 none, 0 single, 1 heavy, 2 multi
+    if (f < n_cols) {
+      const unsigned long long ub = coff[f + 1] - coff[f];
+      const unsigned long long nx = xp[f + 1] - xp[f];
+      if (ub == 0) {
+        ccnt[f] = 0;
+      } else if (nx == 1 && positive) {
+        kind = 0;
+        ccnt[f] = (unsigned)ub;
+      } else {
+        kind = nx >= (unsigned long long)CF_HEAVY_COL ? 1 : 2;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const unsigned m = __ballot_sync(0xffffffffu, kind == k);
+      if (!m) continue;
+      unsigned* cnt = k == 0 ? n_single : k == 1 ? n_heavy : n_multi;
+      int64_t* out = k == 0 ? single : k == 1 ? heavy : multi;
+      unsigned base = 0;
+      if (lane == __ffs(m) - 1) base = atomicAdd(cnt, (unsigned)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+      if (kind == k) out[base + __popc(m & ((1u << lane) - 1))] = f;
+    }
+  }
+}
+
+// C(:, f) = v R(i, :) for the single-nonzero columns: a warp per column,
+// four loads in flight per lane before the stores (no shared memory, so
+// every SM keeps 64 warps resident to hide the latency of R's rows).
+template <typename V>
+__global__ void __launch_bounds__(256)
+    k_copy_rows(CscDev X, CsrDev R, const int64_t* __restrict__ single,
+                const unsigned* __restrict__ n_single, const unsigned long long* __restrict__ coff,
+                uint16_t* __restrict__ crow, V* __restrict__ cval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
+  const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(X.colptr);
+  const int64_t n = *n_single;
+  for (int64_t w = gw; w < n; w += nw) {
+    const int64_t f = single[w];
+    const unsigned long long xa = xp[f];
+    const int i = __ldg(X.row + xa);
+    const int v = __ldg(X.val + xa);
+    const unsigned long long rs = __ldg(rp + i);
+    const int rl = (int)(__ldg(rp + i + 1) - rs);
+    const unsigned long long o = coff[f];
+    int q = lane;
+    for (; q + 96 < rl; q += 128) {
+      int c4[4], v4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c4[u] = __ldg(R.col + rs + q + 32 * u);
+        v4[u] = __ldg(R.val + rs + q + 32 * u);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        crow[o + q + 32 * u] = (uint16_t)c4[u];
+        cval[o + q + 32 * u] = (V)(v * v4[u]);
+      }
+    }
+    for (; q < rl; q += 32) {
+      crow[o + q] = (uint16_t)__ldg(R.col + rs + q);
+      cval[o + q] = (V)(v * __ldg(R.val + rs + q));
+    }
+  }
+}
+
 // Accumulate R^T x_f: dense rows into regs (lane's rows 128 q + 4 lane + k),
 // other rows into the shared accumulator acc (atomics).  Warps of a group
 // [gwarp, gwarp + gwarps) take interleaved 32-entry chunks of the column.
@@ -205,18 +291,17 @@ __device__ __forceinline__ unsigned emit_reg(int* acc, int (&regs)[4 * NQ], unsi
 }
 
 // One persistent kernel, one 32-warp block per SM.  First the columns with
-// at least CF_HEAVY_COL nonzeros (from `list`), a whole block each, the
-// largest work items first; then every other column, a warp each, 32 at a
-// time from a global counter (lane l prefetches column f0 + l's metadata).
-// A column with a single nonzero v in row i and positive values is v R(i, :),
-// copied.  The block accumulator of the first part is warp 0's accumulator
-// of the second; emission leaves both zero.
+// at least CF_HEAVY_COL nonzeros (`list`), a whole block each, the largest
+// work items first; then the other multi-nonzero columns (`mlist`), a warp
+// each.  The block accumulator of the first part is warp 0's accumulator of
+// the second; emission leaves both zero.
 template <typename V, int NQ>
 __global__ void __launch_bounds__(CF_THREADS, 1)
-    k_cf(CscDev X, int64_t n_cols, CsrDev R, Dense dn, const int64_t* __restrict__ list,
-         const unsigned* __restrict__ nlist, const unsigned long long* __restrict__ coff,
+    k_cf(CscDev X, CsrDev R, Dense dn, const int64_t* __restrict__ list,
+         const unsigned* __restrict__ nlist, const int64_t* __restrict__ mlist,
+         const unsigned* __restrict__ mcount, const unsigned long long* __restrict__ coff,
          unsigned* __restrict__ ccnt, uint16_t* __restrict__ crow, V* __restrict__ cval,
-         int positive, unsigned long long* work) {
+         unsigned long long* work) {
   extern __shared__ int4 smem4[];
   constexpr int W = NQ * 128;
   int* dense = reinterpret_cast<int*>(smem4);
@@ -287,98 +372,78 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
   }
   __syncthreads();
   int* acc = accs + warp * W;
-  const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
-  const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(X.colptr);
+  // then the listed columns with 2..CF_HEAVY_COL-1 nonzeros (or one nonzero
+  // with signed values), `grab` list entries per warp at a time
+  const unsigned long long nm = *mcount;
+  const unsigned long long warps_all = (unsigned long long)gridDim.x * nw;
+  const int grab = (int)max(1ull, min(32ull, nm / (warps_all * 4ull)));
   while (true) {
-    unsigned long long f0 = 0;
-    if (lane == 0) f0 = atomicAdd(work, 32ull);
-    f0 = __shfl_sync(0xffffffffu, f0, 0);
-    if (f0 >= (unsigned long long)n_cols) break;
-    const int64_t f = (int64_t)f0 + lane;
-    unsigned long long o = 0, xa = 0, rs = 0;
-    int ub = 0, nx = 0, vv = 0, rl = 0;
-    if (f < n_cols) {
+    unsigned long long i0 = 0;
+    if (lane == 0) i0 = atomicAdd(work, (unsigned long long)grab);
+    i0 = __shfl_sync(0xffffffffu, i0, 0);
+    if (i0 >= nm) break;
+    unsigned long long o = 0;
+    int64_t f = -1;
+    if (lane < grab && i0 + lane < nm) {
+      f = mlist[i0 + lane];
       o = coff[f];
-      ub = (int)(coff[f + 1] - o);
-      xa = xp[f];
-      nx = (int)min(xp[f + 1] - xa, (unsigned long long)0x7fffffff);
-      if (ub > 0 && nx == 1 && positive) {
-        const int i = __ldg(X.row + xa);
-        vv = __ldg(X.val + xa);
-        rs = __ldg(rp + i);
-        rl = (int)(__ldg(rp + i + 1) - rs);
-      }
-      if (ub == 0) ccnt[f] = 0;
     }
-    // columns with work here (empty ones are done, heavy ones were done first)
-    unsigned todo = __ballot_sync(0xffffffffu, ub > 0 && nx < CF_HEAVY_COL);
+    unsigned todo = __ballot_sync(0xffffffffu, f >= 0);
     while (todo) {
       const int e = __ffs(todo) - 1;
       todo &= todo - 1;
       const unsigned long long oe = __shfl_sync(0xffffffffu, o, e);
-      const int nxe = __shfl_sync(0xffffffffu, nx, e);
-      if (nxe == 1 && positive) {
-        const unsigned long long rse = __shfl_sync(0xffffffffu, rs, e);
-        const int rle = __shfl_sync(0xffffffffu, rl, e);
-        const int ve = __shfl_sync(0xffffffffu, vv, e);
-        // a copy of R's row: four loads in flight per lane before the stores
-        int q = lane;
-        for (; q + 96 < rle; q += 128) {
-          int c4[4], v4[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            c4[u] = __ldg(R.col + rse + q + 32 * u);
-            v4[u] = __ldg(R.val + rse + q + 32 * u);
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            crow[oe + q + 32 * u] = (uint16_t)c4[u];
-            cval[oe + q + 32 * u] = (V)(ve * v4[u]);
-          }
-        }
-        for (; q < rle; q += 32) {
-          crow[oe + q] = (uint16_t)__ldg(R.col + rse + q);
-          cval[oe + q] = (V)(ve * __ldg(R.val + rse + q));
-        }
-        if (lane == 0) ccnt[f0 + e] = (unsigned)rle;
-        continue;
-      }
-      accumulate_reg<NQ>(X, R, dn, dense4, (int64_t)f0 + e, acc, regs, 0, 1);
+      const int64_t fe = __shfl_sync(0xffffffffu, f, e);
+      accumulate_reg<NQ>(X, R, dn, dense4, fe, acc, regs, 0, 1);
       __syncwarp();
       const unsigned n = emit_reg<V, NQ>(acc, regs, oe, crow, cval);
       __syncwarp();
-      if (lane == 0) ccnt[f0 + e] = n;
+      if (lane == 0) ccnt[fe] = n;
     }
   }
 }
 
 template <typename V, int NQ>
-ctd_status cf_launch(const CscDev& X, int64_t n_cols, const CsrDev& R, const Dense& dn,
+ctd_status cf_launch(const CscDev& X, const CsrDev& R, const Dense& dn,
                      const unsigned long long* coff, uint32_t* ccnt, uint16_t* crow, V* cval,
-                     int positive, unsigned long long* work, const int64_t* heavy,
-                     const unsigned* nheavy, cudaStream_t st) {
+                     const int64_t* heavy, const unsigned* nheavy, const int64_t* multi,
+                     const unsigned* nmulti, unsigned long long* work, cudaStream_t st) {
   constexpr int W = NQ * 128;
   const size_t smem = ((size_t)dn.hmax + CF_THREADS / 32) * (size_t)W * sizeof(int);
   CTD_TRY(allow_max_smem((const void*)k_cf<V, NQ>));
   int per_sm = 0;
   CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cf<V, NQ>, CF_THREADS, smem));
   if (per_sm < 1) return fail(CTD_ENOTSUP, "C fill: shared memory for the dense rows too large");
-  CTD_LAUNCH((k_cf<V, NQ>), (num_sms() * per_sm), (CF_THREADS), smem, st, X, n_cols, R, dn, heavy,
-             nheavy, coff, ccnt, crow, cval, positive, work);
+  CTD_LAUNCH((k_cf<V, NQ>), (num_sms() * per_sm), (CF_THREADS), smem, st, X, R, dn, heavy,
+             nheavy, multi, nmulti, coff, ccnt, crow, cval, work);
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
 
 template <typename V>
-ctd_status cf_dispatch(int nq, const CscDev& X, int64_t n_cols, const CsrDev& R, const Dense& dn,
-                       const unsigned long long* coff, uint32_t* ccnt, uint16_t* crow, V* cval,
-                       int positive, unsigned long long* work, const int64_t* heavy,
-                       const unsigned* nheavy, cudaStream_t st) {
+ctd_status cf_all(int nq, const CscDev& X, int64_t n_cols, const CsrDev& R, const Dense& dn,
+                  const unsigned long long* coff, uint32_t* ccnt, uint16_t* crow, V* cval,
+                  int positive, int64_t list_cap, Arena& a, cudaStream_t st) {
+  int64_t *single, *heavy, *multi;
+  unsigned* counts;
+  unsigned long long* work;
+  CTD_TRY(a.get(&single, list_cap));
+  CTD_TRY(a.get(&heavy, list_cap));
+  CTD_TRY(a.get(&multi, list_cap));
+  CTD_TRY(a.get(&counts, 3));
+  CTD_TRY(a.get(&work, 2));
+  CTD_CUDA(cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned), st));
+  CTD_CUDA(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), st));
+  CTD_LAUNCH(k_classify, (grid_for(n_cols, 256, (int64_t)num_sms() * 16)), (256), 0, st,
+             reinterpret_cast<const unsigned long long*>(X.colptr), coff, n_cols, positive, ccnt,
+             single, counts, heavy, counts + 1, multi, counts + 2);
+  CTD_LAUNCH(k_copy_rows<V>, (num_sms() * 8), (256), 0, st, X, R, single, counts, coff, crow,
+             cval);
   switch (nq) {
-    case 1: return cf_launch<V, 1>(X, n_cols, R, dn, coff, ccnt, crow, cval, positive, work, heavy, nheavy, st);
-    case 2: return cf_launch<V, 2>(X, n_cols, R, dn, coff, ccnt, crow, cval, positive, work, heavy, nheavy, st);
-    case 4: return cf_launch<V, 4>(X, n_cols, R, dn, coff, ccnt, crow, cval, positive, work, heavy, nheavy, st);
-    default: return cf_launch<V, 8>(X, n_cols, R, dn, coff, ccnt, crow, cval, positive, work, heavy, nheavy, st);
+    case 1: return cf_launch<V, 1>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, counts + 2, work, st);
+    case 2: return cf_launch<V, 2>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, counts + 2, work, st);
+    case 4: return cf_launch<V, 4>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, counts + 2, work, st);
+    default: return cf_launch<V, 8>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, counts + 2, work, st);
   }
 }
 
@@ -386,9 +451,10 @@ ctd_status cf_dispatch(int nq, const CscDev& X, int64_t n_cols, const CsrDev& R,
 
 // C fill with dense long rows and register accumulators; requires
 // ||X||_F^2 < 2^31 and s~ <= 1024 (the caller checks).
-ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
-                             const uint64_t* coff, uint32_t* ccnt, uint16_t* crow, void* cval,
-                             int fp32, int positive, cudaStream_t st) {
+ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t nnz,
+                             const CsrDev& R, const uint64_t* coff, uint32_t* ccnt,
+                             uint16_t* crow, void* cval, int fp32, int positive,
+                             cudaStream_t st) {
   const int width = R.width;
   const int nq0 = (width + 127) / 128;
   const int nq = nq0 <= 1 ? 1 : nq0 <= 2 ? 2 : nq0 <= 4 ? 4 : 8;
@@ -401,35 +467,28 @@ ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, co
   const int minlen = std::max(16, 16 * nq);  // shorter rows are cheaper walked sparsely
   Arena a;
   a.st = st;
-  unsigned *hist, *nheavy;
+  unsigned* hist;
   int *thr, *slot, *rows, *count;
-  unsigned long long* work;
-  int64_t* heavy;
   CTD_TRY(a.get(&hist, width + 1));
   CTD_TRY(a.get(&thr, 1));
   CTD_TRY(a.get(&slot, std::max<int64_t>(n_rows, 1)));
   CTD_TRY(a.get(&rows, std::max(hmax, 1)));
   CTD_TRY(a.get(&count, 1));
-  CTD_TRY(a.get(&work, 2));
-  CTD_TRY(a.get(&heavy, std::max<int64_t>(n_cols, 1)));
-  CTD_TRY(a.get(&nheavy, 1));
   CTD_CUDA(cudaMemsetAsync(hist, 0, (width + 1) * sizeof(unsigned), st));
   CTD_CUDA(cudaMemsetAsync(count, 0, sizeof(int), st));
-  CTD_CUDA(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), st));
-  CTD_CUDA(cudaMemsetAsync(nheavy, 0, sizeof(unsigned), st));
   const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
   const unsigned g = grid_for(n_rows, 256, (int64_t)num_sms() * 4);
   CTD_LAUNCH(k_row_len_hist, (g), (256), 0, st, rp, n_rows, minlen, width, hist);
   CTD_LAUNCH(k_pick_len, (1), (32), 0, st, hist, width, minlen, hmax, thr);
   CTD_LAUNCH(k_assign_slots, (g), (256), 0, st, rp, n_rows, width, thr, slot, rows, count);
-  launch_list_columns(X.colptr, coff, n_cols, CF_HEAVY_COL, heavy, nheavy, st);
   Dense dn{slot, rows, count, hmax};
   const unsigned long long* co = reinterpret_cast<const unsigned long long*>(coff);
+  const int64_t list_cap = std::max<int64_t>(1, std::min(n_cols, nnz));
   if (fp32)
-    return cf_dispatch<float>(nq, X, n_cols, R, dn, co, ccnt, crow, static_cast<float*>(cval),
-                              positive, work, heavy, nheavy, st);
-  return cf_dispatch<double>(nq, X, n_cols, R, dn, co, ccnt, crow, static_cast<double*>(cval),
-                             positive, work, heavy, nheavy, st);
+    return cf_all<float>(nq, X, n_cols, R, dn, co, ccnt, crow, static_cast<float*>(cval),
+                         positive, list_cap, a, st);
+  return cf_all<double>(nq, X, n_cols, R, dn, co, ccnt, crow, static_cast<double*>(cval),
+                        positive, list_cap, a, st);
 }
 
 }  // namespace ctd

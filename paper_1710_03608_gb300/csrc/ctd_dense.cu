@@ -254,78 +254,102 @@ __device__ bool grid_sync(const GridBar& gb) {
   return ok != 0;
 }
 
-__global__ void __launch_bounds__(256)
+// The diagonal block at k0, in order, by warp 0 of the calling block: lane r
+// holds row r in registers; column c is finished left-looking (its entries
+// reduced by the earlier columns, row c's values broadcast by shuffles),
+// then decided and scaled.  No block barriers inside except the first.
+struct CholShared {
+  double D[NB][NB + 1];
+  double Pc[NB][NB + 1];
+  double invd[NB];
+  int kp[NB];
+  double thr_s[NB], piv_s[NB];
+  int force_s[NB];
+  double fpiv_s[NB];
+};
+
+__device__ void chol_diag_block(double* __restrict__ A, int64_t n, int64_t lda, int64_t k0,
+                                const double* __restrict__ thr, const int* __restrict__ force,
+                                const double* __restrict__ fpiv, int* __restrict__ keep,
+                                double* __restrict__ piv, unsigned* __restrict__ status,
+                                CholShared& sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = (int)min((int64_t)NB, n - k0);
+  double* thr_s = sh.thr_s;
+  int* force_s = sh.force_s;
+  double* fpiv_s = sh.fpiv_s;
+  int* kp = sh.kp;
+  double* piv_s = sh.piv_s;
+  if (tid < nb) {
+    thr_s[tid] = thr[k0 + tid];
+    force_s[tid] = force ? force[k0 + tid] : -1;
+    fpiv_s[tid] = fpiv ? fpiv[k0 + tid] : 0.0;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double row[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      row[c] = (lane < nb && c <= lane) ? A[(k0 + lane) + (k0 + c) * lda] : 0.0;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      if (c < nb) {
+        double sred = row[c];
+#pragma unroll
+        for (int q = 0; q < c; ++q)
+          sred = fma(-row[q], __shfl_sync(0xffffffffu, row[q], c), sred);
+        double d = __shfl_sync(0xffffffffu, sred, c);
+        int k = (d > thr_s[c] && d > 0.0) ? 1 : 0;
+        if (force_s[c] >= 0) k = force_s[c];
+        // a keep forced by the explicit residual takes that residual's
+        // squared norm as its pivot (the Gram-based one lost it to rounding)
+        if (force_s[c] == 1 && fpiv_s[c] > 0.0) d = fpiv_s[c];
+        if (k && !(d > 0.0)) {
+          if (lane == 0) atomicOr(status, DEV_CAPACITY);
+          k = 0;
+        }
+        const double l = k ? sqrt(d) : 0.0;
+        const double inv = k ? 1.0 / l : 0.0;
+        if (lane == c)
+          row[c] = l;
+        else if (lane > c)
+          row[c] = sred * inv;
+        if (lane == 0) {
+          kp[c] = k;
+          piv_s[c] = d;
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      if (lane < nb && c <= lane) A[(k0 + lane) + (k0 + c) * lda] = row[c];
+    __syncwarp();
+    if (lane < nb) {
+      keep[k0 + lane] = kp[lane];
+      if (piv) piv[k0 + lane] = piv_s[lane];
+    }
+  }
+  __threadfence();
+}
+
+__global__ void __launch_bounds__(256, 1)
     k_chol_coop(double* __restrict__ A, int64_t n, int64_t lda, const double* __restrict__ thr,
                 const int* __restrict__ force, const double* __restrict__ fpiv,
                 int* __restrict__ keep, double* __restrict__ piv,
                 unsigned* __restrict__ status, GridBar gb) {
-  __shared__ double D[NB][NB + 1];
-  __shared__ double Pc[NB][NB + 1];
-  __shared__ double invd[NB];
-  __shared__ int kp[NB];
-  __shared__ double thr_s[NB], piv_s[NB];
-  __shared__ int force_s[NB];
-  __shared__ double fpiv_s[NB];
+  __shared__ CholShared sh;
+  double(*D)[NB + 1] = sh.D;
+  double(*Pc)[NB + 1] = sh.Pc;
+  double* invd = sh.invd;
+  int* kp = sh.kp;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // the first diagonal block; every later one is factored by block 0 right
+  // after its own trailing tile (tile 0 of the previous panel, which is that
+  // diagonal block), overlapping the other blocks' trailing updates
+  if (blockIdx.x == 0) chol_diag_block(A, n, lda, 0, thr, force, fpiv, keep, piv, status, sh);
+  if (!grid_sync(gb)) return;
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
     const int nb = (int)min((int64_t)NB, n - k0);
-    // --- A: the diagonal block, in order, by warp 0 of block 0.  Lane r
-    // holds row r in registers; column c is finished left-looking (its
-    // entries reduced by the earlier columns, row c's values broadcast by
-    // shuffles), then decided and scaled.  No block barriers inside.
-    if (blockIdx.x == 0) {
-      if (tid < nb) {
-        thr_s[tid] = thr[k0 + tid];
-        force_s[tid] = force ? force[k0 + tid] : -1;
-        fpiv_s[tid] = fpiv ? fpiv[k0 + tid] : 0.0;
-      }
-      __syncthreads();
-      if (warp == 0) {
-        double row[NB];
-#pragma unroll
-        for (int c = 0; c < NB; ++c)
-          row[c] = (lane < nb && c <= lane) ? A[(k0 + lane) + (k0 + c) * lda] : 0.0;
-#pragma unroll
-        for (int c = 0; c < NB; ++c) {
-          if (c < nb) {
-            double sred = row[c];
-#pragma unroll
-            for (int q = 0; q < c; ++q)
-              sred = fma(-row[q], __shfl_sync(0xffffffffu, row[q], c), sred);
-            double d = __shfl_sync(0xffffffffu, sred, c);
-            int k = (d > thr_s[c] && d > 0.0) ? 1 : 0;
-            if (force_s[c] >= 0) k = force_s[c];
-            // a keep forced by the explicit residual takes that residual's
-            // squared norm as its pivot (the Gram-based one lost it to rounding)
-            if (force_s[c] == 1 && fpiv_s[c] > 0.0) d = fpiv_s[c];
-            if (k && !(d > 0.0)) {
-              if (lane == 0) atomicOr(status, DEV_CAPACITY);
-              k = 0;
-            }
-            const double l = k ? sqrt(d) : 0.0;
-            const double inv = k ? 1.0 / l : 0.0;
-            if (lane == c)
-              row[c] = l;
-            else if (lane > c)
-              row[c] = sred * inv;
-            if (lane == 0) {
-              kp[c] = k;
-              piv_s[c] = d;
-            }
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < NB; ++c)
-          if (lane < nb && c <= lane) A[(k0 + lane) + (k0 + c) * lda] = row[c];
-        __syncwarp();
-        if (lane < nb) {
-          keep[k0 + lane] = kp[lane];
-          if (piv) piv[k0 + lane] = piv_s[lane];
-        }
-      }
-      __threadfence();
-    }
-    if (!grid_sync(gb)) return;
     const int64_t k1 = k0 + nb;
     const int64_t rest = n - k1;
     if (rest <= 0) break;
@@ -385,6 +409,10 @@ __global__ void __launch_bounds__(256)
           A[r + c * lda] -= s2;
         }
       }
+    }
+    if (blockIdx.x == 0) {
+      __syncthreads();  // tile 0 (the next diagonal block) is written by this block
+      chol_diag_block(A, n, lda, k1, thr, force, fpiv, keep, piv, status, sh);
     }
     __threadfence();
     if (!grid_sync(gb)) return;

@@ -250,6 +250,54 @@ static ctd_status grow_U(ctd_factors* F, int64_t d, int64_t n, cudaStream_t st) 
   return CTD_OK;
 }
 
+// W(:, c) = Q^T x_c for sparse columns x_c (CSC) and Q given by rows (row i of
+// Q at Qt + i * ld, first d entries used): a block per column, threads over
+// the d entries, the column's nonzeros in order (deterministic).
+__global__ void k_qt_times_sparse(const unsigned long long* __restrict__ cptr,
+                                  const int32_t* __restrict__ crow,
+                                  const int32_t* __restrict__ cval, int n,
+                                  const double* __restrict__ Qt, int64_t ld, int64_t d,
+                                  double* __restrict__ W) {
+  for (int c = blockIdx.x; c < n; c += gridDim.x) {
+    const unsigned long long a = cptr[c], b = cptr[c + 1];
+    for (int64_t r0 = 0; r0 < d; r0 += 4 * (int64_t)blockDim.x) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      for (unsigned long long p = a; p < b; ++p) {
+        const double v = (double)cval[p];
+        const double* q = Qt + (int64_t)crow[p] * ld;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t r = r0 + threadIdx.x + (int64_t)u * blockDim.x;
+          if (r < d) acc[u] = fma(v, q[r], acc[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t r = r0 + threadIdx.x + (int64_t)u * blockDim.x;
+        if (r < d) W[r + (int64_t)c * d] = acc[u];
+      }
+    }
+  }
+}
+
+// y += x (n entries)
+__global__ void k_axpy_f64(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    y[e] += x[e];
+}
+
+// out (lower, n x n, ld ldo) = transpose of the upper triangle of A (ld lda);
+// out's strict upper triangle is left alone
+__global__ void k_lower_from_upper_T(const double* __restrict__ A, int64_t lda, int64_t n,
+                                     double* __restrict__ out, int64_t ldo) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % n, c = e / n;
+    if (r >= c) out[r + c * ldo] = A[c + r * lda];
+  }
+}
+
 // column c of V (m x n, ld m) scaled to unit norm (zero columns stay zero)
 __global__ void k_unit_columns(double* __restrict__ V, int64_t m, int n) {
   __shared__ double part[32];
@@ -384,8 +432,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   const uint64_t* rc_ptr_k = nullptr;  // the candidates as CSC
   const int32_t* rc_row_k = nullptr;
   const int32_t* rc_val_k = nullptr;
-  double* Bm = nullptr;   // R^(t)^T X_c
-  double* W = nullptr;    // L^{-1} R^(t)^T X_c
+  double* W = nullptr;    // Q^(t)^T X_c = L^{-1} R^(t)^T X_c
   // R^(t) already spans every mode-alpha vector (d~_t = I_alpha independent
   // columns): every candidate's residual is exactly zero, so none is kept.
   if (du > 0 && dt < M.n_rows) {
@@ -418,13 +465,12 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
                                 CsrDev{rcr_ptr, rcr_col, rcr_val, du}, S, du, st));
       launch_thresholds(S, du, du, 1.0, xn2, st);  // ||x_k||^2
       if (dt > 0) {
-        // B = R^(t)^T X_c (exact), W = L^{-1} B, S = X_c^T X_c - W^T W
-        CTD_TRY(scratch.get(&Bm, (size_t)dt * du));
+        // W = Q^(t)^T X_c (= L^{-1} R^(t)^T X_c, since R^(t) = Q L^T), a sparse
+        // product with the basis rows; S = X_c^T X_c - W^T W
         CTD_TRY(scratch.get(&W, (size_t)dt * du));
-        CTD_TRY(launch_spmm_dense(M.csc(), D.lastIu, d_count, du,
-                                  CsrDev{F->Rrowptr, F->Rcol, F->Rcval, (int)dt}, Bm, dt, st));
-        CTD_CUDA(cudaMemcpyAsync(W, Bm, (size_t)dt * du * 8, cudaMemcpyDeviceToDevice, st));
-        tri_solve_lower(F->L, D.cap_d, dt, W, dt, du, st);
+        CTD_LAUNCH(k_qt_times_sparse, ((unsigned)std::min(du, 65535)), (256), 0, st,
+                   reinterpret_cast<const unsigned long long*>(rc_ptr), rc_row, rc_val, du,
+                   F->Qt, D.cap_d, dt, W);
         dgemm(true, false, du, du, dt, -1.0, W, dt, W, dt, 1.0, S, du, st);
       }
     }
@@ -458,26 +504,16 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
       PhaseScope ph("d_update_u", st);
       const int64_t dn = dt + kept;
       double* WKs = nullptr;  // W restricted to the kept candidates (dt x kept)
-      double* L = fo.Lk;   // factor of the kept block of S
-      double* Li = fo.Li;  // its inverse
+      double* Li = fo.Li;  // inverse of the filter's factor of the kept block of S
       F->U_valid = false;
       CTD_TRY(grow_U(F, dt, dn, st));
       const int64_t ld = D.cap_d;
-      if (dt > 0) {
-        // W_K = L^{-1} R^(t)^T dR, kept for the M chain (M_{t+1} = W_K^T
-        // L^(t)^{-1} = ((dR)^T R^(t)) U^(t), formed on request) and for
-        // L^(t+1) = [[L, 0], [W_K^T, L_S]]
-        CTD_TRY(dalloc_n(&rec.WK, (size_t)dt * kept, st));
-        WKs = rec.WK;
-        const unsigned gk = grid_for(dt * kept, 256, (int64_t)num_sms() * 8);
-        CTD_LAUNCH(k_gather_cols_f64, (gk), (256), 0, st, W, dt, dt, idx, kept, rec.WK, dt);
-        CTD_LAUNCH(k_transpose_f64, (gk), (256), 0, st, rec.WK, dt, dt, kept, F->L + dt, ld);
-      }
-      CTD_CUDA(cudaMemcpy2DAsync(F->L + dt + dt * ld, ld * 8, L, kept * 8, kept * 8, kept,
-                                 cudaMemcpyDeviceToDevice, st));
-      // Q^(t+1) = [Q^(t), Q_new]: the kept candidates' residuals against
-      // range(Q^(t)) (Gram-Schmidt twice), normalized by L_S^{-T} and then
-      // once more by a Cholesky of their Gram matrix (orthonormal to rounding)
+      // Gram-Schmidt of the kept candidates against Q^(t): X_K = Q^(t) W_K + V
+      // with V orthogonal to range(Q^(t)); then V = Q_new Lam^T (Lam lower
+      // triangular) with Q_new orthonormal.  So R^(t+1) = Q^(t+1) L^(t+1)^T
+      // with L^(t+1) = [[L, 0], [W_K^T, Lam]], a Cholesky factor of
+      // R^(t+1)^T R^(t+1); W_K is kept for the M chain (M_{t+1} = W_K^T
+      // L^(t)^{-1} = ((dR)^T R^(t)) U^(t), formed on request).
       {
         PhaseScope phq("d_q_basis", st);
         const int64_t nr = M.n_rows;
@@ -490,16 +526,22 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
                    reinterpret_cast<const unsigned long long*>(rc_ptr_k), rc_row_k, rc_val_k, idx,
                    kept, V, nr);
         if (dt > 0) {
-          double* Hm;
-          CTD_TRY(scratch.get(&Hm, (size_t)dt * kept));
+          CTD_TRY(dalloc_n(&rec.WK, (size_t)dt * kept, st));
+          WKs = rec.WK;
+          const unsigned gk = grid_for(dt * kept, 256, (int64_t)num_sms() * 8);
+          CTD_LAUNCH(k_gather_cols_f64, (gk), (256), 0, st, W, dt, dt, idx, kept, rec.WK, dt);
           dgemm(true, false, nr, kept, dt, -1.0, F->Qt, ld, WKs, dt, 1.0, V, nr, st);
           // the second pass holds the blocks orthogonal to ~u / rho for a
-          // residual ratio rho >= eps; FP32_BULK's error bar (1e-4 relative)
-          // does not need it
+          // residual ratio rho >= eps (and adds its coefficients to W_K);
+          // FP32_BULK's error bar (1e-4 relative) does not need it
           if (!fp32) {
+            double* Hm;
+            CTD_TRY(scratch.get(&Hm, (size_t)dt * kept));
             dgemm(false, false, dt, kept, nr, 1.0, F->Qt, ld, V, nr, 0.0, Hm, dt, st);
             dgemm(true, false, nr, kept, dt, -1.0, F->Qt, ld, Hm, dt, 1.0, V, nr, st);
+            CTD_LAUNCH(k_axpy_f64, (gk), (256), 0, st, dt * kept, Hm, rec.WK);
           }
+          CTD_LAUNCH(k_transpose_f64, (gk), (256), 0, st, rec.WK, dt, dt, kept, F->L + dt, ld);
         }
         // V2 = V L_S^{-T} is orthonormal up to the filter's rounding; one
         // Cholesky-QR pass makes it so to working precision.  If that pass
@@ -511,6 +553,9 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
         bool ok = false;
         CTD_TRY(cholqr_pass(V2, nr, kept, 0.0, Vq, scratch, st, &ok));
         if (!ok) {
+          double* V0;  // the residuals themselves, for Lam below
+          CTD_TRY(scratch.get(&V0, (size_t)nr * kept));
+          CTD_CUDA(cudaMemcpyAsync(V0, V, (size_t)nr * kept * 8, cudaMemcpyDeviceToDevice, st));
           CTD_LAUNCH(k_unit_columns, ((unsigned)std::min(kept, 4096)), (256), 0, st, V, nr, kept);
           const double u = 1.1102230246251565e-16;
           const double shift = 11.0 * ((double)nr * kept + (double)kept * (kept + 1)) * u * kept;
@@ -518,7 +563,15 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
           if (ok) CTD_TRY(cholqr_pass(V2, nr, kept, 0.0, V, scratch, st, &ok));
           if (ok) CTD_TRY(cholqr_pass(V, nr, kept, 0.0, Vq, scratch, st, &ok));
           if (!ok) return fail(CTD_ENOTSUP, "new basis vectors are numerically dependent");
+          V = V0;
         }
+        // Lam^T = Q_new^T V (upper triangular up to rounding): its lower
+        // transpose is L^(t+1)'s diagonal block
+        double* Lam;
+        CTD_TRY(scratch.get(&Lam, (size_t)kept * kept));
+        dgemm(true, false, kept, kept, nr, 1.0, Vq, nr, V, nr, 0.0, Lam, kept, st);
+        CTD_LAUNCH(k_lower_from_upper_T, (grid_for((int64_t)kept * kept, 256, (int64_t)num_sms() * 4)),
+                   (256), 0, st, Lam, kept, kept, F->L + dt + dt * ld, ld);
         CTD_LAUNCH(k_transpose_f64, (grid_for(nr * kept, 256, (int64_t)num_sms() * 8)), (256), 0,
                    st, Vq, nr, nr, kept, F->Qt + dt, ld);
         CTD_LAUNCH(k_qn_add, (grid_for(nr, 256, (int64_t)num_sms() * 4)), (256), 0, st, F->Qt, ld,
@@ -590,7 +643,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
     CTD_TRY(dalloc(&rec.Cval, std::max<uint64_t>(cap, 1) * (fp32 ? 4 : 8), st));
     {
       PhaseScope ph("d_c_fill", st);
-      CTD_TRY(launch_c_fill(M.csc(), M.n_cols, M.n_rows, R, rec.Coff, rec.Ccnt, rec.Crow, rec.Cval, fp32,
+      CTD_TRY(launch_c_fill(M.csc(), M.n_cols, M.n_rows, M.nnz, R, rec.Coff, rec.Ccnt, rec.Crow, rec.Cval, fp32,
                             D.all_positive, (uint64_t)D.max_T, st));
     }
     double* d_pu;

@@ -54,43 +54,64 @@ __global__ void k_gather_cols(const double* __restrict__ A, int64_t lda, int64_t
   }
 }
 
-// One block per suspect: r = x_k - R^(t) gammaR - Xc[:, K] eta, ratio = ||r|| / ||x_k||.
-__global__ void k_explicit_residual(int64_t n_rows, const unsigned long long* __restrict__ cptr,
-                                    const int32_t* __restrict__ crow,
-                                    const int32_t* __restrict__ cval, int64_t dt,
-                                    const unsigned long long* __restrict__ rptr,
-                                    const int32_t* __restrict__ rrow,
-                                    const int32_t* __restrict__ rval,
-                                    const double* __restrict__ gammaR,
-                                    const int* __restrict__ kept_idx, int kept,
-                                    const double* __restrict__ eta, const int* __restrict__ sus,
-                                    const double* __restrict__ xnorm2, double* __restrict__ rbuf,
-                                    double* __restrict__ ratio, int init) {
-  __shared__ double part[32];
+// The explicit residual of each suspect c, r_c = x_k - R^(t) gammaR_c -
+// Xc[:, K] eta_c, in three kernels: r_c = x_k (or left as is, to refine it),
+// the subtractions (grid (suspect, slice of columns); a warp walks one
+// column of R^(t) or of the kept candidates, lanes striding over its
+// entries, FP64 atomics into r_c), and ratio_c = ||r_c|| / ||x_k||.
+__global__ void k_resid_init(int64_t n_rows, const unsigned long long* __restrict__ cptr,
+                             const int32_t* __restrict__ crow, const int32_t* __restrict__ cval,
+                             const int* __restrict__ sus, double* __restrict__ rbuf) {
   const int c = blockIdx.x;
   const int k = sus[c];
   double* r = rbuf + (int64_t)c * n_rows;
-  if (init) {
-    for (int64_t i = threadIdx.x; i < n_rows; i += blockDim.x) r[i] = 0.0;
-    __syncthreads();
-    for (unsigned long long p = cptr[k] + threadIdx.x; p < cptr[k + 1]; p += blockDim.x)
-      r[crow[p]] = (double)cval[p];
-  }
+  for (int64_t i = threadIdx.x; i < n_rows; i += blockDim.x) r[i] = 0.0;
   __syncthreads();
-  for (int64_t j = threadIdx.x; j < dt; j += blockDim.x) {
-    const double g = gammaR[j + (int64_t)c * dt];
-    if (g != 0.0)
-      for (unsigned long long q = rptr[j]; q < rptr[j + 1]; ++q)
-        atomicAdd(r + rrow[q], -g * (double)rval[q]);
+  for (unsigned long long p = cptr[k] + threadIdx.x; p < cptr[k + 1]; p += blockDim.x)
+    r[crow[p]] = (double)cval[p];
+}
+
+__global__ void k_resid_update(int64_t n_rows, const unsigned long long* __restrict__ cptr,
+                               const int32_t* __restrict__ crow, const int32_t* __restrict__ cval,
+                               int64_t dt, const unsigned long long* __restrict__ rptr,
+                               const int32_t* __restrict__ rrow, const int32_t* __restrict__ rval,
+                               const double* __restrict__ gammaR, const int* __restrict__ kept_idx,
+                               int kept, const double* __restrict__ eta, double* __restrict__ rbuf) {
+  const int c = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t nw = (int64_t)gridDim.y * (blockDim.x >> 5);
+  double* r = rbuf + (int64_t)c * n_rows;
+  for (int64_t j = gw; j < dt + kept; j += nw) {
+    double g;
+    unsigned long long a, b;
+    const int32_t *row, *val;
+    if (j < dt) {
+      g = gammaR[j + (int64_t)c * dt];
+      a = rptr[j];
+      b = rptr[j + 1];
+      row = rrow;
+      val = rval;
+    } else {
+      const int p = (int)(j - dt);
+      g = eta[p + (int64_t)c * kept];
+      const int col = kept_idx[p];
+      a = cptr[col];
+      b = cptr[col + 1];
+      row = crow;
+      val = cval;
+    }
+    if (g == 0.0) continue;
+    for (unsigned long long q = a + lane; q < b; q += 32) atomicAdd(r + row[q], -g * (double)val[q]);
   }
-  for (int p = threadIdx.x; p < kept; p += blockDim.x) {
-    const double g = eta[p + (int64_t)c * kept];
-    const int col = kept_idx[p];
-    if (g != 0.0)
-      for (unsigned long long q = cptr[col]; q < cptr[col + 1]; ++q)
-        atomicAdd(r + crow[q], -g * (double)cval[q]);
-  }
-  __syncthreads();
+}
+
+__global__ void k_resid_norm(int64_t n_rows, const int* __restrict__ sus,
+                             const double* __restrict__ xnorm2, const double* __restrict__ rbuf,
+                             double* __restrict__ ratio) {
+  __shared__ double part[32];
+  const int c = blockIdx.x;
+  const double* r = rbuf + (int64_t)c * n_rows;
   double acc = 0.0;
   for (int64_t i = threadIdx.x; i < n_rows; i += blockDim.x) acc = fma(r[i], r[i], acc);
   for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -99,12 +120,13 @@ __global__ void k_explicit_residual(int64_t n_rows, const unsigned long long* __
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
-    const double xn = xnorm2[k];
+    const double xn = xnorm2[sus[c]];
     ratio[c] = xn > 0.0 ? sqrt(t) / sqrt(xn) : 0.0;
   }
 }
 
-// h_R(j, c) = R^(t)(:, j) . r_c ; h_K(p, c) = x_{K[p]} . r_c for K[p] < k_c (else 0)
+// h_R(j, c) = R^(t)(:, j) . r_c ; h_K(p, c) = x_{K[p]} . r_c for K[p] < k_c (else 0);
+// a warp per column, grid (suspect, slice of columns)
 __global__ void k_residual_dots(int64_t n_rows, const unsigned long long* __restrict__ cptr,
                                 const int32_t* __restrict__ crow, const int32_t* __restrict__ cval,
                                 int64_t dt, const unsigned long long* __restrict__ rptr,
@@ -114,20 +136,41 @@ __global__ void k_residual_dots(int64_t n_rows, const unsigned long long* __rest
                                 double* __restrict__ hR, double* __restrict__ hK) {
   const int c = blockIdx.x;
   const int k = sus[c];
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t nw = (int64_t)gridDim.y * (blockDim.x >> 5);
   const double* r = rbuf + (int64_t)c * n_rows;
-  for (int64_t j = threadIdx.x; j < dt; j += blockDim.x) {
+  for (int64_t j = gw; j < dt + kept; j += nw) {
+    unsigned long long a = 0, b = 0;
+    const int32_t *row = crow, *val = cval;
+    if (j < dt) {
+      a = rptr[j];
+      b = rptr[j + 1];
+      row = rrow;
+      val = rval;
+    } else {
+      const int col = kept_idx[j - dt];
+      if (col < k) {
+        a = cptr[col];
+        b = cptr[col + 1];
+      }
+    }
     double s = 0.0;
-    for (unsigned long long q = rptr[j]; q < rptr[j + 1]; ++q) s = fma((double)rval[q], r[rrow[q]], s);
-    hR[j + (int64_t)c * dt] = s;
+    for (unsigned long long q = a + lane; q < b; q += 32) s = fma((double)val[q], r[row[q]], s);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      if (j < dt)
+        hR[j + (int64_t)c * dt] = s;
+      else
+        hK[(j - dt) + (int64_t)c * kept] = s;
+    }
   }
-  for (int p = threadIdx.x; p < kept; p += blockDim.x) {
-    const int col = kept_idx[p];
-    double s = 0.0;
-    if (col < k)
-      for (unsigned long long q = cptr[col]; q < cptr[col + 1]; ++q)
-        s = fma((double)cval[q], r[crow[q]], s);
-    hK[p + (int64_t)c * kept] = s;
-  }
+}
+
+// columns per suspect spread over this many blocks
+unsigned slices_for(int64_t ncols, int ns) {
+  const int64_t want = std::max<int64_t>(1, (int64_t)num_sms() * 4 / std::max(ns, 1));
+  return (unsigned)std::min<int64_t>(want, std::max<int64_t>(1, (ncols + 7) / 8));
 }
 
 // zero entries (p, c) whose kept column is not before suspect c
@@ -236,10 +279,14 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
       }
       tri_solve_lower_T(in.Lt, in.ldl, in.dt, gammaR, in.dt, ns, st);
     }
-    CTD_LAUNCH(k_explicit_residual, (ns), (256), 0, st, in.n_rows,
+    const unsigned ny = slices_for(in.dt + kept, ns);
+    CTD_LAUNCH(k_resid_init, (ns), (256), 0, st, in.n_rows,
+               reinterpret_cast<const unsigned long long*>(in.cptr), in.crow, in.cval, d_sus, rbuf);
+    CTD_LAUNCH(k_resid_update, (dim3(ns, ny)), (256), 0, st, in.n_rows,
                reinterpret_cast<const unsigned long long*>(in.cptr), in.crow, in.cval, in.dt,
                reinterpret_cast<const unsigned long long*>(in.rptr), in.rrow, in.rval, gammaR,
-               out.idx, kept, eta, d_sus, xn2, rbuf, ratio, 1);
+               out.idx, kept, eta, rbuf);
+    CTD_LAUNCH(k_resid_norm, (ns), (256), 0, st, in.n_rows, d_sus, xn2, rbuf, ratio);
     // one step of iterative refinement: solve the normal equations again for
     // the residual's remaining component in range([R^(t), kept before k])
     {
@@ -248,7 +295,7 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
       CTD_TRY(scratch.get(&zK, (size_t)kk * ns));
       CTD_TRY(scratch.get(&etad, (size_t)kk * ns));
       if (in.dt > 0) CTD_TRY(scratch.get(&hR, (size_t)in.dt * ns));
-      CTD_LAUNCH(k_residual_dots, (ns), (256), 0, st, in.n_rows,
+      CTD_LAUNCH(k_residual_dots, (dim3(ns, ny)), (256), 0, st, in.n_rows,
                  reinterpret_cast<const unsigned long long*>(in.cptr), in.crow, in.cval, in.dt,
                  reinterpret_cast<const unsigned long long*>(in.rptr), in.rrow, in.rval, out.idx,
                  kept, d_sus, rbuf, hR, hK);
@@ -275,10 +322,11 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
           dgemm(false, false, in.dt, ns, kept, -1.0, WK, in.dt, etad, kept, 1.0, hR, in.dt, st);
         tri_solve_lower_T(in.Lt, in.ldl, in.dt, hR, in.dt, ns, st);  // delta gamma_R
       }
-      CTD_LAUNCH(k_explicit_residual, (ns), (256), 0, st, in.n_rows,
+      CTD_LAUNCH(k_resid_update, (dim3(ns, ny)), (256), 0, st, in.n_rows,
                  reinterpret_cast<const unsigned long long*>(in.cptr), in.crow, in.cval, in.dt,
                  reinterpret_cast<const unsigned long long*>(in.rptr), in.rrow, in.rval, hR,
-                 out.idx, kept, etad, d_sus, xn2, rbuf, ratio, 0);
+                 out.idx, kept, etad, rbuf);
+      CTD_LAUNCH(k_resid_norm, (ns), (256), 0, st, in.n_rows, d_sus, xn2, rbuf, ratio);
     }
     std::vector<double> h_ratio(ns);
     CTD_TRY(d2h(h_ratio.data(), ratio, ns, st));

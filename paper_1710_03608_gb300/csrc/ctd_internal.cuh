@@ -217,14 +217,15 @@ void launch_c_bounds(const CscDev& X, int64_t n_cols, const CsrDev& R, uint32_t*
 // ascending (16-bit row indices).  Values stored as float (fp32 != 0) or
 // double.  R's rows must be sorted by column.  positive: every value of X
 // and R is > 0 (enables the one-nonzero copy path).
-ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
-                         const uint64_t* coff, uint32_t* ccnt, uint16_t* crow, void* cval,
-                         int fp32, int positive, uint64_t sqnorm_X, cudaStream_t st);
+ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t nnz,
+                         const CsrDev& R, const uint64_t* coff, uint32_t* ccnt, uint16_t* crow,
+                         void* cval, int fp32, int positive, uint64_t sqnorm_X, cudaStream_t st);
 // The same with the longest rows of R dense in shared memory and register
 // accumulators (ctd_cfill.cu); requires sqnorm_X < 2^31 and width <= 1024.
-ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
-                             const uint64_t* coff, uint32_t* ccnt, uint16_t* crow, void* cval,
-                             int fp32, int positive, cudaStream_t st);
+ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t nnz,
+                             const CsrDev& R, const uint64_t* coff, uint32_t* ccnt,
+                             uint16_t* crow, void* cval, int fp32, int positive,
+                             cudaStream_t st);
 // list[0..count) = columns with >= minc nonzeros and a nonzero C bound
 void launch_list_columns(const uint64_t* colptr, const uint64_t* coff, int64_t n_cols,
                          uint64_t minc, int64_t* list, unsigned* count, cudaStream_t st);

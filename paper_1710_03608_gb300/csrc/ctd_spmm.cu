@@ -390,9 +390,9 @@ static ctd_status c_fill_impl(const CscDev& X, int64_t n_cols, const CsrDev& R,
   return CTD_OK;
 }
 
-ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
-                         const uint64_t* coff, uint32_t* ccnt, uint16_t* crow, void* cval,
-                         int fp32, int positive, uint64_t sqnorm_X, cudaStream_t st) {
+ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t nnz,
+                         const CsrDev& R, const uint64_t* coff, uint32_t* ccnt, uint16_t* crow,
+                         void* cval, int fp32, int positive, uint64_t sqnorm_X, cudaStream_t st) {
   if (n_cols <= 0) return CTD_OK;
   if (R.width <= 0) {
     CTD_CUDA(cudaMemsetAsync(ccnt, 0, n_cols * sizeof(uint32_t), st));
@@ -402,7 +402,8 @@ ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, const 
   // integer partial sums fit int32 (Cauchy-Schwarz) and the warp's register
   // accumulators cover the width: dense long rows + registers
   if (sqnorm_X < (1ull << 31) && R.width <= 1024)
-    return c_fill_dense_rows(X, n_cols, n_rows, R, coff, ccnt, crow, cval, fp32, positive, st);
+    return c_fill_dense_rows(X, n_cols, n_rows, nnz, R, coff, ccnt, crow, cval, fp32, positive,
+                             st);
   unsigned long long* work;
   int64_t* heavy;
   unsigned* nheavy;
@@ -536,7 +537,7 @@ template <typename T, int NK>
 __global__ void __launch_bounds__(QF_THREADS, (NK >= 8 ? 1 : 2))
     k_qform(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs, int nblk,
             const T* __restrict__ qn, const short* __restrict__ slot_of,
-            const int* __restrict__ hot_rows, int n_hot, int64_t n_rows,
+            const int* __restrict__ hot_rows, int n_hot, int64_t n_rows, int grab,
             unsigned long long* work, double* __restrict__ partial) {
   using VT = typename Vec16<T>::type;
   constexpr int VEC = Vec16<T>::n;
@@ -549,11 +550,11 @@ __global__ void __launch_bounds__(QF_THREADS, (NK >= 8 ? 1 : 2))
   const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(X.colptr);
   while (true) {
     unsigned long long f0 = 0;
-    if (lane == 0) f0 = atomicAdd(work, 32ull);
+    if (lane == 0) f0 = atomicAdd(work, (unsigned long long)grab);
     f0 = __shfl_sync(0xffffffffu, f0, 0);
     if (f0 >= (unsigned long long)n_cols) break;
     // lane l: column f0 + l's range; a one-nonzero column is settled here
-    const int64_t fl = (int64_t)f0 + lane;
+    const int64_t fl = lane < grab ? (int64_t)f0 + lane : n_cols;  // lanes past the grab idle
     unsigned long long la = 0, lb = 0;
     T total = (T)0;  // this lane's column; FP32 sums on the FP32 path (GB300's FP64 pipe is narrow)
     if (fl < n_cols) {
@@ -630,7 +631,7 @@ __global__ void __launch_bounds__(QF_THREADS, (NK >= 8 ? 1 : 2))
       if (lane == e) total += ss;  // lane e owns column f0 + e
     }
     for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
-    if (lane == 0) partial[f0 / 32] = (double)total;
+    if (lane == 0) partial[f0 / grab] = (double)total;
   }
 }
 
@@ -683,11 +684,17 @@ static ctd_status sum_f64(const double* in, int64_t n, double* out, Arena& scrat
   return CTD_OK;
 }
 
+// Columns per warp grab: 32 (one per lane's metadata prefetch) unless that
+// would leave most warps idle (few columns, as in one CTD-D slice).
+static int qform_grab(int64_t n_cols, int64_t warps) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(32, n_cols / std::max<int64_t>(warps * 4, 1)));
+}
+
 template <typename T, int NK>
 static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int qs, int nblk,
                                const T* qn, const short* slot_of, const int* hot, int n_hot,
-                               int64_t n_rows, unsigned long long* work, double* partial,
-                               cudaStream_t st) {
+                               int64_t n_rows, unsigned long long* work, double** partial,
+                               int64_t* nparts, Arena& scratch, cudaStream_t st) {
   const size_t smem = (size_t)n_hot * qs * sizeof(T);
   if (smem > 48 * 1024)
     CTD_TRY(allow_max_smem((const void*)k_qform<T, NK>));
@@ -695,8 +702,13 @@ static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int 
   CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qform<T, NK>, QF_THREADS,
                                                          smem));
   if (per_sm < 1) return fail(CTD_ECUDA, "error kernel does not fit on an SM");
-  CTD_LAUNCH((k_qform<T, NK>), (num_sms() * per_sm), (QF_THREADS), smem, st, X, n_cols, Q, qs, nblk,
-             qn, slot_of, hot, n_hot, n_rows, work, partial);
+  const int64_t blocks = (int64_t)num_sms() * per_sm;
+  const int grab = qform_grab(n_cols, blocks * (QF_THREADS / 32));
+  *nparts = (n_cols + grab - 1) / grab;
+  CTD_TRY(scratch.get(partial, *nparts));
+  CTD_CUDA(cudaMemsetAsync(*partial, 0, *nparts * sizeof(double), st));
+  CTD_LAUNCH((k_qform<T, NK>), (blocks), (QF_THREADS), smem, st, X, n_cols, Q, qs, nblk,
+             qn, slot_of, hot, n_hot, n_rows, grab, work, *partial);
   return CTD_OK;
 }
 
@@ -711,14 +723,12 @@ ctd_status launch_qform_rows(const CscDev& X, int64_t n_cols, const double* Q, i
   if (ld % 512 != 0 || ld < width) return fail(CTD_EINVAL, "Q row stride must be a multiple of 512");
   const int nblk = (int)((width + 255) / 256);  // 256 columns (4 loads per lane) per block
   unsigned long long* work;
-  double* partial;
-  const int64_t nchunks = (n_cols + 31) / 32;
+  double* partial = nullptr;
+  int64_t nchunks = 0;
   CTD_TRY(scratch.get(&work, 1));
-  CTD_TRY(scratch.get(&partial, nchunks));
   CTD_CUDA(cudaMemsetAsync(work, 0, 8, st));
-  CTD_CUDA(cudaMemsetAsync(partial, 0, nchunks * sizeof(double), st));
   CTD_TRY((qform_launch<double, 4>(X, n_cols, Q, (int)ld, nblk, qn, nullptr, nullptr, 0, n_rows,
-                                   work, partial, st)));
+                                   work, &partial, &nchunks, scratch, st)));
   CTD_TRY(sum_f64(partial, nchunks, out, scratch, st));
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
@@ -742,16 +752,15 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
   NK = NK <= 1 ? 1 : NK <= 2 ? 2 : NK <= 4 ? 4 : 8;  // the kernel's compiled widths
   const int qs = nblk * NK * span;              // each Q row holds exactly NK loads per lane per block
   void *Q, *qn;
-  double* partial;
+  double* partial = nullptr;
+  int64_t nchunks = 0;
   short* slot_of;
   int* hot;
   unsigned long long* work;
-  const int64_t nchunks = (n_cols + 31) / 32;
   CTD_TRY(scratch.get(reinterpret_cast<unsigned char**>(&Q), (size_t)n_rows * qs * tsz));
   CTD_TRY(scratch.get(reinterpret_cast<unsigned char**>(&qn), (size_t)n_rows * tsz));
   CTD_TRY(scratch.get(&slot_of, n_rows));
   CTD_TRY(scratch.get(&work, 1));
-  CTD_TRY(scratch.get(&partial, nchunks));
   // hot rows (one register block wide only): as many as fit in ~100 KB of
   // shared memory, so two blocks of 16 warps stay resident per SM
   const size_t budget = 100 * 1024;
@@ -765,7 +774,6 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
   if (n_hot)
     CTD_CUDA(cudaMemcpyAsync(hot, hot_rows_host, n_hot * sizeof(int), cudaMemcpyHostToDevice, st));
   CTD_CUDA(cudaMemsetAsync(work, 0, 8, st));
-  CTD_CUDA(cudaMemsetAsync(partial, 0, nchunks * sizeof(double), st));
   const unsigned gq = grid_for(n_rows * qs, 256, (int64_t)num_sms() * 16);
   const unsigned gn = grid_for(n_rows * 32, 256, (int64_t)num_sms() * 8);
   if (fp32) {
@@ -783,10 +791,10 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
 #define QF(NKV)                                                                                 \
   rc = fp32 ? qform_launch<float, NKV>(X, n_cols, static_cast<const float*>(Q), qs, nblk,     \
                                        static_cast<const float*>(qn), slot_of, hot, n_hot,     \
-                                       n_rows, work, partial, st)                              \
+                                       n_rows, work, &partial, &nchunks, scratch, st)          \
             : qform_launch<double, NKV>(X, n_cols, static_cast<const double*>(Q), qs, nblk,    \
                                         static_cast<const double*>(qn), slot_of, hot, n_hot,   \
-                                        n_rows, work, partial, st)
+                                        n_rows, work, &partial, &nchunks, scratch, st)
   if (NK <= 1) {
     QF(1);
   } else if (NK <= 2) {
