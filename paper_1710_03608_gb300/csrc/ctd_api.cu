@@ -326,6 +326,9 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   fi.cptr = rc_ptr;
   fi.crow = rc_row;
   fi.cval = rc_val;
+  fi.c_rowptr = rcr_ptr;
+  fi.c_col = rcr_col;
+  fi.c_val = rcr_val;
   fi.n_rows = M.n_rows;
   FilterOut fo;
   STEP(run_filter(fi, fo, scratch, st));

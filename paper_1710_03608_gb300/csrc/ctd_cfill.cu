@@ -142,9 +142,11 @@ __global__ void k_classify(const unsigned long long* __restrict__ xp,
   }
 }
 
-// C(:, f) = v R(i, :) for the single-nonzero columns: a warp per column,
-// four loads in flight per lane before the stores (no shared memory, so
-// every SM keeps 64 warps resident to hide the latency of R's rows).
+// C(:, f) = v R(i, :) for the single-nonzero columns.  A warp takes 32 list
+// entries; lane l loads column l's metadata (list entry, X entry, R row
+// range, output offset) so the dependent loads overlap across the 32
+// columns, then the warp copies the rows one after another with four loads
+// in flight per lane before the stores.  No shared memory: 64 warps per SM.
 template <typename V>
 __global__ void __launch_bounds__(256)
     k_copy_rows(CscDev X, CsrDev R, const int64_t* __restrict__ single,
@@ -156,31 +158,42 @@ __global__ void __launch_bounds__(256)
   const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
   const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(X.colptr);
   const int64_t n = *n_single;
-  for (int64_t w = gw; w < n; w += nw) {
-    const int64_t f = single[w];
-    const unsigned long long xa = xp[f];
-    const int i = __ldg(X.row + xa);
-    const int v = __ldg(X.val + xa);
-    const unsigned long long rs = __ldg(rp + i);
-    const int rl = (int)(__ldg(rp + i + 1) - rs);
-    const unsigned long long o = coff[f];
-    int q = lane;
-    for (; q + 96 < rl; q += 128) {
-      int c4[4], v4[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        c4[u] = __ldg(R.col + rs + q + 32 * u);
-        v4[u] = __ldg(R.val + rs + q + 32 * u);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        crow[o + q + 32 * u] = (uint16_t)c4[u];
-        cval[o + q + 32 * u] = (V)(v * v4[u]);
-      }
+  for (int64_t w0 = gw * 32; w0 < n; w0 += nw * 32) {
+    unsigned long long rs = 0, o = 0;
+    int rl = 0, v = 0;
+    if (w0 + lane < n) {
+      const int64_t f = single[w0 + lane];
+      const unsigned long long xa = xp[f];
+      o = coff[f];
+      const int i = __ldg(X.row + xa);
+      v = __ldg(X.val + xa);
+      rs = __ldg(rp + i);
+      rl = (int)(__ldg(rp + i + 1) - rs);
     }
-    for (; q < rl; q += 32) {
-      crow[o + q] = (uint16_t)__ldg(R.col + rs + q);
-      cval[o + q] = (V)(v * __ldg(R.val + rs + q));
+    const int m = (int)min((int64_t)32, n - w0);
+    for (int e = 0; e < m; ++e) {
+      const unsigned long long rse = __shfl_sync(0xffffffffu, rs, e);
+      const unsigned long long oe = __shfl_sync(0xffffffffu, o, e);
+      const int rle = __shfl_sync(0xffffffffu, rl, e);
+      const int ve = __shfl_sync(0xffffffffu, v, e);
+      int q = lane;
+      for (; q + 96 < rle; q += 128) {
+        int c4[4], v4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          c4[u] = __ldg(R.col + rse + q + 32 * u);
+          v4[u] = __ldg(R.val + rse + q + 32 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          crow[oe + q + 32 * u] = (uint16_t)c4[u];
+          cval[oe + q + 32 * u] = (V)(ve * v4[u]);
+        }
+      }
+      for (; q < rle; q += 32) {
+        crow[oe + q] = (uint16_t)__ldg(R.col + rse + q);
+        cval[oe + q] = (V)(ve * __ldg(R.val + rse + q));
+      }
     }
   }
 }

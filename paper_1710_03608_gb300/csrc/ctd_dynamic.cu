@@ -482,6 +482,9 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
     fi.cptr = rc_ptr;
     fi.crow = rc_row;
     fi.cval = rc_val;
+    fi.c_rowptr = rcr_ptr;
+    fi.c_col = rcr_col;
+    fi.c_val = rcr_val;
     fi.n_rows = M.n_rows;
     if (dt > 0) {
       fi.dt = dt;
@@ -491,6 +494,9 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
       fi.rptr = F->Rcolptr;
       fi.rrow = F->Rrow;
       fi.rval = F->Rval;
+      fi.r_rowptr = F->Rrowptr;
+      fi.r_col = F->Rcol;
+      fi.r_val = F->Rcval;
     }
     CTD_TRY(run_filter(fi, fo, scratch, st));
     rc_ptr_k = rc_ptr;

@@ -55,55 +55,44 @@ __global__ void k_gather_cols(const double* __restrict__ A, int64_t lda, int64_t
 }
 
 // The explicit residual of each suspect c, r_c = x_k - R^(t) gammaR_c -
-// Xc[:, K] eta_c, in three kernels: r_c = x_k (or left as is, to refine it),
-// the subtractions (grid (suspect, slice of columns); a warp walks one
-// column of R^(t) or of the kept candidates, lanes striding over its
-// entries, FP64 atomics into r_c), and ratio_c = ||r_c|| / ||x_k||.
-__global__ void k_resid_init(int64_t n_rows, const unsigned long long* __restrict__ cptr,
-                             const int32_t* __restrict__ crow, const int32_t* __restrict__ cval,
-                             const int* __restrict__ sus, double* __restrict__ rbuf) {
-  const int c = blockIdx.x;
+// Xc[:, K] eta_c, row by row from the by-row layouts (row i of R^(t) and of
+// the candidates, in column order): a fixed order of operations, so the
+// ratio, and every decision and pivot taken from it, is reproducible.  With
+// init = 0 the rows are subtracted from the residual already in rbuf (the
+// refinement step).  kpos maps a candidate to its kept position (-1 if not
+// kept); eta is zero for kept candidates after k_c.
+__global__ void k_resid_rows(int64_t n_rows, const unsigned long long* __restrict__ crp,
+                             const int32_t* __restrict__ ccol, const int32_t* __restrict__ cval,
+                             const unsigned long long* __restrict__ rrp,
+                             const int32_t* __restrict__ rcol, const int32_t* __restrict__ rval,
+                             int64_t dt, const double* __restrict__ gammaR,
+                             const int* __restrict__ kpos, int kept,
+                             const double* __restrict__ eta, const int* __restrict__ sus,
+                             int init, double* __restrict__ rbuf) {
+  const int c = blockIdx.y;
   const int k = sus[c];
   double* r = rbuf + (int64_t)c * n_rows;
-  for (int64_t i = threadIdx.x; i < n_rows; i += blockDim.x) r[i] = 0.0;
-  __syncthreads();
-  for (unsigned long long p = cptr[k] + threadIdx.x; p < cptr[k + 1]; p += blockDim.x)
-    r[crow[p]] = (double)cval[p];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = init ? 0.0 : r[i];
+    double xk = 0.0;
+    for (unsigned long long p = crp[i]; p < crp[i + 1]; ++p) {
+      const int cc = ccol[p];
+      const double v = (double)cval[p];
+      if (cc == k) xk = v;
+      const int q = kept > 0 ? kpos[cc] : -1;
+      if (q >= 0) acc = fma(-eta[q + (int64_t)c * kept], v, acc);
+    }
+    if (dt > 0)
+      for (unsigned long long p = rrp[i]; p < rrp[i + 1]; ++p)
+        acc = fma(-gammaR[rcol[p] + (int64_t)c * dt], (double)rval[p], acc);
+    r[i] = init ? xk + acc : acc;
+  }
 }
 
-__global__ void k_resid_update(int64_t n_rows, const unsigned long long* __restrict__ cptr,
-                               const int32_t* __restrict__ crow, const int32_t* __restrict__ cval,
-                               int64_t dt, const unsigned long long* __restrict__ rptr,
-                               const int32_t* __restrict__ rrow, const int32_t* __restrict__ rval,
-                               const double* __restrict__ gammaR, const int* __restrict__ kept_idx,
-                               int kept, const double* __restrict__ eta, double* __restrict__ rbuf) {
-  const int c = blockIdx.x;
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t)blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int64_t nw = (int64_t)gridDim.y * (blockDim.x >> 5);
-  double* r = rbuf + (int64_t)c * n_rows;
-  for (int64_t j = gw; j < dt + kept; j += nw) {
-    double g;
-    unsigned long long a, b;
-    const int32_t *row, *val;
-    if (j < dt) {
-      g = gammaR[j + (int64_t)c * dt];
-      a = rptr[j];
-      b = rptr[j + 1];
-      row = rrow;
-      val = rval;
-    } else {
-      const int p = (int)(j - dt);
-      g = eta[p + (int64_t)c * kept];
-      const int col = kept_idx[p];
-      a = cptr[col];
-      b = cptr[col + 1];
-      row = crow;
-      val = cval;
-    }
-    if (g == 0.0) continue;
-    for (unsigned long long q = a + lane; q < b; q += 32) atomicAdd(r + row[q], -g * (double)val[q]);
-  }
+__global__ void k_kpos(const int* __restrict__ idx, int kept, int* __restrict__ kpos) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < kept; p += gridDim.x * blockDim.x)
+    kpos[idx[p]] = p;
 }
 
 __global__ void k_resid_norm(int64_t n_rows, const int* __restrict__ sus,
@@ -280,12 +269,17 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
       tri_solve_lower_T(in.Lt, in.ldl, in.dt, gammaR, in.dt, ns, st);
     }
     const unsigned ny = slices_for(in.dt + kept, ns);
-    CTD_LAUNCH(k_resid_init, (ns), (256), 0, st, in.n_rows,
-               reinterpret_cast<const unsigned long long*>(in.cptr), in.crow, in.cval, d_sus, rbuf);
-    CTD_LAUNCH(k_resid_update, (dim3(ns, ny)), (256), 0, st, in.n_rows,
-               reinterpret_cast<const unsigned long long*>(in.cptr), in.crow, in.cval, in.dt,
-               reinterpret_cast<const unsigned long long*>(in.rptr), in.rrow, in.rval, gammaR,
-               out.idx, kept, eta, rbuf);
+    int* kpos;
+    CTD_TRY(scratch.get(&kpos, du));
+    CTD_CUDA(cudaMemsetAsync(kpos, 0xff, (size_t)du * sizeof(int), st));  // -1
+    if (kept > 0)
+      CTD_LAUNCH(k_kpos, (grid_for(kept, 256, 64)), (256), 0, st, out.idx, kept, kpos);
+    const dim3 grows(grid_for(in.n_rows, 256, std::max<int64_t>(1, (int64_t)num_sms() * 4 / ns)),
+                     ns);
+    CTD_LAUNCH(k_resid_rows, (grows), (256), 0, st, in.n_rows,
+               reinterpret_cast<const unsigned long long*>(in.c_rowptr), in.c_col, in.c_val,
+               reinterpret_cast<const unsigned long long*>(in.r_rowptr), in.r_col, in.r_val,
+               in.dt, gammaR, kpos, kept, eta, d_sus, 1, rbuf);
     CTD_LAUNCH(k_resid_norm, (ns), (256), 0, st, in.n_rows, d_sus, xn2, rbuf, ratio);
     // one step of iterative refinement: solve the normal equations again for
     // the residual's remaining component in range([R^(t), kept before k])
@@ -322,10 +316,10 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
           dgemm(false, false, in.dt, ns, kept, -1.0, WK, in.dt, etad, kept, 1.0, hR, in.dt, st);
         tri_solve_lower_T(in.Lt, in.ldl, in.dt, hR, in.dt, ns, st);  // delta gamma_R
       }
-      CTD_LAUNCH(k_resid_update, (dim3(ns, ny)), (256), 0, st, in.n_rows,
-                 reinterpret_cast<const unsigned long long*>(in.cptr), in.crow, in.cval, in.dt,
-                 reinterpret_cast<const unsigned long long*>(in.rptr), in.rrow, in.rval, hR,
-                 out.idx, kept, etad, rbuf);
+      CTD_LAUNCH(k_resid_rows, (grows), (256), 0, st, in.n_rows,
+                 reinterpret_cast<const unsigned long long*>(in.c_rowptr), in.c_col, in.c_val,
+                 reinterpret_cast<const unsigned long long*>(in.r_rowptr), in.r_col, in.r_val,
+                 in.dt, hR, kpos, kept, etad, d_sus, 0, rbuf);
       CTD_LAUNCH(k_resid_norm, (ns), (256), 0, st, in.n_rows, d_sus, xn2, rbuf, ratio);
     }
     std::vector<double> h_ratio(ns);

@@ -346,6 +346,14 @@ struct FilterIn {
   const uint64_t* rptr = nullptr;
   const int32_t* rrow = nullptr;
   const int32_t* rval = nullptr;
+  // the same two matrices by row (rows sorted by column), for the explicit
+  // residuals: candidates (n_rows x du) and R^(t) (n_rows x dt)
+  const uint64_t* c_rowptr = nullptr;
+  const int32_t* c_col = nullptr;
+  const int32_t* c_val = nullptr;
+  const uint64_t* r_rowptr = nullptr;
+  const int32_t* r_col = nullptr;
+  const int32_t* r_val = nullptr;
   int64_t n_rows = 0;
 };
 // keep[du], idx[kept] (device), count (device, = kept), Lk = factor of the

@@ -10,6 +10,8 @@
   python -m paper_1710_03608_gb300.measure stream [--steps T] [--scale F]
       one CTD-D stream of 2*10^4 x 2*10^4 slices (500K nonzeros each, planted
       block at steps 40-45); per-step nonzeros/s and d~_t.
+  python -m paper_1710_03608_gb300.measure ncu-summary LAUNCHES.csv
+      per-kernel launches, time and share of an ncu launch list (no GPU).
 
 All times are host wall-clock around calls that wait for their work (the
 library's entry points return when the device is done), inputs in HBM.
@@ -194,9 +196,60 @@ def stream(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# summaries of ncu output (text in, text out; no GPU)
+# ---------------------------------------------------------------------------
+def ncu_launch_summary(csv_path: str, top: int = 30) -> str:
+    """Per kernel: launches, total time and share of an `ncu --metrics
+    gpu__time_duration.sum --csv` launch list (serialized, cold-cache times:
+    compare shares, not absolutes)."""
+    import collections
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    h = rows[hi]
+    ki, vi, ui = h.index("Kernel Name"), h.index("Metric Value"), h.index("Metric Unit")
+    scale = {"ns": 1e-6, "nsecond": 1e-6, "us": 1e-3, "usecond": 1e-3, "ms": 1.0,
+             "msecond": 1.0, "s": 1e3, "second": 1e3}
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    for r in rows[hi + 1:]:
+        if len(r) <= vi:
+            continue
+        name = r[ki].split("(")[0].replace("void ", "")
+        agg[name][0] += 1
+        agg[name][1] += float(r[vi].replace(",", "")) * scale.get(r[ui], 1.0)
+    tot = sum(v[1] for v in agg.values())
+    lines = [f"{'kernel':48s} {'launches':>8s} {'total ms':>10s} {'share':>7s}"]
+    for n, (c, t) in sorted(agg.items(), key=lambda x: -x[1][1])[:top]:
+        lines.append(f"{n:48s} {c:8d} {t:10.3f} {100 * t / tot:6.2f}%")
+    lines.append(f"total: {sum(v[0] for v in agg.values())} launches, {tot:.3f} ms")
+    return "\n".join(lines)
+
+
+def ncu_metrics_summary(rep_path: str, kernel_regex: str, names) -> dict:
+    """Selected raw metrics of the captured launches of one kernel from an
+    `ncu -o` report (read with `ncu -i ... --page raw --csv`)."""
+    import csv
+    import re
+    import subprocess
+    out = subprocess.run(["ncu", "-i", rep_path, "--page", "raw", "--csv"],
+                         capture_output=True, text=True, check=True).stdout
+    rows = list(csv.reader(out.splitlines()))
+    h = rows[0]
+    res = []
+    for r in rows[2:]:
+        if not re.search(kernel_regex, r[h.index("Kernel Name")]):
+            continue
+        res.append({k: r[h.index(k)] for k in names if k in h})
+    return {"launches": res}
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
+    ns = sub.add_parser("ncu-summary")
+    ns.add_argument("csv")
+    ns.add_argument("--top", type=int, default=30)
     b = sub.add_parser("batched")
     b.add_argument("--count", type=int, default=256)
     b.add_argument("--workers", type=int, default=0)
@@ -213,6 +266,9 @@ def main():
     sm.add_argument("--scale", type=float, default=1.0)
     sm.add_argument("--d", type=int, default=400)
     args = ap.parse_args()
+    if args.cmd == "ncu-summary":
+        print(ncu_launch_summary(args.csv, args.top))
+        return
     import torch
     torch.cuda.set_device(0)
     ctd.load()
