@@ -304,6 +304,9 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   STEP(scratch.get(&rcr_ptr, M.n_rows + 1));
   launch_gather_columns(M.colptr, M.csc_row, M.csc_val, F->Iu, d_count, su, rc_ptr, rc_row,
                         rc_val, st);
+  // rows of each gathered column in ascending order, so every floating-point
+  // sum over a candidate's entries is reproducible
+  launch_sort_segments(rc_ptr, su, rc_row, rc_val, rcr_col, rcr_val, st);
   STEP(build_csr_from_csc(rc_ptr, rc_row, rc_val, su, nnz_cand, M.n_rows, 0, rcr_ptr, rcr_col,
                           rcr_val, scratch, st));
 

@@ -105,40 +105,67 @@ __device__ __forceinline__ void load_dense(const CsrDev& R, const Dense& dn, int
 // R (`single`, count = ub); at least CF_HEAVY_COL nonzeros: `heavy`; else
 // `multi`.  Appends are warp-aggregated; the order inside a list does not
 // matter (every column writes its own output range).
-__global__ void k_classify(const unsigned long long* __restrict__ xp,
-                           const unsigned long long* __restrict__ coff, int64_t n_cols,
-                           int positive, unsigned* __restrict__ ccnt,
-                           int64_t* __restrict__ single, unsigned* __restrict__ n_single,
-                           int64_t* __restrict__ heavy, unsigned* __restrict__ n_heavy,
-                           int64_t* __restrict__ multi, unsigned* __restrict__ n_multi) {
+constexpr int CL_ITEMS = 8;  // columns per thread in k_classify
+
+__global__ void __launch_bounds__(256)
+    k_classify(const unsigned long long* __restrict__ xp,
+               const unsigned long long* __restrict__ coff, int64_t n_cols, int positive,
+               unsigned* __restrict__ ccnt, int64_t* __restrict__ single,
+               unsigned* __restrict__ n_single, int64_t* __restrict__ heavy,
+               unsigned* __restrict__ n_heavy, int64_t* __restrict__ multi,
+               unsigned* __restrict__ n_multi) {
+  __shared__ unsigned cnt[3], base[3];
   const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t f0 = (int64_t)blockIdx.x * blockDim.x; f0 < n_cols; f0 += stride) {
-    const int64_t f = f0 + threadIdx.x;
-    int kind = -1;  // -1 none, 0 single, 1 heavy, 2 multi
-    if (f < n_cols) {
-      const unsigned long long ub = coff[f + 1] - coff[f];
-      const unsigned long long nx = xp[f + 1] - xp[f];
-      if (ub == 0) {
-        ccnt[f] = 0;
-      } else if (nx == 1 && positive) {
-        kind = 0;
-        ccnt[f] = (unsigned)ub;
-      } else {
-        kind = nx >= (unsigned long long)CF_HEAVY_COL ? 1 : 2;
+  const int64_t span = (int64_t)blockDim.x * CL_ITEMS;
+  for (int64_t b0 = (int64_t)blockIdx.x * span; b0 < n_cols; b0 += (int64_t)gridDim.x * span) {
+    if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int kind[CL_ITEMS];
+    unsigned off[CL_ITEMS];
+#pragma unroll
+    for (int u = 0; u < CL_ITEMS; ++u) {
+      const int64_t f = b0 + (int64_t)u * blockDim.x + threadIdx.x;
+      int k = -1;  // -1 none, 0 single, 1 heavy, 2 multi
+      if (f < n_cols) {
+        const unsigned long long ub = coff[f + 1] - coff[f];
+        const unsigned long long nx = xp[f + 1] - xp[f];
+        if (ub == 0) {
+          ccnt[f] = 0;
+        } else if (nx == 1 && positive) {
+          k = 0;
+          ccnt[f] = (unsigned)ub;
+        } else {
+          k = nx >= (unsigned long long)CF_HEAVY_COL ? 1 : 2;
+        }
+      }
+      kind[u] = k;
+      off[u] = 0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const unsigned m = __ballot_sync(0xffffffffu, k == q);
+        if (!m) continue;
+        const int leader = __ffs(m) - 1;
+        unsigned wb = 0;
+        if (lane == leader) wb = atomicAdd(&cnt[q], (unsigned)__popc(m));
+        wb = __shfl_sync(0xffffffffu, wb, leader);
+        if (k == q) off[u] = wb + __popc(m & ((1u << lane) - 1));
       }
     }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const unsigned m = __ballot_sync(0xffffffffu, kind == k);
-      if (!m) continue;
-      unsigned* cnt = k == 0 ? n_single : k == 1 ? n_heavy : n_multi;
-      int64_t* out = k == 0 ? single : k == 1 ? heavy : multi;
-      unsigned base = 0;
-      if (lane == __ffs(m) - 1) base = atomicAdd(cnt, (unsigned)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-      if (kind == k) out[base + __popc(m & ((1u << lane) - 1))] = f;
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      unsigned* g = threadIdx.x == 0 ? n_single : threadIdx.x == 1 ? n_heavy : n_multi;
+      base[threadIdx.x] = cnt[threadIdx.x] ? atomicAdd(g, cnt[threadIdx.x]) : 0;
     }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < CL_ITEMS; ++u) {
+      const int k = kind[u];
+      if (k < 0) continue;
+      const int64_t f = b0 + (int64_t)u * blockDim.x + threadIdx.x;
+      int64_t* out = k == 0 ? single : k == 1 ? heavy : multi;
+      out[base[k] + off[u]] = f;
+    }
+    __syncthreads();
   }
 }
 
@@ -198,73 +225,94 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Accumulate R^T x_f: dense rows into regs (lane's rows 128 q + 4 lane + k),
-// other rows into the shared accumulator acc (atomics).  Warps of a group
-// [gwarp, gwarp + gwarps) take interleaved 32-entry chunks of the column.
+// One chunk of up to 32 column entries, one per lane (sl = dense slot or -1;
+// rs/rl = the R row's range for a sparse row; rl = 0 for idle lanes):
+// dense rows into regs (lane's rows 128 q + 4 lane + k), other rows into the
+// shared accumulator acc (atomics).
+template <int NQ>
+__device__ __forceinline__ void chunk_reg(const CsrDev& R, const int4* __restrict__ dense4,
+                                          int* acc, int (&regs)[4 * NQ], int v, int sl,
+                                          unsigned long long rs, int rl) {
+  constexpr int W4 = NQ * 32;  // int4 per dense row
+  const int lane = threadIdx.x & 31;
+  unsigned dense_b = __ballot_sync(0xffffffffu, sl >= 0);
+  while (dense_b) {
+    const int src = __ffs(dense_b) - 1;
+    dense_b &= dense_b - 1;
+    const int h = __shfl_sync(0xffffffffu, sl, src);
+    const int vs = __shfl_sync(0xffffffffu, v, src);
+    const int4* d = dense4 + h * W4 + lane;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int4 x = d[q * 32];
+      regs[4 * q + 0] += vs * x.x;
+      regs[4 * q + 1] += vs * x.y;
+      regs[4 * q + 2] += vs * x.z;
+      regs[4 * q + 3] += vs * x.w;
+    }
+  }
+  unsigned longs = __ballot_sync(0xffffffffu, rl >= CF_LONG_ROW);
+  while (longs) {
+    const int src = __ffs(longs) - 1;
+    longs &= longs - 1;
+    const unsigned long long s0 = __shfl_sync(0xffffffffu, rs, src);
+    const int n = __shfl_sync(0xffffffffu, rl, src);
+    const int vs = __shfl_sync(0xffffffffu, v, src);
+    // four loads in flight per lane before the atomics
+    int q = lane;
+    for (; q + 96 < n; q += 128) {
+      int c4[4], v4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c4[u] = __ldg(R.col + s0 + q + 32 * u);
+        v4[u] = __ldg(R.val + s0 + q + 32 * u);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) atomicAdd(acc + c4[u], vs * v4[u]);
+    }
+    for (; q < n; q += 32) atomicAdd(acc + __ldg(R.col + s0 + q), vs * __ldg(R.val + s0 + q));
+  }
+  if (rl >= CF_LONG_ROW) rl = 0;
+  if (__any_sync(0xffffffffu, rl > 0))
+    expand_chunk(rs, rl, v, R.col, R.val,
+                 [&](int m, long long prod) { atomicAdd(acc + m, (int)prod); });
+}
+
+// Row metadata of one entry (row i): dense slot, else the R row's range.
+__device__ __forceinline__ void entry_meta(const CsrDev& R, const Dense& dn, int i, int& sl,
+                                           unsigned long long& rs, int& rl) {
+  sl = -1;
+  rs = 0;
+  rl = 0;
+  if (i < 0) return;
+  sl = __ldg(dn.slot + i);
+  if (sl < 0) {
+    const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
+    rs = __ldg(rp + i);
+    rl = (int)(__ldg(rp + i + 1) - rs);
+  }
+}
+
+// Accumulate R^T x_f over the column's entries [a, b): warps of a group
+// [gwarp, gwarp + gwarps) take interleaved 32-entry chunks.
 template <int NQ>
 __device__ __forceinline__ void accumulate_reg(const CscDev& X, const CsrDev& R, const Dense& dn,
-                                               const int4* __restrict__ dense4, int64_t f,
+                                               const int4* __restrict__ dense4,
+                                               unsigned long long a, unsigned long long b,
                                                int* acc, int (&regs)[4 * NQ], int gwarp,
                                                int gwarps) {
-  constexpr int W4 = NQ * 32;  // int4 per dense row
-  const unsigned long long a = X.colptr[f], b = X.colptr[f + 1];
   const int lane = threadIdx.x & 31;
-  const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
   for (unsigned long long p0 = a + (unsigned long long)gwarp * 32; p0 < b;
        p0 += (unsigned long long)gwarps * 32) {
     const unsigned long long p = p0 + lane;
-    unsigned long long rs = 0;
-    int rl = 0, v = 0, sl = -1;
+    int i = -1, v = 0, sl, rl;
+    unsigned long long rs;
     if (p < b) {
-      const int i = __ldg(X.row + p);
+      i = __ldg(X.row + p);
       v = __ldg(X.val + p);
-      sl = __ldg(dn.slot + i);
-      if (sl < 0) {
-        rs = __ldg(rp + i);
-        rl = (int)(__ldg(rp + i + 1) - rs);
-      }
     }
-    unsigned dense_b = __ballot_sync(0xffffffffu, sl >= 0);
-    while (dense_b) {
-      const int src = __ffs(dense_b) - 1;
-      dense_b &= dense_b - 1;
-      const int h = __shfl_sync(0xffffffffu, sl, src);
-      const int vs = __shfl_sync(0xffffffffu, v, src);
-      const int4* d = dense4 + h * W4 + lane;
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const int4 x = d[q * 32];
-        regs[4 * q + 0] += vs * x.x;
-        regs[4 * q + 1] += vs * x.y;
-        regs[4 * q + 2] += vs * x.z;
-        regs[4 * q + 3] += vs * x.w;
-      }
-    }
-    unsigned longs = __ballot_sync(0xffffffffu, rl >= CF_LONG_ROW);
-    while (longs) {
-      const int src = __ffs(longs) - 1;
-      longs &= longs - 1;
-      const unsigned long long s0 = __shfl_sync(0xffffffffu, rs, src);
-      const int n = __shfl_sync(0xffffffffu, rl, src);
-      const int vs = __shfl_sync(0xffffffffu, v, src);
-      // four loads in flight per lane before the atomics
-      int q = lane;
-      for (; q + 96 < n; q += 128) {
-        int c4[4], v4[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          c4[u] = __ldg(R.col + s0 + q + 32 * u);
-          v4[u] = __ldg(R.val + s0 + q + 32 * u);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) atomicAdd(acc + c4[u], vs * v4[u]);
-      }
-      for (; q < n; q += 32) atomicAdd(acc + __ldg(R.col + s0 + q), vs * __ldg(R.val + s0 + q));
-    }
-    if (rl >= CF_LONG_ROW) rl = 0;
-    if (__any_sync(0xffffffffu, rl > 0))
-      expand_chunk(rs, rl, v, R.col, R.val,
-                   [&](int m, long long prod) { atomicAdd(acc + m, (int)prod); });
+    entry_meta(R, dn, i, sl, rs, rl);
+    chunk_reg<NQ>(R, dense4, acc, regs, v, sl, rs, rl);
   }
 }
 
@@ -338,7 +386,7 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
       __syncthreads();
       if (it >= n) break;
       const int64_t f = list[it];
-      accumulate_reg<NQ>(X, R, dn, dense4, f, acc, regs, warp, nw);
+      accumulate_reg<NQ>(X, R, dn, dense4, X.colptr[f], X.colptr[f + 1], acc, regs, warp, nw);
       // fold each warp's registers into the block accumulator
   #pragma unroll
       for (int q = 0; q < NQ; ++q)
@@ -395,23 +443,55 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
     if (lane == 0) i0 = atomicAdd(work, (unsigned long long)grab);
     i0 = __shfl_sync(0xffffffffu, i0, 0);
     if (i0 >= nm) break;
-    unsigned long long o = 0;
+    // lane l: list entry l's column, output offset and entry range
+    unsigned long long o = 0, xa = 0, xb = 0;
     int64_t f = -1;
     if (lane < grab && i0 + lane < nm) {
       f = mlist[i0 + lane];
       o = coff[f];
+      xa = X.colptr[f];
+      xb = X.colptr[f + 1];
     }
     unsigned todo = __ballot_sync(0xffffffffu, f >= 0);
+    // software pipeline over the grabbed columns: the next column's first
+    // chunk (entries, then their row metadata) is loaded while the current
+    // one accumulates and emits
+    int e = todo ? __ffs(todo) - 1 : 0;
+    unsigned long long ea = __shfl_sync(0xffffffffu, xa, e);
+    unsigned long long eb = __shfl_sync(0xffffffffu, xb, e);
+    int ci = -1, cv = 0;
+    if (todo && ea + lane < eb) {
+      ci = __ldg(X.row + ea + lane);
+      cv = __ldg(X.val + ea + lane);
+    }
+    int csl, crl;
+    unsigned long long crs;
+    entry_meta(R, dn, ci, csl, crs, crl);
     while (todo) {
-      const int e = __ffs(todo) - 1;
       todo &= todo - 1;
       const unsigned long long oe = __shfl_sync(0xffffffffu, o, e);
       const int64_t fe = __shfl_sync(0xffffffffu, f, e);
-      accumulate_reg<NQ>(X, R, dn, dense4, fe, acc, regs, 0, 1);
+      // issue the next column's first-chunk loads
+      const int e2 = todo ? __ffs(todo) - 1 : 0;
+      const unsigned long long na = __shfl_sync(0xffffffffu, xa, e2);
+      const unsigned long long nb = __shfl_sync(0xffffffffu, xb, e2);
+      int ni = -1, nv = 0;
+      if (todo && na + lane < nb) {
+        ni = __ldg(X.row + na + lane);
+        nv = __ldg(X.val + na + lane);
+      }
+      chunk_reg<NQ>(R, dense4, acc, regs, cv, csl, crs, crl);
+      if (eb - ea > 32) accumulate_reg<NQ>(X, R, dn, dense4, ea + 32, eb, acc, regs, 0, 1);
+      // the next column's row metadata, then this column's emission
+      entry_meta(R, dn, ni, csl, crs, crl);
+      cv = nv;
       __syncwarp();
       const unsigned n = emit_reg<V, NQ>(acc, regs, oe, crow, cval);
       __syncwarp();
       if (lane == 0) ccnt[fe] = n;
+      e = e2;
+      ea = na;
+      eb = nb;
     }
   }
 }
@@ -447,7 +527,7 @@ ctd_status cf_all(int nq, const CscDev& X, int64_t n_cols, const CsrDev& R, cons
   CTD_TRY(a.get(&work, 2));
   CTD_CUDA(cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned), st));
   CTD_CUDA(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), st));
-  CTD_LAUNCH(k_classify, (grid_for(n_cols, 256, (int64_t)num_sms() * 16)), (256), 0, st,
+  CTD_LAUNCH(k_classify, (grid_for(n_cols, 256 * CL_ITEMS, (int64_t)num_sms() * 8)), (256), 0, st,
              reinterpret_cast<const unsigned long long*>(X.colptr), coff, n_cols, positive, ccnt,
              single, counts, heavy, counts + 1, multi, counts + 2);
   CTD_LAUNCH(k_copy_rows<V>, (num_sms() * 8), (256), 0, st, X, R, single, counts, coff, crow,

@@ -280,6 +280,11 @@ __global__ void k_qt_times_sparse(const unsigned long long* __restrict__ cptr,
   }
 }
 
+__global__ void k_i32_to_i64(const int* __restrict__ in, int n, int64_t* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+    out[e] = in[e];
+}
+
 // y += x (n entries)
 __global__ void k_axpy_f64(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -453,6 +458,9 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
     CTD_TRY(scratch.get(&rcr_ptr, M.n_rows + 1));
     launch_gather_columns(M.colptr, M.csc_row, M.csc_val, D.lastIu, d_count, du, rc_ptr, rc_row,
                           rc_val, st);
+    // rows of each gathered column in ascending order, so every floating-point
+    // sum over a candidate's entries is reproducible
+    launch_sort_segments(rc_ptr, du, rc_row, rc_val, rcr_col, rcr_val, st);
     CTD_TRY(build_csr_from_csc(rc_ptr, rc_row, rc_val, du, (int64_t)nnz_cand, M.n_rows, 0,
                                rcr_ptr, rcr_col, rcr_val, scratch, st));
     // Gram of the candidates and the Schur complement against R^(t)
@@ -590,7 +598,12 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
       CTD_TRY(scratch.get(&nsz, kept + 1));
       CTD_TRY(scratch.get(&nptr, kept + 1));
       launch_gather_i64(D.lastIu, idx, fo.count, kept, newf, st);
-      launch_column_sizes(M.colptr, newf, fo.count, kept, nsz, st);
+      // the new columns come from the candidates' (row-sorted) CSC, by kept
+      // position, so R's columns keep a reproducible row order
+      int64_t* kp64;
+      CTD_TRY(scratch.get(&kp64, kept));
+      CTD_LAUNCH(k_i32_to_i64, (grid_for(kept, 256, 64)), (256), 0, st, idx, kept, kp64);
+      launch_column_sizes(rc_ptr_k, kp64, fo.count, kept, nsz, st);
       launch_scan_u64(nsz, nptr, kept, false, M.tmp, M.status, st);
       uint64_t nnz_new = 0;
       std::vector<int64_t> hf(kept);
@@ -605,7 +618,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
       CTD_TRY(grow_array(&F->Rrow, nnzR, nnzR + (int64_t)nnz_new, &cap_nnz_r, st));
       CTD_TRY(grow_array(&F->Rval, nnzR, nnzR + (int64_t)nnz_new, &cap_nnz_v, st));
       D.cap_nnz = cap_nnz_r;
-      launch_gather_columns(M.colptr, M.csc_row, M.csc_val, newf, fo.count, kept, nptr,
+      launch_gather_columns(rc_ptr_k, rc_row_k, rc_val_k, kp64, fo.count, kept, nptr,
                             F->Rrow + nnzR, F->Rval + nnzR, st);
       CTD_LAUNCH(k_add_offset, (grid_for(kept + 1, 256, 64)), (256), 0, st,
                  reinterpret_cast<const unsigned long long*>(nptr), kept + 1,

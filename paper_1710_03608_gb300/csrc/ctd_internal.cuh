@@ -230,6 +230,10 @@ ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, in
 void launch_list_columns(const uint64_t* colptr, const uint64_t* coff, int64_t n_cols,
                          uint64_t minc, int64_t* list, unsigned* count, cudaStream_t st);
 // Sort each row of a row-major factor by column (col/val copied to *_out).
+// Sort every segment of (ptr, idx, val) by idx in place (tmp_* hold as many
+// entries as idx; used for segments longer than 2048).
+void launch_sort_segments(const uint64_t* ptr, int64_t nseg, int32_t* idx, int32_t* val,
+                          int32_t* tmp_idx, int32_t* tmp_val, cudaStream_t st);
 void launch_sort_rows(const uint64_t* rowptr, int64_t n_rows, const int32_t* col_in,
                       const int32_t* val_in, int32_t* col_out, int32_t* val_out, cudaStream_t st);
 

@@ -453,6 +453,78 @@ __global__ void k_sort_rows(const unsigned long long* __restrict__ rowptr, int64
   }
 }
 
+// Sort each segment of a compressed layout by index (values follow), in
+// place: a block per segment, bitonic in shared memory up to 2048 entries;
+// longer segments rank each entry by counting (indices within a segment are
+// distinct).  Used to give gathered columns a reproducible order.
+constexpr int SEG_SORT_MAX = 2048;
+
+__global__ void __launch_bounds__(256)
+    k_sort_segments(const unsigned long long* __restrict__ ptr, int64_t nseg,
+                    int32_t* __restrict__ idx, int32_t* __restrict__ val,
+                    int32_t* __restrict__ tmp_idx, int32_t* __restrict__ tmp_val) {
+  __shared__ int32_t ks[SEG_SORT_MAX];
+  __shared__ int32_t vs[SEG_SORT_MAX];
+  for (int64_t g = blockIdx.x; g < nseg; g += gridDim.x) {
+    const unsigned long long a = ptr[g], b = ptr[g + 1];
+    const int n = (int)(b - a);
+    if (n <= 1) continue;
+    if (n <= SEG_SORT_MAX) {
+      int m = 1;
+      while (m < n) m <<= 1;
+      for (int e = threadIdx.x; e < m; e += blockDim.x) {
+        ks[e] = e < n ? idx[a + e] : INT32_MAX;
+        vs[e] = e < n ? val[a + e] : 0;
+      }
+      __syncthreads();
+      for (int k = 2; k <= m; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int e = threadIdx.x; e < m; e += blockDim.x) {
+            const int o = e ^ j;
+            if (o > e) {
+              const bool up = (e & k) == 0;
+              if ((ks[e] > ks[o]) == up) {
+                const int32_t tk = ks[e], tv = vs[e];
+                ks[e] = ks[o];
+                vs[e] = vs[o];
+                ks[o] = tk;
+                vs[o] = tv;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        idx[a + e] = ks[e];
+        val[a + e] = vs[e];
+      }
+      __syncthreads();
+    } else {
+      for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int32_t me = idx[a + e];
+        int r = 0;
+        for (int q = 0; q < n; ++q) r += idx[a + q] < me;
+        tmp_idx[a + r] = me;
+        tmp_val[a + r] = val[a + e];
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        idx[a + e] = tmp_idx[a + e];
+        val[a + e] = tmp_val[a + e];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+void launch_sort_segments(const uint64_t* ptr, int64_t nseg, int32_t* idx, int32_t* val,
+                          int32_t* tmp_idx, int32_t* tmp_val, cudaStream_t st) {
+  if (nseg <= 0) return;
+  CTD_LAUNCH(k_sort_segments, ((unsigned)std::min<int64_t>(nseg, (int64_t)num_sms() * 8)), (256), 0,
+             st, reinterpret_cast<const unsigned long long*>(ptr), nseg, idx, val, tmp_idx,
+             tmp_val);
+}
+
 void launch_sort_rows(const uint64_t* rowptr, int64_t n_rows, const int32_t* col_in,
                       const int32_t* val_in, int32_t* col_out, int32_t* val_out, cudaStream_t st) {
   if (n_rows <= 0) return;
