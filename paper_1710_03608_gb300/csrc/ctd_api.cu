@@ -270,13 +270,22 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
     launch_sample(M.cdf, M.n_cols, s, seed, 0, 0, F->I, st);
     launch_sort_unique(F->I, s, F->Iu, d_count, st);
   }
+  // candidate column sizes from the device count (entries past it are zero),
+  // so one read-back gives T, s' and nnz(R') together
+  std::unique_ptr<PhaseScope> ph_cand(new PhaseScope("candidates", st));
+  uint64_t *rc_ptr, *rc_sizes;
+  STEP(scratch.get(&rc_sizes, s + 1));
+  STEP(scratch.get(&rc_ptr, s + 1));
+  launch_column_sizes(M.colptr, F->Iu, d_count, (int)s, rc_sizes, st);
+  launch_scan_u64(rc_sizes, rc_ptr, s, false, M.tmp, M.status, st);
   STEPC(cudaGetLastError());
   unsigned status = 0;
   int minval = 0, s_unique = 0;
-  uint64_t T = 0;
+  uint64_t T = 0, nnz_cand = 0;
   STEP(d2h(&status, M.status, 1, st));
   STEP(d2h(&minval, M.minval, 1, st));
   STEP(d2h(&s_unique, d_count, 1, st));
+  STEP(d2h(&nnz_cand, rc_ptr + s, 1, st));
   if (M.n_cols > 0) STEP(d2h(&T, M.cdf + (M.n_cols - 1), 1, st));
   STEP(sync(st));
   STEP(status_from_device(status));
@@ -285,16 +294,6 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   if (T == 0) F->s = 0;  // nothing to draw from
   const int su = s_unique;
 
-  // candidate columns R' (CSC) and their row-major copy
-  std::unique_ptr<PhaseScope> ph_cand(new PhaseScope("candidates", st));
-  uint64_t *rc_ptr, *rc_sizes;
-  STEP(scratch.get(&rc_sizes, su + 1));
-  STEP(scratch.get(&rc_ptr, su + 1));
-  launch_column_sizes(M.colptr, F->Iu, d_count, su, rc_sizes, st);
-  launch_scan_u64(rc_sizes, rc_ptr, su, false, M.tmp, M.status, st);
-  uint64_t nnz_cand = 0;
-  STEP(d2h(&nnz_cand, rc_ptr + su, 1, st));
-  STEP(sync(st));
   int32_t *rc_row, *rc_val, *rcr_col, *rcr_val;
   uint64_t* rcr_ptr;
   STEP(scratch.get(&rc_row, nnz_cand));
@@ -358,18 +357,16 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   STEP(F->mem.get(&F->Rcolptr, kept + 1));
   launch_column_sizes(M.colptr, F->fibers, fo.count, kept, r_sizes, st);
   launch_scan_u64(r_sizes, F->Rcolptr, kept, false, M.tmp, M.status, st);
-  uint64_t nnzR = 0;
-  STEP(d2h(&nnzR, F->Rcolptr + kept, 1, st));
-  STEP(sync(st));
-  F->nnz_R = (int64_t)nnzR;
-  STEP(F->mem.get(&F->Rrow, nnzR));
-  STEP(F->mem.get(&F->Rval, nnzR));
+  // nnz(R) <= nnz(R'): size R by that bound and read nnz(R) at the next read-back
+  const uint64_t nnzR_cap = std::max<uint64_t>(nnz_cand, 1);
+  STEP(F->mem.get(&F->Rrow, nnzR_cap));
+  STEP(F->mem.get(&F->Rval, nnzR_cap));
   STEP(F->mem.get(&F->Rrowptr, M.n_rows + 1));
-  STEP(F->mem.get(&F->Rcol, nnzR));
-  STEP(F->mem.get(&F->Rcval, nnzR));
+  STEP(F->mem.get(&F->Rcol, nnzR_cap));
+  STEP(F->mem.get(&F->Rcval, nnzR_cap));
   launch_gather_columns(M.colptr, M.csc_row, M.csc_val, F->fibers, fo.count, kept, F->Rcolptr,
                         F->Rrow, F->Rval, st);
-  STEP(build_csr_from_csc(F->Rcolptr, F->Rrow, F->Rval, kept, (int64_t)nnzR, M.n_rows, 0,
+  STEP(build_csr_from_csc(F->Rcolptr, F->Rrow, F->Rval, kept, (int64_t)nnzR_cap, M.n_rows, 0,
                           F->Rrowptr, F->Rcol, F->Rcval, scratch, st));
   CsrDev R{F->Rrowptr, F->Rcol, F->Rcval, kept};
   ph_r.reset();
@@ -385,9 +382,11 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
       launch_c_bounds(M.csc(), M.n_cols, R, ub, st);
       launch_scan_u32(ub, F->Coff, M.n_cols, false, M.tmp, M.status, st);
     }
-    uint64_t cap = 0;
+    uint64_t cap = 0, nnzR = 0;
     STEP(d2h(&cap, F->Coff + M.n_cols, 1, st));
+    STEP(d2h(&nnzR, F->Rcolptr + kept, 1, st));
     STEP(sync(st));
+    F->nnz_R = (int64_t)nnzR;
     F->C_cap = cap;
     STEP(F->mem.get(&F->Crow, cap));
     const size_t vsz = precision == CTD_FP32_BULK ? 4 : 8;
@@ -403,26 +402,17 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   // Eq. (error): e = (T - ||Q^T X||_F^2) / T with Q = R L^{-T}
   double* d_pu = nullptr;
   if (!(flags & CTD_SKIP_ERROR) && kept > 0) {
-    std::vector<uint32_t> rc(M.n_rows);
-    STEP(d2h(rc.data(), M.rowcnt, M.n_rows, st));
-    STEP(sync(st));
-    std::vector<int> order(M.n_rows);
-    std::iota(order.begin(), order.end(), 0);
-    const int want = (int)std::min<int64_t>(M.n_rows, 4096);
-    std::partial_sort(order.begin(), order.begin() + want, order.end(),
-                      [&](int a, int b) { return rc[a] > rc[b] || (rc[a] == rc[b] && a < b); });
-    int n_hot = want;
-    while (n_hot > 0 && rc[order[n_hot - 1]] == 0) --n_hot;
     STEP(scratch.get(&d_pu, 1));
     PhaseScope ph("error_qform", st);
-    STEP(launch_error_qform(M.csc(), M.n_cols, M.n_rows, R, Z, kept, nullptr, order.data(), n_hot,
+    STEP(launch_error_qform(M.csc(), M.n_cols, M.n_rows, R, Z, kept, M.rowcnt,
                             precision == CTD_FP32_BULK, d_pu, scratch, st));
   }
   uint64_t* d_nnzc;
   STEP(scratch.get(&d_nnzc, 1));
   if (F->Ccnt) launch_sum_u32(F->Ccnt, M.n_cols, d_nnzc, st);
-  uint64_t nnzC = 0;
+  uint64_t nnzC = 0, nnzR_final = 0;
   double pu = 0.0;
+  STEP(d2h(&nnzR_final, F->Rcolptr + kept, 1, st));
   if (F->Ccnt) STEP(d2h(&nnzC, d_nnzc, 1, st));
   if (d_pu) STEP(d2h(&pu, d_pu, 1, st));
   STEP(d2h(&status, M.status, 1, st));
@@ -430,6 +420,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   STEP(sync(st));
   STEP(status_from_device(status));
   F->nnz_C = (int64_t)nnzC;
+  F->nnz_R = (int64_t)nnzR_final;
   if (!(flags & CTD_SKIP_ERROR)) {
     F->have_err = true;
     F->err = T ? std::max(0.0, ((double)T - pu) / (double)T) : 0.0;

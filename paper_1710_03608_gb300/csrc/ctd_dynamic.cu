@@ -252,14 +252,16 @@ static ctd_status grow_U(ctd_factors* F, int64_t d, int64_t n, cudaStream_t st) 
 
 // W(:, c) = Q^T x_c for sparse columns x_c (CSC) and Q given by rows (row i of
 // Q at Qt + i * ld, first d entries used): a block per column, threads over
-// the d entries, the column's nonzeros in order (deterministic).
+// the d entries, the column's nonzeros in order (deterministic); columns with
+// more than skip_above nonzeros are left to the split kernels.
 __global__ void k_qt_times_sparse(const unsigned long long* __restrict__ cptr,
                                   const int32_t* __restrict__ crow,
                                   const int32_t* __restrict__ cval, int n,
                                   const double* __restrict__ Qt, int64_t ld, int64_t d,
-                                  double* __restrict__ W) {
+                                  unsigned long long skip_above, double* __restrict__ W) {
   for (int c = blockIdx.x; c < n; c += gridDim.x) {
     const unsigned long long a = cptr[c], b = cptr[c + 1];
+    if (b - a > skip_above) continue;  // a heavy column: split over blocks elsewhere
     for (int64_t r0 = 0; r0 < d; r0 += 4 * (int64_t)blockDim.x) {
       double acc[4] = {0.0, 0.0, 0.0, 0.0};
       for (unsigned long long p = a; p < b; ++p) {
@@ -476,9 +478,21 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
         // W = Q^(t)^T X_c (= L^{-1} R^(t)^T X_c, since R^(t) = Q L^T), a sparse
         // product with the basis rows; S = X_c^T X_c - W^T W
         CTD_TRY(scratch.get(&W, (size_t)dt * du));
+        // candidates with more than 256 nonzeros: split over blocks
+        const int64_t max_heavy = std::min<int64_t>(du, (int64_t)nnz_cand / 257);
         CTD_LAUNCH(k_qt_times_sparse, ((unsigned)std::min(du, 65535)), (256), 0, st,
                    reinterpret_cast<const unsigned long long*>(rc_ptr), rc_row, rc_val, du,
-                   F->Qt, D.cap_d, dt, W);
+                   F->Qt, D.cap_d, dt, max_heavy > 0 ? 256ull : ~0ull, W);
+        if (max_heavy > 0) {
+          int64_t* hl;
+          unsigned* nh;
+          CTD_TRY(scratch.get(&hl, max_heavy));
+          CTD_TRY(scratch.get(&nh, 1));
+          CTD_CUDA(cudaMemsetAsync(nh, 0, sizeof(unsigned), st));
+          launch_list_columns_nnz(rc_ptr, du, 257, hl, nh, st);
+          CTD_TRY(launch_heavy_columns(hl, nh, max_heavy, rc_ptr, rc_row, rc_val, F->Qt, D.cap_d,
+                                       dt, W, nullptr, scratch, st));
+        }
         dgemm(true, false, du, du, dt, -1.0, W, dt, W, dt, 1.0, S, du, st);
       }
     }
@@ -672,7 +686,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
     {
       // ||P_{t+1} dX||^2 = ||Q^(t+1)^T dX||_F^2 with the maintained basis Q
       PhaseScope ph("d_error", st);
-      CTD_TRY(launch_qform_rows(M.csc(), M.n_cols, F->Qt, D.cap_d, dn, F->qn, M.n_rows, d_pu,
+      CTD_TRY(launch_qform_rows(M.csc(), M.n_cols, M.nnz, F->Qt, D.cap_d, dn, F->qn, M.n_rows, d_pu,
                                 scratch, st));
     }
     launch_sum_u32(rec.Ccnt, M.n_cols, d_nnzc, st);

@@ -175,8 +175,8 @@ void launch_gather_columns(const uint64_t* colptr, const int32_t* row, const int
                            cudaStream_t st);
 
 // Build a row-major copy (rowptr over n_rows, col, val) of a small CSC with
-// ncols columns whose column c gets index col_base + c.  rowcnt must be
-// zeroed (n_rows entries), `tmp` as for scans.
+// ncols columns whose column c gets index col_base + c; rows are sorted by
+// column.  nnz is an upper bound on the entries (sizes the temporaries).
 ctd_status build_csr_from_csc(const uint64_t* colptr, const int32_t* row, const int32_t* val,
                               int64_t ncols, int64_t nnz, int64_t n_rows, int col_base,
                               uint64_t* rowptr_out, int32_t* col_out, int32_t* val_out,
@@ -238,23 +238,33 @@ void launch_sort_rows(const uint64_t* rowptr, int64_t n_rows, const int32_t* col
                       const int32_t* val_in, int32_t* col_out, int32_t* val_out, cudaStream_t st);
 
 // Relative-error numerator ||Q^T X_(alpha)||_F^2 with Q = R Z^T, Z = L^{-1}
-// (kept x kept, column-major, ld ldz).  hot_rows_host: up to n_hot rows of
-// X (most nonzeros first) whose Q rows are staged in shared memory.
+// (kept x kept, column-major, ld ldz).  The rows of X with the most
+// nonzeros (rowcnt, on the device) have their Q rows staged in shared memory.
 struct CsrX {          // X_(alpha) by row: row i holds (col, val)
   const uint64_t* rowptr;
   const int32_t* col;
   const int32_t* val;
 };
 ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
-                              const double* Z, int64_t ldz, const uint32_t* rowcnt_host_unused,
-                              const int* hot_rows_host, int n_hot, int fp32, double* out,
-                              Arena& scratch, cudaStream_t st);
+                              const double* Z, int64_t ldz, const uint32_t* rowcnt, int fp32,
+                              double* out, Arena& scratch, cudaStream_t st);
 
 // ||Q^T X_(alpha)||_F^2 for FP64 Q by rows (row i at Q + i * ld, ld a
 // multiple of 512, zero past `width`), with row norms qn.
-ctd_status launch_qform_rows(const CscDev& X, int64_t n_cols, const double* Q, int64_t ld,
-                             int64_t width, const double* qn, int64_t n_rows, double* out,
-                             Arena& scratch, cudaStream_t st);
+ctd_status launch_qform_rows(const CscDev& X, int64_t n_cols, int64_t nnz, const double* Q,
+                             int64_t ld, int64_t width, const double* qn, int64_t n_rows,
+                             double* out, Arena& scratch, cudaStream_t st);
+// Columns with at least minc nonzeros: list + count (any order).
+void launch_list_columns_nnz(const uint64_t* colptr, int64_t n_cols, uint64_t minc, int64_t* list,
+                             unsigned* count, cudaStream_t st);
+// For the listed columns f (at most max_heavy, count on the device): y_f =
+// sum over the column's entries of v Q(i, :) (Q by rows, row i at Qt + i*ld,
+// d entries), split over blocks and added in a fixed order; stores y_f in
+// W(:, f) (ld d) when W is given and ||y_f||^2 in norms[h] when given.
+ctd_status launch_heavy_columns(const int64_t* list, const unsigned* nlist, int64_t max_heavy,
+                                const uint64_t* cptr, const int32_t* crow, const int32_t* cval,
+                                const double* Qt, int64_t ld, int64_t d, double* W,
+                                double* norms, Arena& scratch, cudaStream_t st);
 
 // ctd_dense.cu -------------------------------------------------------------
 // C = alpha op(A) op(B) + beta C, column-major FP64.

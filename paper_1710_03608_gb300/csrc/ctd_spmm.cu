@@ -339,6 +339,22 @@ __global__ void k_list_columns(const unsigned long long* __restrict__ colptr,
   }
 }
 
+__global__ void k_list_columns_nnz(const unsigned long long* __restrict__ colptr, int64_t n_cols,
+                                   unsigned long long minc, int64_t* __restrict__ list,
+                                   unsigned* __restrict__ count) {
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < n_cols;
+       f += (int64_t)gridDim.x * blockDim.x)
+    if (colptr[f + 1] - colptr[f] >= minc) list[atomicAdd(count, 1u)] = f;
+}
+
+void launch_list_columns_nnz(const uint64_t* colptr, int64_t n_cols, uint64_t minc, int64_t* list,
+                             unsigned* count, cudaStream_t st) {
+  if (n_cols <= 0) return;
+  CTD_LAUNCH(k_list_columns_nnz, (grid_for(n_cols, 256, (int64_t)num_sms() * 8)), (256), 0, st,
+             reinterpret_cast<const unsigned long long*>(colptr), n_cols,
+             (unsigned long long)minc, list, count);
+}
+
 void launch_list_columns(const uint64_t* colptr, const uint64_t* coff, int64_t n_cols,
                          uint64_t minc, int64_t* list, unsigned* count, cudaStream_t st) {
   if (n_cols <= 0) return;
@@ -610,7 +626,8 @@ __global__ void __launch_bounds__(QF_THREADS, (NK >= 8 ? 1 : 2))
     k_qform(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs, int nblk,
             const T* __restrict__ qn, const short* __restrict__ slot_of,
             const int* __restrict__ hot_rows, int n_hot, int64_t n_rows, int grab,
-            unsigned long long* work, double* __restrict__ partial) {
+            unsigned long long skip_above, unsigned long long* work,
+            double* __restrict__ partial) {
   using VT = typename Vec16<T>::type;
   constexpr int VEC = Vec16<T>::n;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -636,6 +653,8 @@ __global__ void __launch_bounds__(QF_THREADS, (NK >= 8 ? 1 : 2))
         const T v = (T)X.val[la];
         total = v * v * qn[X.row[la]];
         lb = la;  // done
+      } else if (lb - la > skip_above) {
+        lb = la;  // a heavy column: handled by the split kernels
       }
     }
     // columns with two or more nonzeros, one at a time
@@ -766,7 +785,8 @@ template <typename T, int NK>
 static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int qs, int nblk,
                                const T* qn, const short* slot_of, const int* hot, int n_hot,
                                int64_t n_rows, unsigned long long* work, double** partial,
-                               int64_t* nparts, Arena& scratch, cudaStream_t st) {
+                               int64_t* nparts, Arena& scratch, cudaStream_t st,
+                               unsigned long long skip_above = ~0ull) {
   const size_t smem = (size_t)n_hot * qs * sizeof(T);
   if (smem > 48 * 1024)
     CTD_TRY(allow_max_smem((const void*)k_qform<T, NK>));
@@ -780,37 +800,189 @@ static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int 
   CTD_TRY(scratch.get(partial, *nparts));
   CTD_CUDA(cudaMemsetAsync(*partial, 0, *nparts * sizeof(double), st));
   CTD_LAUNCH((k_qform<T, NK>), (blocks), (QF_THREADS), smem, st, X, n_cols, Q, qs, nblk,
-             qn, slot_of, hot, n_hot, n_rows, grab, work, *partial);
+             qn, slot_of, hot, n_hot, n_rows, grab, skip_above, work, *partial);
+  return CTD_OK;
+}
+
+// Columns with many nonzeros, split over blocks.  y_f = sum_p v_p Q(i_p, :)
+// over the column's entries (Q by rows: row i at Qt + i * ld, d entries);
+// block (h, s) forms the partial over the s-th of HS contiguous slices of
+// heavy column list[h]'s entries, then one block per column adds the HS
+// partials in order and either stores y_f (W(:, c), c = the column's index)
+// or adds ||y_f||^2 to out[h].  Fixed order throughout.
+constexpr int HS = 16;
+
+__global__ void __launch_bounds__(256)
+    k_heavy_partial(const int64_t* __restrict__ list, const unsigned* __restrict__ nlist,
+                    const unsigned long long* __restrict__ cptr, const int32_t* __restrict__ crow,
+                    const int32_t* __restrict__ cval, const double* __restrict__ Qt, int64_t ld,
+                    int64_t d, double* __restrict__ P) {
+  const unsigned h = blockIdx.x;
+  if (h >= *nlist) return;
+  const int s = blockIdx.y;
+  const int64_t f = list[h];
+  const unsigned long long a = cptr[f], b = cptr[f + 1];
+  const unsigned long long len = b - a, chunk = (len + HS - 1) / HS;
+  const unsigned long long p0 = a + min(len, chunk * s), p1 = a + min(len, chunk * (s + 1));
+  double* out = P + ((int64_t)h * HS + s) * d;
+  for (int64_t r0 = 0; r0 < d; r0 += 4 * (int64_t)blockDim.x) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (unsigned long long p = p0; p < p1; ++p) {
+      const double v = (double)cval[p];
+      const double* q = Qt + (int64_t)crow[p] * ld;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t r = r0 + threadIdx.x + (int64_t)u * blockDim.x;
+        if (r < d) acc[u] = fma(v, q[r], acc[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t r = r0 + threadIdx.x + (int64_t)u * blockDim.x;
+      if (r < d) out[r] = acc[u];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_heavy_finish(const int64_t* __restrict__ list, const unsigned* __restrict__ nlist,
+                   const double* __restrict__ P, int64_t d, double* __restrict__ W,
+                   double* __restrict__ norms) {
+  __shared__ double part[8];
+  const unsigned h = blockIdx.x;
+  if (h >= *nlist) return;
+  const int64_t f = list[h];
+  double ss = 0.0;
+  for (int64_t r = threadIdx.x; r < d; r += blockDim.x) {
+    double y = 0.0;
+#pragma unroll
+    for (int s = 0; s < HS; ++s) y += P[((int64_t)h * HS + s) * d + r];
+    if (W) W[r + f * d] = y;
+    ss = fma(y, y, ss);
+  }
+  if (!norms) return;
+  for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    norms[h] = t;
+  }
+}
+
+ctd_status launch_heavy_columns(const int64_t* list, const unsigned* nlist, int64_t max_heavy,
+                                const uint64_t* cptr, const int32_t* crow, const int32_t* cval,
+                                const double* Qt, int64_t ld, int64_t d, double* W,
+                                double* norms, Arena& scratch, cudaStream_t st) {
+  if (max_heavy <= 0 || d <= 0) return CTD_OK;
+  double* P;
+  CTD_TRY(scratch.get(&P, (size_t)max_heavy * HS * d));
+  CTD_LAUNCH(k_heavy_partial, (dim3((unsigned)max_heavy, HS)), (256), 0, st, list, nlist,
+             reinterpret_cast<const unsigned long long*>(cptr), crow, cval, Qt, ld, d, P);
+  CTD_LAUNCH(k_heavy_finish, ((unsigned)max_heavy), (256), 0, st, list, nlist, P, d, W, norms);
   return CTD_OK;
 }
 
 // ||Q^T X_(alpha)||_F^2 for a dense FP64 Q given by rows (row i at
 // Q + i * ld, ld a multiple of 512, entries past the used width zero) and
 // its row norms qn; no shared-memory staging.
-ctd_status launch_qform_rows(const CscDev& X, int64_t n_cols, const double* Q, int64_t ld,
-                             int64_t width, const double* qn, int64_t n_rows, double* out,
-                             Arena& scratch, cudaStream_t st) {
+ctd_status launch_qform_rows(const CscDev& X, int64_t n_cols, int64_t nnz, const double* Q,
+                             int64_t ld, int64_t width, const double* qn, int64_t n_rows,
+                             double* out, Arena& scratch, cudaStream_t st) {
   CTD_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
   if (width <= 0 || n_cols <= 0) return CTD_OK;
   if (ld % 512 != 0 || ld < width) return fail(CTD_EINVAL, "Q row stride must be a multiple of 512");
   const int nblk = (int)((width + 255) / 256);  // 256 columns (4 loads per lane) per block
+  // columns with more than HEAVY_SPLIT nonzeros go to the split kernels
+  constexpr unsigned long long HEAVY_SPLIT = 256;
+  const int64_t max_heavy = std::min<int64_t>(n_cols, nnz / (int64_t)(HEAVY_SPLIT + 1));
   unsigned long long* work;
   double* partial = nullptr;
   int64_t nchunks = 0;
   CTD_TRY(scratch.get(&work, 1));
   CTD_CUDA(cudaMemsetAsync(work, 0, 8, st));
   CTD_TRY((qform_launch<double, 4>(X, n_cols, Q, (int)ld, nblk, qn, nullptr, nullptr, 0, n_rows,
-                                   work, &partial, &nchunks, scratch, st)));
+                                   work, &partial, &nchunks, scratch, st,
+                                   max_heavy > 0 ? HEAVY_SPLIT : ~0ull)));
+  if (max_heavy > 0) {
+    int64_t* hl;
+    unsigned* nh;
+    double* all;  // the light partials, then one value per heavy column
+    CTD_TRY(scratch.get(&hl, max_heavy));
+    CTD_TRY(scratch.get(&nh, 1));
+    CTD_TRY(scratch.get(&all, nchunks + max_heavy));
+    CTD_CUDA(cudaMemsetAsync(nh, 0, sizeof(unsigned), st));
+    CTD_CUDA(cudaMemsetAsync(all, 0, (nchunks + max_heavy) * sizeof(double), st));
+    CTD_CUDA(cudaMemcpyAsync(all, partial, nchunks * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_list_columns_nnz(X.colptr, n_cols, HEAVY_SPLIT + 1, hl, nh, st);
+    CTD_TRY(launch_heavy_columns(hl, nh, max_heavy, X.colptr, X.row, X.val, Q, ld, width,
+                                 nullptr, all + nchunks, scratch, st));
+    partial = all;
+    nchunks += max_heavy;
+  }
   CTD_TRY(sum_f64(partial, nchunks, out, scratch, st));
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
 
+// Rows of X with the most nonzeros, chosen on the device: a histogram of
+// min(count, HOT_BINS - 1), the smallest count L >= 1 with at most n_hot
+// rows at or above it, and slots for those rows.
+constexpr int HOT_BINS = 65536;
+
+__global__ void k_hot_hist(const uint32_t* __restrict__ cnt, int64_t n, unsigned* __restrict__ hist) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (cnt[i]) atomicAdd(hist + min(cnt[i], (uint32_t)(HOT_BINS - 1)), 1u);
+}
+
+__global__ void __launch_bounds__(1024)
+    k_hot_threshold(const unsigned* __restrict__ hist, int n_hot, int* __restrict__ thr) {
+  constexpr int PER = HOT_BINS / 1024;
+  __shared__ unsigned part[1024];
+  const int t = threadIdx.x;
+  unsigned s = 0;
+  for (int b = 0; b < PER; ++b) s += hist[t * PER + b];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    // from the top: whole groups while they fit, then bin by bin
+    unsigned above = 0;
+    int L = HOT_BINS;  // none
+    int g = 1023;
+    for (; g >= 0 && above + part[g] <= (unsigned)n_hot; --g) {
+      above += part[g];
+      L = g * PER;
+    }
+    if (g >= 0)
+      for (int b = g * PER + PER - 1; b >= g * PER; --b) {
+        if (above + hist[b] > (unsigned)n_hot) break;
+        above += hist[b];
+        L = b;
+      }
+    thr[0] = max(L, 1);
+  }
+}
+
+__global__ void k_hot_assign(const uint32_t* __restrict__ cnt, int64_t n, const int* __restrict__ thr,
+                             int n_hot, short* __restrict__ slot, int* __restrict__ hot,
+                             int* __restrict__ used) {
+  const uint32_t L = (uint32_t)thr[0];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (min(cnt[i], (uint32_t)(HOT_BINS - 1)) >= L) {
+      const int s = atomicAdd(used, 1);
+      if (s < n_hot) {
+        slot[i] = (short)s;
+        hot[s] = (int)i;
+      }
+    }
+}
+
 ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
-                              const double* Z, int64_t ldz, const uint32_t* rowcnt_host_unused,
-                              const int* hot_rows_host, int n_hot_req, int fp32, double* out,
-                              Arena& scratch, cudaStream_t st) {
-  (void)rowcnt_host_unused;
+                              const double* Z, int64_t ldz, const uint32_t* rowcnt, int fp32,
+                              double* out, Arena& scratch, cudaStream_t st) {
   CTD_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
   if (R.width <= 0 || n_cols <= 0) return CTD_OK;
   const size_t tsz = fp32 ? 4 : 8;
@@ -836,15 +1008,26 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
   // hot rows (one register block wide only): as many as fit in ~100 KB of
   // shared memory, so two blocks of 16 warps stay resident per SM
   const size_t budget = 100 * 1024;
-  int n_hot = nblk == 1 ? (int)std::min<size_t>(budget / ((size_t)qs * tsz),
-                                                (size_t)std::max(n_hot_req, 0))
+  int n_hot = nblk == 1 ? (int)std::min<int64_t>((int64_t)(budget / ((size_t)qs * tsz)), n_rows)
                         : 0;
   CTD_TRY(scratch.get(&hot, std::max(n_hot, 1)));
-  std::vector<short> slots(n_rows, (short)-1);
-  for (int q = 0; q < n_hot; ++q) slots[hot_rows_host[q]] = (short)q;
-  CTD_CUDA(cudaMemcpyAsync(slot_of, slots.data(), n_rows * sizeof(short), cudaMemcpyHostToDevice, st));
-  if (n_hot)
-    CTD_CUDA(cudaMemcpyAsync(hot, hot_rows_host, n_hot * sizeof(int), cudaMemcpyHostToDevice, st));
+  // the n_hot rows with the most nonzeros (ties by a threshold on the count:
+  // rows at or above the smallest count that keeps the set within n_hot)
+  CTD_CUDA(cudaMemsetAsync(slot_of, 0xff, n_rows * sizeof(short), st));  // -1
+  CTD_CUDA(cudaMemsetAsync(hot, 0, std::max(n_hot, 1) * sizeof(int), st));  // unused slots: row 0
+  if (n_hot > 0) {
+    unsigned* hist;
+    int *thr, *cnt;
+    CTD_TRY(scratch.get(&hist, HOT_BINS));
+    CTD_TRY(scratch.get(&thr, 1));
+    CTD_TRY(scratch.get(&cnt, 1));
+    CTD_CUDA(cudaMemsetAsync(hist, 0, HOT_BINS * sizeof(unsigned), st));
+    CTD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), st));
+    const unsigned g = grid_for(n_rows, 256, (int64_t)num_sms() * 4);
+    CTD_LAUNCH(k_hot_hist, (g), (256), 0, st, rowcnt, n_rows, hist);
+    CTD_LAUNCH(k_hot_threshold, (1), (1024), 0, st, hist, n_hot, thr);
+    CTD_LAUNCH(k_hot_assign, (g), (256), 0, st, rowcnt, n_rows, thr, n_hot, slot_of, hot, cnt);
+  }
   CTD_CUDA(cudaMemsetAsync(work, 0, 8, st));
   const unsigned gq = grid_for(n_rows * qs, 256, (int64_t)num_sms() * 16);
   const unsigned gn = grid_for(n_rows * 32, 256, (int64_t)num_sms() * 8);

@@ -381,10 +381,16 @@ void launch_gather_columns(const uint64_t* colptr, const int32_t* row, const int
 // ---------------------------------------------------------------------------
 // small CSC -> CSR transposition (for the factor R)
 // ---------------------------------------------------------------------------
-__global__ void k_row_counts(const int32_t* __restrict__ row, int64_t nnz, unsigned* rowcnt) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
-       e += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(rowcnt + row[e], 1u);
+// row counts of a CSC layout, walking its columns (a warp per column), so
+// the number of entries need not be known on the host
+__global__ void k_row_counts(const unsigned long long* __restrict__ colptr,
+                             const int32_t* __restrict__ row, int64_t ncols, unsigned* rowcnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = gw; c < ncols; c += nw)
+    for (unsigned long long p = colptr[c] + lane; p < colptr[c + 1]; p += 32)
+      atomicAdd(rowcnt + row[p], 1u);
 }
 
 // one warp per column: scatter its entries into their rows
@@ -421,9 +427,9 @@ ctd_status build_csr_from_csc(const uint64_t* colptr, const int32_t* row, const 
   CTD_TRY(scratch.get(&val_tmp, nnz));
   CTD_CUDA(cudaMemsetAsync(rowcnt, 0, n_rows * sizeof(unsigned), st));
   CTD_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
-  if (nnz > 0)
-    CTD_LAUNCH(k_row_counts, (grid_for(nnz, 256, (int64_t)num_sms() * 8)), (256), 0, st, row, nnz,
-               rowcnt);
+  if (nnz > 0 && ncols > 0)
+    CTD_LAUNCH(k_row_counts, (grid_for(ncols * 32, 256, 4096)), (256), 0, st,
+               reinterpret_cast<const unsigned long long*>(colptr), row, ncols, rowcnt);
   launch_scan_u32(rowcnt, rowptr_out, n_rows, false, tmp, status, st);
   launch_copy_u64(rowptr_out, cur, n_rows, st);
   if (nnz > 0 && ncols > 0) {
