@@ -351,11 +351,10 @@ __device__ __forceinline__ unsigned emit_reg(int* acc, int (&regs)[4 * NQ], unsi
   return pos;
 }
 
-// One persistent kernel, one 32-warp block per SM.  First the columns with
-// at least CF_HEAVY_COL nonzeros (`list`), a whole block each, the largest
-// work items first; then the other multi-nonzero columns (`mlist`), a warp
-// each.  The block accumulator of the first part is warp 0's accumulator of
-// the second; emission leaves both zero.
+// One persistent kernel, one 32-warp block per SM sharing the dense rows; a
+// warp per column, first the columns with at least CF_HEAVY_COL nonzeros
+// (`list`, the longest work items), then the other multi-nonzero columns
+// (`mlist`).  Each warp's accumulator is left zero by its emission.
 template <typename V, int NQ>
 __global__ void __launch_bounds__(CF_THREADS, 1)
     k_cf(CscDev X, CsrDev R, Dense dn, const int64_t* __restrict__ list,
@@ -373,125 +372,71 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
   int regs[4 * NQ];
 #pragma unroll
   for (int k = 0; k < 4 * NQ; ++k) regs[k] = 0;
-  __shared__ unsigned long long fcur;
-  __shared__ unsigned wcount[CF_THREADS / 32];
-  const int width = R.width;
-  {
-    int* acc = accs;
-    const unsigned long long n = *nlist;
-    while (true) {
-      if (threadIdx.x == 0) fcur = atomicAdd(work + 1, 1ull);
-      __syncthreads();
-      const unsigned long long it = fcur;
-      __syncthreads();
-      if (it >= n) break;
-      const int64_t f = list[it];
-      accumulate_reg<NQ>(X, R, dn, dense4, X.colptr[f], X.colptr[f + 1], acc, regs, warp, nw);
-      // fold each warp's registers into the block accumulator
-  #pragma unroll
-      for (int q = 0; q < NQ; ++q)
-  #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if (regs[4 * q + k] != 0) atomicAdd(acc + q * 128 + 4 * lane + k, regs[4 * q + k]);
-          regs[4 * q + k] = 0;
-        }
-      __syncthreads();
-      // emission: warp w sweeps rows [w * span, (w + 1) * span) after counting
-      const int span = (((width + nw - 1) / nw) + 31) & ~31;
-      const int m_lo = min(width, warp * span), m_hi = min(width, m_lo + span);
-      unsigned cnt = 0;
-      for (int m0 = m_lo; m0 < m_hi; m0 += 32) {
-        const int m = m0 + lane;
-        cnt += __popc(__ballot_sync(0xffffffffu, m < m_hi && acc[m] != 0));
-      }
-      if (lane == 0) wcount[warp] = cnt;
-      __syncthreads();
-      unsigned pos = 0, total = 0;
-      for (int w = 0; w < nw; ++w) {
-        if (w < warp) pos += wcount[w];
-        total += wcount[w];
-      }
-      const unsigned long long off = coff[f];
-      for (int m0 = m_lo; m0 < m_hi; m0 += 32) {
-        const int m = m0 + lane;
-        int x = 0;
-        if (m < m_hi) {
-          x = acc[m];
-          acc[m] = 0;
-        }
-        const unsigned ball = __ballot_sync(0xffffffffu, x != 0);
-        if (x != 0) {
-          const unsigned q = pos + __popc(ball & ((1u << lane) - 1));
-          crow[off + q] = (uint16_t)m;
-          cval[off + q] = (V)x;
-        }
-        pos += __popc(ball);
-      }
-      if (threadIdx.x == 0) ccnt[f] = total;
-      __syncthreads();
-    }
-  }
-  __syncthreads();
   int* acc = accs + warp * W;
-  // then the listed columns with 2..CF_HEAVY_COL-1 nonzeros (or one nonzero
-  // with signed values), `grab` list entries per warp at a time
-  const unsigned long long nm = *mcount;
-  const unsigned long long warps_all = (unsigned long long)gridDim.x * nw;
-  const int grab = (int)max(1ull, min(32ull, nm / (warps_all * 4ull)));
-  while (true) {
-    unsigned long long i0 = 0;
-    if (lane == 0) i0 = atomicAdd(work, (unsigned long long)grab);
-    i0 = __shfl_sync(0xffffffffu, i0, 0);
-    if (i0 >= nm) break;
-    // lane l: list entry l's column, output offset and entry range
-    unsigned long long o = 0, xa = 0, xb = 0;
-    int64_t f = -1;
-    if (lane < grab && i0 + lane < nm) {
-      f = mlist[i0 + lane];
-      o = coff[f];
-      xa = X.colptr[f];
-      xb = X.colptr[f + 1];
-    }
-    unsigned todo = __ballot_sync(0xffffffffu, f >= 0);
-    // software pipeline over the grabbed columns: the next column's first
-    // chunk (entries, then their row metadata) is loaded while the current
-    // one accumulates and emits
-    int e = todo ? __ffs(todo) - 1 : 0;
-    unsigned long long ea = __shfl_sync(0xffffffffu, xa, e);
-    unsigned long long eb = __shfl_sync(0xffffffffu, xb, e);
-    int ci = -1, cv = 0;
-    if (todo && ea + lane < eb) {
-      ci = __ldg(X.row + ea + lane);
-      cv = __ldg(X.val + ea + lane);
-    }
-    int csl, crl;
-    unsigned long long crs;
-    entry_meta(R, dn, ci, csl, crs, crl);
-    while (todo) {
-      todo &= todo - 1;
-      const unsigned long long oe = __shfl_sync(0xffffffffu, o, e);
-      const int64_t fe = __shfl_sync(0xffffffffu, f, e);
-      // issue the next column's first-chunk loads
-      const int e2 = todo ? __ffs(todo) - 1 : 0;
-      const unsigned long long na = __shfl_sync(0xffffffffu, xa, e2);
-      const unsigned long long nb = __shfl_sync(0xffffffffu, xb, e2);
-      int ni = -1, nv = 0;
-      if (todo && na + lane < nb) {
-        ni = __ldg(X.row + na + lane);
-        nv = __ldg(X.val + na + lane);
+  // the columns of the heavy list, one per warp grab (the longest work items
+  // first), then those of the multi list, `grab` per warp grab
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int64_t* lst = pass == 0 ? list : mlist;
+    const unsigned long long nm = pass == 0 ? *nlist : *mcount;
+    unsigned long long* counter = pass == 0 ? work + 1 : work;
+    const unsigned long long warps_all = (unsigned long long)gridDim.x * nw;
+    const int grab = pass == 0 ? 1 : (int)max(1ull, min(32ull, nm / (warps_all * 4ull)));
+    while (true) {
+      unsigned long long i0 = 0;
+      if (lane == 0) i0 = atomicAdd(counter, (unsigned long long)grab);
+      i0 = __shfl_sync(0xffffffffu, i0, 0);
+      if (i0 >= nm) break;
+      // lane l: list entry l's column, output offset and entry range
+      unsigned long long o = 0, xa = 0, xb = 0;
+      int64_t f = -1;
+      if (lane < grab && i0 + lane < nm) {
+        f = lst[i0 + lane];
+        o = coff[f];
+        xa = X.colptr[f];
+        xb = X.colptr[f + 1];
       }
-      chunk_reg<NQ>(R, dense4, acc, regs, cv, csl, crs, crl);
-      if (eb - ea > 32) accumulate_reg<NQ>(X, R, dn, dense4, ea + 32, eb, acc, regs, 0, 1);
-      // the next column's row metadata, then this column's emission
-      entry_meta(R, dn, ni, csl, crs, crl);
-      cv = nv;
-      __syncwarp();
-      const unsigned n = emit_reg<V, NQ>(acc, regs, oe, crow, cval);
-      __syncwarp();
-      if (lane == 0) ccnt[fe] = n;
-      e = e2;
-      ea = na;
-      eb = nb;
+      unsigned todo = __ballot_sync(0xffffffffu, f >= 0);
+      // software pipeline over the grabbed columns: the next column's first
+      // chunk (entries, then their row metadata) is loaded while the current
+      // one accumulates and emits
+      int e = todo ? __ffs(todo) - 1 : 0;
+      unsigned long long ea = __shfl_sync(0xffffffffu, xa, e);
+      unsigned long long eb = __shfl_sync(0xffffffffu, xb, e);
+      int ci = -1, cv = 0;
+      if (todo && ea + lane < eb) {
+        ci = __ldg(X.row + ea + lane);
+        cv = __ldg(X.val + ea + lane);
+      }
+      int csl, crl;
+      unsigned long long crs;
+      entry_meta(R, dn, ci, csl, crs, crl);
+      while (todo) {
+        todo &= todo - 1;
+        const unsigned long long oe = __shfl_sync(0xffffffffu, o, e);
+        const int64_t fe = __shfl_sync(0xffffffffu, f, e);
+        // issue the next column's first-chunk loads
+        const int e2 = todo ? __ffs(todo) - 1 : 0;
+        const unsigned long long na = __shfl_sync(0xffffffffu, xa, e2);
+        const unsigned long long nb = __shfl_sync(0xffffffffu, xb, e2);
+        int ni = -1, nv = 0;
+        if (todo && na + lane < nb) {
+          ni = __ldg(X.row + na + lane);
+          nv = __ldg(X.val + na + lane);
+        }
+        chunk_reg<NQ>(R, dense4, acc, regs, cv, csl, crs, crl);
+        if (eb - ea > 32) accumulate_reg<NQ>(X, R, dn, dense4, ea + 32, eb, acc, regs, 0, 1);
+        // the next column's row metadata, then this column's emission
+        entry_meta(R, dn, ni, csl, crs, crl);
+        cv = nv;
+        __syncwarp();
+        const unsigned n = emit_reg<V, NQ>(acc, regs, oe, crow, cval);
+        __syncwarp();
+        if (lane == 0) ccnt[fe] = n;
+        e = e2;
+        ea = na;
+        eb = nb;
+      }
     }
   }
 }

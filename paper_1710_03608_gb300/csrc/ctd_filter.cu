@@ -12,10 +12,11 @@
 // 1e-2; independent fibers mostly sit far above) is re-tested the way the
 // loop states it: its coefficients gamma are solved through the factor, the
 // residual vector x_k - [R^(t), kept candidates before k] gamma is formed
-// explicitly, and one step of iterative refinement (the normal equations
-// solved again for that residual) removes most of the error the factor's
-// conditioning left in gamma.  The ratio ||res|| / ||x_k|| then has an error
-// far below eps even for kappa(R^T R) ~ 1e11.  If that test disagrees with
+// explicitly; when some ratio is within a factor 4 of eps (or disagrees
+// with the factorization), one step of iterative refinement (the normal
+// equations solved again for that residual) removes most of the error the
+// factor's conditioning left in gamma.  The ratio ||res|| / ||x_k|| then has
+// an error far below eps even for kappa(R^T R) ~ 1e11.  If that test disagrees with
 // the pivot, the first disagreeing candidate's decision is fixed and the
 // factorization is redone.
 #include <algorithm>
@@ -282,8 +283,21 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
                in.dt, gammaR, kpos, kept, eta, d_sus, 1, rbuf);
     CTD_LAUNCH(k_resid_norm, (ns), (256), 0, st, in.n_rows, d_sus, xn2, rbuf, ratio);
     // one step of iterative refinement: solve the normal equations again for
-    // the residual's remaining component in range([R^(t), kept before k])
-    {
+    // the residual's remaining component in range([R^(t), kept before k]).
+    // Its correction to a ratio is of order u * kappa(R); it is taken only
+    // when some ratio lies within a factor 4 of eps or disagrees with the
+    // factorization's decision (otherwise no decision can change).
+    std::vector<double> h_ratio(ns);
+    CTD_TRY(d2h(h_ratio.data(), ratio, ns, st));
+    CTD_CUDA(cudaGetLastError());
+    CTD_TRY(sync(st));
+    bool refine = false;
+    for (int c = 0; c < ns && !refine; ++c) {
+      const double r = h_ratio[c];
+      const int explicit_keep = r > in.eps ? 1 : 0;
+      refine = (r >= 0.25 * in.eps && r <= 4.0 * in.eps) || explicit_keep != h_keep[sus[c]];
+    }
+    if (refine) {
       double *hR = nullptr, *hK, *zK, *etad;
       CTD_TRY(scratch.get(&hK, (size_t)kk * ns));
       CTD_TRY(scratch.get(&zK, (size_t)kk * ns));
@@ -321,11 +335,10 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
                  reinterpret_cast<const unsigned long long*>(in.r_rowptr), in.r_col, in.r_val,
                  in.dt, hR, kpos, kept, etad, d_sus, 0, rbuf);
       CTD_LAUNCH(k_resid_norm, (ns), (256), 0, st, in.n_rows, d_sus, xn2, rbuf, ratio);
+      CTD_TRY(d2h(h_ratio.data(), ratio, ns, st));
+      CTD_CUDA(cudaGetLastError());
+      CTD_TRY(sync(st));
     }
-    std::vector<double> h_ratio(ns);
-    CTD_TRY(d2h(h_ratio.data(), ratio, ns, st));
-    CTD_CUDA(cudaGetLastError());
-    CTD_TRY(sync(st));
     bool changed = false;
     for (int c = 0; c < ns && !changed; ++c) {
       const int k = sus[c];
