@@ -291,14 +291,12 @@ __device__ void chol_diag_block(double* __restrict__ A, int64_t n, int64_t lda, 
 #pragma unroll
     for (int c = 0; c < NB; ++c)
       row[c] = (lane < nb && c <= lane) ? A[(k0 + lane) + (k0 + c) * lda] : 0.0;
+    // right-looking: once column c is decided and scaled, every later
+    // column j is updated (independent multiply-adds, no dependent chain)
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
       if (c < nb) {
-        double sred = row[c];
-#pragma unroll
-        for (int q = 0; q < c; ++q)
-          sred = fma(-row[q], __shfl_sync(0xffffffffu, row[q], c), sred);
-        double d = __shfl_sync(0xffffffffu, sred, c);
+        double d = __shfl_sync(0xffffffffu, row[c], c);
         int k = (d > thr_s[c] && d > 0.0) ? 1 : 0;
         if (force_s[c] >= 0) k = force_s[c];
         // a keep forced by the explicit residual takes that residual's
@@ -313,10 +311,17 @@ __device__ void chol_diag_block(double* __restrict__ A, int64_t n, int64_t lda, 
         if (lane == c)
           row[c] = l;
         else if (lane > c)
-          row[c] = sred * inv;
+          row[c] = row[c] * inv;
         if (lane == 0) {
           kp[c] = k;
           piv_s[c] = d;
+        }
+        if (k) {
+#pragma unroll
+          for (int j = c + 1; j < NB; ++j) {
+            const double ljc = __shfl_sync(0xffffffffu, row[c], j);
+            if (lane >= j) row[j] = fma(-row[c], ljc, row[j]);
+          }
         }
       }
     }
@@ -369,13 +374,15 @@ __global__ void __launch_bounds__(256, 1)
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = k1 + gw; i < n; i += nwarps) {
-      const double a = lane < nb ? A[i + (k0 + lane) * lda] : 0.0;
-      double x = 0.0;
+      // x L11^T = a, right-looking: x_c = a_c / L(c, c) is broadcast and
+      // the lanes after c subtract their share at once
+      double x = lane < nb ? A[i + (k0 + lane) * lda] : 0.0;
       for (int c = 0; c < nb; ++c) {
-        double part = (lane < c) ? x * D[c][lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == c) x = kp[c] ? (a - part) * invd[c] : 0.0;
+        const double xc = __shfl_sync(0xffffffffu, x * invd[c], c);
+        if (lane == c)
+          x = kp[c] ? xc : 0.0;
+        else if (lane > c && kp[c])
+          x = fma(-xc, D[lane][c], x);
       }
       if (lane < nb) A[i + (k0 + lane) * lda] = x;
     }

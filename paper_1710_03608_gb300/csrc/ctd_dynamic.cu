@@ -229,6 +229,9 @@ static ctd_status grow_U(ctd_factors* F, int64_t d, int64_t n, cudaStream_t st) 
   auto& D = *F->dyn;
   if (n <= D.cap_d) return CTD_OK;
   int64_t cap = std::max<int64_t>(std::max<int64_t>(2 * D.cap_d, n), 512);
+  // d~ never exceeds I_alpha: up to 8192 rows, take that size at once (no
+  // regrowth copies; at most 0.5 GB each for L and Q^T)
+  if (F->n_rows <= 8192) cap = std::max<int64_t>(cap, F->n_rows);
   cap = (cap + 511) / 512 * 512;
   const int64_t rows = F->n_rows;
   double *L2, *Q2;
