@@ -621,6 +621,135 @@ struct Vec16<double> {
 
 constexpr int QF_THREADS = 512;
 
+// acc += sum over the chunks c = first, first + step, ... of the column
+// entries [a, b) (32 per chunk) of v * Q(i, coff : coff + NK*32*VEC); lane l
+// holds the VEC consecutive values at (l + 32 k) * VEC.  Rows with a slot
+// (slot_of) are read from the staged copy Qs.
+template <typename T, int NK>
+__device__ __forceinline__ void qrows_accumulate(const CscDev& X, const T* __restrict__ Q, int qs,
+                                                 int64_t coff, const T* __restrict__ Qs,
+                                                 const short* __restrict__ slot_of,
+                                                 unsigned long long a, unsigned long long b,
+                                                 int first, int step,
+                                                 T (&acc)[NK * Vec16<T>::n]) {
+  using VT = typename Vec16<T>::type;
+  constexpr int VEC = Vec16<T>::n;
+  const int lane = threadIdx.x & 31;
+  for (unsigned long long base = a + (unsigned long long)first * 32; base < b;
+       base += (unsigned long long)step * 32) {
+    const int cnt = (int)min((unsigned long long)32, b - base);
+    const T* myrow = nullptr;
+    int myv = 0;
+    if (lane < cnt) {
+      const int i = __ldg(X.row + base + lane);
+      myv = __ldg(X.val + base + lane);
+      const int sl = slot_of ? (int)__ldg(slot_of + i) : -1;
+      myrow = (sl >= 0 ? Qs + (int64_t)sl * qs : Q + (int64_t)i * qs) + coff;
+    }
+    int q = 0;
+    for (; q + 1 < cnt; q += 2) {
+      const VT* r0 = (const VT*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, q);
+      const VT* r1 = (const VT*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, q + 1);
+      const T v0 = (T)__shfl_sync(0xffffffffu, myv, q);
+      const T v1 = (T)__shfl_sync(0xffffffffu, myv, q + 1);
+      VT a0[NK], a1[NK];
+#pragma unroll
+      for (int k = 0; k < NK; ++k) {
+        a0[k] = r0[lane + 32 * k];
+        a1[k] = r1[lane + 32 * k];
+      }
+#pragma unroll
+      for (int k = 0; k < NK; ++k) {
+        const T* x0 = reinterpret_cast<const T*>(&a0[k]);
+        const T* x1 = reinterpret_cast<const T*>(&a1[k]);
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+          acc[k * VEC + u] = fma(v0, x0[u], acc[k * VEC + u]);
+          acc[k * VEC + u] = fma(v1, x1[u], acc[k * VEC + u]);
+        }
+      }
+    }
+    if (q < cnt) {
+      const VT* r0 = (const VT*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, q);
+      const T v0 = (T)__shfl_sync(0xffffffffu, myv, q);
+#pragma unroll
+      for (int k = 0; k < NK; ++k) {
+        const VT a0 = r0[lane + 32 * k];
+        const T* x0 = reinterpret_cast<const T*>(&a0);
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) acc[k * VEC + u] = fma(v0, x0[u], acc[k * VEC + u]);
+      }
+    }
+  }
+}
+
+// Columns with more than heavy_min nonzeros, a whole block each (16 warps
+// split the entries, chunk w, w + 16, ...): each warp's partial y goes to
+// shared memory, the block adds the 16 partials in order and squares;
+// group g (columns 32g .. 32g+31) writes its sum to hpart[g].  Deterministic.
+template <typename T, int NK>
+__global__ void __launch_bounds__(QF_THREADS, 1)
+    k_qform_heavy(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs, int nblk,
+                  const short* __restrict__ slot_of, const int* __restrict__ hot_rows, int n_hot,
+                  unsigned long long heavy_min, double* __restrict__ hpart) {
+  constexpr int VEC = Vec16<T>::n;
+  constexpr int WB = NK * 32 * VEC;  // columns of Q per register block
+  constexpr int NW = QF_THREADS / 32;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* Qs = reinterpret_cast<T*>(smraw);                 // [n_hot][qs]
+  T* ypart = Qs + (size_t)n_hot * qs;                  // [NW][WB]
+  __shared__ T red[NW];
+  for (int64_t e = threadIdx.x; e < (int64_t)n_hot * qs; e += blockDim.x)
+    Qs[e] = Q[(int64_t)hot_rows[e / qs] * qs + (e % qs)];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(X.colptr);
+  const int64_t ngroups = (n_cols + 31) / 32;
+  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const int64_t fl = g * 32 + lane;
+    unsigned long long la = 0, lb = 0;
+    if (fl < n_cols) {
+      la = xp[fl];
+      lb = xp[fl + 1];
+    }
+    unsigned hv = __ballot_sync(0xffffffffu, lb - la > heavy_min);
+    T gsum = (T)0;
+    while (hv) {
+      const int e = __ffs(hv) - 1;
+      hv &= hv - 1;
+      const unsigned long long a = __shfl_sync(0xffffffffu, la, e);
+      const unsigned long long b = __shfl_sync(0xffffffffu, lb, e);
+      for (int cb = 0; cb < nblk; ++cb) {
+        const int64_t coff = (int64_t)cb * WB;
+        T acc[NK * VEC];
+#pragma unroll
+        for (int k = 0; k < NK * VEC; ++k) acc[k] = (T)0;
+        qrows_accumulate<T, NK>(X, Q, qs, coff, Qs, slot_of, a, b, warp, NW, acc);
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) ypart[warp * WB + (lane + 32 * k) * VEC + u] = acc[k * VEC + u];
+        __syncthreads();
+        T ss = (T)0;
+        for (int pcol = threadIdx.x; pcol < WB; pcol += blockDim.x) {
+          T y = (T)0;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) y += ypart[w * WB + pcol];
+          ss = fma(y, y, ss);
+        }
+        for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) red[warp] = ss;
+        __syncthreads();
+        if (threadIdx.x == 0)
+          for (int w = 0; w < NW; ++w) gsum += red[w];
+        __syncthreads();
+      }
+    }
+    if (threadIdx.x == 0) hpart[g] = (double)gsum;
+  }
+}
+
+
 template <typename T, int NK>
 __global__ void __launch_bounds__(QF_THREADS, (NK >= 8 ? 1 : 2))
     k_qform(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs, int nblk,
@@ -670,51 +799,7 @@ __global__ void __launch_bounds__(QF_THREADS, (NK >= 8 ? 1 : 2))
       T acc[NK * VEC];
 #pragma unroll
       for (int k = 0; k < NK * VEC; ++k) acc[k] = (T)0;
-      for (unsigned long long base = a; base < b; base += 32) {
-        const int cnt = (int)min((unsigned long long)32, b - base);
-        const T* myrow = nullptr;
-        int myv = 0;
-        if (lane < cnt) {
-          const int i = __ldg(X.row + base + lane);
-          myv = __ldg(X.val + base + lane);
-          const int sl = slot_of ? (int)__ldg(slot_of + i) : -1;
-          myrow = (sl >= 0 ? Qs + (int64_t)sl * qs : Q + (int64_t)i * qs) + coff;
-        }
-        int q = 0;
-        for (; q + 1 < cnt; q += 2) {
-          const VT* r0 = (const VT*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, q);
-          const VT* r1 = (const VT*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, q + 1);
-          const T v0 = (T)__shfl_sync(0xffffffffu, myv, q);
-          const T v1 = (T)__shfl_sync(0xffffffffu, myv, q + 1);
-          VT a0[NK], a1[NK];
-#pragma unroll
-          for (int k = 0; k < NK; ++k) {
-            a0[k] = r0[lane + 32 * k];
-            a1[k] = r1[lane + 32 * k];
-          }
-#pragma unroll
-          for (int k = 0; k < NK; ++k) {
-            const T* x0 = reinterpret_cast<const T*>(&a0[k]);
-            const T* x1 = reinterpret_cast<const T*>(&a1[k]);
-#pragma unroll
-            for (int u = 0; u < VEC; ++u) {
-              acc[k * VEC + u] = fma(v0, x0[u], acc[k * VEC + u]);
-              acc[k * VEC + u] = fma(v1, x1[u], acc[k * VEC + u]);
-            }
-          }
-        }
-        if (q < cnt) {
-          const VT* r0 = (const VT*)__shfl_sync(0xffffffffu, (unsigned long long)myrow, q);
-          const T v0 = (T)__shfl_sync(0xffffffffu, myv, q);
-#pragma unroll
-          for (int k = 0; k < NK; ++k) {
-            const VT a0 = r0[lane + 32 * k];
-            const T* x0 = reinterpret_cast<const T*>(&a0);
-#pragma unroll
-            for (int u = 0; u < VEC; ++u) acc[k * VEC + u] = fma(v0, x0[u], acc[k * VEC + u]);
-          }
-        }
-      }
+      qrows_accumulate<T, NK>(X, Q, qs, coff, Qs, slot_of, a, b, 0, 1, acc);
 #pragma unroll
       for (int k = 0; k < NK * VEC; ++k) ss = fma(acc[k], acc[k], ss);
       }
@@ -802,6 +887,27 @@ static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int 
   CTD_LAUNCH((k_qform<T, NK>), (blocks), (QF_THREADS), smem, st, X, n_cols, Q, qs, nblk,
              qn, slot_of, hot, n_hot, n_rows, grab, skip_above, work, *partial);
   return CTD_OK;
+}
+
+template <typename T, int NK>
+static ctd_status qform_heavy_launch(const CscDev& X, int64_t n_cols, const T* Q, int qs,
+                                     int nblk, const short* slot_of, const int* hot, int n_hot,
+                                     unsigned long long heavy_min, double* hpart,
+                                     cudaStream_t st) {
+  constexpr int WB = NK * 32 * Vec16<T>::n;
+  const size_t smem = ((size_t)n_hot * qs + (size_t)(QF_THREADS / 32) * WB) * sizeof(T);
+  CTD_TRY(allow_max_smem((const void*)k_qform_heavy<T, NK>));
+  int per_sm = 0;
+  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qform_heavy<T, NK>,
+                                                         QF_THREADS, smem));
+  if (per_sm < 1) return fail(CTD_ECUDA, "error kernel does not fit on an SM");
+  CTD_LAUNCH((k_qform_heavy<T, NK>), (num_sms() * per_sm), (QF_THREADS), smem, st, X, n_cols, Q,
+             qs, nblk, slot_of, hot, n_hot, heavy_min, hpart);
+  return CTD_OK;
+}
+
+__global__ void k_add2(const double* __restrict__ a, const double* __restrict__ b, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = *a + *b;
 }
 
 // Columns with many nonzeros, split over blocks.  y_f = sum_p v_p Q(i_p, :)
@@ -1042,14 +1148,25 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
     CTD_LAUNCH(k_q_rownorms<double>, (gn), (256), 0, st, static_cast<const double*>(Q), n_rows,
                qs, static_cast<double*>(qn));
   }
+  // columns with more than QF_HEAVY nonzeros: a block each (k_qform_heavy)
+  constexpr unsigned long long QF_HEAVY = 256;
+  const int64_t ngroups = (n_cols + 31) / 32;
+  double* hpart;
+  CTD_TRY(scratch.get(&hpart, ngroups));
   ctd_status rc;
 #define QF(NKV)                                                                                 \
   rc = fp32 ? qform_launch<float, NKV>(X, n_cols, static_cast<const float*>(Q), qs, nblk,     \
                                        static_cast<const float*>(qn), slot_of, hot, n_hot,     \
-                                       n_rows, work, &partial, &nchunks, scratch, st)          \
+                                       n_rows, work, &partial, &nchunks, scratch, st, QF_HEAVY) \
             : qform_launch<double, NKV>(X, n_cols, static_cast<const double*>(Q), qs, nblk,    \
                                         static_cast<const double*>(qn), slot_of, hot, n_hot,   \
-                                        n_rows, work, &partial, &nchunks, scratch, st)
+                                        n_rows, work, &partial, &nchunks, scratch, st,         \
+                                        QF_HEAVY);                                             \
+  if (rc == CTD_OK)                                                                             \
+    rc = fp32 ? qform_heavy_launch<float, NKV>(X, n_cols, static_cast<const float*>(Q), qs,    \
+                                               nblk, slot_of, hot, n_hot, QF_HEAVY, hpart, st) \
+              : qform_heavy_launch<double, NKV>(X, n_cols, static_cast<const double*>(Q), qs,  \
+                                                nblk, slot_of, hot, n_hot, QF_HEAVY, hpart, st)
   if (NK <= 1) {
     QF(1);
   } else if (NK <= 2) {
@@ -1061,7 +1178,11 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
   }
 #undef QF
   CTD_TRY(rc);
-  CTD_TRY(sum_f64(partial, nchunks, out, scratch, st));
+  double* two;
+  CTD_TRY(scratch.get(&two, 2));
+  CTD_TRY(sum_f64(partial, nchunks, two, scratch, st));
+  CTD_TRY(sum_f64(hpart, ngroups, two + 1, scratch, st));
+  CTD_LAUNCH(k_add2, (1), (32), 0, st, two, two + 1, out);
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
