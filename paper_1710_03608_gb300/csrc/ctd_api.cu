@@ -404,7 +404,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   if (!(flags & CTD_SKIP_ERROR) && kept > 0) {
     STEP(scratch.get(&d_pu, 1));
     PhaseScope ph("error_qform", st);
-    STEP(launch_error_qform(M.csc(), M.n_cols, M.n_rows, R, Z, kept, M.rowcnt,
+    STEP(launch_error_qform(M.csc(), M.n_cols, M.n_rows, M.nnz, R, Z, kept, M.rowcnt,
                             precision == CTD_FP32_BULK, d_pu, scratch, st));
   }
   uint64_t* d_nnzc;

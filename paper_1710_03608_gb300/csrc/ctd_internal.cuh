@@ -245,9 +245,10 @@ struct CsrX {          // X_(alpha) by row: row i holds (col, val)
   const int32_t* col;
   const int32_t* val;
 };
-ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
-                              const double* Z, int64_t ldz, const uint32_t* rowcnt, int fp32,
-                              double* out, Arena& scratch, cudaStream_t st);
+ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t X_nnz,
+                              const CsrDev& R, const double* Z, int64_t ldz,
+                              const uint32_t* rowcnt, int fp32, double* out, Arena& scratch,
+                              cudaStream_t st);
 
 // ||Q^T X_(alpha)||_F^2 for FP64 Q by rows (row i at Q + i * ld, ld a
 // multiple of 512, zero past `width`), with row norms qn.

@@ -683,71 +683,6 @@ __device__ __forceinline__ void qrows_accumulate(const CscDev& X, const T* __res
   }
 }
 
-// Columns with more than heavy_min nonzeros, a whole block each (16 warps
-// split the entries, chunk w, w + 16, ...): each warp's partial y goes to
-// shared memory, the block adds the 16 partials in order and squares;
-// group g (columns 32g .. 32g+31) writes its sum to hpart[g].  Deterministic.
-template <typename T, int NK>
-__global__ void __launch_bounds__(QF_THREADS, 1)
-    k_qform_heavy(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs, int nblk,
-                  const short* __restrict__ slot_of, const int* __restrict__ hot_rows, int n_hot,
-                  unsigned long long heavy_min, double* __restrict__ hpart) {
-  constexpr int VEC = Vec16<T>::n;
-  constexpr int WB = NK * 32 * VEC;  // columns of Q per register block
-  constexpr int NW = QF_THREADS / 32;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* Qs = reinterpret_cast<T*>(smraw);                 // [n_hot][qs]
-  T* ypart = Qs + (size_t)n_hot * qs;                  // [NW][WB]
-  __shared__ T red[NW];
-  for (int64_t e = threadIdx.x; e < (int64_t)n_hot * qs; e += blockDim.x)
-    Qs[e] = Q[(int64_t)hot_rows[e / qs] * qs + (e % qs)];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(X.colptr);
-  const int64_t ngroups = (n_cols + 31) / 32;
-  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-    const int64_t fl = g * 32 + lane;
-    unsigned long long la = 0, lb = 0;
-    if (fl < n_cols) {
-      la = xp[fl];
-      lb = xp[fl + 1];
-    }
-    unsigned hv = __ballot_sync(0xffffffffu, lb - la > heavy_min);
-    T gsum = (T)0;
-    while (hv) {
-      const int e = __ffs(hv) - 1;
-      hv &= hv - 1;
-      const unsigned long long a = __shfl_sync(0xffffffffu, la, e);
-      const unsigned long long b = __shfl_sync(0xffffffffu, lb, e);
-      for (int cb = 0; cb < nblk; ++cb) {
-        const int64_t coff = (int64_t)cb * WB;
-        T acc[NK * VEC];
-#pragma unroll
-        for (int k = 0; k < NK * VEC; ++k) acc[k] = (T)0;
-        qrows_accumulate<T, NK>(X, Q, qs, coff, Qs, slot_of, a, b, warp, NW, acc);
-#pragma unroll
-        for (int k = 0; k < NK; ++k)
-#pragma unroll
-          for (int u = 0; u < VEC; ++u) ypart[warp * WB + (lane + 32 * k) * VEC + u] = acc[k * VEC + u];
-        __syncthreads();
-        T ss = (T)0;
-        for (int pcol = threadIdx.x; pcol < WB; pcol += blockDim.x) {
-          T y = (T)0;
-#pragma unroll
-          for (int w = 0; w < NW; ++w) y += ypart[w * WB + pcol];
-          ss = fma(y, y, ss);
-        }
-        for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        if (lane == 0) red[warp] = ss;
-        __syncthreads();
-        if (threadIdx.x == 0)
-          for (int w = 0; w < NW; ++w) gsum += red[w];
-        __syncthreads();
-      }
-    }
-    if (threadIdx.x == 0) hpart[g] = (double)gsum;
-  }
-}
 
 
 template <typename T, int NK>
@@ -755,8 +690,9 @@ __global__ void __launch_bounds__(QF_THREADS, (NK >= 8 ? 1 : 2))
     k_qform(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs, int nblk,
             const T* __restrict__ qn, const short* __restrict__ slot_of,
             const int* __restrict__ hot_rows, int n_hot, int64_t n_rows, int grab,
-            unsigned long long skip_above, unsigned long long* work,
-            double* __restrict__ partial) {
+            unsigned long long skip_above, const int64_t* __restrict__ hlist,
+            const unsigned* __restrict__ nh, double* __restrict__ hval,
+            unsigned long long* work, double* __restrict__ partial) {
   using VT = typename Vec16<T>::type;
   constexpr int VEC = Vec16<T>::n;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -766,6 +702,31 @@ __global__ void __launch_bounds__(QF_THREADS, (NK >= 8 ? 1 : 2))
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(X.colptr);
+  // first the heavy columns (more than skip_above nonzeros; `hlist`, in
+  // column order), one per warp grab, so no long column is left for the end
+  if (hlist) {
+    const unsigned nhv = *nh;
+    while (true) {
+      unsigned h = 0;
+      if (lane == 0) h = (unsigned)atomicAdd(work + 1, 1ull);
+      h = __shfl_sync(0xffffffffu, h, 0);
+      if (h >= nhv) break;
+      const int64_t f = hlist[h];
+      const unsigned long long a = xp[f], b = xp[f + 1];
+      T ss = (T)0;
+      for (int cb = 0; cb < nblk; ++cb) {
+        T acc[NK * VEC];
+#pragma unroll
+        for (int k = 0; k < NK * VEC; ++k) acc[k] = (T)0;
+        qrows_accumulate<T, NK>(X, Q, qs, (int64_t)cb * NK * 32 * VEC, Qs, slot_of, a, b, 0, 1,
+                                acc);
+#pragma unroll
+        for (int k = 0; k < NK * VEC; ++k) ss = fma(acc[k], acc[k], ss);
+      }
+      for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      if (lane == 0) hval[h] = (double)ss;
+    }
+  }
   while (true) {
     unsigned long long f0 = 0;
     if (lane == 0) f0 = atomicAdd(work, (unsigned long long)grab);
@@ -783,7 +744,7 @@ __global__ void __launch_bounds__(QF_THREADS, (NK >= 8 ? 1 : 2))
         total = v * v * qn[X.row[la]];
         lb = la;  // done
       } else if (lb - la > skip_above) {
-        lb = la;  // a heavy column: handled by the split kernels
+        lb = la;  // a heavy column: done first, or by the split kernels
       }
     }
     // columns with two or more nonzeros, one at a time
@@ -844,6 +805,10 @@ __global__ void k_sum_f64_fixed(const double* __restrict__ in, int64_t n, double
   }
 }
 
+__global__ void k_add2(const double* __restrict__ a, const double* __restrict__ b, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = *a + *b;
+}
+
 // *out = sum of n doubles, in an order fixed by n alone
 static ctd_status sum_f64(const double* in, int64_t n, double* out, Arena& scratch,
                           cudaStream_t st) {
@@ -871,7 +836,9 @@ static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int 
                                const T* qn, const short* slot_of, const int* hot, int n_hot,
                                int64_t n_rows, unsigned long long* work, double** partial,
                                int64_t* nparts, Arena& scratch, cudaStream_t st,
-                               unsigned long long skip_above = ~0ull) {
+                               unsigned long long skip_above = ~0ull,
+                               const int64_t* hlist = nullptr, const unsigned* nh = nullptr,
+                               double* hval = nullptr) {
   const size_t smem = (size_t)n_hot * qs * sizeof(T);
   if (smem > 48 * 1024)
     CTD_TRY(allow_max_smem((const void*)k_qform<T, NK>));
@@ -885,29 +852,8 @@ static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int 
   CTD_TRY(scratch.get(partial, *nparts));
   CTD_CUDA(cudaMemsetAsync(*partial, 0, *nparts * sizeof(double), st));
   CTD_LAUNCH((k_qform<T, NK>), (blocks), (QF_THREADS), smem, st, X, n_cols, Q, qs, nblk,
-             qn, slot_of, hot, n_hot, n_rows, grab, skip_above, work, *partial);
+             qn, slot_of, hot, n_hot, n_rows, grab, skip_above, hlist, nh, hval, work, *partial);
   return CTD_OK;
-}
-
-template <typename T, int NK>
-static ctd_status qform_heavy_launch(const CscDev& X, int64_t n_cols, const T* Q, int qs,
-                                     int nblk, const short* slot_of, const int* hot, int n_hot,
-                                     unsigned long long heavy_min, double* hpart,
-                                     cudaStream_t st) {
-  constexpr int WB = NK * 32 * Vec16<T>::n;
-  const size_t smem = ((size_t)n_hot * qs + (size_t)(QF_THREADS / 32) * WB) * sizeof(T);
-  CTD_TRY(allow_max_smem((const void*)k_qform_heavy<T, NK>));
-  int per_sm = 0;
-  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qform_heavy<T, NK>,
-                                                         QF_THREADS, smem));
-  if (per_sm < 1) return fail(CTD_ECUDA, "error kernel does not fit on an SM");
-  CTD_LAUNCH((k_qform_heavy<T, NK>), (num_sms() * per_sm), (QF_THREADS), smem, st, X, n_cols, Q,
-             qs, nblk, slot_of, hot, n_hot, heavy_min, hpart);
-  return CTD_OK;
-}
-
-__global__ void k_add2(const double* __restrict__ a, const double* __restrict__ b, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *out = *a + *b;
 }
 
 // Columns with many nonzeros, split over blocks.  y_f = sum_p v_p Q(i_p, :)
@@ -1032,6 +978,71 @@ ctd_status launch_qform_rows(const CscDev& X, int64_t n_cols, int64_t nnz, const
   return CTD_OK;
 }
 
+// The columns with more than `minc` - 1 nonzeros, in ascending order: a
+// count per 4096-column tile, an exclusive scan of the counts, then each
+// tile writes its columns in order (deterministic, unlike atomic appends).
+constexpr int HL_TILE = 4096;
+
+__global__ void k_tile_counts(const unsigned long long* __restrict__ colptr, int64_t n_cols,
+                              unsigned long long minc, unsigned* __restrict__ tcount) {
+  __shared__ unsigned c;
+  const int64_t t = blockIdx.x;
+  if (threadIdx.x == 0) c = 0;
+  __syncthreads();
+  unsigned mine = 0;
+  for (int64_t f = t * HL_TILE + threadIdx.x; f < min(n_cols, (t + 1) * HL_TILE); f += blockDim.x)
+    mine += (colptr[f + 1] - colptr[f] >= minc);
+  atomicAdd(&c, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) tcount[t] = c;
+}
+
+__global__ void k_tile_write(const unsigned long long* __restrict__ colptr, int64_t n_cols,
+                             unsigned long long minc, const unsigned long long* __restrict__ toff,
+                             int64_t* __restrict__ list) {
+  // one warp walks the tile in order; ballots keep the order inside it
+  const int lane = threadIdx.x & 31;
+  const int64_t t = blockIdx.x;
+  unsigned long long pos = toff[t];
+  for (int64_t f0 = t * HL_TILE; f0 < min(n_cols, (t + 1) * HL_TILE); f0 += 32) {
+    const int64_t f = f0 + lane;
+    const bool h = f < n_cols && colptr[f + 1] - colptr[f] >= minc;
+    const unsigned m = __ballot_sync(0xffffffffu, h);
+    if (h) list[pos + __popc(m & ((1u << lane) - 1))] = f;
+    pos += __popc(m);
+  }
+}
+
+__global__ void k_u64_to_u32(const unsigned long long* __restrict__ in, unsigned* out);
+
+static ctd_status ordered_heavy_list(const uint64_t* colptr, int64_t n_cols, uint64_t minc,
+                                     int64_t* list, unsigned* count, Arena& scratch,
+                                     cudaStream_t st) {
+  const int64_t tiles = (n_cols + HL_TILE - 1) / HL_TILE;
+  unsigned* tc;
+  uint64_t* toff;
+  uint64_t* tmp;
+  unsigned* status;
+  CTD_TRY(scratch.get(&tc, tiles));
+  CTD_TRY(scratch.get(&toff, tiles + 1));
+  CTD_TRY(scratch.get(&tmp, scan_tmp_elems(tiles)));
+  CTD_TRY(scratch.get(&status, 1));
+  CTD_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
+  CTD_LAUNCH(k_tile_counts, ((unsigned)tiles), (256), 0, st,
+             reinterpret_cast<const unsigned long long*>(colptr), n_cols,
+             (unsigned long long)minc, tc);
+  launch_scan_u32(tc, toff, tiles, false, tmp, status, st);
+  CTD_LAUNCH(k_tile_write, ((unsigned)tiles), (32), 0, st,
+             reinterpret_cast<const unsigned long long*>(colptr), n_cols,
+             (unsigned long long)minc, reinterpret_cast<const unsigned long long*>(toff), list);
+  CTD_LAUNCH(k_u64_to_u32, (1), (32), 0, st, reinterpret_cast<const unsigned long long*>(toff) + tiles, count);
+  return CTD_OK;
+}
+
+__global__ void k_u64_to_u32(const unsigned long long* __restrict__ in, unsigned* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = (unsigned)*in;
+}
+
 // Rows of X with the most nonzeros, chosen on the device: a histogram of
 // min(count, HOT_BINS - 1), the smallest count L >= 1 with at most n_hot
 // rows at or above it, and slots for those rows.
@@ -1086,9 +1097,10 @@ __global__ void k_hot_assign(const uint32_t* __restrict__ cnt, int64_t n, const 
     }
 }
 
-ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
-                              const double* Z, int64_t ldz, const uint32_t* rowcnt, int fp32,
-                              double* out, Arena& scratch, cudaStream_t st) {
+ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t X_nnz,
+                              const CsrDev& R, const double* Z, int64_t ldz,
+                              const uint32_t* rowcnt, int fp32, double* out, Arena& scratch,
+                              cudaStream_t st) {
   CTD_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
   if (R.width <= 0 || n_cols <= 0) return CTD_OK;
   const size_t tsz = fp32 ? 4 : 8;
@@ -1110,7 +1122,7 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
   CTD_TRY(scratch.get(reinterpret_cast<unsigned char**>(&Q), (size_t)n_rows * qs * tsz));
   CTD_TRY(scratch.get(reinterpret_cast<unsigned char**>(&qn), (size_t)n_rows * tsz));
   CTD_TRY(scratch.get(&slot_of, n_rows));
-  CTD_TRY(scratch.get(&work, 1));
+  CTD_TRY(scratch.get(&work, 2));
   // hot rows (one register block wide only): as many as fit in ~100 KB of
   // shared memory, so two blocks of 16 warps stay resident per SM
   const size_t budget = 100 * 1024;
@@ -1134,7 +1146,7 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
     CTD_LAUNCH(k_hot_threshold, (1), (1024), 0, st, hist, n_hot, thr);
     CTD_LAUNCH(k_hot_assign, (g), (256), 0, st, rowcnt, n_rows, thr, n_hot, slot_of, hot, cnt);
   }
-  CTD_CUDA(cudaMemsetAsync(work, 0, 8, st));
+  CTD_CUDA(cudaMemsetAsync(work, 0, 16, st));
   const unsigned gq = grid_for(n_rows * qs, 256, (int64_t)num_sms() * 16);
   const unsigned gn = grid_for(n_rows * 32, 256, (int64_t)num_sms() * 8);
   if (fp32) {
@@ -1148,25 +1160,28 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
     CTD_LAUNCH(k_q_rownorms<double>, (gn), (256), 0, st, static_cast<const double*>(Q), n_rows,
                qs, static_cast<double*>(qn));
   }
-  // columns with more than QF_HEAVY nonzeros: a block each (k_qform_heavy)
+  // columns with more than QF_HEAVY nonzeros go first (a list in column
+  // order, one value each), then the rest; both sums in a fixed order
   constexpr unsigned long long QF_HEAVY = 256;
-  const int64_t ngroups = (n_cols + 31) / 32;
-  double* hpart;
-  CTD_TRY(scratch.get(&hpart, ngroups));
+  const int64_t max_heavy = std::max<int64_t>(1, std::min<int64_t>(n_cols, (int64_t)(X_nnz / (QF_HEAVY + 1))));
+  int64_t* hlist;
+  unsigned* nh;
+  double* hval;
+  CTD_TRY(scratch.get(&hlist, max_heavy));
+  CTD_TRY(scratch.get(&nh, 1));
+  CTD_TRY(scratch.get(&hval, max_heavy));
+  CTD_CUDA(cudaMemsetAsync(hval, 0, max_heavy * sizeof(double), st));
+  CTD_TRY(ordered_heavy_list(X.colptr, n_cols, QF_HEAVY + 1, hlist, nh, scratch, st));
   ctd_status rc;
 #define QF(NKV)                                                                                 \
   rc = fp32 ? qform_launch<float, NKV>(X, n_cols, static_cast<const float*>(Q), qs, nblk,     \
                                        static_cast<const float*>(qn), slot_of, hot, n_hot,     \
-                                       n_rows, work, &partial, &nchunks, scratch, st, QF_HEAVY) \
+                                       n_rows, work, &partial, &nchunks, scratch, st, QF_HEAVY, \
+                                       hlist, nh, hval)                                         \
             : qform_launch<double, NKV>(X, n_cols, static_cast<const double*>(Q), qs, nblk,    \
                                         static_cast<const double*>(qn), slot_of, hot, n_hot,   \
                                         n_rows, work, &partial, &nchunks, scratch, st,         \
-                                        QF_HEAVY);                                             \
-  if (rc == CTD_OK)                                                                             \
-    rc = fp32 ? qform_heavy_launch<float, NKV>(X, n_cols, static_cast<const float*>(Q), qs,    \
-                                               nblk, slot_of, hot, n_hot, QF_HEAVY, hpart, st) \
-              : qform_heavy_launch<double, NKV>(X, n_cols, static_cast<const double*>(Q), qs,  \
-                                                nblk, slot_of, hot, n_hot, QF_HEAVY, hpart, st)
+                                        QF_HEAVY, hlist, nh, hval)
   if (NK <= 1) {
     QF(1);
   } else if (NK <= 2) {
@@ -1181,7 +1196,7 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, c
   double* two;
   CTD_TRY(scratch.get(&two, 2));
   CTD_TRY(sum_f64(partial, nchunks, two, scratch, st));
-  CTD_TRY(sum_f64(hpart, ngroups, two + 1, scratch, st));
+  CTD_TRY(sum_f64(hval, max_heavy, two + 1, scratch, st));
   CTD_LAUNCH(k_add2, (1), (32), 0, st, two, two + 1, out);
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;

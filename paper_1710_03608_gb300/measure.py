@@ -244,9 +244,43 @@ def ncu_metrics_summary(rep_path: str, kernel_regex: str, names) -> dict:
     return {"launches": res}
 
 
+def ncu_traffic_record(csv_path: str, kernels: str, scale: float, source: str) -> dict:
+    """DRAM bytes (read + write) of the launches whose names match `kernels`
+    in an `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --csv`
+    log, summed over the captured launches and multiplied by `scale` (the
+    ratio of the full workload's units to the captured case's), tagged with
+    the hash of the kernels' source file."""
+    import collections
+    import csv
+    import hashlib
+    import re
+    rows = list(csv.reader(open(csv_path)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    h = rows[hi]
+    ki, mi, vi, ui = (h.index("Kernel Name"), h.index("Metric Name"), h.index("Metric Value"),
+                      h.index("Metric Unit"))
+    unit = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    per = collections.defaultdict(float)
+    for r in rows[hi + 1:]:
+        if len(r) <= vi or not re.search(kernels, r[ki]):
+            continue
+        if r[mi] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            per[r[ki].split("(")[0].replace("void ", "")] += (
+                float(r[vi].replace(",", "")) * unit.get(r[ui], 1.0))
+    total = sum(per.values())
+    sha = hashlib.sha256(open(source, "rb").read()).hexdigest()[:16]
+    return {"source_sha": sha, "bytes_per_launch": total * scale, "captured_bytes": total,
+            "scale": scale, "per_kernel_captured": dict(per)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
+    nt = sub.add_parser("ncu-traffic")
+    nt.add_argument("csv")
+    nt.add_argument("--kernels", required=True)
+    nt.add_argument("--scale", type=float, required=True)
+    nt.add_argument("--source", required=True)
     ns = sub.add_parser("ncu-summary")
     ns.add_argument("csv")
     ns.add_argument("--top", type=int, default=30)
@@ -268,6 +302,9 @@ def main():
     args = ap.parse_args()
     if args.cmd == "ncu-summary":
         print(ncu_launch_summary(args.csv, args.top))
+        return
+    if args.cmd == "ncu-traffic":
+        print(json.dumps(ncu_traffic_record(args.csv, args.kernels, args.scale, args.source)))
         return
     import torch
     torch.cuda.set_device(0)
