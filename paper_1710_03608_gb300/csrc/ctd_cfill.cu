@@ -317,8 +317,8 @@ __device__ __forceinline__ void accumulate_reg(const CscDev& X, const CsrDev& R,
 }
 
 // Emit one column from regs + acc (acc zeroed on the way, regs too): the
-// nonzeros of rows [0, W) in ascending order at crow/cval + off.  Returns
-// their count (same value in every lane).
+// nonzeros of rows [0, W) in ascending order at crow/cval + off, each lane's
+// position from four ballots.  Returns their count (same in every lane).
 template <typename V, int NQ>
 __device__ __forceinline__ unsigned emit_reg(int* acc, int (&regs)[4 * NQ], unsigned long long off,
                                              uint16_t* __restrict__ crow, V* __restrict__ cval) {
@@ -332,15 +332,15 @@ __device__ __forceinline__ unsigned emit_reg(int* acc, int (&regs)[4 * NQ], unsi
     const int x0 = regs[4 * q] + s.x, x1 = regs[4 * q + 1] + s.y;
     const int x2 = regs[4 * q + 2] + s.z, x3 = regs[4 * q + 3] + s.w;
     regs[4 * q] = regs[4 * q + 1] = regs[4 * q + 2] = regs[4 * q + 3] = 0;
-    const int c = (x0 != 0) + (x1 != 0) + (x2 != 0) + (x3 != 0);
-    int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned long long o = off + pos + (unsigned)(incl - c);
+    // lane-major order: entries of the lanes before this one, by ballots
+    const unsigned b0 = __ballot_sync(0xffffffffu, x0 != 0);
+    const unsigned b1 = __ballot_sync(0xffffffffu, x1 != 0);
+    const unsigned b2 = __ballot_sync(0xffffffffu, x2 != 0);
+    const unsigned b3 = __ballot_sync(0xffffffffu, x3 != 0);
+    const unsigned lt = (1u << lane) - 1;
+    const int before = __popc(b0 & lt) + __popc(b1 & lt) + __popc(b2 & lt) + __popc(b3 & lt);
+    const int total = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+    unsigned long long o = off + pos + (unsigned)before;
     const int m0 = q * 128 + 4 * lane;
     if (x0) { crow[o] = (uint16_t)m0;       cval[o] = (V)x0; ++o; }
     if (x1) { crow[o] = (uint16_t)(m0 + 1); cval[o] = (V)x1; ++o; }
