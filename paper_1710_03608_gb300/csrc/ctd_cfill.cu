@@ -169,6 +169,19 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// four consecutive values, 16-byte aligned (float) or two 16-byte halves (double)
+template <typename V>
+__device__ __forceinline__ void store4(V* p, V a, V b, V c, V d);
+template <>
+__device__ __forceinline__ void store4<float>(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+template <>
+__device__ __forceinline__ void store4<double>(double* p, double a, double b, double c, double d) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+
 // C(:, f) = v R(i, :) for the single-nonzero columns.  A warp takes 32 list
 // entries; lane l loads column l's metadata (list entry, X entry, R row
 // range, output offset) so the dependent loads overlap across the 32
@@ -203,23 +216,35 @@ __global__ void __launch_bounds__(256)
       const unsigned long long oe = __shfl_sync(0xffffffffu, o, e);
       const int rle = __shfl_sync(0xffffffffu, rl, e);
       const int ve = __shfl_sync(0xffffffffu, v, e);
-      int q = lane;
-      for (; q + 96 < rle; q += 128) {
+      // the output run [oe, oe + rle): a scalar head up to a multiple of 4,
+      // then 4 entries per lane per step with one 8-byte row store and one
+      // 16-byte value store (vector stores: the kernel is store-bound), then
+      // a scalar tail
+      const int head = (int)min((unsigned long long)rle, (4ull - (oe & 3ull)) & 3ull);
+      if (lane < head) {
+        crow[oe + lane] = (uint16_t)__ldg(R.col + rse + lane);
+        cval[oe + lane] = (V)(ve * __ldg(R.val + rse + lane));
+      }
+      const unsigned long long ob = oe + head, rb = rse + head;
+      const int nvec = (rle - head) >> 2;
+      for (int t = lane; t < nvec; t += 32) {
+        const unsigned long long r = rb + 4ull * t;
         int c4[4], v4[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          c4[u] = __ldg(R.col + rse + q + 32 * u);
-          v4[u] = __ldg(R.val + rse + q + 32 * u);
+          c4[u] = __ldg(R.col + r + u);
+          v4[u] = __ldg(R.val + r + u);
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          crow[oe + q + 32 * u] = (uint16_t)c4[u];
-          cval[oe + q + 32 * u] = (V)(ve * v4[u]);
-        }
+        *reinterpret_cast<ushort4*>(crow + ob + 4ull * t) =
+            make_ushort4((unsigned short)c4[0], (unsigned short)c4[1], (unsigned short)c4[2],
+                         (unsigned short)c4[3]);
+        store4<V>(cval + ob + 4ull * t, (V)(ve * v4[0]), (V)(ve * v4[1]), (V)(ve * v4[2]),
+                  (V)(ve * v4[3]));
       }
-      for (; q < rle; q += 32) {
-        crow[oe + q] = (uint16_t)__ldg(R.col + rse + q);
-        cval[oe + q] = (V)(ve * __ldg(R.val + rse + q));
+      const int done = head + 4 * nvec;
+      if (lane < rle - done) {
+        crow[oe + done + lane] = (uint16_t)__ldg(R.col + rse + done + lane);
+        cval[oe + done + lane] = (V)(ve * __ldg(R.val + rse + done + lane));
       }
     }
   }

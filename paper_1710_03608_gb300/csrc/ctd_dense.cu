@@ -254,6 +254,21 @@ __device__ bool grid_sync(const GridBar& gb) {
   return ok != 0;
 }
 
+// 1 / sqrt(d) for d > 0: an FP32 estimate refined by two Newton-Raphson
+// steps for f(y) = 1/y^2 - d (y <- y (3 - d y^2) / 2), each doubling the
+// correct bits (~22 -> ~44 -> full double); outside FP32's comfortable range
+// the exact FP64 sqrt and division.  On GB300 the FP64 square root and
+// division are long multi-instruction sequences on a narrow pipe, and the
+// diagonal-block factorization takes one per column in sequence.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+  const double hd = 0.5 * d;
+  y = y * fma(-hd * y, y, 1.5);
+  y = y * fma(-hd * y, y, 1.5);
+  return y;
+}
+
 // The diagonal block at k0, in order, by warp 0 of the calling block: lane r
 // holds row r in registers; column c is finished left-looking (its entries
 // reduced by the earlier columns, row c's values broadcast by shuffles),
@@ -306,10 +321,10 @@ __device__ void chol_diag_block(double* __restrict__ A, int64_t n, int64_t lda, 
           if (lane == 0) atomicOr(status, DEV_CAPACITY);
           k = 0;
         }
-        const double l = k ? sqrt(d) : 0.0;
-        const double inv = k ? 1.0 / l : 0.0;
+        const double inv = k ? rsqrt_newton(d) : 0.0;
+        const double l = d * inv;
         if (lane == c)
-          row[c] = l;
+          row[c] = k ? l : 0.0;
         else if (lane > c)
           row[c] = row[c] * inv;
         if (lane == 0) {

@@ -1057,23 +1057,35 @@ __global__ void k_hot_hist(const uint32_t* __restrict__ cnt, int64_t n, unsigned
 __global__ void __launch_bounds__(1024)
     k_hot_threshold(const unsigned* __restrict__ hist, int n_hot, int* __restrict__ thr) {
   constexpr int PER = HOT_BINS / 1024;
-  __shared__ unsigned part[1024];
-  const int t = threadIdx.x;
+  __shared__ unsigned suf[1024];  // suf[g] = rows in groups >= g
+  __shared__ int gstar;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   unsigned s = 0;
   for (int b = 0; b < PER; ++b) s += hist[t * PER + b];
-  part[t] = s;
+  // inclusive suffix sum over the 1024 groups: within warps, then across
+  unsigned x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_down_sync(0xffffffffu, x, o);
+    if (lane + o < 32) x += y;
+  }
+  __shared__ unsigned wsum[32];
+  if (lane == 0) wsum[warp] = x;  // the warp's total
+  __syncthreads();
+  unsigned later = 0;
+  for (int w = warp + 1; w < 32; ++w) later += wsum[w];
+  suf[t] = x + later;
+  if (t == 0) gstar = 1024;
+  __syncthreads();
+  // the lowest group g whose suffix still fits in n_hot
+  if (suf[t] <= (unsigned)n_hot && (t == 0 || suf[t - 1] > (unsigned)n_hot)) gstar = t;
   __syncthreads();
   if (t == 0) {
-    // from the top: whole groups while they fit, then bin by bin
-    unsigned above = 0;
-    int L = HOT_BINS;  // none
-    int g = 1023;
-    for (; g >= 0 && above + part[g] <= (unsigned)n_hot; --g) {
-      above += part[g];
-      L = g * PER;
-    }
-    if (g >= 0)
-      for (int b = g * PER + PER - 1; b >= g * PER; --b) {
+    const int g = gstar;  // groups >= g fit entirely
+    unsigned above = g < 1024 ? suf[g] : 0;
+    int L = g < 1024 ? g * PER : HOT_BINS;
+    if (g > 0)
+      for (int b = g * PER - 1; b >= (g - 1) * PER; --b) {
         if (above + hist[b] > (unsigned)n_hot) break;
         above += hist[b];
         L = b;
