@@ -115,6 +115,55 @@ ctd_status sync(cudaStream_t st) {
   return CTD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// batched small read-backs through pinned staging
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t RB_CHUNK = 1 << 20;
+struct PinnedPool {
+  std::vector<char*> free_chunks;
+  ~PinnedPool() {
+    for (char* c : free_chunks) cudaFreeHost(c);
+  }
+};
+thread_local PinnedPool t_pinned;
+}  // namespace
+
+Readback::Readback(cudaStream_t s) : st(s) {
+  if (!t_pinned.free_chunks.empty()) {
+    chunk = t_pinned.free_chunks.back();
+    t_pinned.free_chunks.pop_back();
+  } else if (cudaMallocHost(reinterpret_cast<void**>(&chunk), RB_CHUNK) != cudaSuccess) {
+    cudaGetLastError();
+    chunk = nullptr;  // direct copies only
+  }
+}
+
+Readback::~Readback() {
+  // copies still in flight into the chunk must land before it is reused
+  if (!items.empty()) cudaStreamSynchronize(st);
+  if (chunk) t_pinned.free_chunks.push_back(chunk);
+}
+
+ctd_status Readback::add_bytes(void* host, const void* dev, size_t bytes) {
+  if (bytes == 0) return CTD_OK;
+  const size_t need = (bytes + 15) & ~size_t(15);
+  if (!chunk || bytes > RB_CHUNK) return d2h_bytes(host, dev, bytes, st);  // synchronous copy
+  if (used + need > RB_CHUNK) CTD_TRY(wait());
+  CTD_CUDA(cudaMemcpyAsync(chunk + used, dev, bytes, cudaMemcpyDeviceToHost, st));
+  items.push_back({host, used, bytes});
+  used += need;
+  return CTD_OK;
+}
+
+ctd_status Readback::wait() {
+  CTD_CUDA(cudaStreamSynchronize(st));
+  for (const Item& it : items) std::memcpy(it.host, chunk + it.off, it.bytes);
+  items.clear();
+  used = 0;
+  return CTD_OK;
+}
+
 // Validate a COO descriptor; produce device views (copying host inputs in).
 ctd_status stage_coo(const ctd_coo3* X, int alpha, Arena& scratch, cudaStream_t st, CooDev* out) {
   if (!X) return fail(CTD_EINVAL, "tensor descriptor is NULL");
@@ -282,12 +331,15 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   unsigned status = 0;
   int minval = 0, s_unique = 0;
   uint64_t T = 0, nnz_cand = 0;
-  STEP(d2h(&status, M.status, 1, st));
-  STEP(d2h(&minval, M.minval, 1, st));
-  STEP(d2h(&s_unique, d_count, 1, st));
-  STEP(d2h(&nnz_cand, rc_ptr + s, 1, st));
-  if (M.n_cols > 0) STEP(d2h(&T, M.cdf + (M.n_cols - 1), 1, st));
-  STEP(sync(st));
+  {
+    Readback rb(st);
+    STEP(rb.add(&status, M.status, 1));
+    STEP(rb.add(&minval, M.minval, 1));
+    STEP(rb.add(&s_unique, d_count, 1));
+    STEP(rb.add(&nnz_cand, rc_ptr + s, 1));
+    if (M.n_cols > 0) STEP(rb.add(&T, M.cdf + (M.n_cols - 1), 1));
+    STEP(rb.wait());
+  }
   STEP(status_from_device(status));
   F->T = T;
   F->s_unique = s_unique;
@@ -383,9 +435,12 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
       launch_scan_u32(ub, F->Coff, M.n_cols, false, M.tmp, M.status, st);
     }
     uint64_t cap = 0, nnzR = 0;
-    STEP(d2h(&cap, F->Coff + M.n_cols, 1, st));
-    STEP(d2h(&nnzR, F->Rcolptr + kept, 1, st));
-    STEP(sync(st));
+    {
+      Readback rb(st);
+      STEP(rb.add(&cap, F->Coff + M.n_cols, 1));
+      STEP(rb.add(&nnzR, F->Rcolptr + kept, 1));
+      STEP(rb.wait());
+    }
     F->nnz_R = (int64_t)nnzR;
     F->C_cap = cap;
     STEP(F->mem.get(&F->Crow, cap));
@@ -412,12 +467,15 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   if (F->Ccnt) launch_sum_u32(F->Ccnt, M.n_cols, d_nnzc, st);
   uint64_t nnzC = 0, nnzR_final = 0;
   double pu = 0.0;
-  STEP(d2h(&nnzR_final, F->Rcolptr + kept, 1, st));
-  if (F->Ccnt) STEP(d2h(&nnzC, d_nnzc, 1, st));
-  if (d_pu) STEP(d2h(&pu, d_pu, 1, st));
-  STEP(d2h(&status, M.status, 1, st));
-  STEPC(cudaGetLastError());
-  STEP(sync(st));
+  {
+    Readback rb(st);
+    STEP(rb.add(&nnzR_final, F->Rcolptr + kept, 1));
+    if (F->Ccnt) STEP(rb.add(&nnzC, d_nnzc, 1));
+    if (d_pu) STEP(rb.add(&pu, d_pu, 1));
+    STEP(rb.add(&status, M.status, 1));
+    STEPC(cudaGetLastError());
+    STEP(rb.wait());
+  }
   STEP(status_from_device(status));
   F->nnz_C = (int64_t)nnzC;
   F->nnz_R = (int64_t)nnzR_final;

@@ -281,6 +281,7 @@ struct CholShared {
   double thr_s[NB], piv_s[NB];
   int force_s[NB];
   double fpiv_s[NB];
+  double colc[2][NB];  // the column just finished (double-buffered)
 };
 
 __device__ void chol_diag_block(double* __restrict__ A, int64_t n, int64_t lda, int64_t k0,
@@ -301,50 +302,67 @@ __device__ void chol_diag_block(double* __restrict__ A, int64_t n, int64_t lda, 
     fpiv_s[tid] = fpiv ? fpiv[k0 + tid] : 0.0;
   }
   __syncthreads();
-  if (warp == 0) {
-    double row[NB];
+  // Four warps, one per SM sub-partition (GB300's FP64 unit is narrow: a
+  // warp-wide FP64 instruction occupies a sub-partition for ~64 cycles, so
+  // one warp alone was the bottleneck).  Warp w holds columns j = 4 t + w,
+  // lane r row r.  Column c's owner decides and scales it and publishes it
+  // in shared memory; after a named barrier of the four warps every warp
+  // updates its later columns (right-looking).
+  constexpr int CW = 4, TPW = NB / CW;
+  if (warp < CW) {
+    double rowj[TPW];
 #pragma unroll
-    for (int c = 0; c < NB; ++c)
-      row[c] = (lane < nb && c <= lane) ? A[(k0 + lane) + (k0 + c) * lda] : 0.0;
-    // right-looking: once column c is decided and scaled, every later
-    // column j is updated (independent multiply-adds, no dependent chain)
+    for (int t = 0; t < TPW; ++t) {
+      const int j = CW * t + warp;
+      rowj[t] = (lane < nb && j <= lane) ? A[(k0 + lane) + (k0 + j) * lda] : 0.0;
+    }
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
       if (c < nb) {
-        double d = __shfl_sync(0xffffffffu, row[c], c);
-        int k = (d > thr_s[c] && d > 0.0) ? 1 : 0;
-        if (force_s[c] >= 0) k = force_s[c];
-        // a keep forced by the explicit residual takes that residual's
-        // squared norm as its pivot (the Gram-based one lost it to rounding)
-        if (force_s[c] == 1 && fpiv_s[c] > 0.0) d = fpiv_s[c];
-        if (k && !(d > 0.0)) {
-          if (lane == 0) atomicOr(status, DEV_CAPACITY);
-          k = 0;
+        const int owner = c % CW, tc = c / CW;
+        double* colc = sh.colc[c & 1];
+        if (warp == owner) {
+          double d = __shfl_sync(0xffffffffu, rowj[tc], c);
+          int k = (d > thr_s[c] && d > 0.0) ? 1 : 0;
+          if (force_s[c] >= 0) k = force_s[c];
+          // a keep forced by the explicit residual takes that residual's
+          // squared norm as its pivot (the Gram-based one lost it to rounding)
+          if (force_s[c] == 1 && fpiv_s[c] > 0.0) d = fpiv_s[c];
+          if (k && !(d > 0.0)) {
+            if (lane == 0) atomicOr(status, DEV_CAPACITY);
+            k = 0;
+          }
+          const double inv = k ? rsqrt_newton(d) : 0.0;
+          double v = 0.0;
+          if (lane == c)
+            v = k ? d * inv : 0.0;
+          else if (lane > c)
+            v = rowj[tc] * inv;
+          rowj[tc] = v;
+          colc[lane] = v;
+          if (lane == 0) {
+            kp[c] = k;
+            piv_s[c] = d;
+          }
         }
-        const double inv = k ? rsqrt_newton(d) : 0.0;
-        const double l = d * inv;
-        if (lane == c)
-          row[c] = k ? l : 0.0;
-        else if (lane > c)
-          row[c] = row[c] * inv;
-        if (lane == 0) {
-          kp[c] = k;
-          piv_s[c] = d;
-        }
-        if (k) {
+        asm volatile("bar.sync 1, %0;" ::"n"(CW * 32));
+        if (kp[c]) {
+          const double lr = colc[lane];
 #pragma unroll
-          for (int j = c + 1; j < NB; ++j) {
-            const double ljc = __shfl_sync(0xffffffffu, row[c], j);
-            if (lane >= j) row[j] = fma(-row[c], ljc, row[j]);
+          for (int t = 0; t < TPW; ++t) {
+            const int j = CW * t + warp;
+            if (j > c && lane >= j) rowj[t] = fma(-lr, colc[j], rowj[t]);
           }
         }
       }
     }
 #pragma unroll
-    for (int c = 0; c < NB; ++c)
-      if (lane < nb && c <= lane) A[(k0 + lane) + (k0 + c) * lda] = row[c];
-    __syncwarp();
-    if (lane < nb) {
+    for (int t = 0; t < TPW; ++t) {
+      const int j = CW * t + warp;
+      if (lane < nb && j <= lane) A[(k0 + lane) + (k0 + j) * lda] = rowj[t];
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(CW * 32));
+    if (warp == 0 && lane < nb) {
       keep[k0 + lane] = kp[lane];
       if (piv) piv[k0 + lane] = piv_s[lane];
     }

@@ -201,7 +201,6 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
   CTD_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
   std::vector<int> h_force(du, -1), h_keep(du);
   std::vector<double> h_piv(du), h_xn(du), h_fpiv(du, 0.0);
-  CTD_TRY(d2h(h_xn.data(), xn2, du, st));
   for (int iter = 0; iter <= du + 1; ++iter) {
     if (iter > 0) {
       CTD_CUDA(cudaMemcpyAsync(in.S, S0, (size_t)du * du * 8, cudaMemcpyDeviceToDevice, st));
@@ -218,12 +217,16 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
     }
     unsigned h_status = 0;
     int kept = 0;
-    CTD_TRY(d2h(&kept, count, 1, st));
-    CTD_TRY(d2h(&h_status, status, 1, st));
-    CTD_TRY(d2h(h_piv.data(), piv, du, st));
-    CTD_TRY(d2h(h_keep.data(), out.keep, du, st));
-    CTD_CUDA(cudaGetLastError());
-    CTD_TRY(sync(st));
+    {
+      Readback rb(st);
+      if (iter == 0) CTD_TRY(rb.add(h_xn.data(), (const double*)xn2, du));
+      CTD_TRY(rb.add(&kept, (const int*)count, 1));
+      CTD_TRY(rb.add(&h_status, (const unsigned*)status, 1));
+      CTD_TRY(rb.add(h_piv.data(), (const double*)piv, du));
+      CTD_TRY(rb.add(h_keep.data(), (const int*)out.keep, du));
+      CTD_CUDA(cudaGetLastError());
+      CTD_TRY(rb.wait());
+    }
     if (h_status & DEV_TIMEOUT) return fail(CTD_ETIMEOUT, "skip-Cholesky grid barrier gave up");
     if (h_status & DEV_CAPACITY)
       return fail(CTD_ENOTSUP,

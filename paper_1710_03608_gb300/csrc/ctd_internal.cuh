@@ -312,6 +312,27 @@ void launch_thresholds(const double* D, int64_t n, int64_t ldd, double eps2, dou
                        cudaStream_t st);
 
 // ctd_api.cu (host helpers shared by the entry points) -------------------
+// Several small device-to-host reads behind one stream synchronization:
+// each add() enqueues an asynchronous copy into a pinned staging chunk (a
+// per-thread pool, so concurrent calls on other threads do not collide);
+// wait() synchronizes the stream once and copies the values out.  Reads too
+// large for a chunk fall back to a direct copy.
+struct Readback {
+  explicit Readback(cudaStream_t s);
+  ~Readback();
+  template <typename T>
+  ctd_status add(T* host, const T* dev, size_t n) {
+    return add_bytes(host, dev, n * sizeof(T));
+  }
+  ctd_status add_bytes(void* host, const void* dev, size_t bytes);
+  ctd_status wait();
+  cudaStream_t st;
+  char* chunk = nullptr;
+  size_t used = 0;
+  struct Item { void* host; size_t off, bytes; };
+  std::vector<Item> items;
+};
+
 ctd_status d2h_bytes(void* host, const void* dev, size_t bytes, cudaStream_t st);
 template <typename T>
 inline ctd_status d2h(T* host, const T* dev, size_t n, cudaStream_t st) {
