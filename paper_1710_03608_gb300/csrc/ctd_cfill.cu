@@ -29,7 +29,8 @@ namespace {
 constexpr int CF_THREADS = 1024;  // one block per SM shares one copy of the dense rows
 constexpr int CF_HEAVY_COL = 128;  // columns with at least this many nonzeros: one block each
 constexpr int CF_LONG_ROW = 16;    // sparse rows at least this long: walked by the whole warp
-constexpr int CF_MAX_DENSE = 64;   // dense rows at most
+constexpr int CF_LONG_GROUP = 2;   // long sparse rows walked together (loads in flight)
+constexpr int CF_MAX_DENSE = 96;   // dense rows at most (shared memory bounds it first)
 
 // --- selection of the dense rows -------------------------------------------
 // hist[len] = number of rows of R with len entries (len >= minlen, capped at width)
@@ -276,26 +277,35 @@ __device__ __forceinline__ void chunk_reg(const CsrDev& R, const int4* __restric
       regs[4 * q + 3] += vs * x.w;
     }
   }
+  // the long sparse rows, CF_LONG_GROUP at a time: each lane loads its entries of
+  // all of them before the atomics, so their L2 latencies overlap
   unsigned longs = __ballot_sync(0xffffffffu, rl >= CF_LONG_ROW);
   while (longs) {
-    const int src = __ffs(longs) - 1;
-    longs &= longs - 1;
-    const unsigned long long s0 = __shfl_sync(0xffffffffu, rs, src);
-    const int n = __shfl_sync(0xffffffffu, rl, src);
-    const int vs = __shfl_sync(0xffffffffu, v, src);
-    // four loads in flight per lane before the atomics
-    int q = lane;
-    for (; q + 96 < n; q += 128) {
-      int c4[4], v4[4];
+    unsigned long long s0[CF_LONG_GROUP];
+    int nn[CF_LONG_GROUP], vs[CF_LONG_GROUP];
+    int maxn = 0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        c4[u] = __ldg(R.col + s0 + q + 32 * u);
-        v4[u] = __ldg(R.val + s0 + q + 32 * u);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) atomicAdd(acc + c4[u], vs * v4[u]);
+    for (int u = 0; u < CF_LONG_GROUP; ++u) {
+      const int src = longs ? __ffs(longs) - 1 : -1;
+      if (longs) longs &= longs - 1;
+      const int sl = src < 0 ? 0 : src;
+      s0[u] = __shfl_sync(0xffffffffu, rs, sl);
+      nn[u] = src < 0 ? 0 : __shfl_sync(0xffffffffu, rl, sl);
+      vs[u] = __shfl_sync(0xffffffffu, v, sl);
+      maxn = max(maxn, nn[u]);
     }
-    for (; q < n; q += 32) atomicAdd(acc + __ldg(R.col + s0 + q), vs * __ldg(R.val + s0 + q));
+    for (int q = lane; q < maxn; q += 32) {
+      int c4[CF_LONG_GROUP], v4[CF_LONG_GROUP];
+#pragma unroll
+      for (int u = 0; u < CF_LONG_GROUP; ++u)
+        if (q < nn[u]) {
+          c4[u] = __ldg(R.col + s0[u] + q);
+          v4[u] = __ldg(R.val + s0[u] + q);
+        }
+#pragma unroll
+      for (int u = 0; u < CF_LONG_GROUP; ++u)
+        if (q < nn[u]) atomicAdd(acc + c4[u], vs[u] * v4[u]);
+    }
   }
   if (rl >= CF_LONG_ROW) rl = 0;
   if (__any_sync(0xffffffffu, rl > 0))
