@@ -37,15 +37,19 @@ Readings of points the paper leaves open (same letters everywhere):
   A21 line 7's residual is evaluated as x minus its orthogonal projection
       onto range(R), by Gram-Schmidt with reorthogonalization (equal to
       x - R U R^T x in exact arithmetic; stable in floating point).
+  A23 Section 5's average norm is the exact sum of the representatives'
+     norms rounded once, divided by their count (no summation order).
 
 Parity pinned by tests/test_oracle_pins.py (brute force, numpy/scipy
-library routines, invariants, chi-square).  The DDoS rule is pinned only
-semantically (planted block), not against the paper's Table 4 numbers
-(parity unpinned for Table 4: the CAIDA data are not available).
+library routines, invariants, chi-square).  The DDoS rule is pinned by a
+hand-computed case and semantically (planted block), not against the
+paper's Table 4 numbers (parity unpinned for Table 4: the CAIDA data are
+not available).
 """
 from __future__ import annotations
 
 import dataclasses
+import math
 from typing import List, Optional, Sequence
 
 import numpy as np
@@ -498,15 +502,21 @@ def dynamic_error_dense(state: DynamicState) -> float:
 # Section 5: DDoS candidates from CTD-D's R
 # ---------------------------------------------------------------------------
 
-def ddos_candidates(fibers: Sequence[tuple], R_cols: Sequence[np.ndarray]) -> List[int]:
-    """Group R's fibers (t, destination) by destination; the first fiber of
-    each group represents it; report the destinations whose representative's
-    norm exceeds the mean norm of all representatives."""
+def ddos_candidates(fibers: Sequence[tuple], R_cols: Sequence[np.ndarray],
+                    with_mean: bool = False):
+    """Section 5's detector on R (reading A23): group R's fibers (t, destination) by
+    destination; the first fiber of each group (in R's column order)
+    represents it; report, ascending, the destinations whose representative's
+    2-norm exceeds the average 2-norm over all representatives.
+
+    Each norm is the square root (rounded once) of the column's exact integer
+    sum of squares; the average is the exact sum of those norms rounded once
+    (math.fsum), divided by their count, so it has no summation order."""
     first = {}
     for (t, dst), col in zip(fibers, R_cols):
         if dst not in first:
-            first[dst] = float(np.sqrt(np.dot(col, col)))
-    if not first:
-        return []
-    mean = sum(first.values()) / len(first)
-    return sorted(dst for dst, nrm in first.items() if nrm > mean)
+            c = np.asarray(col, dtype=np.int64)
+            first[dst] = math.sqrt(float(int(np.dot(c, c))))
+    mean = math.fsum(first.values()) / len(first) if first else 0.0
+    out = sorted(dst for dst, nrm in first.items() if nrm > mean)
+    return (out, mean) if with_mean else out

@@ -1,6 +1,8 @@
 """Pins of the FP64 oracle against things other than itself: brute force on
 dense arrays, numpy/scipy library routines, closed forms, invariants and a
 chi-square test of the sampling law.  CPU only."""
+import math
+
 import numpy as np
 import pytest
 
@@ -284,6 +286,30 @@ def test_ddos_rule_flags_planted_destinations():
     flagged = O.ddos_candidates(st.fibers, st.R_cols)
     assert set(victims) <= set(flagged)
     assert len(flagged) < 10
+
+
+def test_ddos_rule_hand_computed():
+    """Section 5's rule on a hand-made R: fibers (t, destination) in column
+    order; destination 7 appears twice and only its first fiber (norm 3)
+    counts. Representatives' norms 3, 4, 5, 12 -> average 6 -> only 9 flagged;
+    a representative equal to the average is not flagged (strict)."""
+    fibers = [(0, 7), (0, 2), (1, 7), (1, 4), (2, 9)]
+    cols = [np.array([3, 0, 0]), np.array([0, 4, 0]), np.array([100, 0, 0]),
+            np.array([3, 0, 4]), np.array([12, 0, 0])]
+    got, mean = O.ddos_candidates(fibers, cols, with_mean=True)
+    assert mean == 6.0 and got == [9]
+    # norms 2, 4, 6: the average equals the middle one, which is not flagged
+    got, mean = O.ddos_candidates([(0, 1), (0, 2), (0, 3)],
+                                  [np.array([2]), np.array([4]), np.array([6])], with_mean=True)
+    assert mean == 4.0 and got == [3]
+    # the average has no summation order: a thousand norms of sqrt(2) and one of
+    # 1000 sqrt(2), exactly rounded once
+    fib = [(0, d) for d in range(1001)]
+    cols = [np.array([1, 1])] * 1000 + [np.array([1000, 1000])]
+    got, mean = O.ddos_candidates(fib, cols, with_mean=True)
+    assert mean == math.fsum([math.sqrt(2.0)] * 1000 + [math.sqrt(2e6)]) / 1001
+    assert got == [1000]
+    assert O.ddos_candidates([], []) == []
 
 
 # --- A10 / A12 edge cases ----------------------------------------------------------
