@@ -230,6 +230,29 @@ CTD_API ctd_status ctd_get_M(const ctd_factors* F, int64_t t, double* M);
 CTD_API void ctd_free(ctd_factors* F);
 
 /*
+ * ctd_ddos_candidates -- the online DDoS detector of Section 5 ("CTD at
+ * work") on the factor R.  With alpha = 1 (the source mode) each fiber of R
+ * is the traffic of one destination: for CTD-D the fiber's slice-local id
+ * is the destination index; for CTD-S factors the destination of fiber
+ * f = j + J*k is j.  R's fibers are grouped by destination, the first fiber
+ * of a destination in R's column order represents it, and a destination is
+ * a candidate iff its representative's 2-norm (square root, rounded once, of
+ * the column's exact integer sum of squares) exceeds the average norm over
+ * all representatives.  The average is the exact sum of the norms rounded
+ * once, divided by their count: the result does not depend on any
+ * summation order.
+ *  cap        entries of dst
+ *  dst        host int64[cap] (NULL if cap = 0), receives the first cap
+ *             candidates in ascending destination order
+ *  n_found    host, receives the number of candidates (may exceed cap)
+ *  mean_norm  host or NULL, receives the average
+ * Runs on the factors' stream and waits for it.  CTD_EINVAL: NULL F or
+ * n_found, cap < 0, dst NULL with cap > 0, or alpha != 1.
+ */
+CTD_API ctd_status ctd_ddos_candidates(const ctd_factors* F, int64_t cap, int64_t* dst,
+                                       int64_t* n_found, double* mean_norm);
+
+/*
  * ctd_sample_noalloc -- the draws I and their unique set I' of ctd_static
  * (same values as ctd_get_samples on ctd_static(X, alpha, s, eps, seed, ...)),
  * without allocating any device memory.  The paper has no counterpart: this

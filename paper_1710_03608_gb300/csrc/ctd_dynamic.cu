@@ -34,6 +34,10 @@ using namespace ctd;
 
 namespace {
 
+// a keep whose pivot is below this fraction of ||x||^2 (residual ratio below
+// 1e-4) ends a filter round (see ctd_dynamic_step)
+constexpr double WEAK_KEEP = 1e-8;
+
 struct StepRec {
   int64_t d_draws = 0, d_unique = 0, d_kept = 0, d_before = 0, nnz = 0;
   double sq = 0.0, err = 0.0;      // ||dX||^2 and ||dX - P dX||^2
@@ -136,7 +140,7 @@ struct ctd_factors::Dyn {
   unsigned flags = 0;
   int64_t t = 0;
   int64_t cap_d = 0;                 // leading dimension of U
-  int64_t cap_cols = 0, cap_nnz = 0;
+  int64_t cap_cols = 0, cap_nnz = 0, cap_fib = 0;
   std::vector<StepRec> steps;
   std::vector<int64_t> fiber_id, fiber_step;
   double err_num = 0.0, err_den = 0.0;
@@ -169,6 +173,8 @@ ctd_factors::~ctd_factors() {
     L = nullptr;
     Qt = nullptr;
     qn = nullptr;
+    dfree(fibers, stream);
+    fibers = nullptr;
     dfree(Rcolptr, stream);
     dfree(Rrow, stream);
     dfree(Rval, stream);
@@ -436,13 +442,15 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   D.last_d = T ? d : 0;
   D.last_du = du;
 
-  int kept = 0;
-  int* idx = nullptr;
-  FilterOut fo;
-  const uint64_t* rc_ptr_k = nullptr;  // the candidates as CSC
-  const int32_t* rc_row_k = nullptr;
-  const int32_t* rc_val_k = nullptr;
-  double* W = nullptr;    // Q^(t)^T X_c = L^{-1} R^(t)^T X_c
+  // lines 5-16, in rounds.  The block filter takes the sequential loop's
+  // decisions while the kept block of the Schur complement stays well
+  // conditioned.  A candidate kept with a tiny residual (ratio below 1e-4)
+  // would make it ill-conditioned for every later candidate of the block (its
+  // pivots and explicit re-tests would carry errors of order u * kappa), so a
+  // round ends at such a keep: the round's kept candidates join R and the
+  // orthonormal basis Q (explicit Gram-Schmidt, accurate for small residuals),
+  // and the next round tests the remaining candidates against the grown basis.
+  int kept_total = 0;
   // R^(t) already spans every mode-alpha vector (d~_t = I_alpha independent
   // columns): every candidate's residual is exactly zero, so none is kept.
   if (du > 0 && dt < M.n_rows) {
@@ -468,195 +476,241 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
     launch_sort_segments(rc_ptr, du, rc_row, rc_val, rcr_col, rcr_val, st);
     CTD_TRY(build_csr_from_csc(rc_ptr, rc_row, rc_val, du, (int64_t)nnz_cand, M.n_rows, 0,
                                rcr_ptr, rcr_col, rcr_val, scratch, st));
-    // Gram of the candidates and the Schur complement against R^(t)
-    double *S, *xn2;
-    CTD_TRY(scratch.get(&S, (size_t)du * du));
+    // exact Gram of the candidates (once) and their squared norms
+    double *G0, *xn2;
+    CTD_TRY(scratch.get(&G0, (size_t)du * du));
     CTD_TRY(scratch.get(&xn2, du));
     {
       PhaseScope ph("d_gram", st);
       CTD_TRY(launch_spmm_dense(M.csc(), D.lastIu, d_count, du,
-                                CsrDev{rcr_ptr, rcr_col, rcr_val, du}, S, du, st));
-      launch_thresholds(S, du, du, 1.0, xn2, st);  // ||x_k||^2
-      if (dt > 0) {
-        // W = Q^(t)^T X_c (= L^{-1} R^(t)^T X_c, since R^(t) = Q L^T), a sparse
-        // product with the basis rows; S = X_c^T X_c - W^T W
-        CTD_TRY(scratch.get(&W, (size_t)dt * du));
+                                CsrDev{rcr_ptr, rcr_col, rcr_val, du}, G0, du, st));
+      launch_thresholds(G0, du, du, 1.0, xn2, st);  // ||x_k||^2
+    }
+    const int64_t dt0 = dt;  // W_K of the whole step, against Q^(t), for the M chain
+    if (dt0 > 0) CTD_TRY(dalloc_n(&rec.WK, (size_t)dt0 * du, st));
+    uint64_t* rr_ptr = nullptr;  // by-row layout of a later round's candidates
+    int32_t *rr_col = nullptr, *rr_val = nullptr;
+    int* d_kr;
+    CTD_TRY(scratch.get(&d_kr, 1));
+    int start = 0;
+    while (start < du && F->s_kept < M.n_rows) {
+      const int dur = du - start;
+      const int64_t dtc = F->s_kept;
+      const uint64_t* rptr = rc_ptr + start;  // this round's candidates (absolute offsets)
+      const uint64_t* cr_ptr = rcr_ptr;
+      const int32_t *cr_col = rcr_col, *cr_val = rcr_val;
+      if (start > 0) {
+        if (!rr_ptr) {
+          CTD_TRY(scratch.get(&rr_ptr, M.n_rows + 1));
+          CTD_TRY(scratch.get(&rr_col, nnz_cand));
+          CTD_TRY(scratch.get(&rr_val, nnz_cand));
+        }
+        CTD_TRY(build_csr_from_csc(rptr, rc_row, rc_val, dur, (int64_t)nnz_cand, M.n_rows, 0,
+                                   rr_ptr, rr_col, rr_val, scratch, st));
+        cr_ptr = rr_ptr;
+        cr_col = rr_col;
+        cr_val = rr_val;
+      }
+      // the Schur complement of the round's candidates against R:
+      // S = X_r^T X_r - W^T W with W = Q^T X_r (= L^{-1} R^T X_r, R = Q L^T)
+      double *S, *W = nullptr;
+      CTD_TRY(scratch.get(&S, (size_t)dur * dur));
+      CTD_CUDA(cudaMemcpy2DAsync(S, (size_t)dur * 8, G0 + start + (size_t)start * du,
+                                 (size_t)du * 8, (size_t)dur * 8, dur, cudaMemcpyDeviceToDevice,
+                                 st));
+      if (dtc > 0) {
+        PhaseScope ph("d_gram", st);
+        CTD_TRY(scratch.get(&W, (size_t)dtc * dur));
         // candidates with more than 256 nonzeros: split over blocks
-        const int64_t max_heavy = std::min<int64_t>(du, (int64_t)nnz_cand / 257);
-        CTD_LAUNCH(k_qt_times_sparse, ((unsigned)std::min(du, 65535)), (256), 0, st,
-                   reinterpret_cast<const unsigned long long*>(rc_ptr), rc_row, rc_val, du,
-                   F->Qt, D.cap_d, dt, max_heavy > 0 ? 256ull : ~0ull, W);
+        const int64_t max_heavy = std::min<int64_t>(dur, (int64_t)nnz_cand / 257);
+        CTD_LAUNCH(k_qt_times_sparse, ((unsigned)std::min(dur, 65535)), (256), 0, st,
+                   reinterpret_cast<const unsigned long long*>(rptr), rc_row, rc_val, dur, F->Qt,
+                   D.cap_d, dtc, max_heavy > 0 ? 256ull : ~0ull, W);
         if (max_heavy > 0) {
           int64_t* hl;
           unsigned* nh;
           CTD_TRY(scratch.get(&hl, max_heavy));
           CTD_TRY(scratch.get(&nh, 1));
           CTD_CUDA(cudaMemsetAsync(nh, 0, sizeof(unsigned), st));
-          launch_list_columns_nnz(rc_ptr, du, 257, hl, nh, st);
-          CTD_TRY(launch_heavy_columns(hl, nh, max_heavy, rc_ptr, rc_row, rc_val, F->Qt, D.cap_d,
-                                       dt, W, nullptr, scratch, st));
+          launch_list_columns_nnz(rptr, dur, 257, hl, nh, st);
+          CTD_TRY(launch_heavy_columns(hl, nh, max_heavy, rptr, rc_row, rc_val, F->Qt, D.cap_d,
+                                       dtc, W, nullptr, scratch, st));
         }
-        dgemm(true, false, du, du, dt, -1.0, W, dt, W, dt, 1.0, S, du, st);
+        dgemm(true, false, dur, dur, dtc, -1.0, W, dtc, W, dtc, 1.0, S, dur, st);
       }
-    }
-    FilterIn fi;
-    fi.du = du;
-    fi.S = S;
-    fi.xnorm2 = xn2;
-    fi.eps = eps;
-    fi.cptr = rc_ptr;
-    fi.crow = rc_row;
-    fi.cval = rc_val;
-    fi.c_rowptr = rcr_ptr;
-    fi.c_col = rcr_col;
-    fi.c_val = rcr_val;
-    fi.n_rows = M.n_rows;
-    if (dt > 0) {
-      fi.dt = dt;
-      fi.Lt = F->L;
-      fi.ldl = D.cap_d;
-      fi.W = W;
-      fi.rptr = F->Rcolptr;
-      fi.rrow = F->Rrow;
-      fi.rval = F->Rval;
-      fi.r_rowptr = F->Rrowptr;
-      fi.r_col = F->Rcol;
-      fi.r_val = F->Rcval;
-    }
-    CTD_TRY(run_filter(fi, fo, scratch, st));
-    rc_ptr_k = rc_ptr;
-    rc_row_k = rc_row;
-    rc_val_k = rc_val;
-    kept = fo.kept;
-    idx = fo.idx;
-    rec.d_kept = kept;
-
-    if (kept > 0) {
-      PhaseScope ph("d_update_u", st);
-      const int64_t dn = dt + kept;
-      double* WKs = nullptr;  // W restricted to the kept candidates (dt x kept)
-      double* Li = fo.Li;  // inverse of the filter's factor of the kept block of S
-      F->U_valid = false;
-      CTD_TRY(grow_U(F, dt, dn, st));
-      const int64_t ld = D.cap_d;
-      // Gram-Schmidt of the kept candidates against Q^(t): X_K = Q^(t) W_K + V
-      // with V orthogonal to range(Q^(t)); then V = Q_new Lam^T (Lam lower
-      // triangular) with Q_new orthonormal.  So R^(t+1) = Q^(t+1) L^(t+1)^T
-      // with L^(t+1) = [[L, 0], [W_K^T, Lam]], a Cholesky factor of
-      // R^(t+1)^T R^(t+1); W_K is kept for the M chain (M_{t+1} = W_K^T
-      // L^(t)^{-1} = ((dR)^T R^(t)) U^(t), formed on request).
-      {
-        PhaseScope phq("d_q_basis", st);
-        const int64_t nr = M.n_rows;
-        double *V, *V2, *Vq;
-        CTD_TRY(scratch.get(&V, (size_t)nr * kept));
-        CTD_TRY(scratch.get(&V2, (size_t)nr * kept));
-        CTD_TRY(scratch.get(&Vq, (size_t)nr * kept));
-        CTD_CUDA(cudaMemsetAsync(V, 0, (size_t)nr * kept * 8, st));
-        CTD_LAUNCH(k_densify_cols, ((unsigned)std::min(kept, 4096)), (128), 0, st,
-                   reinterpret_cast<const unsigned long long*>(rc_ptr_k), rc_row_k, rc_val_k, idx,
-                   kept, V, nr);
-        if (dt > 0) {
-          CTD_TRY(dalloc_n(&rec.WK, (size_t)dt * kept, st));
-          WKs = rec.WK;
-          const unsigned gk = grid_for(dt * kept, 256, (int64_t)num_sms() * 8);
-          CTD_LAUNCH(k_gather_cols_f64, (gk), (256), 0, st, W, dt, dt, idx, kept, rec.WK, dt);
-          dgemm(true, false, nr, kept, dt, -1.0, F->Qt, ld, WKs, dt, 1.0, V, nr, st);
-          // the second pass holds the blocks orthogonal to ~u / rho for a
-          // residual ratio rho >= eps (and adds its coefficients to W_K);
-          // FP32_BULK's error bar (1e-4 relative) does not need it
-          if (!fp32) {
+      FilterIn fi;
+      fi.du = dur;
+      fi.S = S;
+      fi.xnorm2 = xn2 + start;
+      fi.eps = eps;
+      fi.cptr = rptr;
+      fi.crow = rc_row;
+      fi.cval = rc_val;
+      fi.c_rowptr = cr_ptr;
+      fi.c_col = cr_col;
+      fi.c_val = cr_val;
+      fi.n_rows = M.n_rows;
+      if (dtc > 0) {
+        fi.dt = dtc;
+        fi.Qt = F->Qt;
+        fi.ldq = D.cap_d;
+        fi.W = W;
+      }
+      FilterOut fo;
+      CTD_TRY(run_filter(fi, fo, scratch, st));
+      // the round ends at its first keep with a residual ratio below 1e-4
+      int kr = fo.kept, next = du;
+      for (int c = 0, seen = 0; c < dur; ++c) {
+        if (!fo.keep_h[c]) continue;
+        ++seen;
+        if (fo.piv_h[c] < WEAK_KEEP * fo.xn_h[c]) {
+          kr = seen;
+          next = start + c + 1;
+          break;
+        }
+      }
+      const int* idx = fo.idx;  // round-relative positions of the kept candidates
+      if (kr > 0) {
+        CTD_CUDA(cudaMemcpyAsync(d_kr, &kr, sizeof(int), cudaMemcpyHostToDevice, st));
+        const int64_t dn = dtc + kr;
+        const double* Li = fo.Li;  // inverse of the filter's factor (leading kr x kr used)
+        const int64_t ldli = fo.kept;
+        F->U_valid = false;
+        CTD_TRY(grow_U(F, dtc, dn, st));
+        const int64_t ld = D.cap_d;
+        // Gram-Schmidt of the kept candidates against Q: X_K = Q W_K + V
+        // with V orthogonal to range(Q); then V = Q_new Lam^T (Lam lower
+        // triangular) with Q_new orthonormal.  So R_new = Q_new' L_new^T with
+        // L_new = [[L, 0], [W_K^T, Lam]], a Cholesky factor of R^T R; the
+        // first d_before rows of W_K are kept for the M chain
+        // (M_{t+1} = W_K^T L^(t)^{-1} = ((dR)^T R^(t)) U^(t), formed on request).
+        PhaseScope ph("d_update_u", st);
+        {
+          PhaseScope phq("d_q_basis", st);
+          const int64_t nr = M.n_rows;
+          double *V, *V2, *Vq;
+          CTD_TRY(scratch.get(&V, (size_t)nr * kr));
+          CTD_TRY(scratch.get(&V2, (size_t)nr * kr));
+          CTD_TRY(scratch.get(&Vq, (size_t)nr * kr));
+          CTD_CUDA(cudaMemsetAsync(V, 0, (size_t)nr * kr * 8, st));
+          CTD_LAUNCH(k_densify_cols, ((unsigned)std::min(kr, 4096)), (128), 0, st,
+                     reinterpret_cast<const unsigned long long*>(rptr), rc_row, rc_val, idx, kr,
+                     V, nr);
+          if (dtc > 0) {
+            double* WKs;
+            CTD_TRY(scratch.get(&WKs, (size_t)dtc * kr));
+            const unsigned gk = grid_for(dtc * kr, 256, (int64_t)num_sms() * 8);
+            CTD_LAUNCH(k_gather_cols_f64, (gk), (256), 0, st, W, dtc, dtc, idx, kr, WKs, dtc);
+            dgemm(true, false, nr, kr, dtc, -1.0, F->Qt, ld, WKs, dtc, 1.0, V, nr, st);
+            // the second pass holds the new vectors orthogonal to ~u / rho for
+            // a residual ratio rho >= eps (and adds its coefficients to W_K):
+            // every later decision is taken against this basis
             double* Hm;
-            CTD_TRY(scratch.get(&Hm, (size_t)dt * kept));
-            dgemm(false, false, dt, kept, nr, 1.0, F->Qt, ld, V, nr, 0.0, Hm, dt, st);
-            dgemm(true, false, nr, kept, dt, -1.0, F->Qt, ld, Hm, dt, 1.0, V, nr, st);
-            CTD_LAUNCH(k_axpy_f64, (gk), (256), 0, st, dt * kept, Hm, rec.WK);
+            CTD_TRY(scratch.get(&Hm, (size_t)dtc * kr));
+            dgemm(false, false, dtc, kr, nr, 1.0, F->Qt, ld, V, nr, 0.0, Hm, dtc, st);
+            dgemm(true, false, nr, kr, dtc, -1.0, F->Qt, ld, Hm, dtc, 1.0, V, nr, st);
+            CTD_LAUNCH(k_axpy_f64, (gk), (256), 0, st, dtc * kr, Hm, WKs);
+            CTD_LAUNCH(k_transpose_f64, (gk), (256), 0, st, WKs, dtc, dtc, kr, F->L + dtc, ld);
+            if (dt0 > 0)
+              CTD_CUDA(cudaMemcpy2DAsync(rec.WK + (size_t)kept_total * dt0, (size_t)dt0 * 8, WKs,
+                                         (size_t)dtc * 8, (size_t)dt0 * 8, kr,
+                                         cudaMemcpyDeviceToDevice, st));
           }
-          CTD_LAUNCH(k_transpose_f64, (gk), (256), 0, st, rec.WK, dt, dt, kept, F->L + dt, ld);
+          // V2 = V L_S^{-T} is orthonormal up to the filter's rounding; one
+          // Cholesky-QR pass makes it so to working precision.  If that pass
+          // meets a non-positive pivot (V2 too far from orthonormal), the
+          // residuals are orthonormalized from scratch: unit columns, one
+          // shifted Cholesky-QR pass, then two plain ones (Fukaya et al.,
+          // SIAM J. Sci. Comput. 42(1), 2020).
+          dgemm(false, true, nr, kr, kr, 1.0, V, nr, Li, ldli, 0.0, V2, nr, st);
+          bool ok = false;
+          CTD_TRY(cholqr_pass(V2, nr, kr, 0.0, Vq, scratch, st, &ok));
+          if (!ok) {
+            double* V0;  // the residuals themselves, for Lam below
+            CTD_TRY(scratch.get(&V0, (size_t)nr * kr));
+            CTD_CUDA(cudaMemcpyAsync(V0, V, (size_t)nr * kr * 8, cudaMemcpyDeviceToDevice, st));
+            CTD_LAUNCH(k_unit_columns, ((unsigned)std::min(kr, 4096)), (256), 0, st, V, nr, kr);
+            const double u = 1.1102230246251565e-16;
+            const double shift = 11.0 * ((double)nr * kr + (double)kr * (kr + 1)) * u * kr;
+            CTD_TRY(cholqr_pass(V, nr, kr, shift, V2, scratch, st, &ok));
+            if (ok) CTD_TRY(cholqr_pass(V2, nr, kr, 0.0, V, scratch, st, &ok));
+            if (ok) CTD_TRY(cholqr_pass(V, nr, kr, 0.0, Vq, scratch, st, &ok));
+            if (!ok) return fail(CTD_ENOTSUP, "new basis vectors are numerically dependent");
+            V = V0;
+          }
+          // Lam^T = Q_new^T V (upper triangular up to rounding): its lower
+          // transpose is L's new diagonal block
+          double* Lam;
+          CTD_TRY(scratch.get(&Lam, (size_t)kr * kr));
+          dgemm(true, false, kr, kr, nr, 1.0, Vq, nr, V, nr, 0.0, Lam, kr, st);
+          CTD_LAUNCH(k_lower_from_upper_T,
+                     (grid_for((int64_t)kr * kr, 256, (int64_t)num_sms() * 4)), (256), 0, st, Lam,
+                     kr, kr, F->L + dtc + dtc * ld, ld);
+          CTD_LAUNCH(k_transpose_f64, (grid_for(nr * kr, 256, (int64_t)num_sms() * 8)), (256), 0,
+                     st, Vq, nr, nr, kr, F->Qt + dtc, ld);
+          CTD_LAUNCH(k_qn_add, (grid_for(nr, 256, (int64_t)num_sms() * 4)), (256), 0, st, F->Qt,
+                     ld, dtc, kr, nr, F->qn);
         }
-        // V2 = V L_S^{-T} is orthonormal up to the filter's rounding; one
-        // Cholesky-QR pass makes it so to working precision.  If that pass
-        // meets a non-positive pivot (V2 too far from orthonormal), the
-        // residuals are orthonormalized from scratch: unit columns, one
-        // shifted Cholesky-QR pass, then two plain ones (Fukaya et al.,
-        // SIAM J. Sci. Comput. 42(1), 2020).
-        dgemm(false, true, nr, kept, kept, 1.0, V, nr, Li, kept, 0.0, V2, nr, st);
-        bool ok = false;
-        CTD_TRY(cholqr_pass(V2, nr, kept, 0.0, Vq, scratch, st, &ok));
-        if (!ok) {
-          double* V0;  // the residuals themselves, for Lam below
-          CTD_TRY(scratch.get(&V0, (size_t)nr * kept));
-          CTD_CUDA(cudaMemcpyAsync(V0, V, (size_t)nr * kept * 8, cudaMemcpyDeviceToDevice, st));
-          CTD_LAUNCH(k_unit_columns, ((unsigned)std::min(kept, 4096)), (256), 0, st, V, nr, kept);
-          const double u = 1.1102230246251565e-16;
-          const double shift = 11.0 * ((double)nr * kept + (double)kept * (kept + 1)) * u * kept;
-          CTD_TRY(cholqr_pass(V, nr, kept, shift, V2, scratch, st, &ok));
-          if (ok) CTD_TRY(cholqr_pass(V2, nr, kept, 0.0, V, scratch, st, &ok));
-          if (ok) CTD_TRY(cholqr_pass(V, nr, kept, 0.0, Vq, scratch, st, &ok));
-          if (!ok) return fail(CTD_ENOTSUP, "new basis vectors are numerically dependent");
-          V = V0;
+        // append the kept columns to R (CSC)
+        int64_t* newf;
+        uint64_t *nsz, *nptr;
+        CTD_TRY(scratch.get(&newf, kr));
+        CTD_TRY(scratch.get(&nsz, kr + 1));
+        CTD_TRY(scratch.get(&nptr, kr + 1));
+        launch_gather_i64(D.lastIu + start, idx, d_kr, kr, newf, st);
+        // the new columns come from the candidates' (row-sorted) CSC, by kept
+        // position, so R's columns keep a reproducible row order
+        int64_t* kp64;
+        CTD_TRY(scratch.get(&kp64, kr));
+        CTD_LAUNCH(k_i32_to_i64, (grid_for(kr, 256, 64)), (256), 0, st, idx, kr, kp64);
+        launch_column_sizes(rptr, kp64, d_kr, kr, nsz, st);
+        launch_scan_u64(nsz, nptr, kr, false, M.tmp, M.status, st);
+        uint64_t nnz_new = 0;
+        std::vector<int64_t> hf(kr);
+        CTD_TRY(d2h(&nnz_new, nptr + kr, 1, st));
+        CTD_TRY(d2h(hf.data(), newf, kr, st));
+        CTD_TRY(sync(st));
+        const int64_t nnzR = F->nnz_R;
+        int64_t cap_cols = D.cap_cols + 1;
+        CTD_TRY(grow_array(&F->Rcolptr, dtc + 1, dn + 1, &cap_cols, st));
+        D.cap_cols = cap_cols - 1;
+        int64_t cap_nnz_r = D.cap_nnz, cap_nnz_v = D.cap_nnz;
+        CTD_TRY(grow_array(&F->Rrow, nnzR, nnzR + (int64_t)nnz_new, &cap_nnz_r, st));
+        CTD_TRY(grow_array(&F->Rval, nnzR, nnzR + (int64_t)nnz_new, &cap_nnz_v, st));
+        D.cap_nnz = cap_nnz_r;
+        launch_gather_columns(rptr, rc_row, rc_val, kp64, d_kr, kr, nptr, F->Rrow + nnzR,
+                              F->Rval + nnzR, st);
+        CTD_LAUNCH(k_add_offset, (grid_for(kr + 1, 256, 64)), (256), 0, st,
+                   reinterpret_cast<const unsigned long long*>(nptr), kr + 1,
+                   (unsigned long long)nnzR,
+                   reinterpret_cast<unsigned long long*>(F->Rcolptr + dtc));
+        // the fiber ids on the device too (the detector of Section 5 reads them)
+        CTD_TRY(grow_array(&F->fibers, dtc, dn, &D.cap_fib, st));
+        CTD_CUDA(cudaMemcpyAsync(F->fibers + dtc, newf, (size_t)kr * sizeof(int64_t),
+                                 cudaMemcpyDeviceToDevice, st));
+        F->nnz_R = nnzR + (int64_t)nnz_new;
+        F->s_kept = dn;
+        for (int q = 0; q < kr; ++q) {
+          D.fiber_id.push_back(hf[q]);
+          D.fiber_step.push_back(D.t);
         }
-        // Lam^T = Q_new^T V (upper triangular up to rounding): its lower
-        // transpose is L^(t+1)'s diagonal block
-        double* Lam;
-        CTD_TRY(scratch.get(&Lam, (size_t)kept * kept));
-        dgemm(true, false, kept, kept, nr, 1.0, Vq, nr, V, nr, 0.0, Lam, kept, st);
-        CTD_LAUNCH(k_lower_from_upper_T, (grid_for((int64_t)kept * kept, 256, (int64_t)num_sms() * 4)),
-                   (256), 0, st, Lam, kept, kept, F->L + dt + dt * ld, ld);
-        CTD_LAUNCH(k_transpose_f64, (grid_for(nr * kept, 256, (int64_t)num_sms() * 8)), (256), 0,
-                   st, Vq, nr, nr, kept, F->Qt + dt, ld);
-        CTD_LAUNCH(k_qn_add, (grid_for(nr, 256, (int64_t)num_sms() * 4)), (256), 0, st, F->Qt, ld,
-                   dt, kept, nr, F->qn);
+        kept_total += kr;
       }
-      // append dR to R (CSC), then rebuild the by-row copy
-      int64_t* newf;
-      uint64_t *nsz, *nptr;
-      CTD_TRY(scratch.get(&newf, kept));
-      CTD_TRY(scratch.get(&nsz, kept + 1));
-      CTD_TRY(scratch.get(&nptr, kept + 1));
-      launch_gather_i64(D.lastIu, idx, fo.count, kept, newf, st);
-      // the new columns come from the candidates' (row-sorted) CSC, by kept
-      // position, so R's columns keep a reproducible row order
-      int64_t* kp64;
-      CTD_TRY(scratch.get(&kp64, kept));
-      CTD_LAUNCH(k_i32_to_i64, (grid_for(kept, 256, 64)), (256), 0, st, idx, kept, kp64);
-      launch_column_sizes(rc_ptr_k, kp64, fo.count, kept, nsz, st);
-      launch_scan_u64(nsz, nptr, kept, false, M.tmp, M.status, st);
-      uint64_t nnz_new = 0;
-      std::vector<int64_t> hf(kept);
-      CTD_TRY(d2h(&nnz_new, nptr + kept, 1, st));
-      CTD_TRY(d2h(hf.data(), newf, kept, st));
-      CTD_TRY(sync(st));
-      const int64_t nnzR = F->nnz_R;
-      int64_t cap_cols = D.cap_cols + 1;
-      CTD_TRY(grow_array(&F->Rcolptr, dt + 1, dn + 1, &cap_cols, st));
-      D.cap_cols = cap_cols - 1;
-      int64_t cap_nnz_r = D.cap_nnz, cap_nnz_v = D.cap_nnz;
-      CTD_TRY(grow_array(&F->Rrow, nnzR, nnzR + (int64_t)nnz_new, &cap_nnz_r, st));
-      CTD_TRY(grow_array(&F->Rval, nnzR, nnzR + (int64_t)nnz_new, &cap_nnz_v, st));
-      D.cap_nnz = cap_nnz_r;
-      launch_gather_columns(rc_ptr_k, rc_row_k, rc_val_k, kp64, fo.count, kept, nptr,
-                            F->Rrow + nnzR, F->Rval + nnzR, st);
-      CTD_LAUNCH(k_add_offset, (grid_for(kept + 1, 256, 64)), (256), 0, st,
-                 reinterpret_cast<const unsigned long long*>(nptr), kept + 1,
-                 (unsigned long long)nnzR,
-                 reinterpret_cast<unsigned long long*>(F->Rcolptr + dt));
-      F->nnz_R = nnzR + (int64_t)nnz_new;
-      F->s_kept = dn;
-      for (int q = 0; q < kept; ++q) {
-        D.fiber_id.push_back(hf[q]);
-        D.fiber_step.push_back(D.t);
-      }
+      start = next;
+    }
+    if (kept_total > 0) {
+      // R by row (rows sorted by column), for the C fill
       dfree(F->Rrowptr, st);
       dfree(F->Rcol, st);
       dfree(F->Rcval, st);
       CTD_TRY(dalloc_n(&F->Rrowptr, M.n_rows + 1, st));
       CTD_TRY(dalloc_n(&F->Rcol, std::max<int64_t>(F->nnz_R, 1), st));
       CTD_TRY(dalloc_n(&F->Rcval, std::max<int64_t>(F->nnz_R, 1), st));
-      CTD_TRY(build_csr_from_csc(F->Rcolptr, F->Rrow, F->Rval, dn, F->nnz_R, M.n_rows, 0,
+      CTD_TRY(build_csr_from_csc(F->Rcolptr, F->Rrow, F->Rval, F->s_kept, F->nnz_R, M.n_rows, 0,
                                  F->Rrowptr, F->Rcol, F->Rcval, scratch, st));
     }
   }
+  rec.d_kept = kept_total;
 
   // lines 17-21: the new columns R^(t+1)^T dX (exact), and the error increment
   const int64_t dn = F->s_kept;

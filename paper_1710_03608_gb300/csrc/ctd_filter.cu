@@ -10,15 +10,17 @@
 // reach of that error for fibers that depend on an ill-conditioned R.  So
 // every candidate whose pivot is below 1e-4 ||x_k||^2 (residual ratio below
 // 1e-2; independent fibers mostly sit far above) is re-tested the way the
-// loop states it: its coefficients gamma are solved through the factor, the
-// residual vector x_k - [R^(t), kept candidates before k] gamma is formed
-// explicitly; when some ratio is within a factor 4 of eps (or disagrees
-// with the factorization), one step of iterative refinement (the normal
-// equations solved again for that residual) removes most of the error the
-// factor's conditioning left in gamma.  The ratio ||res|| / ||x_k|| then has
-// an error far below eps even for kappa(R^T R) ~ 1e11.  If that test disagrees with
-// the pivot, the first disagreeing candidate's decision is fixed and the
-// factorization is redone.
+// loop states it: the residual vector x_k - [R^(t), kept candidates before
+// k] gamma is formed explicitly.  Against R^(t) (CTD-D) it is taken through
+// the orthonormal basis Q of range(R^(t)) that the dynamic state keeps, so
+// its accuracy does not depend on kappa(R^T R): near full row rank that
+// condition number is huge, and coefficients on R itself (solved through
+// the Cholesky factor of R^T R) lose every digit.  When some ratio is
+// within a factor 4 of eps (or disagrees with the factorization), one step
+// of iterative refinement (the least-squares correction for the residual,
+// again through Q and the candidates' factor) removes most of the error
+// left in gamma.  If that test disagrees with the pivot, the first
+// disagreeing candidate's decision is fixed and the factorization is redone.
 #include <algorithm>
 #include <vector>
 
@@ -55,18 +57,16 @@ __global__ void k_gather_cols(const double* __restrict__ A, int64_t lda, int64_t
   }
 }
 
-// The explicit residual of each suspect c, r_c = x_k - R^(t) gammaR_c -
-// Xc[:, K] eta_c, row by row from the by-row layouts (row i of R^(t) and of
+// The candidate part of the explicit residual of each suspect c,
+// r_c = x_k - Xc[:, K] eta_c, row by row from the by-row layout (row i of
 // the candidates, in column order): a fixed order of operations, so the
 // ratio, and every decision and pivot taken from it, is reproducible.  With
-// init = 0 the rows are subtracted from the residual already in rbuf (the
-// refinement step).  kpos maps a candidate to its kept position (-1 if not
-// kept); eta is zero for kept candidates after k_c.
+// init = 0 the products are subtracted from the residual already in rbuf
+// (the refinement step).  kpos maps a candidate to its kept position (-1 if
+// not kept); eta is zero for kept candidates after k_c.  The R^(t) part,
+// Q gamma_c, is subtracted afterwards by a GEMM.
 __global__ void k_resid_rows(int64_t n_rows, const unsigned long long* __restrict__ crp,
                              const int32_t* __restrict__ ccol, const int32_t* __restrict__ cval,
-                             const unsigned long long* __restrict__ rrp,
-                             const int32_t* __restrict__ rcol, const int32_t* __restrict__ rval,
-                             int64_t dt, const double* __restrict__ gammaR,
                              const int* __restrict__ kpos, int kept,
                              const double* __restrict__ eta, const int* __restrict__ sus,
                              int init, double* __restrict__ rbuf) {
@@ -84,9 +84,6 @@ __global__ void k_resid_rows(int64_t n_rows, const unsigned long long* __restric
       const int q = kept > 0 ? kpos[cc] : -1;
       if (q >= 0) acc = fma(-eta[q + (int64_t)c * kept], v, acc);
     }
-    if (dt > 0)
-      for (unsigned long long p = rrp[i]; p < rrp[i + 1]; ++p)
-        acc = fma(-gammaR[rcol[p] + (int64_t)c * dt], (double)rval[p], acc);
     r[i] = init ? xk + acc : acc;
   }
 }
@@ -115,45 +112,30 @@ __global__ void k_resid_norm(int64_t n_rows, const int* __restrict__ sus,
   }
 }
 
-// h_R(j, c) = R^(t)(:, j) . r_c ; h_K(p, c) = x_{K[p]} . r_c for K[p] < k_c (else 0);
-// a warp per column, grid (suspect, slice of columns)
-__global__ void k_residual_dots(int64_t n_rows, const unsigned long long* __restrict__ cptr,
+// h_K(p, c) = x_{K[p]} . r_c for K[p] < k_c (else 0); a warp per kept
+// column, grid (suspect, slice of columns)
+__global__ void k_residual_dots(const unsigned long long* __restrict__ cptr,
                                 const int32_t* __restrict__ crow, const int32_t* __restrict__ cval,
-                                int64_t dt, const unsigned long long* __restrict__ rptr,
-                                const int32_t* __restrict__ rrow, const int32_t* __restrict__ rval,
                                 const int* __restrict__ kept_idx, int kept,
-                                const int* __restrict__ sus, const double* __restrict__ rbuf,
-                                double* __restrict__ hR, double* __restrict__ hK) {
+                                const int* __restrict__ sus, int64_t n_rows,
+                                const double* __restrict__ rbuf, double* __restrict__ hK) {
   const int c = blockIdx.x;
   const int k = sus[c];
   const int lane = threadIdx.x & 31;
   const int64_t gw = (int64_t)blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t nw = (int64_t)gridDim.y * (blockDim.x >> 5);
   const double* r = rbuf + (int64_t)c * n_rows;
-  for (int64_t j = gw; j < dt + kept; j += nw) {
+  for (int64_t j = gw; j < kept; j += nw) {
     unsigned long long a = 0, b = 0;
-    const int32_t *row = crow, *val = cval;
-    if (j < dt) {
-      a = rptr[j];
-      b = rptr[j + 1];
-      row = rrow;
-      val = rval;
-    } else {
-      const int col = kept_idx[j - dt];
-      if (col < k) {
-        a = cptr[col];
-        b = cptr[col + 1];
-      }
+    const int col = kept_idx[j];
+    if (col < k) {
+      a = cptr[col];
+      b = cptr[col + 1];
     }
     double s = 0.0;
-    for (unsigned long long q = a + lane; q < b; q += 32) s = fma((double)val[q], r[row[q]], s);
+    for (unsigned long long q = a + lane; q < b; q += 32) s = fma((double)cval[q], r[crow[q]], s);
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-      if (j < dt)
-        hR[j + (int64_t)c * dt] = s;
-      else
-        hK[(j - dt) + (int64_t)c * kept] = s;
-    }
+    if (lane == 0) hK[j + (int64_t)c * kept] = s;
   }
 }
 
@@ -240,13 +222,18 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
     std::vector<int> sus;
     for (int k = 0; k < du; ++k)
       if (h_xn[k] > 0.0 && h_piv[k] < SUSPECT * h_xn[k]) sus.push_back(k);
-    if (sus.empty()) return CTD_OK;
+    if (sus.empty()) {
+      out.keep_h = h_keep;
+      out.piv_h = h_piv;
+      out.xn_h = h_xn;
+      return CTD_OK;
+    }
     // explicit residuals of the suspects
     PhaseScope ph("filter_recheck", st);
     const int ns = (int)sus.size();
     const int kk = std::max(kept, 1);
     int* d_sus;
-    double *Stil, *eta, *ratio, *rbuf, *gammaR = nullptr;
+    double *Stil, *eta, *ratio, *rbuf, *gammaQ = nullptr, *WK = nullptr;
     CTD_TRY(scratch.get(&d_sus, ns));
     CTD_TRY(scratch.get(&Stil, (size_t)kk * ns));
     CTD_TRY(scratch.get(&eta, (size_t)kk * ns));
@@ -259,20 +246,19 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
                  du, out.idx, kept, d_sus, ns, Stil);
       dgemm(true, false, kept, ns, kept, 1.0, out.Li, kept, Stil, kept, 0.0, eta, kept, st);
     }
+    // coefficients on Q: gamma_c = Q^T (x_k - Xc[:, K] eta_c) = W_k - W_K eta_c
     if (in.dt > 0) {
-      CTD_TRY(scratch.get(&gammaR, (size_t)in.dt * ns));
+      CTD_TRY(scratch.get(&gammaQ, (size_t)in.dt * ns));
       CTD_LAUNCH(k_gather_cols, (grid_for(in.dt * ns, 256, (int64_t)num_sms() * 8)), (256), 0, st,
-                 in.W, in.dt, in.dt, d_sus, ns, gammaR, in.dt);
+                 in.W, in.dt, in.dt, d_sus, ns, gammaQ, in.dt);
       if (kept > 0) {
-        double* WK;
         CTD_TRY(scratch.get(&WK, (size_t)in.dt * kept));
         CTD_LAUNCH(k_gather_cols, (grid_for(in.dt * kept, 256, (int64_t)num_sms() * 8)), (256), 0,
                    st, in.W, in.dt, in.dt, out.idx, kept, WK, in.dt);
-        dgemm(false, false, in.dt, ns, kept, -1.0, WK, in.dt, eta, kept, 1.0, gammaR, in.dt, st);
+        dgemm(false, false, in.dt, ns, kept, -1.0, WK, in.dt, eta, kept, 1.0, gammaQ, in.dt, st);
       }
-      tri_solve_lower_T(in.Lt, in.ldl, in.dt, gammaR, in.dt, ns, st);
     }
-    const unsigned ny = slices_for(in.dt + kept, ns);
+    const unsigned ny = slices_for(kept, ns);
     int* kpos;
     CTD_TRY(scratch.get(&kpos, du));
     CTD_CUDA(cudaMemsetAsync(kpos, 0xff, (size_t)du * sizeof(int), st));  // -1
@@ -281,15 +267,18 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
     const dim3 grows(grid_for(in.n_rows, 256, std::max<int64_t>(1, (int64_t)num_sms() * 4 / ns)),
                      ns);
     CTD_LAUNCH(k_resid_rows, (grows), (256), 0, st, in.n_rows,
-               reinterpret_cast<const unsigned long long*>(in.c_rowptr), in.c_col, in.c_val,
-               reinterpret_cast<const unsigned long long*>(in.r_rowptr), in.r_col, in.r_val,
-               in.dt, gammaR, kpos, kept, eta, d_sus, 1, rbuf);
+               reinterpret_cast<const unsigned long long*>(in.c_rowptr), in.c_col, in.c_val, kpos,
+               kept, eta, d_sus, 1, rbuf);
+    // minus Q gamma (Q = Qt^T, n_rows x dt)
+    if (in.dt > 0)
+      dgemm(true, false, in.n_rows, ns, in.dt, -1.0, in.Qt, in.ldq, gammaQ, in.dt, 1.0, rbuf,
+            in.n_rows, st);
     CTD_LAUNCH(k_resid_norm, (ns), (256), 0, st, in.n_rows, d_sus, xn2, rbuf, ratio);
-    // one step of iterative refinement: solve the normal equations again for
-    // the residual's remaining component in range([R^(t), kept before k]).
-    // Its correction to a ratio is of order u * kappa(R); it is taken only
-    // when some ratio lies within a factor 4 of eps or disagrees with the
-    // factorization's decision (otherwise no decision can change).
+    // one step of iterative refinement: the least-squares correction of the
+    // residual against [Q, kept before k].  Its change to a ratio is of the
+    // order of the rounding left in gamma; it is taken only when some ratio
+    // lies within a factor 4 of eps or disagrees with the factorization's
+    // decision (otherwise no decision can change).
     std::vector<double> h_ratio(ns);
     CTD_TRY(d2h(h_ratio.data(), ratio, ns, st));
     CTD_CUDA(cudaGetLastError());
@@ -301,24 +290,22 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
       refine = (r >= 0.25 * in.eps && r <= 4.0 * in.eps) || explicit_keep != h_keep[sus[c]];
     }
     if (refine) {
-      double *hR = nullptr, *hK, *zK, *etad;
+      double *hQ = nullptr, *hK, *zK, *etad;
       CTD_TRY(scratch.get(&hK, (size_t)kk * ns));
       CTD_TRY(scratch.get(&zK, (size_t)kk * ns));
       CTD_TRY(scratch.get(&etad, (size_t)kk * ns));
-      if (in.dt > 0) CTD_TRY(scratch.get(&hR, (size_t)in.dt * ns));
-      CTD_LAUNCH(k_residual_dots, (dim3(ns, ny)), (256), 0, st, in.n_rows,
-                 reinterpret_cast<const unsigned long long*>(in.cptr), in.crow, in.cval, in.dt,
-                 reinterpret_cast<const unsigned long long*>(in.rptr), in.rrow, in.rval, out.idx,
-                 kept, d_sus, rbuf, hR, hK);
-      double* WK = nullptr;
+      if (kept > 0)
+        CTD_LAUNCH(k_residual_dots, (dim3(ns, ny)), (256), 0, st,
+                   reinterpret_cast<const unsigned long long*>(in.cptr), in.crow, in.cval, out.idx,
+                   kept, d_sus, in.n_rows, rbuf, hK);
       if (in.dt > 0) {
-        tri_solve_lower(in.Lt, in.ldl, in.dt, hR, in.dt, ns, st);  // z_R
-        if (kept > 0) {
-          CTD_TRY(scratch.get(&WK, (size_t)in.dt * kept));
-          CTD_LAUNCH(k_gather_cols, (grid_for(in.dt * kept, 256, (int64_t)num_sms() * 8)), (256),
-                     0, st, in.W, in.dt, in.dt, out.idx, kept, WK, in.dt);
-          dgemm(true, false, kept, ns, in.dt, -1.0, WK, in.dt, hR, in.dt, 1.0, hK, kept, st);
-        }
+        // h_Q = Q^T r; the candidates' part of the correction sees the
+        // residual projected off Q: h_K - W_K^T h_Q
+        CTD_TRY(scratch.get(&hQ, (size_t)in.dt * ns));
+        dgemm(false, false, in.dt, ns, in.n_rows, 1.0, in.Qt, in.ldq, rbuf, in.n_rows, 0.0, hQ,
+              in.dt, st);
+        if (kept > 0)
+          dgemm(true, false, kept, ns, in.dt, -1.0, WK, in.dt, hQ, in.dt, 1.0, hK, kept, st);
       }
       CTD_CUDA(cudaMemsetAsync(etad, 0, (size_t)kk * ns * 8, st));
       if (kept > 0) {
@@ -328,15 +315,16 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
         CTD_LAUNCH(k_mask_before, (gm), (256), 0, st, zK, kept, out.idx, d_sus, ns);
         dgemm(true, false, kept, ns, kept, 1.0, out.Li, kept, zK, kept, 0.0, etad, kept, st);
       }
-      if (in.dt > 0) {
-        if (kept > 0)
-          dgemm(false, false, in.dt, ns, kept, -1.0, WK, in.dt, etad, kept, 1.0, hR, in.dt, st);
-        tri_solve_lower_T(in.Lt, in.ldl, in.dt, hR, in.dt, ns, st);  // delta gamma_R
-      }
+      // r -= Xc[:, K] eta_d, then r -= Q (h_Q - W_K eta_d)
       CTD_LAUNCH(k_resid_rows, (grows), (256), 0, st, in.n_rows,
                  reinterpret_cast<const unsigned long long*>(in.c_rowptr), in.c_col, in.c_val,
-                 reinterpret_cast<const unsigned long long*>(in.r_rowptr), in.r_col, in.r_val,
-                 in.dt, hR, kpos, kept, etad, d_sus, 0, rbuf);
+                 kpos, kept, etad, d_sus, 0, rbuf);
+      if (in.dt > 0) {
+        if (kept > 0)
+          dgemm(false, false, in.dt, ns, kept, -1.0, WK, in.dt, etad, kept, 1.0, hQ, in.dt, st);
+        dgemm(true, false, in.n_rows, ns, in.dt, -1.0, in.Qt, in.ldq, hQ, in.dt, 1.0, rbuf,
+              in.n_rows, st);
+      }
       CTD_LAUNCH(k_resid_norm, (ns), (256), 0, st, in.n_rows, d_sus, xn2, rbuf, ratio);
       CTD_TRY(d2h(h_ratio.data(), ratio, ns, st));
       CTD_CUDA(cudaGetLastError());
@@ -353,7 +341,12 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
       }
     }
     if (out.ratios) out.ratios->assign(h_ratio.begin(), h_ratio.end());
-    if (!changed) return CTD_OK;
+    if (!changed) {
+      out.keep_h = h_keep;
+      out.piv_h = h_piv;
+      out.xn_h = h_xn;
+      return CTD_OK;
+    }
   }
   return fail(CTD_ENOTSUP, "independence filter did not settle");
 }

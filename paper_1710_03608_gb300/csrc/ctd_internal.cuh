@@ -375,21 +375,17 @@ struct FilterIn {
   const uint64_t* cptr = nullptr;
   const int32_t* crow = nullptr;
   const int32_t* cval = nullptr;
+  // CTD-D: the candidates are tested against range(R^(t)) through its
+  // orthonormal basis Q (n_rows x dt; Q(i, j) at Qt[j + i * ldq]) and
+  // W = Q^T X_c (dt x du)
   int64_t dt = 0;
-  const double* Lt = nullptr;
-  int64_t ldl = 0;
+  const double* Qt = nullptr;
+  int64_t ldq = 0;
   const double* W = nullptr;
-  const uint64_t* rptr = nullptr;
-  const int32_t* rrow = nullptr;
-  const int32_t* rval = nullptr;
-  // the same two matrices by row (rows sorted by column), for the explicit
-  // residuals: candidates (n_rows x du) and R^(t) (n_rows x dt)
+  // the candidates by row (rows sorted by column), for the explicit residuals
   const uint64_t* c_rowptr = nullptr;
   const int32_t* c_col = nullptr;
   const int32_t* c_val = nullptr;
-  const uint64_t* r_rowptr = nullptr;
-  const int32_t* r_col = nullptr;
-  const int32_t* r_val = nullptr;
   int64_t n_rows = 0;
 };
 // keep[du], idx[kept] (device), count (device, = kept), Lk = factor of the
@@ -402,6 +398,10 @@ struct FilterOut {
   double* Lk = nullptr;
   double* Li = nullptr;
   std::vector<double>* ratios = nullptr;
+  // host copies of the final decisions: keep flag, pivot (the squared
+  // residual the factorization used) and ||x||^2 per candidate
+  std::vector<int> keep_h;
+  std::vector<double> piv_h, xn_h;
 };
 ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaStream_t st);
 

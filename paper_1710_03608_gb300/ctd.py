@@ -31,7 +31,8 @@ EXPORTED = ["ctd_static", "ctd_dynamic_create", "ctd_dynamic_step", "ctd_error",
             "ctd_get_samples", "ctd_get_fibers", "ctd_get_R", "ctd_get_U", "ctd_get_C_columns",
             "ctd_get_C", "ctd_get_step", "ctd_get_M", "ctd_free", "ctd_last_error",
             "ctd_version", "ctd_profile", "ctd_profile_report", "ctd_sample_noalloc", "ctd_static_batched", "ctd_server_create", "ctd_server_submit",
-            "ctd_server_wait", "ctd_server_result", "ctd_server_state", "ctd_server_free"]
+            "ctd_server_wait", "ctd_server_result", "ctd_server_state", "ctd_server_free",
+            "ctd_ddos_candidates"]
 
 
 class CtdError(RuntimeError):
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ctd_server_state": [P, I32, C.POINTER(P)],
         "ctd_sample_noalloc": [C.POINTER(ctd_coo3), I32, I64, U64, P, P, C.POINTER(C.c_int), P],
         "ctd_profile_report": [C.c_char_p, C.c_size_t],
+        "ctd_ddos_candidates": [P, I64, P, C.POINTER(C.c_int64), C.POINTER(D)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -250,6 +252,15 @@ class Factors:
         m = np.empty((info[1], info[2]), np.float64)
         _check(load().ctd_get_M(self.h, int(t), _ptr(m)))
         return m
+
+    def ddos_candidates(self):
+        """Section 5's detector on R (alpha = 1): the candidate destinations
+        ascending, and the average representative norm."""
+        cap = int(self.sizes().s_kept)  # at most one candidate per kept fiber
+        n, mean = C.c_int64(0), C.c_double(0.0)
+        out = np.empty(max(cap, 1), np.int64)
+        _check(load().ctd_ddos_candidates(self.h, cap, _ptr(out), C.byref(n), C.byref(mean)))
+        return out[:n.value], mean.value
 
 
 def ctd_static(X: Coo, alpha: int, s: int, eps: float, seed: int = 0,

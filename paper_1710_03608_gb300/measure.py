@@ -196,6 +196,51 @@ def stream(args):
     print(json.dumps(line), flush=True)
 
 
+def ddos(args):
+    """Section 5's detector on the C3-shaped stream with its planted block
+    (200 sources x 50 destinations of Poisson(40) counts at steps 40-45, the
+    block scaled with the slice): CTD-D with the paper's detector setting
+    (d = 10, eps = 0.15), the detector run after every step, scored against
+    the planted destinations."""
+    st = synth.traffic_stream_20k(scale=args.scale, steps=args.steps)
+    G = ctd.Dynamic(st.dims2, 1, ctd.CTD_FP32_BULK, 0, 0, ctd.CTD_KEEP_LAST_C)
+    truth = set(int(x) for x in st.planted_dst)
+    ctd.profile(True)
+    step_s, det_s, tot_nnz = 0.0, [], 0
+    trace = []
+    for t in range(args.steps):
+        sl = st.slice(t)
+        X = ctd.Coo.from_synth(sl)
+        _sync()
+        t0 = time.perf_counter()
+        G.step_slice(X, args.d, args.eps)
+        _sync()
+        t1 = time.perf_counter()
+        cand, mean = G.ddos_candidates()
+        t2 = time.perf_counter()
+        step_s += t1 - t0
+        det_s.append(t2 - t1)
+        tot_nnz += sl.nnz
+        hit = len(truth & set(int(x) for x in cand))
+        trace.append({"t": t, "candidates": int(cand.size), "planted_found": hit,
+                      "kept": int(G.sizes().s_kept)})
+    cand_set = set(int(x) for x in cand)
+    tp = len(truth & cand_set)
+    rec = tp / len(truth) if truth else 0.0
+    prec = tp / len(cand_set) if cand_set else 0.0
+    f1 = 2 * prec * rec / (prec + rec) if prec + rec else 0.0
+    line = {"workload": f"CTD-D stream of {args.steps} slices {st.dims2[0]}x{st.dims2[1]}, "
+                        f"{st.nnz} nonzeros each, planted {len(st.planted_src)} x "
+                        f"{len(truth)} block at steps {list(st.planted_steps)}; d = {args.d}, "
+                        f"eps = {args.eps}",
+            "recall": rec, "precision": prec, "f1": f1, "candidates": sorted(cand_set),
+            "planted_dst": sorted(truth), "final_kept": int(G.sizes().s_kept),
+            "step_nnz_per_s": tot_nnz / step_s,
+            "detector_ms": {"median": 1e3 * float(np.median(det_s)), "max": 1e3 * max(det_s)},
+            "phases_ms": ctd.profile_report()["phases"], "trace": trace}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------
 # summaries of ncu output (text in, text out; no GPU)
 # ---------------------------------------------------------------------------
@@ -299,6 +344,11 @@ def main():
     sm.add_argument("--steps", type=int, default=100)
     sm.add_argument("--scale", type=float, default=1.0)
     sm.add_argument("--d", type=int, default=400)
+    dd = sub.add_parser("ddos")
+    dd.add_argument("--steps", type=int, default=48)
+    dd.add_argument("--scale", type=float, default=1.0)
+    dd.add_argument("--d", type=int, default=10)
+    dd.add_argument("--eps", type=float, default=0.15)
     args = ap.parse_args()
     if args.cmd == "ncu-summary":
         print(ncu_launch_summary(args.csv, args.top))
@@ -309,7 +359,7 @@ def main():
     import torch
     torch.cuda.set_device(0)
     ctd.load()
-    {"batched": batched, "serving": serving, "stream": stream}[args.cmd](args)
+    {"batched": batched, "serving": serving, "stream": stream, "ddos": ddos}[args.cmd](args)
 
 
 if __name__ == "__main__":
