@@ -143,6 +143,22 @@ Readback::~Readback() {
   // copies still in flight into the chunk must land before it is reused
   if (!items.empty()) cudaStreamSynchronize(st);
   if (chunk) t_pinned.free_chunks.push_back(chunk);
+  if (ev) cudaEventDestroy(ev);
+}
+
+ctd_status Readback::mark() {
+  if (!ev) CTD_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  CTD_CUDA(cudaEventRecord(ev, st));
+  return CTD_OK;
+}
+
+ctd_status Readback::wait_mark() {
+  if (!ev) return wait();
+  CTD_CUDA(cudaEventSynchronize(ev));
+  for (const Item& it : items) std::memcpy(it.host, chunk + it.off, it.bytes);
+  items.clear();
+  used = 0;
+  return CTD_OK;
 }
 
 ctd_status Readback::add_bytes(void* host, const void* dev, size_t bytes) {
@@ -423,7 +439,11 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   CsrDev R{F->Rrowptr, F->Rcol, F->Rcval, kept};
   ph_r.reset();
 
-  // line 16: C = R^T X_(alpha)
+  // line 16: C = R^T X_(alpha), and Eq. (error).  The C capacity is read back
+  // while the error kernels (which do not need C) run, so the GPU does not
+  // idle across that read-back.
+  Readback rbc(st);
+  uint64_t cap = 0, nnzR = 0;
   if (!(flags & CTD_SKIP_C)) {
     uint32_t* ub;
     STEP(scratch.get(&ub, M.n_cols));
@@ -434,14 +454,22 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
       launch_c_bounds(M.csc(), M.n_cols, R, ub, st);
       launch_scan_u32(ub, F->Coff, M.n_cols, false, M.tmp, M.status, st);
     }
-    uint64_t cap = 0, nnzR = 0;
-    {
-      Readback rb(st);
-      STEP(rb.add(&cap, F->Coff + M.n_cols, 1));
-      STEP(rb.add(&nnzR, F->Rcolptr + kept, 1));
-      STEP(rb.wait());
-    }
+    STEP(rbc.add(&cap, F->Coff + M.n_cols, 1));
+    STEP(rbc.add(&nnzR, F->Rcolptr + kept, 1));
+    STEP(rbc.mark());
+  }
+  // Eq. (error): e = (T - ||Q^T X||_F^2) / T with Q = R L^{-T}
+  double* d_pu = nullptr;
+  if (!(flags & CTD_SKIP_ERROR) && kept > 0) {
+    STEP(scratch.get(&d_pu, 1));
+    PhaseScope ph("error_qform", st);
+    STEP(launch_error_qform(M.csc(), M.n_cols, M.n_rows, M.nnz, R, Z, kept, M.rowcnt,
+                            precision == CTD_FP32_BULK, d_pu, scratch, st));
+  }
+  if (!(flags & CTD_SKIP_C)) {
+    STEP(rbc.wait_mark());
     F->nnz_R = (int64_t)nnzR;
+    R.nnz = F->nnz_R;
     F->C_cap = cap;
     STEP(F->mem.get(&F->Crow, cap));
     const size_t vsz = precision == CTD_FP32_BULK ? 4 : 8;
@@ -452,15 +480,6 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
     PhaseScope ph("c_fill", st);
     STEP(launch_c_fill(M.csc(), M.n_cols, M.n_rows, M.nnz, R, F->Coff, F->Ccnt, F->Crow, F->Cval,
                        precision == CTD_FP32_BULK, minval > 0, T, st));
-  }
-
-  // Eq. (error): e = (T - ||Q^T X||_F^2) / T with Q = R L^{-T}
-  double* d_pu = nullptr;
-  if (!(flags & CTD_SKIP_ERROR) && kept > 0) {
-    STEP(scratch.get(&d_pu, 1));
-    PhaseScope ph("error_qform", st);
-    STEP(launch_error_qform(M.csc(), M.n_cols, M.n_rows, M.nnz, R, Z, kept, M.rowcnt,
-                            precision == CTD_FP32_BULK, d_pu, scratch, st));
   }
   uint64_t* d_nnzc;
   STEP(scratch.get(&d_nnzc, 1));

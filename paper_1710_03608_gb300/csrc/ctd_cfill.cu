@@ -8,10 +8,13 @@
 // H longest rows live densely in shared memory (int32, padded to NQ * 128
 // columns), and lane l of a warp owns output rows m = 128 q + 4 l + {0..3}
 // in registers: one dense row adds into them with NQ 128-bit shared loads
-// and 4 NQ integer multiply-adds, no atomics.  The other rows go through the
-// sparse walk into a per-warp shared accumulator as before, and the emission
-// adds the two, compacts the nonzeros of each 128-row slab with a warp scan
-// and writes them in ascending row order.
+// and 4 NQ integer multiply-adds, no atomics.  The other rows go through a
+// sparse walk into a per-warp shared accumulator, and the emission adds the
+// two, compacts the nonzeros of each 128-row slab (ballots) through shared
+// memory and writes them in ascending row order, consecutive lanes on
+// consecutive entries.  A column with one nonzero v at row
+// i is v R(i, :): those are copied from images of R's rows laid out so that
+// every copy moves aligned 8- and 16-byte vectors (k_img_fill, k_copy_flat).
 //
 // Exactness: every partial sum is an integer of magnitude at most
 // ||x_f|| ||r_m|| <= ||X||_F^2 < 2^31 (Cauchy-Schwarz); this path is taken
@@ -26,8 +29,11 @@ namespace ctd {
 
 namespace {
 
-constexpr int CF_THREADS = 1024;  // one block per SM shares one copy of the dense rows
-constexpr int CF_HEAVY_COL = 128;  // columns with at least this many nonzeros: one block each
+// one 24-warp block per SM shares one copy of the dense rows (24 rather than
+// 32 warps: 80 registers a thread instead of 64, and fewer accumulators
+// leave room for more dense rows; measured faster on the traffic tensor)
+constexpr int CF_THREADS = 768;
+constexpr int CF_HEAVY_COL = 128;  // columns with at least this many nonzeros: taken first
 constexpr int CF_LONG_ROW = 16;    // sparse rows at least this long: walked by the whole warp
 constexpr int CF_LONG_GROUP = 2;   // long sparse rows walked together (loads in flight)
 constexpr int CF_MAX_DENSE = 96;   // dense rows at most (shared memory bounds it first)
@@ -183,24 +189,87 @@ __device__ __forceinline__ void store4<double>(double* p, double a, double b, do
   reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
 }
 
-// C(:, f) = v R(i, :) for the single-nonzero columns.  A warp takes 32 list
-// entries; lane l loads column l's metadata (list entry, X entry, R row
-// range, output offset) so the dependent loads overlap across the 32
-// columns, then the warp copies the rows one after another with four loads
-// in flight per lane before the stores.  No shared memory: 64 warps per SM.
-template <typename V>
-__global__ void __launch_bounds__(256)
-    k_copy_rows(CscDev X, CsrDev R, const int64_t* __restrict__ single,
-                const unsigned* __restrict__ n_single, const unsigned long long* __restrict__ coff,
-                uint16_t* __restrict__ crow, V* __restrict__ cval) {
+// R's rows at four alignments, for the copies: image k (k = 0..3) holds row
+// i at ip[i] + k + e (e = 0..len-1) inside a slot of roundup(len + 3, 4)
+// entries that starts at the 4-aligned ip[i], zeros elsewhere, columns as
+// uint16.  An output run starting at o reads image (o mod 4), where every
+// 4-aligned quad of the run lines up with a 4-aligned quad of the image:
+// 8- and 16-byte loads and stores throughout.
+__global__ void k_img_sizes(const unsigned long long* __restrict__ rp, int64_t n_rows,
+                            unsigned long long* __restrict__ sz) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long len = rp[i + 1] - rp[i];
+    sz[i] = len ? ((len + 6ull) & ~3ull) : 0ull;
+  }
+}
+
+__global__ void k_img_fill(CsrDev R, int64_t n_rows, const unsigned long long* __restrict__ ip,
+                           int64_t P, uint16_t* __restrict__ icol, int* __restrict__ ival) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
+  for (int64_t i = gw; i < n_rows; i += nw) {
+    const unsigned long long rs = rp[i];
+    const long long len = (long long)(rp[i + 1] - rs);
+    const unsigned long long b = ip[i], S = ip[i + 1] - b;
+    for (unsigned long long j = lane; j < S; j += 32) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const long long e = (long long)j - k;
+        const bool in = e >= 0 && e < len;
+        icol[(int64_t)k * P + b + j] = in ? (uint16_t)__ldg(R.col + rs + e) : (uint16_t)0;
+        ival[(int64_t)k * P + b + j] = in ? __ldg(R.val + rs + e) : 0;
+      }
+    }
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ void put_quad(uint16_t* crow, V* cval, unsigned long long o, ushort4 c,
+                                         V a, V b, V d, V e);
+template <>
+__device__ __forceinline__ void put_quad<float>(uint16_t* crow, float* cval, unsigned long long o,
+                                                ushort4 c, float a, float b, float d, float e) {
+  *reinterpret_cast<ushort4*>(crow + o) = c;
+  *reinterpret_cast<float4*>(cval + o) = make_float4(a, b, d, e);
+}
+template <>
+__device__ __forceinline__ void put_quad<double>(uint16_t* crow, double* cval, unsigned long long o,
+                                                 ushort4 c, double a, double b, double d, double e) {
+  *reinterpret_cast<ushort4*>(crow + o) = c;
+  reinterpret_cast<double2*>(cval + o)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(cval + o)[1] = make_double2(d, e);
+}
+
+// The copies of a warp's 32 list entries as one flat sequence of image
+// quads: entry e's run is nq_e quads, and lane l owns quads l, l + 32, ...
+// of the concatenated runs (found by a binary search over the lanes'
+// inclusive prefix sums of nq), CP_UNROLL rounds of loads in flight before
+// their stores.  The L2 latency of the image loads is then paid once per
+// 32 * CP_UNROLL quads instead of once or twice per row.
+constexpr int CP_UNROLL = 4;
+
+__device__ __forceinline__ unsigned long long shfl64(unsigned long long x, int src) {
+  return __shfl_sync(0xffffffffu, x, src);
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256)
+    k_copy_flat(CscDev X, const unsigned long long* __restrict__ rp,
+                const unsigned long long* __restrict__ ip, const uint16_t* __restrict__ icol,
+                const int* __restrict__ ival, int64_t P, const int64_t* __restrict__ single,
+                const unsigned* __restrict__ n_single,
+                const unsigned long long* __restrict__ coff, uint16_t* __restrict__ crow,
+                V* __restrict__ cval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(X.colptr);
   const int64_t n = *n_single;
   for (int64_t w0 = gw * 32; w0 < n; w0 += nw * 32) {
-    unsigned long long rs = 0, o = 0;
+    unsigned long long b = 0, o = 0;
     int rl = 0, v = 0;
     if (w0 + lane < n) {
       const int64_t f = single[w0 + lane];
@@ -208,44 +277,62 @@ __global__ void __launch_bounds__(256)
       o = coff[f];
       const int i = __ldg(X.row + xa);
       v = __ldg(X.val + xa);
-      rs = __ldg(rp + i);
-      rl = (int)(__ldg(rp + i + 1) - rs);
+      b = __ldg(ip + i);
+      rl = (int)(__ldg(rp + i + 1) - __ldg(rp + i));
     }
-    const int m = (int)min((int64_t)32, n - w0);
-    for (int e = 0; e < m; ++e) {
-      const unsigned long long rse = __shfl_sync(0xffffffffu, rs, e);
-      const unsigned long long oe = __shfl_sync(0xffffffffu, o, e);
-      const int rle = __shfl_sync(0xffffffffu, rl, e);
-      const int ve = __shfl_sync(0xffffffffu, v, e);
-      // the output run [oe, oe + rle): a scalar head up to a multiple of 4,
-      // then 4 entries per lane per step with one 8-byte row store and one
-      // 16-byte value store (vector stores: the kernel is store-bound), then
-      // a scalar tail
-      const int head = (int)min((unsigned long long)rle, (4ull - (oe & 3ull)) & 3ull);
-      if (lane < head) {
-        crow[oe + lane] = (uint16_t)__ldg(R.col + rse + lane);
-        cval[oe + lane] = (V)(ve * __ldg(R.val + rse + lane));
-      }
-      const unsigned long long ob = oe + head, rb = rse + head;
-      const int nvec = (rle - head) >> 2;
-      for (int t = lane; t < nvec; t += 32) {
-        const unsigned long long r = rb + 4ull * t;
-        int c4[4], v4[4];
+    const int nq = rl > 0 ? ((int)(o & 3ull) + rl + 3) >> 2 : 0;
+    int incl = nq;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          c4[u] = __ldg(R.col + r + u);
-          v4[u] = __ldg(R.val + r + u);
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const int excl = incl - nq;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int g0 = 0; g0 < total; g0 += 32 * CP_UNROLL) {
+      ushort4 c[CP_UNROLL];
+      int4 w[CP_UNROLL];
+      unsigned long long oq[CP_UNROLL];
+      int lo[CP_UNROLL], hi[CP_UNROLL], vv[CP_UNROLL];
+#pragma unroll
+      for (int u = 0; u < CP_UNROLL; ++u) {
+        const int g = g0 + 32 * u + lane;
+        const int gg = min(g, total - 1);
+        // e = number of entries whose run ends at or before quad gg
+        int e = 0;
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1)
+          if (__shfl_sync(0xffffffffu, incl, e + s - 1) <= gg) e += s;
+        const int t = gg - __shfl_sync(0xffffffffu, excl, e);
+        const unsigned long long be = shfl64(b, e), oe = shfl64(o, e);
+        const int rle = __shfl_sync(0xffffffffu, rl, e);
+        vv[u] = __shfl_sync(0xffffffffu, v, e);
+        const int k = (int)(oe & 3ull);
+        oq[u] = oe - (unsigned long long)k + 4ull * (unsigned long long)t;
+        lo[u] = k - 4 * t;        // entries u' of the quad in [lo, hi) belong to the run
+        hi[u] = k + rle - 4 * t;
+        if (g >= total) hi[u] = -1;  // idle
+        const int64_t off = (int64_t)k * P + (int64_t)be + 4 * (int64_t)t;
+        if (g < total) {
+          c[u] = *reinterpret_cast<const ushort4*>(icol + off);
+          w[u] = *reinterpret_cast<const int4*>(ival + off);
         }
-        *reinterpret_cast<ushort4*>(crow + ob + 4ull * t) =
-            make_ushort4((unsigned short)c4[0], (unsigned short)c4[1], (unsigned short)c4[2],
-                         (unsigned short)c4[3]);
-        store4<V>(cval + ob + 4ull * t, (V)(ve * v4[0]), (V)(ve * v4[1]), (V)(ve * v4[2]),
-                  (V)(ve * v4[3]));
       }
-      const int done = head + 4 * nvec;
-      if (lane < rle - done) {
-        crow[oe + done + lane] = (uint16_t)__ldg(R.col + rse + done + lane);
-        cval[oe + done + lane] = (V)(ve * __ldg(R.val + rse + done + lane));
+#pragma unroll
+      for (int u = 0; u < CP_UNROLL; ++u) {
+        if (hi[u] <= 0) continue;
+        const int ve = vv[u];
+        const V a0 = (V)(ve * w[u].x), a1 = (V)(ve * w[u].y), a2 = (V)(ve * w[u].z),
+                a3 = (V)(ve * w[u].w);
+        const unsigned long long ot = oq[u];
+        if (lo[u] <= 0 && hi[u] >= 4) {
+          put_quad<V>(crow, cval, ot, c[u], a0, a1, a2, a3);
+        } else {
+          if (0 >= lo[u] && 0 < hi[u]) { crow[ot] = c[u].x; cval[ot] = a0; }
+          if (1 >= lo[u] && 1 < hi[u]) { crow[ot + 1] = c[u].y; cval[ot + 1] = a1; }
+          if (2 >= lo[u] && 2 < hi[u]) { crow[ot + 2] = c[u].z; cval[ot + 2] = a2; }
+          if (3 >= lo[u] && 3 < hi[u]) { crow[ot + 3] = c[u].w; cval[ot + 3] = a3; }
+        }
       }
     }
   }
@@ -386,7 +473,58 @@ __device__ __forceinline__ unsigned emit_reg(int* acc, int (&regs)[4 * NQ], unsi
   return pos;
 }
 
-// One persistent kernel, one 32-warp block per SM sharing the dense rows; a
+// Emission through shared memory (FP32 values): per 128-row slab, each lane
+// puts its nonzeros at their run positions in the slab's own accumulator
+// words (values) and in the warp's row staging `srow`, then the warp writes
+// the run with consecutive lanes on consecutive entries (one 64-byte row
+// store and one 128-byte value store per 32 entries), and zeroes the slab.
+template <int NQ>
+__device__ __forceinline__ unsigned emit_staged(int* acc, int (&regs)[4 * NQ], uint16_t* srow,
+                                                unsigned long long off,
+                                                uint16_t* __restrict__ crow,
+                                                float* __restrict__ cval) {
+  const int lane = threadIdx.x & 31;
+  int4* acc4 = reinterpret_cast<int4*>(acc);
+  unsigned pos = 0;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int4 s = acc4[q * 32 + lane];
+    const int x0 = regs[4 * q] + s.x, x1 = regs[4 * q + 1] + s.y;
+    const int x2 = regs[4 * q + 2] + s.z, x3 = regs[4 * q + 3] + s.w;
+    regs[4 * q] = regs[4 * q + 1] = regs[4 * q + 2] = regs[4 * q + 3] = 0;
+    const unsigned b0 = __ballot_sync(0xffffffffu, x0 != 0);
+    const unsigned b1 = __ballot_sync(0xffffffffu, x1 != 0);
+    const unsigned b2 = __ballot_sync(0xffffffffu, x2 != 0);
+    const unsigned b3 = __ballot_sync(0xffffffffu, x3 != 0);
+    const unsigned lt = (1u << lane) - 1;
+    int p = __popc(b0 & lt) + __popc(b1 & lt) + __popc(b2 & lt) + __popc(b3 & lt);
+    const int total = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+    float* sv = reinterpret_cast<float*>(acc) + q * 128;  // the slab's words, read above
+    const int m0 = q * 128 + 4 * lane;
+    __syncwarp();
+    if (x0) { sv[p] = (float)x0; srow[p] = (uint16_t)m0;       ++p; }
+    if (x1) { sv[p] = (float)x1; srow[p] = (uint16_t)(m0 + 1); ++p; }
+    if (x2) { sv[p] = (float)x2; srow[p] = (uint16_t)(m0 + 2); ++p; }
+    if (x3) { sv[p] = (float)x3; srow[p] = (uint16_t)(m0 + 3); }
+    __syncwarp();
+    const unsigned long long o = off + pos;
+    for (int j = lane; j < total; j += 32) {
+      crow[o + j] = srow[j];
+      cval[o + j] = sv[j];
+    }
+    __syncwarp();
+    acc4[q * 32 + lane] = make_int4(0, 0, 0, 0);
+    pos += (unsigned)total;
+  }
+  return pos;
+}
+
+template <typename V>
+struct IsF32 { static constexpr bool v = false; };
+template <>
+struct IsF32<float> { static constexpr bool v = true; };
+
+// One persistent kernel, one block per SM sharing the dense rows; a
 // warp per column, first the columns with at least CF_HEAVY_COL nonzeros
 // (`list`, the longest work items), then the other multi-nonzero columns
 // (`mlist`).  Each warp's accumulator is left zero by its emission.
@@ -408,6 +546,8 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
 #pragma unroll
   for (int k = 0; k < 4 * NQ; ++k) regs[k] = 0;
   int* acc = accs + warp * W;
+  // row staging of the emission: 128 entries per warp after the accumulators
+  uint16_t* srow = reinterpret_cast<uint16_t*>(accs + nw * W) + warp * 128;
   // the columns of the heavy list, one per warp grab (the longest work items
   // first), then those of the multi list, `grab` per warp grab
 #pragma unroll 1
@@ -465,7 +605,11 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
         entry_meta(R, dn, ni, csl, crs, crl);
         cv = nv;
         __syncwarp();
-        const unsigned n = emit_reg<V, NQ>(acc, regs, oe, crow, cval);
+        unsigned n;
+        if constexpr (IsF32<V>::v)
+          n = emit_staged<NQ>(acc, regs, srow, oe, crow, cval);
+        else
+          n = emit_reg<V, NQ>(acc, regs, oe, crow, cval);
         __syncwarp();
         if (lane == 0) ccnt[fe] = n;
         e = e2;
@@ -482,7 +626,8 @@ ctd_status cf_launch(const CscDev& X, const CsrDev& R, const Dense& dn,
                      const int64_t* heavy, const unsigned* nheavy, const int64_t* multi,
                      const unsigned* nmulti, unsigned long long* work, cudaStream_t st) {
   constexpr int W = NQ * 128;
-  const size_t smem = ((size_t)dn.hmax + CF_THREADS / 32) * (size_t)W * sizeof(int);
+  const size_t smem = ((size_t)dn.hmax + CF_THREADS / 32) * (size_t)W * sizeof(int) +
+                      (size_t)(CF_THREADS / 32) * 128 * sizeof(uint16_t);
   CTD_TRY(allow_max_smem((const void*)k_cf<V, NQ>));
   int per_sm = 0;
   CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cf<V, NQ>, CF_THREADS, smem));
@@ -494,7 +639,8 @@ ctd_status cf_launch(const CscDev& X, const CsrDev& R, const Dense& dn,
 }
 
 template <typename V>
-ctd_status cf_all(int nq, const CscDev& X, int64_t n_cols, const CsrDev& R, const Dense& dn,
+ctd_status cf_all(int nq, const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
+                  const Dense& dn,
                   const unsigned long long* coff, uint32_t* ccnt, uint16_t* crow, V* cval,
                   int positive, int64_t list_cap, Arena& a, cudaStream_t st) {
   int64_t *single, *heavy, *multi;
@@ -510,8 +656,32 @@ ctd_status cf_all(int nq, const CscDev& X, int64_t n_cols, const CsrDev& R, cons
   CTD_LAUNCH(k_classify, (grid_for(n_cols, 256 * CL_ITEMS, (int64_t)num_sms() * 8)), (256), 0, st,
              reinterpret_cast<const unsigned long long*>(X.colptr), coff, n_cols, positive, ccnt,
              single, counts, heavy, counts + 1, multi, counts + 2);
-  CTD_LAUNCH(k_copy_rows<V>, (num_sms() * 8), (256), 0, st, X, R, single, counts, coff, crow,
-             cval);
+  // row images (see k_img_sizes): P entries per image, a multiple of 4
+  unsigned long long *sz, *ip, *stmp;
+  unsigned* sstat;
+  CTD_TRY(a.get(&sz, n_rows + 1));
+  CTD_TRY(a.get(&ip, n_rows + 1));
+  CTD_TRY(a.get(&stmp, scan_tmp_elems(n_rows + 1)));
+  CTD_TRY(a.get(&sstat, 1));
+  const int64_t P = (R.nnz + 6 * n_rows + 3) & ~(int64_t)3;
+  uint16_t* icol;
+  int* ival;
+  CTD_TRY(a.get(&icol, 4 * P));
+  CTD_TRY(a.get(&ival, 4 * P));
+  const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
+  const unsigned g = grid_for(n_rows, 256, (int64_t)num_sms() * 4);
+  CTD_CUDA(cudaMemsetAsync(sz + n_rows, 0, sizeof(unsigned long long), st));
+  CTD_LAUNCH(k_img_sizes, (g), (256), 0, st, rp, n_rows, sz);
+  launch_scan_u64(reinterpret_cast<const uint64_t*>(sz), reinterpret_cast<uint64_t*>(ip),
+                  n_rows + 1, false, reinterpret_cast<uint64_t*>(stmp), sstat, st);
+  CTD_LAUNCH(k_img_fill, (grid_for(n_rows * 32, 256, (int64_t)num_sms() * 8)), (256), 0, st, R,
+             n_rows, ip, P, icol, ival);
+  {
+    PhaseScope ph("c_fill_copy", st);
+    CTD_LAUNCH(k_copy_flat<V>, (num_sms() * 8), (256), 0, st, X, rp, ip, icol, ival, P, single,
+               counts, coff, crow, cval);
+  }
+  PhaseScope ph("c_fill_multi", st);
   switch (nq) {
     case 1: return cf_launch<V, 1>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, counts + 2, work, st);
     case 2: return cf_launch<V, 2>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, counts + 2, work, st);
@@ -528,14 +698,15 @@ ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, in
                              const CsrDev& R, const uint64_t* coff, uint32_t* ccnt,
                              uint16_t* crow, void* cval, int fp32, int positive,
                              cudaStream_t st) {
+  if (R.nnz < 0) return fail(CTD_EINVAL, "C fill: the entry count of R is not set");
   const int width = R.width;
   const int nq0 = (width + 127) / 128;
   const int nq = nq0 <= 1 ? 1 : nq0 <= 2 ? 2 : nq0 <= 4 ? 4 : 8;
   const int W = nq * 128;
   const size_t row_b = (size_t)W * sizeof(int);
-  // one block of 32 warps per SM: dense rows + 32 warp accumulators in ~220 KB
+  // one block per SM: dense rows, the warps' accumulators and row staging in ~220 KB
   const int budget = 220 * 1024;
-  int hmax = (int)(budget / (int64_t)row_b) - CF_THREADS / 32;
+  int hmax = (int)((budget - (CF_THREADS / 32) * 256) / (int64_t)row_b) - CF_THREADS / 32;
   hmax = std::max(0, std::min(hmax, CF_MAX_DENSE));
   const int minlen = std::max(16, 16 * nq);  // shorter rows are cheaper walked sparsely
   Arena a;
@@ -558,9 +729,9 @@ ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, in
   const unsigned long long* co = reinterpret_cast<const unsigned long long*>(coff);
   const int64_t list_cap = std::max<int64_t>(1, std::min(n_cols, nnz));
   if (fp32)
-    return cf_all<float>(nq, X, n_cols, R, dn, co, ccnt, crow, static_cast<float*>(cval),
+    return cf_all<float>(nq, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<float*>(cval),
                          positive, list_cap, a, st);
-  return cf_all<double>(nq, X, n_cols, R, dn, co, ccnt, crow, static_cast<double*>(cval),
+  return cf_all<double>(nq, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<double*>(cval),
                         positive, list_cap, a, st);
 }
 

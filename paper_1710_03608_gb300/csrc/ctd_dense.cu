@@ -528,27 +528,6 @@ void launch_gather_lower(const double* A, int64_t lda, const int* idx, const int
       A, lda, idx, count_dev, nk_max, B, ldb);
 }
 
-// ---------------------------------------------------------------------------
-// Z = L^{-1}
-// ---------------------------------------------------------------------------
-__global__ void k_identity(double* Z, int64_t n, int64_t ldz) {
-  const int64_t total = n * n;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e % n, c = e / n;
-    Z[r + c * ldz] = r == c ? 1.0 : 0.0;
-  }
-}
-
-// Z = L^{-1}: forward substitution with the identity as right-hand sides
-// (blocked: substitution on 32-row diagonal blocks, GEMM updates below).
-void tri_inverse(const double* L, int64_t ldl, int64_t n, double* Z, int64_t ldz,
-                 cudaStream_t st) {
-  if (n <= 0) return;
-  CTD_LAUNCH(k_identity, (grid_for(n * n, 256, (int64_t)num_sms() * 8)), (256), 0, st, Z, n, ldz);
-  tri_solve_lower(L, ldl, n, Z, ldz, n, st);
-}
-
 // U = Z^T Z for Z = L^{-1}: lower tiles then mirror.
 void u_from_linv(const double* Z, int64_t n, int64_t ldz, double* U, int64_t ldu,
                  cudaStream_t st) {
@@ -557,58 +536,74 @@ void u_from_linv(const double* Z, int64_t n, int64_t ldz, double* U, int64_t ldu
 }
 
 // ---------------------------------------------------------------------------
-// B <- L^{-1} B for lower-triangular L (n x n) and nrhs right-hand sides,
-// by blocked forward substitution: each 32-row diagonal block is solved by
-// substitution (one thread per right-hand side), then the rows below are
-// updated with a GEMM.  Substitution keeps the solve backward stable, which
-// the independence test needs: pivots ||x||^2 - ||L^{-1} R^T x||^2 then carry
+// Triangular solves.  Substitution keeps them backward stable, which the
+// independence test needs: pivots ||x||^2 - ||L^{-1} R^T x||^2 then carry
 // errors of order n u ||x||^2, not kappa(L) u ||x||^2.
 // ---------------------------------------------------------------------------
-// One warp per right-hand side: lane r holds x_r of the 32-row block; once
-// x_r is known (lane r), it is broadcast and every lane below subtracts its
-// share (right-looking), so a column costs 32 FP64 multiply-adds per lane and
-// the reciprocal diagonal is formed once per block.  (A thread per column
-// left most SMs idle: GB300's FP64 pipe is narrow, so the work must spread.)
-__global__ void k_trsm_diag(const double* __restrict__ L, int64_t ldl, int64_t n, int64_t k0,
-                            double* __restrict__ B, int64_t ldb, int64_t nrhs) {
-  __shared__ double Ls[NB][NB + 1];
-  __shared__ double inv[NB];
-  const int nb = (int)min((int64_t)NB, n - k0);
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e % NB, c = e / NB;
-    Ls[r][c] = (r < nb && c <= r) ? L[(k0 + r) + (k0 + c) * ldl] : 0.0;
-  }
-  __syncthreads();
-  if (threadIdx.x < NB) inv[threadIdx.x] = threadIdx.x < nb ? 1.0 / Ls[threadIdx.x][threadIdx.x] : 0.0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (j >= nrhs) return;
-  double* col = B + j * ldb + k0;
-  double x = lane < nb ? col[lane] : 0.0;
-#pragma unroll
-  for (int r = 0; r < NB; ++r) {
-    if (r < nb) {
-      const double xr = __shfl_sync(0xffffffffu, x * inv[r], r);
-      if (lane == r) x = xr;
-      else if (lane > r) x = fma(-Ls[lane][r], xr, x);
+// Z = L^{-1} in one launch: a block per column j of Z solves L z = e_j by
+// blocked forward substitution from row j down (z is zero above row j), the
+// column held in shared memory.  Warp 0 substitutes through each 32-row
+// diagonal block (right-looking; lane r holds z_r, the reciprocal diagonal
+// formed once per block), then every thread updates rows below with that
+// block's 32 values in a fixed order.  Forward substitution keeps the
+// inverse backward stable.  (Per-block substitution and GEMM launches took
+// 29 latency-bound launches for n = 456.)
+constexpr int TI_THREADS = 256;
+
+__global__ void __launch_bounds__(TI_THREADS)
+    k_tri_inv_cols(const double* __restrict__ L, int64_t ldl, int n, double* __restrict__ Z,
+                   int64_t ldz) {
+  extern __shared__ double zs[];  // [n]
+  __shared__ double Ls[NB][NB + 1];  // the current diagonal block
+  const int j = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int r = tid; r < n; r += TI_THREADS) zs[r] = r == j ? 1.0 : 0.0;
+  for (int k0 = (j / NB) * NB; k0 < n; k0 += NB) {
+    const int nb = min(NB, n - k0);
+    for (int e = tid; e < NB * NB; e += TI_THREADS) {
+      const int r = e % NB, c = e / NB;
+      Ls[r][c] = (r < nb && c <= r) ? L[(k0 + r) + (int64_t)(k0 + c) * ldl] : 0.0;
     }
+    __syncthreads();
+    if (warp == 0) {
+      double x = lane < nb ? zs[k0 + lane] : 0.0;
+      const double rinv = lane < nb ? 1.0 / Ls[lane][lane] : 0.0;
+      for (int c = 0; c < nb; ++c) {
+        const double xc = __shfl_sync(0xffffffffu, x * rinv, c);
+        if (lane == c)
+          x = xc;
+        else if (lane > c && lane < nb)
+          x = fma(-Ls[lane][c], xc, x);
+      }
+      if (lane < nb) zs[k0 + lane] = x;
+    }
+    __syncthreads();
+    for (int r = k0 + nb + tid; r < n; r += TI_THREADS) {
+      double acc = zs[r];
+      for (int c = 0; c < nb; ++c) acc = fma(-L[r + (int64_t)(k0 + c) * ldl], zs[k0 + c], acc);
+      zs[r] = acc;
+    }
+    __syncthreads();
   }
-  if (lane < nb) col[lane] = x;
+  for (int r = tid; r < n; r += TI_THREADS) Z[r + (int64_t)j * ldz] = r < j ? 0.0 : zs[r];
 }
 
-void tri_solve_lower(const double* L, int64_t ldl, int64_t n, double* B, int64_t ldb, int64_t nrhs,
-                     cudaStream_t st) {
-  if (n <= 0 || nrhs <= 0) return;
-  for (int64_t k0 = 0; k0 < n; k0 += NB) {
-    const int64_t nb = std::min<int64_t>(NB, n - k0);
-    CTD_LAUNCH(k_trsm_diag, ((unsigned)((nrhs + 7) / 8)), (256), 0, st, L, ldl, n, k0, B, ldb,
-               nrhs);
-    const int64_t rest = n - k0 - nb;
-    if (rest > 0)
-      dgemm(false, false, rest, nrhs, nb, -1.0, L + (k0 + nb) + k0 * ldl, ldl, B + k0, ldb, 1.0,
-            B + k0 + nb, ldb, st);
+ctd_status tri_inverse(const double* L, int64_t ldl, int64_t n, double* Z, int64_t ldz,
+                       cudaStream_t st) {
+  if (n <= 0) return CTD_OK;
+  // the column lives in shared memory: n <= 28,000 or so
+  const size_t smem = (size_t)n * sizeof(double);
+  if (smem > 48 * 1024) {
+    CTD_TRY(allow_max_smem((const void*)k_tri_inv_cols));
+    int dev = 0, optin = 0;
+    CTD_CUDA(cudaGetDevice(&dev));
+    CTD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (smem > (size_t)optin)
+      return fail(CTD_ENOTSUP, "triangular inverse: more kept fibers than one column of shared memory holds");
   }
+  CTD_LAUNCH(k_tri_inv_cols, ((unsigned)n), (TI_THREADS), smem, st, L, ldl, (int)n, Z, ldz);
+  CTD_CUDA(cudaGetLastError());
+  return CTD_OK;
 }
 
 // B <- L^{-T} B (backward substitution with the transpose of lower L).

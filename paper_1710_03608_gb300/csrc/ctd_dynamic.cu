@@ -372,7 +372,7 @@ static ctd_status cholqr_pass(const double* V, int64_t m, int n, double shift, d
   *ok = nk == n;
   if (!*ok) return CTD_OK;
   launch_gather_lower(G, n, idx, idx + n, n, L, n, st);
-  tri_inverse(L, n, n, Li, n, st);
+  CTD_TRY(tri_inverse(L, n, n, Li, n, st));
   dgemm(false, true, m, n, n, 1.0, V, m, Li, n, 0.0, out, m, st);
   return CTD_OK;
 }
@@ -717,6 +717,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   double pu = 0.0;
   if (dn > 0 && X.nnz > 0) {
     CsrDev R{F->Rrowptr, F->Rcol, F->Rcval, (int)dn};
+    R.nnz = F->nnz_R;
     uint32_t* ub;
     CTD_TRY(scratch.get(&ub, M.n_cols));
     CTD_TRY(dalloc_n(&rec.Coff, M.n_cols + 1, st));
@@ -726,16 +727,12 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
       launch_c_bounds(M.csc(), M.n_cols, R, ub, st);
       launch_scan_u32(ub, rec.Coff, M.n_cols, false, M.tmp, M.status, st);
     }
+    // the capacity is read back while the error kernels (which do not need
+    // C) run
     uint64_t cap = 0;
-    CTD_TRY(d2h(&cap, rec.Coff + M.n_cols, 1, st));
-    CTD_TRY(sync(st));
-    CTD_TRY(dalloc_n(&rec.Crow, std::max<uint64_t>(cap, 1), st));
-    CTD_TRY(dalloc(&rec.Cval, std::max<uint64_t>(cap, 1) * (fp32 ? 4 : 8), st));
-    {
-      PhaseScope ph("d_c_fill", st);
-      CTD_TRY(launch_c_fill(M.csc(), M.n_cols, M.n_rows, M.nnz, R, rec.Coff, rec.Ccnt, rec.Crow, rec.Cval, fp32,
-                            D.all_positive, (uint64_t)D.max_T, st));
-    }
+    Readback rbc(st);
+    CTD_TRY(rbc.add(&cap, rec.Coff + M.n_cols, 1));
+    CTD_TRY(rbc.mark());
     double* d_pu;
     uint64_t* d_nnzc;
     CTD_TRY(scratch.get(&d_pu, 1));
@@ -745,6 +742,14 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
       PhaseScope ph("d_error", st);
       CTD_TRY(launch_qform_rows(M.csc(), M.n_cols, M.nnz, F->Qt, D.cap_d, dn, F->qn, M.n_rows, d_pu,
                                 scratch, st));
+    }
+    CTD_TRY(rbc.wait_mark());
+    CTD_TRY(dalloc_n(&rec.Crow, std::max<uint64_t>(cap, 1), st));
+    CTD_TRY(dalloc(&rec.Cval, std::max<uint64_t>(cap, 1) * (fp32 ? 4 : 8), st));
+    {
+      PhaseScope ph("d_c_fill", st);
+      CTD_TRY(launch_c_fill(M.csc(), M.n_cols, M.n_rows, M.nnz, R, rec.Coff, rec.Ccnt, rec.Crow, rec.Cval, fp32,
+                            D.all_positive, (uint64_t)D.max_T, st));
     }
     launch_sum_u32(rec.Ccnt, M.n_cols, d_nnzc, st);
     uint64_t nnzc = 0;
@@ -881,7 +886,7 @@ ctd_status dyn_U(const ctd_factors* Fc, double* U) {
     a.st = st;
     double* Li;
     CTD_TRY(a.get(&Li, (size_t)n * n));
-    tri_inverse(F->L, F->dyn->cap_d, n, Li, n, st);
+    CTD_TRY(tri_inverse(F->L, F->dyn->cap_d, n, Li, n, st));
     u_from_linv(Li, n, n, F->U, n, st);
     CTD_CUDA(cudaGetLastError());
     F->U_valid = true;

@@ -57,35 +57,92 @@ __global__ void k_gather_cols(const double* __restrict__ A, int64_t lda, int64_t
   }
 }
 
-// The candidate part of the explicit residual of each suspect c,
-// r_c = x_k - Xc[:, K] eta_c, row by row from the by-row layout (row i of
-// the candidates, in column order): a fixed order of operations, so the
-// ratio, and every decision and pivot taken from it, is reproducible.  With
-// init = 0 the products are subtracted from the residual already in rbuf
-// (the refinement step).  kpos maps a candidate to its kept position (-1 if
-// not kept); eta is zero for kept candidates after k_c.  The R^(t) part,
-// Q gamma_c, is subtracted afterwards by a GEMM.
-__global__ void k_resid_rows(int64_t n_rows, const unsigned long long* __restrict__ crp,
-                             const int32_t* __restrict__ ccol, const int32_t* __restrict__ cval,
-                             const int* __restrict__ kpos, int kept,
-                             const double* __restrict__ eta, const int* __restrict__ sus,
-                             int init, double* __restrict__ rbuf) {
-  const int c = blockIdx.y;
-  const int k = sus[c];
-  double* r = rbuf + (int64_t)c * n_rows;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rows;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double acc = init ? 0.0 : r[i];
-    double xk = 0.0;
-    for (unsigned long long p = crp[i]; p < crp[i + 1]; ++p) {
-      const int cc = ccol[p];
-      const double v = (double)cval[p];
-      if (cc == k) xk = v;
-      const int q = kept > 0 ? kpos[cc] : -1;
-      if (q >= 0) acc = fma(-eta[q + (int64_t)c * kept], v, acc);
+// The candidate part of the explicit residuals, r_c = x_k - Xc[:, K] eta_c
+// for every suspect c at once: a sparse-times-dense product by rows.  A
+// warp takes row i of the candidates' by-row layout, broadcasts the row's
+// entries (32 at a time, in column order) and each lane updates suspects
+// c = lane, lane + 32, ... (up to RS_CHUNK per pass) with the kept entries'
+// eta rows (etaT, kept x ns row-major), so a row is read once for all
+// suspects; the order of operations per (i, c) is fixed (reproducible
+// ratios and decisions).  sus_of[cc] = c if candidate cc is suspect c, else
+// -1: that entry is x_k's own value.  With init = 0 the products are
+// subtracted from the residual already in rbuf (the refinement step).  eta
+// is zero for kept candidates after k_c.  The R^(t) part, Q gamma_c, is
+// subtracted afterwards by a GEMM.  (A thread per (row, suspect) walked the
+// long rows, those of the frequent mode-alpha indices, as chains of
+// dependent loads, once per suspect.)
+constexpr int RS_PER_LANE = 8;
+constexpr int RS_CHUNK = 32 * RS_PER_LANE;
+
+__global__ void __launch_bounds__(256)
+    k_resid_rows(int64_t n_rows, const unsigned long long* __restrict__ crp,
+                 const int32_t* __restrict__ ccol, const int32_t* __restrict__ cval,
+                 const int* __restrict__ kpos, const int* __restrict__ sus_of,
+                 const double* __restrict__ etaT, int ns, int init, double* __restrict__ rbuf) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = gw; i < n_rows; i += nw) {
+    const unsigned long long a = crp[i], b = crp[i + 1];
+    for (int c0 = 0; c0 < ns; c0 += RS_CHUNK) {
+      double acc[RS_PER_LANE];
+#pragma unroll
+      for (int u = 0; u < RS_PER_LANE; ++u) acc[u] = 0.0;
+      for (unsigned long long base = a; base < b; base += 32) {
+        const int cnt = (int)min((unsigned long long)32, b - base);
+        int q = -1, sc = -1;
+        double v = 0.0;
+        if (lane < cnt) {
+          const int cc = ccol[base + lane];
+          v = (double)cval[base + lane];
+          q = kpos[cc];
+          sc = sus_of[cc];
+        }
+        for (int e = 0; e < cnt; ++e) {
+          const int qe = __shfl_sync(0xffffffffu, q, e);
+          const int se = __shfl_sync(0xffffffffu, sc, e);
+          const double ve = __shfl_sync(0xffffffffu, v, e);
+          if (qe >= 0) {
+            const double* er = etaT + (int64_t)qe * ns + c0 + lane;
+#pragma unroll
+            for (int u = 0; u < RS_PER_LANE; ++u)
+              if (c0 + lane + 32 * u < ns) acc[u] = fma(-ve, er[32 * u], acc[u]);
+          }
+          if (init && se >= c0 && se < c0 + RS_CHUNK) {
+            // x_k(i), the suspect's own entry (static indices keep acc in registers)
+            const int us = (se - c0) >> 5, ls = (se - c0) & 31;
+#pragma unroll
+            for (int u = 0; u < RS_PER_LANE; ++u) acc[u] += (u == us && lane == ls) ? ve : 0.0;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < RS_PER_LANE; ++u) {
+        const int c = c0 + lane + 32 * u;
+        if (c < ns) {
+          double* r = rbuf + (int64_t)c * n_rows + i;
+          *r = init ? acc[u] : *r + acc[u];
+        }
+      }
     }
-    r[i] = init ? xk + acc : acc;
   }
+}
+
+// etaT[q * ns + c] = eta[q + c * kept]
+__global__ void k_transpose_eta(const double* __restrict__ eta, int kept, int ns,
+                                double* __restrict__ etaT) {
+  const int64_t total = (int64_t)kept * ns;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(e / ns), c = (int)(e % ns);
+    etaT[e] = eta[q + (int64_t)c * kept];
+  }
+}
+
+// sus_of[sus[c]] = c
+__global__ void k_sus_of(const int* __restrict__ sus, int ns, int* __restrict__ sus_of) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ns; c += gridDim.x * blockDim.x)
+    sus_of[sus[c]] = c;
 }
 
 __global__ void k_kpos(const int* __restrict__ idx, int kept, int* __restrict__ kpos) {
@@ -217,8 +274,11 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
     out.kept = kept;
     CTD_TRY(scratch.get(&out.Lk, (size_t)std::max(kept, 1) * std::max(kept, 1)));
     CTD_TRY(scratch.get(&out.Li, (size_t)std::max(kept, 1) * std::max(kept, 1)));
-    launch_gather_lower(in.S, du, out.idx, count, kept, out.Lk, kept, st);
-    tri_inverse(out.Lk, kept, kept, out.Li, kept, st);
+    {
+      PhaseScope ph("filter_inverse", st);
+      launch_gather_lower(in.S, du, out.idx, count, kept, out.Lk, kept, st);
+      CTD_TRY(tri_inverse(out.Lk, kept, kept, out.Li, kept, st));
+    }
     std::vector<int> sus;
     for (int k = 0; k < du; ++k)
       if (h_xn[k] > 0.0 && h_piv[k] < SUSPECT * h_xn[k]) sus.push_back(k);
@@ -264,11 +324,18 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
     CTD_CUDA(cudaMemsetAsync(kpos, 0xff, (size_t)du * sizeof(int), st));  // -1
     if (kept > 0)
       CTD_LAUNCH(k_kpos, (grid_for(kept, 256, 64)), (256), 0, st, out.idx, kept, kpos);
-    const dim3 grows(grid_for(in.n_rows, 256, std::max<int64_t>(1, (int64_t)num_sms() * 4 / ns)),
-                     ns);
+    int* sus_of;
+    double* etaT;
+    CTD_TRY(scratch.get(&sus_of, du));
+    CTD_TRY(scratch.get(&etaT, (size_t)kk * ns));
+    CTD_CUDA(cudaMemsetAsync(sus_of, 0xff, (size_t)du * sizeof(int), st));  // -1
+    CTD_LAUNCH(k_sus_of, (grid_for(ns, 256, 64)), (256), 0, st, d_sus, ns, sus_of);
+    const unsigned gt = grid_for((int64_t)kk * ns, 256, (int64_t)num_sms() * 8);
+    const unsigned grows = grid_for(in.n_rows * 32, 256, (int64_t)num_sms() * 16);  // a warp per row
+    if (kept > 0) CTD_LAUNCH(k_transpose_eta, (gt), (256), 0, st, eta, kept, ns, etaT);
     CTD_LAUNCH(k_resid_rows, (grows), (256), 0, st, in.n_rows,
                reinterpret_cast<const unsigned long long*>(in.c_rowptr), in.c_col, in.c_val, kpos,
-               kept, eta, d_sus, 1, rbuf);
+               sus_of, etaT, ns, 1, rbuf);
     // minus Q gamma (Q = Qt^T, n_rows x dt)
     if (in.dt > 0)
       dgemm(true, false, in.n_rows, ns, in.dt, -1.0, in.Qt, in.ldq, gammaQ, in.dt, 1.0, rbuf,
@@ -316,9 +383,10 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
         dgemm(true, false, kept, ns, kept, 1.0, out.Li, kept, zK, kept, 0.0, etad, kept, st);
       }
       // r -= Xc[:, K] eta_d, then r -= Q (h_Q - W_K eta_d)
+      if (kept > 0) CTD_LAUNCH(k_transpose_eta, (gt), (256), 0, st, etad, kept, ns, etaT);
       CTD_LAUNCH(k_resid_rows, (grows), (256), 0, st, in.n_rows,
                  reinterpret_cast<const unsigned long long*>(in.c_rowptr), in.c_col, in.c_val,
-                 kpos, kept, etad, d_sus, 0, rbuf);
+                 kpos, sus_of, etaT, ns, 0, rbuf);
       if (in.dt > 0) {
         if (kept > 0)
           dgemm(false, false, in.dt, ns, kept, -1.0, WK, in.dt, etad, kept, 1.0, hQ, in.dt, st);

@@ -201,6 +201,7 @@ struct CsrDev {        // a factor by row: row i holds (col, val) pairs
   const int32_t* col;
   const int32_t* val;
   int width;           // number of columns
+  int64_t nnz = -1;    // number of entries (-1: not known on the host)
 };
 
 // Dense products: out(:, c) = R^T x_{fibers[c]} for c < nf (column-major,
@@ -295,11 +296,8 @@ void launch_compact_flags(const int* keep, int n, int* idx, int* count, cudaStre
 void launch_gather_lower(const double* A, int64_t lda, const int* idx, const int* count_dev,
                          int nk_max, double* B, int64_t ldb, cudaStream_t st);
 // Z = L^{-1} for lower-triangular L (n x n), in place into Z (Z != L).
-void tri_inverse(const double* L, int64_t ldl, int64_t n, double* Z, int64_t ldz,
-                 cudaStream_t st);
-// B <- L^{-1} B (lower-triangular L, n x n; nrhs columns), by substitution.
-void tri_solve_lower(const double* L, int64_t ldl, int64_t n, double* B, int64_t ldb, int64_t nrhs,
-                     cudaStream_t st);
+ctd_status tri_inverse(const double* L, int64_t ldl, int64_t n, double* Z, int64_t ldz,
+                       cudaStream_t st);
 // U = Z^T Z (symmetric, full) for lower-triangular Z.
 void u_from_linv(const double* Z, int64_t n, int64_t ldz, double* U, int64_t ldu,
                  cudaStream_t st);
@@ -326,7 +324,13 @@ struct Readback {
   }
   ctd_status add_bytes(void* host, const void* dev, size_t bytes);
   ctd_status wait();
+  // mark() records an event after the copies queued so far; wait_mark()
+  // waits for that event only (work queued after mark() keeps running) and
+  // delivers those copies
+  ctd_status mark();
+  ctd_status wait_mark();
   cudaStream_t st;
+  cudaEvent_t ev = nullptr;
   char* chunk = nullptr;
   size_t used = 0;
   struct Item { void* host; size_t off, bytes; };

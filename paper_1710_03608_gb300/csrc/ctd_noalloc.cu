@@ -19,8 +19,11 @@ constexpr int64_t NA_MAX_COLS = CTD_NOALLOC_MAX_COLS;
 
 // Column sums of squares, then (in place) their inclusive prefix sums.
 static __device__ __align__(256) unsigned long long g_na_cdf[NA_MAX_COLS];
-// Tile totals of the prefix sum (2 * tiles + 4 entries, see scan_tmp_elems).
-static __device__ __align__(256) unsigned long long g_na_tiles[2 * (NA_MAX_COLS / 4096) + 8];
+// Scratch of the prefix sum: scan_tmp_elems(n) = 9 * ceil(n / 4096) + 4
+// entries (a tile sum and eight warp sums per 4096-entry tile); checked on
+// the host before every call.
+constexpr int64_t NA_TILES_ELEMS = 9 * ((NA_MAX_COLS + 4095) / 4096) + 8;
+static __device__ __align__(256) unsigned long long g_na_tiles[NA_TILES_ELEMS];
 // Status word (bad index, overflow) and the unique count.
 static __device__ __align__(256) unsigned g_na_status[2];
 
@@ -98,6 +101,8 @@ extern "C" ctd_status ctd_sample_noalloc(const ctd_coo3* X, int alpha, int64_t s
   if (n_cols > NA_MAX_COLS)
     return fail(CTD_EINVAL, "N_alpha exceeds CTD_NOALLOC_MAX_COLS (" +
                                 std::to_string(NA_MAX_COLS) + ")");
+  if (scan_tmp_elems(n_cols) > (size_t)NA_TILES_ELEMS)
+    return fail(CTD_EINVAL, "prefix-sum scratch too small for N_alpha");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Addr a;
   CTD_TRY(device_addresses(&a));

@@ -557,27 +557,48 @@ void launch_sort_rows(const uint64_t* rowptr, int64_t n_rows, const int32_t* col
 // ||Q^T x_f||^2 costs nnz * s~ multiply-adds; a column with one nonzero v in
 // row i contributes v^2 ||Q(i, :)||^2, read from the precomputed row norms.
 // ---------------------------------------------------------------------------
-// One warp per (row i, 32-column chunk of Q): lane c accumulates
-// Q(i, c) = sum over row i of R of R(i, m) Z(c, m) (Z lower triangular).
+// One warp per (row i of R, group of 64 columns of Q): Q(i, c) = sum over
+// the row's entries m <= c of R(i, m) Z(c, m) (Z lower triangular), in the
+// row's entry order; lane l owns columns c0 + l and c0 + 32 + l.  The row's
+// entries are loaded 32 at a time (coalesced) and broadcast by shuffles, so
+// the Z loads of successive entries are independent and overlap; R's rows
+// are sorted by column, so the walk stops at the first entry past the group.
 template <typename T>
 __global__ void k_build_q(CsrDev R, int64_t n_rows, const double* __restrict__ Z, int64_t ldz,
                           int qs, T* __restrict__ Q) {
   const int lane = threadIdx.x & 31;
-  const int nchunk = qs / 32;
+  const int ng = qs / 64;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
-  for (int64_t w = gw; w < n_rows * nchunk; w += nw) {
-    const int64_t i = w / nchunk;
-    const int c = (int)(w % nchunk) * 32 + lane;
+  for (int64_t w = gw; w < n_rows * ng; w += nw) {
+    const int64_t i = w / ng;
+    const int c0 = (int)(w % ng) * 64;
+    const int cA = c0 + lane, cB = c0 + 32 + lane;
     const unsigned long long a = rp[i], b = rp[i + 1];
-    double acc = 0.0;
-    if (c < R.width)
-      for (unsigned long long q = a; q < b; ++q) {
-        const int m = R.col[q];
-        if (c >= m) acc = fma((double)R.val[q], Z[c + (int64_t)m * ldz], acc);
+    double accA = 0.0, accB = 0.0;
+    for (unsigned long long base = a; base < b; base += 32) {
+      const int cnt = (int)min((unsigned long long)32, b - base);
+      int mm = INT_MAX;
+      double vv = 0.0;
+      if (lane < cnt) {
+        mm = R.col[base + lane];
+        vv = (double)R.val[base + lane];
       }
-    Q[i * qs + c] = (T)acc;
+      // the entries before the group's end form a prefix (sorted row)
+      const int nlive = __popc(__ballot_sync(0xffffffffu, mm < c0 + 64));
+#pragma unroll 4
+      for (int e = 0; e < nlive; ++e) {
+        const int m = __shfl_sync(0xffffffffu, mm, e);
+        const double v = __shfl_sync(0xffffffffu, vv, e);
+        const double* z = Z + (int64_t)m * ldz;
+        if (cA >= m && cA < R.width) accA = fma(v, z[cA], accA);
+        if (cB >= m && cB < R.width) accB = fma(v, z[cB], accB);
+      }
+      if (nlive < cnt) break;
+    }
+    Q[i * qs + cA] = (T)accA;
+    Q[i * qs + cB] = (T)accB;
   }
 }
 
@@ -619,7 +640,10 @@ struct Vec16<double> {
   static constexpr int n = 2;
 };
 
-constexpr int QF_THREADS = 512;
+// threads per block: one 32-warp block per SM for the register widths up
+// to NK = 4 (one copy of the staged rows per SM), two 16-warp blocks at NK = 8
+template <int NK>
+constexpr int qf_threads() { return NK >= 8 ? 512 : 1024; }
 
 // acc += sum over the chunks c = first, first + step, ... of the column
 // entries [a, b) (32 per chunk) of v * Q(i, coff : coff + NK*32*VEC); lane l
@@ -686,7 +710,7 @@ __device__ __forceinline__ void qrows_accumulate(const CscDev& X, const T* __res
 
 
 template <typename T, int NK>
-__global__ void __launch_bounds__(QF_THREADS, (NK >= 8 ? 1 : 2))
+__global__ void __launch_bounds__(qf_threads<NK>(), 1)
     k_qform(CscDev X, int64_t n_cols, const T* __restrict__ Q, int qs, int nblk,
             const T* __restrict__ qn, const short* __restrict__ slot_of,
             const int* __restrict__ hot_rows, int n_hot, int64_t n_rows, int grab,
@@ -843,6 +867,7 @@ static ctd_status qform_launch(const CscDev& X, int64_t n_cols, const T* Q, int 
   if (smem > 48 * 1024)
     CTD_TRY(allow_max_smem((const void*)k_qform<T, NK>));
   int per_sm = 0;
+  constexpr int QF_THREADS = qf_threads<NK>();
   CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qform<T, NK>, QF_THREADS,
                                                          smem));
   if (per_sm < 1) return fail(CTD_ECUDA, "error kernel does not fit on an SM");
@@ -1135,9 +1160,9 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, i
   CTD_TRY(scratch.get(reinterpret_cast<unsigned char**>(&qn), (size_t)n_rows * tsz));
   CTD_TRY(scratch.get(&slot_of, n_rows));
   CTD_TRY(scratch.get(&work, 2));
-  // hot rows (one register block wide only): as many as fit in ~100 KB of
-  // shared memory, so two blocks of 16 warps stay resident per SM
-  const size_t budget = 100 * 1024;
+  // hot rows (one register block wide only): as many as fit in ~200 KB of
+  // shared memory (one block per SM; 100 KB each for two blocks at NK = 8)
+  const size_t budget = NK >= 8 ? 100 * 1024 : 200 * 1024;
   int n_hot = nblk == 1 ? (int)std::min<int64_t>((int64_t)(budget / ((size_t)qs * tsz)), n_rows)
                         : 0;
   CTD_TRY(scratch.get(&hot, std::max(n_hot, 1)));
@@ -1159,7 +1184,7 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, i
     CTD_LAUNCH(k_hot_assign, (g), (256), 0, st, rowcnt, n_rows, thr, n_hot, slot_of, hot, cnt);
   }
   CTD_CUDA(cudaMemsetAsync(work, 0, 16, st));
-  const unsigned gq = grid_for(n_rows * qs, 256, (int64_t)num_sms() * 16);
+  const unsigned gq = grid_for(n_rows * (qs / 64) * 32, 256, (int64_t)num_sms() * 16);
   const unsigned gn = grid_for(n_rows * 32, 256, (int64_t)num_sms() * 8);
   if (fp32) {
     CTD_LAUNCH(k_build_q<float>, (gq), (256), 0, st, R, n_rows, Z, ldz, qs,

@@ -116,13 +116,29 @@ void launch_fiber_norms(const CooDev& X, uint64_t* norm2, uint32_t* colcnt, uint
 }
 
 // ---------------------------------------------------------------------------
-// K2: reduce-then-scan prefix sums (no inter-block waits)
+// K2: reduce-then-scan prefix sums (no inter-block waits).  Pass 1 writes
+// every warp's sum (512 inputs) and every tile's sum (4096 inputs); one block
+// scans the tile sums; pass 2 reads each input once more, starting from its
+// tile's offset plus the sums of the warps before it in the tile.  Sums are
+// saturating u64 additions: a total at or past 2^63 (the int64 range of the
+// CDF) sets DEV_OVERFLOW, integer arithmetic only (GB300's FP64 pipe is
+// narrow, and a double running sum per element made these passes FP64-bound).
 // ---------------------------------------------------------------------------
 constexpr int SCAN_WARPS = 8;
 constexpr int SCAN_PER_WARP = 512;                       // 16 per lane
 constexpr int SCAN_TILE = SCAN_WARPS * SCAN_PER_WARP;    // 4096
 
-size_t scan_tmp_elems(int64_t n) { return 2 * (size_t)((n + SCAN_TILE - 1) / SCAN_TILE) + 4; }
+// tmp layout: [ntiles + 1] tile sums (exclusive offsets after the tile scan,
+// the total last), then [ntiles * SCAN_WARPS] warp sums
+size_t scan_tmp_elems(int64_t n) {
+  const size_t nt = (size_t)((n + SCAN_TILE - 1) / SCAN_TILE);
+  return nt * (SCAN_WARPS + 1) + 4;
+}
+
+__device__ __forceinline__ unsigned long long sat_add(unsigned long long a, unsigned long long b) {
+  const unsigned long long s = a + b;
+  return s < a ? ~0ull : s;
+}
 
 __device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long x) {
   const int lane = threadIdx.x & 31;
@@ -140,62 +156,57 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
   return x;
 }
 
+__device__ __forceinline__ unsigned long long warp_sat_sum(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x = sat_add(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
 template <typename Tin>
 __global__ void k_scan_reduce(const Tin* __restrict__ in, int64_t n,
-                              unsigned long long* __restrict__ tile_sum, double* tile_dsum) {
+                              unsigned long long* __restrict__ tile_sum,
+                              unsigned long long* __restrict__ warp_sums) {
   __shared__ unsigned long long ws[SCAN_WARPS];
-  __shared__ double wd[SCAN_WARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)warp * SCAN_PER_WARP;
   unsigned long long acc = 0;
-  double dacc = 0.0;
+#pragma unroll
   for (int it = 0; it < SCAN_PER_WARP / 32; ++it) {
-    int64_t e = base + it * 32 + lane;
-    if (e < n) {
-      unsigned long long x = (unsigned long long)in[e];
-      acc += x;
-      dacc += (double)x;
-    }
+    const int64_t e = base + it * 32 + lane;
+    if (e < n) acc = sat_add(acc, (unsigned long long)in[e]);
   }
-  acc = warp_sum(acc);
-  for (int o = 16; o; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+  acc = warp_sat_sum(acc);
   if (lane == 0) {
     ws[warp] = acc;
-    wd[warp] = dacc;
+    warp_sums[(int64_t)blockIdx.x * SCAN_WARPS + warp] = acc;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
-    double d = 0.0;
-    for (int w = 0; w < SCAN_WARPS; ++w) {
-      t += ws[w];
-      d += wd[w];
-    }
+    for (int w = 0; w < SCAN_WARPS; ++w) t = sat_add(t, ws[w]);
     tile_sum[blockIdx.x] = t;
-    tile_dsum[blockIdx.x] = d;
   }
 }
 
-// Exclusive scan of the tile sums in one block; detects overflow past 2^63.
-__global__ void k_scan_tiles(unsigned long long* tile_sum, const double* tile_dsum, int64_t ntiles,
-                             unsigned* status) {
+// Exclusive scan of the tile sums in one block; flags a total past 2^63.
+__global__ void k_scan_tiles(unsigned long long* tile_sum, int64_t ntiles, unsigned* status) {
   __shared__ unsigned long long wsum[32];
   __shared__ unsigned long long carry_s;
-  __shared__ double dcarry_s;
+  __shared__ int sat_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
   if (threadIdx.x == 0) {
     carry_s = 0;
-    dcarry_s = 0.0;
+    sat_s = 0;
   }
   __syncthreads();
   for (int64_t base = 0; base < ntiles; base += blockDim.x) {
-    int64_t e = base + threadIdx.x;
-    unsigned long long x = e < ntiles ? tile_sum[e] : 0ull;
-    double dx = e < ntiles ? tile_dsum[e] : 0.0;
+    const int64_t e = base + threadIdx.x;
+    const unsigned long long x = e < ntiles ? tile_sum[e] : 0ull;
+    // a saturated tile, or a block sum that wraps, is an overflow
+    if (x >= (1ull << 63)) sat_s = 1;
     unsigned long long inc = warp_incl_scan(x);
     if (lane == 31) wsum[warp] = inc;
-    for (int o = 16; o; o >>= 1) dx += __shfl_xor_sync(0xffffffffu, dx, o);
     __syncthreads();
     if (warp == 0) {
       unsigned long long w = lane < nw ? wsum[lane] : 0ull;
@@ -203,41 +214,35 @@ __global__ void k_scan_tiles(unsigned long long* tile_sum, const double* tile_ds
       if (lane < nw) wsum[lane] = wi - w;
     }
     __syncthreads();
-    unsigned long long excl = carry_s + wsum[warp] + inc - x;
+    const unsigned long long excl = carry_s + wsum[warp] + inc - x;
     if (e < ntiles) tile_sum[e] = excl;
+    // the first prefix to reach 2^63 is computed exactly (every earlier one
+    // and every tile sum are below 2^63), so checking each prefix suffices
+    if (excl + x >= (1ull << 63)) sat_s = 1;
     __syncthreads();
-    if (lane == 0) atomicAdd(&dcarry_s, dx);
     if (threadIdx.x == blockDim.x - 1) carry_s = excl + x;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     tile_sum[ntiles] = carry_s;
-    if (dcarry_s >= 9.2e18) atomicOr(status, DEV_OVERFLOW);
+    if (sat_s || carry_s >= (1ull << 63)) atomicOr(status, DEV_OVERFLOW);
   }
 }
 
 template <typename Tin>
 __global__ void k_scan_apply(const Tin* __restrict__ in, unsigned long long* __restrict__ out,
                              int64_t n, const unsigned long long* __restrict__ tile_off,
-                             bool inclusive) {
-  __shared__ unsigned long long ws[SCAN_WARPS];
+                             const unsigned long long* __restrict__ warp_sums, bool inclusive) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)warp * SCAN_PER_WARP;
-  unsigned long long tot = 0;
-  for (int it = 0; it < SCAN_PER_WARP / 32; ++it) {
-    int64_t e = base + it * 32 + lane;
-    if (e < n) tot += (unsigned long long)in[e];
-  }
-  tot = warp_sum(tot);
-  if (lane == 0) ws[warp] = tot;
-  __syncthreads();
   unsigned long long carry = tile_off[blockIdx.x];
-  for (int w = 0; w < warp; ++w) carry += ws[w];
+  for (int w = 0; w < warp; ++w) carry += warp_sums[(int64_t)blockIdx.x * SCAN_WARPS + w];
   const int shift = inclusive ? 0 : 1;
+#pragma unroll 4
   for (int it = 0; it < SCAN_PER_WARP / 32; ++it) {
-    int64_t e = base + it * 32 + lane;
-    unsigned long long x = e < n ? (unsigned long long)in[e] : 0ull;
-    unsigned long long inc = warp_incl_scan(x);
+    const int64_t e = base + it * 32 + lane;
+    const unsigned long long x = e < n ? (unsigned long long)in[e] : 0ull;
+    const unsigned long long inc = warp_incl_scan(x);
     if (e < n) out[e + shift] = carry + inc;
     carry += __shfl_sync(0xffffffffu, inc, 31);
   }
@@ -252,13 +257,12 @@ static void scan_impl(const Tin* in, uint64_t* out, int64_t n, bool inclusive, u
     if (!inclusive) cudaMemsetAsync(out, 0, sizeof(uint64_t), st);
     return;
   }
-  // tmp layout: [ntiles+1] u64 sums, then ntiles doubles (same byte size)
   unsigned long long* ts = reinterpret_cast<unsigned long long*>(tmp);
-  double* td = reinterpret_cast<double*>(tmp + ntiles + 2);
-  CTD_LAUNCH(k_scan_reduce<Tin>, ((unsigned)ntiles), (SCAN_WARPS * 32), 0, st, in, n, ts, td);
-  CTD_LAUNCH(k_scan_tiles, (1), (1024), 0, st, ts, td, ntiles, status);
-  CTD_LAUNCH(k_scan_apply<Tin>, ((unsigned)ntiles), (SCAN_WARPS * 32), 0, st, 
-      in, reinterpret_cast<unsigned long long*>(out), n, ts, inclusive);
+  unsigned long long* wsums = ts + ntiles + 2;
+  CTD_LAUNCH(k_scan_reduce<Tin>, ((unsigned)ntiles), (SCAN_WARPS * 32), 0, st, in, n, ts, wsums);
+  CTD_LAUNCH(k_scan_tiles, (1), (1024), 0, st, ts, ntiles, status);
+  CTD_LAUNCH(k_scan_apply<Tin>, ((unsigned)ntiles), (SCAN_WARPS * 32), 0, st, in,
+             reinterpret_cast<unsigned long long*>(out), n, ts, wsums, inclusive);
 }
 
 void launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, bool inclusive, uint64_t* tmp,

@@ -171,3 +171,20 @@ def test_traffic_10m_full_size(traffic_full):
     cols = np.concatenate([rng.choice(nz, 200, replace=False),
                            nz[np.argsort(np.diff(ref.X.ptr)[nz])[-20:]], [0, ref.X.n_cols - 1]])
     check(F, ref, 1e-6, 1, full_c=False, c_cols=cols, err_ref=O.projection_error(ref.X, ref.R))
+
+
+def test_sqnorm_range():
+    """||X||_F^2 must stay below 2^63 (the int64 CDF, reading A12): three
+    values of 2^31 - 1 pass it and the call reports CTD_EOVERFLOW; two stay
+    below it and the call succeeds with the exact total."""
+    m = ctd()
+    big = 2 ** 31 - 1
+    i, j, k = np.array([0, 1, 2]), np.array([0, 1, 2]), np.array([0, 0, 1])
+    coo = synth.Coo3((4, 3, 2), i, j, k, np.full(3, big, np.int64))
+    with pytest.raises(m.CtdError) as e:
+        run(coo, 1, 5, 1e-6, 0, 0)
+    assert e.value.status == "CTD_EOVERFLOW"
+    coo2 = synth.Coo3((4, 3, 2), i[:2], j[:2], k[:2], np.full(2, big, np.int64))
+    F = run(coo2, 1, 64, 1e-6, 0, 0)
+    assert F.sizes().sqnorm_X == float(2 * big * big)
+    assert F.sizes().s_kept == 2
