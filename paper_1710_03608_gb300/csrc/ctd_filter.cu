@@ -61,33 +61,33 @@ __global__ void k_gather_cols(const double* __restrict__ A, int64_t lda, int64_t
 // for every suspect c at once: a sparse-times-dense product by rows.  A
 // warp takes row i of the candidates' by-row layout, broadcasts the row's
 // entries (32 at a time, in column order) and each lane updates suspects
-// c = lane, lane + 32, ... (up to RS_CHUNK per pass) with the kept entries'
-// eta rows (etaT, kept x ns row-major), so a row is read once for all
-// suspects; the order of operations per (i, c) is fixed (reproducible
-// ratios and decisions).  sus_of[cc] = c if candidate cc is suspect c, else
+// c = lane, lane + 32, ... (32 NPL per pass) with the kept entries' eta
+// rows (etaT, kept x ns row-major), the eta loads of eight entries in flight
+// together, so a row is read once for all suspects; the order of operations
+// per (i, c) is fixed (reproducible ratios and decisions).  sus_of[cc] = c if candidate cc is suspect c, else
 // -1: that entry is x_k's own value.  With init = 0 the products are
 // subtracted from the residual already in rbuf (the refinement step).  eta
 // is zero for kept candidates after k_c.  The R^(t) part, Q gamma_c, is
 // subtracted afterwards by a GEMM.  (A thread per (row, suspect) walked the
 // long rows, those of the frequent mode-alpha indices, as chains of
 // dependent loads, once per suspect.)
-constexpr int RS_PER_LANE = 8;
-constexpr int RS_CHUNK = 32 * RS_PER_LANE;
-
+template <int NPL>  // suspects per lane per pass (32 * NPL per pass)
 __global__ void __launch_bounds__(256)
     k_resid_rows(int64_t n_rows, const unsigned long long* __restrict__ crp,
                  const int32_t* __restrict__ ccol, const int32_t* __restrict__ cval,
                  const int* __restrict__ kpos, const int* __restrict__ sus_of,
                  const double* __restrict__ etaT, int ns, int init, double* __restrict__ rbuf) {
+  constexpr int CH = 32 * NPL;
+  constexpr int EU = 8;  // entries whose eta loads are in flight together
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = gw; i < n_rows; i += nw) {
     const unsigned long long a = crp[i], b = crp[i + 1];
-    for (int c0 = 0; c0 < ns; c0 += RS_CHUNK) {
-      double acc[RS_PER_LANE];
+    for (int c0 = 0; c0 < ns; c0 += CH) {
+      double acc[NPL];
 #pragma unroll
-      for (int u = 0; u < RS_PER_LANE; ++u) acc[u] = 0.0;
+      for (int w = 0; w < NPL; ++w) acc[w] = 0.0;
       for (unsigned long long base = a; base < b; base += 32) {
         const int cnt = (int)min((unsigned long long)32, b - base);
         int q = -1, sc = -1;
@@ -98,34 +98,64 @@ __global__ void __launch_bounds__(256)
           q = kpos[cc];
           sc = sus_of[cc];
         }
-        for (int e = 0; e < cnt; ++e) {
-          const int qe = __shfl_sync(0xffffffffu, q, e);
-          const int se = __shfl_sync(0xffffffffu, sc, e);
-          const double ve = __shfl_sync(0xffffffffu, v, e);
-          if (qe >= 0) {
-            const double* er = etaT + (int64_t)qe * ns + c0 + lane;
+        for (int e0 = 0; e0 < cnt; e0 += EU) {
+          int qe[EU];
+          double ve[EU], ld[EU][NPL];
 #pragma unroll
-            for (int u = 0; u < RS_PER_LANE; ++u)
-              if (c0 + lane + 32 * u < ns) acc[u] = fma(-ve, er[32 * u], acc[u]);
+          for (int u = 0; u < EU; ++u) {  // lanes past cnt carry q = -1
+            qe[u] = __shfl_sync(0xffffffffu, q, e0 + u);
+            ve[u] = __shfl_sync(0xffffffffu, v, e0 + u);
+#pragma unroll
+            for (int w = 0; w < NPL; ++w) {
+              const int c = c0 + lane + 32 * w;
+              ld[u][w] = (qe[u] >= 0 && c < ns) ? etaT[(int64_t)qe[u] * ns + c] : 0.0;
+            }
           }
-          if (init && se >= c0 && se < c0 + RS_CHUNK) {
-            // x_k(i), the suspect's own entry (static indices keep acc in registers)
-            const int us = (se - c0) >> 5, ls = (se - c0) & 31;
 #pragma unroll
-            for (int u = 0; u < RS_PER_LANE; ++u) acc[u] += (u == us && lane == ls) ? ve : 0.0;
+          for (int u = 0; u < EU; ++u)
+#pragma unroll
+            for (int w = 0; w < NPL; ++w) acc[w] = fma(-ve[u], ld[u][w], acc[w]);
+          if (init) {
+            // x_k(i), the suspect's own entry (static indices keep acc in registers)
+#pragma unroll
+            for (int u = 0; u < EU; ++u) {
+              const int se = __shfl_sync(0xffffffffu, sc, e0 + u);
+              if (se >= c0 && se < c0 + CH) {
+                const int us = (se - c0) >> 5, ls = (se - c0) & 31;
+#pragma unroll
+                for (int w = 0; w < NPL; ++w) acc[w] += (w == us && lane == ls) ? ve[u] : 0.0;
+              }
+            }
           }
         }
       }
 #pragma unroll
-      for (int u = 0; u < RS_PER_LANE; ++u) {
-        const int c = c0 + lane + 32 * u;
+      for (int w = 0; w < NPL; ++w) {
+        const int c = c0 + lane + 32 * w;
         if (c < ns) {
           double* r = rbuf + (int64_t)c * n_rows + i;
-          *r = init ? acc[u] : *r + acc[u];
+          *r = init ? acc[w] : *r + acc[w];
         }
       }
     }
   }
+}
+
+static void launch_resid_rows(int64_t n_rows, const uint64_t* crp, const int32_t* ccol,
+                              const int32_t* cval, const int* kpos, const int* sus_of,
+                              const double* etaT, int ns, int init, double* rbuf,
+                              cudaStream_t st) {
+  const unsigned g = grid_for(n_rows * 32, 256, (int64_t)num_sms() * 16);  // a warp per row
+  const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(crp);
+  if (ns <= 32)
+    CTD_LAUNCH(k_resid_rows<1>, (g), (256), 0, st, n_rows, rp, ccol, cval, kpos, sus_of, etaT, ns,
+               init, rbuf);
+  else if (ns <= 64)
+    CTD_LAUNCH(k_resid_rows<2>, (g), (256), 0, st, n_rows, rp, ccol, cval, kpos, sus_of, etaT, ns,
+               init, rbuf);
+  else
+    CTD_LAUNCH(k_resid_rows<4>, (g), (256), 0, st, n_rows, rp, ccol, cval, kpos, sus_of, etaT, ns,
+               init, rbuf);
 }
 
 // etaT[q * ns + c] = eta[q + c * kept]
@@ -331,11 +361,9 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
     CTD_CUDA(cudaMemsetAsync(sus_of, 0xff, (size_t)du * sizeof(int), st));  // -1
     CTD_LAUNCH(k_sus_of, (grid_for(ns, 256, 64)), (256), 0, st, d_sus, ns, sus_of);
     const unsigned gt = grid_for((int64_t)kk * ns, 256, (int64_t)num_sms() * 8);
-    const unsigned grows = grid_for(in.n_rows * 32, 256, (int64_t)num_sms() * 16);  // a warp per row
     if (kept > 0) CTD_LAUNCH(k_transpose_eta, (gt), (256), 0, st, eta, kept, ns, etaT);
-    CTD_LAUNCH(k_resid_rows, (grows), (256), 0, st, in.n_rows,
-               reinterpret_cast<const unsigned long long*>(in.c_rowptr), in.c_col, in.c_val, kpos,
-               sus_of, etaT, ns, 1, rbuf);
+    launch_resid_rows(in.n_rows, in.c_rowptr, in.c_col, in.c_val, kpos, sus_of, etaT, ns, 1, rbuf,
+                      st);
     // minus Q gamma (Q = Qt^T, n_rows x dt)
     if (in.dt > 0)
       dgemm(true, false, in.n_rows, ns, in.dt, -1.0, in.Qt, in.ldq, gammaQ, in.dt, 1.0, rbuf,
@@ -384,9 +412,8 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
       }
       // r -= Xc[:, K] eta_d, then r -= Q (h_Q - W_K eta_d)
       if (kept > 0) CTD_LAUNCH(k_transpose_eta, (gt), (256), 0, st, etad, kept, ns, etaT);
-      CTD_LAUNCH(k_resid_rows, (grows), (256), 0, st, in.n_rows,
-                 reinterpret_cast<const unsigned long long*>(in.c_rowptr), in.c_col, in.c_val,
-                 kpos, sus_of, etaT, ns, 0, rbuf);
+      launch_resid_rows(in.n_rows, in.c_rowptr, in.c_col, in.c_val, kpos, sus_of, etaT, ns, 0,
+                        rbuf, st);
       if (in.dt > 0) {
         if (kept > 0)
           dgemm(false, false, in.dt, ns, kept, -1.0, WK, in.dt, etad, kept, 1.0, hQ, in.dt, st);

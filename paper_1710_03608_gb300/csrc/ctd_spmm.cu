@@ -449,22 +449,46 @@ ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_
   return rc;
 }
 
-// Sort each row of a row-major factor by column (rank by counting; rows are
-// short).  One warp per row; in/out arrays differ.
-__global__ void k_sort_rows(const unsigned long long* __restrict__ rowptr, int64_t n_rows,
-                            const int32_t* __restrict__ col_in, const int32_t* __restrict__ val_in,
-                            int32_t* __restrict__ col_out, int32_t* __restrict__ val_out) {
-  const int lane = threadIdx.x & 31;
+// Sort each row of a row-major factor by column: one warp per row, each
+// entry placed at its rank (the number of smaller columns; columns within a
+// row are distinct).  Rows of up to SR_SMEM entries are ranked against a
+// copy of their columns in the warp's shared memory (the long rows, those
+// of the frequent mode-alpha indices, would otherwise rescan global memory
+// once per entry); longer rows rank against global memory.  In/out arrays
+// differ.
+constexpr int SR_SMEM = 512;
+
+__global__ void __launch_bounds__(256)
+    k_sort_rows(const unsigned long long* __restrict__ rowptr, int64_t n_rows,
+                const int32_t* __restrict__ col_in, const int32_t* __restrict__ val_in,
+                int32_t* __restrict__ col_out, int32_t* __restrict__ val_out) {
+  __shared__ int32_t keys[8][SR_SMEM];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int32_t* kw = keys[wib];
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = gw; i < n_rows; i += nw) {
     const unsigned long long a = rowptr[i], b = rowptr[i + 1];
-    for (unsigned long long p = a + lane; p < b; p += 32) {
-      const int m = col_in[p];
-      unsigned long long r = 0;
-      for (unsigned long long q = a; q < b; ++q) r += (col_in[q] < m);
-      col_out[a + r] = m;
-      val_out[a + r] = val_in[p];
+    const int len = (int)(b - a);
+    if (len <= SR_SMEM) {
+      for (int e = lane; e < len; e += 32) kw[e] = col_in[a + e];
+      __syncwarp();
+      for (int e = lane; e < len; e += 32) {
+        const int m = kw[e];
+        int r = 0;
+        for (int q = 0; q < len; ++q) r += (kw[q] < m);
+        col_out[a + r] = m;
+        val_out[a + r] = val_in[a + e];
+      }
+      __syncwarp();
+    } else {
+      for (unsigned long long p = a + lane; p < b; p += 32) {
+        const int m = col_in[p];
+        unsigned long long r = 0;
+        for (unsigned long long q = a; q < b; ++q) r += (col_in[q] < m);
+        col_out[a + r] = m;
+        val_out[a + r] = val_in[p];
+      }
     }
   }
 }
