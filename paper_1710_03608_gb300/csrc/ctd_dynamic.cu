@@ -297,6 +297,19 @@ __global__ void k_i32_to_i64(const int* __restrict__ in, int n, int64_t* __restr
 }
 
 // y += x (n entries)
+// Y(:, idx[c]) += X(:, c) (or = when add is 0), m rows, for c < n
+__global__ void k_scatter_cols_f64(const double* __restrict__ X, int64_t ldx, int64_t m,
+                                   const int* __restrict__ idx, int n, int add,
+                                   double* __restrict__ Y, int64_t ldy) {
+  const int64_t total = m * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % m, c = e / m;
+    double* y = Y + r + (int64_t)idx[c] * ldy;
+    *y = add ? *y + X[r + c * ldx] : X[r + c * ldx];
+  }
+}
+
 __global__ void k_axpy_f64(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
@@ -602,14 +615,44 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
             const unsigned gk = grid_for(dtc * kr, 256, (int64_t)num_sms() * 8);
             CTD_LAUNCH(k_gather_cols_f64, (gk), (256), 0, st, W, dtc, dtc, idx, kr, WKs, dtc);
             dgemm(true, false, nr, kr, dtc, -1.0, F->Qt, ld, WKs, dtc, 1.0, V, nr, st);
-            // the second pass holds the new vectors orthogonal to ~u / rho for
-            // a residual ratio rho >= eps (and adds its coefficients to W_K):
-            // every later decision is taken against this basis
-            double* Hm;
-            CTD_TRY(scratch.get(&Hm, (size_t)dtc * kr));
-            dgemm(false, false, dtc, kr, nr, 1.0, F->Qt, ld, V, nr, 0.0, Hm, dtc, st);
-            dgemm(true, false, nr, kr, dtc, -1.0, F->Qt, ld, Hm, dtc, 1.0, V, nr, st);
-            CTD_LAUNCH(k_axpy_f64, (gk), (256), 0, st, dtc * kr, Hm, WKs);
+            // a second pass holds the new vectors orthogonal to ~u / rho for a
+            // residual ratio rho >= eps (and adds its coefficients to W_K):
+            // every later decision is taken against this basis.  A vector
+            // whose first pass kept at least 1/sqrt(2) of its norm is
+            // orthogonal to working accuracy after that pass (Kahan's
+            // criterion, as given in Parlett, The Symmetric Eigenvalue
+            // Problem), so in FP32 bulk mode only the weaker vectors take the
+            // second pass; FP64 mode (error bar 1e-10) takes it for all.
+            std::vector<int> weak;
+            for (int c = 0, seen = 0; c < dur && seen < kr; ++c) {
+              if (!fo.keep_h[c]) continue;
+              if (!fp32 || fo.piv_h[c] < 0.5 * fo.xn_h[c]) weak.push_back(seen);
+              ++seen;
+            }
+            const int nwk = (int)weak.size();
+            if (nwk == kr) {
+              double* Hm;
+              CTD_TRY(scratch.get(&Hm, (size_t)dtc * kr));
+              dgemm(false, false, dtc, kr, nr, 1.0, F->Qt, ld, V, nr, 0.0, Hm, dtc, st);
+              dgemm(true, false, nr, kr, dtc, -1.0, F->Qt, ld, Hm, dtc, 1.0, V, nr, st);
+              CTD_LAUNCH(k_axpy_f64, (gk), (256), 0, st, dtc * kr, Hm, WKs);
+            } else if (nwk > 0) {
+              int* d_weak;
+              double *Vw, *Hm;
+              CTD_TRY(scratch.get(&d_weak, nwk));
+              CTD_TRY(scratch.get(&Vw, (size_t)nr * nwk));
+              CTD_TRY(scratch.get(&Hm, (size_t)dtc * nwk));
+              CTD_CUDA(cudaMemcpyAsync(d_weak, weak.data(), nwk * sizeof(int),
+                                       cudaMemcpyHostToDevice, st));
+              const unsigned gv = grid_for(nr * nwk, 256, (int64_t)num_sms() * 8);
+              const unsigned gh = grid_for(dtc * nwk, 256, (int64_t)num_sms() * 8);
+              CTD_LAUNCH(k_gather_cols_f64, (gv), (256), 0, st, V, nr, nr, d_weak, nwk, Vw, nr);
+              dgemm(false, false, dtc, nwk, nr, 1.0, F->Qt, ld, Vw, nr, 0.0, Hm, dtc, st);
+              dgemm(true, false, nr, nwk, dtc, -1.0, F->Qt, ld, Hm, dtc, 1.0, Vw, nr, st);
+              CTD_LAUNCH(k_scatter_cols_f64, (gv), (256), 0, st, Vw, nr, nr, d_weak, nwk, 0, V, nr);
+              CTD_LAUNCH(k_scatter_cols_f64, (gh), (256), 0, st, Hm, dtc, dtc, d_weak, nwk, 1, WKs,
+                         dtc);
+            }
             CTD_LAUNCH(k_transpose_f64, (gk), (256), 0, st, WKs, dtc, dtc, kr, F->L + dtc, ld);
             if (dt0 > 0)
               CTD_CUDA(cudaMemcpy2DAsync(rec.WK + (size_t)kept_total * dt0, (size_t)dt0 * 8, WKs,
