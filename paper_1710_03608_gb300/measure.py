@@ -241,6 +241,50 @@ def ddos(args):
     print(json.dumps(line), flush=True)
 
 
+def sweep(args):
+    """Sample-size sweep (Section 4, the experiment behind Fig. 4): CTD-S for
+    s = 1 ... 1000 on a tensor shaped like the Haggle contact data of
+    Table 3 (77 x 274 x 1567, 27,972 nonzeros; Zipf(1.2) ids, uniform time,
+    Poisson(3)+1 counts) and on the 10^7-nonzero traffic tensor. Per s: the
+    relative error, the kept count s~ (bounded by the rank of X_(1), at most
+    77 on the first tensor), the device time of a call, and the memory of
+    the result (R as CSC, U dense, C as CSC with 16-bit rows)."""
+    tensors = [("haggle-shaped 77x274x1567, 27972 nnz",
+                synth.traffic((77, 274, 1567), 27972, 1.2, 1.2, "poisson1", 2001, 3.0)),
+               ("traffic 10000x10000x1000, 1e7 nnz", synth.traffic_10m())]
+    if args.small_only:
+        tensors = tensors[:1]
+    svals = [1, 2, 5, 10, 20, 50, 100, 200, 500, 1000]
+    out = []
+    for name, coo in tensors:
+        X = ctd.Coo.from_synth(coo)
+        for _ in range(2):
+            ctd.ctd_static(X, 1, 50, 1e-6, 0, ctd.CTD_FP32_BULK).free()
+        rows = []
+        for s_ in svals:
+            times = []
+            for rep in range(args.reps):
+                _sync()
+                t0 = time.perf_counter()
+                F = ctd.ctd_static(X, 1, s_, 1e-6, rep, ctd.CTD_FP32_BULK)
+                e = F.error()
+                _sync()
+                times.append(time.perf_counter() - t0)
+                sz = F.sizes()
+                if rep == 0:
+                    row = {"s": s_, "s_unique": int(sz.s_unique), "s_kept": int(sz.s_kept),
+                           "rel_error": e, "nnz_R": int(sz.nnz_R), "nnz_C": int(sz.nnz_C),
+                           "memory_bytes": int(12 * sz.nnz_R + 8 * (sz.s_kept + 1)
+                                               + 8 * sz.s_kept ** 2 + 6 * sz.nnz_C
+                                               + 12 * (sz.n_cols + 1))}
+                F.free()
+            row["ms_median"] = 1e3 * float(np.median(times))
+            rows.append(row)
+        out.append({"tensor": name, "nnz": int(coo.nnz), "rows": rows})
+    print(json.dumps({"workload": "CTD-S sample-size sweep, FP32_BULK, eps = 1e-6", "runs": out}),
+          flush=True)
+
+
 # ---------------------------------------------------------------------------
 # summaries of ncu output (text in, text out; no GPU)
 # ---------------------------------------------------------------------------
@@ -344,6 +388,9 @@ def main():
     sm.add_argument("--steps", type=int, default=100)
     sm.add_argument("--scale", type=float, default=1.0)
     sm.add_argument("--d", type=int, default=400)
+    sw = sub.add_parser("sweep")
+    sw.add_argument("--reps", type=int, default=3)
+    sw.add_argument("--small-only", action="store_true")
     dd = sub.add_parser("ddos")
     dd.add_argument("--steps", type=int, default=48)
     dd.add_argument("--scale", type=float, default=1.0)
@@ -359,7 +406,8 @@ def main():
     import torch
     torch.cuda.set_device(0)
     ctd.load()
-    {"batched": batched, "serving": serving, "stream": stream, "ddos": ddos}[args.cmd](args)
+    {"batched": batched, "serving": serving, "stream": stream, "ddos": ddos,
+     "sweep": sweep}[args.cmd](args)
 
 
 if __name__ == "__main__":
