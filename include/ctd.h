@@ -219,6 +219,30 @@ CTD_API ctd_status ctd_get_C_columns(const ctd_factors* F, int64_t ncols, const 
  * row[nnz_C], val[nnz_C]. */
 CTD_API ctd_status ctd_get_C(const ctd_factors* F, int64_t* colptr, int32_t* row, double* val);
 
+/*
+ * ctd_dynamic_from_static -- a CTD-D state that starts from CTD-S factors of
+ * the historical part of a tensor, as in the paper's CTD-D experiments
+ * (Sec. 4, "Performance of CTD-D": the first 80% of the time mode is the
+ * history, decomposed by CTD-S; later slices arrive one by one).  The
+ * tensor of S must have time as mode 3 and S alpha 1 or 2; the state's
+ * slices are dims[0] x dims[1].  A fiber f = w + W k of S (W the slice's
+ * column count, A1) becomes slice fiber w of time step k.  R is copied;
+ * L (Cholesky factor of R^T R) and the orthonormal basis Q come from R's
+ * exact Gram matrix and the same orthonormalization as a step's new
+ * columns; C of the history is record 0 (ctd_get_step(0) describes the
+ * history: d' = s', Delta d~ = s~), so the state's columns are the
+ * history's N_alpha columns followed by W per later step.  The next step's
+ * draws use counter step = dims[2] (the time index of the slice).
+ *  S          CTD-S factors computed with C and the error (no skip flags);
+ *             not modified
+ *  stream_id, flags   as for ctd_dynamic_create
+ *  stream     CUDA stream of the state
+ * CTD_EINVAL: NULL arguments, S not CTD-S, alpha 3, or C or the error
+ * skipped; CTD_ENOTSUP: R's columns numerically dependent.
+ */
+CTD_API ctd_status ctd_dynamic_from_static(const ctd_factors* S, uint64_t stream_id,
+                                           unsigned flags, void* stream, ctd_factors** state);
+
 /* CTD-D: per-step record.  info = {d', Delta d~, d~_t before the step,
  * nnz of the slice}, sq = {||dX||^2, ||dX - P dX||^2}. */
 CTD_API ctd_status ctd_get_step(const ctd_factors* F, int64_t t, int64_t info[4], double sq[2]);

@@ -20,6 +20,8 @@ What each function follows:
   relative_error_dense   Eq. (error), brute force on small inputs
   projection_error       Lemma 3.2 (Eqs. 4-7): error = ||X - R R^+ X||^2/||X||^2
   ddos_candidates        Section 5, detection rule on R's fibers
+  dynamic_state_from_static   Section 4's CTD-D setting: CTD-S factors of the
+                         history as the starting state of Algorithm 2
 
 Readings of points the paper leaves open (same letters everywhere):
   A1 column order of X_(alpha): little-endian over the other modes
@@ -481,6 +483,33 @@ def ctd_d_step(state: DynamicState, dims2, i, j, val, d: int, eps: float,
     state.err_den += Ts
     state.t += 1
     return StepResult(Id, Iu, np.asarray(kept, np.int64), new_f, M, C_new, Ts, np.asarray(ratios))
+
+
+def dynamic_state_from_static(res: StaticResult, dims3, track_c: bool = True,
+                              keep_X: bool = False) -> DynamicState:
+    """The starting state of the paper's CTD-D experiments (Section 4,
+    performance of CTD-D): the history, the first time slices of a tensor
+    whose third mode is time, decomposed by Algorithm 1 (alpha = 1), then
+    extended slice by slice by Algorithm 2.  A column f = j + J k of the
+    history (reading A1) is fiber j of time step k; C^(t) of the history is
+    Eq. (3)'s C = R^T X_(1); the error bookkeeping starts from the
+    history's ||X - R R^+ X||^2 (Lemma 3.2) over ||X||^2.  The next step is
+    time step K (its draws use that counter)."""
+    I, J, K = (int(d) for d in dims3)
+    st = DynamicState(I, J)
+    st.track_c = track_c
+    st.R_cols = [res.R[:, c].astype(np.float64) for c in range(res.R.shape[1])]
+    st.fibers = [(int(f) // J, int(f) % J) for f in res.fibers]
+    st.U = res.U.copy() if st.R_cols else None
+    if track_c:
+        st.C = (c_full(res.X, res.R).toarray().astype(np.float64) if st.R_cols
+                else np.zeros((0, res.X.n_cols)))
+    if keep_X:
+        st.X_blocks.append(res.X)
+    st.t = K
+    st.err_num = projection_error(res.X, res.R) * float(res.T) if res.T else 0.0
+    st.err_den = int(res.T)
+    return st
 
 
 def dynamic_error_dense(state: DynamicState) -> float:

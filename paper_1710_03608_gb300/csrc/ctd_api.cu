@@ -358,6 +358,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   }
   STEP(status_from_device(status));
   F->T = T;
+  F->min_val = minval;
   F->s_unique = s_unique;
   if (T == 0) F->s = 0;  // nothing to draw from
   const int su = s_unique;

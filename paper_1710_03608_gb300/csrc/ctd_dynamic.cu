@@ -40,6 +40,8 @@ constexpr double WEAK_KEEP = 1e-8;
 
 struct StepRec {
   int64_t d_draws = 0, d_unique = 0, d_kept = 0, d_before = 0, nnz = 0;
+  int64_t ncols = 0;               // columns of X_(alpha) this record covers (a slice: J;
+                                   // a seeded history: J times its time slices)
   double sq = 0.0, err = 0.0;      // ||dX||^2 and ||dX - P dX||^2
   double* WK = nullptr;            // W_K = L^(t)^{-1} R^(t)^T dR: d_before x d_kept
   double* M = nullptr;             // Y_K = L^(t)^{-T} W_K = U^(t) R^(t)^T dR, computed on
@@ -138,7 +140,8 @@ __global__ void k_add_offset(const unsigned long long* __restrict__ in, int64_t 
 struct ctd_factors::Dyn {
   int64_t I = 0, J = 0;
   unsigned flags = 0;
-  int64_t t = 0;
+  int64_t t = 0;                     // records so far (a seeded history is record 0)
+  int64_t hist_k = 0;                // time slices of a seeded history (0: none)
   int64_t cap_d = 0;                 // leading dimension of U
   int64_t cap_cols = 0, cap_nnz = 0, cap_fib = 0;
   std::vector<StepRec> steps;
@@ -152,6 +155,12 @@ struct ctd_factors::Dyn {
   int64_t* lastI = nullptr;          // device [8192]
   int64_t* lastIu = nullptr;
 };
+
+// time index of the next incoming slice (the Philox counter's step and the
+// step recorded with the fibers it contributes)
+static inline int64_t next_time(const ctd_factors::Dyn& D) {
+  return D.hist_k > 0 ? D.hist_k + (D.t - 1) : D.t;
+}
 
 ctd_factors::~ctd_factors() {
   if (dyn) {
@@ -403,6 +412,48 @@ static ctd_status grow_array(T** p, int64_t used, int64_t need, int64_t* cap, cu
   return CTD_OK;
 }
 
+// The new columns' residuals V (nr x kr, orthogonal to range(Q) already)
+// become kr new basis vectors: V2 = V L_S^{-T} (L_S the filter's factor of
+// their Schur complement, Li its inverse) is orthonormal up to the filter's
+// rounding and one Cholesky-QR pass makes it so to working precision.  If
+// that pass meets a non-positive pivot (V2 too far from orthonormal), the
+// residuals are orthonormalized from scratch: unit columns, one shifted
+// Cholesky-QR pass, then two plain ones (Fukaya et al., SIAM J. Sci. Comput.
+// 42(1), 2020).  Lam^T = Q_new^T V (upper triangular up to rounding) gives
+// L's new diagonal block; Q_new^T goes into Qt after the first dtc rows and
+// the row norms of Q grow by those of Q_new.  V2 and Vq are nr x kr scratch.
+static ctd_status finish_basis(ctd_factors* F, int64_t dtc, int kr, double* V, double* V2,
+                               double* Vq, const double* Li, int64_t ldli, Arena& scratch,
+                               cudaStream_t st) {
+  const int64_t nr = F->n_rows, ld = F->dyn->cap_d;
+  dgemm(false, true, nr, kr, kr, 1.0, V, nr, Li, ldli, 0.0, V2, nr, st);
+  bool ok = false;
+  CTD_TRY(cholqr_pass(V2, nr, kr, 0.0, Vq, scratch, st, &ok));
+  if (!ok) {
+    double* V0;  // the residuals themselves, for Lam below
+    CTD_TRY(scratch.get(&V0, (size_t)nr * kr));
+    CTD_CUDA(cudaMemcpyAsync(V0, V, (size_t)nr * kr * 8, cudaMemcpyDeviceToDevice, st));
+    CTD_LAUNCH(k_unit_columns, ((unsigned)std::min(kr, 4096)), (256), 0, st, V, nr, kr);
+    const double u = 1.1102230246251565e-16;
+    const double shift = 11.0 * ((double)nr * kr + (double)kr * (kr + 1)) * u * kr;
+    CTD_TRY(cholqr_pass(V, nr, kr, shift, V2, scratch, st, &ok));
+    if (ok) CTD_TRY(cholqr_pass(V2, nr, kr, 0.0, V, scratch, st, &ok));
+    if (ok) CTD_TRY(cholqr_pass(V, nr, kr, 0.0, Vq, scratch, st, &ok));
+    if (!ok) return fail(CTD_ENOTSUP, "new basis vectors are numerically dependent");
+    V = V0;
+  }
+  double* Lam;
+  CTD_TRY(scratch.get(&Lam, (size_t)kr * kr));
+  dgemm(true, false, kr, kr, nr, 1.0, Vq, nr, V, nr, 0.0, Lam, kr, st);
+  CTD_LAUNCH(k_lower_from_upper_T, (grid_for((int64_t)kr * kr, 256, (int64_t)num_sms() * 4)),
+             (256), 0, st, Lam, kr, kr, F->L + dtc + dtc * ld, ld);
+  CTD_LAUNCH(k_transpose_f64, (grid_for(nr * kr, 256, (int64_t)num_sms() * 8)), (256), 0, st, Vq,
+             nr, nr, kr, F->Qt + dtc, ld);
+  CTD_LAUNCH(k_qn_add, (grid_for(nr, 256, (int64_t)num_sms() * 4)), (256), 0, st, F->Qt, ld, dtc,
+             kr, nr, F->qn);
+  return CTD_OK;
+}
+
 extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int64_t d, double eps,
                                        void* stream) {
   if (!F || !dXd) return fail(CTD_EINVAL, "NULL argument");
@@ -424,6 +475,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   rec.d_draws = d;
   rec.d_before = dt;
   rec.nnz = X.nnz;
+  rec.ncols = F->n_cols;
 
   // lines 1-4
   Matricized M;
@@ -435,7 +487,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   CTD_TRY(scratch.get(&d_count, 4));
   {
     PhaseScope ph("d_sample_unique", st);
-    launch_sample(M.cdf, M.n_cols, d, F->seed, (uint64_t)D.t, F->stream_id, D.lastI, st);
+    launch_sample(M.cdf, M.n_cols, d, F->seed, (uint64_t)next_time(D), F->stream_id, D.lastI, st);
     launch_sort_unique(D.lastI, d, D.lastIu, d_count, st);
   }
   unsigned status = 0;
@@ -659,40 +711,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
                                          (size_t)dtc * 8, (size_t)dt0 * 8, kr,
                                          cudaMemcpyDeviceToDevice, st));
           }
-          // V2 = V L_S^{-T} is orthonormal up to the filter's rounding; one
-          // Cholesky-QR pass makes it so to working precision.  If that pass
-          // meets a non-positive pivot (V2 too far from orthonormal), the
-          // residuals are orthonormalized from scratch: unit columns, one
-          // shifted Cholesky-QR pass, then two plain ones (Fukaya et al.,
-          // SIAM J. Sci. Comput. 42(1), 2020).
-          dgemm(false, true, nr, kr, kr, 1.0, V, nr, Li, ldli, 0.0, V2, nr, st);
-          bool ok = false;
-          CTD_TRY(cholqr_pass(V2, nr, kr, 0.0, Vq, scratch, st, &ok));
-          if (!ok) {
-            double* V0;  // the residuals themselves, for Lam below
-            CTD_TRY(scratch.get(&V0, (size_t)nr * kr));
-            CTD_CUDA(cudaMemcpyAsync(V0, V, (size_t)nr * kr * 8, cudaMemcpyDeviceToDevice, st));
-            CTD_LAUNCH(k_unit_columns, ((unsigned)std::min(kr, 4096)), (256), 0, st, V, nr, kr);
-            const double u = 1.1102230246251565e-16;
-            const double shift = 11.0 * ((double)nr * kr + (double)kr * (kr + 1)) * u * kr;
-            CTD_TRY(cholqr_pass(V, nr, kr, shift, V2, scratch, st, &ok));
-            if (ok) CTD_TRY(cholqr_pass(V2, nr, kr, 0.0, V, scratch, st, &ok));
-            if (ok) CTD_TRY(cholqr_pass(V, nr, kr, 0.0, Vq, scratch, st, &ok));
-            if (!ok) return fail(CTD_ENOTSUP, "new basis vectors are numerically dependent");
-            V = V0;
-          }
-          // Lam^T = Q_new^T V (upper triangular up to rounding): its lower
-          // transpose is L's new diagonal block
-          double* Lam;
-          CTD_TRY(scratch.get(&Lam, (size_t)kr * kr));
-          dgemm(true, false, kr, kr, nr, 1.0, Vq, nr, V, nr, 0.0, Lam, kr, st);
-          CTD_LAUNCH(k_lower_from_upper_T,
-                     (grid_for((int64_t)kr * kr, 256, (int64_t)num_sms() * 4)), (256), 0, st, Lam,
-                     kr, kr, F->L + dtc + dtc * ld, ld);
-          CTD_LAUNCH(k_transpose_f64, (grid_for(nr * kr, 256, (int64_t)num_sms() * 8)), (256), 0,
-                     st, Vq, nr, nr, kr, F->Qt + dtc, ld);
-          CTD_LAUNCH(k_qn_add, (grid_for(nr, 256, (int64_t)num_sms() * 4)), (256), 0, st, F->Qt,
-                     ld, dtc, kr, nr, F->qn);
+          CTD_TRY(finish_basis(F, dtc, kr, V, V2, Vq, Li, ldli, scratch, st));
         }
         // append the kept columns to R (CSC)
         int64_t* newf;
@@ -735,7 +754,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
         F->s_kept = dn;
         for (int q = 0; q < kr; ++q) {
           D.fiber_id.push_back(hf[q]);
-          D.fiber_step.push_back(D.t);
+          D.fiber_step.push_back(next_time(D));
         }
         kept_total += kr;
       }
@@ -829,6 +848,179 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   F->nnz_C = D.nnzC_total;
   F->have_err = true;
   F->err = D.err_den > 0 ? D.err_num / D.err_den : 0.0;
+  return CTD_OK;
+}
+
+__global__ void k_fiber_mod(const int64_t* __restrict__ f, int64_t n, int64_t w,
+                            int64_t* __restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = f[e] % w;
+}
+
+__global__ void k_iota(int n, int* __restrict__ a32, int64_t* __restrict__ a64) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    a32[e] = e;
+    a64[e] = e;
+  }
+}
+
+// A CTD-D state that starts from CTD-S factors of the history (the setting of
+// the paper's CTD-D experiments): R, its fibers (f = w + W k becomes time k,
+// slice fiber w), the basis Q and the Cholesky factor L of R^T R (from the
+// exact Gram of R, then the same orthonormalization as a step), and C of
+// the history as record 0.
+extern "C" ctd_status ctd_dynamic_from_static(const ctd_factors* S, uint64_t stream_id,
+                                              unsigned flags, void* stream,
+                                              ctd_factors** state) {
+  if (!S || !state) return fail(CTD_EINVAL, "NULL argument");
+  if (S->kind != 0) return fail(CTD_EINVAL, "not CTD-S factors");
+  if (S->alpha != 1 && S->alpha != 2) return fail(CTD_EINVAL, "alpha must be 1 or 2 (time is mode 3)");
+  if (!S->Coff || !S->have_err)
+    return fail(CTD_EINVAL, "the CTD-S factors need C and the error (no skip flags)");
+  CTD_TRY(sync(S->stream));
+  const int64_t dims2[2] = {S->dims[0], S->dims[1]};
+  ctd_factors* F = nullptr;
+  CTD_TRY(ctd_dynamic_create(dims2, S->alpha, S->precision, S->seed, stream_id, flags, &F));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  F->stream = st;
+  auto& D = *F->dyn;
+  const int64_t n = S->s_kept, nr = F->n_rows, W = F->n_cols, N = S->n_cols;
+  const int64_t nnzR = S->nnz_R;
+  const bool fp32 = S->precision == CTD_FP32_BULK;
+  auto bail = [&](ctd_status rc) {
+    cudaStreamSynchronize(st);
+    ctd_free(F);
+    return rc;
+  };
+#define SEED(expr)                     \
+  do {                                 \
+    ctd_status _r = (expr);            \
+    if (_r != CTD_OK) return bail(_r); \
+  } while (0)
+#define SEEDC(call)                                                              \
+  do {                                                                           \
+    if ((call) != cudaSuccess) return bail(fail(CTD_ECUDA, std::string(#call))); \
+  } while (0)
+  Arena scratch;
+  scratch.st = st;
+  if (n > 0) {
+    // R (CSC), its fibers, R by row
+    dfree(F->Rcolptr, st);
+    SEED(dalloc_n(&F->Rcolptr, n + 1, st));
+    SEED(dalloc_n(&F->Rrow, std::max<int64_t>(nnzR, 1), st));
+    SEED(dalloc_n(&F->Rval, std::max<int64_t>(nnzR, 1), st));
+    SEED(dalloc_n(&F->fibers, n, st));
+    SEEDC(cudaMemcpyAsync(F->Rcolptr, S->Rcolptr, (n + 1) * 8, cudaMemcpyDeviceToDevice, st));
+    SEEDC(cudaMemcpyAsync(F->Rrow, S->Rrow, nnzR * 4, cudaMemcpyDeviceToDevice, st));
+    SEEDC(cudaMemcpyAsync(F->Rval, S->Rval, nnzR * 4, cudaMemcpyDeviceToDevice, st));
+    CTD_LAUNCH(k_fiber_mod, (grid_for(n, 256, 256)), (256), 0, st, S->fibers, n, W, F->fibers);
+    D.cap_cols = n;
+    D.cap_nnz = std::max<int64_t>(nnzR, 1);
+    D.cap_fib = n;
+    F->s_kept = n;
+    F->nnz_R = nnzR;
+    std::vector<int64_t> hf(n);
+    SEED(d2h(hf.data(), S->fibers, n, st));
+    SEED(sync(st));
+    for (int64_t c = 0; c < n; ++c) {
+      D.fiber_id.push_back(hf[c] % W);
+      D.fiber_step.push_back(hf[c] / W);
+    }
+    SEED(dalloc_n(&F->Rrowptr, nr + 1, st));
+    SEED(dalloc_n(&F->Rcol, std::max<int64_t>(nnzR, 1), st));
+    SEED(dalloc_n(&F->Rcval, std::max<int64_t>(nnzR, 1), st));
+    SEED(build_csr_from_csc(F->Rcolptr, F->Rrow, F->Rval, n, nnzR, nr, 0, F->Rrowptr, F->Rcol,
+                            F->Rcval, scratch, st));
+    // L: Cholesky factor of the exact Gram of R (all columns independent)
+    int *i32, *keep, *idx, *cnt, *force;
+    int64_t* i64;
+    double *G, *thr, *piv, *Lk, *Li, *V, *V2, *Vq;
+    unsigned* status;
+    SEED(scratch.get(&i32, n));
+    SEED(scratch.get(&i64, n));
+    SEED(scratch.get(&keep, n));
+    SEED(scratch.get(&idx, n));
+    SEED(scratch.get(&cnt, 1));
+    SEED(scratch.get(&force, n));
+    SEED(scratch.get(&G, (size_t)n * n));
+    SEED(scratch.get(&thr, n));
+    SEED(scratch.get(&piv, n));
+    SEED(scratch.get(&Lk, (size_t)n * n));
+    SEED(scratch.get(&Li, (size_t)n * n));
+    SEED(scratch.get(&status, 4));
+    CTD_LAUNCH(k_iota, (grid_for(n, 256, 256)), (256), 0, st, (int)n, i32, i64);
+    SEEDC(cudaMemcpyAsync(cnt, &n, sizeof(int), cudaMemcpyHostToDevice, st));
+    SEED(launch_spmm_dense(CscDev{F->Rcolptr, F->Rrow, F->Rval}, i64, cnt, (int)n,
+                           CsrDev{F->Rrowptr, F->Rcol, F->Rcval, (int)n}, G, n, st));
+    SEEDC(cudaMemsetAsync(thr, 0, n * 8, st));
+    SEEDC(cudaMemsetAsync(force, 0xff, n * sizeof(int), st));
+    SEEDC(cudaMemsetAsync(status, 0, 4 * sizeof(unsigned), st));
+    launch_chol_skip(G, n, n, thr, keep, st, force, piv, status);
+    launch_compact_flags(keep, (int)n, idx, cnt, st);
+    int kept = 0;
+    unsigned h_status = 0;
+    SEED(d2h(&kept, cnt, 1, st));
+    SEED(d2h(&h_status, status, 1, st));
+    SEED(sync(st));
+    if (h_status & DEV_TIMEOUT) return bail(fail(CTD_ETIMEOUT, "skip-Cholesky grid barrier gave up"));
+    if (kept != n)
+      return bail(fail(CTD_ENOTSUP, "the history's fibers are numerically dependent"));
+    launch_gather_lower(G, n, idx, cnt, (int)n, Lk, n, st);
+    SEED(tri_inverse(Lk, n, n, Li, n, st));
+    // Q and L through the same orthonormalization as a step's new columns
+    SEED(grow_U(F, 0, n, st));
+    SEED(scratch.get(&V, (size_t)nr * n));
+    SEED(scratch.get(&V2, (size_t)nr * n));
+    SEED(scratch.get(&Vq, (size_t)nr * n));
+    SEEDC(cudaMemsetAsync(V, 0, (size_t)nr * n * 8, st));
+    CTD_LAUNCH(k_densify_cols, ((unsigned)std::min<int64_t>(n, 4096)), (128), 0, st,
+               reinterpret_cast<const unsigned long long*>(F->Rcolptr), F->Rrow, F->Rval, i32,
+               (int)n, V, nr);
+    SEED(finish_basis(F, 0, (int)n, V, V2, Vq, Li, n, scratch, st));
+    F->U_valid = false;
+  }
+  // record 0: the history, whose C is CTD-S's C
+  StepRec rec;
+  rec.d_draws = S->s;
+  rec.d_unique = S->s_unique;
+  rec.d_kept = n;
+  rec.d_before = 0;
+  rec.nnz = S->nnz_X;
+  rec.ncols = N;
+  rec.sq = (double)S->T;
+  rec.err = S->err * (double)S->T;
+  rec.nnzC = S->nnz_C;
+  const size_t vsz = fp32 ? 4 : 8;
+  SEED(dalloc_n(&rec.Coff, N + 1, st));
+  SEED(dalloc_n(&rec.Ccnt, std::max<int64_t>(N, 1), st));
+  SEED(dalloc_n(&rec.Crow, std::max<uint64_t>(S->C_cap, 1), st));
+  SEED(dalloc(&rec.Cval, std::max<uint64_t>(S->C_cap, 1) * vsz, st));
+  SEEDC(cudaMemcpyAsync(rec.Coff, S->Coff, (N + 1) * 8, cudaMemcpyDeviceToDevice, st));
+  SEEDC(cudaMemcpyAsync(rec.Ccnt, S->Ccnt, N * 4, cudaMemcpyDeviceToDevice, st));
+  if (S->C_cap) {
+    SEEDC(cudaMemcpyAsync(rec.Crow, S->Crow, S->C_cap * 2, cudaMemcpyDeviceToDevice, st));
+    SEEDC(cudaMemcpyAsync(rec.Cval, S->Cval, S->C_cap * vsz, cudaMemcpyDeviceToDevice, st));
+  }
+  D.steps.push_back(rec);
+  D.t = 1;
+  D.hist_k = S->dims[2];
+  D.err_num = rec.err;
+  D.err_den = rec.sq;
+  D.sq_total = rec.sq;
+  D.nnz_total = S->nnz_X;
+  D.nnzC_total = S->nnz_C;
+  D.all_positive = S->min_val > 0;
+  D.max_T = rec.sq;
+  F->nnz_X = S->nnz_X;
+  F->T = S->T;
+  F->nnz_C = S->nnz_C;
+  F->have_err = true;
+  F->err = S->err;
+  SEED(sync(st));
+#undef SEED
+#undef SEEDC
+  *state = F;
   return CTD_OK;
 }
 
@@ -942,12 +1134,16 @@ ctd_status dyn_U(const ctd_factors* Fc, double* U) {
 // step appends, M_{t'} times the column so far (Eq. C_t+1_final, line 18).
 ctd_status dyn_C_columns(const ctd_factors* F, int64_t ncols, const int64_t* cols, double* out) {
   const auto& D = *F->dyn;
-  const int64_t J = F->n_cols, h = F->s_kept;
+  const int64_t h = F->s_kept;
   cudaStream_t st = F->stream;
   std::vector<std::vector<double>> Mh(D.steps.size());
+  std::vector<int64_t> start(D.steps.size() + 1, 0);  // first column of each record
+  for (size_t r = 0; r < D.steps.size(); ++r) start[r + 1] = start[r] + D.steps[r].ncols;
   for (int64_t c = 0; c < ncols; ++c) {
-    const int64_t t = cols[c] / J, f = cols[c] % J;
-    if (cols[c] < 0 || t >= D.t) return fail(CTD_EINVAL, "column out of range");
+    if (cols[c] < 0 || cols[c] >= start.back()) return fail(CTD_EINVAL, "column out of range");
+    const int64_t t =
+        (int64_t)(std::upper_bound(start.begin(), start.end(), cols[c]) - start.begin()) - 1;
+    const int64_t f = cols[c] - start[t];
     const StepRec& r = D.steps[t];
     std::vector<double> v(r.d_before + r.d_kept, 0.0);
     if (r.Coff) {

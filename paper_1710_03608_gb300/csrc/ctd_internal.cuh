@@ -423,6 +423,8 @@ struct ctd_factors {
   // sizes
   int64_t s = 0, s_unique = 0, s_kept = 0, nnz_R = 0, nnz_C = 0, nnz_X = 0;
   uint64_t T = 0;
+  int min_val = 0;               // CTD-S: the smallest value of X (positive values allow the
+                                 // C fill's row copies)
   double err = 0.0;
   bool have_err = false;
   // device arrays (owned)

@@ -32,7 +32,7 @@ EXPORTED = ["ctd_static", "ctd_dynamic_create", "ctd_dynamic_step", "ctd_error",
             "ctd_get_C", "ctd_get_step", "ctd_get_M", "ctd_free", "ctd_last_error",
             "ctd_version", "ctd_profile", "ctd_profile_report", "ctd_sample_noalloc", "ctd_static_batched", "ctd_server_create", "ctd_server_submit",
             "ctd_server_wait", "ctd_server_result", "ctd_server_state", "ctd_server_free",
-            "ctd_ddos_candidates"]
+            "ctd_ddos_candidates", "ctd_dynamic_from_static"]
 
 
 class CtdError(RuntimeError):
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ctd_sample_noalloc": [C.POINTER(ctd_coo3), I32, I64, U64, P, P, C.POINTER(C.c_int), P],
         "ctd_profile_report": [C.c_char_p, C.c_size_t],
         "ctd_ddos_candidates": [P, I64, P, C.POINTER(C.c_int64), C.POINTER(D)],
+        "ctd_dynamic_from_static": [P, U64, C.c_uint, P, C.POINTER(P)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -314,6 +315,17 @@ class Dynamic(Factors):
         _check(lib.ctd_dynamic_create(C.byref(d2), int(alpha), int(precision), int(seed),
                                       int(stream_id), int(flags), C.byref(out)))
         super().__init__(out.value)
+
+    @classmethod
+    def from_static(cls, S: "Factors", stream_id: int = 0, flags: int = 0, stream=None):
+        """A CTD-D state seeded with CTD-S factors of the history (the
+        paper's CTD-D setting); see ctd_dynamic_from_static."""
+        out = C.c_void_p()
+        st = _stream_handle(stream) if stream is not None else _default_stream()
+        _check(load().ctd_dynamic_from_static(S.h, int(stream_id), int(flags), st, C.byref(out)))
+        obj = cls.__new__(cls)
+        Factors.__init__(obj, out.value)
+        return obj
 
     def step_slice(self, dX: Coo, d: int, eps: float, stream=None):
         st = _stream_handle(stream) if not _host(dX) or stream is not None else _default_stream()

@@ -285,6 +285,73 @@ def sweep(args):
           flush=True)
 
 
+def protocol(args):
+    """The paper's CTD-D vs CTD-S comparison (Section 4, performance of
+    CTD-D): the first 80% of the time mode is the history, decomposed by
+    CTD-S with s draws and used to seed CTD-D; the later slices arrive one
+    at a time.  At each arriving slice: one CTD-D step with d = 0.01 s, and
+    CTD-S recomputed on the whole tensor so far with s; device-resident
+    inputs, both timed to the end of the call (error included).  Averages
+    over the measured steps."""
+    tensors = [("haggle-shaped 77x274x1567, 27972 nnz",
+                synth.traffic((77, 274, 1567), 27972, 1.2, 1.2, "poisson1", 2001, 3.0), None),
+               ("traffic 10000x10000x1000, 1e7 nnz", synth.traffic_10m(), args.big_steps)]
+    import torch
+    out = []
+    for name, coo, max_steps in tensors:
+        I, J, K = coo.dims
+        kh = int(0.8 * K)
+        s_ = args.s
+        d = max(1, int(round(0.01 * s_)))
+        hist = coo.subset(coo.k < kh)
+        hist = synth.Coo3((I, J, kh), hist.i, hist.j, hist.k, hist.val)
+        S = ctd.ctd_static(ctd.Coo.from_synth(hist), 1, s_, 1e-6, 0, ctd.CTD_FP32_BULK)
+        S.error()
+        G = ctd.Dynamic.from_static(S)
+        # device copies of the whole tensor, in time order, for the CTD-S arm
+        order = np.argsort(coo.k, kind="stable")
+        dev = [torch.from_numpy(np.ascontiguousarray(a[order], dtype=np.int32)).cuda()
+               for a in (coo.i, coo.j, coo.k, coo.val)]
+        kcount = np.bincount(coo.k, minlength=K)
+        upto = np.cumsum(kcount)
+        steps = K - kh if max_steps is None else min(K - kh, max_steps)
+        # warm both arms
+        for _ in range(2):
+            ctd.ctd_static(ctd.Coo((I, J, kh + 1), *(a[:upto[kh]] for a in dev)), 1, s_, 1e-6, 0,
+                           ctd.CTD_FP32_BULK).free()
+        td, ts, ed, es = [], [], [], []
+        for t in range(kh, kh + steps):
+            m = coo.k == t
+            sl = synth.Coo3((I, J, 1), coo.i[m], coo.j[m], np.zeros(int(m.sum()), np.int64),
+                            coo.val[m])
+            X = ctd.Coo.from_synth(sl)
+            _sync()
+            t0 = time.perf_counter()
+            G.step_slice(X, d, 1e-6)
+            e1 = G.error()
+            _sync()
+            td.append(time.perf_counter() - t0)
+            ed.append(e1)
+            n = int(upto[t])
+            Xs = ctd.Coo((I, J, t + 1), *(a[:n] for a in dev))
+            _sync()
+            t0 = time.perf_counter()
+            F = ctd.ctd_static(Xs, 1, s_, 1e-6, 0, ctd.CTD_FP32_BULK)
+            e2 = F.error()
+            _sync()
+            ts.append(time.perf_counter() - t0)
+            es.append(e2)
+            F.free()
+        out.append({"tensor": name, "history_slices": kh, "steps_measured": steps, "s": s_,
+                    "d": d, "ctd_d_ms": 1e3 * float(np.mean(td)),
+                    "ctd_s_ms": 1e3 * float(np.mean(ts)),
+                    "speedup": float(np.mean(ts) / np.mean(td)),
+                    "ctd_d_error": float(np.mean(ed)), "ctd_s_error": float(np.mean(es)),
+                    "ctd_d_kept_final": int(G.sizes().s_kept)})
+    print(json.dumps({"workload": "CTD-D vs CTD-S, 80% history, d = 0.01 s, eps = 1e-6, FP32_BULK",
+                      "runs": out}), flush=True)
+
+
 # ---------------------------------------------------------------------------
 # summaries of ncu output (text in, text out; no GPU)
 # ---------------------------------------------------------------------------
@@ -391,6 +458,9 @@ def main():
     sw = sub.add_parser("sweep")
     sw.add_argument("--reps", type=int, default=3)
     sw.add_argument("--small-only", action="store_true")
+    pr = sub.add_parser("protocol")
+    pr.add_argument("--s", type=int, default=500)
+    pr.add_argument("--big-steps", type=int, default=40)
     dd = sub.add_parser("ddos")
     dd.add_argument("--steps", type=int, default=48)
     dd.add_argument("--scale", type=float, default=1.0)
@@ -407,7 +477,7 @@ def main():
     torch.cuda.set_device(0)
     ctd.load()
     {"batched": batched, "serving": serving, "stream": stream, "ddos": ddos,
-     "sweep": sweep}[args.cmd](args)
+     "sweep": sweep, "protocol": protocol}[args.cmd](args)
 
 
 if __name__ == "__main__":

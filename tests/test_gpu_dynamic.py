@@ -168,3 +168,54 @@ def test_near_saturation_weak_keeps():
     assert G.sizes().s_kept == len(st.R_cols) == 2000
     e = st.err_num / st.err_den
     assert abs(G.error() - e) <= error_tol(1, e)
+
+
+def _stack(slices):
+    I, J = slices[0].dims[0], slices[0].dims[1]
+    i = np.concatenate([s.i for s in slices])
+    j = np.concatenate([s.j for s in slices])
+    k = np.concatenate([np.full(s.nnz, t) for t, s in enumerate(slices)])
+    v = np.concatenate([s.val for s in slices])
+    return synth.Coo3((I, J, len(slices)), i, j, k, v)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_seeded_from_static(precision):
+    """The paper's CTD-D setting (Sec. 4): CTD-S factors of an 8-slice
+    history seed the state, then two slices arrive. Against the oracle's
+    seeded state and Algorithm 2 steps: fibers (time, slice fiber), R, U,
+    every column of C (history through the M chain, new blocks exact) and
+    the error."""
+    m = ctd()
+    slices = [synth.tiny((60, 40, 1), 200, seed=90 + t) for t in range(10)]
+    hist = _stack(slices[:8])
+    S = m.ctd_static(m.Coo.from_synth(hist), 1, 60, 1e-6, 5, precision)
+    G = m.Dynamic.from_static(S)
+    ref = O.ctd_s(hist.dims, hist.i, hist.j, hist.k, hist.val, 1, 60, 1e-6, 5)
+    st = O.dynamic_state_from_static(ref, hist.dims, keep_X=True)
+
+    def compare(new_block=None):
+        fib, fstep = G.fibers()
+        assert [(int(a), int(b)) for a, b in zip(fstep, fib)] == st.fibers
+        R_ref = np.stack([np.rint(c).astype(np.int64) for c in st.R_cols], axis=1)
+        assert np.array_equal(G.R_dense(), R_ref)
+        assert rel_fro(G.U(), st.U) <= u_tol(R_ref)
+        ncols = st.C.shape[1]
+        got = G.C_columns(np.arange(ncols))
+        assert rel_fro(got, st.C) <= max(u_tol(R_ref), 1e-12)
+        if new_block:
+            assert np.array_equal(got[:, -new_block:], st.C[:, -new_block:])
+        e = O.dynamic_error_dense(st)
+        assert abs(G.error() - e) <= error_tol(precision, e) + 1e-12
+
+    compare()
+    info, _ = G.step(0)
+    assert info[1] == len(st.R_cols) and info[2] == 0
+    for t, sl in enumerate(slices[8:]):
+        G.step_slice(m.Coo.from_synth(sl), 15, 1e-6)
+        step = O.ctd_d_step(st, (60, 40), sl.i, sl.j, sl.val, 15, 1e-6, 5, keep_X=True)
+        assert tie_margin(step.ratios, 1e-6) > 1e-7, "near-tie"
+        info, _ = G.step(t + 1)
+        assert info[1] == len(step.new_fibers)
+        compare(new_block=40)
+    assert G.sizes().t_steps == 3

@@ -329,3 +329,52 @@ def test_negative_values_allowed():
     L, *_ = np.linalg.lstsq(R0, Xa, rcond=None)
     e_ls = np.sum((R0 @ L - Xa) ** 2) / np.sum(Xa ** 2)
     assert abs(O.projection_error(res.X, res.R) - e_ls) < 1e-10
+
+
+# --- Section 4's CTD-D setting: a state seeded with CTD-S factors of the history ---
+
+def _stream_tensor(slices):
+    """Stack slices (I x J x 1 each) along time: slice k becomes k = k."""
+    I, J = slices[0].dims[0], slices[0].dims[1]
+    i = np.concatenate([s.i for s in slices])
+    j = np.concatenate([s.j for s in slices])
+    k = np.concatenate([np.full(s.nnz, t) for t, s in enumerate(slices)])
+    v = np.concatenate([s.val for s in slices])
+    return (I, J, len(slices)), i, j, k, v
+
+
+def test_seeded_state_one_slice_equals_one_step():
+    """Seeding with CTD-S of a one-slice history equals one Algorithm 2 step
+    from the empty state on that slice (same draws: counter step 0)."""
+    sl = synth.tiny((30, 20, 1), 120, seed=61)
+    dims3, i, j, k, v = _stream_tensor([sl])
+    ref = O.ctd_s(dims3, i, j, k, v, 1, 25, 1e-6, 4)
+    seeded = O.dynamic_state_from_static(ref, dims3)
+    st = O.DynamicState(30, 20)
+    O.ctd_d_step(st, (30, 20), sl.i, sl.j, sl.val, 25, 1e-6, 4)
+    assert seeded.fibers == st.fibers and seeded.t == st.t == 1
+    assert np.array_equal(np.stack(seeded.R_cols, 1), np.stack(st.R_cols, 1))
+    assert np.allclose(seeded.U, st.U, rtol=1e-10, atol=0)
+    assert np.array_equal(seeded.C, st.C)
+    assert abs(seeded.err_num / seeded.err_den - st.err_num / st.err_den) <= 1e-12
+
+
+def test_seeded_state_error_two_routes():
+    """After seeding with a 6-slice history and three more steps, the literal
+    Eq. (error) with the dense C (R U C over all columns) equals the per-step
+    projection bookkeeping; the history's fibers are its slices' columns."""
+    slices = [synth.tiny((40, 25, 1), 150, seed=70 + t) for t in range(9)]
+    dims3, i, j, k, v = _stream_tensor(slices[:6])
+    ref = O.ctd_s(dims3, i, j, k, v, 1, 40, 1e-6, 2)
+    st = O.dynamic_state_from_static(ref, dims3, keep_X=True)
+    assert abs(O.dynamic_error_dense(st) - st.err_num / st.err_den) <= 1e-10
+    for (t, jj), col in zip(st.fibers, st.R_cols):
+        s_ = slices[t]
+        dense = np.zeros(40)
+        m = s_.j == jj
+        dense[s_.i[m]] = s_.val[m]
+        assert np.array_equal(dense, col)
+    for sl in slices[6:]:
+        O.ctd_d_step(st, (40, 25), sl.i, sl.j, sl.val, 12, 1e-6, 2, keep_X=True)
+    assert st.t == 9
+    assert abs(O.dynamic_error_dense(st) - st.err_num / st.err_den) <= 1e-9
