@@ -76,14 +76,20 @@ __global__ void __launch_bounds__(256)
     k_resid_rows(int64_t n_rows, const unsigned long long* __restrict__ crp,
                  const int32_t* __restrict__ ccol, const int32_t* __restrict__ cval,
                  const int* __restrict__ kpos, const int* __restrict__ sus_of,
-                 const double* __restrict__ etaT, int ns, int init, double* __restrict__ rbuf) {
+                 const double* __restrict__ etaT, int ns, int init, int seg,
+                 double* __restrict__ part) {
   constexpr int CH = 32 * NPL;
   constexpr int EU = 8;  // entries whose eta loads are in flight together
   const int lane = threadIdx.x & 31;
+  const int k = blockIdx.y;  // the row's segment: entries [k seg, (k + 1) seg)
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = gw; i < n_rows; i += nw) {
-    const unsigned long long a = crp[i], b = crp[i + 1];
+    const unsigned long long a0 = crp[i], b0 = crp[i + 1];
+    const unsigned long long a = a0 + (unsigned long long)k * seg;
+    if (k > 0 && a >= b0) continue;  // no such segment (segment 0 always writes)
+    const unsigned long long b = min(b0, a + (unsigned long long)seg);
+    double* out = part + ((int64_t)k * n_rows + i) * ns;
     for (int c0 = 0; c0 < ns; c0 += CH) {
       double acc[NPL];
 #pragma unroll
@@ -132,30 +138,62 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int w = 0; w < NPL; ++w) {
         const int c = c0 + lane + 32 * w;
-        if (c < ns) {
-          double* r = rbuf + (int64_t)c * n_rows + i;
-          *r = init ? acc[w] : *r + acc[w];
-        }
+        if (c < ns) out[c] = acc[w];
       }
     }
   }
 }
 
-static void launch_resid_rows(int64_t n_rows, const uint64_t* crp, const int32_t* ccol,
-                              const int32_t* cval, const int* kpos, const int* sus_of,
-                              const double* etaT, int ns, int init, double* rbuf,
-                              cudaStream_t st) {
-  const unsigned g = grid_for(n_rows * 32, 256, (int64_t)num_sms() * 16);  // a warp per row
+// rbuf(i, c) (=, or += with init = 0) the sum of row i's segment partials
+// in segment order
+__global__ void k_resid_combine(int64_t n_rows, const unsigned long long* __restrict__ crp,
+                                int ns, int seg, const double* __restrict__ part, int init,
+                                double* __restrict__ rbuf) {
+  const int64_t total = n_rows * ns;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ns;
+    const int c = (int)(e % ns);
+    const unsigned long long len = crp[i + 1] - crp[i];
+    const int nseg = len == 0 ? 1 : (int)((len + seg - 1) / seg);
+    double s = 0.0;
+    for (int k = 0; k < nseg; ++k) s += part[((int64_t)k * n_rows + i) * ns + c];
+    double* r = rbuf + (int64_t)c * n_rows + i;
+    *r = init ? s : *r + s;
+  }
+}
+
+// Rows are split into at most RS_SEGS segments of seg entries (a multiple of
+// 32, at least 64), a warp per (row, segment): the long rows of the
+// frequent mode-alpha indices no longer serialize on one warp (each entry
+// costs NPL FP64 instructions of 64 cycles).
+constexpr int RS_SEGS = 8;
+
+static ctd_status launch_resid_rows(int64_t n_rows, int du, const uint64_t* crp,
+                                    const int32_t* ccol, const int32_t* cval, const int* kpos,
+                                    const int* sus_of, const double* etaT, int ns, int init,
+                                    double* rbuf, Arena& scratch, cudaStream_t st) {
+  // at most RS_SEGS segments, and partials within 256 MB
+  const int64_t per = std::max<int64_t>(1, n_rows * ns * (int64_t)sizeof(double));
+  const int segs = (int)std::max<int64_t>(1, std::min<int64_t>(RS_SEGS, (256ll << 20) / per));
+  int seg = (du + segs - 1) / segs;
+  seg = std::max(64, (seg + 31) / 32 * 32);
+  double* part;
+  CTD_TRY(scratch.get(&part, (size_t)segs * n_rows * ns));
+  const dim3 g(grid_for(n_rows * 32, 256, (int64_t)num_sms() * 16), segs);
   const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(crp);
   if (ns <= 32)
     CTD_LAUNCH(k_resid_rows<1>, (g), (256), 0, st, n_rows, rp, ccol, cval, kpos, sus_of, etaT, ns,
-               init, rbuf);
+               init, seg, part);
   else if (ns <= 64)
     CTD_LAUNCH(k_resid_rows<2>, (g), (256), 0, st, n_rows, rp, ccol, cval, kpos, sus_of, etaT, ns,
-               init, rbuf);
+               init, seg, part);
   else
     CTD_LAUNCH(k_resid_rows<4>, (g), (256), 0, st, n_rows, rp, ccol, cval, kpos, sus_of, etaT, ns,
-               init, rbuf);
+               init, seg, part);
+  CTD_LAUNCH(k_resid_combine, (grid_for(n_rows * ns, 256, (int64_t)num_sms() * 16)), (256), 0, st,
+             n_rows, rp, ns, seg, part, init, rbuf);
+  return CTD_OK;
 }
 
 // etaT[q * ns + c] = eta[q + c * kept]
@@ -362,8 +400,8 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
     CTD_LAUNCH(k_sus_of, (grid_for(ns, 256, 64)), (256), 0, st, d_sus, ns, sus_of);
     const unsigned gt = grid_for((int64_t)kk * ns, 256, (int64_t)num_sms() * 8);
     if (kept > 0) CTD_LAUNCH(k_transpose_eta, (gt), (256), 0, st, eta, kept, ns, etaT);
-    launch_resid_rows(in.n_rows, in.c_rowptr, in.c_col, in.c_val, kpos, sus_of, etaT, ns, 1, rbuf,
-                      st);
+    CTD_TRY(launch_resid_rows(in.n_rows, du, in.c_rowptr, in.c_col, in.c_val, kpos, sus_of, etaT,
+                              ns, 1, rbuf, scratch, st));
     // minus Q gamma (Q = Qt^T, n_rows x dt)
     if (in.dt > 0)
       dgemm(true, false, in.n_rows, ns, in.dt, -1.0, in.Qt, in.ldq, gammaQ, in.dt, 1.0, rbuf,
@@ -412,8 +450,8 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
       }
       // r -= Xc[:, K] eta_d, then r -= Q (h_Q - W_K eta_d)
       if (kept > 0) CTD_LAUNCH(k_transpose_eta, (gt), (256), 0, st, etad, kept, ns, etaT);
-      launch_resid_rows(in.n_rows, in.c_rowptr, in.c_col, in.c_val, kpos, sus_of, etaT, ns, 0,
-                        rbuf, st);
+      CTD_TRY(launch_resid_rows(in.n_rows, du, in.c_rowptr, in.c_col, in.c_val, kpos, sus_of,
+                                etaT, ns, 0, rbuf, scratch, st));
       if (in.dt > 0) {
         if (kept > 0)
           dgemm(false, false, in.dt, ns, kept, -1.0, WK, in.dt, etad, kept, 1.0, hQ, in.dt, st);
