@@ -269,6 +269,20 @@ ctd_status matricize(const CooDev& X, bool want_rows, Arena& A, cudaStream_t st,
 
 using namespace ctd;
 
+// *out = max |val[e]| over the first *count entries (out zeroed beforehand)
+__global__ void k_abs_max(const int32_t* __restrict__ val, const uint64_t* __restrict__ count,
+                          int* __restrict__ out) {
+  const int64_t n = (int64_t)*count;
+  int m = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int v = val[e];
+    m = max(m, v == INT32_MIN ? INT32_MAX : abs(v));
+  }
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
 // ---------------------------------------------------------------------------
 // CTD-S
 // ---------------------------------------------------------------------------
@@ -445,6 +459,8 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   // idle across that read-back.
   Readback rbc(st);
   uint64_t cap = 0, nnzR = 0;
+  int rmax = -1;
+  int* d_rmax = nullptr;
   if (!(flags & CTD_SKIP_C)) {
     uint32_t* ub;
     STEP(scratch.get(&ub, M.n_cols));
@@ -455,8 +471,14 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
       launch_c_bounds(M.csc(), M.n_cols, R, ub, st);
       launch_scan_u32(ub, F->Coff, M.n_cols, false, M.tmp, M.status, st);
     }
+    // largest |R| (the C fill stores its longest rows as int16 when they fit)
+    STEP(scratch.get(&d_rmax, 1));
+    STEPC(cudaMemsetAsync(d_rmax, 0, sizeof(int), st));
+    CTD_LAUNCH(k_abs_max, (grid_for((int64_t)nnzR_cap, 256, (int64_t)num_sms() * 4)), (256), 0,
+               st, F->Rval, F->Rcolptr + kept, d_rmax);
     STEP(rbc.add(&cap, F->Coff + M.n_cols, 1));
     STEP(rbc.add(&nnzR, F->Rcolptr + kept, 1));
+    STEP(rbc.add(&rmax, (const int*)d_rmax, 1));
     STEP(rbc.mark());
   }
   // Eq. (error): e = (T - ||Q^T X||_F^2) / T with Q = R L^{-T}
@@ -471,6 +493,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
     STEP(rbc.wait_mark());
     F->nnz_R = (int64_t)nnzR;
     R.nnz = F->nnz_R;
+    R.max_abs = rmax;
     F->C_cap = cap;
     STEP(F->mem.get(&F->Crow, cap));
     const size_t vsz = precision == CTD_FP32_BULK ? 4 : 8;

@@ -21,6 +21,7 @@
 // only then.  Which rows are dense changes the order of integer additions
 // only, so the result does not depend on the selection.
 #include <algorithm>
+#include <type_traits>
 
 #include "ctd_expand.cuh"
 #include "ctd_internal.cuh"
@@ -36,7 +37,7 @@ constexpr int CF_THREADS = 768;
 constexpr int CF_HEAVY_COL = 128;  // columns with at least this many nonzeros: taken first
 constexpr int CF_LONG_ROW = 16;    // sparse rows at least this long: walked by the whole warp
 constexpr int CF_LONG_GROUP = 2;   // long sparse rows walked together (loads in flight)
-constexpr int CF_MAX_DENSE = 96;   // dense rows at most (shared memory bounds it first)
+constexpr int CF_MAX_DENSE = 192;  // dense rows at most (shared memory bounds it first)
 
 // --- selection of the dense rows -------------------------------------------
 // hist[len] = number of rows of R with len entries (len >= minlen, capped at width)
@@ -88,9 +89,14 @@ struct Dense {
   int hmax;          // shared memory is sized for this many
 };
 
-// Fill the dense rows (H x W ints at `dense`) and zero `acc_n` ints at `acc`.
-__device__ __forceinline__ void load_dense(const CsrDev& R, const Dense& dn, int* dense, int W,
+// Fill the dense rows (H x W entries at `dense`, int16 when SH, else int32)
+// and zero `acc_n` ints at `acc`.  R's values fit int16 when SH (checked on
+// the host from max |R|).
+template <bool SH>
+__device__ __forceinline__ void load_dense(const CsrDev& R, const Dense& dn, void* dense_v, int W,
                                            int* acc, int acc_n) {
+  using DT = typename std::conditional<SH, short, int>::type;
+  DT* dense = static_cast<DT*>(dense_v);
   const int H = min(*dn.count, dn.hmax);
   for (int e = threadIdx.x; e < H * W; e += blockDim.x) dense[e] = 0;
   for (int e = threadIdx.x; e < acc_n; e += blockDim.x) acc[e] = 0;
@@ -100,7 +106,7 @@ __device__ __forceinline__ void load_dense(const CsrDev& R, const Dense& dn, int
   for (int h = warp; h < H; h += nw) {
     const int i = dn.rows[h];
     for (unsigned long long p = rp[i] + lane; p < rp[i + 1]; p += 32)
-      dense[h * W + __ldg(R.col + p)] = __ldg(R.val + p);
+      dense[h * W + __ldg(R.col + p)] = (DT)__ldg(R.val + p);
   }
   __syncthreads();
 }
@@ -342,11 +348,11 @@ __global__ void __launch_bounds__(256)
 // rs/rl = the R row's range for a sparse row; rl = 0 for idle lanes):
 // dense rows into regs (lane's rows 128 q + 4 lane + k), other rows into the
 // shared accumulator acc (atomics).
-template <int NQ>
-__device__ __forceinline__ void chunk_reg(const CsrDev& R, const int4* __restrict__ dense4,
+template <int NQ, bool SH>
+__device__ __forceinline__ void chunk_reg(const CsrDev& R, const void* __restrict__ dense_v,
                                           int* acc, int (&regs)[4 * NQ], int v, int sl,
                                           unsigned long long rs, int rl) {
-  constexpr int W4 = NQ * 32;  // int4 per dense row
+  constexpr int W4 = NQ * 32;  // 4-entry groups per dense row
   const int lane = threadIdx.x & 31;
   unsigned dense_b = __ballot_sync(0xffffffffu, sl >= 0);
   while (dense_b) {
@@ -354,14 +360,27 @@ __device__ __forceinline__ void chunk_reg(const CsrDev& R, const int4* __restric
     dense_b &= dense_b - 1;
     const int h = __shfl_sync(0xffffffffu, sl, src);
     const int vs = __shfl_sync(0xffffffffu, v, src);
-    const int4* d = dense4 + h * W4 + lane;
+    if (SH) {
+      // four int16 per 8-byte load, sign-extended
+      const uint2* d = static_cast<const uint2*>(dense_v) + h * W4 + lane;
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      const int4 x = d[q * 32];
-      regs[4 * q + 0] += vs * x.x;
-      regs[4 * q + 1] += vs * x.y;
-      regs[4 * q + 2] += vs * x.z;
-      regs[4 * q + 3] += vs * x.w;
+      for (int q = 0; q < NQ; ++q) {
+        const uint2 x = d[q * 32];
+        regs[4 * q + 0] += vs * (int)(short)(x.x & 0xffffu);
+        regs[4 * q + 1] += vs * ((int)x.x >> 16);
+        regs[4 * q + 2] += vs * (int)(short)(x.y & 0xffffu);
+        regs[4 * q + 3] += vs * ((int)x.y >> 16);
+      }
+    } else {
+      const int4* d = static_cast<const int4*>(dense_v) + h * W4 + lane;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int4 x = d[q * 32];
+        regs[4 * q + 0] += vs * x.x;
+        regs[4 * q + 1] += vs * x.y;
+        regs[4 * q + 2] += vs * x.z;
+        regs[4 * q + 3] += vs * x.w;
+      }
     }
   }
   // the long sparse rows, CF_LONG_GROUP at a time: each lane loads its entries of
@@ -417,9 +436,9 @@ __device__ __forceinline__ void entry_meta(const CsrDev& R, const Dense& dn, int
 
 // Accumulate R^T x_f over the column's entries [a, b): warps of a group
 // [gwarp, gwarp + gwarps) take interleaved 32-entry chunks.
-template <int NQ>
+template <int NQ, bool SH>
 __device__ __forceinline__ void accumulate_reg(const CscDev& X, const CsrDev& R, const Dense& dn,
-                                               const int4* __restrict__ dense4,
+                                               const void* __restrict__ dense4,
                                                unsigned long long a, unsigned long long b,
                                                int* acc, int (&regs)[4 * NQ], int gwarp,
                                                int gwarps) {
@@ -434,7 +453,7 @@ __device__ __forceinline__ void accumulate_reg(const CscDev& X, const CsrDev& R,
       v = __ldg(X.val + p);
     }
     entry_meta(R, dn, i, sl, rs, rl);
-    chunk_reg<NQ>(R, dense4, acc, regs, v, sl, rs, rl);
+    chunk_reg<NQ, SH>(R, dense4, acc, regs, v, sl, rs, rl);
   }
 }
 
@@ -528,7 +547,7 @@ struct IsF32<float> { static constexpr bool v = true; };
 // warp per column, first the columns with at least CF_HEAVY_COL nonzeros
 // (`list`, the longest work items), then the other multi-nonzero columns
 // (`mlist`).  Each warp's accumulator is left zero by its emission.
-template <typename V, int NQ>
+template <typename V, int NQ, bool SH>
 __global__ void __launch_bounds__(CF_THREADS, 1)
     k_cf(CscDev X, CsrDev R, Dense dn, const int64_t* __restrict__ list,
          const unsigned* __restrict__ nlist, const int64_t* __restrict__ mlist,
@@ -537,11 +556,11 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
          unsigned long long* work) {
   extern __shared__ int4 smem4[];
   constexpr int W = NQ * 128;
-  int* dense = reinterpret_cast<int*>(smem4);
+  unsigned char* dense = reinterpret_cast<unsigned char*>(smem4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  int* accs = dense + (size_t)dn.hmax * W;
-  load_dense(R, dn, dense, W, accs, nw * W);
-  const int4* dense4 = reinterpret_cast<const int4*>(dense);
+  int* accs = reinterpret_cast<int*>(dense + (size_t)dn.hmax * W * (SH ? 2 : 4));
+  load_dense<SH>(R, dn, dense, W, accs, nw * W);
+  const void* dense4 = dense;
   int regs[4 * NQ];
 #pragma unroll
   for (int k = 0; k < 4 * NQ; ++k) regs[k] = 0;
@@ -599,8 +618,8 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
           ni = __ldg(X.row + na + lane);
           nv = __ldg(X.val + na + lane);
         }
-        chunk_reg<NQ>(R, dense4, acc, regs, cv, csl, crs, crl);
-        if (eb - ea > 32) accumulate_reg<NQ>(X, R, dn, dense4, ea + 32, eb, acc, regs, 0, 1);
+        chunk_reg<NQ, SH>(R, dense4, acc, regs, cv, csl, crs, crl);
+        if (eb - ea > 32) accumulate_reg<NQ, SH>(X, R, dn, dense4, ea + 32, eb, acc, regs, 0, 1);
         // the next column's row metadata, then this column's emission
         entry_meta(R, dn, ni, csl, crs, crl);
         cv = nv;
@@ -620,26 +639,27 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
   }
 }
 
-template <typename V, int NQ>
+template <typename V, int NQ, bool SH>
 ctd_status cf_launch(const CscDev& X, const CsrDev& R, const Dense& dn,
                      const unsigned long long* coff, uint32_t* ccnt, uint16_t* crow, V* cval,
                      const int64_t* heavy, const unsigned* nheavy, const int64_t* multi,
                      const unsigned* nmulti, unsigned long long* work, cudaStream_t st) {
   constexpr int W = NQ * 128;
-  const size_t smem = ((size_t)dn.hmax + CF_THREADS / 32) * (size_t)W * sizeof(int) +
+  const size_t smem = (size_t)dn.hmax * W * (SH ? 2 : 4) +
+                      (size_t)(CF_THREADS / 32) * W * sizeof(int) +
                       (size_t)(CF_THREADS / 32) * 128 * sizeof(uint16_t);
-  CTD_TRY(allow_max_smem((const void*)k_cf<V, NQ>));
+  CTD_TRY(allow_max_smem((const void*)k_cf<V, NQ, SH>));
   int per_sm = 0;
-  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cf<V, NQ>, CF_THREADS, smem));
+  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cf<V, NQ, SH>, CF_THREADS, smem));
   if (per_sm < 1) return fail(CTD_ENOTSUP, "C fill: shared memory for the dense rows too large");
-  CTD_LAUNCH((k_cf<V, NQ>), (num_sms() * per_sm), (CF_THREADS), smem, st, X, R, dn, heavy,
+  CTD_LAUNCH((k_cf<V, NQ, SH>), (num_sms() * per_sm), (CF_THREADS), smem, st, X, R, dn, heavy,
              nheavy, multi, nmulti, coff, ccnt, crow, cval, work);
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
 
 template <typename V>
-ctd_status cf_all(int nq, const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
+ctd_status cf_all(int nq, bool sh, const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
                   const Dense& dn,
                   const unsigned long long* coff, uint32_t* ccnt, uint16_t* crow, V* cval,
                   int positive, int64_t list_cap, Arena& a, cudaStream_t st) {
@@ -682,12 +702,24 @@ ctd_status cf_all(int nq, const CscDev& X, int64_t n_cols, int64_t n_rows, const
                counts, coff, crow, cval);
   }
   PhaseScope ph("c_fill_multi", st);
-  switch (nq) {
-    case 1: return cf_launch<V, 1>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, counts + 2, work, st);
-    case 2: return cf_launch<V, 2>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, counts + 2, work, st);
-    case 4: return cf_launch<V, 4>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, counts + 2, work, st);
-    default: return cf_launch<V, 8>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, counts + 2, work, st);
+#define CF_GO(NQV, SHV)                                                                          \
+  return cf_launch<V, NQV, SHV>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, \
+                                counts + 2, work, st)
+  if (sh) {
+    switch (nq) {
+      case 1: CF_GO(1, true);
+      case 2: CF_GO(2, true);
+      case 4: CF_GO(4, true);
+      default: CF_GO(8, true);
+    }
   }
+  switch (nq) {
+    case 1: CF_GO(1, false);
+    case 2: CF_GO(2, false);
+    case 4: CF_GO(4, false);
+    default: CF_GO(8, false);
+  }
+#undef CF_GO
 }
 
 }  // namespace
@@ -703,10 +735,12 @@ ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, in
   const int nq0 = (width + 127) / 128;
   const int nq = nq0 <= 1 ? 1 : nq0 <= 2 ? 2 : nq0 <= 4 ? 4 : 8;
   const int W = nq * 128;
-  const size_t row_b = (size_t)W * sizeof(int);
+  // dense rows as int16 when every value of R fits (twice as many rows)
+  const bool sh = R.max_abs >= 0 && R.max_abs <= 32767;
+  const size_t row_b = (size_t)W * (sh ? 2 : 4);
   // one block per SM: dense rows, the warps' accumulators and row staging in ~220 KB
   const int budget = 220 * 1024;
-  int hmax = (int)((budget - (CF_THREADS / 32) * 256) / (int64_t)row_b) - CF_THREADS / 32;
+  int hmax = (int)((budget - (int64_t)(CF_THREADS / 32) * (256 + W * 4)) / (int64_t)row_b);
   hmax = std::max(0, std::min(hmax, CF_MAX_DENSE));
   const int minlen = std::max(16, 16 * nq);  // shorter rows are cheaper walked sparsely
   Arena a;
@@ -729,9 +763,9 @@ ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, in
   const unsigned long long* co = reinterpret_cast<const unsigned long long*>(coff);
   const int64_t list_cap = std::max<int64_t>(1, std::min(n_cols, nnz));
   if (fp32)
-    return cf_all<float>(nq, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<float*>(cval),
+    return cf_all<float>(nq, sh, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<float*>(cval),
                          positive, list_cap, a, st);
-  return cf_all<double>(nq, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<double*>(cval),
+  return cf_all<double>(nq, sh, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<double*>(cval),
                         positive, list_cap, a, st);
 }
 

@@ -202,6 +202,7 @@ struct CsrDev {        // a factor by row: row i holds (col, val) pairs
   const int32_t* val;
   int width;           // number of columns
   int64_t nnz = -1;    // number of entries (-1: not known on the host)
+  int max_abs = -1;    // largest |value| (-1: not known on the host)
 };
 
 // Dense products: out(:, c) = R^T x_{fibers[c]} for c < nf (column-major,
