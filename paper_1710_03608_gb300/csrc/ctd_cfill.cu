@@ -37,7 +37,7 @@ constexpr int CF_THREADS = 768;
 constexpr int CF_HEAVY_COL = 128;  // columns with at least this many nonzeros: taken first
 constexpr int CF_LONG_ROW = 16;    // sparse rows at least this long: walked by the whole warp
 constexpr int CF_LONG_GROUP = 2;   // long sparse rows walked together (loads in flight)
-constexpr int CF_MAX_DENSE = 192;  // dense rows at most (shared memory bounds it first)
+constexpr int CF_MAX_DENSE = 320;  // dense rows at most (shared memory bounds it first)
 
 // --- selection of the dense rows -------------------------------------------
 // hist[len] = number of rows of R with len entries (len >= minlen, capped at width)
@@ -89,13 +89,14 @@ struct Dense {
   int hmax;          // shared memory is sized for this many
 };
 
-// Fill the dense rows (H x W entries at `dense`, int16 when SH, else int32)
-// and zero `acc_n` ints at `acc`.  R's values fit int16 when SH (checked on
-// the host from max |R|).
-template <bool SH>
+// Fill the dense rows (H x W entries of DB bytes at `dense`: int8, int16 or
+// int32) and zero `acc_n` ints at `acc`.  R's values fit the entry type
+// (checked on the host from max |R|).
+template <int DB>
 __device__ __forceinline__ void load_dense(const CsrDev& R, const Dense& dn, void* dense_v, int W,
                                            int* acc, int acc_n) {
-  using DT = typename std::conditional<SH, short, int>::type;
+  using DT = typename std::conditional<DB == 1, signed char,
+                                       typename std::conditional<DB == 2, short, int>::type>::type;
   DT* dense = static_cast<DT*>(dense_v);
   const int H = min(*dn.count, dn.hmax);
   for (int e = threadIdx.x; e < H * W; e += blockDim.x) dense[e] = 0;
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(256)
 // rs/rl = the R row's range for a sparse row; rl = 0 for idle lanes):
 // dense rows into regs (lane's rows 128 q + 4 lane + k), other rows into the
 // shared accumulator acc (atomics).
-template <int NQ, bool SH>
+template <int NQ, int DB>
 __device__ __forceinline__ void chunk_reg(const CsrDev& R, const void* __restrict__ dense_v,
                                           int* acc, int (&regs)[4 * NQ], int v, int sl,
                                           unsigned long long rs, int rl) {
@@ -360,7 +361,18 @@ __device__ __forceinline__ void chunk_reg(const CsrDev& R, const void* __restric
     dense_b &= dense_b - 1;
     const int h = __shfl_sync(0xffffffffu, sl, src);
     const int vs = __shfl_sync(0xffffffffu, v, src);
-    if (SH) {
+    if (DB == 1) {
+      // four int8 per 4-byte load, sign-extended
+      const unsigned* d = static_cast<const unsigned*>(dense_v) + h * W4 + lane;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int x = (int)d[q * 32];
+        regs[4 * q + 0] += vs * ((x << 24) >> 24);
+        regs[4 * q + 1] += vs * ((x << 16) >> 24);
+        regs[4 * q + 2] += vs * ((x << 8) >> 24);
+        regs[4 * q + 3] += vs * (x >> 24);
+      }
+    } else if (DB == 2) {
       // four int16 per 8-byte load, sign-extended
       const uint2* d = static_cast<const uint2*>(dense_v) + h * W4 + lane;
 #pragma unroll
@@ -436,7 +448,7 @@ __device__ __forceinline__ void entry_meta(const CsrDev& R, const Dense& dn, int
 
 // Accumulate R^T x_f over the column's entries [a, b): warps of a group
 // [gwarp, gwarp + gwarps) take interleaved 32-entry chunks.
-template <int NQ, bool SH>
+template <int NQ, int DB>
 __device__ __forceinline__ void accumulate_reg(const CscDev& X, const CsrDev& R, const Dense& dn,
                                                const void* __restrict__ dense4,
                                                unsigned long long a, unsigned long long b,
@@ -453,7 +465,7 @@ __device__ __forceinline__ void accumulate_reg(const CscDev& X, const CsrDev& R,
       v = __ldg(X.val + p);
     }
     entry_meta(R, dn, i, sl, rs, rl);
-    chunk_reg<NQ, SH>(R, dense4, acc, regs, v, sl, rs, rl);
+    chunk_reg<NQ, DB>(R, dense4, acc, regs, v, sl, rs, rl);
   }
 }
 
@@ -547,7 +559,7 @@ struct IsF32<float> { static constexpr bool v = true; };
 // warp per column, first the columns with at least CF_HEAVY_COL nonzeros
 // (`list`, the longest work items), then the other multi-nonzero columns
 // (`mlist`).  Each warp's accumulator is left zero by its emission.
-template <typename V, int NQ, bool SH>
+template <typename V, int NQ, int DB>
 __global__ void __launch_bounds__(CF_THREADS, 1)
     k_cf(CscDev X, CsrDev R, Dense dn, const int64_t* __restrict__ list,
          const unsigned* __restrict__ nlist, const int64_t* __restrict__ mlist,
@@ -558,8 +570,8 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
   constexpr int W = NQ * 128;
   unsigned char* dense = reinterpret_cast<unsigned char*>(smem4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  int* accs = reinterpret_cast<int*>(dense + (size_t)dn.hmax * W * (SH ? 2 : 4));
-  load_dense<SH>(R, dn, dense, W, accs, nw * W);
+  int* accs = reinterpret_cast<int*>(dense + (size_t)dn.hmax * W * DB);
+  load_dense<DB>(R, dn, dense, W, accs, nw * W);
   const void* dense4 = dense;
   int regs[4 * NQ];
 #pragma unroll
@@ -618,8 +630,8 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
           ni = __ldg(X.row + na + lane);
           nv = __ldg(X.val + na + lane);
         }
-        chunk_reg<NQ, SH>(R, dense4, acc, regs, cv, csl, crs, crl);
-        if (eb - ea > 32) accumulate_reg<NQ, SH>(X, R, dn, dense4, ea + 32, eb, acc, regs, 0, 1);
+        chunk_reg<NQ, DB>(R, dense4, acc, regs, cv, csl, crs, crl);
+        if (eb - ea > 32) accumulate_reg<NQ, DB>(X, R, dn, dense4, ea + 32, eb, acc, regs, 0, 1);
         // the next column's row metadata, then this column's emission
         entry_meta(R, dn, ni, csl, crs, crl);
         cv = nv;
@@ -639,27 +651,27 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
   }
 }
 
-template <typename V, int NQ, bool SH>
+template <typename V, int NQ, int DB>
 ctd_status cf_launch(const CscDev& X, const CsrDev& R, const Dense& dn,
                      const unsigned long long* coff, uint32_t* ccnt, uint16_t* crow, V* cval,
                      const int64_t* heavy, const unsigned* nheavy, const int64_t* multi,
                      const unsigned* nmulti, unsigned long long* work, cudaStream_t st) {
   constexpr int W = NQ * 128;
-  const size_t smem = (size_t)dn.hmax * W * (SH ? 2 : 4) +
+  const size_t smem = (size_t)dn.hmax * W * DB +
                       (size_t)(CF_THREADS / 32) * W * sizeof(int) +
                       (size_t)(CF_THREADS / 32) * 128 * sizeof(uint16_t);
-  CTD_TRY(allow_max_smem((const void*)k_cf<V, NQ, SH>));
+  CTD_TRY(allow_max_smem((const void*)k_cf<V, NQ, DB>));
   int per_sm = 0;
-  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cf<V, NQ, SH>, CF_THREADS, smem));
+  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cf<V, NQ, DB>, CF_THREADS, smem));
   if (per_sm < 1) return fail(CTD_ENOTSUP, "C fill: shared memory for the dense rows too large");
-  CTD_LAUNCH((k_cf<V, NQ, SH>), (num_sms() * per_sm), (CF_THREADS), smem, st, X, R, dn, heavy,
+  CTD_LAUNCH((k_cf<V, NQ, DB>), (num_sms() * per_sm), (CF_THREADS), smem, st, X, R, dn, heavy,
              nheavy, multi, nmulti, coff, ccnt, crow, cval, work);
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
 
 template <typename V>
-ctd_status cf_all(int nq, bool sh, const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
+ctd_status cf_all(int nq, int db, const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
                   const Dense& dn,
                   const unsigned long long* coff, uint32_t* ccnt, uint16_t* crow, V* cval,
                   int positive, int64_t list_cap, Arena& a, cudaStream_t st) {
@@ -702,23 +714,20 @@ ctd_status cf_all(int nq, bool sh, const CscDev& X, int64_t n_cols, int64_t n_ro
                counts, coff, crow, cval);
   }
   PhaseScope ph("c_fill_multi", st);
-#define CF_GO(NQV, SHV)                                                                          \
-  return cf_launch<V, NQV, SHV>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, \
+#define CF_GO(NQV, DBV)                                                                          \
+  return cf_launch<V, NQV, DBV>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, \
                                 counts + 2, work, st)
-  if (sh) {
-    switch (nq) {
-      case 1: CF_GO(1, true);
-      case 2: CF_GO(2, true);
-      case 4: CF_GO(4, true);
-      default: CF_GO(8, true);
-    }
+#define CF_NQ(DBV)          \
+  switch (nq) {             \
+    case 1: CF_GO(1, DBV);  \
+    case 2: CF_GO(2, DBV);  \
+    case 4: CF_GO(4, DBV);  \
+    default: CF_GO(8, DBV); \
   }
-  switch (nq) {
-    case 1: CF_GO(1, false);
-    case 2: CF_GO(2, false);
-    case 4: CF_GO(4, false);
-    default: CF_GO(8, false);
-  }
+  if (db == 1) CF_NQ(1)
+  if (db == 2) CF_NQ(2)
+  CF_NQ(4)
+#undef CF_NQ
 #undef CF_GO
 }
 
@@ -735,14 +744,16 @@ ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, in
   const int nq0 = (width + 127) / 128;
   const int nq = nq0 <= 1 ? 1 : nq0 <= 2 ? 2 : nq0 <= 4 ? 4 : 8;
   const int W = nq * 128;
-  // dense rows as int16 when every value of R fits (twice as many rows)
-  const bool sh = R.max_abs >= 0 && R.max_abs <= 32767;
-  const size_t row_b = (size_t)W * (sh ? 2 : 4);
+  // dense rows in the narrowest integer type every value of R fits (int8 or
+  // int16: four or two times as many rows in the same shared memory)
+  const int db = (R.max_abs >= 0 && R.max_abs <= 127) ? 1
+                 : (R.max_abs >= 0 && R.max_abs <= 32767) ? 2 : 4;
+  const size_t row_b = (size_t)W * db;
   // one block per SM: dense rows, the warps' accumulators and row staging in ~220 KB
   const int budget = 220 * 1024;
   int hmax = (int)((budget - (int64_t)(CF_THREADS / 32) * (256 + W * 4)) / (int64_t)row_b);
   hmax = std::max(0, std::min(hmax, CF_MAX_DENSE));
-  const int minlen = std::max(16, 16 * nq);  // shorter rows are cheaper walked sparsely
+  const int minlen = std::max(16, 8 * nq);  // shorter rows are cheaper walked sparsely
   Arena a;
   a.st = st;
   unsigned* hist;
@@ -763,9 +774,9 @@ ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, in
   const unsigned long long* co = reinterpret_cast<const unsigned long long*>(coff);
   const int64_t list_cap = std::max<int64_t>(1, std::min(n_cols, nnz));
   if (fp32)
-    return cf_all<float>(nq, sh, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<float*>(cval),
+    return cf_all<float>(nq, db, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<float*>(cval),
                          positive, list_cap, a, st);
-  return cf_all<double>(nq, sh, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<double*>(cval),
+  return cf_all<double>(nq, db, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<double*>(cval),
                         positive, list_cap, a, st);
 }
 
