@@ -99,13 +99,21 @@ def test_traffic_scaled_full(precision):
     check(F, ref, 1e-6, precision, err_ref=O.projection_error(ref.X, ref.R))
 
 
-@pytest.mark.parametrize("case", ["int64_sums", "wide_registers", "wider_than_registers"])
+@pytest.mark.parametrize("case", ["int64_sums", "wide_registers", "wider_than_registers",
+                                  "int16_rows", "int32_rows"])
 def test_c_fill_paths(case):
     """Each C = R^T X path against the oracle: partial sums beyond int32
-    (||X||_F^2 >= 2^31), s~ in (512, 1024] (the widest register layout) and
-    s~ > 1024 (shared-memory accumulators only)."""
+    (||X||_F^2 >= 2^31), s~ in (512, 1024] (the widest register layout),
+    s~ > 1024 (shared-memory accumulators only), and the dense rows of R
+    stored as int16 (max |R| in (127, 32767]) or int32 (larger), the int8
+    layout being the default of the small-count cases."""
     if case == "int64_sums":
         coo, s = synth.tiny((60, 40, 10), 3000, seed=31, vmax=100_000), 300
+    elif case == "int16_rows":
+        coo, s = synth.tiny((60, 40, 10), 3000, seed=34, vmax=300), 300
+    elif case == "int32_rows":
+        coo, s = synth.tiny((40, 30, 4), 3000, seed=36, vmax=300), 2000
+        coo.val[7] = 33_000  # ||X||^2 stays below 2^31; this fiber is kept
     elif case == "wide_registers":
         coo, s = synth.tiny((900, 600, 2), 15_000, seed=32, vmax=5), 2000
     else:
@@ -115,6 +123,10 @@ def test_c_fill_paths(case):
     kept = ref.R.shape[1]
     if case == "int64_sums":
         assert F.sizes().sqnorm_X >= 2 ** 31
+    elif case in ("int16_rows", "int32_rows"):
+        assert F.sizes().sqnorm_X < 2 ** 31
+        top = np.abs(ref.R).max()
+        assert (127 < top <= 32767) if case == "int16_rows" else top > 32767
     elif case == "wide_registers":
         assert 512 < kept <= 1024
     else:
