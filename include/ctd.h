@@ -312,6 +312,18 @@ CTD_API ctd_status ctd_sample_noalloc(const ctd_coo3* X, int alpha, int64_t s, u
 CTD_API ctd_status ctd_profile(int enable);
 CTD_API ctd_status ctd_profile_report(char* buf, size_t len);
 
+/* Failure-path hooks for tests (no counterpart in the paper).
+ * ctd_fault_inject_alloc(n): after n more successful device allocations
+ *   every allocation of the library fails with CTD_ENOMEM (-1 disables);
+ *   process-wide.  Calls then return CTD_ENOMEM and release what they held.
+ * ctd_selftest_bounded_wait(limit, stream): one thread waits, with the wait
+ *   of the skip-Cholesky's grid barrier, on a word nothing changes, for at
+ *   most `limit` (1 .. 2^24) naps of ~32 ns; it gives up, records the
+ *   timeout in the status word and returns CTD_ETIMEOUT, leaving the
+ *   context usable.  Waits for the stream. */
+CTD_API ctd_status ctd_fault_inject_alloc(int64_t fail_after);
+CTD_API ctd_status ctd_selftest_bounded_wait(int64_t spin_limit, void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 CTD_API const char* ctd_last_error(void);
 

@@ -88,8 +88,21 @@ ctd_status allow_max_smem(const void* fn) {
   return CTD_OK;
 }
 
+// Fault injection for tests (ctd_fault_inject_alloc): after this many more
+// successful device allocations every allocation fails with CTD_ENOMEM;
+// -1 disables.
+static std::atomic<long long> g_alloc_fail_after{-1};
+
 ctd_status dalloc(void** p, size_t bytes, cudaStream_t st) {
   init_pool_once();
+  const long long fa = g_alloc_fail_after.load();
+  if (fa >= 0) {
+    if (fa == 0) {
+      *p = nullptr;
+      return fail(CTD_ENOMEM, "device allocation refused (fault injection)");
+    }
+    g_alloc_fail_after.fetch_sub(1);
+  }
   cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 1, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -757,3 +770,8 @@ extern "C" ctd_status ctd_profile_report(char* buf, size_t len) {
 extern "C" const char* ctd_last_error(void) { return ctd::g_last_error.c_str(); }
 
 extern "C" const char* ctd_version(void) { return "ctd-gb300 0.1 (sm_103a)"; }
+
+extern "C" ctd_status ctd_fault_inject_alloc(int64_t fail_after) {
+  ctd::g_alloc_fail_after.store(fail_after < 0 ? -1 : (long long)fail_after);
+  return CTD_OK;
+}

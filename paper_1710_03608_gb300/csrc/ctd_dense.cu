@@ -223,13 +223,28 @@ struct GridBar {
 };
 
 // returns false if the barrier timed out (or an earlier one did)
+// Wait until *vgen differs from g, at most `limit` naps of ~32 ns; on giving
+// up (or when another waiter already did) set DEV_TIMEOUT and return false.
+__device__ bool bounded_wait_change(volatile unsigned* vgen, unsigned g, unsigned* status,
+                                    long long limit) {
+  volatile unsigned* vstat = status;
+  long long spins = 0;
+  while (*vgen == g) {
+    if ((*vstat & DEV_TIMEOUT) || ++spins > limit) {
+      atomicOr(status, DEV_TIMEOUT);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  return true;
+}
+
 __device__ bool grid_sync(const GridBar& gb) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
     volatile unsigned* vgen = gb.gen;
-    volatile unsigned* vstat = gb.status;
     const unsigned g = *vgen;
     __threadfence();
     const unsigned arrived = atomicAdd(gb.count, 1u);
@@ -237,16 +252,8 @@ __device__ bool grid_sync(const GridBar& gb) {
       *gb.count = 0;
       __threadfence();
       atomicAdd(gb.gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == g) {
-        if ((*vstat & DEV_TIMEOUT) || ++spins > BARRIER_SPIN_LIMIT) {
-          atomicOr(gb.status, DEV_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
+    } else if (!bounded_wait_change(vgen, g, gb.status, BARRIER_SPIN_LIMIT)) {
+      ok = 0;
     }
     __threadfence();
   }
@@ -694,3 +701,31 @@ void launch_thresholds(const double* D, int64_t n, int64_t ldd, double eps2, dou
 }
 
 }  // namespace ctd
+
+// The failure path of the bounded waits, exercised on purpose: one thread
+// waits, with the grid barrier's wait, on a word nothing changes.
+__global__ void k_selftest_wait(unsigned* word, unsigned* status, long long limit) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    volatile unsigned* v = word;
+    ctd::bounded_wait_change(v, *v, status, limit);
+  }
+}
+
+extern "C" ctd_status ctd_selftest_bounded_wait(int64_t spin_limit, void* stream) {
+  using namespace ctd;
+  if (spin_limit < 1 || spin_limit > (1 << 24)) return fail(CTD_EINVAL, "spin_limit must be in [1, 2^24]");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned* buf = nullptr;
+  CTD_TRY(dalloc_n(&buf, 2, st));
+  unsigned h = 0;
+  ctd_status rc = CTD_OK;
+  if (cudaMemsetAsync(buf, 0, 2 * sizeof(unsigned), st) != cudaSuccess) rc = fail(CTD_ECUDA, "memset failed");
+  if (rc == CTD_OK) {
+    CTD_LAUNCH(k_selftest_wait, (1), (32), 0, st, buf, buf + 1, (long long)spin_limit);
+    rc = d2h(&h, buf + 1, 1, st);
+    if (rc == CTD_OK) rc = sync(st);
+  }
+  dfree(buf, st);
+  if (rc != CTD_OK) return rc;
+  return status_from_device(h);
+}

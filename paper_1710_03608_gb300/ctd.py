@@ -32,7 +32,8 @@ EXPORTED = ["ctd_static", "ctd_dynamic_create", "ctd_dynamic_step", "ctd_error",
             "ctd_get_C", "ctd_get_step", "ctd_get_M", "ctd_free", "ctd_last_error",
             "ctd_version", "ctd_profile", "ctd_profile_report", "ctd_sample_noalloc", "ctd_static_batched", "ctd_server_create", "ctd_server_submit",
             "ctd_server_wait", "ctd_server_result", "ctd_server_state", "ctd_server_free",
-            "ctd_ddos_candidates", "ctd_dynamic_from_static"]
+            "ctd_ddos_candidates", "ctd_dynamic_from_static", "ctd_fault_inject_alloc",
+            "ctd_selftest_bounded_wait"]
 
 
 class CtdError(RuntimeError):
@@ -95,6 +96,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ctd_profile_report": [C.c_char_p, C.c_size_t],
         "ctd_ddos_candidates": [P, I64, P, C.POINTER(C.c_int64), C.POINTER(D)],
         "ctd_dynamic_from_static": [P, U64, C.c_uint, P, C.POINTER(P)],
+        "ctd_fault_inject_alloc": [I64],
+        "ctd_selftest_bounded_wait": [I64, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -340,6 +343,19 @@ def sample_noalloc(X: Coo, alpha: int, s: int, seed: int, draws, unique, stream=
     _check(load().ctd_sample_noalloc(C.byref(X.desc), int(alpha), int(s), int(seed), _ptr(draws),
                                      _ptr(unique), C.byref(n), C.c_void_p(_stream_handle(stream))))
     return n.value
+
+
+def fault_inject_alloc(fail_after: int) -> None:
+    """After fail_after more device allocations, every allocation of the
+    library fails (CTD_ENOMEM); -1 disables (a test hook)."""
+    _check(load().ctd_fault_inject_alloc(int(fail_after)))
+
+
+def selftest_bounded_wait(spin_limit: int, stream=None) -> None:
+    """Runs the bounded device wait on a word nothing changes; raises
+    CtdError(CTD_ETIMEOUT) (a test of the failure path)."""
+    st = _stream_handle(stream) if stream is not None else _default_stream()
+    _check(load().ctd_selftest_bounded_wait(int(spin_limit), st))
 
 
 def profile(enable: bool = True) -> None:

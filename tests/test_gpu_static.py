@@ -200,3 +200,36 @@ def test_sqnorm_range():
     F = run(coo2, 1, 64, 1e-6, 0, 0)
     assert F.sizes().sqnorm_X == float(2 * big * big)
     assert F.sizes().s_kept == 2
+
+
+def test_bounded_wait_gives_up_and_context_survives():
+    """The grid barrier's bounded wait, on a word nothing changes, gives up
+    with CTD_ETIMEOUT (no trap, no hang); the next call works."""
+    m = ctd()
+    with pytest.raises(m.CtdError) as e:
+        m.selftest_bounded_wait(1 << 12)
+    assert e.value.status == "CTD_ETIMEOUT"
+    coo = synth.small_uniform()
+    F = run(coo, 1, 50, 1e-6, 0, 0)
+    ref = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 50, 1e-6, 0)
+    assert F.sizes().s_kept == ref.R.shape[1]
+
+
+def test_allocation_failure_is_reported():
+    """With device allocations refused after n more, a call returns
+    CTD_ENOMEM and releases what it held; with the hook off the same call
+    gives the oracle's result."""
+    m = ctd()
+    coo = synth.small_uniform()
+    X = m.Coo.from_synth(coo)
+    try:
+        for n in (0, 3, 10, 20):
+            m.fault_inject_alloc(n)
+            with pytest.raises(m.CtdError) as e:
+                m.ctd_static(X, 1, 50, 1e-6, 0, m.CTD_FP64)
+            assert e.value.status == "CTD_ENOMEM"
+    finally:
+        m.fault_inject_alloc(-1)
+    F = m.ctd_static(X, 1, 50, 1e-6, 0, m.CTD_FP64)
+    ref = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 50, 1e-6, 0)
+    assert np.array_equal(F.R_dense(), ref.R)
