@@ -71,6 +71,16 @@ typedef enum {
 /* Flags for ctd_static. */
 #define CTD_SKIP_C 1u      /* do not materialize C (R, U and the error only) */
 #define CTD_SKIP_ERROR 2u  /* do not compute the relative error */
+/* Also for ctd_dynamic_create: after the matricization (Algorithm 1 line 1)
+ * sort each column's entries of X_(alpha) by (row, value).  The scatter
+ * that builds the columns leaves their entries in the order its atomics
+ * were taken, which changes from run to run; integer results (C, R, the
+ * Gram matrix, the kept set) are exact in any order, but floating-point
+ * sums over a column's entries (the error through Q, W = Q^T X_c of CTD-D)
+ * round differently in the last bits.  With this flag every result is
+ * bit-identical from run to run, at the cost of the sort: about 0.4 ms per
+ * 10^7 nonzeros on GB300, 7% of a CTD-S call on the traffic tensor. */
+#define CTD_DETERMINISTIC 8u
 
 typedef struct {
   int64_t dims[3];     /* I, J, K */
@@ -107,7 +117,7 @@ typedef struct {
  *           a fiber x is kept iff ||res|| > eps ||x||
  *  seed     Philox4x64-10 key; draw k uses counter (k, 0, 0, 0)
  *  precision ctd_precision
- *  flags    CTD_SKIP_C | CTD_SKIP_ERROR
+ *  flags    CTD_SKIP_C | CTD_SKIP_ERROR | CTD_DETERMINISTIC
  *  out      receives a new ctd_factors (free with ctd_free)
  * Errors: CTD_EINVAL (arguments, index out of range), CTD_EOVERFLOW,
  * CTD_ENOMEM, CTD_ECUDA.  An all-zero tensor gives empty factors and
@@ -139,7 +149,8 @@ CTD_API ctd_status ctd_static_batched(int n, const ctd_coo3* X, int alpha, const
  * is the third).  `stream_id` selects an independent Philox counter space
  * (draw k of step t uses counter (k, t, stream_id, 0)).  flags: 0 keeps the
  * new-column block of every step; CTD_KEEP_LAST_C keeps only the newest
- * step's block (older columns can then no longer be read).
+ * step's block (older columns can then no longer be read); CTD_DETERMINISTIC
+ * sorts every slice's columns as for ctd_static.
  * Starting empty, the first kept fiber x gives U = 1/(x^T x) as in
  * Algorithm 1 line 5, so a first step equals ctd_static on that slice.
  */

@@ -234,7 +234,8 @@ ctd_status stage_coo(const ctd_coo3* X, int alpha, Arena& scratch, cudaStream_t 
 }
 
 // Algorithm 1 lines 1-2 (and the layouts the later lines read).
-ctd_status matricize(const CooDev& X, bool want_rows, Arena& A, cudaStream_t st, Matricized* M) {
+ctd_status matricize(const CooDev& X, bool want_rows, Arena& A, cudaStream_t st, Matricized* M,
+                     bool sort_cols) {
   mode_extents(X.dims, X.alpha, &M->n_rows, &M->n_cols);
   M->nnz = X.nnz;
   uint64_t* norm2;
@@ -273,6 +274,14 @@ ctd_status matricize(const CooDev& X, bool want_rows, Arena& A, cudaStream_t st,
     launch_copy_u64(M->rowptr, rowcur, M->n_rows, st);
   }
   launch_coo_scatter(X, norm2, rowcur, M->csc_row, M->csc_val, M->csr_col, M->csr_val, st);
+  if (sort_cols) {
+    // one entry order per column, whatever order the scatter's atomics took;
+    // the column cursors (norm2) are free now and serve as the sort's
+    // scratch when they are long enough
+    uint64_t* keys = norm2;
+    if (M->n_cols < X.nnz) CTD_TRY(A.get(&keys, X.nnz));
+    CTD_TRY(launch_sort_cols(M->colptr, M->n_cols, X.nnz, M->csc_row, M->csc_val, keys, A, st));
+  }
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
@@ -348,7 +357,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   Matricized M;
   {
     PhaseScope ph("matricize", st);
-    STEP(matricize(X, false, scratch, st, &M));
+    STEP(matricize(X, false, scratch, st, &M, (flags & CTD_DETERMINISTIC) != 0));
   }
   F->n_rows = M.n_rows;
   F->n_cols = M.n_cols;

@@ -205,7 +205,8 @@ extern "C" ctd_status ctd_dynamic_create(const int64_t dims2[2], int alpha, int 
     return fail(CTD_EINVAL, "slice dimensions must be in [1, 2^31)");
   if (precision != CTD_FP64 && precision != CTD_FP32_BULK)
     return fail(CTD_EINVAL, "unknown precision");
-  if (flags & ~(unsigned)CTD_KEEP_LAST_C) return fail(CTD_EINVAL, "unknown flag");
+  if (flags & ~(unsigned)(CTD_KEEP_LAST_C | CTD_DETERMINISTIC))
+    return fail(CTD_EINVAL, "unknown flag");
   ctd_factors* F = new ctd_factors();
   F->kind = 1;
   F->alpha = alpha;
@@ -481,7 +482,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   Matricized M;
   {
     PhaseScope ph("d_matricize", st);
-    CTD_TRY(matricize(X, false, scratch, st, &M));
+    CTD_TRY(matricize(X, false, scratch, st, &M, (D.flags & CTD_DETERMINISTIC) != 0));
   }
   int* d_count;
   CTD_TRY(scratch.get(&d_count, 4));

@@ -158,6 +158,11 @@ void launch_coo_scatter(const CooDev& X, uint64_t* colcur, uint64_t* rowcur,
                         int32_t* csr_val, cudaStream_t st);
 
 // Copy u64 -> u64 (cursor initialization) for n elements.
+// Sort every column's entries of a compressed layout by (row, value), in
+// place; `keys` holds at least nnz u64 (scratch for columns longer than one
+// block's shared memory).
+ctd_status launch_sort_cols(const uint64_t* colptr, int64_t n_cols, int64_t nnz, int32_t* row,
+                            int32_t* val, uint64_t* keys, Arena& A, cudaStream_t st);
 void launch_copy_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t st);
 // out[0] = sum of n u32 values (as u64).
 void launch_sum_u32(const uint32_t* in, int64_t n, uint64_t* out, cudaStream_t st);
@@ -364,7 +369,9 @@ struct Matricized {
   CsrX csr() const { return CsrX{rowptr, csr_col, csr_val}; }
 };
 // Algorithm 1 lines 1-2: squared norms, CDF and the column/row layouts.
-ctd_status matricize(const CooDev& X, bool want_rows, Arena& A, cudaStream_t st, Matricized* M);
+// sort_cols: put each column's entries in (row, value) order (CTD_DETERMINISTIC)
+ctd_status matricize(const CooDev& X, bool want_rows, Arena& A, cudaStream_t st, Matricized* M,
+                     bool sort_cols = false);
 
 // ctd_filter.cu: the independence filter over a block of du candidates.
 // S (du x du, ld du) holds the candidates' Schur complement against R^(t)

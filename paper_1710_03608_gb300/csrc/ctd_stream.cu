@@ -312,6 +312,254 @@ void launch_coo_scatter(const CooDev& X, uint64_t* colcur, uint64_t* rowcur, int
                                   csr_col, csr_val);
 }
 
+// ---------------------------------------------------------------------------
+// K5b: one order inside every column
+// ---------------------------------------------------------------------------
+// The scatter leaves a column's entries in the order its cursor atomics were
+// taken, which differs from run to run.  Integer work (the Gram matrix, C) is
+// exact in any order, but floating-point sums over a column's entries (the
+// error of Eq. 3 through Q, W = Q^T X_c of CTD-D) round differently.  These
+// kernels sort each column's entries by (row, value), so those sums take one
+// order whatever the scheduling.  Key: the row in the high 32 bits, the value
+// mapped to an order-preserving unsigned in the low 32.
+__device__ __forceinline__ unsigned long long col_key(int32_t r, int32_t v) {
+  return ((unsigned long long)(uint32_t)r << 32) | (unsigned long long)((uint32_t)v ^ 0x80000000u);
+}
+__device__ __forceinline__ void col_key_split(unsigned long long k, int32_t* r, int32_t* v) {
+  *r = (int32_t)(k >> 32);
+  *v = (int32_t)((uint32_t)k ^ 0x80000000u);
+}
+
+constexpr int SC_WARP = 1024;   // longest column sorted by one warp
+constexpr int SC_BLOCK = 4096;  // piece of a longer column sorted in one block's shared memory
+constexpr int SC_WARPS = 4;     // warps per block of k_sort_cols_mid (8 KB of keys each)
+
+// A warp per 32 consecutive columns.  Columns of 2..32 entries go in chunks
+// of whole columns (at most 32 entries, one per lane), each entry ranked
+// against its own column's entries by shuffles; longer columns are listed
+// for k_sort_cols_mid (up to SC_WARP entries) or k_sort_cols_block.  A
+// chunk is read whole before any of its entries is written.
+__global__ void __launch_bounds__(256)
+    k_sort_cols_short(const unsigned long long* __restrict__ colptr, int64_t n_cols,
+                      int32_t* __restrict__ row, int32_t* __restrict__ val,
+                      int64_t* __restrict__ mids, unsigned* __restrict__ n_mid,
+                      int64_t* __restrict__ longs, unsigned* __restrict__ n_long) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t f0 = gw * 32; f0 < n_cols; f0 += nw * 32) {
+    const int64_t f = f0 + lane;
+    unsigned long long a = 0, b = 0;
+    if (f < n_cols) {
+      a = colptr[f];
+      b = colptr[f + 1];
+    }
+    const long long n = (long long)(b - a);
+    if (n > SC_WARP) longs[atomicAdd(n_long, 1u)] = f;
+    else if (n > 32) mids[atomicAdd(n_mid, 1u)] = f;
+    // short columns: lane prefix sums of their lengths, then chunks
+    const int ns = (n >= 2 && n <= 32) ? (int)n : 0;
+    int incl = ns;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(FULL, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const int excl = incl - ns;
+    const int total = __shfl_sync(FULL, incl, 31);
+    int base = 0;
+    while (base < total) {
+      // the chunk: the short columns that start at or after `base` and end
+      // within base + 32 (at least one: each has at most 32 entries)
+      const unsigned inm = __ballot_sync(FULL, ns > 0 && excl >= base && incl <= base + 32);
+      const int end = __shfl_sync(FULL, incl, 31 - __clz(inm));
+      const int g = base + lane;
+      const bool valid = g < end;
+      // the column (owner lane) of entry g: the lanes whose run ends at or before g
+      int e = 0;
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1)
+        if (__shfl_sync(FULL, incl, e + s - 1) <= g) e += s;
+      e = min(e, 31);
+      const unsigned long long ea = __shfl_sync(FULL, a, e);
+      const int s0 = __shfl_sync(FULL, excl, e) - base;  // the column's first lane
+      const int ne = __shfl_sync(FULL, ns, e);
+      const int t = g - base - s0;                        // place in the column
+      unsigned long long k = ~0ull;
+      if (valid) k = col_key(row[ea + t], val[ea + t]);
+      const int maxn = (int)__reduce_max_sync(FULL, valid ? (unsigned)ne : 0u);
+      int r = 0;
+      for (int j = 0; j < maxn; ++j) {
+        const unsigned long long kj = __shfl_sync(FULL, k, min(s0 + j, 31));
+        r += (j < ne) & ((kj < k) | ((kj == k) & (j < t)));
+      }
+      if (valid && r != t) {
+        int32_t rr, vv;
+        col_key_split(k, &rr, &vv);
+        row[ea + r] = rr;
+        val[ea + r] = vv;
+      }
+      base = end;
+    }
+  }
+}
+
+// A warp per listed column of 33..SC_WARP entries: bitonic sort of the
+// keys in the warp's shared memory (padded to a power of two), the m/2
+// compare-exchanges of each stage spread over the lanes.
+__global__ void __launch_bounds__(SC_WARPS * 32)
+    k_sort_cols_mid(const unsigned long long* __restrict__ colptr,
+                    const int64_t* __restrict__ mids, const unsigned* __restrict__ n_mid,
+                    int32_t* __restrict__ row, int32_t* __restrict__ val) {
+  __shared__ unsigned long long ks_all[SC_WARPS][SC_WARP];
+  unsigned long long* ks = ks_all[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nm = *n_mid;
+  for (int64_t c = gw; c < nm; c += nw) {
+    const int64_t f = mids[c];
+    const unsigned long long a = colptr[f];
+    const int n = (int)(colptr[f + 1] - a);
+    int m = 64;
+    while (m < n) m <<= 1;
+    // loads eight at a time per lane, so their latencies overlap
+    for (int p0 = 0; p0 < m; p0 += 256) {
+      unsigned long long x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int p = p0 + 32 * u + lane;
+        x[u] = p < n ? col_key(row[a + p], val[a + p]) : ~0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int p = p0 + 32 * u + lane;
+        if (p < m) ks[p] = x[u];
+      }
+    }
+    __syncwarp();
+    for (int k = 2; k <= m; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int q = lane; q < (m >> 1); q += 32) {
+          const int e = ((q & ~(j - 1)) << 1) | (q & (j - 1));  // bit j of e clear
+          const int o = e | j;
+          const bool up = (e & k) == 0;
+          const unsigned long long x = ks[e], y = ks[o];
+          if ((x > y) == up) {
+            ks[e] = y;
+            ks[o] = x;
+          }
+        }
+        __syncwarp();
+      }
+    for (int p = lane; p < n; p += 32) {
+      int32_t rr, vv;
+      col_key_split(ks[p], &rr, &vv);
+      row[a + p] = rr;
+      val[a + p] = vv;
+    }
+    __syncwarp();
+  }
+}
+
+// A block per listed column (more than SC_WARP entries): bitonic sort of
+// SC_BLOCK-entry pieces in shared memory; a column of several pieces keeps
+// the sorted pieces in `keys` (indexed like the entries) and puts each entry
+// at its merged rank: its place in its piece plus, in every other piece, the
+// entries below it (and the equal ones of earlier pieces).
+__global__ void __launch_bounds__(1024)
+    k_sort_cols_block(const unsigned long long* __restrict__ colptr,
+                      const int64_t* __restrict__ longs, const unsigned* __restrict__ n_long,
+                      int32_t* __restrict__ row, int32_t* __restrict__ val,
+                      unsigned long long* __restrict__ keys) {
+  __shared__ unsigned long long ks[SC_BLOCK];
+  const unsigned nl = *n_long;
+  for (unsigned g = blockIdx.x; g < nl; g += gridDim.x) {
+    const int64_t f = longs[g];
+    const unsigned long long a = colptr[f];
+    const long long n = (long long)(colptr[f + 1] - a);
+    const long long npc = (n + SC_BLOCK - 1) / SC_BLOCK;
+    for (long long c = 0; c < npc; ++c) {
+      const long long c0 = c * SC_BLOCK;
+      const int len = (int)min((long long)SC_BLOCK, n - c0);
+      int m = 1;
+      while (m < len) m <<= 1;
+      for (int e = threadIdx.x; e < m; e += blockDim.x)
+        ks[e] = e < len ? col_key(row[a + c0 + e], val[a + c0 + e]) : ~0ull;
+      __syncthreads();
+      for (int k = 2; k <= m; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int q = threadIdx.x; q < (m >> 1); q += blockDim.x) {
+            const int e = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+            const int o = e | j;
+            const bool up = (e & k) == 0;
+            const unsigned long long x = ks[e], y = ks[o];
+            if ((x > y) == up) {
+              ks[e] = y;
+              ks[o] = x;
+            }
+          }
+          __syncthreads();
+        }
+      for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        if (npc == 1) {
+          int32_t rr, vv;
+          col_key_split(ks[e], &rr, &vv);
+          row[a + e] = rr;
+          val[a + e] = vv;
+        } else {
+          keys[a + c0 + e] = ks[e];
+        }
+      }
+      __syncthreads();
+    }
+    if (npc > 1) {
+      for (long long p = threadIdx.x; p < n; p += blockDim.x) {
+        const long long cp = p / SC_BLOCK;
+        const unsigned long long k = keys[a + p];
+        long long r = p - cp * SC_BLOCK;
+        for (long long c = 0; c < npc; ++c) {
+          if (c == cp) continue;
+          const unsigned long long* ck = keys + a + c * SC_BLOCK;
+          int lo = 0, hi = (int)min((long long)SC_BLOCK, n - c * SC_BLOCK);
+          while (lo < hi) {
+            const int md = (lo + hi) >> 1;
+            const bool below = c < cp ? ck[md] <= k : ck[md] < k;
+            if (below) lo = md + 1;
+            else hi = md;
+          }
+          r += lo;
+        }
+        int32_t rr, vv;
+        col_key_split(k, &rr, &vv);
+        row[a + r] = rr;
+        val[a + r] = vv;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+ctd_status launch_sort_cols(const uint64_t* colptr, int64_t n_cols, int64_t nnz, int32_t* row,
+                            int32_t* val, uint64_t* keys, Arena& A, cudaStream_t st) {
+  if (nnz <= 1) return CTD_OK;
+  int64_t *mids, *longs;
+  unsigned* counts;
+  CTD_TRY(A.get(&mids, nnz / 33 + 1));
+  CTD_TRY(A.get(&longs, nnz / (SC_WARP + 1) + 1));
+  CTD_TRY(A.get(&counts, 2));
+  CTD_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned), st));
+  const unsigned long long* cp = reinterpret_cast<const unsigned long long*>(colptr);
+  CTD_LAUNCH(k_sort_cols_short, (grid_for(n_cols, 256, (int64_t)num_sms() * 8)), (256), 0, st,
+             cp, n_cols, row, val, mids, counts, longs, counts + 1);
+  CTD_LAUNCH(k_sort_cols_mid, ((unsigned)num_sms() * 6), (SC_WARPS * 32), 0, st, cp, mids, counts,
+             row, val);
+  CTD_LAUNCH(k_sort_cols_block, ((unsigned)num_sms()), (1024), 0, st, cp, longs, counts + 1, row,
+             val, reinterpret_cast<unsigned long long*>(keys));
+  return CTD_OK;
+}
+
 __global__ void k_copy_u64(const unsigned long long* __restrict__ in, unsigned long long* out,
                            int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;

@@ -23,6 +23,7 @@ CTD_MEM_HOST = 1
 CTD_SKIP_C = 1
 CTD_SKIP_ERROR = 2
 CTD_KEEP_LAST_C = 4
+CTD_DETERMINISTIC = 8
 
 STATUS = {0: "CTD_OK", 1: "CTD_EINVAL", 2: "CTD_ENOMEM", 3: "CTD_EOVERFLOW", 4: "CTD_ECUDA",
           5: "CTD_ETIMEOUT", 6: "CTD_ENOTSUP"}

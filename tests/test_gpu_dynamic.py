@@ -170,6 +170,24 @@ def test_near_saturation_weak_keeps():
     assert abs(G.error() - e) <= error_tol(1, e)
 
 
+def test_repeat_streams_bit_identical():
+    """With CTD_DETERMINISTIC, two CTD-D runs over the same 1,000 x 1,000
+    traffic slices (FP32 bulk) give bit-identical errors, kept counts and R
+    after every step."""
+    m = ctd()
+    S = synth.traffic_stream_20k(scale=0.05, steps=10)
+    runs = []
+    for _ in range(2):
+        G = m.Dynamic(S.dims2, 1, m.CTD_FP32_BULK, 0, 0, m.CTD_DETERMINISTIC)
+        hist = []
+        for t in range(S.steps):
+            G.step_slice(m.Coo.from_synth(S.slice(t)), 400, 1e-6)
+            info, _ = G.step(t)
+            hist.append((int(info[1]), G.error()))
+        runs.append((hist, G.R_dense().tobytes()))
+    assert runs[0] == runs[1]
+
+
 def _stack(slices):
     I, J = slices[0].dims[0], slices[0].dims[1]
     i = np.concatenate([s.i for s in slices])

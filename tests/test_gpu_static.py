@@ -99,6 +99,16 @@ def test_traffic_scaled_full(precision):
     check(F, ref, 1e-6, precision, err_ref=O.projection_error(ref.X, ref.R))
 
 
+def test_deterministic_flag_parity():
+    """The sorted-column path (CTD_DETERMINISTIC) against the oracle on the
+    2,000 x 2,000 x 200 traffic tensor, FP32 bulk."""
+    m = ctd()
+    coo = synth.traffic_10m(scale=0.2)
+    F = run(coo, 1, 500, 1e-6, 0, 1, flags=m.CTD_DETERMINISTIC)
+    ref = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 500, 1e-6, 0)
+    check(F, ref, 1e-6, 1, err_ref=O.projection_error(ref.X, ref.R))
+
+
 @pytest.mark.parametrize("case", ["int64_sums", "wide_registers", "wider_than_registers",
                                   "int16_rows", "int32_rows"])
 def test_c_fill_paths(case):
@@ -183,6 +193,25 @@ def test_traffic_10m_full_size(traffic_full):
     cols = np.concatenate([rng.choice(nz, 200, replace=False),
                            nz[np.argsort(np.diff(ref.X.ptr)[nz])[-20:]], [0, ref.X.n_cols - 1]])
     check(F, ref, 1e-6, 1, full_c=False, c_cols=cols, err_ref=O.projection_error(ref.X, ref.R))
+
+
+def test_repeat_calls_bit_identical(traffic_full):
+    """With CTD_DETERMINISTIC, three calls on the 10^7-nonzero workload (FP32
+    bulk, then FP64) give bit-identical U, C and error: each column's
+    entries are put in one order after the matricization, so no
+    floating-point sum depends on the order the scatter's atomics took."""
+    m = ctd()
+    coo, _ = traffic_full
+    X = m.Coo.from_synth(coo)
+    for precision in (1, 0):
+        seen = []
+        for _ in range(3):
+            F = m.ctd_static(X, 1, 500, 1e-6, 0, precision, m.CTD_DETERMINISTIC)
+            p, r, v = F.C()
+            seen.append((F.error(), F.U().tobytes(), hash(p.tobytes()), hash(r.tobytes()),
+                         hash(v.tobytes())))
+            F.free()
+        assert all(x == seen[0] for x in seen[1:])
 
 
 def test_sqnorm_range():
