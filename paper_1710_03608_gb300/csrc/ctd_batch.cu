@@ -30,15 +30,27 @@ extern "C" ctd_status ctd_static_batched(int n, const ctd_coo3* X, int alpha, co
   CTD_CUDA(cudaGetDevice(&dev));
   cudaStream_t caller = static_cast<cudaStream_t>(stream);
   // fork: worker streams wait for the caller's stream
-  cudaEvent_t fork;
-  CTD_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-  CTD_CUDA(cudaEventRecord(fork, caller));
+  cudaEvent_t fork = nullptr;
   std::vector<cudaStream_t> st(workers, nullptr);
   std::vector<cudaEvent_t> join(workers, nullptr);
-  for (int w = 0; w < workers; ++w) {
-    CTD_CUDA(cudaStreamCreateWithFlags(&st[w], cudaStreamNonBlocking));
-    CTD_CUDA(cudaEventCreateWithFlags(&join[w], cudaEventDisableTiming));
-    CTD_CUDA(cudaStreamWaitEvent(st[w], fork, 0));
+  // on a failed set-up step, release what was created before it
+  auto release = [&] {
+    for (int w = 0; w < workers; ++w) {
+      if (join[w]) cudaEventDestroy(join[w]);
+      if (st[w]) cudaStreamDestroy(st[w]);
+    }
+    if (fork) cudaEventDestroy(fork);
+  };
+  cudaError_t ce = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventRecord(fork, caller);
+  for (int w = 0; w < workers && ce == cudaSuccess; ++w) {
+    ce = cudaStreamCreateWithFlags(&st[w], cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&join[w], cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st[w], fork, 0);
+  }
+  if (ce != cudaSuccess) {
+    release();
+    return fail(CTD_ECUDA, std::string("ctd_static_batched set-up: ") + cudaGetErrorString(ce));
   }
   // largest tensors first: the queue's tail is short work
   std::vector<int> order(n);
@@ -64,7 +76,15 @@ extern "C" ctd_status ctd_static_batched(int n, const ctd_coo3* X, int alpha, co
     cudaEventRecord(join[w], st[w]);
   };
   std::vector<std::thread> pool;
-  for (int w = 1; w < workers; ++w) pool.emplace_back(work, w);
+  // a thread that cannot be started leaves its share of the queue to the
+  // others (no exception crosses the C ABI)
+  for (int w = 1; w < workers; ++w) {
+    try {
+      pool.emplace_back(work, w);
+    } catch (...) {
+      cudaEventRecord(join[w], st[w]);
+    }
+  }
   work(0);
   for (auto& th : pool) th.join();
   // join: the caller's stream waits for every worker stream

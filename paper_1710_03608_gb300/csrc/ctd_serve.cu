@@ -14,6 +14,7 @@
 #include <condition_variable>
 #include <deque>
 #include <mutex>
+#include <new>
 #include <thread>
 #include <vector>
 
@@ -133,7 +134,8 @@ extern "C" ctd_status ctd_server_create(int n_streams, const int64_t dims2[2], i
   if (!(eps >= 0.0 && eps < 1.0)) return fail(CTD_EINVAL, "eps must be in [0, 1)");
   if (workers <= 0) workers = 8;
   if (!(mem_fraction > 0.0 && mem_fraction <= 1.0)) mem_fraction = 0.9;
-  ctd_server* S = new ctd_server();
+  ctd_server* S = new (std::nothrow) ctd_server();
+  if (!S) return fail(CTD_ENOMEM, "host allocation failed");
   S->n_streams = n_streams;
   S->d = d;
   S->eps = eps;
@@ -156,7 +158,17 @@ extern "C" ctd_status ctd_server_create(int n_streams, const int64_t dims2[2], i
       ctd_server_free(S);
       return fail(CTD_ECUDA, "stream creation failed");
     }
-  for (int w = 0; w < workers; ++w) S->pool.emplace_back(worker, S, w);
+  for (int w = 0; w < workers; ++w) {
+    try {
+      S->pool.emplace_back(worker, S, w);
+    } catch (...) {  // no exception crosses the C ABI; run with the threads started
+      if (S->pool.empty()) {
+        ctd_server_free(S);
+        return fail(CTD_ENOMEM, "could not start a worker thread");
+      }
+      break;
+    }
+  }
   *out = S;
   return CTD_OK;
 }
