@@ -33,7 +33,7 @@ ctd_status status_from_device(unsigned w) {
 // ---------------------------------------------------------------------------
 static std::atomic<long long> g_launches{0};
 static std::mutex g_prof_mu;
-static bool g_prof = false;
+static std::atomic<bool> g_prof{false};  // read by every phase scope, on any thread
 struct PhaseRec {
   std::string name;
   cudaEvent_t a, b;
@@ -628,9 +628,11 @@ static ctd_status csc_to_host_sorted(const uint64_t* dptr, const int32_t* drow, 
 extern "C" ctd_status ctd_get_R(const ctd_factors* F, int64_t* colptr, int32_t* row,
                                 int32_t* val) {
   if (!F || !colptr || (F->nnz_R && (!row || !val))) return fail(CTD_EINVAL, "NULL argument");
-  if (F->kind == 1) return dyn_R(F, colptr, row, val);
-  return csc_to_host_sorted(F->Rcolptr, F->Rrow, F->Rval, F->s_kept, F->nnz_R, F->stream, colptr,
-                            row, val);
+  return guarded([&] {
+    if (F->kind == 1) return dyn_R(F, colptr, row, val);
+    return csc_to_host_sorted(F->Rcolptr, F->Rrow, F->Rval, F->s_kept, F->nnz_R, F->stream,
+                              colptr, row, val);
+  });
 }
 
 extern "C" ctd_status ctd_get_U(const ctd_factors* F, double* U) {
@@ -659,7 +661,7 @@ __global__ void k_c_columns(const unsigned long long* __restrict__ coff,
 extern "C" ctd_status ctd_get_C_columns(const ctd_factors* F, int64_t ncols, const int64_t* cols,
                                         double* out) {
   if (!F || ncols < 0 || (ncols && (!cols || !out))) return fail(CTD_EINVAL, "NULL argument");
-  if (F->kind == 1) return dyn_C_columns(F, ncols, cols, out);
+  if (F->kind == 1) return guarded([&] { return dyn_C_columns(F, ncols, cols, out); });
   if (!F->Coff) return fail(CTD_EINVAL, "C was not materialized (CTD_SKIP_C)");
   for (int64_t c = 0; c < ncols; ++c)
     if (cols[c] < 0 || cols[c] >= F->n_cols) return fail(CTD_EINVAL, "column out of range");
@@ -691,10 +693,17 @@ extern "C" ctd_status ctd_get_C_columns(const ctd_factors* F, int64_t ncols, con
   return sync(st);
 }
 
+static ctd_status get_C_host(const ctd_factors* F, int64_t* colptr, int32_t* row, double* val);
+
 extern "C" ctd_status ctd_get_C(const ctd_factors* F, int64_t* colptr, int32_t* row, double* val) {
   if (!F || !colptr) return fail(CTD_EINVAL, "NULL argument");
   if (F->kind != 0) return fail(CTD_ENOTSUP, "CTD-D keeps C implicit; use ctd_get_C_columns");
   if (!F->Coff) return fail(CTD_EINVAL, "C was not materialized (CTD_SKIP_C)");
+  return guarded([&] { return get_C_host(F, colptr, row, val); });
+}
+
+// C's stored layout (offsets with capacity, counts, rows, values) to a packed host CSC.
+static ctd_status get_C_host(const ctd_factors* F, int64_t* colptr, int32_t* row, double* val) {
   cudaStream_t st = F->stream;
   const int64_t n = F->n_cols;
   std::vector<uint64_t> off(n + 1);

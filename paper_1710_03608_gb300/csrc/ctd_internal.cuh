@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -17,6 +19,19 @@ namespace ctd {
 // ---------------------------------------------------------------------------
 void set_error(const std::string& msg);
 ctd_status fail(ctd_status st, const std::string& msg);
+
+// Runs fn() and turns a host allocation failure inside it into CTD_ENOMEM:
+// no exception may cross the C ABI (getters size host buffers by the data).
+template <typename Fn>
+ctd_status guarded(Fn&& fn) {
+  try {
+    return fn();
+  } catch (const std::bad_alloc&) {
+    return fail(CTD_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(CTD_EINVAL, std::string("unexpected host error: ") + e.what());
+  }
+}
 
 #define CTD_CUDA(call)                                                        \
   do {                                                                        \
