@@ -24,7 +24,7 @@
  *    and synchronize.
  *  - No call throws.  Every call returns a ctd_status; on failure
  *    ctd_last_error() gives a message (per thread).  Outputs are left
- *    untouched on failure.
+ *    untouched on failure (for the in-place ctd_dynamic_step, see there).
  *  - Integer work (norms, CDF, draws, dedup, R, C) is exact.  U and the
  *    relative error are computed in FP64; with CTD_FP32_BULK the stored C
  *    values are float (each is an exactly rounded integer).
@@ -168,6 +168,11 @@ CTD_API ctd_status ctd_dynamic_create(const int64_t dims2[2], int alpha, int pre
  * The new columns' block R^(t+1)^T dX is stored exactly; the lower-left
  * block of Eq. (C_t+1_final) is kept as M_{t+1} = ((dR)^T R^(t)) U^(t)
  * (the paper's left-to-right order) and applied to old columns on request.
+ * On failure: a step that failed before it changed the state (invalid
+ * arguments, an error while reading dX or drawing its columns) leaves the
+ * state as it was, and the step may be retried.  A step that failed later
+ * (e.g. CTD_ENOMEM while growing R) leaves the state incomplete: every
+ * later step and getter on it returns CTD_EINVAL; only ctd_free applies.
  */
 CTD_API ctd_status ctd_dynamic_step(ctd_factors* state, const ctd_coo3* dX, int64_t d,
                             double eps, void* stream);

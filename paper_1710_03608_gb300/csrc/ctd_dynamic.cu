@@ -152,6 +152,7 @@ struct ctd_factors::Dyn {
   int64_t last_d = 0, last_du = 0;
   bool all_positive = true;          // every value seen so far > 0
   double max_T = 0.0;                // largest ||dX||^2 so far
+  bool incomplete = false;           // a step failed after it began to change the state
   int64_t* lastI = nullptr;          // device [8192]
   int64_t* lastIu = nullptr;
 };
@@ -252,7 +253,10 @@ static ctd_status grow_U(ctd_factors* F, int64_t d, int64_t n, cudaStream_t st) 
   const int64_t rows = F->n_rows;
   double *L2, *Q2;
   CTD_TRY(dalloc_n(&L2, (size_t)cap * cap, st));
-  CTD_TRY(dalloc_n(&Q2, (size_t)cap * rows, st));
+  if (ctd_status rc = dalloc_n(&Q2, (size_t)cap * rows, st); rc != CTD_OK) {
+    dfree(L2, st);
+    return rc;
+  }
   CTD_CUDA(cudaMemsetAsync(L2, 0, (size_t)cap * cap * 8, st));
   CTD_CUDA(cudaMemsetAsync(Q2, 0, (size_t)cap * rows * 8, st));
   if (d > 0) {
@@ -462,6 +466,8 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   if (d < 1 || d > 8192) return fail(CTD_EINVAL, "d must be in [1, 8192]");
   if (!(eps >= 0.0 && eps < 1.0)) return fail(CTD_EINVAL, "eps must be in [0, 1)");
   auto& D = *F->dyn;
+  if (D.incomplete)
+    return fail(CTD_EINVAL, "an earlier step on this state failed part-way; create a new state");
   if (dXd->dims[0] != D.I || dXd->dims[1] != D.J || dXd->dims[2] != 1)
     return fail(CTD_EINVAL, "slice dimensions differ from the state's");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -473,6 +479,22 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   const int64_t dt = F->s_kept;
   const bool fp32 = F->precision == CTD_FP32_BULK;
   StepRec rec;
+  // a step that fails returns the device buffers of its own record
+  bool recorded = false;
+  struct RecRelease {
+    StepRec& r;
+    bool& done;
+    cudaStream_t st;
+    ~RecRelease() {
+      if (done) return;
+      dfree(r.WK, st);
+      dfree(r.M, st);
+      dfree(r.Coff, st);
+      dfree(r.Ccnt, st);
+      dfree(r.Crow, st);
+      dfree(r.Cval, st);
+    }
+  } rec_release{rec, recorded, st};
   rec.d_draws = d;
   rec.d_before = dt;
   rec.nnz = X.nnz;
@@ -503,6 +525,9 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   CTD_TRY(status_from_device(status));
   rec.sq = (double)T;
   rec.d_unique = du;
+  // from here on the step changes the state; a failure below leaves it
+  // incomplete, and later steps refuse it
+  D.incomplete = true;
   if (X.nnz > 0 && minval <= 0) D.all_positive = false;
   D.max_T = std::max(D.max_T, (double)T);
   D.last_d = T ? d : 0;
@@ -843,12 +868,14 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
     prev.Cval = nullptr;
   }
   D.steps.push_back(rec);
+  recorded = true;
   D.t += 1;
   F->nnz_X = D.nnz_total;
   F->T = (uint64_t)D.sq_total;
   F->nnz_C = D.nnzC_total;
   F->have_err = true;
   F->err = D.err_den > 0 ? D.err_num / D.err_den : 0.0;
+  D.incomplete = false;
   return CTD_OK;
 }
 
@@ -1025,9 +1052,19 @@ extern "C" ctd_status ctd_dynamic_from_static(const ctd_factors* S, uint64_t str
   return CTD_OK;
 }
 
+// Getters refuse a state that a failed step left part-way changed.
+namespace ctd {
+ctd_status dyn_check_complete(const ctd_factors* F) {
+  if (F->kind == 1 && F->dyn && F->dyn->incomplete)
+    return fail(CTD_EINVAL, "an earlier step on this state failed part-way; create a new state");
+  return CTD_OK;
+}
+}  // namespace ctd
+
 extern "C" ctd_status ctd_get_step(const ctd_factors* F, int64_t t, int64_t info[4],
                                    double sq[2]) {
   if (!F || !F->dyn) return fail(CTD_EINVAL, "not a CTD-D state");
+  CTD_TRY(dyn_check_complete(F));
   if (t < 0 || t >= F->dyn->t) return fail(CTD_EINVAL, "step out of range");
   const StepRec& r = F->dyn->steps[t];
   if (info) {
@@ -1061,6 +1098,7 @@ static ctd_status ensure_M(const ctd_factors* Fc, int64_t t) {
 
 extern "C" ctd_status ctd_get_M(const ctd_factors* F, int64_t t, double* M) {
   if (!F || !F->dyn) return fail(CTD_EINVAL, "not a CTD-D state");
+  CTD_TRY(dyn_check_complete(F));
   if (t < 0 || t >= F->dyn->t) return fail(CTD_EINVAL, "step out of range");
   const StepRec& r = F->dyn->steps[t];
   const size_t n = (size_t)r.d_kept * r.d_before;
@@ -1077,6 +1115,7 @@ extern "C" ctd_status ctd_get_M(const ctd_factors* F, int64_t t, double* M) {
 namespace ctd {
 
 ctd_status dyn_sizes(const ctd_factors* F, ctd_sizes* o) {
+  CTD_TRY(dyn_check_complete(F));
   const auto& D = *F->dyn;
   o->n_rows = F->n_rows;
   o->n_cols = F->n_cols;
@@ -1092,6 +1131,7 @@ ctd_status dyn_sizes(const ctd_factors* F, ctd_sizes* o) {
 }
 
 ctd_status dyn_samples(const ctd_factors* F, int64_t* I, int64_t* Iu) {
+  CTD_TRY(dyn_check_complete(F));
   const auto& D = *F->dyn;
   if (I) CTD_TRY(d2h(I, D.lastI, (size_t)D.last_d, F->stream));
   if (Iu) CTD_TRY(d2h(Iu, D.lastIu, (size_t)D.last_du, F->stream));
@@ -1099,6 +1139,7 @@ ctd_status dyn_samples(const ctd_factors* F, int64_t* I, int64_t* Iu) {
 }
 
 ctd_status dyn_fibers(const ctd_factors* F, int64_t* fiber, int64_t* step) {
+  CTD_TRY(dyn_check_complete(F));
   const auto& D = *F->dyn;
   for (size_t c = 0; c < D.fiber_id.size(); ++c) {
     if (fiber) fiber[c] = D.fiber_id[c];
@@ -1110,6 +1151,7 @@ ctd_status dyn_fibers(const ctd_factors* F, int64_t* fiber, int64_t* step) {
 // U^(t) = (R^T R)^{-1} = L^{-T} L^{-1}, formed from the maintained factor on
 // the first request after a step that kept fibers, then cached.
 ctd_status dyn_U(const ctd_factors* Fc, double* U) {
+  CTD_TRY(dyn_check_complete(Fc));
   ctd_factors* F = const_cast<ctd_factors*>(Fc);
   const int64_t n = F->s_kept;
   if (n == 0) return CTD_OK;
@@ -1134,6 +1176,7 @@ ctd_status dyn_U(const ctd_factors* Fc, double* U) {
 // Column (t, f) of C^(now): the step's exact block, then the rows each later
 // step appends, M_{t'} times the column so far (Eq. C_t+1_final, line 18).
 ctd_status dyn_C_columns(const ctd_factors* F, int64_t ncols, const int64_t* cols, double* out) {
+  CTD_TRY(dyn_check_complete(F));
   const auto& D = *F->dyn;
   const int64_t h = F->s_kept;
   cudaStream_t st = F->stream;
@@ -1195,6 +1238,7 @@ ctd_status dyn_C_columns(const ctd_factors* F, int64_t ncols, const int64_t* col
 }
 
 ctd_status dyn_R(const ctd_factors* F, int64_t* colptr, int32_t* row, int32_t* val) {
+  CTD_TRY(dyn_check_complete(F));
   const int64_t n = F->s_kept, nnz = F->nnz_R;
   std::vector<uint64_t> p(n + 1);
   std::vector<int32_t> r(nnz), v(nnz);

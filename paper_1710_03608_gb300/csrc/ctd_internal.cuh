@@ -487,4 +487,6 @@ ctd_status dyn_fibers(const ctd_factors* F, int64_t* fiber, int64_t* step);
 ctd_status dyn_U(const ctd_factors* F, double* U);
 ctd_status dyn_C_columns(const ctd_factors* F, int64_t ncols, const int64_t* cols, double* out);
 ctd_status dyn_R(const ctd_factors* F, int64_t* colptr, int32_t* row, int32_t* val);
+// CTD_EINVAL if a failed step left this CTD-D state part-way changed; CTD_OK otherwise
+ctd_status dyn_check_complete(const ctd_factors* F);
 }  // namespace ctd

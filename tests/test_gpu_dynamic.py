@@ -112,6 +112,51 @@ def test_keep_last_c_releases_older_blocks():
         G.C_columns([0])
 
 
+def test_failed_step_is_either_harmless_or_refused():
+    """A step whose device allocations are refused returns CTD_ENOMEM.  If
+    it failed before it changed the state, the same step succeeds afterwards
+    and the stream ends as one that never failed; if it failed part-way, the
+    state refuses further steps and getters (CTD_EINVAL) instead of going on
+    from a half-updated R."""
+    m = ctd()
+    dims2 = (60, 40)
+    sl = slices_small(3, dims2, seed=12)
+    X = [m.Coo.from_synth(s) for s in sl]
+    ref = m.Dynamic(dims2, 1, m.CTD_FP64, 5)
+    for x in X:
+        ref.step_slice(x, 10, 1e-6)
+    R_ref, e_ref = ref.R_dense(), ref.error()
+    outcomes = set()
+    try:
+        for n in (0, 4, 8, 12, 16, 24, 32, 48, 64, 96, 128):
+            G = m.Dynamic(dims2, 1, m.CTD_FP64, 5)
+            G.step_slice(X[0], 10, 1e-6)
+            m.fault_inject_alloc(n)
+            try:
+                G.step_slice(X[1], 10, 1e-6)
+                outcomes.add("no refusal reached")
+                continue
+            except m.CtdError as e:
+                assert e.status == "CTD_ENOMEM"
+            finally:
+                m.fault_inject_alloc(-1)
+            try:
+                G.step_slice(X[1], 10, 1e-6)
+            except m.CtdError as e:
+                assert e.status == "CTD_EINVAL" and "part-way" in str(e)
+                with pytest.raises(m.CtdError):
+                    G.sizes()
+                outcomes.add("refused")
+                continue
+            G.step_slice(X[2], 10, 1e-6)
+            assert np.array_equal(G.R_dense(), R_ref)
+            assert abs(G.error() - e_ref) <= 1e-10 * max(e_ref, 1e-2)
+            outcomes.add("harmless")
+    finally:
+        m.fault_inject_alloc(-1)
+    assert {"refused", "harmless"} <= outcomes, outcomes
+
+
 def test_traffic_stream_scaled():
     """Slices of 1,000 x 1,000 (1,250 nonzeros each, Zipf(1.1), Poisson(2)+1)
     with a planted 10 x 2 block of Poisson(40) counts at steps 40-45
