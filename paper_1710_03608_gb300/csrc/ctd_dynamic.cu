@@ -75,33 +75,6 @@ __global__ void k_transpose_f64(const double* __restrict__ A, int64_t lda, int64
   }
 }
 
-// dense (ld x J) FP64 copy of a sparse new-column block (rows < height)
-template <typename V>
-__global__ void k_densify(const unsigned long long* __restrict__ coff,
-                          const unsigned* __restrict__ ccnt, const uint16_t* __restrict__ crow,
-                          const V* __restrict__ cval, int64_t n_cols, double* __restrict__ out,
-                          int64_t ld) {
-  for (int64_t f = blockIdx.x; f < n_cols; f += gridDim.x) {
-    const unsigned long long o = coff[f];
-    for (unsigned q = threadIdx.x; q < ccnt[f]; q += blockDim.x)
-      out[f * ld + crow[o + q]] = (double)cval[o + q];
-  }
-}
-
-__global__ void k_sumsq(const double* __restrict__ A, int64_t n, double* __restrict__ out) {
-  __shared__ double part[32];
-  double acc = 0.0;
-  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc = fma(A[e], A[e], acc);
-  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
-    *out = t;
-  }
-}
-
 // V(:, c) = candidate column idx[c] (dense n_rows x n, V zeroed beforehand)
 __global__ void k_densify_cols(const unsigned long long* __restrict__ cptr,
                                const int32_t* __restrict__ crow, const int32_t* __restrict__ cval,

@@ -80,7 +80,6 @@ void launch_sample(const uint64_t* cdf, int64_t n, int64_t s, uint64_t seed, uin
 // K4: sort-unique of s <= 8192 draws in one block (bitonic sort in shared
 // memory, then a flag scan).  Negative entries (no draw) are dropped.
 // ---------------------------------------------------------------------------
-constexpr int SU_MAX = 8192;
 constexpr int SU_THREADS = 1024;
 
 __global__ void __launch_bounds__(SU_THREADS) k_sort_unique(const int64_t* __restrict__ in,
