@@ -43,7 +43,6 @@ def test_binding_names_match_header(lib):
 
 def test_no_compute_without_gpu_raises_cleanly(lib):
     """Without a GPU a call fails with a status, not a crash or a CPU fallback."""
-    import numpy as np
     import torch
     if torch.cuda.is_available():
         pytest.skip("GPU present")
