@@ -51,7 +51,7 @@ extern "C" {
 typedef enum {
   CTD_OK = 0,
   CTD_EINVAL = 1,     /* bad argument, index out of range, size over a limit */
-  CTD_ENOMEM = 2,     /* device allocation failed */
+  CTD_ENOMEM = 2,     /* device allocation failed (host allocation, in a getter) */
   CTD_EOVERFLOW = 3,  /* ||X||_F^2 or an exact product does not fit 64 bits */
   CTD_ECUDA = 4,      /* a CUDA runtime call failed */
   CTD_ETIMEOUT = 5,   /* a bounded device wait gave up */

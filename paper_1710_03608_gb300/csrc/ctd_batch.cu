@@ -50,6 +50,7 @@ extern "C" ctd_status ctd_static_batched(int n, const ctd_coo3* X, int alpha, co
   }
   if (ce != cudaSuccess) {
     release();
+    for (int t = 0; t < n; ++t) out[t] = nullptr;
     return fail(CTD_ECUDA, std::string("ctd_static_batched set-up: ") + cudaGetErrorString(ce));
   }
   // largest tensors first: the queue's tail is short work
