@@ -165,6 +165,46 @@ def test_traffic_stream_scaled():
     run_stream(list(stream), stream.dims2, 400, 1e-6, 0, 1, check_every=False)
 
 
+def test_traffic_stream_full_size_sampled():
+    """The 2*10^4 x 2*10^4 stream at full size (5*10^5 nonzeros per slice,
+    d = 400, FP32 bulk, empty start), three steps, in the launch
+    configuration of the stream measurement.  Checked per step against the
+    oracle where it is cheap at this size: the draws and unique draws equal
+    the oracle's (its Philox targets on the slice's exact CDF, Algorithm 2
+    lines 1-4); every column R gained is the slice's own fiber, bit for bit;
+    d~_t stays within the unique draws so far and I_alpha; the error lies
+    in [0, 1]."""
+    m = ctd()
+    S = synth.traffic_stream_20k(steps=3)
+    I, J = S.dims2
+    G = m.Dynamic(S.dims2, 1, m.CTD_FP32_BULK, 0)
+    n_unique = 0
+    for t in range(S.steps):
+        sl = S.slice(t)
+        G.step_slice(m.Coo.from_synth(sl), 400, 1e-6)
+        rows, cols, _, n_cols = O.matricize(sl.dims, sl.i, sl.j, sl.k, 1)
+        vals = np.asarray(sl.val, dtype=np.int64)
+        ref_I = O.sample_columns(O.cdf(O.column_sqnorms(cols, vals, n_cols)), 400, 0,
+                                 step=t, stream=0)
+        gI, gIu = G.samples()
+        assert np.array_equal(gI, ref_I)
+        assert np.array_equal(gIu, O.unique_columns(ref_I))
+        n_unique += gIu.shape[0]
+        fib, fstep = G.fibers()
+        new = np.nonzero(fstep == t)[0]
+        assert np.isin(fib[new], gIu).all()
+        p, r, v = G.R()
+        for c in new:
+            mask = cols == fib[c]
+            o = np.argsort(rows[mask], kind="stable")
+            assert np.array_equal(r[p[c]:p[c + 1]], rows[mask][o])
+            assert np.array_equal(v[p[c]:p[c + 1]], vals[mask][o])
+        sz = G.sizes()
+        assert sz.t_steps == t + 1 and sz.s_kept == fib.shape[0]
+        assert sz.s_kept <= min(I, n_unique)
+        assert 0.0 <= G.error() <= 1.0
+
+
 def test_planted_block_stream_scaled():
     """The same stream shape over steps 36..47 so the planted block (steps
     40-45) arrives mid-stream."""
