@@ -1,0 +1,81 @@
+"""The ncu summary parsers behind profiles/ (CPU): launch shares with unit
+scaling, and the DRAM-traffic record scaled to a full launch and tagged
+with the kernels' source hash (which the bench checks before reporting it)."""
+import csv
+import hashlib
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+HEADER = ["ID", "Process ID", "Process Name", "Host Name", "Kernel Name", "Context", "Stream",
+          "Block Size", "Grid Size", "Device", "CC", "Section Name", "Metric Name",
+          "Metric Unit", "Metric Value"]
+
+
+def _write(path, rows, preamble=True):
+    with open(path, "w", newline="") as f:
+        if preamble:  # ncu prints its own log lines before the table
+            f.write("==PROF== Connected to process 1\n")
+        w = csv.writer(f, quoting=csv.QUOTE_ALL)
+        w.writerow(HEADER)
+        for k, (name, metric, unit, value) in enumerate(rows):
+            w.writerow([k, 1, "python", "h", name, 1, 7, "(256, 1, 1)", "(152, 1, 1)", 0, "10.3",
+                        "Command line profiler metrics", metric, unit, value])
+
+
+def test_launch_summary_shares_and_units(tmp_path):
+    from paper_1710_03608_gb300 import measure
+    p = tmp_path / "launches.csv"
+    _write(p, [
+        ("void ctd::k_fiber_norms(const int *, int)", "gpu__time_duration.sum", "usecond", "250"),
+        ("void ctd::k_fiber_norms(const int *, int)", "gpu__time_duration.sum", "nsecond",
+         "250,000"),
+        ("ctd::<unnamed>::k_cf<float, 4, 1>(ctd::CscDev)", "gpu__time_duration.sum", "msecond",
+         "1.5"),
+    ])
+    out = measure.ncu_launch_summary(str(p)).splitlines()
+    assert out[1].split()[0] == "ctd::<unnamed>::k_cf<float,"   # largest first
+    norms = next(ln for ln in out if ln.startswith("ctd::k_fiber_norms"))
+    f = norms.split()
+    assert f[1] == "2" and float(f[2]) == pytest.approx(0.5) and f[3] == "25.00%"
+    assert out[-1] == "total: 3 launches, 2.000 ms"
+
+
+def test_traffic_record_scales_and_hashes(tmp_path):
+    from paper_1710_03608_gb300 import measure
+    src = tmp_path / "kernels.cu"
+    src.write_text("__global__ void k_cf() {}\n")
+    p = tmp_path / "traffic.csv"
+    _write(p, [
+        ("void ctd::k_copy_flat<float>(int)", "dram__bytes_read.sum", "Mbyte", "100"),
+        ("void ctd::k_copy_flat<float>(int)", "dram__bytes_write.sum", "Gbyte", "0.2"),
+        ("void ctd::k_cf<float, 4, 1>(int)", "dram__bytes_read.sum", "byte", "1,000,000"),
+        ("void ctd::k_cf<float, 4, 1>(int)", "gpu__time_duration.sum", "usecond", "9"),
+        ("void ctd::k_fiber_norms(int)", "dram__bytes_read.sum", "Mbyte", "999"),
+    ])
+    rec = measure.ncu_traffic_record(str(p), "k_copy_flat|k_cf", 2.5, str(src))
+    assert rec["captured_bytes"] == pytest.approx(301e6)
+    assert rec["bytes_per_launch"] == pytest.approx(2.5 * 301e6)
+    assert rec["per_kernel_captured"] == {"ctd::k_copy_flat<float>": pytest.approx(300e6),
+                                          "ctd::k_cf<float, 4, 1>": pytest.approx(1e6)}
+    assert rec["source_sha"] == hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+
+
+def test_bench_reports_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
+    import json
+
+    import bench
+    src = tmp_path / "kernels.cu"
+    src.write_text("A\n")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    sha = hashlib.sha256(b"A\n").hexdigest()[:16]
+    (prof / "traffic.json").write_text(json.dumps({"source_sha": sha, "bytes_per_launch": 5.0}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.ncu_traffic(str(src))["bytes_per_launch"] == 5.0
+    src.write_text("B\n")                    # the kernels changed since the capture
+    assert bench.ncu_traffic(str(src)) is None
