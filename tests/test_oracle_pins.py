@@ -105,6 +105,21 @@ def test_draw_target_is_floor_of_scaled_u():
             assert 0 <= t < T
 
 
+def test_draw_maps_target_to_smallest_column_past_it():
+    """Algorithm 1 line 3 with reading A2: on a CDF with T = 4 every target
+    t in {0..3} lands on a step, so a search that took cdf[f] >= t (or
+    dropped the zero-norm columns differently) picks another column."""
+    sq = np.array([0, 1, 0, 1, 1, 0, 1], dtype=np.int64)   # cdf 0 1 1 2 3 3 4
+    want = {0: 1, 1: 3, 2: 4, 3: 6}
+    draws = O.sample_columns(O.cdf(sq), 64, seed=5, step=2, stream=1)
+    seen = set()
+    for k, f in enumerate(draws):
+        t = O.draw_target(k, 4, seed=5, step=2, stream=1)
+        assert f == want[t]
+        seen.add(t)
+    assert seen == {0, 1, 2, 3}
+
+
 # --- P4: unique ---------------------------------------------------------------
 
 def test_unique_is_the_distinct_sorted_draws():
