@@ -165,6 +165,18 @@ def test_filter_tie_counts_as_dependent():
     assert kept == [0]
 
 
+def test_filter_compares_norms_against_eps():
+    """Algorithm 1 line 8 compares ||res|| with eps ||x|| (reading A5), not
+    squared norms with eps or eps^2: at eps = 0.1 a fiber with residual
+    ratio 0.050 is dependent and one with 0.206 is kept.  Comparing
+    ||res||^2 with eps ||x||^2 would drop both; comparing ||res|| with
+    eps^2 ||x|| would keep both."""
+    X = np.array([[100, 0, 0], [100, 5, 0], [100, 0, 21]], dtype=np.int64).T
+    kept, R_cols, _, ratios = O._filter(lambda f: X[:, f], [0, 1, 2], [], None, 0.1)
+    assert kept == [0, 2]
+    assert np.array_equal(np.stack(R_cols, axis=1), X[:, [0, 2]])
+
+
 @pytest.mark.parametrize("seed", [1, 2, 3])
 def test_ctd_s_rank_and_U(seed):
     coo = synth.tiny((12, 6, 5), 90, seed=seed)
