@@ -51,3 +51,43 @@ def test_no_compute_without_gpu_raises_cleanly(lib):
     X = ctd.Coo.from_synth(x, device=False)
     with pytest.raises(ctd.CtdError):
         ctd.ctd_static(X, 1, 5, 1e-6, 0, 0, stream=0)
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "ctd.h"
+
+int main(void) {
+  const char* v = ctd_version();
+  if (!v || strncmp(v, "ctd-gb300", 9) != 0) return 2;
+  /* an invalid argument is rejected before any device work */
+  ctd_factors* F = NULL;
+  if (ctd_static(NULL, 1, 10, 1e-6, 0, CTD_FP64, 0, NULL, &F) != CTD_EINVAL || F) return 3;
+  if (!ctd_last_error() || !ctd_last_error()[0]) return 4;
+  int32_t i[1] = {0}, j[1] = {0}, k[1] = {0}, val[1] = {1};
+  ctd_coo3 X = {{1, 1, 1}, 1, i, j, k, val, CTD_MEM_HOST};
+  if (ctd_static(&X, 4, 10, 1e-6, 0, CTD_FP64, 0, NULL, &F) != CTD_EINVAL || F) return 5;
+  printf("%s\n", v);
+  return 0;
+}
+"""
+
+
+def test_plain_c_caller(lib, tmp_path):
+    """The header is plain C99 and a C program links the library and calls
+    it (no GPU work: the version and argument checks)."""
+    import shutil
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    src = tmp_path / "caller.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(lib)
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", libdir,
+                        "-lctd", "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.startswith("ctd-gb300")
