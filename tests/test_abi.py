@@ -91,3 +91,31 @@ def test_plain_c_caller(lib, tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
     assert r.stdout.startswith("ctd-gb300")
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built library the binding raises on first use: there is
+    no fallback path that computes anything."""
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1710_03608_gb300 import ctd\n"
+            "try:\n"
+            "    ctd.load(%r)\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n"
+            "    sys.exit(0)\n"
+            "sys.exit(1)\n") % (ROOT, str(tmp_path / "libctd.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "not built" in r.stdout, (r.stdout, r.stderr)
+
+
+def test_host_coo_must_be_contiguous_int32():
+    import numpy as np
+    from paper_1710_03608_gb300 import ctd
+    a = np.zeros(4, np.int32)
+    with pytest.raises(TypeError):
+        ctd.Coo((2, 2, 1), a, a, a, np.zeros(4, np.int64))
+    with pytest.raises(TypeError):
+        ctd.Coo((2, 2, 1), a, a, a, np.zeros(8, np.int32)[::2])
+    X = ctd.Coo((2, 2, 1), a, a, a, a)
+    assert X.desc.memory == ctd.CTD_MEM_HOST and X.desc.nnz == 4
