@@ -57,3 +57,33 @@ def test_single_rank_passthrough():
     import bench
     assert bench.max_over_ranks(7.5, 1) == 7.5
     assert bench.whole_job_value(10, 1, 1.0) == 10_000.0
+
+
+def test_reference_arm_rank0_only(monkeypatch, capsys):
+    """Under torchrun the oracle's reference arm runs on rank 0 alone; the
+    line carries the oracle's own throughput as value, cpu_baseline and e2e
+    (no host-device bytes)."""
+    import argparse
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    calls = []
+
+    def fake_sample():
+        calls.append(1)
+        return {"nnz": 1000, "seconds": 0.5, "err": 0.1, "dims": [30, 30, 3]}
+
+    monkeypatch.setattr(bench, "run_oracle_sample", fake_sample)
+    args = argparse.Namespace(gpus=2, steps=3, warmup=2, impl="reference")
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    bench.reference_arm(args)
+    assert not calls and capsys.readouterr().out == ""
+    monkeypatch.setenv("RANK", "0")
+    bench.reference_arm(args)
+    assert len(calls) == 5                    # warm-up + timed samples
+    line = json.loads(capsys.readouterr().out.strip())
+    assert line["impl"] == "reference" and line["value"] == pytest.approx(2000.0)
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["steps"] == 3 and line["warmup"] == 2 and line["higher_is_better"] is True
