@@ -220,6 +220,25 @@ def test_error_forms_agree_with_lstsq(seed):
     assert 0.0 <= e_ls <= 1.0
 
 
+def test_error_hand_computed():
+    """Eq. (error) by hand on X_(1) = [[1, 1], [0, 1]] (||X||^2 = 3):
+    R = x_0 = (1, 0): U = 1, C = [1, 1], residual [[0, 0], [0, 1]], e = 1/3;
+    R = x_1 = (1, 1): U = 1/2, C = [1, 2], residual [[1/2, 0], [-1/2, 0]],
+    e = 1/6; both fibers: e = 0.  The squared ratio (reading A6): its root
+    would give 0.577 and 0.408."""
+    X = O.Matricized.from_coo((2, 2, 1), [0, 0, 1], [0, 1, 1], [0, 0, 0], [1, 1, 1], 1)
+    for R, U, e in ((np.array([[1], [0]]), np.array([[1.0]]), 1 / 3),
+                    (np.array([[1], [1]]), np.array([[0.5]]), 1 / 6),
+                    (np.array([[1, 1], [0, 1]]), None, 0.0)):
+        C = O.c_full(X, R)
+        if R.shape[1] == 1:
+            assert np.array_equal(C.toarray(), R.T @ np.array([[1, 1], [0, 1]]))
+        else:
+            U = np.linalg.inv((R.T @ R).astype(float))
+        assert O.relative_error_dense(X, R, U, C) == pytest.approx(e, abs=1e-15)
+        assert O.projection_error(X, R) == pytest.approx(e, abs=1e-15)
+
+
 def test_sampling_every_fiber_gives_exact_reconstruction():
     coo = synth.tiny((6, 4, 3), 30, seed=2)
     res = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 4000, 1e-6, 5)
