@@ -300,6 +300,28 @@ def test_dynamic_c_exact_when_history_is_spanned():
     assert np.allclose(st.C, R.T @ Xd, rtol=1e-9, atol=1e-7)
 
 
+def test_dynamic_c_hand_computed():
+    """Algorithm 2 and Eq. (C_t+1_final) by hand, I = 3, two slices of two
+    columns, eps = 0.5.  Slice 0: a = (1, 0, 0) and a' = (2, 1, 0); a' has
+    residual ratio 1/sqrt(5) = 0.447 <= 0.5 against a, so R^(1) = [a] (its
+    history is not spanned) and C^(1) = a^T [a, a'] = [1, 2].  Slice 1:
+    b = (0, 0, 1) and an empty column; b is orthogonal to a, so it is kept:
+    R^(2) = [a, b], the lower-left block (b^T a) U C^(1) is 0, and
+    C^(2) = [[1, 2, 0, 0], [0, 0, 1, 0]].  The error: a' keeps its residual
+    (0, 1, 0) of squared norm 1 out of ||X||^2 = 1 + 5 + 1, e = 1/7."""
+    st = O.DynamicState(3, 2)
+    r0 = O.ctd_d_step(st, (3, 2), [0, 0, 1], [0, 1, 1], [1, 2, 1], 50, 0.5, seed=3,
+                      keep_X=True)
+    assert list(r0.I_unique) == [0, 1] and list(r0.new_fibers) == [0]
+    assert np.array_equal(st.C, [[1.0, 2.0]])
+    r1 = O.ctd_d_step(st, (3, 2), [2], [0], [1], 50, 0.5, seed=3, keep_X=True)
+    assert list(r1.new_fibers) == [0]
+    assert np.array_equal(np.stack(st.R_cols, axis=1), [[1, 0], [0, 0], [0, 1]])
+    assert np.array_equal(st.C, [[1.0, 2.0, 0.0, 0.0], [0.0, 0.0, 1.0, 0.0]])
+    assert st.err_num / st.err_den == pytest.approx(1 / 7, abs=1e-15)
+    assert O.dynamic_error_dense(st) == pytest.approx(1 / 7, abs=1e-15)
+
+
 def test_reordering_parenthesizations_agree():
     rng = np.random.default_rng(0)
     dR = rng.integers(0, 4, size=(30, 3)).astype(float)
