@@ -305,21 +305,25 @@ def test_dynamic_c_hand_computed():
     columns, eps = 0.5.  Slice 0: a = (1, 0, 0) and a' = (2, 1, 0); a' has
     residual ratio 1/sqrt(5) = 0.447 <= 0.5 against a, so R^(1) = [a] (its
     history is not spanned) and C^(1) = a^T [a, a'] = [1, 2].  Slice 1:
-    b = (0, 0, 1) and an empty column; b is orthogonal to a, so it is kept:
-    R^(2) = [a, b], the lower-left block (b^T a) U C^(1) is 0, and
-    C^(2) = [[1, 2, 0, 0], [0, 0, 1, 0]].  The error: a' keeps its residual
-    (0, 1, 0) of squared norm 1 out of ||X||^2 = 1 + 5 + 1, e = 1/7."""
+    b = (1, 1, 1) and an empty column; b's residual ratio against a is
+    sqrt(2/3) > 0.5, so it is kept: R^(2) = [a, b].  The lower-left block
+    ((b^T a) U^(1)) C^(1) = [1, 2] -- not b^T [a, a'] = [1, 3], since a' is
+    outside range R^(1) -- the upper-right a^T [b, 0] = [1, 0] and the new
+    block b^T [b, 0] = [3, 0], so C^(2) = [[1, 2, 1, 0], [1, 2, 3, 0]].
+    The error: a' keeps its reconstruction a * 2 and residual (0, 1, 0) of
+    squared norm 1; b is exact; e = 1 / (1 + 5 + 3) = 1/9 (reading A20)."""
     st = O.DynamicState(3, 2)
     r0 = O.ctd_d_step(st, (3, 2), [0, 0, 1], [0, 1, 1], [1, 2, 1], 50, 0.5, seed=3,
                       keep_X=True)
     assert list(r0.I_unique) == [0, 1] and list(r0.new_fibers) == [0]
     assert np.array_equal(st.C, [[1.0, 2.0]])
-    r1 = O.ctd_d_step(st, (3, 2), [2], [0], [1], 50, 0.5, seed=3, keep_X=True)
+    r1 = O.ctd_d_step(st, (3, 2), [0, 1, 2], [0, 0, 0], [1, 1, 1], 50, 0.5, seed=3, keep_X=True)
     assert list(r1.new_fibers) == [0]
-    assert np.array_equal(np.stack(st.R_cols, axis=1), [[1, 0], [0, 0], [0, 1]])
-    assert np.array_equal(st.C, [[1.0, 2.0, 0.0, 0.0], [0.0, 0.0, 1.0, 0.0]])
-    assert st.err_num / st.err_den == pytest.approx(1 / 7, abs=1e-15)
-    assert O.dynamic_error_dense(st) == pytest.approx(1 / 7, abs=1e-15)
+    assert np.array_equal(np.stack(st.R_cols, axis=1), [[1, 1], [0, 1], [0, 1]])
+    assert np.allclose(r1.M, [[1.0]], rtol=0, atol=1e-15)
+    assert np.allclose(st.C, [[1, 2, 1, 0], [1, 2, 3, 0]], rtol=0, atol=1e-14)
+    assert st.err_num / st.err_den == pytest.approx(1 / 9, abs=1e-15)
+    assert O.dynamic_error_dense(st) == pytest.approx(1 / 9, abs=1e-14)
 
 
 def test_reordering_parenthesizations_agree():
