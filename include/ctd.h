@@ -4,7 +4,7 @@
  * CTD (Lee, Choi, Sael) decomposes a sparse tensor X into C x_alpha (R U):
  *   R  holds actual, linearly independent mode-alpha fibers of X,
  *   U  = (R^T R)^{-1}  (the small pseudoinverse, Lemma 3.2),
- *   C  = X x_alpha R^T, i.e. C_(alpha) = R^T X_(alpha)  (Algorithm 1 line 16, Eq. 3).
+ *   C  = X x_alpha R^T, i.e. C_(alpha) = R^T X_(alpha)  (Algorithm 1, Eq. 3).
  * CTD-S (Algorithm 1) does this for a static tensor; CTD-D (Algorithm 2)
  * updates the factors when a new time slice arrives.
  *
@@ -71,7 +71,7 @@ typedef enum {
 /* Flags for ctd_static. */
 #define CTD_SKIP_C 1u      /* do not materialize C (R, U and the error only) */
 #define CTD_SKIP_ERROR 2u  /* do not compute the relative error */
-/* Also for ctd_dynamic_create: after the matricization (Algorithm 1 line 1)
+/* Also for ctd_dynamic_create: after the matricization (Algorithm 1)
  * sort each column's entries of X_(alpha) by (row, value).  The scatter
  * that builds the columns leaves their entries in the order its atomics
  * were taken, which changes from run to run; integer results (C, R, the
@@ -112,8 +112,8 @@ typedef struct {
  * size s, tolerance eps; ENSURE: C, U, R).
  *  X        tensor (device or host memory, see ctd_coo3.memory)
  *  alpha    1..3
- *  s        number of draws with replacement (line 3), 1..8192
- *  eps      tolerance of the independence test (line 8), 0 <= eps < 1;
+ *  s        number of draws with replacement, 1..8192
+ *  eps      tolerance of the independence test, 0 <= eps < 1;
  *           a fiber x is kept iff ||res|| > eps ||x||
  *  seed     Philox4x64-10 key; draw k uses counter (k, 0, 0, 0)
  *  precision ctd_precision
@@ -152,7 +152,7 @@ CTD_API ctd_status ctd_static_batched(int n, const ctd_coo3* X, int alpha, const
  * step's block (older columns can then no longer be read); CTD_DETERMINISTIC
  * sorts every slice's columns as for ctd_static.
  * Starting empty, the first kept fiber x gives U = 1/(x^T x) as in
- * Algorithm 1 line 5, so a first step equals ctd_static on that slice.
+ * Algorithm 1, so a first step equals ctd_static on that slice.
  */
 #define CTD_KEEP_LAST_C 4u
 CTD_API ctd_status ctd_dynamic_create(const int64_t dims2[2], int alpha, int precision,
@@ -163,8 +163,8 @@ CTD_API ctd_status ctd_dynamic_create(const int64_t dims2[2], int alpha, int pre
  * ctd_dynamic_step -- one step of CTD-D, Algorithm 2, in place:
  * (C^(t), U^(t), R^(t)) -> (C^(t+1), U^(t+1), R^(t+1)).
  *  dX   the new slice, dims = {dims2[0], dims2[1], 1}
- *  d    draws for this step (line 3), 1..8192
- *  eps  tolerance (line 9)
+ *  d    draws for this step, 1..8192
+ *  eps  tolerance of the independence test
  * The new columns' block R^(t+1)^T dX is stored exactly; the lower-left
  * block of Eq. (C_t+1_final) is kept as M_{t+1} = ((dR)^T R^(t)) U^(t)
  * (the paper's left-to-right order) and applied to old columns on request.
@@ -211,7 +211,7 @@ CTD_API ctd_status ctd_error(const ctd_factors* F, double* rel_err);
 /* Sizes; waits for outstanding work on the factors' stream. */
 CTD_API ctd_status ctd_get_sizes(const ctd_factors* F, ctd_sizes* out);
 
-/* The s draws I (line 3) and the s' unique ones I' ascending (line 4). */
+/* The s draws I and the s' unique ones I' ascending. */
 CTD_API ctd_status ctd_get_samples(const ctd_factors* F, int64_t* I, int64_t* I_unique);
 
 /* Column ids of R's fibers in column order (CTD-D: the slice-local fiber id

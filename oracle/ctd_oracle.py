@@ -10,13 +10,13 @@ reads a value computed by the GPU path.
 
 What each function follows:
   matricize              Section 2.1 (mode-alpha matricization), reading A1
-  column_sqnorms, cdf    Algorithm 1 line 2, Eq. (1)
+  column_sqnorms, cdf    Algorithm 1 (squared norms), Eq. (1)
   philox4x64_10          Salmon et al., SC'11 (counter-based RNG), reading A2
-  sample_columns         Algorithm 1 line 3 (with replacement), reading A2
-  unique_columns         Algorithm 1 line 4, reading A3
-  ctd_s                  Algorithm 1 lines 1-16, literally, FP64
-  ctd_d_step             Algorithm 2 lines 1-21, literally, FP64
-  c_columns              Algorithm 1 line 16 / Eq. (3), exact int64
+  sample_columns         Algorithm 1 (draws with replacement), reading A2
+  unique_columns         Algorithm 1 (unique draws), reading A3
+  ctd_s                  Algorithm 1, step by step, FP64
+  ctd_d_step             Algorithm 2, step by step, FP64
+  c_columns              Algorithm 1's C / Eq. (3), exact int64
   relative_error_dense   Eq. (error), brute force on small inputs
   projection_error       Lemma 3.2 (Eqs. 4-7): error = ||X - R R^+ X||^2/||X||^2
   ddos_candidates        Section 5, detection rule on R's fibers
@@ -34,9 +34,9 @@ Readings of points the paper leaves open (same letters everywhere):
   A5 Euclidean norms.
   A6 the relative error is the squared ratio.
   A9 a dynamic state may start empty; the first kept fiber then gives
-     U = 1/(x^T x), as in Algorithm 1 line 5.
+     U = 1/(x^T x), as for Algorithm 1's first kept fiber.
   A10 an all-zero input yields no draws and an empty factor.
-  A21 line 7's residual is evaluated as x minus its orthogonal projection
+  A21 the test's residual is evaluated as x minus its orthogonal projection
       onto range(R), by Gram-Schmidt with reorthogonalization (equal to
       x - R U R^T x in exact arithmetic; stable in floating point).
   A23 Section 5's average norm is the exact sum of the representatives'
@@ -86,7 +86,7 @@ def matricize(dims, i, j, k, alpha: int):
 
 
 # ---------------------------------------------------------------------------
-# Algorithm 1 line 2 / Eq. (1): squared column norms and their prefix sums
+# Algorithm 1 / Eq. (1): squared column norms and their prefix sums
 # ---------------------------------------------------------------------------
 
 def column_sqnorms(cols, vals, n_cols: int) -> np.ndarray:
@@ -140,7 +140,7 @@ def philox4x64_10(counter: Sequence[int], key: Sequence[int]) -> List[int]:
 
 
 # ---------------------------------------------------------------------------
-# Algorithm 1 lines 3-4: sampling with replacement, then unique
+# Algorithm 1: sampling with replacement, then unique
 # ---------------------------------------------------------------------------
 
 def draw_target(k: int, total: int, seed: int, step: int = 0, stream: int = 0) -> int:
@@ -151,7 +151,7 @@ def draw_target(k: int, total: int, seed: int, step: int = 0, stream: int = 0) -
 
 def sample_columns(cdf_arr: np.ndarray, s: int, seed: int, step: int = 0,
                    stream: int = 0) -> np.ndarray:
-    """s column indices drawn with P(f) = |x_f|^2 / ||X||_F^2 (Alg. 1 line 3)."""
+    """s column indices drawn with P(f) = |x_f|^2 / ||X||_F^2 (Algorithm 1)."""
     if cdf_arr.size == 0 or int(cdf_arr[-1]) == 0:
         return np.zeros(0, dtype=np.int64)  # reading A10
     total = int(cdf_arr[-1])
@@ -164,7 +164,7 @@ def sample_columns(cdf_arr: np.ndarray, s: int, seed: int, step: int = 0,
 
 
 def unique_columns(I: np.ndarray) -> np.ndarray:
-    """I' = the distinct elements of I, ascending (Alg. 1 line 4, reading A3)."""
+    """I' = the distinct elements of I, ascending (Algorithm 1, reading A3)."""
     return np.unique(np.asarray(I, dtype=np.int64))
 
 
@@ -209,7 +209,7 @@ class Matricized:
 
 
 # ---------------------------------------------------------------------------
-# Algorithm 1 lines 5-15 / Algorithm 2 lines 6-16: the independence filter
+# Algorithm 1 / Algorithm 2: the independence filter
 # ---------------------------------------------------------------------------
 
 def _filter(x_of, candidates, R_cols: List[np.ndarray], U: Optional[np.ndarray],
@@ -218,8 +218,8 @@ def _filter(x_of, candidates, R_cols: List[np.ndarray], U: Optional[np.ndarray],
 
     R_cols holds the current columns (dense float64, length I_alpha); U is
     their (R^T R)^{-1} (None when R is empty).  For each candidate x
-    (Alg. 1 lines 6-15 / Alg. 2 lines 6-16):
-      line 7: res = x - R U R^T x.  Because U = (R^T R)^{-1} (Colibri's
+    (Algorithm 1 / Algorithm 2), step by step:
+      residual: res = x - R U R^T x.  Because U = (R^T R)^{-1} (Colibri's
         Theorem 1, used in Lemma 3.2), R U R^T is the orthogonal projector
         onto range(R), so res is x minus its projection.  It is evaluated
         as res = x - Q (Q^T x) with an orthonormal basis Q of range(R),
@@ -227,10 +227,10 @@ def _filter(x_of, candidates, R_cols: List[np.ndarray], U: Optional[np.ndarray],
         ||res|| accurate to rounding however ill-conditioned R gets; the
         product R (U (R^T x)) with the incrementally updated U loses that
         accuracy once kappa(R^T R) grows large (reading A21).
-      line 8: skip when ||res|| <= eps ||x|| (reading A4);
-      line 11: delta = ||res||^2, y = U R^T x;
-      line 12: U grows by the block update;
-      line 13: x is appended to R (and res / ||res|| to Q).
+      test: skip when ||res|| <= eps ||x|| (reading A4);
+      update: delta = ||res||^2, y = U R^T x;
+      U grows by the block update;
+      x is appended to R (and res / ||res|| to Q).
     Returns (kept candidate positions, R_cols, U, ratios) where ratios[k] =
     ||res|| / ||x|| for every candidate (for tie margins).
     """
@@ -251,7 +251,7 @@ def _filter(x_of, candidates, R_cols: List[np.ndarray], U: Optional[np.ndarray],
         n = n0 + len(kept)
         xn = float(np.sqrt(x @ x))
         if n == 0:
-            # Alg. 1 line 5 (and reading A9): R <- [x], U <- 1/(x^T x)
+            # Algorithm 1's first kept fiber (and reading A9): R <- [x], U <- 1/(x^T x)
             if xn == 0.0:
                 ratios.append(0.0)
                 continue
@@ -296,8 +296,8 @@ class StaticResult:
     T: int                   # ||X||_F^2, exact
     sqnorms: np.ndarray      # |x_f|^2 for every column
     cdf: np.ndarray
-    I: np.ndarray            # the s draws (Alg. 1 line 3)
-    I_unique: np.ndarray     # I' (Alg. 1 line 4)
+    I: np.ndarray            # the s draws (Algorithm 1)
+    I_unique: np.ndarray     # I' (Algorithm 1)
     kept: np.ndarray         # positions in I' of the columns of R
     fibers: np.ndarray       # column ids of R's fibers (= I_unique[kept])
     R: np.ndarray            # dense int64 I_alpha x s~
@@ -308,15 +308,15 @@ class StaticResult:
 
 def ctd_s(dims, i, j, k, val, alpha: int, s: int, eps: float, seed: int,
           step: int = 0, stream: int = 0) -> StaticResult:
-    """Algorithm 1 (CTD-S) lines 1-15.  C (line 16) is available through
+    """Algorithm 1 (CTD-S) up to U.  C is available through
     `c_full` or `c_columns` because it can be far larger than R and U."""
-    X = Matricized.from_coo(dims, i, j, k, val, alpha)            # line 1
+    X = Matricized.from_coo(dims, i, j, k, val, alpha)            # matricize
     rows, cols, _, n_cols = matricize(dims, i, j, k, alpha)
-    sq = column_sqnorms(cols, val, n_cols)                          # line 2
+    sq = column_sqnorms(cols, val, n_cols)                          # squared norms
     c = cdf(sq)
     T = int(c[-1]) if c.size else 0
-    I = sample_columns(c, s, seed, step, stream)                    # line 3
-    Iu = unique_columns(I)                                          # line 4
+    I = sample_columns(c, s, seed, step, stream)                    # draws
+    Iu = unique_columns(I)                                          # unique
     kept, R_cols, U, ratios = _filter(X.column, list(Iu), [], None, eps)  # 5-15
     fibers = Iu[np.asarray(kept, dtype=np.int64)] if kept else np.zeros(0, np.int64)
     if R_cols:
@@ -329,7 +329,7 @@ def ctd_s(dims, i, j, k, val, alpha: int, s: int, eps: float, seed: int,
 
 
 # ---------------------------------------------------------------------------
-# Algorithm 1 line 16 / Eq. (3): C_(alpha) = R^T X_(alpha), exact
+# Algorithm 1 / Eq. (3): C_(alpha) = R^T X_(alpha), exact
 # ---------------------------------------------------------------------------
 
 def c_columns(X: Matricized, R: np.ndarray, cols) -> np.ndarray:
@@ -428,25 +428,25 @@ def ctd_d_step(state: DynamicState, dims2, i, j, val, d: int, eps: float,
                seed: int, stream: int = 0, keep_X: bool = False) -> StepResult:
     """Algorithm 2 for one incoming slice Delta X (I x J x 1) with alpha = 1.
 
-    Lines 1-4 sample d columns of Delta X_(alpha) exactly as Algorithm 1;
-    line 5 warm-starts from R^(t), U^(t); lines 6-16 run the same sequential
-    test against the growing R^(t+1); lines 17-21 update C_(alpha) with the
+    It samples d columns of Delta X_(alpha) exactly as Algorithm 1 does,
+    warm-starts from R^(t), U^(t), runs the same sequential test against
+    the growing R^(t+1), and updates C_(alpha) with the
     block form of Eq. (C_t+1_final), whose lower-left block is evaluated
     left to right as (((Delta R)^T R^(t)) U^(t)) C^(t) (the reordering)."""
     I_, J_ = (int(dims2[0]), int(dims2[1]))
     k = np.zeros_like(np.asarray(i))
-    dX = Matricized.from_coo((I_, J_, 1), i, j, k, val, 1)          # line 1
-    sq = column_sqnorms(matricize((I_, J_, 1), i, j, k, 1)[1], val, J_)  # line 2
+    dX = Matricized.from_coo((I_, J_, 1), i, j, k, val, 1)          # matricize
+    sq = column_sqnorms(matricize((I_, J_, 1), i, j, k, 1)[1], val, J_)  # squared norms
     c = cdf(sq)
     Ts = int(c[-1]) if c.size else 0
-    Id = sample_columns(c, d, seed, state.t, stream)                 # line 3
-    Iu = unique_columns(Id)                                          # line 4
-    R_old = [col.copy() for col in state.R_cols]                     # line 5
+    Id = sample_columns(c, d, seed, state.t, stream)                 # draws
+    Iu = unique_columns(Id)                                          # unique
+    R_old = [col.copy() for col in state.R_cols]                     # warm start
     U_old = None if state.U is None else state.U.copy()
     d_t = len(R_old)
     kept, R_cols, U, ratios = _filter(dX.column, list(Iu), list(R_old), U_old, eps)  # 6-16
     new_f = Iu[np.asarray(kept, dtype=np.int64)] if kept else np.zeros(0, np.int64)
-    # lines 17-21
+    # C update, Eq. (C_t+1_final)
     R_new_int = (np.stack([dX.column(int(f)) for f in new_f], axis=1)
                  if len(new_f) else np.zeros((I_, 0), np.int64))
     R_old_int = (np.stack([np.rint(col).astype(np.int64) for col in R_old], axis=1)
@@ -460,11 +460,11 @@ def ctd_d_step(state: DynamicState, dims2, i, j, val, d: int, eps: float,
         # C^(t) is d~_t x N^(t); before the first step it has no columns
         top = state.C if state.C is not None else np.zeros((d_t, 0))
         if len(new_f):
-            # line 18: lower-left block, parenthesized from the left
+            # lower-left block, parenthesized from the left
             lower = M @ top if M is not None else np.zeros((len(new_f), top.shape[1]))
             left = np.concatenate([top, lower], axis=0)
         else:
-            left = top                                                # line 20
+            left = top                                                # no fiber kept: the block above only
         state.C = np.concatenate([left, C_new.astype(np.float64)], axis=1)
     state.R_cols = R_cols
     state.U = U if R_cols else None

@@ -233,7 +233,7 @@ ctd_status stage_coo(const ctd_coo3* X, int alpha, Arena& scratch, cudaStream_t 
   return CTD_OK;
 }
 
-// Algorithm 1 lines 1-2 (and the layouts the later lines read).
+// Algorithm 1's matricization and squared norms (and the layouts later steps read).
 ctd_status matricize(const CooDev& X, bool want_rows, Arena& A, cudaStream_t st, Matricized* M,
                      bool sort_cols) {
   mode_extents(X.dims, X.alpha, &M->n_rows, &M->n_cols);
@@ -353,7 +353,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
       return bail(fail(CTD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e))); \
   } while (0)
 
-  // lines 1-2
+  // matricization and squared norms
   Matricized M;
   {
     PhaseScope ph("matricize", st);
@@ -361,7 +361,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   }
   F->n_rows = M.n_rows;
   F->n_cols = M.n_cols;
-  // line 3: draws; line 4: unique
+  // draws, then their unique set
   STEP(F->mem.get(&F->I, s));
   STEP(F->mem.get(&F->Iu, s));
   int* d_count;
@@ -415,7 +415,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
                           rcr_val, scratch, st));
 
   ph_cand.reset();
-  // lines 5-15: Gram matrix, in-order Cholesky with skip (+ explicit re-test)
+  // independence test: Gram matrix, in-order Cholesky with skip (+ explicit re-test)
   double *G, *xn2;
   STEP(scratch.get(&G, (size_t)su * su));
   STEP(scratch.get(&xn2, su));
@@ -476,7 +476,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   CsrDev R{F->Rrowptr, F->Rcol, F->Rcval, kept};
   ph_r.reset();
 
-  // line 16: C = R^T X_(alpha), and Eq. (error).  The C capacity is read back
+  // C = R^T X_(alpha), and Eq. (error).  The C capacity is read back
   // while the error kernels (which do not need C) run, so the GPU does not
   // idle across that read-back.
   Readback rbc(st);

@@ -1,4 +1,4 @@
-// C = R^T X_(alpha) (Algorithm 1 line 16, Eq. 3) with register accumulators.
+// C = R^T X_(alpha) (Algorithm 1, Eq. 3) with register accumulators.
 //
 // On count data the products are dominated by a few long rows of R (the
 // frequent mode-alpha indices occur in many sampled fibers): on a Zipf(1.2)

@@ -1,6 +1,6 @@
 // FP64 dense kernels for the independence filter and the middle factor U.
 //
-// Algorithm 1 lines 6-15 test each sampled fiber x_k, in order, against the
+// Algorithm 1's independence test takes each sampled fiber x_k, in order, against the
 // span of the fibers kept so far: it is skipped iff ||res|| <= eps ||x_k||,
 // res = x_k - R U R^T x_k.  With G = R'^T R' the Gram matrix of the
 // candidates, ||res||^2 is the k-th diagonal entry of the Schur complement

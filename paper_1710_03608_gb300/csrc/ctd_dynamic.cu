@@ -1,7 +1,7 @@
 // CTD-D (Algorithm 2): one time step on a new slice dX.
 //
-// Lines 1-4 are those of Algorithm 1 on dX alone (counter (k, t, stream)).
-// Line 5 warm-starts from R^(t), U^(t).  Lines 6-16 test the d' candidates
+// The first steps (matricize, draw, unique) are those of Algorithm 1 on dX
+// alone (counter (k, t, stream)).  The step warm-starts from R^(t), U^(t) and tests the d' candidates
 // in order against the growing R^(t+1).  For a block of candidates X_c the
 // squared residual of candidate k against R^(t) and the candidates kept
 // before it is the pivot of an in-order Cholesky (with skip) of the Schur
@@ -13,9 +13,9 @@
 // B^T U B with the explicit inverse would amplify them by kappa and keep
 // dependent fibers.  The block form takes the same decisions as the
 // sequential loop.  With Y_K = U^(t) B_K and S_K = L_S L_S^T, the rank-|K|
-// update of U is the block form of the line-13 update applied |K| times:
+// update of U is the block form of Algorithm 1's update of U applied |K| times:
 //     U^(t+1) = [[U + Y_K S_K^{-1} Y_K^T, -Y_K S_K^{-1}], [., S_K^{-1}]].
-// Lines 17-21: the new columns R^(t+1)^T dX are computed exactly; the
+// C update: the new columns R^(t+1)^T dX are computed exactly; the
 // lower-left block ((dR)^T R^(t)) U^(t) C^(t) of Eq. (C_t+1_final) is kept
 // as M_{t+1} = ((dR)^T R^(t)) U^(t) = Y_K^T (the paper's left-to-right
 // order) and applied to old columns when they are read.
@@ -473,7 +473,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   rec.nnz = X.nnz;
   rec.ncols = F->n_cols;
 
-  // lines 1-4
+  // matricize, draw, unique
   Matricized M;
   {
     PhaseScope ph("d_matricize", st);
@@ -506,7 +506,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   D.last_d = T ? d : 0;
   D.last_du = du;
 
-  // lines 5-16, in rounds.  The block filter takes the sequential loop's
+  // the independence test, in rounds.  The block filter takes the sequential loop's
   // decisions while the kept block of the Schur complement stays well
   // conditioned.  A candidate kept with a tiny residual (ratio below 1e-4)
   // would make it ill-conditioned for every later candidate of the block (its
@@ -773,7 +773,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   }
   rec.d_kept = kept_total;
 
-  // lines 17-21: the new columns R^(t+1)^T dX (exact), and the error increment
+  // C update: the new columns R^(t+1)^T dX (exact), and the error increment
   const int64_t dn = F->s_kept;
   double pu = 0.0;
   if (dn > 0 && X.nnz > 0) {
@@ -1147,7 +1147,7 @@ ctd_status dyn_U(const ctd_factors* Fc, double* U) {
 }
 
 // Column (t, f) of C^(now): the step's exact block, then the rows each later
-// step appends, M_{t'} times the column so far (Eq. C_t+1_final, line 18).
+// step appends, M_{t'} times the column so far (Eq. C_t+1_final).
 ctd_status dyn_C_columns(const ctd_factors* F, int64_t ncols, const int64_t* cols, double* out) {
   CTD_TRY(dyn_check_complete(F));
   const auto& D = *F->dyn;

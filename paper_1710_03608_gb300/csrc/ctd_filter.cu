@@ -1,4 +1,4 @@
-// The independence filter (Algorithm 1 lines 6-15, Algorithm 2 lines 6-16)
+// The independence filter (Algorithm 1 and Algorithm 2)
 // for a block of candidate fibers, with the sequential loop's decisions.
 //
 // Fast path: an in-order Cholesky with skip of the candidates' Schur

@@ -383,7 +383,7 @@ struct Matricized {
   CscDev csc() const { return CscDev{colptr, csc_row, csc_val}; }
   CsrX csr() const { return CsrX{rowptr, csr_col, csr_val}; }
 };
-// Algorithm 1 lines 1-2: squared norms, CDF and the column/row layouts.
+// Algorithm 1's first steps: squared norms, CDF and the column/row layouts.
 // sort_cols: put each column's entries in (row, value) order (CTD_DETERMINISTIC)
 ctd_status matricize(const CooDev& X, bool want_rows, Arena& A, cudaStream_t st, Matricized* M,
                      bool sort_cols = false);

@@ -1,5 +1,5 @@
 // An entry point that allocates no device memory: the column distribution,
-// the draws and their unique set of ctd_static (Algorithm 1 lines 1-4),
+// the draws and their unique set of ctd_static (the first steps of Algorithm 1),
 // with its scratch in file-scope device arrays.
 //
 // Some callers cannot call cudaMalloc: code that runs inside another

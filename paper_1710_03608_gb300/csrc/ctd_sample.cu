@@ -1,5 +1,5 @@
-// Norm-proportional sampling with replacement (Algorithm 1 line 3,
-// Algorithm 2 line 3) and the unique step (line 4).
+// Norm-proportional sampling with replacement (the draws of
+// Algorithms 1 and 2) and the unique step.
 //
 // Draw k of step t in counter space `stream_id` uses Philox4x64-10
 // (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2,

@@ -1,7 +1,7 @@
 // Sparse products with the factor R:
 //   * dense columns  out(:, c) = R^T x_f      (the Gram matrices of the
-//     independence filter, Algorithm 1 lines 6-15 / Algorithm 2 lines 6-16),
-//   * the sparse core C_(alpha) = R^T X_(alpha) (Algorithm 1 line 16, Eq. 3),
+//     independence filter of Algorithm 1 / Algorithm 2),
+//   * the sparse core C_(alpha) = R^T X_(alpha) (Algorithm 1, Eq. 3),
 //   * the error numerator ||P_R X||_F^2 = ||Q^T X_(alpha)||_F^2 with
 //     Q = R L^{-T} (Eq. error, Lemma 3.2).
 //

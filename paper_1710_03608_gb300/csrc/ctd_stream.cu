@@ -1,7 +1,7 @@
 // Streaming passes over the COO input: squared column norms (Algorithm 1
-// line 2 / Eq. 1), prefix sums (the column distribution's CDF and the
+// Eq. 1), prefix sums (the column distribution's CDF and the
 // counting-sort offsets), the counting-sort scatter into column- and
-// row-major layouts (the matricization of line 1), and column gathers.
+// row-major layouts (the matricization), and column gathers.
 #include "ctd_internal.cuh"
 
 namespace ctd {

@@ -171,7 +171,7 @@ def test_traffic_stream_full_size_sampled():
     configuration of the stream measurement.  Checked per step against the
     oracle where it is cheap at this size: the draws and unique draws equal
     the oracle's (its Philox targets on the slice's exact CDF, Algorithm 2
-    lines 1-4); every column R gained is the slice's own fiber, bit for bit;
+    draws); every column R gained is the slice's own fiber, bit for bit;
     d~_t stays within the unique draws so far and I_alpha; the error lies
     in [0, 1]."""
     m = ctd()

@@ -106,7 +106,7 @@ def test_draw_target_is_floor_of_scaled_u():
 
 
 def test_draw_maps_target_to_smallest_column_past_it():
-    """Algorithm 1 line 3 with reading A2: on a CDF with T = 4 every target
+    """Algorithm 1's draw with reading A2: on a CDF with T = 4 every target
     t in {0..3} lands on a step, so a search that took cdf[f] >= t (or
     dropped the zero-norm columns differently) picks another column."""
     sq = np.array([0, 1, 0, 1, 1, 0, 1], dtype=np.int64)   # cdf 0 1 1 2 3 3 4
@@ -166,7 +166,7 @@ def test_filter_tie_counts_as_dependent():
 
 
 def test_filter_compares_norms_against_eps():
-    """Algorithm 1 line 8 compares ||res|| with eps ||x|| (reading A5), not
+    """Algorithm 1's independence test compares ||res|| with eps ||x|| (reading A5), not
     squared norms with eps or eps^2: at eps = 0.1 a fiber with residual
     ratio 0.050 is dependent and one with 0.206 is kept.  Comparing
     ||res||^2 with eps ||x||^2 would drop both; comparing ||res|| with
