@@ -90,17 +90,24 @@ def matricize(dims, i, j, k, alpha: int):
 # ---------------------------------------------------------------------------
 
 def column_sqnorms(cols, vals, n_cols: int) -> np.ndarray:
-    """|X_(alpha)(:, f)|^2 for every column f, exact in int64."""
+    """|X_(alpha)(:, f)|^2 for every column f, exact.
+
+    Each square is below 2^63 (|v| <= 2^31).  When the column sums could
+    leave the int64 range they are formed in Python integers, and a column
+    sum at or past 2^63 raises OverflowError (reading A12: the
+    distribution's integers are int64)."""
     v = np.asarray(vals, dtype=np.int64)
-    out = np.zeros(n_cols, dtype=np.int64)
-    np.add.at(out, np.asarray(cols, dtype=np.int64), v * v)
-    return out
-
-
-def column_counts(cols, n_cols: int) -> np.ndarray:
-    out = np.zeros(n_cols, dtype=np.int64)
-    np.add.at(out, np.asarray(cols, dtype=np.int64), 1)
-    return out
+    cols = np.asarray(cols, dtype=np.int64)
+    sq = v * v
+    if sq.size == 0 or int(sq.max()) * int(np.bincount(cols).max()) < (1 << 63):
+        out = np.zeros(n_cols, dtype=np.int64)
+        np.add.at(out, cols, sq)
+        return out
+    exact = np.zeros(n_cols, dtype=object)
+    np.add.at(exact, cols, sq.astype(object))
+    if any(int(x) >= (1 << 63) for x in exact):
+        raise OverflowError("a squared column norm does not fit in int64")
+    return exact.astype(np.int64)
 
 
 def cdf(sqnorms: np.ndarray) -> np.ndarray:

@@ -39,6 +39,21 @@ def test_norms_and_cdf_match_dense_unfolding(alpha):
     assert np.array_equal(np.diff(np.concatenate([[0], c])), sq)
 
 
+def test_sqnorms_exact_past_int64_or_raise():
+    """Column sums are exact integers: two values of 2^31 - 1 in one fiber sum
+    to 2^63 - 2^33 + 2 (Python-int arithmetic) and are returned exactly;
+    three reach past 2^63 and raise (reading A12), and so do five, whose sum
+    would also wrap an unsigned 64-bit accumulator back to a small value."""
+    big = 2 ** 31 - 1
+    assert 2 * big * big == 2 ** 63 - 2 ** 33 + 2
+    sq = O.column_sqnorms(np.array([3, 3, 0]), np.array([big, big, 2]), 5)
+    assert int(sq[3]) == 2 ** 63 - 2 ** 33 + 2 and int(sq[0]) == 4
+    for n in (3, 5):
+        with pytest.raises(OverflowError):
+            O.column_sqnorms(np.array([1] * n), np.array([big] * n), 2)
+    assert (5 * big * big) % 2 ** 64 < 2 ** 63  # the wrapped sum looks valid
+
+
 def test_matricized_columns_match_dense():
     coo = synth.tiny((6, 5, 4), 40, seed=5)
     Xa = unfold(dense(coo), 1)
