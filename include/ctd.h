@@ -81,6 +81,11 @@ typedef enum {
  * bit-identical from run to run, at the cost of the sort: about 0.4 ms per
  * 10^7 nonzeros on GB300, 7% of a CTD-S call on the traffic tensor. */
 #define CTD_DETERMINISTIC 8u
+/* For ctd_static: keep the column distribution of the draws (the squared
+ * column norms and their prefix sums, Eq. 1) in the factors, where
+ * ctd_get_column_dist reads it.  Costs 16 bytes of device memory per
+ * column of X_(alpha) for the life of the factors. */
+#define CTD_KEEP_DIST 16u
 
 typedef struct {
   int64_t dims[3];     /* I, J, K */
@@ -117,7 +122,7 @@ typedef struct {
  *           a fiber x is kept iff ||res|| > eps ||x||
  *  seed     Philox4x64-10 key; draw k uses counter (k, 0, 0, 0)
  *  precision ctd_precision
- *  flags    CTD_SKIP_C | CTD_SKIP_ERROR | CTD_DETERMINISTIC
+ *  flags    CTD_SKIP_C | CTD_SKIP_ERROR | CTD_DETERMINISTIC | CTD_KEEP_DIST
  *  out      receives a new ctd_factors (free with ctd_free)
  * Errors: CTD_EINVAL (arguments, index out of range), CTD_EOVERFLOW,
  * CTD_ENOMEM, CTD_ECUDA.  An all-zero tensor gives empty factors and
@@ -270,6 +275,19 @@ CTD_API ctd_status ctd_get_M(const ctd_factors* F, int64_t t, double* M);
 CTD_API void ctd_free(ctd_factors* F);
 
 /*
+ * ctd_get_column_dist -- the distribution Algorithm 1 draws fibers from
+ * (Eq. 1): norm2[f] = ||X_(alpha)(:, f)||^2, the exact integer sum of the
+ * squares of column f's values, and cdf[f] = norm2[0] + ... + norm2[f], for
+ * the N_alpha columns in the order of A1 (f = j + J k for alpha = 1).  Draw
+ * k takes the smallest f with cdf[f] > floor(u_k cdf[N_alpha - 1] / 2^64).
+ *  norm2, cdf  host uint64[N_alpha] (either may be NULL)
+ * Needs factors from ctd_static called with CTD_KEEP_DIST.  Waits for the
+ * factors' stream.  CTD_EINVAL: NULL F, CTD-D factors, or factors made
+ * without CTD_KEEP_DIST.
+ */
+CTD_API ctd_status ctd_get_column_dist(const ctd_factors* F, uint64_t* norm2, uint64_t* cdf);
+
+/*
  * ctd_ddos_candidates -- the online DDoS detector of Section 5 ("CTD at
  * work") on the factor R.  With alpha = 1 (the source mode) each fiber of R
  * is the traffic of one destination: for CTD-D the fiber's slice-local id
@@ -304,14 +322,18 @@ CTD_API ctd_status ctd_ddos_candidates(const ctd_factors* F, int64_t cap, int64_
  *  draws     device int64[s], receives I;  unique: device int64[s],
  *            receives I' ascending in its first *n_unique entries
  *  n_unique  host int, receives s'
+ * When ||X||_F = 0 there is nothing to draw from: every draws[k] is -1 and
+ * *n_unique = 0 (ctd_static then reports s_draws = 0 and no samples).
  * Scratch lives in file-scope device arrays of the library, sized for
  * N_alpha <= CTD_NOALLOC_MAX_COLS columns (8 MiB); every GPU that loads the
  * library holds them until the process exits.  Larger N_alpha returns
  * CTD_EINVAL.  The first call on a device looks up the arrays' device
- * addresses for that device (once, with it current); make that first call
- * before any stream capture.  Every call on a device shares the same arrays:
- * calls that overlap on the GPU (other streams, other threads) race, so
- * serialize them.  The call waits for its stream before returning.
+ * addresses for that device (once, with it current).  Every call reads its
+ * status back and waits for its stream, so it cannot be called while that
+ * stream is being captured into a CUDA graph.  Every call on a device
+ * shares the same arrays: calls that overlap on the GPU (other streams,
+ * other threads) race, so serialize them.  Errors as ctd_static, including
+ * CTD_EOVERFLOW when a column's squared norm or ||X||_F^2 reaches 2^63.
  */
 #define CTD_NOALLOC_MAX_COLS (1 << 20)
 CTD_API ctd_status ctd_sample_noalloc(const ctd_coo3* X, int alpha, int64_t s, uint64_t seed,

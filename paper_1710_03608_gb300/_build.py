@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libctd.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 SOURCES = ["ctd_stream.cu", "ctd_sample.cu", "ctd_spmm.cu", "ctd_dense.cu", "ctd_filter.cu", "ctd_api.cu",
            "ctd_dynamic.cu", "ctd_noalloc.cu", "ctd_batch.cu",
-           "ctd_serve.cu", "ctd_cfill.cu", "ctd_detect.cu"]
+           "ctd_serve.cu", "ctd_cfill.cu", "ctd_detect.cu", "ctd_matricize.cu"]
 
 
 def nvcc() -> str:

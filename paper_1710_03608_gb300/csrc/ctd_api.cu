@@ -213,16 +213,19 @@ ctd_status stage_coo(const ctd_coo3* X, int alpha, Arena& scratch, cudaStream_t 
   c.alpha = alpha;
   for (int d = 0; d < 3; ++d) c.dims[d] = X->dims[d];
   if (X->memory == CTD_MEM_HOST && X->nnz > 0) {
+    // each array starts on a 16-byte boundary (the streaming kernels read
+    // four entries per load when all four do)
+    const int64_t ld = (X->nnz + 3) & ~(int64_t)3;
     int32_t* buf;
-    CTD_TRY(scratch.get(&buf, 4 * (size_t)X->nnz));
+    CTD_TRY(scratch.get(&buf, 4 * (size_t)ld));
     const int32_t* src[4] = {X->i, X->j, X->k, X->val};
     for (int a = 0; a < 4; ++a)
-      CTD_CUDA(cudaMemcpyAsync(buf + a * X->nnz, src[a], X->nnz * sizeof(int32_t),
+      CTD_CUDA(cudaMemcpyAsync(buf + a * ld, src[a], X->nnz * sizeof(int32_t),
                                cudaMemcpyHostToDevice, st));
     c.i = buf;
-    c.j = buf + X->nnz;
-    c.k = buf + 2 * X->nnz;
-    c.v = buf + 3 * X->nnz;
+    c.j = buf + ld;
+    c.k = buf + 2 * ld;
+    c.v = buf + 3 * ld;
   } else {
     c.i = X->i;
     c.j = X->j;
@@ -233,59 +236,58 @@ ctd_status stage_coo(const ctd_coo3* X, int alpha, Arena& scratch, cudaStream_t 
   return CTD_OK;
 }
 
-// Algorithm 1's matricization and squared norms (and the layouts later steps read).
-ctd_status matricize(const CooDev& X, bool want_rows, Arena& A, cudaStream_t st, Matricized* M,
-                     bool sort_cols) {
+// Algorithm 1's matricization and squared norms (and the layout later steps
+// read): count entries per column, scan the counts into column offsets (the
+// scan also leaves each column's u32 cursor in the count array), scatter the
+// entries, then the squared column norms as a segmented sum over each
+// column's contiguous entries, fused with the first pass of their prefix
+// sum (the CDF).
+ctd_status matricize(const CooDev& X, Arena& A, cudaStream_t st, Matricized* M, bool sort_cols,
+                     Arena* dist) {
   mode_extents(X.dims, X.alpha, &M->n_rows, &M->n_cols);
   M->nnz = X.nnz;
-  uint64_t* norm2;
-  uint32_t *colcnt, *rowcnt;
-  CTD_TRY(A.get(&norm2, M->n_cols));
-  CTD_TRY(A.get(&colcnt, M->n_cols));
+  Arena& D = dist ? *dist : A;
+  uint32_t* rowcnt;
   CTD_TRY(A.get(&rowcnt, M->n_rows));
   M->rowcnt = rowcnt;
-  CTD_TRY(A.get(&M->cdf, M->n_cols));
+  CTD_TRY(D.get(&M->norm2, M->n_cols));
+  CTD_TRY(D.get(&M->cdf, M->n_cols));
   CTD_TRY(A.get(&M->colptr, M->n_cols + 1));
-  CTD_TRY(A.get(&M->rowptr, M->n_rows + 1));
   CTD_TRY(A.get(&M->csc_row, X.nnz));
   CTD_TRY(A.get(&M->csc_val, X.nnz));
-  if (want_rows) {
-    CTD_TRY(A.get(&M->csr_col, X.nnz));
-    CTD_TRY(A.get(&M->csr_val, X.nnz));
-  }
   CTD_TRY(A.get(&M->minval, 1));
   CTD_TRY(A.get(&M->status, 1));
   CTD_TRY(A.get(&M->tmp, scan_tmp_elems(std::max(M->n_cols, M->n_rows) + 1)));
-  CTD_CUDA(cudaMemsetAsync(norm2, 0, M->n_cols * 8, st));
-  CTD_CUDA(cudaMemsetAsync(colcnt, 0, M->n_cols * 4, st));
   CTD_CUDA(cudaMemsetAsync(rowcnt, 0, M->n_rows * 4, st));
   CTD_CUDA(cudaMemsetAsync(M->status, 0, 4, st));
-  const int big = INT32_MAX;
-  CTD_CUDA(cudaMemcpyAsync(M->minval, &big, 4, cudaMemcpyHostToDevice, st));
-  launch_fiber_norms(X, norm2, colcnt, rowcnt, M->minval, M->status, st);
-  launch_scan_u64(norm2, M->cdf, M->n_cols, true, M->tmp, M->status, st);
-  launch_scan_u32(colcnt, M->colptr, M->n_cols, false, M->tmp, M->status, st);
-  launch_scan_u32(rowcnt, M->rowptr, M->n_rows, false, M->tmp, M->status, st);
-  // cursors: reuse norm2 (n_cols u64) for columns; a fresh array for rows
-  uint64_t* rowcur = nullptr;
-  launch_copy_u64(M->colptr, norm2, M->n_cols, st);
-  if (want_rows) {
-    CTD_TRY(A.get(&rowcur, M->n_rows));
-    launch_copy_u64(M->rowptr, rowcur, M->n_rows, st);
+  CTD_CUDA(cudaMemsetAsync(M->minval, 0xff, 4, st));  // code of "no value yet"
+  bool bucketed = false;
+  CTD_TRY(matricize_bucketed(X, A, st, M, &bucketed));
+  if (!bucketed) {
+    uint32_t* colcnt;
+    CTD_TRY(A.get(&colcnt, M->n_cols));
+    CTD_CUDA(cudaMemsetAsync(colcnt, 0, M->n_cols * 4, st));
+    launch_count(X, colcnt, rowcnt, M->status, st);
+    // column offsets; colcnt becomes each column's cursor (its first position)
+    launch_scan_u32(colcnt, M->colptr, M->n_cols, false, M->tmp, M->status, st, colcnt);
+    launch_coo_scatter(X, colcnt, M->csc_row, M->csc_val, st);
   }
-  launch_coo_scatter(X, norm2, rowcur, M->csc_row, M->csc_val, M->csr_col, M->csr_val, st);
   if (sort_cols) {
     // one entry order per column, whatever order the scatter's atomics took;
-    // the column cursors (norm2) are free now and serve as the sort's
-    // scratch when they are long enough
-    uint64_t* keys = norm2;
+    // the CDF array is not written yet and serves as the sort's scratch when
+    // it is long enough (the squared norms are exact in any order)
+    uint64_t* keys = M->cdf;
     if (M->n_cols < X.nnz) CTD_TRY(A.get(&keys, X.nnz));
     CTD_TRY(launch_sort_cols(M->colptr, M->n_cols, X.nnz, M->csc_row, M->csc_val, keys, A, st));
   }
+  if (bucketed)
+    launch_scan_finish(M->norm2, M->cdf, M->n_cols, M->tmp, M->status, st);
+  else
+    launch_sqnorms_cdf(M->colptr, M->csc_val, M->n_cols, M->norm2, M->cdf, M->minval, M->tmp,
+                       M->status, st);
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
-
 
 }  // namespace ctd
 
@@ -357,7 +359,12 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   Matricized M;
   {
     PhaseScope ph("matricize", st);
-    STEP(matricize(X, false, scratch, st, &M, (flags & CTD_DETERMINISTIC) != 0));
+    STEP(matricize(X, scratch, st, &M, (flags & CTD_DETERMINISTIC) != 0,
+                   (flags & CTD_KEEP_DIST) ? &F->mem : nullptr));
+  }
+  if (flags & CTD_KEEP_DIST) {
+    F->norm2 = M.norm2;
+    F->cdf = M.cdf;
   }
   F->n_rows = M.n_rows;
   F->n_cols = M.n_cols;
@@ -381,12 +388,13 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   launch_scan_u64(rc_sizes, rc_ptr, s, false, M.tmp, M.status, st);
   STEPC(cudaGetLastError());
   unsigned status = 0;
-  int minval = 0, s_unique = 0;
+  unsigned minkey = 0;
+  int s_unique = 0;
   uint64_t T = 0, nnz_cand = 0;
   {
     Readback rb(st);
     STEP(rb.add(&status, M.status, 1));
-    STEP(rb.add(&minval, M.minval, 1));
+    STEP(rb.add(&minkey, M.minval, 1));
     STEP(rb.add(&s_unique, d_count, 1));
     STEP(rb.add(&nnz_cand, rc_ptr + s, 1));
     if (M.n_cols > 0) STEP(rb.add(&T, M.cdf + (M.n_cols - 1), 1));
@@ -394,6 +402,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   }
   STEP(status_from_device(status));
   F->T = T;
+  const int minval = decode_min(minkey);
   F->min_val = minval;
   F->s_unique = s_unique;
   if (T == 0) F->s = 0;  // nothing to draw from
@@ -586,6 +595,15 @@ extern "C" ctd_status ctd_get_samples(const ctd_factors* F, int64_t* I, int64_t*
   if (F->kind == 1) return dyn_samples(F, I, Iu);
   if (I) CTD_TRY(d2h(I, F->I, (size_t)F->s, F->stream));
   if (Iu) CTD_TRY(d2h(Iu, F->Iu, (size_t)F->s_unique, F->stream));
+  return sync(F->stream);
+}
+
+extern "C" ctd_status ctd_get_column_dist(const ctd_factors* F, uint64_t* norm2, uint64_t* cdf) {
+  if (!F) return fail(CTD_EINVAL, "NULL argument");
+  if (F->kind != 0) return fail(CTD_EINVAL, "the column distribution is kept for CTD-S only");
+  if (!F->cdf) return fail(CTD_EINVAL, "factors were made without CTD_KEEP_DIST");
+  if (norm2) CTD_TRY(d2h(norm2, F->norm2, (size_t)F->n_cols, F->stream));
+  if (cdf) CTD_TRY(d2h(cdf, F->cdf, (size_t)F->n_cols, F->stream));
   return sync(F->stream);
 }
 

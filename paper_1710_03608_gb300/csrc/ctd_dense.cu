@@ -11,10 +11,13 @@
 // Theorem 1).  In exact arithmetic this makes the same decisions and the
 // same U as the sequential loop.
 //
-// The factorization is blocked by 32 columns: a one-warp kernel decides and
-// factors the diagonal block in order, a row kernel forms the panel below
-// it, and a tiled kernel applies the trailing update.  All arithmetic is
-// FP64 on the CUDA cores.
+// The factorization is one cooperative launch (a block per SM), blocked by
+// 32 columns: four warps of block 0 (one per SM sub-partition) decide and
+// factor each diagonal block in order, in registers, right after their own
+// trailing tile of the previous panel (lookahead); the blocks then solve
+// the panel's rows and apply the trailing update in 32 x 32 tiles, with
+// two bounded grid barriers per panel.  All arithmetic is FP64 on the
+// CUDA cores.
 #include "ctd_internal.cuh"
 
 namespace ctd {
@@ -466,21 +469,25 @@ __global__ void __launch_bounds__(256, 1)
   }
 }
 
-void launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr, int* keep,
-                      cudaStream_t st, const int* force, double* piv, unsigned* status,
-                      const double* fpiv) {
-  if (n <= 0) return;
+ctd_status launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr, int* keep,
+                            cudaStream_t st, const int* force, double* piv, unsigned* status,
+                            const double* fpiv) {
+  if (n <= 0) return CTD_OK;
   // barrier words live in the status array's tail: status[1] count, status[2] generation
   GridBar gb{status + 1, status + 2, status};
-  cudaMemsetAsync(status + 1, 0, 2 * sizeof(unsigned), st);
+  CTD_CUDA(cudaMemsetAsync(status + 1, 0, 2 * sizeof(unsigned), st));
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_coop, 256, 0);
-  const int nblocks = num_sms() * (per_sm > 0 ? 1 : 0);
-  if (nblocks <= 0) return;
+  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_coop, 256, 0));
+  if (per_sm <= 0) return fail(CTD_ECUDA, "the skip-Cholesky kernel cannot be resident");
+  const int nblocks = num_sms();
   void* args[] = {&A, &n, &lda, const_cast<double**>(&thr), const_cast<int**>(&force),
                   const_cast<double**>(&fpiv), &keep, &piv, &status, &gb};
   note_launch();
-  cudaLaunchCooperativeKernel((const void*)k_chol_coop, dim3(nblocks), dim3(256), args, 0, st);
+  // a failed cooperative launch leaves keep/piv unwritten: report it before
+  // anything reads them
+  CTD_CUDA(cudaLaunchCooperativeKernel((const void*)k_chol_coop, dim3(nblocks), dim3(256), args,
+                                       0, st));
+  return CTD_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -360,7 +360,7 @@ static ctd_status cholqr_pass(const double* V, int64_t m, int n, double shift, d
   if (shift > 0.0) CTD_LAUNCH(k_add_diag, (grid_for(n, 256, 64)), (256), 0, st, G, n, n, shift);
   CTD_CUDA(cudaMemsetAsync(thr, 0, (size_t)n * 8, st));
   CTD_CUDA(cudaMemsetAsync(status, 0, 4 * sizeof(unsigned), st));
-  launch_chol_skip(G, n, n, thr, keep, st, nullptr, nullptr, status);
+  CTD_TRY(launch_chol_skip(G, n, n, thr, keep, st, nullptr, nullptr, status));
   launch_compact_flags(keep, n, idx, idx + n, st);
   int nk = 0;
   unsigned h_status = 0;
@@ -477,7 +477,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   Matricized M;
   {
     PhaseScope ph("d_matricize", st);
-    CTD_TRY(matricize(X, false, scratch, st, &M, (D.flags & CTD_DETERMINISTIC) != 0));
+    CTD_TRY(matricize(X, scratch, st, &M, (D.flags & CTD_DETERMINISTIC) != 0));
   }
   int* d_count;
   CTD_TRY(scratch.get(&d_count, 4));
@@ -487,9 +487,11 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
     launch_sort_unique(D.lastI, d, D.lastIu, d_count, st);
   }
   unsigned status = 0;
-  int du = 0, minval = 0;
+  int du = 0;
+  unsigned minkey = 0;
   uint64_t T = 0;
-  CTD_TRY(d2h(&minval, M.minval, 1, st));
+  CTD_TRY(d2h(&minkey, M.minval, 1, st));
+  const int minval = decode_min(minkey);
   CTD_TRY(d2h(&status, M.status, 1, st));
   CTD_TRY(d2h(&du, d_count, 1, st));
   if (M.n_cols > 0) CTD_TRY(d2h(&T, M.cdf + (M.n_cols - 1), 1, st));
@@ -957,7 +959,7 @@ extern "C" ctd_status ctd_dynamic_from_static(const ctd_factors* S, uint64_t str
     SEEDC(cudaMemsetAsync(thr, 0, n * 8, st));
     SEEDC(cudaMemsetAsync(force, 0xff, n * sizeof(int), st));
     SEEDC(cudaMemsetAsync(status, 0, 4 * sizeof(unsigned), st));
-    launch_chol_skip(G, n, n, thr, keep, st, force, piv, status);
+    SEED(launch_chol_skip(G, n, n, thr, keep, st, force, piv, status));
     launch_compact_flags(keep, (int)n, idx, cnt, st);
     int kept = 0;
     unsigned h_status = 0;

@@ -318,8 +318,8 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
     }
     {
       PhaseScope ph("filter_chol", st);
-      launch_chol_skip(in.S, du, du, thr, out.keep, st, force, piv, status,
-                       iter > 0 ? fpiv : nullptr);
+      CTD_TRY(launch_chol_skip(in.S, du, du, thr, out.keep, st, force, piv, status,
+                               iter > 0 ? fpiv : nullptr));
       launch_compact_flags(out.keep, du, out.idx, count, st);
     }
     unsigned h_status = 0;

@@ -149,28 +149,81 @@ struct CooDev {
 // Mode-alpha row extent and column count.
 void mode_extents(const int64_t dims[3], int alpha, int64_t* n_rows, int64_t* n_cols);
 
-// K1: squared column norms (exact u64), per-column and per-row counts.
-// norm2/colcnt/rowcnt must be zeroed.  Also reduces min(value) into
-// *minval (initialize to INT32_MAX).
-void launch_fiber_norms(const CooDev& X, uint64_t* norm2, uint32_t* colcnt,
-                        uint32_t* rowcnt, int* minval, unsigned* status,
-                        cudaStream_t st);
+// Row (mode-alpha index) and column of X_(alpha) for one nonzero: the
+// little-endian order of the other two modes (alpha = 1: f = j + J k;
+// alpha = 2: f = i + I k; alpha = 3: f = i + I j).  false for an index
+// outside its mode's extent.  Every kernel that maps COO entries to
+// columns goes through this one definition.
+struct ModeMap {
+  int alpha;
+  int64_t I, J, K;
+  __device__ __forceinline__ bool map(int32_t a, int32_t b, int32_t c, int32_t* row,
+                                      int64_t* col) const {
+    if (a < 0 || b < 0 || c < 0 || a >= I || b >= J || c >= K) return false;
+    if (alpha == 1) {
+      *row = a;
+      *col = (int64_t)b + J * (int64_t)c;
+    } else if (alpha == 2) {
+      *row = b;
+      *col = (int64_t)a + I * (int64_t)c;
+    } else {
+      *row = c;
+      *col = (int64_t)a + I * (int64_t)b;
+    }
+    return true;
+  }
+};
+inline ModeMap make_mode_map(const int64_t dims[3], int alpha) {
+  ModeMap m;
+  m.alpha = alpha;
+  m.I = dims[0];
+  m.J = dims[1];
+  m.K = dims[2];
+  return m;
+}
+
+// K1a: entries per column (colcnt) and per row (rowcnt) of X_(alpha);
+// both zeroed beforehand.  Out-of-range indices set DEV_BAD_INDEX.
+void launch_count(const CooDev& X, uint32_t* colcnt, uint32_t* rowcnt, unsigned* status,
+                  cudaStream_t st);
+// K1b: squared column norms from the column-major layout: norm2[f] = the
+// sum of val[p]^2 over p in [colptr[f], colptr[f+1]) (saturating u64),
+// followed by their inclusive prefix sum cdf (the column distribution).
+// Also reduces the smallest value into *minkey as the order-preserving code
+// (unsigned)v ^ 2^31 (initialize to all ones; decode_min turns it back).
+// A total at or past 2^63 sets DEV_OVERFLOW.
+void launch_sqnorms_cdf(const uint64_t* colptr, const int32_t* val, int64_t n_cols,
+                        uint64_t* norm2, uint64_t* cdf, unsigned* minkey, uint64_t* tmp,
+                        unsigned* status, cudaStream_t st);
 
 // K2: prefix sums.  out[n] (inclusive) or out[n+1] (exclusive, out[0]=0).
-// `tmp` needs scan_tmp_elems(n) entries.  *overflow_flag gets DEV_OVERFLOW
-// when the running double sum passes 2^63.
+// `tmp` needs scan_tmp_elems(n) entries.  Sums are saturating u64 adds; a
+// total at or past 2^63 sets DEV_OVERFLOW in *status.  in == out is
+// allowed for the inclusive u64 scan (each element is read before it is
+// written, by the same thread).  cur32 (optional, u32 scan only) receives
+// the exclusive prefix of every element as u32 and may alias `in`.
 size_t scan_tmp_elems(int64_t n);
+// Tiling of the scans: a tile of SCAN_TILE elements is one block of
+// SCAN_WARPS warps, each warp a segment of SCAN_PER_WARP elements.
+constexpr int SCAN_WARPS = 8;
+constexpr int SCAN_PER_WARP = 512;                       // 16 per lane
+constexpr int SCAN_TILE = SCAN_WARPS * SCAN_PER_WARP;    // 4096
 void launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, bool inclusive,
                      uint64_t* tmp, unsigned* status, cudaStream_t st);
 void launch_scan_u32(const uint32_t* in, uint64_t* out, int64_t n, bool inclusive,
-                     uint64_t* tmp, unsigned* status, cudaStream_t st);
+                     uint64_t* tmp, unsigned* status, cudaStream_t st,
+                     uint32_t* cur32 = nullptr);
+// Tile scan and apply of an inclusive u64 scan whose tile and warp sums were
+// written by another kernel into tmp (same layout and tiling as the scans
+// above: 4096-element tiles of eight 512-element warp segments).
+void launch_scan_finish(const uint64_t* in, uint64_t* out, int64_t n, uint64_t* tmp,
+                        unsigned* status, cudaStream_t st);
 
-// K5a: counting-sort scatter of the COO into column-major (CSC: row, val)
-// and row-major (CSR: col, val) layouts.  colcur/rowcur start as copies of
-// the exclusive offsets and are consumed.
-void launch_coo_scatter(const CooDev& X, uint64_t* colcur, uint64_t* rowcur,
-                        int32_t* csc_row, int32_t* csc_val, int32_t* csr_col,
-                        int32_t* csr_val, cudaStream_t st);
+// K5a: counting-sort scatter of the COO into the column-major layout (CSC:
+// row, val).  cur[f] starts as column f's first position (u32: nnz < 2^31)
+// and is consumed.
+void launch_coo_scatter(const CooDev& X, uint32_t* cur, int32_t* csc_row, int32_t* csc_val,
+                        cudaStream_t st);
 
 // Copy u64 -> u64 (cursor initialization) for n elements.
 // Sort every column's entries of a compressed layout by (row, value), in
@@ -262,11 +315,6 @@ void launch_sort_rows(const uint64_t* rowptr, int64_t n_rows, const int32_t* col
 // Relative-error numerator ||Q^T X_(alpha)||_F^2 with Q = R Z^T, Z = L^{-1}
 // (kept x kept, column-major, ld ldz).  The rows of X with the most
 // nonzeros (rowcnt, on the device) have their Q rows staged in shared memory.
-struct CsrX {          // X_(alpha) by row: row i holds (col, val)
-  const uint64_t* rowptr;
-  const int32_t* col;
-  const int32_t* val;
-};
 ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t X_nnz,
                               const CsrDev& R, const double* Z, int64_t ldz,
                               const uint32_t* rowcnt, int fp32, double* out, Arena& scratch,
@@ -305,9 +353,9 @@ void dgemm(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, cons
 // positive pivot sets DEV_CAPACITY in status[0]; a grid barrier that gives
 // up sets DEV_TIMEOUT.  status must hold 3 words (status[1..2] are the grid
 // barrier's counter and generation).
-void launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr, int* keep,
-                      cudaStream_t st, const int* force, double* piv, unsigned* status,
-                      const double* fpiv = nullptr);
+ctd_status launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr, int* keep,
+                            cudaStream_t st, const int* force, double* piv, unsigned* status,
+                            const double* fpiv = nullptr);
 // B <- L^{-T} B for lower-triangular L, by backward substitution.
 void tri_solve_lower_T(const double* L, int64_t ldl, int64_t n, double* B, int64_t ldb,
                        int64_t nrhs, cudaStream_t st);
@@ -366,27 +414,38 @@ inline ctd_status d2h(T* host, const T* dev, size_t n, cudaStream_t st) {
 ctd_status sync(cudaStream_t st);
 ctd_status stage_coo(const ctd_coo3* X, int alpha, Arena& scratch, cudaStream_t st, CooDev* out);
 
-// X_(alpha) in both layouts plus its column distribution.
+// X_(alpha) by column plus its column distribution.
 struct Matricized {
   int64_t n_rows = 0, n_cols = 0, nnz = 0;
+  uint64_t* norm2 = nullptr;    // [n_cols] squared column norms
   uint64_t* cdf = nullptr;      // [n_cols] inclusive prefix of squared norms
   uint64_t* colptr = nullptr;   // [n_cols+1]
-  uint64_t* rowptr = nullptr;   // [n_rows+1]
   int32_t* csc_row = nullptr;
   int32_t* csc_val = nullptr;
-  int32_t* csr_col = nullptr;
-  int32_t* csr_val = nullptr;
-  int* minval = nullptr;
+  unsigned* minval = nullptr;   // code of the smallest value (see launch_sqnorms_cdf)
   unsigned* status = nullptr;
   uint64_t* tmp = nullptr;
   uint32_t* rowcnt = nullptr;   // [n_rows] nonzeros per row
   CscDev csc() const { return CscDev{colptr, csc_row, csc_val}; }
-  CsrX csr() const { return CsrX{rowptr, csr_col, csr_val}; }
 };
-// Algorithm 1's first steps: squared norms, CDF and the column/row layouts.
-// sort_cols: put each column's entries in (row, value) order (CTD_DETERMINISTIC)
-ctd_status matricize(const CooDev& X, bool want_rows, Arena& A, cudaStream_t st, Matricized* M,
-                     bool sort_cols = false);
+// ctd_matricize.cu: the same layout, norms and scan tile sums by a bucketed
+// counting sort (coalesced writes), for shapes with many columns.  *used is
+// false (and nothing the plain passes need was written) when the shape does
+// not suit it; then the caller runs the plain passes.  M's arrays are
+// allocated, rowcnt/status zeroed and minval initialized by the caller; on
+// success norm2 holds the squared norms and tmp the scan's tile and warp
+// sums (finish with launch_scan_finish).
+ctd_status matricize_bucketed(const CooDev& X, Arena& A, cudaStream_t st, Matricized* M,
+                              bool* used);
+// The smallest value from its order-preserving code (INT32_MAX when X has
+// no entries).
+inline int decode_min(unsigned key) { return (int)(key ^ 0x80000000u); }
+// Algorithm 1's first steps: the column-major layout of X_(alpha), the
+// squared column norms and their CDF.  sort_cols: put each column's entries
+// in (row, value) order (CTD_DETERMINISTIC).  dist (optional): the arena
+// that receives norm2 and cdf (so a caller can keep them); A otherwise.
+ctd_status matricize(const CooDev& X, Arena& A, cudaStream_t st, Matricized* M,
+                     bool sort_cols = false, Arena* dist = nullptr);
 
 // ctd_filter.cu: the independence filter over a block of du candidates.
 // S (du x du, ld du) holds the candidates' Schur complement against R^(t)
@@ -473,6 +532,8 @@ struct ctd_factors {
   uint16_t* Crow = nullptr;
   void* Cval = nullptr;          // float or double
   uint64_t C_cap = 0;
+  uint64_t* norm2 = nullptr;     // CTD-S with CTD_KEEP_DIST: [n_cols] squared column norms
+  uint64_t* cdf = nullptr;       // and their inclusive prefix sums
   // CTD-D extras live in ctd_dynamic.cu
   struct Dyn;
   Dyn* dyn = nullptr;

@@ -56,25 +56,30 @@ ctd_status device_addresses(Addr* out) {
   return CTD_OK;
 }
 
+// Squared column norms by one atomic add per entry (no column-major layout
+// exists here).  The add returns the column's previous sum: a sum that
+// wraps past 2^64 shows as a result below its previous value and sets
+// DEV_OVERFLOW (a sum in [2^63, 2^64) is flagged by the prefix sum).
 __global__ void k_na_sqnorms(const int32_t* __restrict__ ii, const int32_t* __restrict__ jj,
                              const int32_t* __restrict__ kk, const int32_t* __restrict__ vv,
-                             int64_t nnz, int alpha, int64_t I, int64_t J, int64_t K,
-                             unsigned long long* __restrict__ sq, unsigned* status) {
-  bool bad = false;
+                             int64_t nnz, ModeMap mm, unsigned long long* __restrict__ sq,
+                             unsigned* status) {
+  bool bad = false, wrapped = false;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t a = ii[e], b = jj[e], c = kk[e];
-    if (a < 0 || b < 0 || c < 0 || a >= I || b >= J || c >= K) {
+    int32_t row;
+    int64_t col;
+    if (!mm.map(ii[e], jj[e], kk[e], &row, &col)) {
       bad = true;
       continue;
     }
-    const int64_t col = alpha == 1 ? b + J * (int64_t)c
-                        : alpha == 2 ? a + I * (int64_t)c
-                                     : a + I * (int64_t)b;
     const long long v = vv[e];
-    atomicAdd(sq + col, (unsigned long long)(v * v));
+    const unsigned long long v2 = (unsigned long long)(v * v);
+    const unsigned long long old = atomicAdd(sq + col, v2);
+    if (old + v2 < old) wrapped = true;
   }
   if (bad) atomicOr(status, DEV_BAD_INDEX);
+  if (wrapped) atomicOr(status, DEV_OVERFLOW);
 }
 
 }  // namespace
@@ -111,8 +116,7 @@ extern "C" ctd_status ctd_sample_noalloc(const ctd_coo3* X, int alpha, int64_t s
   CTD_CUDA(cudaMemsetAsync(a.status, 0, 2 * sizeof(unsigned), st));
   if (X->nnz > 0)
     CTD_LAUNCH(k_na_sqnorms, (grid_for(X->nnz, 256, (int64_t)num_sms() * 8)), (256), 0, st,
-               X->i, X->j, X->k, X->val, X->nnz, alpha, X->dims[0], X->dims[1], X->dims[2], a.cdf,
-               a.status);
+               X->i, X->j, X->k, X->val, X->nnz, make_mode_map(X->dims, alpha), a.cdf, a.status);
   uint64_t* cdf = reinterpret_cast<uint64_t*>(a.cdf);
   launch_scan_u64(cdf, cdf, n_cols, true, reinterpret_cast<uint64_t*>(a.tiles), a.status, st);
   launch_sample(cdf, n_cols, s, seed, 0, 0, draws, st);

@@ -2,6 +2,9 @@
 // Eq. 1), prefix sums (the column distribution's CDF and the
 // counting-sort offsets), the counting-sort scatter into column- and
 // row-major layouts (the matricization), and column gathers.
+#include <algorithm>
+#include <cstdlib>
+
 #include "ctd_internal.cuh"
 
 namespace ctd {
@@ -19,79 +22,68 @@ void mode_extents(const int64_t dims[3], int alpha, int64_t* n_rows, int64_t* n_
   }
 }
 
-// Row (mode-alpha index) and little-endian column of one nonzero.
-struct ModeMap {
-  int alpha;
-  int64_t I, J, K;
-  __device__ __forceinline__ bool map(int32_t a, int32_t b, int32_t c, int32_t* row,
-                                      int64_t* col) const {
-    if (a < 0 || b < 0 || c < 0 || a >= I || b >= J || c >= K) return false;
-    if (alpha == 1) {
-      *row = a;
-      *col = (int64_t)b + J * (int64_t)c;
-    } else if (alpha == 2) {
-      *row = b;
-      *col = (int64_t)a + I * (int64_t)c;
-    } else {
-      *row = c;
-      *col = (int64_t)a + I * (int64_t)b;
-    }
-    return true;
-  }
-};
+static ModeMap make_map(const CooDev& X) { return make_mode_map(X.dims, X.alpha); }
 
-static ModeMap make_map(const CooDev& X) {
-  ModeMap m;
-  m.alpha = X.alpha;
-  m.I = X.dims[0];
-  m.J = X.dims[1];
-  m.K = X.dims[2];
-  return m;
+// The COO arrays are read with 16-byte loads (four entries per array per
+// load) when all four start on a 16-byte boundary, with the streaming
+// cache hint: each entry is read once, and the random-access arrays of the
+// pass (counts, cursors, the column-major output) should keep L2.
+static bool coo_vec4(const CooDev& X) {
+  return ((reinterpret_cast<uintptr_t>(X.i) | reinterpret_cast<uintptr_t>(X.j) |
+           reinterpret_cast<uintptr_t>(X.k) | reinterpret_cast<uintptr_t>(X.v)) & 15) == 0;
 }
 
 // ---------------------------------------------------------------------------
-// K1: norms and counts
+// K1a: entries per column and per row
 // ---------------------------------------------------------------------------
 // Row counts go to a per-block shared-memory histogram when the rows fit
 // (Zipf sources put ~10% of all nonzeros on one row; global atomics on that
 // one address would serialize), then one global add per touched row.
+// Column counts are one non-returning 4-byte atomic per entry.
 constexpr int NORMS_SMEM_ROWS = 16384;
 
-__global__ void k_fiber_norms(const int32_t* __restrict__ ii, const int32_t* __restrict__ jj,
-                              const int32_t* __restrict__ kk, const int32_t* __restrict__ vv,
-                              int64_t nnz, ModeMap mm, int64_t n_rows,
-                              unsigned long long* __restrict__ norm2,
-                              unsigned* __restrict__ colcnt, unsigned* __restrict__ rowcnt,
-                              int* minval, unsigned* status) {
+template <bool VEC>
+__global__ void __launch_bounds__(512)
+    k_count(const int32_t* __restrict__ ii, const int32_t* __restrict__ jj,
+            const int32_t* __restrict__ kk, int64_t nnz, ModeMap mm, int64_t n_rows,
+            unsigned* __restrict__ colcnt, unsigned* __restrict__ rowcnt, unsigned* status) {
   extern __shared__ unsigned rowhist[];
   const bool priv = n_rows <= NORMS_SMEM_ROWS;
   if (priv) {
     for (int64_t r = threadIdx.x; r < n_rows; r += blockDim.x) rowhist[r] = 0;
     __syncthreads();
   }
-  int local_min = INT32_MAX;
   bool bad = false;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+  auto one = [&](int32_t a, int32_t b, int32_t c) {
     int32_t row;
     int64_t col;
-    const int32_t v = __ldg(vv + e);
-    if (!mm.map(__ldg(ii + e), __ldg(jj + e), __ldg(kk + e), &row, &col)) {
+    if (!mm.map(a, b, c, &row, &col)) {
       bad = true;
-      continue;
+      return;
     }
-    const unsigned long long v2 = (unsigned long long)((long long)v * (long long)v);
-    atomicAdd(norm2 + col, v2);
     atomicAdd(colcnt + col, 1u);
     if (priv)
       atomicAdd(rowhist + row, 1u);
     else
       atomicAdd(rowcnt + row, 1u);
-    local_min = min(local_min, v);
+  };
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t tail0 = 0;
+  if (VEC) {
+    const int64_t nq = nnz >> 2;
+    for (int64_t q = gt; q < nq; q += stride) {
+      const int4 a = __ldcs(reinterpret_cast<const int4*>(ii) + q);
+      const int4 b = __ldcs(reinterpret_cast<const int4*>(jj) + q);
+      const int4 c = __ldcs(reinterpret_cast<const int4*>(kk) + q);
+      one(a.x, b.x, c.x);
+      one(a.y, b.y, c.y);
+      one(a.z, b.z, c.z);
+      one(a.w, b.w, c.w);
+    }
+    tail0 = nq << 2;
   }
-  // warp-reduce the minimum before one atomic
-  for (int o = 16; o; o >>= 1) local_min = min(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
-  if ((threadIdx.x & 31) == 0 && local_min != INT32_MAX) atomicMin(minval, local_min);
+  for (int64_t e = tail0 + gt; e < nnz; e += stride) one(__ldcs(ii + e), __ldcs(jj + e), __ldcs(kk + e));
   if (bad) atomicOr(status, DEV_BAD_INDEX);
   if (priv) {
     __syncthreads();
@@ -100,19 +92,26 @@ __global__ void k_fiber_norms(const int32_t* __restrict__ ii, const int32_t* __r
   }
 }
 
-void launch_fiber_norms(const CooDev& X, uint64_t* norm2, uint32_t* colcnt, uint32_t* rowcnt,
-                        int* minval, unsigned* status, cudaStream_t st) {
+void launch_count(const CooDev& X, uint32_t* colcnt, uint32_t* rowcnt, unsigned* status,
+                  cudaStream_t st) {
   if (X.nnz == 0) return;
   const int bs = 512;
   int64_t n_rows, n_cols;
   mode_extents(X.dims, X.alpha, &n_rows, &n_cols);
   const bool priv = n_rows <= NORMS_SMEM_ROWS;
   const size_t smem = priv ? (size_t)n_rows * 4 : 0;
-  if (smem > 48 * 1024)
-    allow_max_smem((const void*)k_fiber_norms);
-  unsigned g = grid_for(X.nnz, bs, (int64_t)num_sms() * 2);
-  CTD_LAUNCH(k_fiber_norms, (g), (bs), smem, st, X.i, X.j, X.k, X.v, X.nnz, make_map(X), n_rows,
-             reinterpret_cast<unsigned long long*>(norm2), colcnt, rowcnt, minval, status);
+  const bool vec = coo_vec4(X);
+  const void* fn = vec ? (const void*)k_count<true> : (const void*)k_count<false>;
+  if (smem > 48 * 1024) allow_max_smem(fn);
+  // 4 entries per thread on the vector path; at most 2 blocks per SM (the
+  // row histogram is zeroed and flushed once per block)
+  const unsigned g = grid_for((X.nnz + 3) / (vec ? 4 : 1), bs, (int64_t)num_sms() * 2);
+  if (vec)
+    CTD_LAUNCH(k_count<true>, (g), (bs), smem, st, X.i, X.j, X.k, X.nnz, make_map(X), n_rows,
+               colcnt, rowcnt, status);
+  else
+    CTD_LAUNCH(k_count<false>, (g), (bs), smem, st, X.i, X.j, X.k, X.nnz, make_map(X), n_rows,
+               colcnt, rowcnt, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -124,9 +123,6 @@ void launch_fiber_norms(const CooDev& X, uint64_t* norm2, uint32_t* colcnt, uint
 // CDF) sets DEV_OVERFLOW, integer arithmetic only (GB300's FP64 pipe is
 // narrow, and a double running sum per element made these passes FP64-bound).
 // ---------------------------------------------------------------------------
-constexpr int SCAN_WARPS = 8;
-constexpr int SCAN_PER_WARP = 512;                       // 16 per lane
-constexpr int SCAN_TILE = SCAN_WARPS * SCAN_PER_WARP;    // 4096
 
 // tmp layout: [ntiles + 1] tile sums (exclusive offsets after the tile scan,
 // the total last), then [ntiles * SCAN_WARPS] warp sums
@@ -229,10 +225,14 @@ __global__ void k_scan_tiles(unsigned long long* tile_sum, int64_t ntiles, unsig
   }
 }
 
+// `in` and `out` may be the same array (inclusive u64 scan), and cur32 may
+// alias `in`: each element is read once, by the thread that then writes it,
+// before that write, so neither pointer is declared __restrict__.
 template <typename Tin>
-__global__ void k_scan_apply(const Tin* __restrict__ in, unsigned long long* __restrict__ out,
-                             int64_t n, const unsigned long long* __restrict__ tile_off,
-                             const unsigned long long* __restrict__ warp_sums, bool inclusive) {
+__global__ void k_scan_apply(const Tin* in, unsigned long long* out, int64_t n,
+                             const unsigned long long* __restrict__ tile_off,
+                             const unsigned long long* __restrict__ warp_sums, bool inclusive,
+                             uint32_t* cur32) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)warp * SCAN_PER_WARP;
   unsigned long long carry = tile_off[blockIdx.x];
@@ -243,7 +243,10 @@ __global__ void k_scan_apply(const Tin* __restrict__ in, unsigned long long* __r
     const int64_t e = base + it * 32 + lane;
     const unsigned long long x = e < n ? (unsigned long long)in[e] : 0ull;
     const unsigned long long inc = warp_incl_scan(x);
-    if (e < n) out[e + shift] = carry + inc;
+    if (e < n) {
+      out[e + shift] = carry + inc;
+      if (cur32) cur32[e] = (uint32_t)(carry + inc - x);
+    }
     carry += __shfl_sync(0xffffffffu, inc, 31);
   }
   if (!inclusive && blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
@@ -251,7 +254,7 @@ __global__ void k_scan_apply(const Tin* __restrict__ in, unsigned long long* __r
 
 template <typename Tin>
 static void scan_impl(const Tin* in, uint64_t* out, int64_t n, bool inclusive, uint64_t* tmp,
-                      unsigned* status, cudaStream_t st) {
+                      unsigned* status, cudaStream_t st, uint32_t* cur32 = nullptr) {
   const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (n == 0) {
     if (!inclusive) cudaMemsetAsync(out, 0, sizeof(uint64_t), st);
@@ -262,7 +265,114 @@ static void scan_impl(const Tin* in, uint64_t* out, int64_t n, bool inclusive, u
   CTD_LAUNCH(k_scan_reduce<Tin>, ((unsigned)ntiles), (SCAN_WARPS * 32), 0, st, in, n, ts, wsums);
   CTD_LAUNCH(k_scan_tiles, (1), (1024), 0, st, ts, ntiles, status);
   CTD_LAUNCH(k_scan_apply<Tin>, ((unsigned)ntiles), (SCAN_WARPS * 32), 0, st, in,
-             reinterpret_cast<unsigned long long*>(out), n, ts, wsums, inclusive);
+             reinterpret_cast<unsigned long long*>(out), n, ts, wsums, inclusive, cur32);
+}
+
+// ---------------------------------------------------------------------------
+// K1b: squared column norms (Eq. 1's numerators) from the column-major
+// layout, as the first pass of the CDF's reduce-then-scan
+// ---------------------------------------------------------------------------
+// A warp takes 512 consecutive columns in 16 groups of 32 (a block of 8
+// warps is one 4096-column scan tile), a lane per column.  Most columns of
+// count data hold a few entries: each lane walks its own column if it has
+// at most 32 (the group's entries are contiguous, so after the first touch
+// these reads hit L1); longer columns are then summed by the whole warp,
+// one at a time, with coalesced reads.  No atomics; every sum is a
+// saturating u64 add, so a column whose exact sum reaches 2^64 stays
+// saturated and the tile check flags the overflow.
+__global__ void __launch_bounds__(SCAN_WARPS * 32)
+    k_sqnorms_reduce(const unsigned long long* __restrict__ colptr,
+                     const int32_t* __restrict__ val, int64_t n,
+                     unsigned long long* __restrict__ norm2,
+                     unsigned long long* __restrict__ tile_sum,
+                     unsigned long long* __restrict__ warp_sums, unsigned* minkey) {
+  const unsigned FULL = 0xffffffffu;
+  __shared__ unsigned long long ws[SCAN_WARPS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)warp * SCAN_PER_WARP;
+  const unsigned long long end_all = colptr[n];
+  unsigned long long acc = 0;
+  int vmin = INT32_MAX;
+  unsigned long long a_next = base + lane < n ? colptr[base + lane] : end_all;
+  for (int it = 0; it < SCAN_PER_WARP / 32; ++it) {
+    const int64_t f = base + it * 32 + lane;
+    const unsigned long long a = a_next;
+    // start of the column after this lane's (lane 31: the next group's first)
+    unsigned long long b = __shfl_down_sync(FULL, a, 1);
+    if (lane == 31) b = f + 1 < n ? colptr[f + 1] : end_all;
+    if (it + 1 < SCAN_PER_WARP / 32) a_next = f + 32 < n ? colptr[f + 32] : end_all;
+    const int len = (int)min(b - a, 33ull);
+    const int lshort = len <= 32 ? len : 0;
+    const int maxs = (int)__reduce_max_sync(FULL, (unsigned)lshort);
+    unsigned long long mine = 0;
+    for (int t = 0; t < maxs; ++t)
+      if (t < lshort) {
+        const int v = __ldg(val + a + t);
+        vmin = min(vmin, v);
+        mine = sat_add(mine, (unsigned long long)((long long)v * (long long)v));
+      }
+    unsigned longs = __ballot_sync(FULL, len > 32);
+    while (longs) {
+      const int c = __ffs(longs) - 1;
+      longs &= longs - 1;
+      const unsigned long long la = __shfl_sync(FULL, a, c), lb = __shfl_sync(FULL, b, c);
+      unsigned long long part = 0;
+      for (unsigned long long p = la + lane; p < lb; p += 32) {
+        const int v = __ldg(val + p);
+        vmin = min(vmin, v);
+        part = sat_add(part, (unsigned long long)((long long)v * (long long)v));
+      }
+      part = warp_sat_sum(part);
+      if (lane == c) mine = part;
+    }
+    if (f < n) norm2[f] = mine;
+    acc = sat_add(acc, mine);
+  }
+  acc = warp_sat_sum(acc);
+  for (int o = 16; o; o >>= 1) vmin = min(vmin, __shfl_xor_sync(FULL, vmin, o));
+  if (lane == 0) {
+    ws[warp] = acc;
+    warp_sums[(int64_t)blockIdx.x * SCAN_WARPS + warp] = acc;
+    if (vmin != INT32_MAX) atomicMin(minkey, (unsigned)vmin ^ 0x80000000u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < SCAN_WARPS; ++w) t = sat_add(t, ws[w]);
+    tile_sum[blockIdx.x] = t;
+  }
+}
+
+void launch_sqnorms_cdf(const uint64_t* colptr, const int32_t* val, int64_t n, uint64_t* norm2,
+                        uint64_t* cdf, unsigned* minkey, uint64_t* tmp, unsigned* status,
+                        cudaStream_t st) {
+  if (n == 0) return;
+  const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  unsigned long long* ts = reinterpret_cast<unsigned long long*>(tmp);
+  unsigned long long* wsums = ts + ntiles + 2;
+  unsigned long long* nn = reinterpret_cast<unsigned long long*>(norm2);
+  CTD_LAUNCH(k_sqnorms_reduce, ((unsigned)ntiles), (SCAN_WARPS * 32), 0, st,
+             reinterpret_cast<const unsigned long long*>(colptr), val, n, nn, ts, wsums, minkey);
+  CTD_LAUNCH(k_scan_tiles, (1), (1024), 0, st, ts, ntiles, status);
+  CTD_LAUNCH(k_scan_apply<unsigned long long>, ((unsigned)ntiles), (SCAN_WARPS * 32), 0, st, nn,
+             reinterpret_cast<unsigned long long*>(cdf), n, ts, wsums, true, (uint32_t*)nullptr);
+}
+
+// The last two passes of a scan whose first pass was fused into another
+// kernel: that kernel wrote, per 4096-element tile, the tile's sum at
+// tile_sum[t] and its eight 512-element warp sums at warp_sums[8 t + w]
+// (tmp laid out as scan_impl's: tile sums first, warp sums after
+// ntiles + 2 entries).
+void launch_scan_finish(const uint64_t* in, uint64_t* out, int64_t n, uint64_t* tmp,
+                        unsigned* status, cudaStream_t st) {
+  if (n == 0) return;
+  const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  unsigned long long* ts = reinterpret_cast<unsigned long long*>(tmp);
+  unsigned long long* wsums = ts + ntiles + 2;
+  CTD_LAUNCH(k_scan_tiles, (1), (1024), 0, st, ts, ntiles, status);
+  CTD_LAUNCH(k_scan_apply<unsigned long long>, ((unsigned)ntiles), (SCAN_WARPS * 32), 0, st,
+             reinterpret_cast<const unsigned long long*>(in),
+             reinterpret_cast<unsigned long long*>(out), n, ts, wsums, true, (uint32_t*)nullptr);
 }
 
 void launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, bool inclusive, uint64_t* tmp,
@@ -271,45 +381,104 @@ void launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, bool inclusiv
                                 inclusive, tmp, status, st);
 }
 void launch_scan_u32(const uint32_t* in, uint64_t* out, int64_t n, bool inclusive, uint64_t* tmp,
-                     unsigned* status, cudaStream_t st) {
-  scan_impl<unsigned>(in, out, n, inclusive, tmp, status, st);
+                     unsigned* status, cudaStream_t st, uint32_t* cur32) {
+  scan_impl<unsigned>(in, out, n, inclusive, tmp, status, st, cur32);
 }
 
 // ---------------------------------------------------------------------------
-// K5a: counting-sort scatter (CSC by column and CSR by row)
+// K5a: counting-sort scatter into the column-major layout
 // ---------------------------------------------------------------------------
-__global__ void k_coo_scatter(const int32_t* __restrict__ ii, const int32_t* __restrict__ jj,
-                              const int32_t* __restrict__ kk, const int32_t* __restrict__ vv,
-                              int64_t nnz, ModeMap mm, unsigned long long* colcur,
-                              unsigned long long* rowcur, int32_t* __restrict__ csc_row,
-                              int32_t* __restrict__ csc_val, int32_t* __restrict__ csr_col,
-                              int32_t* __restrict__ csr_val) {
+// Each entry takes its place from its column's u32 cursor (one returning
+// atomic) and writes its row and value there.  A thread takes four entries
+// and issues their four atomics before any store, so their round trips
+// overlap.  The random targets (cursors, rows, values) are kept L2-resident
+// by splitting the columns into ranges, one pass over the COO per range:
+// an entry is placed in the pass whose range holds its column.  Without
+// the split the targets of a 10^7-entry tensor (120 MB) and the streamed
+// COO do not fit in L2 together, and every partial-sector store becomes a
+// DRAM read-modify-write.
+template <bool VEC>
+__global__ void __launch_bounds__(256)
+    k_coo_scatter(const int32_t* __restrict__ ii, const int32_t* __restrict__ jj,
+                  const int32_t* __restrict__ kk, const int32_t* __restrict__ vv, int64_t nnz,
+                  ModeMap mm, int64_t c_lo, int64_t c_hi, unsigned* __restrict__ cur,
+                  int32_t* __restrict__ csc_row, int32_t* __restrict__ csc_val) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+  int64_t tail0 = 0;
+  if (VEC) {
+    const int64_t nq = nnz >> 2;
+    for (int64_t q = gt; q < nq; q += stride) {
+      const int4 a = __ldcs(reinterpret_cast<const int4*>(ii) + q);
+      const int4 b = __ldcs(reinterpret_cast<const int4*>(jj) + q);
+      const int4 c = __ldcs(reinterpret_cast<const int4*>(kk) + q);
+      const int32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w},
+                    cv[4] = {c.x, c.y, c.z, c.w};
+      int32_t row[4];
+      int64_t col[4];
+      bool ok[4];
+      bool any = false;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ok[u] = mm.map(av[u], bv[u], cv[u], &row[u], &col[u]) && col[u] >= c_lo && col[u] < c_hi;
+        any |= ok[u];
+      }
+      if (!any) continue;
+      const int4 v = __ldcs(reinterpret_cast<const int4*>(vv) + q);
+      const int32_t vals[4] = {v.x, v.y, v.z, v.w};
+      unsigned pos[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pos[u] = ok[u] ? atomicAdd(cur + col[u], 1u) : 0u;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (ok[u]) {
+          csc_row[pos[u]] = row[u];
+          csc_val[pos[u]] = vals[u];
+        }
+    }
+    tail0 = nq << 2;
+  }
+  for (int64_t e = tail0 + gt; e < nnz; e += stride) {
     int32_t row;
     int64_t col;
-    const int32_t v = __ldg(vv + e);
-    if (!mm.map(__ldg(ii + e), __ldg(jj + e), __ldg(kk + e), &row, &col)) continue;
-    unsigned long long pc = atomicAdd(colcur + col, 1ull);
-    csc_row[pc] = row;
-    csc_val[pc] = v;
-    if (csr_col) {
-      unsigned long long pr = atomicAdd(rowcur + row, 1ull);
-      csr_col[pr] = (int32_t)col;
-      csr_val[pr] = v;
-    }
+    if (!mm.map(__ldcs(ii + e), __ldcs(jj + e), __ldcs(kk + e), &row, &col)) continue;
+    if (col < c_lo || col >= c_hi) continue;
+    const unsigned p = atomicAdd(cur + col, 1u);
+    csc_row[p] = row;
+    csc_val[p] = __ldcs(vv + e);
   }
 }
 
-void launch_coo_scatter(const CooDev& X, uint64_t* colcur, uint64_t* rowcur, int32_t* csc_row,
-                        int32_t* csc_val, int32_t* csr_col, int32_t* csr_val, cudaStream_t st) {
+// Bytes of random targets one pass may hold in L2 (cursors and entries).
+static int64_t scatter_l2_budget() {
+  static int64_t b = [] {
+    const char* e = getenv("CTD_SCATTER_L2_MB");  // tuning override
+    const long mb = e ? atol(e) : 0;
+    return (int64_t)(mb > 0 ? mb : 48) << 20;
+  }();
+  return b;
+}
+
+void launch_coo_scatter(const CooDev& X, uint32_t* cur, int32_t* csc_row, int32_t* csc_val,
+                        cudaStream_t st) {
   if (X.nnz == 0) return;
+  int64_t n_rows, n_cols;
+  mode_extents(X.dims, X.alpha, &n_rows, &n_cols);
   const int bs = 256;
-  unsigned g = grid_for(X.nnz, bs, (int64_t)num_sms() * 8);
-  CTD_LAUNCH(k_coo_scatter, (g), (bs), 0, st, X.i, X.j, X.k, X.v, X.nnz, make_map(X),
-                                  reinterpret_cast<unsigned long long*>(colcur),
-                                  reinterpret_cast<unsigned long long*>(rowcur), csc_row, csc_val,
-                                  csr_col, csr_val);
+  const bool vec = coo_vec4(X);
+  const unsigned g = grid_for((X.nnz + 3) / (vec ? 4 : 1), bs, (int64_t)num_sms() * 8);
+  const int64_t targets = 4 * n_cols + 8 * X.nnz;
+  const int64_t passes = std::max<int64_t>(1, std::min<int64_t>(8, (targets + scatter_l2_budget() - 1) / scatter_l2_budget()));
+  const int64_t span = (n_cols + passes - 1) / passes;
+  for (int64_t p = 0; p < passes; ++p) {
+    const int64_t lo = p * span, hi = std::min(n_cols, lo + span);
+    if (vec)
+      CTD_LAUNCH(k_coo_scatter<true>, (g), (bs), 0, st, X.i, X.j, X.k, X.v, X.nnz, make_map(X),
+                 lo, hi, cur, csc_row, csc_val);
+    else
+      CTD_LAUNCH(k_coo_scatter<false>, (g), (bs), 0, st, X.i, X.j, X.k, X.v, X.nnz, make_map(X),
+                 lo, hi, cur, csc_row, csc_val);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -24,13 +24,14 @@ CTD_SKIP_C = 1
 CTD_SKIP_ERROR = 2
 CTD_KEEP_LAST_C = 4
 CTD_DETERMINISTIC = 8
+CTD_KEEP_DIST = 16
 
 STATUS = {0: "CTD_OK", 1: "CTD_EINVAL", 2: "CTD_ENOMEM", 3: "CTD_EOVERFLOW", 4: "CTD_ECUDA",
           5: "CTD_ETIMEOUT", 6: "CTD_ENOTSUP"}
 
 EXPORTED = ["ctd_static", "ctd_dynamic_create", "ctd_dynamic_step", "ctd_error", "ctd_get_sizes",
             "ctd_get_samples", "ctd_get_fibers", "ctd_get_R", "ctd_get_U", "ctd_get_C_columns",
-            "ctd_get_C", "ctd_get_step", "ctd_get_M", "ctd_free", "ctd_last_error",
+            "ctd_get_C", "ctd_get_column_dist", "ctd_get_step", "ctd_get_M", "ctd_free", "ctd_last_error",
             "ctd_version", "ctd_profile", "ctd_profile_report", "ctd_sample_noalloc", "ctd_static_batched", "ctd_server_create", "ctd_server_submit",
             "ctd_server_wait", "ctd_server_result", "ctd_server_state", "ctd_server_free",
             "ctd_ddos_candidates", "ctd_dynamic_from_static", "ctd_fault_inject_alloc",
@@ -83,6 +84,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ctd_get_U": [P, P],
         "ctd_get_C_columns": [P, I64, P, P],
         "ctd_get_C": [P, P, P, P],
+        "ctd_get_column_dist": [P, P, P],
         "ctd_get_step": [P, I64, P, P],
         "ctd_get_M": [P, I64, P],
         "ctd_profile": [I32],
@@ -201,6 +203,14 @@ class Factors:
         Iu = np.empty(s.s_unique, np.int64)
         _check(load().ctd_get_samples(self.h, _ptr(I), _ptr(Iu)))
         return I, Iu
+
+    def column_dist(self):
+        """(norm2, cdf) of the draws' distribution (factors made with CTD_KEEP_DIST)."""
+        s = self.sizes()
+        n2 = np.empty(s.n_cols, np.uint64)
+        cdf = np.empty(s.n_cols, np.uint64)
+        _check(load().ctd_get_column_dist(self.h, _ptr(n2), _ptr(cdf)))
+        return n2, cdf
 
     def fibers(self):
         s = self.sizes()

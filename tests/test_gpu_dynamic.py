@@ -54,7 +54,24 @@ def check_step(G, st, step, t, eps, precision, dense_error=True):
     assert np.array_equal(G.R_dense(), R_ref)
     if st.R_cols:
         assert rel_fro(G.U(), st.U) <= u_tol(R_ref)
-    if step.M is not None:
+    tol = max(u_tol(R_ref), 1e-12)
+    # per-entry bars for this step's M and lower-left block of C: with
+    # M = ((Delta R)^T R^(t)) U^(t) (Eq. C_t+1_final, left to right), an error
+    # of relative size tol in U^(t) moves row m of M by at most
+    # tol ||g_m|| ||U^(t)||_F (g_m the exact integer row m of (Delta R)^T R^(t)),
+    # and entry (m, f) of the block M C^(t) by that times ||C^(t)(:, f)||
+    dt_new = R_ref.shape[1]
+    dt_old = dt_new - len(step.new_fibers)
+    row_scale = None
+    if step.M is not None and dt_old > 0 and dt_new > dt_old:
+        Rt, dR = R_ref[:, :dt_old], R_ref[:, dt_old:]
+        g = (dR.T @ Rt).astype(np.float64)
+        Ut = np.linalg.inv((Rt.T @ Rt).astype(np.float64))
+        row_scale = 4.0 * tol * np.linalg.norm(g, axis=1) * np.linalg.norm(Ut)
+        Mg = G.M(t)
+        assert rel_fro(Mg, step.M) <= u_tol(R_ref)
+        assert np.all(np.abs(Mg - step.M) <= row_scale[:, None])
+    elif step.M is not None:
         assert rel_fro(G.M(t), step.M) <= u_tol(R_ref)
     # every column of C^(t+1) (exact new block, implicit lower-left blocks)
     J = st.n_cols_slice
@@ -62,8 +79,13 @@ def check_step(G, st, step, t, eps, precision, dense_error=True):
     if st.C is not None and st.C.shape[0]:
         got = G.C_columns(np.arange(ncols))
         assert got.shape == st.C.shape
-        assert rel_fro(got, st.C) <= max(u_tol(R_ref), 1e-12)
+        assert rel_fro(got, st.C) <= tol
         assert np.array_equal(got[:, -J:], st.C[:, -J:])       # new block is exact
+        if row_scale is not None and t > 0:
+            old = st.C[:dt_old, :J * t]
+            bar = row_scale[:, None] * np.linalg.norm(old, axis=0)[None, :]
+            diff = np.abs(got[dt_old:, :J * t] - st.C[dt_old:, :J * t])
+            assert np.all(diff <= bar), float(np.max(diff - bar))
     # the literal X~ = R U C (Eq. error) loses every digit once U is the inverse
     # of a nearly singular R^T R (full row rank); there the oracle's per-step
     # projection form (Householder QR of R, reading A20) is the reference

@@ -62,6 +62,72 @@ def test_small_uniform_full(alpha, precision):
     check(F, ref, eps, precision, err_ref=e_ref)
 
 
+def check_dist(F, ref):
+    """Rows 1-2 element by element: every squared column norm and every CDF
+    entry equal to the oracle's exact integers."""
+    n2, c = F.column_dist()
+    assert np.array_equal(n2.astype(np.int64), ref.sqnorms)
+    assert np.array_equal(c.astype(np.int64), ref.cdf)
+
+
+@pytest.mark.parametrize("alpha", [1, 2, 3])
+@pytest.mark.parametrize("host", [False, True])
+def test_column_dist_small(alpha, host):
+    m = ctd()
+    coo = synth.small_uniform()
+    F = run(coo, alpha, 50, 1e-6, 0, 0, host=host, flags=m.CTD_KEEP_DIST)
+    ref = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, alpha, 50, 1e-6, 0)
+    check_dist(F, ref)
+
+
+@pytest.mark.parametrize("nnz", [1, 3, 4097, 20_001])
+def test_column_dist_ragged(nnz):
+    """Signed values, nnz around the 4-entry vector width, column counts
+    that are not multiples of the 4096-column scan tile."""
+    m = ctd()
+    coo = synth.tiny((37, 53, 29), nnz, seed=nnz, vmax=9, signed=True)
+    for alpha in (1, 3):
+        F = run(coo, alpha, 64, 1e-6, 1, 0, flags=m.CTD_KEEP_DIST)
+        ref = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, alpha, 64, 1e-6, 1)
+        check_dist(F, ref)
+        assert np.array_equal(F.samples()[0], ref.I)
+
+
+def bucket_case(kind):
+    """A 40 x 5000 x 1000 tensor: 5*10^6 columns of X_(1), enough for the
+    bucketed matricization (611 buckets of 8192 columns).  "balanced": 3*10^5
+    uniform entries (about 500 per bucket).  "over_capacity": 15,000 more
+    entries in the first bucket's columns, more than a place block stages
+    (10,240), so that bucket writes straight to global memory.  "skewed":
+    40,000 more, past twice that, so the plain passes run instead."""
+    dims = (40, 5000, 1000)
+    base = synth.tiny(dims, 300_000, seed=51, vmax=6, signed=True)
+    if kind == "balanced":
+        return base
+    extra = 15_000 if kind == "over_capacity" else 40_000
+    rng = np.random.default_rng(52)
+    lin = rng.choice(40 * 8192, size=extra, replace=False)
+    col = lin // 40
+    i = np.concatenate([base.i, lin % 40])
+    j = np.concatenate([base.j, col % 5000])
+    k = np.concatenate([base.k, col // 5000])
+    v = np.concatenate([base.val, rng.integers(1, 7, size=extra)])
+    key = i + 40 * (j + 5000 * k)
+    _, first = np.unique(key, return_index=True)
+    first = np.sort(first)
+    return synth.Coo3(dims, i[first], j[first], k[first], v[first])
+
+
+@pytest.mark.parametrize("kind", ["balanced", "over_capacity", "skewed"])
+def test_bucketed_matricize(kind):
+    m = ctd()
+    coo = bucket_case(kind)
+    F = run(coo, 1, 200, 1e-6, 4, 0, flags=m.CTD_KEEP_DIST)
+    ref = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 200, 1e-6, 4)
+    check_dist(F, ref)
+    check(F, ref, 1e-6, 0, err_ref=O.projection_error(ref.X, ref.R))
+
+
 def test_host_input_matches_device_input():
     coo = synth.small_uniform()
     Fd = run(coo, 1, 50, 1e-6, 3, 0)
@@ -195,6 +261,33 @@ def test_traffic_10m_full_size(traffic_full):
     check(F, ref, 1e-6, 1, full_c=False, c_cols=cols, err_ref=O.projection_error(ref.X, ref.R))
 
 
+def test_traffic_10m_dist_and_full_c(traffic_full):
+    """The 10^7-nonzero workload in the bench's launch configuration (FP32
+    bulk): all 10^7 squared column norms and CDF entries bit-exact, and the
+    whole of C = R^T X_(alpha) (6.6*10^8 entries) equal to the oracle's exact
+    product, compared in blocks of 10^6 columns."""
+    m = ctd()
+    coo, ref = traffic_full
+    F = run(coo, 1, 500, 1e-6, 0, 1, flags=m.CTD_KEEP_DIST)
+    check_dist(F, ref)
+    assert np.array_equal(F.R_dense(), ref.R)
+    p, r, v = F.C()
+    assert p[0] == 0 and p[-1] == F.sizes().nnz_C
+    Xs = ref.X.scipy()
+    import scipy.sparse as sp
+    Rt = sp.csr_matrix(ref.R.T.astype(np.int64))
+    step = 1_000_000
+    for a in range(0, ref.X.n_cols, step):
+        b = min(a + step, ref.X.n_cols)
+        want = (Rt @ Xs[:, a:b]).tocsc()
+        want.eliminate_zeros()
+        want.sort_indices()
+        lo, hi = int(p[a]), int(p[b])
+        assert np.array_equal(p[a:b + 1] - lo, want.indptr), a
+        assert np.array_equal(r[lo:hi], want.indices), a
+        assert np.array_equal(v[lo:hi], want.data.astype(np.float32).astype(np.float64)), a
+
+
 def test_repeat_calls_bit_identical(traffic_full):
     """With CTD_DETERMINISTIC, three calls on the 10^7-nonzero workload (FP32
     bulk, then FP64) give bit-identical U, C and error: each column's
@@ -229,6 +322,23 @@ def test_sqnorm_range():
     F = run(coo2, 1, 64, 1e-6, 0, 0)
     assert F.sizes().sqnorm_X == float(2 * big * big)
     assert F.sizes().s_kept == 2
+
+
+@pytest.mark.parametrize("n", [3, 5])
+def test_fiber_sum_overflow(n):
+    """n values of 2^31 - 1 in one fiber: the column's exact sum passes 2^63
+    (n = 5 would also wrap a 64-bit accumulator to a value below 2^63), so
+    the call reports CTD_EOVERFLOW (reading A12), as the oracle raises."""
+    m = ctd()
+    big = 2 ** 31 - 1
+    i = np.arange(n)
+    coo = synth.Coo3((8, 3, 2), i, np.ones(n, np.int64), np.zeros(n, np.int64),
+                     np.full(n, big, np.int64))
+    with pytest.raises(OverflowError):
+        O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 5, 1e-6, 0)
+    with pytest.raises(m.CtdError) as e:
+        run(coo, 1, 5, 1e-6, 0, 0)
+    assert e.value.status == "CTD_EOVERFLOW"
 
 
 def test_bounded_wait_gives_up_and_context_survives():

@@ -20,24 +20,25 @@ def ctd():
     return m
 
 
-def noalloc(m, X, s, seed):
+def noalloc(m, X, s, seed, alpha=1):
     import torch
     draws = torch.full((s,), -7, dtype=torch.int64, device="cuda")
     uniq = torch.full((s,), -7, dtype=torch.int64, device="cuda")
-    n = m.sample_noalloc(X, 1, s, seed, draws, uniq)
+    n = m.sample_noalloc(X, alpha, s, seed, draws, uniq)
     return draws.cpu().numpy(), uniq.cpu().numpy()[:n]
 
 
-def test_two_calls_match_ctd_static():
+@pytest.mark.parametrize("alpha", [1, 2, 3])
+def test_two_calls_match_ctd_static(alpha):
     import torch
     m = ctd()
     coo = synth.small_uniform()
     X = m.Coo.from_synth(coo)
-    F = m.ctd_static(X, 1, 50, 1e-6, 3, m.CTD_FP64)
+    F = m.ctd_static(X, alpha, 50, 1e-6, 3, m.CTD_FP64)
     I_ref, Iu_ref = F.samples()
-    first = noalloc(m, X, 50, 3)
+    first = noalloc(m, X, 50, 3, alpha)
     free_before = torch.cuda.mem_get_info()[0]
-    second = noalloc(m, X, 50, 3)
+    second = noalloc(m, X, 50, 3, alpha)
     torch.cuda.synchronize()
     assert torch.cuda.mem_get_info()[0] == free_before  # nothing allocated
     for draws, uniq in (first, second):
@@ -58,6 +59,30 @@ def test_previous_contents_do_not_leak():
         draws, uniq = noalloc(m, X, s, seed)
         assert np.array_equal(draws, ref[0])
         assert np.array_equal(uniq, ref[1])
+
+
+def test_all_zero_input_draws_nothing():
+    """||X|| = 0: no column can be drawn.  ctd_static reports zero draws;
+    this entry point marks every draw -1 and reports no unique draw."""
+    m = ctd()
+    coo = synth.tiny((5, 4, 3), 10, seed=1)
+    coo.val[:] = 0
+    X = m.Coo.from_synth(coo)
+    assert m.ctd_static(X, 1, 10, 1e-6, 0, m.CTD_FP64).sizes().s_draws == 0
+    draws, uniq = noalloc(m, X, 10, 0)
+    assert np.all(draws == -1) and uniq.size == 0
+
+
+def test_fiber_sum_overflow_is_reported():
+    """Five values of 2^31 - 1 in one fiber: the column's sum of squares
+    wraps a 64-bit accumulator; the call must still report CTD_EOVERFLOW."""
+    m = ctd()
+    big = 2 ** 31 - 1
+    coo = synth.Coo3((8, 3, 2), np.arange(5), np.ones(5, np.int64), np.zeros(5, np.int64),
+                     np.full(5, big, np.int64))
+    with pytest.raises(m.CtdError) as e:
+        noalloc(m, m.Coo.from_synth(coo), 5, 0)
+    assert e.value.status == "CTD_EOVERFLOW"
 
 
 def test_limits_are_reported():
