@@ -255,12 +255,12 @@ ctd_status matricize(const CooDev& X, Arena& A, cudaStream_t st, Matricized* M, 
   CTD_TRY(A.get(&M->colptr, M->n_cols + 1));
   CTD_TRY(A.get(&M->csc_row, X.nnz));
   CTD_TRY(A.get(&M->csc_val, X.nnz));
-  CTD_TRY(A.get(&M->minval, 1));
+  CTD_TRY(A.get(&M->minval, 2));
   CTD_TRY(A.get(&M->status, 1));
   CTD_TRY(A.get(&M->tmp, scan_tmp_elems(std::max(M->n_cols, M->n_rows) + 1)));
   CTD_CUDA(cudaMemsetAsync(rowcnt, 0, M->n_rows * 4, st));
   CTD_CUDA(cudaMemsetAsync(M->status, 0, 4, st));
-  CTD_CUDA(cudaMemsetAsync(M->minval, 0xff, 4, st));  // code of "no value yet"
+  CTD_CUDA(cudaMemsetAsync(M->minval, 0xff, 8, st));  // codes of "no value yet"
   bool bucketed = false;
   CTD_TRY(matricize_bucketed(X, A, st, M, &bucketed));
   if (!bucketed) {
@@ -388,13 +388,13 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   launch_scan_u64(rc_sizes, rc_ptr, s, false, M.tmp, M.status, st);
   STEPC(cudaGetLastError());
   unsigned status = 0;
-  unsigned minkey = 0;
+  unsigned minkey[2] = {0, 0};
   int s_unique = 0;
   uint64_t T = 0, nnz_cand = 0;
   {
     Readback rb(st);
     STEP(rb.add(&status, M.status, 1));
-    STEP(rb.add(&minkey, M.minval, 1));
+    STEP(rb.add(minkey, M.minval, 2));
     STEP(rb.add(&s_unique, d_count, 1));
     STEP(rb.add(&nnz_cand, rc_ptr + s, 1));
     if (M.n_cols > 0) STEP(rb.add(&T, M.cdf + (M.n_cols - 1), 1));
@@ -402,7 +402,9 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   }
   STEP(status_from_device(status));
   F->T = T;
-  const int minval = decode_min(minkey);
+  const int minval = decode_min(minkey[0]);
+  // X's values fit int8: the C fill can take four products per instruction
+  const bool x_int8 = minval >= -128 && decode_max(minkey[1]) <= 127;
   F->min_val = minval;
   F->s_unique = s_unique;
   if (T == 0) F->s = 0;  // nothing to draw from
@@ -534,11 +536,11 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
     F->Cval = cv;
     PhaseScope ph("c_fill", st);
     STEP(launch_c_fill(M.csc(), M.n_cols, M.n_rows, M.nnz, R, F->Coff, F->Ccnt, F->Crow, F->Cval,
-                       precision == CTD_FP32_BULK, minval > 0, T, st));
+                       precision == CTD_FP32_BULK, minval > 0, x_int8, T, st));
   }
   uint64_t* d_nnzc;
   STEP(scratch.get(&d_nnzc, 1));
-  if (F->Ccnt) launch_sum_u32(F->Ccnt, M.n_cols, d_nnzc, st);
+  if (F->Ccnt) launch_sum_u32(F->Ccnt, M.n_cols, d_nnzc, st, C_COUNT);
   uint64_t nnzC = 0, nnzR_final = 0;
   double pu = 0.0;
   {
@@ -670,8 +672,13 @@ __global__ void k_c_columns(const unsigned long long* __restrict__ coff,
     const int64_t f = cols[c];
     const unsigned long long o = coff[f];
     const unsigned n = ccnt[f];
-    for (unsigned q = threadIdx.x; q < n; q += blockDim.x)
-      out[c * height + crow[o + q]] = (double)cval[o + q];
+    if (n & C_DENSE) {
+      for (int64_t m = threadIdx.x; m < height; m += blockDim.x)
+        out[c * height + m] = (double)cval[o + m];
+    } else {
+      for (unsigned q = threadIdx.x; q < n; q += blockDim.x)
+        out[c * height + crow[o + q]] = (double)cval[o + q];
+    }
   }
 }
 }  // namespace ctd
@@ -741,8 +748,18 @@ static ctd_status get_C_host(const ctd_factors* F, int64_t* colptr, int32_t* row
     CTD_TRY(sync(st));
   }
   int64_t pos = 0;
+  const int64_t h = F->s_kept;
   for (int64_t f = 0; f < n; ++f) {
     colptr[f] = pos;
+    if (cnt[f] & C_DENSE) {
+      for (int64_t m = 0; m < h; ++m)
+        if (v[off[f] + m] != 0.0) {
+          if (row) row[pos] = (int32_t)m;
+          if (val) val[pos] = v[off[f] + m];
+          ++pos;
+        }
+      continue;
+    }
     for (uint32_t q = 0; q < cnt[f]; ++q) {
       if (row) row[pos] = r[off[f] + q];
       if (val) val[pos] = v[off[f] + q];

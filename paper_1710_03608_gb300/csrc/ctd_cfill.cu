@@ -146,8 +146,7 @@ __global__ void __launch_bounds__(256)
         if (ub == 0) {
           ccnt[f] = 0;
         } else if (nx == 1 && positive) {
-          k = 0;
-          ccnt[f] = (unsigned)ub;
+          k = 0;  // the copy writes the count (R's row length)
         } else {
           k = nx >= (unsigned long long)CF_HEAVY_COL ? 1 : 2;
         }
@@ -268,8 +267,8 @@ __global__ void __launch_bounds__(256)
                 const unsigned long long* __restrict__ ip, const uint16_t* __restrict__ icol,
                 const int* __restrict__ ival, int64_t P, const int64_t* __restrict__ single,
                 const unsigned* __restrict__ n_single,
-                const unsigned long long* __restrict__ coff, uint16_t* __restrict__ crow,
-                V* __restrict__ cval) {
+                const unsigned long long* __restrict__ coff, unsigned* __restrict__ ccnt,
+                uint16_t* __restrict__ crow, V* __restrict__ cval) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -286,6 +285,7 @@ __global__ void __launch_bounds__(256)
       v = __ldg(X.val + xa);
       b = __ldg(ip + i);
       rl = (int)(__ldg(rp + i + 1) - __ldg(rp + i));
+      ccnt[f] = (unsigned)rl;  // v > 0 and R > 0: every product is nonzero
     }
     const int nq = rl > 0 ? ((int)(o & 3ull) + rl + 3) >> 2 : 0;
     int incl = nq;
@@ -348,14 +348,46 @@ __global__ void __launch_bounds__(256)
 // One chunk of up to 32 column entries, one per lane (sl = dense slot or -1;
 // rs/rl = the R row's range for a sparse row; rl = 0 for idle lanes):
 // dense rows into regs (lane's rows 128 q + 4 lane + k), other rows into the
-// shared accumulator acc (atomics).
-template <int NQ, int DB>
+// shared accumulator acc (atomics).  P4 (int8 dense rows, X's values in
+// [-128, 127]): four entries at a time; each lane loads the four rows'
+// words for its outputs 4 lane + {0..3}, transposes the 4 x 4 bytes with
+// byte permutes so that each word holds one output's four row values, and
+// adds the four products with one dp4a per output (exact int32 sums).
+template <int NQ, int DB, bool P4>
 __device__ __forceinline__ void chunk_reg(const CsrDev& R, const void* __restrict__ dense_v,
                                           int* acc, int (&regs)[4 * NQ], int v, int sl,
                                           unsigned long long rs, int rl) {
   constexpr int W4 = NQ * 32;  // 4-entry groups per dense row
   const int lane = threadIdx.x & 31;
   unsigned dense_b = __ballot_sync(0xffffffffu, sl >= 0);
+  if (P4 && DB == 1) {
+    while (dense_b) {
+      int h[4], vp = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int src = dense_b ? __ffs(dense_b) - 1 : -1;
+        if (dense_b) dense_b &= dense_b - 1;
+        const int s = src < 0 ? 0 : src;
+        const int hs = __shfl_sync(0xffffffffu, sl, s);
+        const int vs = __shfl_sync(0xffffffffu, v, s);
+        // a missing fourth entry repeats the first row with value 0
+        h[u] = src < 0 ? h[0] : hs;
+        vp |= ((src < 0 ? 0 : vs) & 0xff) << (8 * u);
+      }
+      const unsigned* d = static_cast<const unsigned*>(dense_v) + lane;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const unsigned w0 = d[h[0] * W4 + q * 32], w1 = d[h[1] * W4 + q * 32];
+        const unsigned w2 = d[h[2] * W4 + q * 32], w3 = d[h[3] * W4 + q * 32];
+        const unsigned lo01 = __byte_perm(w0, w1, 0x5140), hi01 = __byte_perm(w0, w1, 0x7362);
+        const unsigned lo23 = __byte_perm(w2, w3, 0x5140), hi23 = __byte_perm(w2, w3, 0x7362);
+        regs[4 * q + 0] = __dp4a((int)__byte_perm(lo01, lo23, 0x5410), vp, regs[4 * q + 0]);
+        regs[4 * q + 1] = __dp4a((int)__byte_perm(lo01, lo23, 0x7632), vp, regs[4 * q + 1]);
+        regs[4 * q + 2] = __dp4a((int)__byte_perm(hi01, hi23, 0x5410), vp, regs[4 * q + 2]);
+        regs[4 * q + 3] = __dp4a((int)__byte_perm(hi01, hi23, 0x7632), vp, regs[4 * q + 3]);
+      }
+    }
+  }
   while (dense_b) {
     const int src = __ffs(dense_b) - 1;
     dense_b &= dense_b - 1;
@@ -448,7 +480,7 @@ __device__ __forceinline__ void entry_meta(const CsrDev& R, const Dense& dn, int
 
 // Accumulate R^T x_f over the column's entries [a, b): warps of a group
 // [gwarp, gwarp + gwarps) take interleaved 32-entry chunks.
-template <int NQ, int DB>
+template <int NQ, int DB, bool P4>
 __device__ __forceinline__ void accumulate_reg(const CscDev& X, const CsrDev& R, const Dense& dn,
                                                const void* __restrict__ dense4,
                                                unsigned long long a, unsigned long long b,
@@ -465,89 +497,8 @@ __device__ __forceinline__ void accumulate_reg(const CscDev& X, const CsrDev& R,
       v = __ldg(X.val + p);
     }
     entry_meta(R, dn, i, sl, rs, rl);
-    chunk_reg<NQ, DB>(R, dense4, acc, regs, v, sl, rs, rl);
+    chunk_reg<NQ, DB, P4>(R, dense4, acc, regs, v, sl, rs, rl);
   }
-}
-
-// Emit one column from regs + acc (acc zeroed on the way, regs too): the
-// nonzeros of rows [0, W) in ascending order at crow/cval + off, each lane's
-// position from four ballots.  Returns their count (same in every lane).
-template <typename V, int NQ>
-__device__ __forceinline__ unsigned emit_reg(int* acc, int (&regs)[4 * NQ], unsigned long long off,
-                                             uint16_t* __restrict__ crow, V* __restrict__ cval) {
-  const int lane = threadIdx.x & 31;
-  int4* acc4 = reinterpret_cast<int4*>(acc);
-  unsigned pos = 0;
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    const int4 s = acc4[q * 32 + lane];
-    acc4[q * 32 + lane] = make_int4(0, 0, 0, 0);
-    const int x0 = regs[4 * q] + s.x, x1 = regs[4 * q + 1] + s.y;
-    const int x2 = regs[4 * q + 2] + s.z, x3 = regs[4 * q + 3] + s.w;
-    regs[4 * q] = regs[4 * q + 1] = regs[4 * q + 2] = regs[4 * q + 3] = 0;
-    // lane-major order: entries of the lanes before this one, by ballots
-    const unsigned b0 = __ballot_sync(0xffffffffu, x0 != 0);
-    const unsigned b1 = __ballot_sync(0xffffffffu, x1 != 0);
-    const unsigned b2 = __ballot_sync(0xffffffffu, x2 != 0);
-    const unsigned b3 = __ballot_sync(0xffffffffu, x3 != 0);
-    const unsigned lt = (1u << lane) - 1;
-    const int before = __popc(b0 & lt) + __popc(b1 & lt) + __popc(b2 & lt) + __popc(b3 & lt);
-    const int total = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
-    unsigned long long o = off + pos + (unsigned)before;
-    const int m0 = q * 128 + 4 * lane;
-    if (x0) { crow[o] = (uint16_t)m0;       cval[o] = (V)x0; ++o; }
-    if (x1) { crow[o] = (uint16_t)(m0 + 1); cval[o] = (V)x1; ++o; }
-    if (x2) { crow[o] = (uint16_t)(m0 + 2); cval[o] = (V)x2; ++o; }
-    if (x3) { crow[o] = (uint16_t)(m0 + 3); cval[o] = (V)x3; }
-    pos += (unsigned)total;
-  }
-  return pos;
-}
-
-// Emission through shared memory (FP32 values): per 128-row slab, each lane
-// puts its nonzeros at their run positions in the slab's own accumulator
-// words (values) and in the warp's row staging `srow`, then the warp writes
-// the run with consecutive lanes on consecutive entries (one 64-byte row
-// store and one 128-byte value store per 32 entries), and zeroes the slab.
-template <int NQ>
-__device__ __forceinline__ unsigned emit_staged(int* acc, int (&regs)[4 * NQ], uint16_t* srow,
-                                                unsigned long long off,
-                                                uint16_t* __restrict__ crow,
-                                                float* __restrict__ cval) {
-  const int lane = threadIdx.x & 31;
-  int4* acc4 = reinterpret_cast<int4*>(acc);
-  unsigned pos = 0;
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    const int4 s = acc4[q * 32 + lane];
-    const int x0 = regs[4 * q] + s.x, x1 = regs[4 * q + 1] + s.y;
-    const int x2 = regs[4 * q + 2] + s.z, x3 = regs[4 * q + 3] + s.w;
-    regs[4 * q] = regs[4 * q + 1] = regs[4 * q + 2] = regs[4 * q + 3] = 0;
-    const unsigned b0 = __ballot_sync(0xffffffffu, x0 != 0);
-    const unsigned b1 = __ballot_sync(0xffffffffu, x1 != 0);
-    const unsigned b2 = __ballot_sync(0xffffffffu, x2 != 0);
-    const unsigned b3 = __ballot_sync(0xffffffffu, x3 != 0);
-    const unsigned lt = (1u << lane) - 1;
-    int p = __popc(b0 & lt) + __popc(b1 & lt) + __popc(b2 & lt) + __popc(b3 & lt);
-    const int total = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
-    float* sv = reinterpret_cast<float*>(acc) + q * 128;  // the slab's words, read above
-    const int m0 = q * 128 + 4 * lane;
-    __syncwarp();
-    if (x0) { sv[p] = (float)x0; srow[p] = (uint16_t)m0;       ++p; }
-    if (x1) { sv[p] = (float)x1; srow[p] = (uint16_t)(m0 + 1); ++p; }
-    if (x2) { sv[p] = (float)x2; srow[p] = (uint16_t)(m0 + 2); ++p; }
-    if (x3) { sv[p] = (float)x3; srow[p] = (uint16_t)(m0 + 3); }
-    __syncwarp();
-    const unsigned long long o = off + pos;
-    for (int j = lane; j < total; j += 32) {
-      crow[o + j] = srow[j];
-      cval[o + j] = sv[j];
-    }
-    __syncwarp();
-    acc4[q * 32 + lane] = make_int4(0, 0, 0, 0);
-    pos += (unsigned)total;
-  }
-  return pos;
 }
 
 template <typename V>
@@ -555,11 +506,97 @@ struct IsF32 { static constexpr bool v = false; };
 template <>
 struct IsF32<float> { static constexpr bool v = true; };
 
+// Emit one column from regs + acc (both left zero).  First the final values
+// (registers plus the warp's shared accumulator) and their nonzero count;
+// then the column is stored densely (every row's value, zeros included,
+// 16-byte stores straight from the registers; count | C_DENSE) when its
+// capacity holds all rows and it is dense enough that this writes no more
+// bytes than the sparse form (at least 2/3 nonzero with FP32 values, 4/5
+// with FP64); otherwise as ascending (row, value) pairs, each lane's
+// position from four ballots per 128-row slab, FP32 pairs staged in the
+// slab's own accumulator words and the warp's row staging `srow` so that
+// consecutive lanes store consecutive entries.
+template <typename V, int NQ>
+__device__ __forceinline__ unsigned emit_final(int* acc, int (&regs)[4 * NQ], uint16_t* srow,
+                                               unsigned long long off, unsigned long long cap,
+                                               int width, uint16_t* __restrict__ crow,
+                                               V* __restrict__ cval) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int4* acc4 = reinterpret_cast<int4*>(acc);
+  unsigned total = 0;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int4 s = acc4[q * 32 + lane];
+    acc4[q * 32 + lane] = make_int4(0, 0, 0, 0);
+    regs[4 * q] += s.x;
+    regs[4 * q + 1] += s.y;
+    regs[4 * q + 2] += s.z;
+    regs[4 * q + 3] += s.w;
+    total += __popc(__ballot_sync(FULL, regs[4 * q] != 0)) +
+             __popc(__ballot_sync(FULL, regs[4 * q + 1] != 0)) +
+             __popc(__ballot_sync(FULL, regs[4 * q + 2] != 0)) +
+             __popc(__ballot_sync(FULL, regs[4 * q + 3] != 0));
+  }
+  const unsigned long long wpad = (unsigned long long)((width + 3) & ~3);
+  const bool dense = cap >= wpad && (IsF32<V>::v ? 3ull * total >= 2ull * (unsigned)width
+                                                 : 5ull * total >= 4ull * (unsigned)width);
+  if (dense) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int m0 = q * 128 + 4 * lane;
+      if (m0 < width)
+        store4<V>(cval + off + m0, (V)regs[4 * q], (V)regs[4 * q + 1], (V)regs[4 * q + 2],
+                  (V)regs[4 * q + 3]);
+      regs[4 * q] = regs[4 * q + 1] = regs[4 * q + 2] = regs[4 * q + 3] = 0;
+    }
+    return total | C_DENSE;
+  }
+  __syncwarp();  // every lane's slab words are zero before any lane stages into them
+  unsigned pos = 0;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int x0 = regs[4 * q], x1 = regs[4 * q + 1], x2 = regs[4 * q + 2], x3 = regs[4 * q + 3];
+    regs[4 * q] = regs[4 * q + 1] = regs[4 * q + 2] = regs[4 * q + 3] = 0;
+    const unsigned b0 = __ballot_sync(FULL, x0 != 0);
+    const unsigned b1 = __ballot_sync(FULL, x1 != 0);
+    const unsigned b2 = __ballot_sync(FULL, x2 != 0);
+    const unsigned b3 = __ballot_sync(FULL, x3 != 0);
+    const unsigned lt = (1u << lane) - 1;
+    int p = __popc(b0 & lt) + __popc(b1 & lt) + __popc(b2 & lt) + __popc(b3 & lt);
+    const int tot = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+    const int m0 = q * 128 + 4 * lane;
+    if constexpr (IsF32<V>::v) {
+      float* sv = reinterpret_cast<float*>(acc) + q * 128;  // the slab's words (zero)
+      if (x0) { sv[p] = (float)x0; srow[p] = (uint16_t)m0;       ++p; }
+      if (x1) { sv[p] = (float)x1; srow[p] = (uint16_t)(m0 + 1); ++p; }
+      if (x2) { sv[p] = (float)x2; srow[p] = (uint16_t)(m0 + 2); ++p; }
+      if (x3) { sv[p] = (float)x3; srow[p] = (uint16_t)(m0 + 3); }
+      __syncwarp();
+      const unsigned long long o = off + pos;
+      for (int j = lane; j < tot; j += 32) {
+        crow[o + j] = srow[j];
+        cval[o + j] = sv[j];
+      }
+      __syncwarp();
+      acc4[q * 32 + lane] = make_int4(0, 0, 0, 0);
+    } else {
+      unsigned long long o = off + pos + (unsigned)p;
+      if (x0) { crow[o] = (uint16_t)m0;       cval[o] = (V)x0; ++o; }
+      if (x1) { crow[o] = (uint16_t)(m0 + 1); cval[o] = (V)x1; ++o; }
+      if (x2) { crow[o] = (uint16_t)(m0 + 2); cval[o] = (V)x2; ++o; }
+      if (x3) { crow[o] = (uint16_t)(m0 + 3); cval[o] = (V)x3; }
+    }
+    pos += (unsigned)tot;
+  }
+  return pos;
+}
+
 // One persistent kernel, one block per SM sharing the dense rows; a
 // warp per column, first the columns with at least CF_HEAVY_COL nonzeros
 // (`list`, the longest work items), then the other multi-nonzero columns
 // (`mlist`).  Each warp's accumulator is left zero by its emission.
-template <typename V, int NQ, int DB>
+template <typename V, int NQ, int DB, bool P4>
 __global__ void __launch_bounds__(CF_THREADS, 1)
     k_cf(CscDev X, CsrDev R, Dense dn, const int64_t* __restrict__ list,
          const unsigned* __restrict__ nlist, const int64_t* __restrict__ mlist,
@@ -621,6 +658,7 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
         todo &= todo - 1;
         const unsigned long long oe = __shfl_sync(0xffffffffu, o, e);
         const int64_t fe = __shfl_sync(0xffffffffu, f, e);
+        const unsigned long long ce = coff[fe + 1] - oe;  // capacity (read early)
         // issue the next column's first-chunk loads
         const int e2 = todo ? __ffs(todo) - 1 : 0;
         const unsigned long long na = __shfl_sync(0xffffffffu, xa, e2);
@@ -630,17 +668,14 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
           ni = __ldg(X.row + na + lane);
           nv = __ldg(X.val + na + lane);
         }
-        chunk_reg<NQ, DB>(R, dense4, acc, regs, cv, csl, crs, crl);
-        if (eb - ea > 32) accumulate_reg<NQ, DB>(X, R, dn, dense4, ea + 32, eb, acc, regs, 0, 1);
+        chunk_reg<NQ, DB, P4>(R, dense4, acc, regs, cv, csl, crs, crl);
+        if (eb - ea > 32)
+          accumulate_reg<NQ, DB, P4>(X, R, dn, dense4, ea + 32, eb, acc, regs, 0, 1);
         // the next column's row metadata, then this column's emission
         entry_meta(R, dn, ni, csl, crs, crl);
         cv = nv;
         __syncwarp();
-        unsigned n;
-        if constexpr (IsF32<V>::v)
-          n = emit_staged<NQ>(acc, regs, srow, oe, crow, cval);
-        else
-          n = emit_reg<V, NQ>(acc, regs, oe, crow, cval);
+        const unsigned n = emit_final<V, NQ>(acc, regs, srow, oe, ce, R.width, crow, cval);
         __syncwarp();
         if (lane == 0) ccnt[fe] = n;
         e = e2;
@@ -651,7 +686,7 @@ __global__ void __launch_bounds__(CF_THREADS, 1)
   }
 }
 
-template <typename V, int NQ, int DB>
+template <typename V, int NQ, int DB, bool P4>
 ctd_status cf_launch(const CscDev& X, const CsrDev& R, const Dense& dn,
                      const unsigned long long* coff, uint32_t* ccnt, uint16_t* crow, V* cval,
                      const int64_t* heavy, const unsigned* nheavy, const int64_t* multi,
@@ -660,18 +695,19 @@ ctd_status cf_launch(const CscDev& X, const CsrDev& R, const Dense& dn,
   const size_t smem = (size_t)dn.hmax * W * DB +
                       (size_t)(CF_THREADS / 32) * W * sizeof(int) +
                       (size_t)(CF_THREADS / 32) * 128 * sizeof(uint16_t);
-  CTD_TRY(allow_max_smem((const void*)k_cf<V, NQ, DB>));
+  CTD_TRY(allow_max_smem((const void*)k_cf<V, NQ, DB, P4>));
   int per_sm = 0;
-  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cf<V, NQ, DB>, CF_THREADS, smem));
+  CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cf<V, NQ, DB, P4>, CF_THREADS,
+                                                         smem));
   if (per_sm < 1) return fail(CTD_ENOTSUP, "C fill: shared memory for the dense rows too large");
-  CTD_LAUNCH((k_cf<V, NQ, DB>), (num_sms() * per_sm), (CF_THREADS), smem, st, X, R, dn, heavy,
+  CTD_LAUNCH((k_cf<V, NQ, DB, P4>), (num_sms() * per_sm), (CF_THREADS), smem, st, X, R, dn, heavy,
              nheavy, multi, nmulti, coff, ccnt, crow, cval, work);
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
 
 template <typename V>
-ctd_status cf_all(int nq, int db, const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
+ctd_status cf_all(int nq, int db, bool p4, const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
                   const Dense& dn,
                   const unsigned long long* coff, uint32_t* ccnt, uint16_t* crow, V* cval,
                   int positive, int64_t list_cap, Arena& a, cudaStream_t st) {
@@ -711,22 +747,23 @@ ctd_status cf_all(int nq, int db, const CscDev& X, int64_t n_cols, int64_t n_row
   {
     PhaseScope ph("c_fill_copy", st);
     CTD_LAUNCH(k_copy_flat<V>, (num_sms() * 8), (256), 0, st, X, rp, ip, icol, ival, P, single,
-               counts, coff, crow, cval);
+               counts, coff, ccnt, crow, cval);
   }
   PhaseScope ph("c_fill_multi", st);
-#define CF_GO(NQV, DBV)                                                                          \
-  return cf_launch<V, NQV, DBV>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, \
-                                counts + 2, work, st)
-#define CF_NQ(DBV)          \
-  switch (nq) {             \
-    case 1: CF_GO(1, DBV);  \
-    case 2: CF_GO(2, DBV);  \
-    case 4: CF_GO(4, DBV);  \
-    default: CF_GO(8, DBV); \
+#define CF_GO(NQV, DBV, P4V)                                                                  \
+  return cf_launch<V, NQV, DBV, P4V>(X, R, dn, coff, ccnt, crow, cval, heavy, counts + 1, multi, \
+                                     counts + 2, work, st)
+#define CF_NQ(DBV, P4V)          \
+  switch (nq) {                  \
+    case 1: CF_GO(1, DBV, P4V);  \
+    case 2: CF_GO(2, DBV, P4V);  \
+    case 4: CF_GO(4, DBV, P4V);  \
+    default: CF_GO(8, DBV, P4V); \
   }
-  if (db == 1) CF_NQ(1)
-  if (db == 2) CF_NQ(2)
-  CF_NQ(4)
+  if (db == 1 && p4) CF_NQ(1, true)
+  if (db == 1) CF_NQ(1, false)
+  if (db == 2) CF_NQ(2, false)
+  CF_NQ(4, false)
 #undef CF_NQ
 #undef CF_GO
 }
@@ -737,7 +774,7 @@ ctd_status cf_all(int nq, int db, const CscDev& X, int64_t n_cols, int64_t n_row
 // ||X||_F^2 < 2^31 and s~ <= 1024 (the caller checks).
 ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t nnz,
                              const CsrDev& R, const uint64_t* coff, uint32_t* ccnt,
-                             uint16_t* crow, void* cval, int fp32, int positive,
+                             uint16_t* crow, void* cval, int fp32, int positive, int x_int8,
                              cudaStream_t st) {
   if (R.nnz < 0) return fail(CTD_EINVAL, "C fill: the entry count of R is not set");
   const int width = R.width;
@@ -774,9 +811,9 @@ ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, in
   const unsigned long long* co = reinterpret_cast<const unsigned long long*>(coff);
   const int64_t list_cap = std::max<int64_t>(1, std::min(n_cols, nnz));
   if (fp32)
-    return cf_all<float>(nq, db, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<float*>(cval),
+    return cf_all<float>(nq, db, x_int8 != 0, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<float*>(cval),
                          positive, list_cap, a, st);
-  return cf_all<double>(nq, db, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<double*>(cval),
+  return cf_all<double>(nq, db, x_int8 != 0, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<double*>(cval),
                         positive, list_cap, a, st);
 }
 

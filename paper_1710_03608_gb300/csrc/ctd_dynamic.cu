@@ -488,10 +488,11 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
   }
   unsigned status = 0;
   int du = 0;
-  unsigned minkey = 0;
+  unsigned minkey[2] = {0, 0};
   uint64_t T = 0;
-  CTD_TRY(d2h(&minkey, M.minval, 1, st));
-  const int minval = decode_min(minkey);
+  CTD_TRY(d2h(minkey, M.minval, 2, st));
+  const int minval = decode_min(minkey[0]);
+  const bool x_int8 = minval >= -128 && decode_max(minkey[1]) <= 127;
   CTD_TRY(d2h(&status, M.status, 1, st));
   CTD_TRY(d2h(&du, d_count, 1, st));
   if (M.n_cols > 0) CTD_TRY(d2h(&T, M.cdf + (M.n_cols - 1), 1, st));
@@ -812,9 +813,9 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
     {
       PhaseScope ph("d_c_fill", st);
       CTD_TRY(launch_c_fill(M.csc(), M.n_cols, M.n_rows, M.nnz, R, rec.Coff, rec.Ccnt, rec.Crow, rec.Cval, fp32,
-                            D.all_positive, (uint64_t)D.max_T, st));
+                            D.all_positive, x_int8, (uint64_t)D.max_T, st));
     }
-    launch_sum_u32(rec.Ccnt, M.n_cols, d_nnzc, st);
+    launch_sum_u32(rec.Ccnt, M.n_cols, d_nnzc, st, C_COUNT);
     uint64_t nnzc = 0;
     CTD_TRY(d2h(&pu, d_pu, 1, st));
     CTD_TRY(d2h(&nnzc, d_nnzc, 1, st));
@@ -1171,8 +1172,14 @@ ctd_status dyn_C_columns(const ctd_factors* F, int64_t ncols, const int64_t* col
       CTD_TRY(d2h(&off, r.Coff + f, 1, st));
       CTD_TRY(d2h(&n, r.Ccnt + f, 1, st));
       CTD_TRY(sync(st));
+      // a densely stored column holds every row's value (see C_DENSE)
+      const bool dense = (n & C_DENSE) != 0;
+      if (dense) n = (uint32_t)v.size();
       std::vector<uint16_t> rows(n);
-      CTD_TRY(d2h(rows.data(), r.Crow + off, n, st));
+      if (dense)
+        for (uint32_t q = 0; q < n; ++q) rows[q] = (uint16_t)q;
+      else
+        CTD_TRY(d2h(rows.data(), r.Crow + off, n, st));
       if (F->precision == CTD_FP32_BULK) {
         std::vector<float> vals(n);
         CTD_TRY(d2h(vals.data(), static_cast<const float*>(r.Cval) + off, n, st));

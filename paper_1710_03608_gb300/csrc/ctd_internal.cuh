@@ -189,8 +189,9 @@ void launch_count(const CooDev& X, uint32_t* colcnt, uint32_t* rowcnt, unsigned*
 // K1b: squared column norms from the column-major layout: norm2[f] = the
 // sum of val[p]^2 over p in [colptr[f], colptr[f+1]) (saturating u64),
 // followed by their inclusive prefix sum cdf (the column distribution).
-// Also reduces the smallest value into *minkey as the order-preserving code
-// (unsigned)v ^ 2^31 (initialize to all ones; decode_min turns it back).
+// Also reduces the smallest value into minkey[0] as the order-preserving
+// code (unsigned)v ^ 2^31, and the largest into minkey[1] as the complement
+// of its code (both initialized to all ones; decode_min / decode_max).
 // A total at or past 2^63 sets DEV_OVERFLOW.
 void launch_sqnorms_cdf(const uint64_t* colptr, const int32_t* val, int64_t n_cols,
                         uint64_t* norm2, uint64_t* cdf, unsigned* minkey, uint64_t* tmp,
@@ -232,8 +233,9 @@ void launch_coo_scatter(const CooDev& X, uint32_t* cur, int32_t* csc_row, int32_
 ctd_status launch_sort_cols(const uint64_t* colptr, int64_t n_cols, int64_t nnz, int32_t* row,
                             int32_t* val, uint64_t* keys, Arena& A, cudaStream_t st);
 void launch_copy_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t st);
-// out[0] = sum of n u32 values (as u64).
-void launch_sum_u32(const uint32_t* in, int64_t n, uint64_t* out, cudaStream_t st);
+// out[0] = sum of n u32 values (as u64), each masked with `mask` first.
+void launch_sum_u32(const uint32_t* in, int64_t n, uint64_t* out, cudaStream_t st,
+                    uint32_t mask = 0xffffffffu);
 // out[c] = in[idx[c]] for c < *count.
 void launch_gather_i64(const int64_t* in, const int* idx, const int* count, int nmax,
                        int64_t* out, cudaStream_t st);
@@ -285,21 +287,30 @@ ctd_status launch_spmm_dense(const CscDev& X, const int64_t* fibers, const int* 
                              cudaStream_t st);
 
 // Sparse product C = R^T X_(alpha) over all n_cols columns.
-// bounds: ub[f] = min(width, sum of R row lengths over column f).
+// bounds: ub[f] = min(width, sum of R row lengths over column f) rounded up
+// to a multiple of 4 (the column's capacity; columns start 4-aligned).
+// Column f's storage at offset coff[f]: ccnt[f] & C_COUNT nonzeros; if
+// ccnt[f] & C_DENSE the column is stored densely (cval[coff[f] + m] for
+// rows m < width, zeros included; crow unused), else as ascending 16-bit
+// rows crow[coff[f] + q] with values cval[coff[f] + q].
+constexpr uint32_t C_DENSE = 0x80000000u;
+constexpr uint32_t C_COUNT = 0x7fffffffu;
 void launch_c_bounds(const CscDev& X, int64_t n_cols, const CsrDev& R, uint32_t* ub,
                      cudaStream_t st);
 // fill: column f's entries go to [coff[f], coff[f] + ccnt[f]) with rows
 // ascending (16-bit row indices).  Values stored as float (fp32 != 0) or
 // double.  R's rows must be sorted by column.  positive: every value of X
-// and R is > 0 (enables the one-nonzero copy path).
+// and R is > 0 (enables the one-nonzero copy path).  x_int8: every value of
+// X is in [-128, 127] (four products per instruction on int8 rows of R).
 ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t nnz,
                          const CsrDev& R, const uint64_t* coff, uint32_t* ccnt, uint16_t* crow,
-                         void* cval, int fp32, int positive, uint64_t sqnorm_X, cudaStream_t st);
+                         void* cval, int fp32, int positive, int x_int8, uint64_t sqnorm_X,
+                         cudaStream_t st);
 // The same with the longest rows of R dense in shared memory and register
 // accumulators (ctd_cfill.cu); requires sqnorm_X < 2^31 and width <= 1024.
 ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t nnz,
                              const CsrDev& R, const uint64_t* coff, uint32_t* ccnt,
-                             uint16_t* crow, void* cval, int fp32, int positive,
+                             uint16_t* crow, void* cval, int fp32, int positive, int x_int8,
                              cudaStream_t st);
 // list[0..count) = columns with >= minc nonzeros and a nonzero C bound
 void launch_list_columns(const uint64_t* colptr, const uint64_t* coff, int64_t n_cols,
@@ -422,7 +433,8 @@ struct Matricized {
   uint64_t* colptr = nullptr;   // [n_cols+1]
   int32_t* csc_row = nullptr;
   int32_t* csc_val = nullptr;
-  unsigned* minval = nullptr;   // code of the smallest value (see launch_sqnorms_cdf)
+  unsigned* minval = nullptr;   // [2] codes of the smallest and largest value (see
+                                // launch_sqnorms_cdf)
   unsigned* status = nullptr;
   uint64_t* tmp = nullptr;
   uint32_t* rowcnt = nullptr;   // [n_rows] nonzeros per row
@@ -440,6 +452,8 @@ ctd_status matricize_bucketed(const CooDev& X, Arena& A, cudaStream_t st, Matric
 // The smallest value from its order-preserving code (INT32_MAX when X has
 // no entries).
 inline int decode_min(unsigned key) { return (int)(key ^ 0x80000000u); }
+// The largest value from its code (INT32_MIN when X has no entries).
+inline int decode_max(unsigned key) { return (int)(~key ^ 0x80000000u); }
 // Algorithm 1's first steps: the column-major layout of X_(alpha), the
 // squared column norms and their CDF.  sort_cols: put each column's entries
 // in (row, value) order (CTD_DETERMINISTIC).  dist (optional): the arena

@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(MQ_THREADS, 2)
   // barrier above).
   const int32_t* vals = staged ? o_val : csc_val + s;
   unsigned long long acc = 0;
-  int vmin = INT32_MAX;
+  int vmin = INT32_MAX, vmax = INT32_MIN;
   for (int i = 0; i < SCAN_PER_WARP / 32; ++i) {
     const int c = warp * SCAN_PER_WARP + i * 32 + lane;
     const unsigned a = (c > 0 && c <= ncols) ? cnt[c - 1] : 0u;
@@ -349,6 +349,7 @@ __global__ void __launch_bounds__(MQ_THREADS, 2)
       if (q < lshort) {
         const int v = vals[a + q];
         vmin = min(vmin, v);
+        vmax = max(vmax, v);
         nrm = sat_add64(nrm, (unsigned long long)((long long)v * (long long)v));
       }
     unsigned longs = __ballot_sync(0xffffffffu, len > 32);
@@ -360,6 +361,7 @@ __global__ void __launch_bounds__(MQ_THREADS, 2)
       for (unsigned p = la + lane; p < lz; p += 32) {
         const int v = vals[p];
         vmin = min(vmin, v);
+        vmax = max(vmax, v);
         part = sat_add64(part, (unsigned long long)((long long)v * (long long)v));
       }
 #pragma unroll
@@ -375,13 +377,17 @@ __global__ void __launch_bounds__(MQ_THREADS, 2)
   for (int o = 16; o; o >>= 1) {
     acc = sat_add64(acc, __shfl_xor_sync(0xffffffffu, acc, o));
     vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+    vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
   }
   const int64_t ntiles = (n_cols + SCAN_TILE - 1) / SCAN_TILE;
   if (lane == 0) {
     segs[warp] = acc;
     const int64_t tile = (c0 / SCAN_TILE) + warp / SCAN_WARPS;
     if (tile < ntiles) warp_sums[tile * SCAN_WARPS + (warp % SCAN_WARPS)] = acc;
-    if (vmin != INT32_MAX) atomicMin(minkey, (unsigned)vmin ^ 0x80000000u);
+    if (vmin <= vmax) {
+      atomicMin(minkey, (unsigned)vmin ^ 0x80000000u);
+      atomicMin(minkey + 1, ~((unsigned)vmax ^ 0x80000000u));
+    }
   }
   __syncthreads();
   if (t < MQ_THREADS / 32 / SCAN_WARPS) {

@@ -97,7 +97,9 @@ __global__ void k_c_bounds(CscDev X, int64_t n_cols, CsrDev R, unsigned* __restr
       const int i = __ldg(X.row + p);
       s += __ldg(rp + i + 1) - __ldg(rp + i);
     }
-    ub[f] = (unsigned)min(s, (unsigned long long)R.width);
+    // capacity: the bound rounded up to a multiple of 4, so that every
+    // column of C starts on a 16-byte boundary of its value array
+    ub[f] = ((unsigned)min(s, (unsigned long long)R.width) + 3u) & ~3u;
   }
 }
 
@@ -408,7 +410,8 @@ static ctd_status c_fill_impl(const CscDev& X, int64_t n_cols, const CsrDev& R,
 
 ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t nnz,
                          const CsrDev& R, const uint64_t* coff, uint32_t* ccnt, uint16_t* crow,
-                         void* cval, int fp32, int positive, uint64_t sqnorm_X, cudaStream_t st) {
+                         void* cval, int fp32, int positive, int x_int8, uint64_t sqnorm_X,
+                         cudaStream_t st) {
   if (n_cols <= 0) return CTD_OK;
   if (R.width <= 0) {
     CTD_CUDA(cudaMemsetAsync(ccnt, 0, n_cols * sizeof(uint32_t), st));
@@ -419,7 +422,7 @@ ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_
   // accumulators cover the width: dense long rows + registers
   if (sqnorm_X < (1ull << 31) && R.width <= 1024)
     return c_fill_dense_rows(X, n_cols, n_rows, nnz, R, coff, ccnt, crow, cval, fp32, positive,
-                             st);
+                             x_int8, st);
   unsigned long long* work;
   int64_t* heavy;
   unsigned* nheavy;

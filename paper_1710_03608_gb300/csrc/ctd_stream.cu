@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32)
   const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)warp * SCAN_PER_WARP;
   const unsigned long long end_all = colptr[n];
   unsigned long long acc = 0;
-  int vmin = INT32_MAX;
+  int vmin = INT32_MAX, vmax = INT32_MIN;
   unsigned long long a_next = base + lane < n ? colptr[base + lane] : end_all;
   for (int it = 0; it < SCAN_PER_WARP / 32; ++it) {
     const int64_t f = base + it * 32 + lane;
@@ -309,6 +309,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32)
       if (t < lshort) {
         const int v = __ldg(val + a + t);
         vmin = min(vmin, v);
+        vmax = max(vmax, v);
         mine = sat_add(mine, (unsigned long long)((long long)v * (long long)v));
       }
     unsigned longs = __ballot_sync(FULL, len > 32);
@@ -320,6 +321,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32)
       for (unsigned long long p = la + lane; p < lb; p += 32) {
         const int v = __ldg(val + p);
         vmin = min(vmin, v);
+        vmax = max(vmax, v);
         part = sat_add(part, (unsigned long long)((long long)v * (long long)v));
       }
       part = warp_sat_sum(part);
@@ -329,11 +331,17 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32)
     acc = sat_add(acc, mine);
   }
   acc = warp_sat_sum(acc);
-  for (int o = 16; o; o >>= 1) vmin = min(vmin, __shfl_xor_sync(FULL, vmin, o));
+  for (int o = 16; o; o >>= 1) {
+    vmin = min(vmin, __shfl_xor_sync(FULL, vmin, o));
+    vmax = max(vmax, __shfl_xor_sync(FULL, vmax, o));
+  }
   if (lane == 0) {
     ws[warp] = acc;
     warp_sums[(int64_t)blockIdx.x * SCAN_WARPS + warp] = acc;
-    if (vmin != INT32_MAX) atomicMin(minkey, (unsigned)vmin ^ 0x80000000u);
+    if (vmin <= vmax) {
+      atomicMin(minkey, (unsigned)vmin ^ 0x80000000u);
+      atomicMin(minkey + 1, ~((unsigned)vmax ^ 0x80000000u));
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -864,12 +872,13 @@ ctd_status build_csr_from_csc(const uint64_t* colptr, const int32_t* row, const 
   return CTD_OK;
 }
 
-__global__ void k_sum_u32(const unsigned* __restrict__ in, int64_t n, unsigned long long* out) {
+__global__ void k_sum_u32(const unsigned* __restrict__ in, int64_t n, unsigned long long* out,
+                          unsigned mask) {
   __shared__ unsigned long long part[32];
   unsigned long long acc = 0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
-    acc += in[e];
+    acc += in[e] & mask;
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -880,11 +889,12 @@ __global__ void k_sum_u32(const unsigned* __restrict__ in, int64_t n, unsigned l
   }
 }
 
-void launch_sum_u32(const uint32_t* in, int64_t n, uint64_t* out, cudaStream_t st) {
+void launch_sum_u32(const uint32_t* in, int64_t n, uint64_t* out, cudaStream_t st,
+                    uint32_t mask) {
   cudaMemsetAsync(out, 0, sizeof(uint64_t), st);
   if (n <= 0) return;
-  CTD_LAUNCH(k_sum_u32, (grid_for(n, 1024, (int64_t)num_sms() * 2)), (1024), 0, st, 
-      in, n, reinterpret_cast<unsigned long long*>(out));
+  CTD_LAUNCH(k_sum_u32, (grid_for(n, 1024, (int64_t)num_sms() * 2)), (1024), 0, st,
+             in, n, reinterpret_cast<unsigned long long*>(out), mask);
 }
 
 __global__ void k_gather_i64(const int64_t* __restrict__ in, const int* __restrict__ idx,

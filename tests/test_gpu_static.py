@@ -176,14 +176,26 @@ def test_deterministic_flag_parity():
 
 
 @pytest.mark.parametrize("case", ["int64_sums", "wide_registers", "wider_than_registers",
-                                  "int16_rows", "int32_rows"])
+                                  "int16_rows", "int32_rows", "int8_rows_wide_x"])
 def test_c_fill_paths(case):
     """Each C = R^T X path against the oracle: partial sums beyond int32
     (||X||_F^2 >= 2^31), s~ in (512, 1024] (the widest register layout),
-    s~ > 1024 (shared-memory accumulators only), and the dense rows of R
-    stored as int16 (max |R| in (127, 32767]) or int32 (larger), the int8
-    layout being the default of the small-count cases."""
-    if case == "int64_sums":
+    s~ > 1024 (shared-memory accumulators only), the dense rows of R
+    stored as int16 (max |R| in (127, 32767]) or int32 (larger), and int8
+    rows while X has a value outside int8 (so the four-products-per-
+    instruction form is off); the int8 layout with X in int8 is the default
+    of the small-count cases."""
+    if case == "int8_rows_wide_x":
+        # fiber 0 = 100 e_0 is kept first; fiber 1 = 200 e_0 is parallel to it and
+        # skipped, so R stays within int8 while X holds 200
+        base = synth.tiny((60, 40, 10), 3000, seed=37, vmax=5)
+        keep = ~((base.k == 0) & (base.j <= 1))
+        coo = synth.Coo3(base.dims, np.concatenate([base.i[keep], [0, 0]]),
+                         np.concatenate([base.j[keep], [0, 1]]),
+                         np.concatenate([base.k[keep], [0, 0]]),
+                         np.concatenate([base.val[keep], [100, 200]]))
+        s = 2000
+    elif case == "int64_sums":
         coo, s = synth.tiny((60, 40, 10), 3000, seed=31, vmax=100_000), 300
     elif case == "int16_rows":
         coo, s = synth.tiny((60, 40, 10), 3000, seed=34, vmax=300), 300
@@ -205,6 +217,9 @@ def test_c_fill_paths(case):
         assert (127 < top <= 32767) if case == "int16_rows" else top > 32767
     elif case == "wide_registers":
         assert 512 < kept <= 1024
+    elif case == "int8_rows_wide_x":
+        assert np.abs(ref.R).max() <= 127 < np.abs(coo.val).max()
+        assert 1 not in ref.fibers
     else:
         assert kept > 1024
     check(F, ref, 1e-6, 0, err_ref=O.projection_error(ref.X, ref.R))
