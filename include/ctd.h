@@ -340,6 +340,35 @@ CTD_API ctd_status ctd_sample_noalloc(const ctd_coo3* X, int alpha, int64_t s, u
                                       int64_t* draws, int64_t* unique, int* n_unique,
                                       void* stream);
 
+/*
+ * ctd_set_allocator -- where the library's device memory comes from (the
+ * boundary's memory convention: the factors of Algorithms 1 and 2 and
+ * every scratch array of a call).  The paper runs on a CPU and says
+ * nothing of it.  With a hook set, every device allocation of the library
+ * is alloc(bytes, stream) and is returned with release(ptr, stream); with
+ * none (the default, or both NULL) the library uses the device's
+ * stream-ordered pool (cudaMallocAsync / cudaFreeAsync).
+ *  alloc    returns device memory usable by work enqueued on `stream` from
+ *           now on, at least 256-byte aligned, or NULL (the call then
+ *           returns CTD_ENOMEM and releases what it held)
+ *  release  takes back a block alloc made, in stream order: work already
+ *           enqueued on `stream` may still use it, work enqueued later on
+ *           that stream may reuse it (the contract of a stream-ordered or
+ *           stream-aware caching allocator, e.g. PyTorch's)
+ * Both functions may be called from any thread that calls the library and
+ * from the library's worker threads (batched and serving forms), with the
+ * block's device current.  A block goes back to the functions that made
+ * it, even if the hook changed in between.  Process-wide; set it while no
+ * call of the library is running.  CTD_EINVAL: exactly one of the two NULL.
+ */
+typedef void* (*ctd_alloc_fn)(size_t bytes, void* stream);
+typedef void (*ctd_release_fn)(void* ptr, void* stream);
+CTD_API ctd_status ctd_set_allocator(ctd_alloc_fn alloc, ctd_release_fn release);
+
+/* Device bytes the library holds right now (factors and scratch, from the
+ * hook or the pool), as it requested them. */
+CTD_API ctd_status ctd_allocated_bytes(size_t* bytes);
+
 /* Diagnostics (no counterpart in the paper).  ctd_profile(1) clears and
  * starts per-phase device timing: each phase of a call is bracketed by a
  * CUDA event pair on the call's stream.  ctd_profile_report waits for the

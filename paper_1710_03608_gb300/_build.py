@@ -15,6 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libctd.so")
+TORCH_SHIM = os.path.join(HERE, "libctd_torch.so")
+TORCH_SHIM_SRC = os.path.join(CSRC, "ctd_torch_alloc.cpp")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 SOURCES = ["ctd_stream.cu", "ctd_sample.cu", "ctd_spmm.cu", "ctd_dense.cu", "ctd_filter.cu", "ctd_api.cu",
            "ctd_dynamic.cu", "ctd_noalloc.cu", "ctd_batch.cu",
@@ -34,7 +36,7 @@ def _flags(extra=()):
 
 
 def _deps_mtime() -> float:
-    paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh"))]
     paths += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     paths.append(__file__)
     return max(os.path.getmtime(p) for p in paths)
@@ -67,6 +69,30 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
     return LIB
+
+
+def build_torch_shim(force: bool = False) -> str:
+    """Build libctd_torch.so (PyTorch's caching allocator as the library's
+    allocator hook) against the installed torch's headers; return its path."""
+    if (not force and os.path.exists(TORCH_SHIM)
+            and os.path.getmtime(TORCH_SHIM) >= max(os.path.getmtime(TORCH_SHIM_SRC),
+                                                    os.path.getmtime(__file__))):
+        return TORCH_SHIM
+    import torch
+    from torch.utils import cpp_extension
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "include")
+    incs = [*cpp_extension.include_paths(), cuda_inc]
+    libdir = os.path.join(os.path.dirname(torch.__file__), "lib")
+    abi = int(torch._C._GLIBCXX_USE_CXX11_ABI)
+    tmp = TORCH_SHIM + ".tmp"
+    cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-fvisibility=hidden",
+           f"-D_GLIBCXX_USE_CXX11_ABI={abi}", *[f"-I{p}" for p in incs], TORCH_SHIM_SRC,
+           "-o", tmp, f"-L{libdir}", "-lc10_cuda", "-lc10", f"-Wl,-rpath,{libdir}"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"torch allocator shim failed to build:\n{r.stderr}")
+    os.replace(tmp, TORCH_SHIM)
+    return TORCH_SHIM
 
 
 if __name__ == "__main__":

@@ -4,8 +4,9 @@
 #include <cstring>
 #include <memory>
 #include <mutex>
-#include <set>
 #include <numeric>
+#include <set>
+#include <unordered_map>
 
 #include "ctd_internal.cuh"
 
@@ -93,8 +94,37 @@ ctd_status allow_max_smem(const void* fn) {
 // -1 disables.
 static std::atomic<long long> g_alloc_fail_after{-1};
 
+// The allocator hook (ctd_set_allocator) and the library's live device
+// bytes.  Every live allocation is recorded with its size and the release
+// function of the hook that made it (none: the library's pool), so a block
+// goes back to whoever made it even if the hook changes in between, and
+// live_bytes() counts what the library holds.
+namespace {
+struct AllocHook {
+  ctd_alloc_fn alloc = nullptr;
+  ctd_release_fn release = nullptr;
+};
+struct LiveBlock {
+  size_t bytes;
+  ctd_release_fn release;
+};
+std::mutex g_hook_mu;
+AllocHook g_hook;
+std::unordered_map<void*, LiveBlock> g_live;
+size_t g_live_bytes = 0;
+}  // namespace
+
+size_t live_bytes() {
+  std::lock_guard<std::mutex> lk(g_hook_mu);
+  return g_live_bytes;
+}
+
+bool allocator_hooked() {
+  std::lock_guard<std::mutex> lk(g_hook_mu);
+  return g_hook.alloc != nullptr;
+}
+
 ctd_status dalloc(void** p, size_t bytes, cudaStream_t st) {
-  init_pool_once();
   const long long fa = g_alloc_fail_after.load();
   if (fa >= 0) {
     if (fa == 0) {
@@ -103,18 +133,49 @@ ctd_status dalloc(void** p, size_t bytes, cudaStream_t st) {
     }
     g_alloc_fail_after.fetch_sub(1);
   }
-  cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 1, st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    *p = nullptr;
-    return fail(CTD_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) +
-                                " bytes failed: " + cudaGetErrorString(e));
+  const size_t nb = bytes ? bytes : 1;
+  AllocHook h;
+  {
+    std::lock_guard<std::mutex> lk(g_hook_mu);
+    h = g_hook;
   }
+  if (h.alloc) {
+    *p = h.alloc(nb, st);
+    if (!*p)
+      return fail(CTD_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) +
+                                  " bytes refused by the allocator hook");
+  } else {
+    init_pool_once();
+    cudaError_t e = cudaMallocAsync(p, nb, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return fail(CTD_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) +
+                                  " bytes failed: " + cudaGetErrorString(e));
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_hook_mu);
+  g_live[*p] = LiveBlock{nb, h.alloc ? h.release : nullptr};
+  g_live_bytes += nb;
   return CTD_OK;
 }
 
 void dfree(void* p, cudaStream_t st) {
-  if (p) cudaFreeAsync(p, st);
+  if (!p) return;
+  ctd_release_fn rel = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_hook_mu);
+    auto it = g_live.find(p);
+    if (it != g_live.end()) {
+      rel = it->second.release;
+      g_live_bytes -= it->second.bytes;
+      g_live.erase(it);
+    }
+  }
+  if (rel)
+    rel(p, st);
+  else
+    cudaFreeAsync(p, st);
 }
 
 ctd_status d2h_bytes(void* host, const void* dev, size_t bytes, cudaStream_t st) {
@@ -774,6 +835,21 @@ extern "C" void ctd_free(ctd_factors* F) {
   if (!F) return;
   cudaStreamSynchronize(F->stream);
   delete F;
+}
+
+extern "C" ctd_status ctd_set_allocator(ctd_alloc_fn alloc, ctd_release_fn release) {
+  if ((alloc == nullptr) != (release == nullptr))
+    return fail(CTD_EINVAL, "give both functions, or neither (the library's own pool)");
+  std::lock_guard<std::mutex> lk(g_hook_mu);
+  g_hook.alloc = alloc;
+  g_hook.release = release;
+  return CTD_OK;
+}
+
+extern "C" ctd_status ctd_allocated_bytes(size_t* bytes) {
+  if (!bytes) return fail(CTD_EINVAL, "NULL argument");
+  *bytes = live_bytes();
+  return CTD_OK;
 }
 
 extern "C" ctd_status ctd_profile(int enable) {

@@ -82,6 +82,9 @@ ctd_status status_from_device(unsigned word);
 // ---------------------------------------------------------------------------
 ctd_status dalloc(void** p, size_t bytes, cudaStream_t st);
 void dfree(void* p, cudaStream_t st);
+// Device bytes the library holds now, and whether an allocator hook is set.
+size_t live_bytes();
+bool allocator_hooked();
 
 template <typename T>
 ctd_status dalloc_n(T** p, size_t n, cudaStream_t st) {

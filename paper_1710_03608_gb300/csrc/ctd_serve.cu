@@ -7,9 +7,14 @@
 // whose stream is idle, as soon as a worker frees up: steps of different
 // streams overlap on the device, and a request that arrives while others
 // run is admitted without waiting for a batch boundary.  Admission also
-// checks device memory: a step starts only if the free memory, less the
-// estimates of the steps already running, covers its own estimate (at
-// least one step always runs, so the queue cannot stall).
+// checks device memory: a step starts only if the memory available to the
+// library, less the estimates of the steps already running, covers its own
+// estimate (at least one step always runs, so the queue cannot stall).
+// Available: a fraction of the device's free memory with the library's own
+// pool; with an allocator hook (ctd_set_allocator), whose cache keeps what
+// the library frees out of the device's free count, a budget fixed at
+// creation (that fraction of free memory plus what the library then held)
+// less the bytes the library holds now.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -43,6 +48,7 @@ struct ctd_server {
   int64_t d = 0;
   double eps = 0.0;
   double mem_fraction = 0.9;
+  size_t budget = 0;   // with an allocator hook: bytes the library may hold
   int dev = 0;
   std::vector<ctd_factors*> states;
   std::vector<std::deque<int64_t>> queue;   // tickets per stream
@@ -86,7 +92,11 @@ void worker(ctd_server* S, int w) {
         }
         if (best >= 0) {
           Request& r = S->req[best];
-          const size_t avail = (size_t)((double)free_b * S->mem_fraction);
+          size_t avail = (size_t)((double)free_b * S->mem_fraction);
+          if (allocator_hooked()) {
+            const size_t held = live_bytes();
+            avail = S->budget > held ? S->budget - held : 0;
+          }
           const bool fits = S->running == 0 || S->running_bytes + r.estimate <= avail;
           if (fits) {
             ticket = best;
@@ -141,6 +151,11 @@ extern "C" ctd_status ctd_server_create(int n_streams, const int64_t dims2[2], i
   S->eps = eps;
   S->mem_fraction = mem_fraction;
   cudaGetDevice(&S->dev);
+  {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    S->budget = (size_t)(mem_fraction * (double)(free_b + live_bytes()));
+  }
   S->states.assign(n_streams, nullptr);
   S->queue.resize(n_streams);
   S->busy.assign(n_streams, 0);

@@ -15,6 +15,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libctd.so")
+TORCH_SHIM_PATH = os.path.join(_HERE, "libctd_torch.so")
 
 CTD_FP64 = 0
 CTD_FP32_BULK = 1
@@ -35,7 +36,7 @@ EXPORTED = ["ctd_static", "ctd_dynamic_create", "ctd_dynamic_step", "ctd_error",
             "ctd_version", "ctd_profile", "ctd_profile_report", "ctd_sample_noalloc", "ctd_static_batched", "ctd_server_create", "ctd_server_submit",
             "ctd_server_wait", "ctd_server_result", "ctd_server_state", "ctd_server_free",
             "ctd_ddos_candidates", "ctd_dynamic_from_static", "ctd_fault_inject_alloc",
-            "ctd_selftest_bounded_wait"]
+            "ctd_selftest_bounded_wait", "ctd_set_allocator", "ctd_allocated_bytes"]
 
 
 class CtdError(RuntimeError):
@@ -101,6 +102,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ctd_dynamic_from_static": [P, U64, C.c_uint, P, C.POINTER(P)],
         "ctd_fault_inject_alloc": [I64],
         "ctd_selftest_bounded_wait": [I64, P],
+        "ctd_set_allocator": [P, P],
+        "ctd_allocated_bytes": [C.POINTER(C.c_size_t)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -113,7 +116,43 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.ctd_last_error.restype = C.c_char_p
     lib.ctd_version.restype = C.c_char_p
     _lib = lib
+    if os.environ.get("CTD_ALLOCATOR", "torch") == "torch" and os.path.exists(TORCH_SHIM_PATH):
+        import torch
+        if torch.cuda.is_available():
+            use_torch_allocator(True)
     return lib
+
+
+_shim: Optional[C.CDLL] = None
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Route every device allocation of the library through PyTorch's CUDA
+    caching allocator (enable=True; the default once the allocator shim is
+    built), or back to the library's own stream-ordered pool (False).  Set
+    CTD_ALLOCATOR=pool in the environment to keep the pool at load time."""
+    global _shim
+    lib = load()
+    if not enable:
+        _check(lib.ctd_set_allocator(None, None))
+        return
+    import torch
+    torch.cuda.init()
+    if _shim is None:
+        if not os.path.exists(TORCH_SHIM_PATH):
+            raise RuntimeError(f"allocator shim not built: {TORCH_SHIM_PATH} is missing "
+                               "(run __graft_entry__.build())")
+        _shim = C.CDLL(TORCH_SHIM_PATH)
+    alloc = C.cast(_shim.ctd_torch_alloc, C.c_void_p)
+    release = C.cast(_shim.ctd_torch_release, C.c_void_p)
+    _check(lib.ctd_set_allocator(alloc, release))
+
+
+def allocated_bytes() -> int:
+    """Device bytes the library holds now (factors and scratch)."""
+    n = C.c_size_t()
+    _check(load().ctd_allocated_bytes(C.byref(n)))
+    return n.value
 
 
 def _check(code: int):

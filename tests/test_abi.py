@@ -58,6 +58,9 @@ C_PROGRAM = r"""
 #include <string.h>
 #include "ctd.h"
 
+static void* my_alloc(size_t bytes, void* stream) { (void)bytes; (void)stream; return NULL; }
+static void my_release(void* p, void* stream) { (void)p; (void)stream; }
+
 int main(void) {
   const char* v = ctd_version();
   if (!v || strncmp(v, "ctd-gb300", 9) != 0) return 2;
@@ -68,6 +71,14 @@ int main(void) {
   int32_t i[1] = {0}, j[1] = {0}, k[1] = {0}, val[1] = {1};
   ctd_coo3 X = {{1, 1, 1}, 1, i, j, k, val, CTD_MEM_HOST};
   if (ctd_static(&X, 4, 10, 1e-6, 0, CTD_FP64, 0, NULL, &F) != CTD_EINVAL || F) return 5;
+  /* the allocator hook takes both functions or neither */
+  if (ctd_set_allocator(my_alloc, NULL) != CTD_EINVAL) return 6;
+  if (ctd_set_allocator(NULL, my_release) != CTD_EINVAL) return 7;
+  if (ctd_set_allocator(my_alloc, my_release) != CTD_OK) return 8;
+  if (ctd_set_allocator(NULL, NULL) != CTD_OK) return 9;
+  size_t held = 1;
+  if (ctd_allocated_bytes(&held) != CTD_OK || held != 0) return 10;
+  if (ctd_allocated_bytes(NULL) != CTD_EINVAL) return 11;
   printf("%s\n", v);
   return 0;
 }
