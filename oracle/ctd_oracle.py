@@ -18,6 +18,7 @@ What each function follows:
   ctd_d_step             Algorithm 2, step by step, FP64
   c_columns              Algorithm 1's C / Eq. (3), exact int64
   relative_error_dense   Eq. (error), brute force on small inputs
+  memory_usage           Eq. (memoryEff): (nnz(C) + nnz(U) + nnz(R)) / nnz(X)
   projection_error       Lemma 3.2 (Eqs. 4-7): error = ||X - R R^+ X||^2/||X||^2
   ddos_candidates        Section 5, detection rule on R's fibers
   dynamic_state_from_static   Section 4's CTD-D setting: CTD-S factors of the
@@ -373,6 +374,20 @@ def relative_error_dense(X: Matricized, R: np.ndarray, U: np.ndarray, C) -> floa
     if den == 0.0:
         return 0.0
     return float(np.sum((Xt - Xd) ** 2)) / den
+
+
+def memory_usage(X: Matricized, R: np.ndarray, U: np.ndarray, C) -> float:
+    """Eq. (memoryEff), Section 4 (Experimental Settings): the memory of the
+    factors relative to the tensor's, counted in nonzero entries,
+    (nnz(C) + nnz(U) + nnz(R)) / nnz(X).  C, R and X are exact integers; an
+    entry of the floating-point U counts when its magnitude exceeds 1e-12 of
+    U's largest (reading A27: a zero of the exact inverse may carry rounding
+    noise)."""
+    nnz_x = int(np.count_nonzero(X.vals))
+    nnz_c = int(C.count_nonzero()) if hasattr(C, "count_nonzero") else int(np.count_nonzero(C))
+    U = np.asarray(U, dtype=np.float64)
+    nnz_u = int(np.count_nonzero(np.abs(U) > 1e-12 * np.abs(U).max())) if U.size else 0
+    return (nnz_c + nnz_u + int(np.count_nonzero(R))) / nnz_x
 
 
 def projection_error(X: Matricized, R: np.ndarray, chunk: int = 1 << 17) -> float:

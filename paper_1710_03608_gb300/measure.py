@@ -36,6 +36,19 @@ def _sync():
     torch.cuda.synchronize()
 
 
+def memory_usage(F) -> float:
+    """Eq. (memoryEff) of the paper's Section 4 for CTD-S factors:
+    (nnz(C) + nnz(U) + nnz(R)) / nnz(X), nonzero entries counted; an entry
+    of U counts when its magnitude exceeds 1e-12 of U's largest (U is read
+    back to count)."""
+    sz = F.sizes()
+    nnz_u = 0
+    if sz.s_kept:
+        U = np.abs(F.U())
+        nnz_u = int(np.count_nonzero(U > 1e-12 * U.max()))
+    return (sz.nnz_C + nnz_u + sz.nnz_R) / max(sz.nnz_X, 1)
+
+
 # ---------------------------------------------------------------------------
 # autotuner: worker streams for the batched form
 # ---------------------------------------------------------------------------
@@ -47,9 +60,9 @@ def tuned_workers(default: int = 8) -> int:
         return default
 
 
-def autotune_workers(Xs, s, seeds, candidates=(2, 4, 8, 12, 16, 24)) -> dict:
+def autotune_workers(Xs, s, seeds, candidates=(2, 4, 8, 12, 16, 24), save: bool = True) -> dict:
     """Time ctd_static_batched on the given tensors for each worker count;
-    keep the fastest in the tuning file."""
+    keep the fastest in the tuning file (when `save`)."""
     times = {}
     for w in candidates:
         for _ in range(2):
@@ -61,9 +74,10 @@ def autotune_workers(Xs, s, seeds, candidates=(2, 4, 8, 12, 16, 24)) -> dict:
             del Fs
         times[w] = dt
     best = min(times, key=times.get)
-    os.makedirs(os.path.dirname(TUNE_FILE), exist_ok=True)
-    with open(TUNE_FILE, "w") as f:
-        json.dump({"batched_workers": best, "times_s": times}, f)
+    if save:
+        os.makedirs(os.path.dirname(TUNE_FILE), exist_ok=True)
+        with open(TUNE_FILE, "w") as f:
+            json.dump({"batched_workers": best, "times_s": times}, f)
     return {"best": best, "times_s": times}
 
 
@@ -248,7 +262,8 @@ def sweep(args):
     Poisson(3)+1 counts) and on the 10^7-nonzero traffic tensor. Per s: the
     relative error, the kept count s~ (bounded by the rank of X_(1), at most
     77 on the first tensor), the device time of a call, and the memory of
-    the result (R as CSC, U dense, C as CSC with 16-bit rows)."""
+    the result: the paper's memory usage (Eq. memoryEff) and the bytes of
+    R as CSC, U dense, C as CSC with 16-bit rows."""
     tensors = [("haggle-shaped 77x274x1567, 27972 nnz",
                 synth.traffic((77, 274, 1567), 27972, 1.2, 1.2, "poisson1", 2001, 3.0)),
                ("traffic 10000x10000x1000, 1e7 nnz", synth.traffic_10m())]
@@ -274,6 +289,7 @@ def sweep(args):
                 if rep == 0:
                     row = {"s": s_, "s_unique": int(sz.s_unique), "s_kept": int(sz.s_kept),
                            "rel_error": e, "nnz_R": int(sz.nnz_R), "nnz_C": int(sz.nnz_C),
+                           "memory_usage": memory_usage(F),
                            "memory_bytes": int(12 * sz.nnz_R + 8 * (sz.s_kept + 1)
                                                + 8 * sz.s_kept ** 2 + 6 * sz.nnz_C
                                                + 12 * (sz.n_cols + 1))}

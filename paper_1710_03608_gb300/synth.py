@@ -145,6 +145,68 @@ def traffic(dims, nnz: int, a_src: float, a_dst: float, values: str, seed: int,
     return _finish(rng, dims, ii, jj, kk, vals)
 
 
+def traffic_device(dims, nnz: int, a_src: float, a_dst: float, values: str, vparam: float,
+                   seed: int, device: str = "cuda"):
+    """The law of `traffic` drawn on the GPU (for timing runs of workloads
+    too large to draw on the host in reasonable time).
+
+    Same rules as above -- Zipf ids through a seeded rank -> id permutation,
+    uniform time, the first `nnz` distinct coordinates of the draw stream,
+    Geometric or Poisson+1 counts, a seeded shuffle -- with draws from a
+    seeded torch generator on `device`, so the tensors follow the same
+    distributions as `traffic`'s but are not the same draws.  Returns int32
+    tensors (i, j, k, val) on the device."""
+    import torch
+    I, J, K = (int(d) for d in dims)
+    if nnz > I * J * K:
+        raise ValueError("more nonzeros than cells")
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+
+    def zipf(n, a):
+        w = torch.arange(1, n + 1, device=device, dtype=torch.float64).pow(-a)
+        cdf = torch.cumsum(w, 0)
+        cdf = cdf / cdf[-1]
+        perm = torch.randperm(n, generator=g, device=device)
+
+        def draw(m):
+            u = torch.rand(m, generator=g, device=device, dtype=torch.float64)
+            return perm[torch.searchsorted(cdf, u, right=True).clamp_(max=n - 1)]
+        return draw
+
+    di, dj = zipf(I, a_src), zipf(J, a_dst)
+    keys = torch.empty(0, dtype=torch.int64, device=device)
+    batch = int(nnz * 1.1) + 16
+    for _ in range(64):
+        ii = di(batch)
+        jj = dj(batch)
+        kk = torch.randint(0, K, (batch,), generator=g, device=device)
+        keys = torch.cat([keys, ii + I * (jj + J * kk)])
+        uniq, inv = torch.unique(keys, sorted=True, return_inverse=True)
+        if uniq.numel() >= nnz:
+            break
+        # draws are cheap here: ask for plenty more than the shortfall
+        batch = max(8 * (nnz - uniq.numel()) + 1024, batch)
+    else:  # pragma: no cover - only for degenerate laws
+        raise RuntimeError("could not draw enough distinct coordinates")
+    first = torch.full((uniq.numel(),), keys.numel(), dtype=torch.int64, device=device)
+    first.scatter_reduce_(0, inv, torch.arange(keys.numel(), device=device), reduce="amin")
+    key = uniq[torch.argsort(first)[:nnz]]
+    del keys, inv, first, uniq
+    if values == "geometric":
+        v = torch.empty(nnz, device=device, dtype=torch.float64).geometric_(vparam, generator=g)
+    elif values == "poisson1":
+        v = torch.poisson(torch.full((nnz,), float(vparam), device=device), generator=g) + 1
+    else:
+        raise ValueError(values)
+    order = torch.randperm(nnz, generator=g, device=device)
+    key = key[order]
+    v = v[order]
+    ii = (key % I).to(torch.int32)
+    rest = key // I
+    return ii, (rest % J).to(torch.int32), (rest // J).to(torch.int32), v.to(torch.int32)
+
+
 def _values(rng, kind: str, p: float, n: int) -> np.ndarray:
     if kind == "geometric":
         return rng.geometric(p, size=n)

@@ -128,6 +128,16 @@ def test_bucketed_matricize(kind):
     check(F, ref, 1e-6, 0, err_ref=O.projection_error(ref.X, ref.R))
 
 
+def test_memory_usage_matches_oracle():
+    """Eq. (memoryEff) from the library's factors equals the oracle's count."""
+    from paper_1710_03608_gb300 import measure
+    coo = synth.small_uniform()
+    F = run(coo, 1, 50, 1e-6, 0, 0)
+    ref = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, 1, 50, 1e-6, 0)
+    want = O.memory_usage(ref.X, ref.R, ref.U, O.c_full(ref.X, ref.R))
+    assert measure.memory_usage(F) == want
+
+
 def test_host_input_matches_device_input():
     coo = synth.small_uniform()
     Fd = run(coo, 1, 50, 1e-6, 3, 0)

@@ -465,3 +465,17 @@ def test_seeded_state_error_two_routes():
         O.ctd_d_step(st, (40, 25), sl.i, sl.j, sl.val, 12, 1e-6, 2, keep_X=True)
     assert st.t == 9
     assert abs(O.dynamic_error_dense(st) - st.err_num / st.err_den) <= 1e-9
+
+
+def test_memory_usage_by_hand():
+    """Eq. (memoryEff) on a 2 x 2 x 1 tensor with X(0,0) = 1 and X(1,1) = 2,
+    every fiber sampled: R = diag(1, 2) (2 nonzeros), U = (R^T R)^{-1} =
+    diag(1, 1/4) (2), C = R^T X_(1) = diag(1, 4) (2), nnz(X) = 2, so the
+    memory usage is (2 + 2 + 2) / 2 = 3."""
+    res = O.ctd_s((2, 2, 1), np.array([0, 1]), np.array([0, 1]), np.array([0, 0]),
+                  np.array([1, 2]), 1, 64, 1e-6, 0)
+    assert np.array_equal(res.R, np.array([[1, 0], [0, 2]]))
+    assert np.allclose(res.U, np.diag([1.0, 0.25]))
+    C = O.c_full(res.X, res.R)
+    assert np.array_equal(C.toarray(), np.array([[1, 0], [0, 4]]))
+    assert O.memory_usage(res.X, res.R, res.U, C) == 3.0

@@ -96,3 +96,36 @@ def test_poisson_arrivals():
         steps = [r.step for r in R if r.stream == s]
         assert steps == list(range(len(steps)))
     assert all(1e4 <= r.nnz <= 1e6 for r in R)
+
+
+@pytest.mark.parametrize("values, vparam, mean", [("geometric", 0.3, 1 / 0.3), ("poisson1", 3.0, 4.0)])
+def test_device_generator_follows_the_traffic_law(values, vparam, mean):
+    """The on-device generator (here on the CPU device) draws the same law as
+    `traffic`: distinct in-range coordinates, the value law, Zipf(1.2) ids,
+    uniform time, and the same tensor for the same seed."""
+    import torch
+    dims = (2000, 2000, 200)
+    out = synth.traffic_device(dims, 80_000, 1.2, 1.2, values, vparam, 11, device="cpu")
+    i, j, k, v = (t.numpy() for t in out)
+    x = synth.Coo3(dims, i, j, k, v)
+    assert all(t.dtype == torch.int32 for t in out) and x.nnz == 80_000
+    _distinct_in_range(x)
+    assert x.val.min() >= 1
+    assert x.val.mean() == pytest.approx(mean, rel=0.05)
+    assert _zipf_slope(x.i) == pytest.approx(-1.2, abs=0.25)
+    assert _zipf_slope(x.j) == pytest.approx(-1.2, abs=0.25)
+    share = np.bincount(x.k, minlength=200) / x.nnz
+    assert np.abs(share * 200 - 1).max() < 0.25
+    again = synth.traffic_device(dims, 80_000, 1.2, 1.2, values, vparam, 11, device="cpu")
+    assert all(torch.equal(a, b) for a, b in zip(out, again))
+
+
+def test_device_generator_saturating_law():
+    """A Zipf law that needs many draws per distinct coordinate (one of the
+    256-tensor specs with 1.7*10^6 nonzeros) still yields nnz distinct
+    coordinates."""
+    sp = synth.batch_256()[3]
+    out = synth.traffic_device(sp.dims, sp.nnz, 1.2, 1.2, "poisson1", 3.0, sp.seed, device="cpu")
+    x = synth.Coo3(sp.dims, *(t.numpy() for t in out))
+    assert x.nnz == sp.nnz
+    _distinct_in_range(x)
