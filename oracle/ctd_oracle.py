@@ -10,11 +10,14 @@ reads a value computed by the GPU path.
 
 What each function follows:
   matricize              Section 2.1 (mode-alpha matricization), reading A1
+  matricize_nway         Section 2.1 for an N-way tensor, reading A1
   column_sqnorms, cdf    Algorithm 1 (squared norms), Eq. (1)
   philox4x64_10          Salmon et al., SC'11 (counter-based RNG), reading A2
   sample_columns         Algorithm 1 (draws with replacement), reading A2
   unique_columns         Algorithm 1 (unique draws), reading A3
   ctd_s                  Algorithm 1, step by step, FP64
+  ctd_s_nway             Algorithm 1 on an N-way tensor (Section 2.1's
+                         matricization of any order, Algorithm 1 unchanged)
   ctd_d_step             Algorithm 2, step by step, FP64
   c_columns              Algorithm 1's C / Eq. (3), exact int64
   relative_error_dense   Eq. (error), brute force on small inputs
@@ -84,6 +87,29 @@ def matricize(dims, i, j, k, alpha: int):
     if alpha == 3:
         return k, i + I * j, K, I * J
     raise ValueError("alpha must be 1, 2 or 3")
+
+
+def matricize_nway(dims, idx, alpha: int):
+    """Section 2.1 for an N-way tensor: the row of a nonzero is its mode-alpha
+    index and its column is the little-endian index of the other modes,
+    col = sum over n != alpha of i_n * prod over m < n, m != alpha of I_m
+    (reading A1; for N = 3 this is `matricize`).
+
+    Returns (rows int64, cols int64, I_alpha, N_alpha)."""
+    dims = [int(d) for d in dims]
+    N = len(dims)
+    if not 1 <= alpha <= N:
+        raise ValueError("alpha must be in 1..N")
+    idx = [np.asarray(x, dtype=np.int64) for x in idx]
+    rows = idx[alpha - 1]
+    cols = np.zeros_like(rows)
+    stride = 1
+    for n in range(N):
+        if n == alpha - 1:
+            continue
+        cols = cols + idx[n] * stride
+        stride *= dims[n]
+    return rows, cols, dims[alpha - 1], stride
 
 
 # ---------------------------------------------------------------------------
@@ -192,7 +218,10 @@ class Matricized:
 
     @staticmethod
     def from_coo(dims, i, j, k, val, alpha: int) -> "Matricized":
-        rows, cols, n_rows, n_cols = matricize(dims, i, j, k, alpha)
+        return Matricized.from_rows_cols(*matricize(dims, i, j, k, alpha), val)
+
+    @staticmethod
+    def from_rows_cols(rows, cols, n_rows: int, n_cols: int, val) -> "Matricized":
         order = np.lexsort((rows, cols))
         rows = rows[order]
         cols = cols[order]
@@ -318,8 +347,19 @@ def ctd_s(dims, i, j, k, val, alpha: int, s: int, eps: float, seed: int,
           step: int = 0, stream: int = 0) -> StaticResult:
     """Algorithm 1 (CTD-S) up to U.  C is available through
     `c_full` or `c_columns` because it can be far larger than R and U."""
-    X = Matricized.from_coo(dims, i, j, k, val, alpha)            # matricize
-    rows, cols, _, n_cols = matricize(dims, i, j, k, alpha)
+    return _ctd_s(matricize(dims, i, j, k, alpha), val, s, eps, seed, step, stream)
+
+
+def ctd_s_nway(dims, idx, val, alpha: int, s: int, eps: float, seed: int) -> StaticResult:
+    """Algorithm 1 on an N-way tensor (idx: the N index arrays): the same
+    steps on the mode-alpha matricization of `matricize_nway`."""
+    return _ctd_s(matricize_nway(dims, idx, alpha), val, s, eps, seed, 0, 0)
+
+
+def _ctd_s(mat, val, s: int, eps: float, seed: int, step: int, stream: int) -> StaticResult:
+    """Algorithm 1's steps on a matricization (rows, cols, I_alpha, N_alpha)."""
+    rows, cols, n_rows, n_cols = mat
+    X = Matricized.from_rows_cols(rows, cols, n_rows, n_cols, val)  # matricize
     sq = column_sqnorms(cols, val, n_cols)                          # squared norms
     c = cdf(sq)
     T = int(c[-1]) if c.size else 0

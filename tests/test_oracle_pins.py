@@ -479,3 +479,53 @@ def test_memory_usage_by_hand():
     C = O.c_full(res.X, res.R)
     assert np.array_equal(C.toarray(), np.array([[1, 0], [0, 4]]))
     assert O.memory_usage(res.X, res.R, res.U, C) == 3.0
+
+
+# --- N-way tensors (Section 2.1 of any order) ------------------------------
+
+def _random_nway(dims, nnz, seed):
+    rng = np.random.default_rng(seed)
+    lin = rng.choice(int(np.prod(dims)), size=nnz, replace=False)
+    idx, rest = [], lin
+    for d in dims:
+        idx.append(rest % d)
+        rest = rest // d
+    val = rng.integers(1, 6, size=nnz) * rng.choice([-1, 1], size=nnz)
+    return idx, val
+
+
+@pytest.mark.parametrize("dims", [(5, 7), (3, 4, 2, 5), (2, 3, 2, 3, 2)])
+def test_nway_matricization_matches_dense_unfolding(dims):
+    """Every nonzero lands at its (row, column) of numpy's mode-n unfolding
+    (mode n first, then Fortran order), for every mode."""
+    idx, val = _random_nway(dims, 25, seed=len(dims))
+    X = np.zeros(dims, dtype=np.int64)
+    X[tuple(idx)] = val
+    for alpha in range(1, len(dims) + 1):
+        Xa = unfold(X, alpha)
+        rows, cols, n_rows, n_cols = O.matricize_nway(dims, idx, alpha)
+        assert (n_rows, n_cols) == Xa.shape
+        assert np.array_equal(Xa[rows, cols], val)
+        assert np.array_equal(O.column_sqnorms(cols, val, n_cols), np.sum(Xa * Xa, axis=0))
+
+
+def test_nway_matricization_by_hand():
+    """dims (2, 3, 2, 2), the entry at (1, 2, 0, 1), mode 3: its row is i3 = 0
+    and its column i1 + 2 i2 + (2 * 3) i4 = 1 + 4 + 6 = 11 of 12."""
+    rows, cols, n_rows, n_cols = O.matricize_nway((2, 3, 2, 2), [[1], [2], [0], [1]], 3)
+    assert (int(rows[0]), int(cols[0]), n_rows, n_cols) == (0, 11, 2, 12)
+
+
+def test_nway_reduces_to_three_way():
+    """For N = 3 the N-way matricization is the 3-way one, and a 4-way tensor
+    whose last mode has extent 1 gives CTD-S's result on the 3-way tensor."""
+    coo = synth.tiny((6, 5, 4), 40, seed=21, signed=True)
+    for alpha in (1, 2, 3):
+        a = O.matricize(coo.dims, coo.i, coo.j, coo.k, alpha)
+        b = O.matricize_nway(coo.dims, [coo.i, coo.j, coo.k], alpha)
+        assert all(np.array_equal(x, y) for x, y in zip(a[:2], b[:2])) and a[2:] == b[2:]
+        r3 = O.ctd_s(coo.dims, coo.i, coo.j, coo.k, coo.val, alpha, 30, 1e-6, 2)
+        r4 = O.ctd_s_nway(coo.dims + (1,), [coo.i, coo.j, coo.k, np.zeros_like(coo.i)],
+                          coo.val, alpha, 30, 1e-6, 2)
+        assert np.array_equal(r3.I, r4.I) and np.array_equal(r3.fibers, r4.fibers)
+        assert np.array_equal(r3.R, r4.R) and np.array_equal(r3.U, r4.U)
