@@ -133,6 +133,35 @@ CTD_API ctd_status ctd_static(const ctd_coo3* X, int alpha, int64_t s, double ep
                       void* stream, ctd_factors** out);
 
 /*
+ * ctd_static_nway -- CTD-S (Algorithm 1) on an N-way tensor (Section 2.1:
+ * Algorithm 1 takes an N-way tensor and a mode alpha; its matricization
+ * X_(alpha) has the mode-alpha index as row and the other modes, in
+ * little-endian order, as column: f = sum over n != alpha of
+ * i_n * prod over m < n, m != alpha of I_m).  Same result as ctd_static on
+ * the 3-way tensor I_alpha x N_alpha x 1 with alpha = 1, which is what it
+ * runs after mapping every nonzero on the device; the factors' column ids
+ * (ctd_get_fibers, the columns of C) are the N-way f above.
+ *  X        order N in 1 .. CTD_MAX_ORDER, dims[0 .. N), idx[0 .. N) the index
+ *           arrays (int32, 0-based), val int32 counts; device or host memory
+ *  alpha    1 .. N
+ *  others   as ctd_static
+ * Errors as ctd_static; CTD_EINVAL also when N_alpha >= 2^31 or an index is
+ * outside its mode.
+ */
+#define CTD_MAX_ORDER 8
+typedef struct {
+  int32_t order;                       /* N */
+  int64_t dims[CTD_MAX_ORDER];         /* I_1 .. I_N */
+  int64_t nnz;
+  const int32_t* idx[CTD_MAX_ORDER];   /* idx[n][e]: mode-(n+1) index of nonzero e */
+  const int32_t* val;
+  int32_t memory;                      /* ctd_memory */
+} ctd_coon;
+CTD_API ctd_status ctd_static_nway(const ctd_coon* X, int alpha, int64_t s, double eps,
+                                   uint64_t seed, int precision, unsigned flags, void* stream,
+                                   ctd_factors** out);
+
+/*
  * ctd_static_batched -- CTD-S (Algorithm 1) on n independent tensors, each
  * exactly as ctd_static(&X[t], alpha, s[t], eps, seeds[t], precision, flags)
  * would decompose it.  The per-tensor pipelines run concurrently on

@@ -36,7 +36,8 @@ EXPORTED = ["ctd_static", "ctd_dynamic_create", "ctd_dynamic_step", "ctd_error",
             "ctd_version", "ctd_profile", "ctd_profile_report", "ctd_sample_noalloc", "ctd_static_batched", "ctd_server_create", "ctd_server_submit",
             "ctd_server_wait", "ctd_server_result", "ctd_server_state", "ctd_server_free",
             "ctd_ddos_candidates", "ctd_dynamic_from_static", "ctd_fault_inject_alloc",
-            "ctd_selftest_bounded_wait", "ctd_set_allocator", "ctd_allocated_bytes"]
+            "ctd_selftest_bounded_wait", "ctd_set_allocator", "ctd_allocated_bytes",
+            "ctd_static_nway"]
 
 
 class CtdError(RuntimeError):
@@ -50,6 +51,14 @@ class ctd_coo3(C.Structure):
     _fields_ = [("dims", C.c_int64 * 3), ("nnz", C.c_int64), ("i", C.c_void_p),
                 ("j", C.c_void_p), ("k", C.c_void_p), ("val", C.c_void_p),
                 ("memory", C.c_int32)]
+
+
+CTD_MAX_ORDER = 8
+
+
+class ctd_coon(C.Structure):
+    _fields_ = [("order", C.c_int32), ("dims", C.c_int64 * CTD_MAX_ORDER), ("nnz", C.c_int64),
+                ("idx", C.c_void_p * CTD_MAX_ORDER), ("val", C.c_void_p), ("memory", C.c_int32)]
 
 
 class ctd_sizes(C.Structure):
@@ -103,6 +112,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ctd_fault_inject_alloc": [I64],
         "ctd_selftest_bounded_wait": [I64, P],
         "ctd_set_allocator": [P, P],
+        "ctd_static_nway": [C.POINTER(ctd_coon), I32, I64, D, U64, I32, C.c_uint, P, C.POINTER(P)],
         "ctd_allocated_bytes": [C.POINTER(C.c_size_t)],
     }
     for name, args in sig.items():
@@ -207,6 +217,39 @@ class Coo:
             return Coo(x.dims, *t)
         return Coo(x.dims, *(np.ascontiguousarray(a, dtype=np.int32)
                              for a in (x.i, x.j, x.k, x.val)))
+
+
+class CooN:
+    """An N-way COO descriptor (ctd_coon) over N index arrays and the values:
+    torch CUDA int32 tensors or numpy int32 arrays (host).  Keeps references
+    so the buffers outlive the call."""
+
+    def __init__(self, dims, idx, val):
+        self.dims = tuple(int(d) for d in dims)
+        if not 1 <= len(self.dims) <= CTD_MAX_ORDER or len(idx) != len(self.dims):
+            raise ValueError("one index array per mode, 1 .. CTD_MAX_ORDER modes")
+        self._keep = (*idx, val)
+        host = isinstance(val, np.ndarray)
+        for a in self._keep:
+            if host:
+                if not isinstance(a, np.ndarray) or a.dtype != np.int32 or not a.flags.c_contiguous:
+                    raise TypeError("host COO arrays must be contiguous int32")
+            elif str(a.dtype) != "torch.int32" or not a.is_contiguous() or not a.is_cuda:
+                raise TypeError("device COO tensors must be contiguous CUDA int32")
+        N = len(self.dims)
+        d = (C.c_int64 * CTD_MAX_ORDER)(*self.dims, *([1] * (CTD_MAX_ORDER - N)))
+        ix = (C.c_void_p * CTD_MAX_ORDER)(*[_ptr(a) for a in idx], *([None] * (CTD_MAX_ORDER - N)))
+        self.desc = ctd_coon(N, d, int(val.shape[0]), ix, _ptr(val),
+                             CTD_MEM_HOST if host else CTD_MEM_DEVICE)
+
+    @staticmethod
+    def from_arrays(dims, idx, val, device: bool = True) -> "CooN":
+        """From numpy index arrays and values (copied to the GPU if device)."""
+        arrs = [np.ascontiguousarray(a, dtype=np.int32) for a in (*idx, val)]
+        if device:
+            import torch
+            arrs = [torch.from_numpy(a).cuda() for a in arrs]
+        return CooN(dims, arrs[:-1], arrs[-1])
 
 
 class Factors:
@@ -325,6 +368,18 @@ def ctd_static(X: Coo, alpha: int, s: int, eps: float, seed: int = 0,
     st = _stream_handle(stream) if not _host(X) or stream is not None else _default_stream()
     _check(lib.ctd_static(C.byref(X.desc), int(alpha), int(s), float(eps), int(seed),
                           int(precision), int(flags), C.c_void_p(st), C.byref(out)))
+    return Factors(out.value)
+
+
+def ctd_static_nway(X: CooN, alpha: int, s: int, eps: float, seed: int = 0,
+                    precision: int = CTD_FP64, flags: int = 0, stream=None) -> Factors:
+    """CTD-S (Algorithm 1) on an N-way tensor through the C ABI."""
+    lib = load()
+    out = C.c_void_p()
+    host = X.desc.memory == CTD_MEM_HOST
+    st = _stream_handle(stream) if not host or stream is not None else _default_stream()
+    _check(lib.ctd_static_nway(C.byref(X.desc), int(alpha), int(s), float(eps), int(seed),
+                               int(precision), int(flags), C.c_void_p(st), C.byref(out)))
     return Factors(out.value)
 
 

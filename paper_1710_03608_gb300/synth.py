@@ -373,3 +373,20 @@ def tiny(dims=(6, 5, 4), nnz: int = 30, seed: int = 7, vmax: int = 5, signed: bo
     if signed:
         vals = vals * rng.choice([-1, 1], size=nnz)
     return _finish(rng, dims, ii, jj, kk, vals)
+
+
+def nway_uniform(dims, nnz: int, seed: int, vmax: int = 5, signed: bool = False):
+    """An N-way tensor with `nnz` distinct uniform coordinates and values in
+    1 .. vmax (random signs if `signed`): (list of N int32 index arrays,
+    int32 values), in a seeded random order."""
+    rng = np.random.default_rng(seed)
+    cells = int(np.prod([int(d) for d in dims]))
+    lin = rng.choice(cells, size=nnz, replace=False).astype(np.int64)
+    idx, rest = [], lin
+    for d in dims:
+        idx.append(np.ascontiguousarray(rest % int(d), dtype=np.int32))
+        rest = rest // int(d)
+    val = rng.integers(1, vmax + 1, size=nnz)
+    if signed:
+        val = val * rng.choice([-1, 1], size=nnz)
+    return idx, np.ascontiguousarray(val, dtype=np.int32)

@@ -129,3 +129,14 @@ def test_device_generator_saturating_law():
     x = synth.Coo3(sp.dims, *(t.numpy() for t in out))
     assert x.nnz == sp.nnz
     _distinct_in_range(x)
+
+
+def test_nway_uniform():
+    dims = (9, 8, 7, 6)
+    idx, val = synth.nway_uniform(dims, 500, seed=3, vmax=7, signed=True)
+    assert len(idx) == 4 and all(a.dtype == np.int32 for a in idx) and val.dtype == np.int32
+    for a, d in zip(idx, dims):
+        assert (a >= 0).all() and (a < d).all()
+    lin = sum(a.astype(np.int64) * int(np.prod(dims[:n])) for n, a in enumerate(idx))
+    assert np.unique(lin).shape[0] == 500
+    assert 1 <= np.abs(val).min() and np.abs(val).max() <= 7 and (val < 0).any()
