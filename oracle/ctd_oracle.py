@@ -12,6 +12,7 @@ What each function follows:
   matricize              Section 2.1 (mode-alpha matricization), reading A1
   matricize_nway         Section 2.1 for an N-way tensor, reading A1
   column_sqnorms, cdf    Algorithm 1 (squared norms), Eq. (1)
+  sampling_weights, column_weights   Eq. (1) for real (FP32) values, reading A28
   philox4x64_10          Salmon et al., SC'11 (counter-based RNG), reading A2
   sample_columns         Algorithm 1 (draws with replacement), reading A2
   unique_columns         Algorithm 1 (unique draws), reading A3
@@ -43,6 +44,9 @@ Readings of points the paper leaves open (same letters everywhere):
   A21 the test's residual is evaluated as x minus its orthogonal projection
       onto range(R), by Gram-Schmidt with reorthogonalization (equal to
       x - R U R^T x in exact arithmetic; stable in floating point).
+  A28 real values: each square on a fixed-point grid, floor(v^2 2^(32-E))
+     with 2^E the smallest power of two above the largest square; the draws
+     use those exact integers.
   A23 Section 5's average norm is the exact sum of the representatives'
      norms rounded once, divided by their count (no summation order).
 
@@ -137,6 +141,28 @@ def column_sqnorms(cols, vals, n_cols: int) -> np.ndarray:
     return exact.astype(np.int64)
 
 
+def sampling_weights(vals) -> np.ndarray:
+    """Eq. (1)'s summands for real values (reading A28): the FP32 values'
+    squares (exact in FP64) on a fixed-point grid, floor(v^2 * 2^(32 - E))
+    with M = f * 2^E (f in [1/2, 1)) the largest square, so every weight is
+    an exact integer below 2^32 (all zero when every value is zero)."""
+    v = np.asarray(vals, dtype=np.float32).astype(np.float64)
+    sq = v * v
+    M = float(sq.max()) if sq.size else 0.0
+    if M == 0.0:
+        return np.zeros(sq.shape[0], dtype=np.int64)
+    E = math.frexp(M)[1]
+    return np.floor(np.ldexp(sq, 32 - E)).astype(np.int64)
+
+
+def column_weights(cols, vals, n_cols: int) -> np.ndarray:
+    """Per column of X_(alpha), the sum of its values' sampling weights
+    (real values, reading A28); exact int64 (each weight < 2^32)."""
+    out = np.zeros(n_cols, dtype=np.int64)
+    np.add.at(out, np.asarray(cols, dtype=np.int64), sampling_weights(vals))
+    return out
+
+
 def cdf(sqnorms: np.ndarray) -> np.ndarray:
     """Inclusive prefix sum of the squared norms; the last entry is ||X||_F^2."""
     out = np.cumsum(np.asarray(sqnorms, dtype=np.int64))
@@ -208,7 +234,8 @@ def unique_columns(I: np.ndarray) -> np.ndarray:
 
 @dataclasses.dataclass
 class Matricized:
-    """X_(alpha) as exact int64 CSC: column f holds rows[ptr[f]:ptr[f+1]]."""
+    """X_(alpha) as CSC: column f holds rows[ptr[f]:ptr[f+1]]; values exact
+    int64 for counts, float64 (from FP32) for real values."""
 
     n_rows: int
     n_cols: int
@@ -225,20 +252,29 @@ class Matricized:
         order = np.lexsort((rows, cols))
         rows = rows[order]
         cols = cols[order]
-        vals = np.asarray(val, dtype=np.int64)[order]
+        vals = np.asarray(val)
+        vals = vals.astype(np.float64 if np.issubdtype(vals.dtype, np.floating) else np.int64)
+        vals = vals[order]
         ptr = np.zeros(n_cols + 1, dtype=np.int64)
         np.add.at(ptr, cols + 1, 1)
         ptr = np.cumsum(ptr)
         return Matricized(n_rows, n_cols, ptr, rows, vals)
 
     def column(self, f: int) -> np.ndarray:
-        """Dense int64 column X_(alpha)(:, f)."""
-        x = np.zeros(self.n_rows, dtype=np.int64)
+        """Dense column X_(alpha)(:, f) (int64, or float64 for real values)."""
+        x = np.zeros(self.n_rows, dtype=self.vals.dtype)
         a, b = int(self.ptr[f]), int(self.ptr[f + 1])
         x[self.rows[a:b]] = self.vals[a:b]
         return x
 
-    def sqnorm(self) -> int:
+    @property
+    def real(self) -> bool:
+        return bool(np.issubdtype(self.vals.dtype, np.floating))
+
+    def sqnorm(self):
+        """||X||_F^2: exact int for counts, FP64 for real values."""
+        if self.real:
+            return float(np.sum(self.vals * self.vals))
         return int(np.sum(self.vals * self.vals))
 
     def scipy(self):
@@ -360,7 +396,10 @@ def _ctd_s(mat, val, s: int, eps: float, seed: int, step: int, stream: int) -> S
     """Algorithm 1's steps on a matricization (rows, cols, I_alpha, N_alpha)."""
     rows, cols, n_rows, n_cols = mat
     X = Matricized.from_rows_cols(rows, cols, n_rows, n_cols, val)  # matricize
-    sq = column_sqnorms(cols, val, n_cols)                          # squared norms
+    if X.real:                                                      # squared norms
+        sq = column_weights(cols, val, n_cols)                      # (A28 for reals)
+    else:
+        sq = column_sqnorms(cols, val, n_cols)
     c = cdf(sq)
     T = int(c[-1]) if c.size else 0
     I = sample_columns(c, s, seed, step, stream)                    # draws
@@ -370,7 +409,7 @@ def _ctd_s(mat, val, s: int, eps: float, seed: int, step: int, stream: int) -> S
     if R_cols:
         R = np.stack([X.column(int(f)) for f in fibers], axis=1)
     else:
-        R = np.zeros((X.n_rows, 0), dtype=np.int64)
+        R = np.zeros((X.n_rows, 0), dtype=X.vals.dtype)
         U = np.zeros((0, 0))
     return StaticResult(T, sq, c, I, Iu, np.asarray(kept, dtype=np.int64), fibers,
                         R, U, np.asarray(ratios), X)
@@ -381,9 +420,10 @@ def _ctd_s(mat, val, s: int, eps: float, seed: int, step: int, stream: int) -> S
 # ---------------------------------------------------------------------------
 
 def c_columns(X: Matricized, R: np.ndarray, cols) -> np.ndarray:
-    """Dense exact int64 columns C_(alpha)(:, cols) = R^T X_(alpha)(:, cols)."""
-    R = np.asarray(R, dtype=np.int64)
-    out = np.zeros((R.shape[1], len(cols)), dtype=np.int64)
+    """Dense columns C_(alpha)(:, cols) = R^T X_(alpha)(:, cols): exact int64
+    for counts, float64 for real values."""
+    R = np.asarray(R, dtype=X.vals.dtype)
+    out = np.zeros((R.shape[1], len(cols)), dtype=X.vals.dtype)
     for n, f in enumerate(cols):
         a, b = int(X.ptr[f]), int(X.ptr[f + 1])
         if b > a:
@@ -392,8 +432,9 @@ def c_columns(X: Matricized, R: np.ndarray, cols) -> np.ndarray:
 
 
 def c_full(X: Matricized, R: np.ndarray):
-    """C_(alpha) = R^T X_(alpha) as an exact int64 scipy CSC matrix."""
-    Rs = _sp.csc_matrix(np.asarray(R, dtype=np.int64))
+    """C_(alpha) = R^T X_(alpha) as a scipy CSC matrix (exact int64 for
+    counts, float64 for real values)."""
+    Rs = _sp.csc_matrix(np.asarray(R, dtype=X.vals.dtype))
     C = (Rs.T @ X.scipy()).tocsc()
     C.eliminate_zeros()
     C.sort_indices()

@@ -529,3 +529,43 @@ def test_nway_reduces_to_three_way():
                           coo.val, alpha, 30, 1e-6, 2)
         assert np.array_equal(r3.I, r4.I) and np.array_equal(r3.fibers, r4.fibers)
         assert np.array_equal(r3.R, r4.R) and np.array_equal(r3.U, r4.U)
+
+
+# --- real values (reading A28) ---------------------------------------------
+
+def test_sampling_weights_by_hand():
+    """Values 1.5, -0.5, 3: squares 2.25, 0.25, 9; the largest is 9 = 0.5625 * 2^4,
+    so the grid is 2^(32 - 4) and the weights are 2.25 * 2^28, 0.25 * 2^28 and
+    9 * 2^28 exactly; all zeros give zero weights."""
+    w = O.sampling_weights(np.array([1.5, -0.5, 3.0], dtype=np.float32))
+    assert list(w) == [603979776, 67108864, 2415919104]
+    assert list(O.sampling_weights(np.zeros(3, np.float32))) == [0, 0, 0]
+
+
+def test_real_values_holding_integers_draw_as_counts():
+    """A real tensor whose values are small integers has weights proportional
+    to the integer squares (a power of two apart), and floor(u T / 2^64)
+    compared with a CDF scaled by a power of two picks the same column, so
+    the draws, the kept fibers, R and U equal the integer oracle's."""
+    coo = synth.tiny((8, 7, 6), 120, seed=41, vmax=9, signed=True)
+    idx = [coo.i, coo.j, coo.k]
+    for alpha in (1, 2, 3):
+        ri = O.ctd_s_nway(coo.dims, idx, coo.val, alpha, 60, 1e-6, 5)
+        rr = O.ctd_s_nway(coo.dims, idx, coo.val.astype(np.float32), alpha, 60, 1e-6, 5)
+        assert np.array_equal(ri.I, rr.I) and np.array_equal(ri.fibers, rr.fibers)
+        assert np.array_equal(ri.R.astype(np.float64), rr.R)
+        assert np.allclose(ri.U, rr.U, rtol=1e-12, atol=0)
+        assert rr.X.sqnorm() == float(ri.X.sqnorm())
+
+
+def test_real_sampling_law():
+    """The draws of a real tensor follow P(f) = ||x_f||^2 / ||X||^2 up to the
+    grid: chi-square of 20,000 draws on 6 columns against the exact law."""
+    vals = np.array([0.3, 1.7, -2.2, 0.05, 3.1, 1.0], dtype=np.float32)
+    w = O.column_weights(np.arange(6), vals, 6)
+    p_exact = vals.astype(np.float64) ** 2 / np.sum(vals.astype(np.float64) ** 2)
+    assert np.allclose(w / w.sum(), p_exact, rtol=1e-8, atol=1e-9)
+    I = O.sample_columns(O.cdf(w), 20000, 7)
+    obs = np.bincount(I, minlength=6)
+    chi2 = float(np.sum((obs - 20000 * p_exact) ** 2 / (20000 * p_exact)))
+    assert chi2 < 20.5   # 5 degrees of freedom, p = 0.001
