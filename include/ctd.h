@@ -142,20 +142,32 @@ CTD_API ctd_status ctd_static(const ctd_coo3* X, int alpha, int64_t s, double ep
  * runs after mapping every nonzero on the device; the factors' column ids
  * (ctd_get_fibers, the columns of C) are the N-way f above.
  *  X        order N in 1 .. CTD_MAX_ORDER, dims[0 .. N), idx[0 .. N) the index
- *           arrays (int32, 0-based), val int32 counts; device or host memory
+ *           arrays (int32, 0-based), val the values: int32 counts
+ *           (val_type CTD_VAL_INT32) or real values as FP32 (CTD_VAL_FP32);
+ *           device or host memory.  Real values take the draws on the
+ *           squares' fixed-point grid of reading A28 (each square rounded
+ *           down to a multiple of 2^-32 of the largest square's power of
+ *           two; exact and device-independent) and FP64 arithmetic after the
+ *           draws: R, U and C hold the same values as with integers up to
+ *           rounding, the error is FP64, and the dense R/C copies this path
+ *           makes need I_alpha * s' < 2^31 (else CTD_ENOTSUP).  CTD-D and
+ *           the detector take integer counts only.
  *  alpha    1 .. N
  *  others   as ctd_static
- * Errors as ctd_static; CTD_EINVAL also when N_alpha >= 2^31 or an index is
- * outside its mode.
+ * Errors as ctd_static; CTD_EINVAL also when N_alpha >= 2^31, an index is
+ * outside its mode, or a real value is not finite.
  */
 #define CTD_MAX_ORDER 8
+#define CTD_VAL_INT32 0
+#define CTD_VAL_FP32 1
 typedef struct {
   int32_t order;                       /* N */
   int64_t dims[CTD_MAX_ORDER];         /* I_1 .. I_N */
   int64_t nnz;
   const int32_t* idx[CTD_MAX_ORDER];   /* idx[n][e]: mode-(n+1) index of nonzero e */
-  const int32_t* val;
+  const void* val;                     /* int32 counts or FP32 values (val_type) */
   int32_t memory;                      /* ctd_memory */
+  int32_t val_type;                    /* CTD_VAL_INT32 or CTD_VAL_FP32 */
 } ctd_coon;
 CTD_API ctd_status ctd_static_nway(const ctd_coon* X, int alpha, int64_t s, double eps,
                                    uint64_t seed, int precision, unsigned flags, void* stream,
@@ -258,6 +270,10 @@ CTD_API ctd_status ctd_get_R(const ctd_factors* F, int64_t* colptr, int32_t* row
 
 /* U, s~ x s~, row-major (symmetric). */
 CTD_API ctd_status ctd_get_U(const ctd_factors* F, double* U);
+/* R as ctd_get_R with its values as double: integer counts, or the FP32
+ * values of a real-valued tensor (ctd_get_R then returns their bits). */
+CTD_API ctd_status ctd_get_R_f64(const ctd_factors* F, int64_t* colptr, int32_t* row,
+                                 double* val);
 
 /* Dense columns of C_(alpha): out is s~ x ncols, column-major.
  * CTD-S: cols are column ids of X_(alpha).  CTD-D: column c of step t is

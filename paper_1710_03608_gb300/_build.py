@@ -21,7 +21,7 @@ ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 SOURCES = ["ctd_stream.cu", "ctd_sample.cu", "ctd_spmm.cu", "ctd_dense.cu", "ctd_filter.cu", "ctd_api.cu",
            "ctd_dynamic.cu", "ctd_noalloc.cu", "ctd_batch.cu",
            "ctd_serve.cu", "ctd_cfill.cu", "ctd_detect.cu", "ctd_matricize.cu",
-           "ctd_nway.cu"]
+           "ctd_nway.cu", "ctd_real.cu"]
 
 
 def nvcc() -> str:

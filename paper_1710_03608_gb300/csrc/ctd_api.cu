@@ -304,7 +304,7 @@ ctd_status stage_coo(const ctd_coo3* X, int alpha, Arena& scratch, cudaStream_t 
 // column's contiguous entries, fused with the first pass of their prefix
 // sum (the CDF).
 ctd_status matricize(const CooDev& X, Arena& A, cudaStream_t st, Matricized* M, bool sort_cols,
-                     Arena* dist) {
+                     Arena* dist, int wshift) {
   mode_extents(X.dims, X.alpha, &M->n_rows, &M->n_cols);
   M->nnz = X.nnz;
   Arena& D = dist ? *dist : A;
@@ -323,7 +323,7 @@ ctd_status matricize(const CooDev& X, Arena& A, cudaStream_t st, Matricized* M, 
   CTD_CUDA(cudaMemsetAsync(M->status, 0, 4, st));
   CTD_CUDA(cudaMemsetAsync(M->minval, 0xff, 8, st));  // codes of "no value yet"
   bool bucketed = false;
-  CTD_TRY(matricize_bucketed(X, A, st, M, &bucketed));
+  CTD_TRY(matricize_bucketed(X, A, st, M, &bucketed, wshift));
   if (!bucketed) {
     uint32_t* colcnt;
     CTD_TRY(A.get(&colcnt, M->n_cols));
@@ -345,7 +345,7 @@ ctd_status matricize(const CooDev& X, Arena& A, cudaStream_t st, Matricized* M, 
     launch_scan_finish(M->norm2, M->cdf, M->n_cols, M->tmp, M->status, st);
   else
     launch_sqnorms_cdf(M->colptr, M->csc_val, M->n_cols, M->norm2, M->cdf, M->minval, M->tmp,
-                       M->status, st);
+                       M->status, st, wshift);
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
 }
@@ -388,15 +388,28 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
     PhaseScope ph("stage", st);
     CTD_TRY(stage_coo(Xd, alpha, scratch, st, &X));
   }
+  return static_impl(X, s, eps, seed, precision, flags, st, scratch, 0, out);
+}
+
+namespace ctd {
+// Algorithm 1 on a staged tensor (device COO, mode and dims in X); real:
+// the values' payloads hold FP32 values.
+ctd_status static_impl(const CooDev& X, int64_t s, double eps, uint64_t seed, int precision,
+                       unsigned flags, cudaStream_t st, Arena& scratch, int real,
+                       ctd_factors** out) {
+  const int alpha = X.alpha;
+  int wshift = WSHIFT_INT;
+  if (real) CTD_TRY(real_weight_shift(X.v, X.nnz, &wshift, scratch, st));
 
   ctd_factors* F = new ctd_factors();
+  F->real = real != 0;
   F->mem.st = st;
   F->kind = 0;
   F->alpha = alpha;
   F->precision = precision;
   F->stream = st;
   F->seed = seed;
-  for (int d = 0; d < 3; ++d) F->dims[d] = Xd->dims[d];
+  for (int d = 0; d < 3; ++d) F->dims[d] = X.dims[d];
   F->nnz_X = X.nnz;
   F->s = s;
   auto bail = [&](ctd_status rc) {
@@ -421,7 +434,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   {
     PhaseScope ph("matricize", st);
     STEP(matricize(X, scratch, st, &M, (flags & CTD_DETERMINISTIC) != 0,
-                   (flags & CTD_KEEP_DIST) ? &F->mem : nullptr));
+                   (flags & CTD_KEEP_DIST) ? &F->mem : nullptr, wshift));
   }
   if (flags & CTD_KEEP_DIST) {
     F->norm2 = M.norm2;
@@ -463,9 +476,11 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   }
   STEP(status_from_device(status));
   F->T = T;
-  const int minval = decode_min(minkey[0]);
-  // X's values fit int8: the C fill can take four products per instruction
-  const bool x_int8 = minval >= -128 && decode_max(minkey[1]) <= 127;
+  // integer counts: the smallest value (all positive: the C fill copies R's
+  // rows for one-nonzero columns) and whether they fit int8 (four products
+  // per instruction); neither applies to real values
+  const int minval = real ? 0 : decode_min(minkey[0]);
+  const bool x_int8 = !real && minval >= -128 && decode_max(minkey[1]) <= 127;
   F->min_val = minval;
   F->s_unique = s_unique;
   if (T == 0) F->s = 0;  // nothing to draw from
@@ -494,7 +509,10 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   CsrDev Rc{rcr_ptr, rcr_col, rcr_val, su};
   {
     PhaseScope ph("gram", st);
-    STEP(launch_spmm_dense(M.csc(), F->Iu, d_count, su, Rc, G, su, st));
+    if (real)
+      STEP(real_gram(rc_ptr, rc_row, rc_val, d_count, su, M.n_rows, G, scratch, st));
+    else
+      STEP(launch_spmm_dense(M.csc(), F->Iu, d_count, su, Rc, G, su, st));
     launch_thresholds(G, su, su, 1.0, xn2, st);
   }
   FilterIn fi;
@@ -509,6 +527,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   fi.c_col = rcr_col;
   fi.c_val = rcr_val;
   fi.n_rows = M.n_rows;
+  fi.real = real;
   FilterOut fo;
   STEP(run_filter(fi, fo, scratch, st));
   const int kept = fo.kept;
@@ -568,8 +587,9 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
     // largest |R| (the C fill stores its longest rows as int16 when they fit)
     STEP(scratch.get(&d_rmax, 1));
     STEPC(cudaMemsetAsync(d_rmax, 0, sizeof(int), st));
-    CTD_LAUNCH(k_abs_max, (grid_for((int64_t)nnzR_cap, 256, (int64_t)num_sms() * 4)), (256), 0,
-               st, F->Rval, F->Rcolptr + kept, d_rmax);
+    if (!real)
+      CTD_LAUNCH(k_abs_max, (grid_for((int64_t)nnzR_cap, 256, (int64_t)num_sms() * 4)), (256), 0,
+                 st, F->Rval, F->Rcolptr + kept, d_rmax);
     STEP(rbc.add(&cap, F->Coff + M.n_cols, 1));
     STEP(rbc.add(&nnzR, F->Rcolptr + kept, 1));
     STEP(rbc.add(&rmax, (const int*)d_rmax, 1));
@@ -580,8 +600,17 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   if (!(flags & CTD_SKIP_ERROR) && kept > 0) {
     STEP(scratch.get(&d_pu, 1));
     PhaseScope ph("error_qform", st);
-    STEP(launch_error_qform(M.csc(), M.n_cols, M.n_rows, M.nnz, R, Z, kept, M.rowcnt,
-                            precision == CTD_FP32_BULK, d_pu, scratch, st));
+    if (real)
+      STEP(real_error_qform(M.csc(), M.n_cols, M.n_rows, F->Rcolptr, F->Rrow, F->Rval, kept, Z,
+                            kept, d_pu, scratch, st));
+    else
+      STEP(launch_error_qform(M.csc(), M.n_cols, M.n_rows, M.nnz, R, Z, kept, M.rowcnt,
+                              precision == CTD_FP32_BULK, d_pu, scratch, st));
+  }
+  double* d_sq = nullptr;  // real values: ||X||_F^2 in FP64
+  if (real) {
+    STEP(scratch.get(&d_sq, 1));
+    STEP(real_sqnorm(M.csc_val, M.nnz, d_sq, scratch, st));
   }
   if (!(flags & CTD_SKIP_C)) {
     STEP(rbc.wait_mark());
@@ -596,8 +625,12 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
     F->mem.ptrs.push_back(cv);
     F->Cval = cv;
     PhaseScope ph("c_fill", st);
-    STEP(launch_c_fill(M.csc(), M.n_cols, M.n_rows, M.nnz, R, F->Coff, F->Ccnt, F->Crow, F->Cval,
-                       precision == CTD_FP32_BULK, minval > 0, x_int8, T, st));
+    if (real)
+      STEP(real_c_fill(M.csc(), M.n_cols, R, F->Coff, F->Ccnt, F->Crow, F->Cval,
+                       precision == CTD_FP32_BULK, st));
+    else
+      STEP(launch_c_fill(M.csc(), M.n_cols, M.n_rows, M.nnz, R, F->Coff, F->Ccnt, F->Crow,
+                         F->Cval, precision == CTD_FP32_BULK, minval > 0, x_int8, T, st));
   }
   uint64_t* d_nnzc;
   STEP(scratch.get(&d_nnzc, 1));
@@ -609,6 +642,7 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
     STEP(rb.add(&nnzR_final, F->Rcolptr + kept, 1));
     if (F->Ccnt) STEP(rb.add(&nnzC, d_nnzc, 1));
     if (d_pu) STEP(rb.add(&pu, d_pu, 1));
+    if (d_sq) STEP(rb.add(&F->sqnorm_real, d_sq, 1));
     STEP(rb.add(&status, M.status, 1));
     STEPC(cudaGetLastError());
     STEP(rb.wait());
@@ -618,13 +652,15 @@ extern "C" ctd_status ctd_static(const ctd_coo3* Xd, int alpha, int64_t s, doubl
   F->nnz_R = (int64_t)nnzR_final;
   if (!(flags & CTD_SKIP_ERROR)) {
     F->have_err = true;
-    F->err = T ? std::max(0.0, ((double)T - pu) / (double)T) : 0.0;
+    const double tot = real ? F->sqnorm_real : (double)T;
+    F->err = tot > 0.0 ? std::max(0.0, (tot - pu) / tot) : 0.0;
   }
   *out = F;
 #undef STEP
 #undef STEPC
   return CTD_OK;
 }
+}  // namespace ctd
 
 // ---------------------------------------------------------------------------
 // getters
@@ -649,7 +685,7 @@ extern "C" ctd_status ctd_get_sizes(const ctd_factors* F, ctd_sizes* o) {
   o->nnz_C = F->nnz_C;
   o->t_steps = 0;
   o->nnz_X = F->nnz_X;
-  o->sqnorm_X = (double)F->T;
+  o->sqnorm_X = F->real ? F->sqnorm_real : (double)F->T;
   return CTD_OK;
 }
 
@@ -713,6 +749,25 @@ extern "C" ctd_status ctd_get_R(const ctd_factors* F, int64_t* colptr, int32_t* 
     if (F->kind == 1) return dyn_R(F, colptr, row, val);
     return csc_to_host_sorted(F->Rcolptr, F->Rrow, F->Rval, F->s_kept, F->nnz_R, F->stream,
                               colptr, row, val);
+  });
+}
+
+extern "C" ctd_status ctd_get_R_f64(const ctd_factors* F, int64_t* colptr, int32_t* row,
+                                    double* val) {
+  if (!F || !colptr || (F->nnz_R && (!row || !val))) return fail(CTD_EINVAL, "NULL argument");
+  return guarded([&]() -> ctd_status {
+    std::vector<int32_t> bits((size_t)std::max<int64_t>(F->nnz_R, 1));
+    CTD_TRY(ctd_get_R(F, colptr, row, bits.data()));
+    for (int64_t q = 0; q < F->nnz_R; ++q) {
+      if (F->real) {
+        float x;
+        std::memcpy(&x, &bits[q], sizeof(float));
+        val[q] = x;
+      } else {
+        val[q] = bits[q];
+      }
+    }
+    return CTD_OK;
   });
 }
 

@@ -168,6 +168,7 @@ extern "C" ctd_status ctd_ddos_candidates(const ctd_factors* F, int64_t cap, int
                                           int64_t* n_found, double* mean_norm) {
   if (!F || !n_found || cap < 0 || (cap > 0 && !dst)) return fail(CTD_EINVAL, "NULL argument or cap < 0");
   if (F->alpha != 1) return fail(CTD_EINVAL, "the detector reads destinations from alpha = 1 fibers");
+  if (F->real) return fail(CTD_ENOTSUP, "the detector takes integer counts");
   CTD_TRY(dyn_check_complete(F));
   cudaStream_t st = F->stream;
   const int64_t ncols = F->s_kept, nkeys = F->dims[1];

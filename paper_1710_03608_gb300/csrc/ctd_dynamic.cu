@@ -879,6 +879,7 @@ extern "C" ctd_status ctd_dynamic_from_static(const ctd_factors* S, uint64_t str
                                               ctd_factors** state) {
   if (!S || !state) return fail(CTD_EINVAL, "NULL argument");
   if (S->kind != 0) return fail(CTD_EINVAL, "not CTD-S factors");
+  if (S->real) return fail(CTD_ENOTSUP, "CTD-D takes integer counts");
   if (S->alpha != 1 && S->alpha != 2) return fail(CTD_EINVAL, "alpha must be 1 or 2 (time is mode 3)");
   if (!S->Coff || !S->have_err)
     return fail(CTD_EINVAL, "the CTD-S factors need C and the error (no skip flags)");

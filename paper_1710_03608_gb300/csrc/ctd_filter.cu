@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256)
                  const int32_t* __restrict__ ccol, const int32_t* __restrict__ cval,
                  const int* __restrict__ kpos, const int* __restrict__ sus_of,
                  const double* __restrict__ etaT, int ns, int init, int seg,
-                 double* __restrict__ part) {
+                 double* __restrict__ part, int real) {
   constexpr int CH = 32 * NPL;
   constexpr int EU = 8;  // entries whose eta loads are in flight together
   const int lane = threadIdx.x & 31;
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256)
         double v = 0.0;
         if (lane < cnt) {
           const int cc = ccol[base + lane];
-          v = (double)cval[base + lane];
+          v = value_f64(cval[base + lane], real);
           q = kpos[cc];
           sc = sus_of[cc];
         }
@@ -172,7 +172,7 @@ constexpr int RS_SEGS = 8;
 static ctd_status launch_resid_rows(int64_t n_rows, int du, const uint64_t* crp,
                                     const int32_t* ccol, const int32_t* cval, const int* kpos,
                                     const int* sus_of, const double* etaT, int ns, int init,
-                                    double* rbuf, Arena& scratch, cudaStream_t st) {
+                                    double* rbuf, int real, Arena& scratch, cudaStream_t st) {
   // at most RS_SEGS segments, and partials within 256 MB
   const int64_t per = std::max<int64_t>(1, n_rows * ns * (int64_t)sizeof(double));
   const int segs = (int)std::max<int64_t>(1, std::min<int64_t>(RS_SEGS, (256ll << 20) / per));
@@ -184,13 +184,13 @@ static ctd_status launch_resid_rows(int64_t n_rows, int du, const uint64_t* crp,
   const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(crp);
   if (ns <= 32)
     CTD_LAUNCH(k_resid_rows<1>, (g), (256), 0, st, n_rows, rp, ccol, cval, kpos, sus_of, etaT, ns,
-               init, seg, part);
+               init, seg, part, real);
   else if (ns <= 64)
     CTD_LAUNCH(k_resid_rows<2>, (g), (256), 0, st, n_rows, rp, ccol, cval, kpos, sus_of, etaT, ns,
-               init, seg, part);
+               init, seg, part, real);
   else
     CTD_LAUNCH(k_resid_rows<4>, (g), (256), 0, st, n_rows, rp, ccol, cval, kpos, sus_of, etaT, ns,
-               init, seg, part);
+               init, seg, part, real);
   CTD_LAUNCH(k_resid_combine, (grid_for(n_rows * ns, 256, (int64_t)num_sms() * 16)), (256), 0, st,
              n_rows, rp, ns, seg, part, init, rbuf);
   return CTD_OK;
@@ -243,7 +243,8 @@ __global__ void k_residual_dots(const unsigned long long* __restrict__ cptr,
                                 const int32_t* __restrict__ crow, const int32_t* __restrict__ cval,
                                 const int* __restrict__ kept_idx, int kept,
                                 const int* __restrict__ sus, int64_t n_rows,
-                                const double* __restrict__ rbuf, double* __restrict__ hK) {
+                                const double* __restrict__ rbuf, double* __restrict__ hK,
+                                int real) {
   const int c = blockIdx.x;
   const int k = sus[c];
   const int lane = threadIdx.x & 31;
@@ -258,7 +259,7 @@ __global__ void k_residual_dots(const unsigned long long* __restrict__ cptr,
       b = cptr[col + 1];
     }
     double s = 0.0;
-    for (unsigned long long q = a + lane; q < b; q += 32) s = fma((double)cval[q], r[crow[q]], s);
+    for (unsigned long long q = a + lane; q < b; q += 32) s = fma(value_f64(cval[q], real), r[crow[q]], s);
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) hK[j + (int64_t)c * kept] = s;
   }
@@ -401,7 +402,7 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
     const unsigned gt = grid_for((int64_t)kk * ns, 256, (int64_t)num_sms() * 8);
     if (kept > 0) CTD_LAUNCH(k_transpose_eta, (gt), (256), 0, st, eta, kept, ns, etaT);
     CTD_TRY(launch_resid_rows(in.n_rows, du, in.c_rowptr, in.c_col, in.c_val, kpos, sus_of, etaT,
-                              ns, 1, rbuf, scratch, st));
+                              ns, 1, rbuf, in.real, scratch, st));
     // minus Q gamma (Q = Qt^T, n_rows x dt)
     if (in.dt > 0)
       dgemm(true, false, in.n_rows, ns, in.dt, -1.0, in.Qt, in.ldq, gammaQ, in.dt, 1.0, rbuf,
@@ -430,7 +431,7 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
       if (kept > 0)
         CTD_LAUNCH(k_residual_dots, (dim3(ns, ny)), (256), 0, st,
                    reinterpret_cast<const unsigned long long*>(in.cptr), in.crow, in.cval, out.idx,
-                   kept, d_sus, in.n_rows, rbuf, hK);
+                   kept, d_sus, in.n_rows, rbuf, hK, in.real);
       if (in.dt > 0) {
         // h_Q = Q^T r; the candidates' part of the correction sees the
         // residual projected off Q: h_K - W_K^T h_Q
@@ -451,7 +452,7 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
       // r -= Xc[:, K] eta_d, then r -= Q (h_Q - W_K eta_d)
       if (kept > 0) CTD_LAUNCH(k_transpose_eta, (gt), (256), 0, st, etad, kept, ns, etaT);
       CTD_TRY(launch_resid_rows(in.n_rows, du, in.c_rowptr, in.c_col, in.c_val, kpos, sus_of,
-                                etaT, ns, 0, rbuf, scratch, st));
+                                etaT, ns, 0, rbuf, in.real, scratch, st));
       if (in.dt > 0) {
         if (kept > 0)
           dgemm(false, false, in.dt, ns, kept, -1.0, WK, in.dt, etad, kept, 1.0, hQ, in.dt, st);

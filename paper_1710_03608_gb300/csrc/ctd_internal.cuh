@@ -186,6 +186,25 @@ inline ModeMap make_mode_map(const int64_t dims[3], int alpha) {
   return m;
 }
 
+// The sampling weight of one value of X (Eq. 1's summand).  Integer counts
+// (wshift == WSHIFT_INT): the exact square.  Real values (the 32-bit payload
+// holds an FP32 value): the square on a fixed-point grid, floor(v^2 *
+// 2^wshift), with 2^-wshift = 2^(E - 32) where 2^E bounds the largest
+// square (reading A28); v^2 is exact in FP64 and the scaling is a power of
+// two, so the weight is exact and the same on every device.
+constexpr int WSHIFT_INT = -0x7fffffff - 1;
+__device__ __forceinline__ unsigned long long sample_weight(int32_t bits, int wshift) {
+  if (wshift == WSHIFT_INT) return (unsigned long long)((long long)bits * (long long)bits);
+  const double f = (double)__int_as_float(bits);
+  return (unsigned long long)floor(ldexp(f * f, wshift));
+}
+
+// A value of X (or R) as FP64: an integer count, or (real) the FP32 value
+// its 32-bit payload holds.
+__device__ __forceinline__ double value_f64(int32_t bits, int real) {
+  return real ? (double)__int_as_float(bits) : (double)bits;
+}
+
 // K1a: entries per column (colcnt) and per row (rowcnt) of X_(alpha);
 // both zeroed beforehand.  Out-of-range indices set DEV_BAD_INDEX.
 void launch_count(const CooDev& X, uint32_t* colcnt, uint32_t* rowcnt, unsigned* status,
@@ -199,7 +218,7 @@ void launch_count(const CooDev& X, uint32_t* colcnt, uint32_t* rowcnt, unsigned*
 // A total at or past 2^63 sets DEV_OVERFLOW.
 void launch_sqnorms_cdf(const uint64_t* colptr, const int32_t* val, int64_t n_cols,
                         uint64_t* norm2, uint64_t* cdf, unsigned* minkey, uint64_t* tmp,
-                        unsigned* status, cudaStream_t st);
+                        unsigned* status, cudaStream_t st, int wshift = WSHIFT_INT);
 
 // K2: prefix sums.  out[n] (inclusive) or out[n+1] (exclusive, out[0]=0).
 // `tmp` needs scan_tmp_elems(n) entries.  Sums are saturating u64 adds; a
@@ -352,6 +371,28 @@ ctd_status launch_heavy_columns(const int64_t* list, const unsigned* nlist, int6
                                 const double* Qt, int64_t ld, int64_t d, double* W,
                                 double* norms, Arena& scratch, cudaStream_t st);
 
+// *out = the sum of in[0 .. n) in a fixed order (the same on every run).
+ctd_status sum_f64(const double* in, int64_t n, double* out, Arena& scratch, cudaStream_t st);
+
+// ctd_real.cu: the stages of Algorithm 1 that differ for real (FP32) values.
+ctd_status real_weight_shift(const int32_t* v, int64_t nnz, int* wshift, Arena& scratch,
+                             cudaStream_t st);
+ctd_status real_sqnorm(const int32_t* v, int64_t nnz, double* out, Arena& scratch,
+                       cudaStream_t st);
+ctd_status real_gram(const uint64_t* cptr, const int32_t* crow, const int32_t* cval,
+                     const int* nc_dev, int su, int64_t n_rows, double* G, Arena& scratch,
+                     cudaStream_t st);
+ctd_status real_c_fill(const CscDev& X, int64_t n_cols, const CsrDev& R, const uint64_t* coff,
+                       uint32_t* ccnt, uint16_t* crow, void* cval, int fp32, cudaStream_t st);
+ctd_status real_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows,
+                            const uint64_t* Rcolptr, const int32_t* Rrow, const int32_t* Rval,
+                            int kept, const double* Z, int64_t ldz, double* out, Arena& scratch,
+                            cudaStream_t st);
+// Algorithm 1 on a staged tensor; real: the values' payloads are FP32.
+ctd_status static_impl(const CooDev& X, int64_t s, double eps, uint64_t seed, int precision,
+                       unsigned flags, cudaStream_t st, Arena& scratch, int real,
+                       ctd_factors** out);
+
 // ctd_dense.cu -------------------------------------------------------------
 // C = alpha op(A) op(B) + beta C, column-major FP64.
 void dgemm(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
@@ -452,7 +493,7 @@ struct Matricized {
 // success norm2 holds the squared norms and tmp the scan's tile and warp
 // sums (finish with launch_scan_finish).
 ctd_status matricize_bucketed(const CooDev& X, Arena& A, cudaStream_t st, Matricized* M,
-                              bool* used);
+                              bool* used, int wshift = WSHIFT_INT);
 // The smallest value from its order-preserving code (INT32_MAX when X has
 // no entries).
 inline int decode_min(unsigned key) { return (int)(key ^ 0x80000000u); }
@@ -462,8 +503,10 @@ inline int decode_max(unsigned key) { return (int)(~key ^ 0x80000000u); }
 // squared column norms and their CDF.  sort_cols: put each column's entries
 // in (row, value) order (CTD_DETERMINISTIC).  dist (optional): the arena
 // that receives norm2 and cdf (so a caller can keep them); A otherwise.
+// wshift: WSHIFT_INT for integer counts, else the real values' weight grid
+// (sample_weight).
 ctd_status matricize(const CooDev& X, Arena& A, cudaStream_t st, Matricized* M,
-                     bool sort_cols = false, Arena* dist = nullptr);
+                     bool sort_cols = false, Arena* dist = nullptr, int wshift = WSHIFT_INT);
 
 // ctd_filter.cu: the independence filter over a block of du candidates.
 // S (du x du, ld du) holds the candidates' Schur complement against R^(t)
@@ -491,6 +534,7 @@ struct FilterIn {
   const int32_t* c_col = nullptr;
   const int32_t* c_val = nullptr;
   int64_t n_rows = 0;
+  int real = 0;  // the values' payloads hold FP32 values (else integer counts)
 };
 // keep[du], idx[kept] (device), count (device, = kept), Lk = factor of the
 // kept block (kept x kept, lower), Li = Lk^{-1}.
@@ -523,6 +567,8 @@ struct ctd_factors {
   // sizes
   int64_t s = 0, s_unique = 0, s_kept = 0, nnz_R = 0, nnz_C = 0, nnz_X = 0;
   uint64_t T = 0;
+  bool real = false;             // the values (of X and R) are FP32, not integer counts
+  double sqnorm_real = 0.0;      // real values: ||X||_F^2 in FP64
   int min_val = 0;               // CTD-S: the smallest value of X (positive values allow the
                                  // C fill's row copies)
   double err = 0.0;

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(MQ_THREADS, 2)
                const int32_t* __restrict__ stg_val, unsigned long long* __restrict__ colptr,
                int32_t* __restrict__ csc_row, int32_t* __restrict__ csc_val,
                unsigned long long* __restrict__ norm2, unsigned long long* __restrict__ tile_sum,
-               unsigned long long* __restrict__ warp_sums, unsigned* minkey) {
+               unsigned long long* __restrict__ warp_sums, unsigned* minkey, int wshift) {
   extern __shared__ unsigned sq[];
   unsigned* cnt = sq;                                          // [MB_W]
   int32_t* o_row = reinterpret_cast<int32_t*>(cnt + MB_W);     // [MQ_CAP]
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(MQ_THREADS, 2)
         const int v = vals[a + q];
         vmin = min(vmin, v);
         vmax = max(vmax, v);
-        nrm = sat_add64(nrm, (unsigned long long)((long long)v * (long long)v));
+        nrm = sat_add64(nrm, sample_weight(v, wshift));
       }
     unsigned longs = __ballot_sync(0xffffffffu, len > 32);
     while (longs) {
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(MQ_THREADS, 2)
         const int v = vals[p];
         vmin = min(vmin, v);
         vmax = max(vmax, v);
-        part = sat_add64(part, (unsigned long long)((long long)v * (long long)v));
+        part = sat_add64(part, sample_weight(v, wshift));
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) part = sat_add64(part, __shfl_xor_sync(0xffffffffu, part, o));
@@ -410,7 +410,7 @@ static_assert(MQ_THREADS / 32 == 2 * SCAN_WARPS, "a place block covers two scan 
 // needs, when it does not suit.  M's arrays are allocated by the caller;
 // rowcnt, status and minval are zeroed / initialized by the caller.
 ctd_status matricize_bucketed(const CooDev& X, Arena& A, cudaStream_t st, Matricized* M,
-                              bool* used) {
+                              bool* used, int wshift) {
   *used = false;
   const int64_t nb64 = (M->n_cols + MB_W - 1) / MB_W;
   if (X.nnz == 0 || nb64 < 2 * (int64_t)num_sms() || nb64 > MB_MAX_BUCKETS) return CTD_OK;
@@ -475,7 +475,7 @@ ctd_status matricize_bucketed(const CooDev& X, Arena& A, cudaStream_t st, Matric
                reinterpret_cast<const unsigned long long*>(bstart), nb, M->n_cols, stg_lc,
                stg_row, stg_val, reinterpret_cast<unsigned long long*>(M->colptr), M->csc_row,
                M->csc_val, reinterpret_cast<unsigned long long*>(M->norm2), ts, ts + ntiles + 2,
-               M->minval);
+               M->minval, wshift);
   }
   *used = true;
   return CTD_OK;

@@ -62,6 +62,12 @@ extern "C" ctd_status ctd_static_nway(const ctd_coon* X, int alpha, int64_t s, d
   if (X->nnz < 0 || X->nnz > INT32_MAX) return fail(CTD_EINVAL, "nnz must be in [0, 2^31)");
   if (X->memory != CTD_MEM_DEVICE && X->memory != CTD_MEM_HOST)
     return fail(CTD_EINVAL, "unknown memory kind");
+  if (X->val_type != CTD_VAL_INT32 && X->val_type != CTD_VAL_FP32)
+    return fail(CTD_EINVAL, "unknown value type");
+  if (s < 1 || s > 8192) return fail(CTD_EINVAL, "s must be in [1, 8192]");
+  if (!(eps >= 0.0 && eps < 1.0)) return fail(CTD_EINVAL, "eps must be in [0, 1)");
+  if (precision != CTD_FP64 && precision != CTD_FP32_BULK)
+    return fail(CTD_EINVAL, "unknown precision");
   NwayMap m{};
   m.order = N;
   m.alpha = alpha;
@@ -89,7 +95,8 @@ extern "C" ctd_status ctd_static_nway(const ctd_coon* X, int alpha, int64_t s, d
   CTD_TRY(scratch.get(&buf, 4 * (size_t)std::max<int64_t>(ld, 1)));
   CTD_TRY(scratch.get(&status, 1));
   CTD_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
-  const int32_t* src_val = X->val;
+  // values move as 32-bit payloads (int32 counts or FP32 bits)
+  const int32_t* src_val = static_cast<const int32_t*>(X->val);
   if (X->memory == CTD_MEM_HOST && nnz > 0) {
     // the index arrays and values copied in, then mapped on the device
     int32_t* in;
@@ -113,15 +120,17 @@ extern "C" ctd_status ctd_static_nway(const ctd_coon* X, int alpha, int64_t s, d
   CTD_CUDA(cudaGetLastError());
   CTD_TRY(sync(st));
   if (h_status & DEV_BAD_INDEX) return fail(CTD_EINVAL, "an index is outside its mode");
-  ctd_coo3 x3{};
+  CooDev x3;
   x3.dims[0] = X->dims[alpha - 1];
   x3.dims[1] = n_cols;
   x3.dims[2] = 1;
+  x3.alpha = 1;
   x3.nnz = nnz;
   x3.i = buf;
   x3.j = buf + ld;
   x3.k = buf + 2 * ld;
-  x3.val = buf + 3 * ld;
-  x3.memory = CTD_MEM_DEVICE;
-  return ctd_static(&x3, 1, s, eps, seed, precision, flags, stream, out);
+  x3.v = buf + 3 * ld;
+  PhaseScope ph_call("call", st);
+  return static_impl(x3, s, eps, seed, precision, flags, st, scratch,
+                     X->val_type == CTD_VAL_FP32, out);
 }

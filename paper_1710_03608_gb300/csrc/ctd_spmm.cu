@@ -861,7 +861,7 @@ __global__ void k_add2(const double* __restrict__ a, const double* __restrict__ 
 }
 
 // *out = sum of n doubles, in an order fixed by n alone
-static ctd_status sum_f64(const double* in, int64_t n, double* out, Arena& scratch,
+ctd_status sum_f64(const double* in, int64_t n, double* out, Arena& scratch,
                           cudaStream_t st) {
   if (n <= 8192) {
     CTD_LAUNCH(k_sum_f64_fixed, (1), (1024), 0, st, in, n, out);

@@ -285,7 +285,8 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32)
                      const int32_t* __restrict__ val, int64_t n,
                      unsigned long long* __restrict__ norm2,
                      unsigned long long* __restrict__ tile_sum,
-                     unsigned long long* __restrict__ warp_sums, unsigned* minkey) {
+                     unsigned long long* __restrict__ warp_sums, unsigned* minkey,
+                     int wshift) {
   const unsigned FULL = 0xffffffffu;
   __shared__ unsigned long long ws[SCAN_WARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32)
         const int v = __ldg(val + a + t);
         vmin = min(vmin, v);
         vmax = max(vmax, v);
-        mine = sat_add(mine, (unsigned long long)((long long)v * (long long)v));
+        mine = sat_add(mine, sample_weight(v, wshift));
       }
     unsigned longs = __ballot_sync(FULL, len > 32);
     while (longs) {
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32)
         const int v = __ldg(val + p);
         vmin = min(vmin, v);
         vmax = max(vmax, v);
-        part = sat_add(part, (unsigned long long)((long long)v * (long long)v));
+        part = sat_add(part, sample_weight(v, wshift));
       }
       part = warp_sat_sum(part);
       if (lane == c) mine = part;
@@ -353,14 +354,15 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32)
 
 void launch_sqnorms_cdf(const uint64_t* colptr, const int32_t* val, int64_t n, uint64_t* norm2,
                         uint64_t* cdf, unsigned* minkey, uint64_t* tmp, unsigned* status,
-                        cudaStream_t st) {
+                        cudaStream_t st, int wshift) {
   if (n == 0) return;
   const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   unsigned long long* ts = reinterpret_cast<unsigned long long*>(tmp);
   unsigned long long* wsums = ts + ntiles + 2;
   unsigned long long* nn = reinterpret_cast<unsigned long long*>(norm2);
   CTD_LAUNCH(k_sqnorms_reduce, ((unsigned)ntiles), (SCAN_WARPS * 32), 0, st,
-             reinterpret_cast<const unsigned long long*>(colptr), val, n, nn, ts, wsums, minkey);
+             reinterpret_cast<const unsigned long long*>(colptr), val, n, nn, ts, wsums, minkey,
+             wshift);
   CTD_LAUNCH(k_scan_tiles, (1), (1024), 0, st, ts, ntiles, status);
   CTD_LAUNCH(k_scan_apply<unsigned long long>, ((unsigned)ntiles), (SCAN_WARPS * 32), 0, st, nn,
              reinterpret_cast<unsigned long long*>(cdf), n, ts, wsums, true, (uint32_t*)nullptr);

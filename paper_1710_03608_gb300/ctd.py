@@ -37,7 +37,7 @@ EXPORTED = ["ctd_static", "ctd_dynamic_create", "ctd_dynamic_step", "ctd_error",
             "ctd_server_wait", "ctd_server_result", "ctd_server_state", "ctd_server_free",
             "ctd_ddos_candidates", "ctd_dynamic_from_static", "ctd_fault_inject_alloc",
             "ctd_selftest_bounded_wait", "ctd_set_allocator", "ctd_allocated_bytes",
-            "ctd_static_nway"]
+            "ctd_static_nway", "ctd_get_R_f64"]
 
 
 class CtdError(RuntimeError):
@@ -54,11 +54,14 @@ class ctd_coo3(C.Structure):
 
 
 CTD_MAX_ORDER = 8
+CTD_VAL_INT32 = 0
+CTD_VAL_FP32 = 1
 
 
 class ctd_coon(C.Structure):
     _fields_ = [("order", C.c_int32), ("dims", C.c_int64 * CTD_MAX_ORDER), ("nnz", C.c_int64),
-                ("idx", C.c_void_p * CTD_MAX_ORDER), ("val", C.c_void_p), ("memory", C.c_int32)]
+                ("idx", C.c_void_p * CTD_MAX_ORDER), ("val", C.c_void_p), ("memory", C.c_int32),
+                ("val_type", C.c_int32)]
 
 
 class ctd_sizes(C.Structure):
@@ -91,6 +94,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ctd_get_samples": [P, P, P],
         "ctd_get_fibers": [P, P, P],
         "ctd_get_R": [P, P, P, P],
+        "ctd_get_R_f64": [P, P, P, P],
         "ctd_get_U": [P, P],
         "ctd_get_C_columns": [P, I64, P, P],
         "ctd_get_C": [P, P, P, P],
@@ -221,8 +225,9 @@ class Coo:
 
 class CooN:
     """An N-way COO descriptor (ctd_coon) over N index arrays and the values:
-    torch CUDA int32 tensors or numpy int32 arrays (host).  Keeps references
-    so the buffers outlive the call."""
+    torch CUDA tensors or numpy arrays (host), indices int32, values int32
+    counts or float32 real values.  Keeps references so the buffers outlive
+    the call."""
 
     def __init__(self, dims, idx, val):
         self.dims = tuple(int(d) for d in dims)
@@ -230,22 +235,28 @@ class CooN:
             raise ValueError("one index array per mode, 1 .. CTD_MAX_ORDER modes")
         self._keep = (*idx, val)
         host = isinstance(val, np.ndarray)
-        for a in self._keep:
+        self.real = str(val.dtype) in ("float32", "torch.float32")
+        for n, a in enumerate(self._keep):
+            want = ("float32" if self.real and n == len(idx) else "int32")
             if host:
-                if not isinstance(a, np.ndarray) or a.dtype != np.int32 or not a.flags.c_contiguous:
-                    raise TypeError("host COO arrays must be contiguous int32")
-            elif str(a.dtype) != "torch.int32" or not a.is_contiguous() or not a.is_cuda:
-                raise TypeError("device COO tensors must be contiguous CUDA int32")
+                if not isinstance(a, np.ndarray) or str(a.dtype) != want or not a.flags.c_contiguous:
+                    raise TypeError(f"host COO arrays must be contiguous {want}")
+            elif str(a.dtype) != "torch." + want or not a.is_contiguous() or not a.is_cuda:
+                raise TypeError(f"device COO tensors must be contiguous CUDA {want}")
         N = len(self.dims)
         d = (C.c_int64 * CTD_MAX_ORDER)(*self.dims, *([1] * (CTD_MAX_ORDER - N)))
         ix = (C.c_void_p * CTD_MAX_ORDER)(*[_ptr(a) for a in idx], *([None] * (CTD_MAX_ORDER - N)))
         self.desc = ctd_coon(N, d, int(val.shape[0]), ix, _ptr(val),
-                             CTD_MEM_HOST if host else CTD_MEM_DEVICE)
+                             CTD_MEM_HOST if host else CTD_MEM_DEVICE,
+                             CTD_VAL_FP32 if self.real else CTD_VAL_INT32)
 
     @staticmethod
     def from_arrays(dims, idx, val, device: bool = True) -> "CooN":
-        """From numpy index arrays and values (copied to the GPU if device)."""
-        arrs = [np.ascontiguousarray(a, dtype=np.int32) for a in (*idx, val)]
+        """From numpy index arrays and values (copied to the GPU if device);
+        floating-point values become float32 real values, others int32."""
+        vdt = np.float32 if np.issubdtype(np.asarray(val).dtype, np.floating) else np.int32
+        arrs = [np.ascontiguousarray(a, dtype=np.int32) for a in idx]
+        arrs.append(np.ascontiguousarray(val, dtype=vdt))
         if device:
             import torch
             arrs = [torch.from_numpy(a).cuda() for a in arrs]
@@ -255,8 +266,9 @@ class CooN:
 class Factors:
     """Owns a ctd_factors handle; getters copy to host numpy arrays."""
 
-    def __init__(self, handle: int):
+    def __init__(self, handle: int, real: bool = False):
         self.h = C.c_void_p(handle)
+        self.real = real
 
     def __del__(self):
         try:
@@ -305,14 +317,18 @@ class Factors:
         s = self.sizes()
         p = np.empty(s.s_kept + 1, np.int64)
         r = np.empty(s.nnz_R, np.int32)
-        v = np.empty(s.nnz_R, np.int32)
-        _check(load().ctd_get_R(self.h, _ptr(p), _ptr(r), _ptr(v)))
+        if self.real:
+            v = np.empty(s.nnz_R, np.float64)
+            _check(load().ctd_get_R_f64(self.h, _ptr(p), _ptr(r), _ptr(v)))
+        else:
+            v = np.empty(s.nnz_R, np.int32)
+            _check(load().ctd_get_R(self.h, _ptr(p), _ptr(r), _ptr(v)))
         return p, r, v
 
     def R_dense(self):
         s = self.sizes()
         p, r, v = self.R()
-        out = np.zeros((s.n_rows, s.s_kept), np.int64)
+        out = np.zeros((s.n_rows, s.s_kept), np.float64 if self.real else np.int64)
         for c in range(s.s_kept):
             out[r[p[c]:p[c + 1]], c] = v[p[c]:p[c + 1]]
         return out
@@ -380,7 +396,7 @@ def ctd_static_nway(X: CooN, alpha: int, s: int, eps: float, seed: int = 0,
     st = _stream_handle(stream) if not host or stream is not None else _default_stream()
     _check(lib.ctd_static_nway(C.byref(X.desc), int(alpha), int(s), float(eps), int(seed),
                                int(precision), int(flags), C.c_void_p(st), C.byref(out)))
-    return Factors(out.value)
+    return Factors(out.value, real=X.real)
 
 
 def ctd_static_batched(Xs, alpha: int, s, seeds, eps: float, precision: int = CTD_FP64,

@@ -390,3 +390,14 @@ def nway_uniform(dims, nnz: int, seed: int, vmax: int = 5, signed: bool = False)
     if signed:
         val = val * rng.choice([-1, 1], size=nnz)
     return idx, np.ascontiguousarray(val, dtype=np.int32)
+
+
+def nway_real(dims, nnz: int, seed: int, spread: float = 1.5):
+    """An N-way tensor with `nnz` distinct uniform coordinates and real FP32
+    values sign * exp(N(0, spread^2)) (magnitudes spread over several
+    octaves): (list of N int32 index arrays, float32 values)."""
+    idx, _ = nway_uniform(dims, nnz, seed)
+    rng = np.random.default_rng([seed, 0xF32])
+    mag = np.exp(rng.normal(0.0, spread, size=nnz))
+    val = mag * rng.choice([-1.0, 1.0], size=nnz)
+    return idx, np.ascontiguousarray(val, dtype=np.float32)

@@ -39,3 +39,15 @@ def tie_margin(ratios, eps):
     """Smallest distance of a residual ratio ||res||/||x|| to eps (reading A14)."""
     r = np.asarray(ratios, dtype=np.float64)
     return float(np.min(np.abs(r - eps))) if r.size else np.inf
+
+
+def error_tol_real(e_ref, R):
+    """Bar for the error of real-valued tensors.  The Gram matrix of real
+    values is not exact, so the Q-form (Q = R L^{-T} from its Cholesky
+    factor) loses orthogonality in proportion to kappa(R^T R): its error is
+    within 4 n u kappa(R^T R) (n = rows of R, u = 2^-53; the factor covers
+    the Gram's and the factorization's backward errors), on top of the
+    FP64 bar (reading A29)."""
+    R = np.asarray(R, dtype=np.float64)
+    kappa = np.linalg.cond(R.T @ R) if R.shape[1] else 1.0
+    return max(error_tol(0, e_ref), 4.0 * R.shape[0] * 2.0 ** -53 * kappa)
