@@ -21,6 +21,7 @@
 // only then.  Which rows are dense changes the order of integer additions
 // only, so the result does not depend on the selection.
 #include <algorithm>
+#include <cstdlib>
 #include <type_traits>
 
 #include "ctd_expand.cuh"
@@ -51,18 +52,37 @@ __global__ void k_row_len_hist(const unsigned long long* __restrict__ rowptr, in
 }
 
 // thr[0] = the smallest length L >= minlen with #rows(len >= L) <= hmax
-// (width + 1 if none qualifies)
+// (width + 1 if none qualifies).  One warp walks the lengths down from
+// `width` 32 at a time: a prefix sum over the lanes gives #rows(len >= L)
+// for each lane's L, and the first lane past hmax ends the walk (the count
+// only grows as L falls).
 __global__ void k_pick_len(const unsigned* __restrict__ hist, int width, int minlen, int hmax,
                            int* __restrict__ thr) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  unsigned above = 0;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  unsigned long long carry = 0;
   int L = width + 1;
-  for (int len = width; len >= minlen; --len) {
-    if (above + hist[len] > (unsigned)hmax) break;
-    above += hist[len];
-    L = len;
+  for (int top = width; top >= minlen; top -= 32) {
+    const int len = top - lane;
+    unsigned long long x = len >= minlen ? hist[len] : 0ull;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
+    }
+    const bool over = len >= minlen && carry + x > (unsigned long long)hmax;
+    const unsigned ob = __ballot_sync(0xffffffffu, over);
+    const unsigned ok = __ballot_sync(0xffffffffu, len >= minlen && !over);
+    if (ob) {
+      // lanes before the first one over are fine: the last of them is L
+      const int first = __ffs(ob) - 1;
+      if (first > 0) L = top - (first - 1);
+      break;
+    }
+    if (ok) L = top - (31 - __clz(ok));  // every length of this chunk is fine
+    carry += __shfl_sync(0xffffffffu, x, 31);
   }
-  thr[0] = L;
+  if (lane == 0) thr[0] = L;
 }
 
 // slot[i] in [0, H) for the rows with len >= thr, -1 otherwise; rows[slot] = i
@@ -136,13 +156,21 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     int kind[CL_ITEMS];
     unsigned off[CL_ITEMS];
+    // every item's offsets first, so their loads are in flight together
+    unsigned long long ubs[CL_ITEMS], nxs[CL_ITEMS];
+#pragma unroll
+    for (int u = 0; u < CL_ITEMS; ++u) {
+      const int64_t f = b0 + (int64_t)u * blockDim.x + threadIdx.x;
+      ubs[u] = f < n_cols ? coff[f + 1] - coff[f] : 0ull;
+      nxs[u] = f < n_cols ? xp[f + 1] - xp[f] : 0ull;
+    }
 #pragma unroll
     for (int u = 0; u < CL_ITEMS; ++u) {
       const int64_t f = b0 + (int64_t)u * blockDim.x + threadIdx.x;
       int k = -1;  // -1 none, 0 single, 1 heavy, 2 multi
       if (f < n_cols) {
-        const unsigned long long ub = coff[f + 1] - coff[f];
-        const unsigned long long nx = xp[f + 1] - xp[f];
+        const unsigned long long ub = ubs[u];
+        const unsigned long long nx = nxs[u];
         if (ub == 0) {
           ccnt[f] = 0;
         } else if (nx == 1 && positive) {
@@ -255,14 +283,13 @@ __device__ __forceinline__ void put_quad<double>(uint16_t* crow, double* cval, u
 // inclusive prefix sums of nq), CP_UNROLL rounds of loads in flight before
 // their stores.  The L2 latency of the image loads is then paid once per
 // 32 * CP_UNROLL quads instead of once or twice per row.
-constexpr int CP_UNROLL = 4;
 
 __device__ __forceinline__ unsigned long long shfl64(unsigned long long x, int src) {
   return __shfl_sync(0xffffffffu, x, src);
 }
 
-template <typename V>
-__global__ void __launch_bounds__(256)
+template <typename V, int UNR, int MINB>
+__global__ void __launch_bounds__(256, MINB)
     k_copy_flat(CscDev X, const unsigned long long* __restrict__ rp,
                 const unsigned long long* __restrict__ ip, const uint16_t* __restrict__ icol,
                 const int* __restrict__ ival, int64_t P, const int64_t* __restrict__ single,
@@ -296,13 +323,13 @@ __global__ void __launch_bounds__(256)
     }
     const int excl = incl - nq;
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    for (int g0 = 0; g0 < total; g0 += 32 * CP_UNROLL) {
-      ushort4 c[CP_UNROLL];
-      int4 w[CP_UNROLL];
-      unsigned long long oq[CP_UNROLL];
-      int lo[CP_UNROLL], hi[CP_UNROLL], vv[CP_UNROLL];
+    for (int g0 = 0; g0 < total; g0 += 32 * UNR) {
+      ushort4 c[UNR];
+      int4 w[UNR];
+      unsigned long long oq[UNR];
+      int lo[UNR], hi[UNR], vv[UNR];
 #pragma unroll
-      for (int u = 0; u < CP_UNROLL; ++u) {
+      for (int u = 0; u < UNR; ++u) {
         const int g = g0 + 32 * u + lane;
         const int gg = min(g, total - 1);
         // e = number of entries whose run ends at or before quad gg
@@ -326,7 +353,7 @@ __global__ void __launch_bounds__(256)
         }
       }
 #pragma unroll
-      for (int u = 0; u < CP_UNROLL; ++u) {
+      for (int u = 0; u < UNR; ++u) {
         if (hi[u] <= 0) continue;
         const int ve = vv[u];
         const V a0 = (V)(ve * w[u].x), a1 = (V)(ve * w[u].y), a2 = (V)(ve * w[u].z),
@@ -746,8 +773,10 @@ ctd_status cf_all(int nq, int db, bool p4, const CscDev& X, int64_t n_cols, int6
              n_rows, ip, P, icol, ival);
   {
     PhaseScope ph("c_fill_copy", st);
-    CTD_LAUNCH(k_copy_flat<V>, (num_sms() * 8), (256), 0, st, X, rp, ip, icol, ival, P, single,
-               counts, coff, ccnt, crow, cval);
+    // four rounds of loads in flight; tighter register bounds (more warps
+    // per SM) measured no faster: the copy is bound by its stores
+    CTD_LAUNCH((k_copy_flat<V, 4, 1>), (num_sms() * 8), (256), 0, st, X, rp, ip, icol, ival, P,
+               single, counts, coff, ccnt, crow, cval);
   }
   PhaseScope ph("c_fill_multi", st);
 #define CF_GO(NQV, DBV, P4V)                                                                  \
