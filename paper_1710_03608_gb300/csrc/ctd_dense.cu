@@ -479,6 +479,8 @@ ctd_status launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr
   int per_sm = 0;
   CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_coop, 256, 0));
   if (per_sm <= 0) return fail(CTD_ECUDA, "the skip-Cholesky kernel cannot be resident");
+  // one block per SM: measured on the 10^7-nonzero tensor (s' = 498), 152
+  // blocks took 0.81 ms, 304 (two per SM) 0.97, 76 0.85, 38 0.97, 19 1.22
   const int nblocks = num_sms();
   void* args[] = {&A, &n, &lda, const_cast<double**>(&thr), const_cast<int**>(&force),
                   const_cast<double**>(&fpiv), &keep, &piv, &status, &gb};
