@@ -754,9 +754,9 @@ ctd_status cf_all(int nq, int db, bool p4, const CscDev& X, int64_t n_cols, int6
   // row images (see k_img_sizes): P entries per image, a multiple of 4
   unsigned long long *sz, *ip, *stmp;
   unsigned* sstat;
-  CTD_TRY(a.get(&sz, n_rows + 1));
+  CTD_TRY(a.get(&sz, n_rows));
   CTD_TRY(a.get(&ip, n_rows + 1));
-  CTD_TRY(a.get(&stmp, scan_tmp_elems(n_rows + 1)));
+  CTD_TRY(a.get(&stmp, scan_tmp_elems(n_rows)));
   CTD_TRY(a.get(&sstat, 1));
   const int64_t P = (R.nnz + 6 * n_rows + 3) & ~(int64_t)3;
   uint16_t* icol;
@@ -765,10 +765,10 @@ ctd_status cf_all(int nq, int db, bool p4, const CscDev& X, int64_t n_cols, int6
   CTD_TRY(a.get(&ival, 4 * P));
   const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
   const unsigned g = grid_for(n_rows, 256, (int64_t)num_sms() * 4);
-  CTD_CUDA(cudaMemsetAsync(sz + n_rows, 0, sizeof(unsigned long long), st));
   CTD_LAUNCH(k_img_sizes, (g), (256), 0, st, rp, n_rows, sz);
+  // exclusive: n_rows + 1 outputs, ip[n_rows] = the images' total
   launch_scan_u64(reinterpret_cast<const uint64_t*>(sz), reinterpret_cast<uint64_t*>(ip),
-                  n_rows + 1, false, reinterpret_cast<uint64_t*>(stmp), sstat, st);
+                  n_rows, false, reinterpret_cast<uint64_t*>(stmp), sstat, st);
   CTD_LAUNCH(k_img_fill, (grid_for(n_rows * 32, 256, (int64_t)num_sms() * 8)), (256), 0, st, R,
              n_rows, ip, P, icol, ival);
   {
