@@ -189,6 +189,47 @@ ctd_status sync(cudaStream_t st) {
   return CTD_OK;
 }
 
+namespace {
+thread_local SideStream t_side;
+}
+
+SideStream::~SideStream() {
+  // at thread exit; errors (a runtime already shut down) are of no use here
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
+  if (st) cudaStreamDestroy(st);
+}
+
+ctd_status SideStream::fork(cudaStream_t main) {
+  CTD_CUDA(cudaEventRecord(ev_fork, main));
+  CTD_CUDA(cudaStreamWaitEvent(st, ev_fork, 0));
+  return CTD_OK;
+}
+
+ctd_status SideStream::join(cudaStream_t main) {
+  CTD_CUDA(cudaEventRecord(ev_join, st));
+  CTD_CUDA(cudaStreamWaitEvent(main, ev_join, 0));
+  return CTD_OK;
+}
+
+ctd_status side_stream(SideStream** out) {
+  int dev = 0;
+  CTD_CUDA(cudaGetDevice(&dev));
+  SideStream& s = t_side;
+  if (s.dev != dev) {
+    if (s.ev_fork) cudaEventDestroy(s.ev_fork);
+    if (s.ev_join) cudaEventDestroy(s.ev_join);
+    if (s.st) cudaStreamDestroy(s.st);
+    s = SideStream();
+    CTD_CUDA(cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking));
+    CTD_CUDA(cudaEventCreateWithFlags(&s.ev_fork, cudaEventDisableTiming));
+    CTD_CUDA(cudaEventCreateWithFlags(&s.ev_join, cudaEventDisableTiming));
+    s.dev = dev;
+  }
+  *out = &s;
+  return CTD_OK;
+}
+
 // ---------------------------------------------------------------------------
 // batched small read-backs through pinned staging
 // ---------------------------------------------------------------------------
@@ -412,8 +453,11 @@ ctd_status static_impl(const CooDev& X, int64_t s, double eps, uint64_t seed, in
   for (int d = 0; d < 3; ++d) F->dims[d] = X.dims[d];
   F->nnz_X = X.nnz;
   F->s = s;
+  // the error's stream (set once it has work queued)
+  SideStream* side = nullptr;
   auto bail = [&](ctd_status rc) {
     cudaStreamSynchronize(st);
+    if (side) cudaStreamSynchronize(side->st);
     delete F;
     return rc;
   };
@@ -534,12 +578,17 @@ ctd_status static_impl(const CooDev& X, int64_t s, double eps, uint64_t seed, in
   int* idx = fo.idx;
   F->s_kept = kept;
 
-  // U = (R^T R)^{-1} = L^{-T} L^{-1}
+  // U = (R^T R)^{-1} = L^{-T} L^{-1}: an output only, so it is formed on
+  // the second stream (below) beside R's build and C's fill
   double* Z = fo.Li;
   STEP(F->mem.get(&F->U, (size_t)kept * kept));
-  {
-    PhaseScope ph("u_inverse", st);
-    u_from_linv(Z, kept, kept, F->U, kept, st);
+  if (kept > 0) {
+    SideStream* ss = nullptr;
+    STEP(side_stream(&ss));
+    STEP(ss->fork(st));
+    side = ss;
+    PhaseScope ph("u_inverse", side->st);
+    u_from_linv(Z, kept, kept, F->U, kept, side->st);
   }
 
   // R: kept columns of R', CSC and row-major
@@ -567,9 +616,26 @@ ctd_status static_impl(const CooDev& X, int64_t s, double eps, uint64_t seed, in
   CsrDev R{F->Rrowptr, F->Rcol, F->Rcval, kept};
   ph_r.reset();
 
-  // C = R^T X_(alpha), and Eq. (error).  The C capacity is read back
-  // while the error kernels (which do not need C) run, so the GPU does not
-  // idle across that read-back.
+  // Eq. (error): e = (T - ||Q^T X||_F^2) / T with Q = R L^{-T}.  It needs
+  // neither C nor C's capacity, so it runs on the second stream beside the
+  // read-back of that capacity and C's fill; the main stream joins that
+  // stream before the final read-back.
+  double* d_pu = nullptr;
+  Arena side_scratch;
+  if (!(flags & CTD_SKIP_ERROR) && kept > 0) {
+    STEP(scratch.get(&d_pu, 1));
+    STEP(side->fork(st));  // after R
+    side_scratch.st = side->st;
+    PhaseScope ph("error_qform", side->st);
+    if (real)
+      STEP(real_error_qform(M.csc(), M.n_cols, M.n_rows, F->Rcolptr, F->Rrow, F->Rval, kept, Z,
+                            kept, d_pu, side_scratch, side->st));
+    else
+      STEP(launch_error_qform(M.csc(), M.n_cols, M.n_rows, M.nnz, R, Z, kept, M.rowcnt,
+                              precision == CTD_FP32_BULK, d_pu, side_scratch, side->st));
+  }
+
+  // C = R^T X_(alpha)
   Readback rbc(st);
   uint64_t cap = 0, nnzR = 0;
   int rmax = -1;
@@ -594,18 +660,6 @@ ctd_status static_impl(const CooDev& X, int64_t s, double eps, uint64_t seed, in
     STEP(rbc.add(&nnzR, F->Rcolptr + kept, 1));
     STEP(rbc.add(&rmax, (const int*)d_rmax, 1));
     STEP(rbc.mark());
-  }
-  // Eq. (error): e = (T - ||Q^T X||_F^2) / T with Q = R L^{-T}
-  double* d_pu = nullptr;
-  if (!(flags & CTD_SKIP_ERROR) && kept > 0) {
-    STEP(scratch.get(&d_pu, 1));
-    PhaseScope ph("error_qform", st);
-    if (real)
-      STEP(real_error_qform(M.csc(), M.n_cols, M.n_rows, F->Rcolptr, F->Rrow, F->Rval, kept, Z,
-                            kept, d_pu, scratch, st));
-    else
-      STEP(launch_error_qform(M.csc(), M.n_cols, M.n_rows, M.nnz, R, Z, kept, M.rowcnt,
-                              precision == CTD_FP32_BULK, d_pu, scratch, st));
   }
   double* d_sq = nullptr;  // real values: ||X||_F^2 in FP64
   if (real) {
@@ -637,6 +691,7 @@ ctd_status static_impl(const CooDev& X, int64_t s, double eps, uint64_t seed, in
   if (F->Ccnt) launch_sum_u32(F->Ccnt, M.n_cols, d_nnzc, st, C_COUNT);
   uint64_t nnzC = 0, nnzR_final = 0;
   double pu = 0.0;
+  if (side) STEP(side->join(st));
   {
     Readback rb(st);
     STEP(rb.add(&nnzR_final, F->Rcolptr + kept, 1));

@@ -468,6 +468,21 @@ inline ctd_status d2h(T* host, const T* dev, size_t n, cudaStream_t st) {
   return d2h_bytes(host, dev, n * sizeof(T), st);
 }
 ctd_status sync(cudaStream_t st);
+
+// A second stream of the calling host thread (non-blocking, on the current
+// device, kept for the thread's lifetime) for work that can run beside the
+// main chain, with a fork and a join event.  fork(st) orders the side stream
+// after everything queued on st so far; join(st) orders st after everything
+// queued on the side stream so far.
+struct SideStream {
+  cudaStream_t st = nullptr;
+  ctd_status fork(cudaStream_t main);
+  ctd_status join(cudaStream_t main);
+  int dev = -1;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  ~SideStream();
+};
+ctd_status side_stream(SideStream** out);
 ctd_status stage_coo(const ctd_coo3* X, int alpha, Arena& scratch, cudaStream_t st, CooDev* out);
 
 // X_(alpha) by column plus its column distribution.
