@@ -395,6 +395,12 @@ ctd_status matricize(const CooDev& X, Arena& A, cudaStream_t st, Matricized* M, 
 
 using namespace ctd;
 
+// kpos[idx[p]] = p: the place of each kept candidate among the kept ones
+__global__ void k_kept_positions(const int* __restrict__ idx, int kept, int* __restrict__ kpos) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < kept; p += gridDim.x * blockDim.x)
+    kpos[idx[p]] = p;
+}
+
 // *out = max |val[e]| over the first *count entries (out zeroed beforehand)
 __global__ void k_abs_max(const int32_t* __restrict__ val, const uint64_t* __restrict__ count,
                           int* __restrict__ out) {
@@ -611,8 +617,15 @@ ctd_status static_impl(const CooDev& X, int64_t s, double eps, uint64_t seed, in
   STEP(F->mem.get(&F->Rcval, nnzR_cap));
   launch_gather_columns(M.colptr, M.csc_row, M.csc_val, F->fibers, fo.count, kept, F->Rcolptr,
                         F->Rrow, F->Rval, st);
-  STEP(build_csr_from_csc(F->Rcolptr, F->Rrow, F->Rval, kept, (int64_t)nnzR_cap, M.n_rows, 0,
-                          F->Rrowptr, F->Rcol, F->Rcval, scratch, st));
+  // R by row: the rows of R' (sorted by candidate) restricted to the kept
+  // candidates, each renumbered to its place among them
+  int* kpos;
+  STEP(scratch.get(&kpos, std::max(su, 1)));
+  STEPC(cudaMemsetAsync(kpos, 0xff, (size_t)std::max(su, 1) * sizeof(int), st));  // -1
+  if (kept > 0)
+    CTD_LAUNCH(k_kept_positions, (grid_for(kept, 256, 64)), (256), 0, st, idx, kept, kpos);
+  STEP(csr_keep_columns(rcr_ptr, rcr_col, rcr_val, M.n_rows, kpos, F->Rrowptr, F->Rcol,
+                        F->Rcval, scratch, st));
   CsrDev R{F->Rrowptr, F->Rcol, F->Rcval, kept};
   ph_r.reset();
 

@@ -275,6 +275,14 @@ void launch_gather_columns(const uint64_t* colptr, const int32_t* row, const int
 // Build a row-major copy (rowptr over n_rows, col, val) of a small CSC with
 // ncols columns whose column c gets index col_base + c; rows are sorted by
 // column.  nnz is an upper bound on the entries (sizes the temporaries).
+// The rows of a factor by row (rowptr, col, val; rows sorted by column)
+// restricted to the columns c with kpos[c] >= 0, renumbered to kpos[c]
+// (increasing on those columns): the output rows stay sorted.  rowptr_out:
+// n_rows + 1 entries; col_out / val_out: room for the kept entries.
+ctd_status csr_keep_columns(const uint64_t* rowptr, const int32_t* col, const int32_t* val,
+                            int64_t n_rows, const int* kpos, uint64_t* rowptr_out,
+                            int32_t* col_out, int32_t* val_out, Arena& scratch,
+                            cudaStream_t st);
 ctd_status build_csr_from_csc(const uint64_t* colptr, const int32_t* row, const int32_t* val,
                               int64_t ncols, int64_t nnz, int64_t n_rows, int col_base,
                               uint64_t* rowptr_out, int32_t* col_out, int32_t* val_out,

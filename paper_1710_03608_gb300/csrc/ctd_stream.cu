@@ -874,6 +874,77 @@ ctd_status build_csr_from_csc(const uint64_t* colptr, const int32_t* row, const 
   return CTD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// A factor by row restricted to a subset of its columns (R from R'): row i
+// keeps the entries whose column c has kpos[c] >= 0, renumbered to kpos[c].
+// kpos is increasing on the kept columns, so rows sorted by column stay
+// sorted.  A warp per row; a kept entry's place is the count of kept
+// entries before it (ballots), so the order is that of the input row.
+// ---------------------------------------------------------------------------
+__global__ void k_rsub_counts(const unsigned long long* __restrict__ rowptr,
+                              const int32_t* __restrict__ col, const int* __restrict__ kpos,
+                              int64_t n_rows, unsigned* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = gw; i < n_rows; i += nw) {
+    const unsigned long long a = rowptr[i], b = rowptr[i + 1];
+    unsigned c = 0;
+    for (unsigned long long p = a + lane; p - lane < b; p += 32) {
+      const bool k = p < b && kpos[col[p]] >= 0;
+      c += __popc(__ballot_sync(0xffffffffu, k));
+    }
+    if (lane == 0) cnt[i] = c;
+  }
+}
+
+__global__ void k_rsub_write(const unsigned long long* __restrict__ rowptr,
+                             const int32_t* __restrict__ col, const int32_t* __restrict__ val,
+                             const int* __restrict__ kpos, int64_t n_rows,
+                             const unsigned long long* __restrict__ rowptr_out,
+                             int32_t* __restrict__ col_out, int32_t* __restrict__ val_out) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = gw; i < n_rows; i += nw) {
+    const unsigned long long a = rowptr[i], b = rowptr[i + 1];
+    unsigned long long o = rowptr_out[i];
+    for (unsigned long long p = a + lane; p - lane < b; p += 32) {
+      const int kp = p < b ? kpos[col[p]] : -1;
+      const unsigned m = __ballot_sync(0xffffffffu, kp >= 0);
+      if (kp >= 0) {
+        const unsigned long long q = o + __popc(m & lt);
+        col_out[q] = kp;
+        val_out[q] = val[p];
+      }
+      o += __popc(m);
+    }
+  }
+}
+
+ctd_status csr_keep_columns(const uint64_t* rowptr, const int32_t* col, const int32_t* val,
+                            int64_t n_rows, const int* kpos, uint64_t* rowptr_out,
+                            int32_t* col_out, int32_t* val_out, Arena& scratch,
+                            cudaStream_t st) {
+  unsigned* cnt;
+  uint64_t* tmp;
+  unsigned* status;
+  CTD_TRY(scratch.get(&cnt, std::max<int64_t>(n_rows, 1)));
+  CTD_TRY(scratch.get(&tmp, scan_tmp_elems(n_rows)));
+  CTD_TRY(scratch.get(&status, 1));
+  CTD_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
+  const unsigned g = grid_for(n_rows * 32, 256, (int64_t)num_sms() * 8);
+  const auto* rp = reinterpret_cast<const unsigned long long*>(rowptr);
+  if (n_rows > 0) CTD_LAUNCH(k_rsub_counts, (g), (256), 0, st, rp, col, kpos, n_rows, cnt);
+  launch_scan_u32(cnt, rowptr_out, n_rows, false, tmp, status, st);
+  if (n_rows > 0)
+    CTD_LAUNCH(k_rsub_write, (g), (256), 0, st, rp, col, val, kpos, n_rows,
+               reinterpret_cast<const unsigned long long*>(rowptr_out), col_out, val_out);
+  CTD_CUDA(cudaGetLastError());
+  return CTD_OK;
+}
+
 __global__ void k_sum_u32(const unsigned* __restrict__ in, int64_t n, unsigned long long* out,
                           unsigned mask) {
   __shared__ unsigned long long part[32];

@@ -136,3 +136,40 @@ def test_pool_and_hook_give_identical_results(restore_allocator):
         out.append((F.error(), F.U().tobytes(), p.tobytes(), r.tobytes(), v.tobytes()))
         F.free()
     assert out[0] == out[1]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_every_allocation_failure_point_releases(restore_allocator, precision):
+    """A refusal at each of the call's allocations in turn, including those of
+    U and the error on the second stream while the main stream's kernels are
+    in flight: CTD_ENOMEM, every block handed back, nothing held; then the
+    same call succeeds with the same result as before (CTD_DETERMINISTIC: one
+    entry order per column, so the error repeats bit for bit)."""
+    import torch
+    m = ctd()
+    prec = m.CTD_FP64 if precision == "fp64" else m.CTD_FP32_BULK
+    coo = synth.traffic((300, 200, 40), 20_000, 1.2, 1.2, "poisson1", 9, 3.0)
+    X = m.Coo.from_synth(coo)
+    counting = CountingHook()
+    counting.install(m)
+    det = m.CTD_DETERMINISTIC
+    ref = m.ctd_static(X, 1, 60, 1e-6, 4, prec, det)
+    want_R, want_e = ref.R_dense(), ref.error()
+    ref.free()
+    total = counting.allocs
+    assert total > 10
+    for n in range(total):
+        hook = CountingHook(refuse_after=n)
+        hook.install(m)
+        with pytest.raises(m.CtdError) as e:
+            m.ctd_static(X, 1, 60, 1e-6, 4, prec, det)
+        assert e.value.status == "CTD_ENOMEM", n
+        torch.cuda.synchronize()
+        assert hook.releases == hook.allocs and not hook.live, n
+        assert m.allocated_bytes() == 0
+    hook = CountingHook()
+    hook.install(m)
+    F = m.ctd_static(X, 1, 60, 1e-6, 4, prec, det)
+    assert np.array_equal(F.R_dense(), want_R)
+    assert F.error() == want_e
+    F.free()
