@@ -442,6 +442,21 @@ def ours(args):
             "traffic": traffic,
             # DRAM bytes the launch moved (ncu) over its live duration
             "dram_frac": (traffic / (cf_ms * 1e-3) / 1e9 / peak) if traffic else None}
+    # the same fill with nothing beside it: three calls with the error off
+    # (CTD_SKIP_ERROR), after the timed region; inside it the error's kernels
+    # share the GPU with the fill from a second stream
+    ctd.profile(True)
+    for _ in range(3):
+        ctd.ctd_static(X, 1, S, EPS, seed, ctd.CTD_FP32_BULK, ctd.CTD_SKIP_ERROR, st).free()
+    torch.cuda.synchronize()
+    ph_alone = ctd.profile_report()["phases"]
+    ctd.profile(False)
+    cfa = ph_alone.get("c_fill", {"ms": float("nan"), "calls": 1})
+    cfa_ms = cfa["ms"] / max(cfa["calls"], 1)
+    roof["alone"] = {"ms": cfa_ms, "achieved": alg / (cfa_ms * 1e-3) / 1e9,
+                     "frac": alg / (cfa_ms * 1e-3) / 1e9 / peak,
+                     "dram_frac": (traffic / (cfa_ms * 1e-3) / 1e9 / peak) if traffic else None,
+                     "how": "3 calls with the error off, after the timed region"}
     phases = {k: {"ms_per_step": round(v["ms"] / args.steps, 4),
                   "calls_per_step": round(v["calls"] / args.steps, 2)} for k, v in ph.items()}
     if "call" in ph:
