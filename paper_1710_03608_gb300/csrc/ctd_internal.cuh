@@ -351,8 +351,12 @@ void launch_list_columns(const uint64_t* colptr, const uint64_t* coff, int64_t n
 // entries as idx; used for segments longer than 2048).
 void launch_sort_segments(const uint64_t* ptr, int64_t nseg, int32_t* idx, int32_t* val,
                           int32_t* tmp_idx, int32_t* tmp_val, cudaStream_t st);
+// Sort each row of (rowptr, col, val) by column into the out arrays; the
+// columns lie in [col_base, col_base + ncols) (ncols <= 8192 enables the
+// bitmap ranking of long rows; 0 or larger: comparisons only).
 void launch_sort_rows(const uint64_t* rowptr, int64_t n_rows, const int32_t* col_in,
-                      const int32_t* val_in, int32_t* col_out, int32_t* val_out, cudaStream_t st);
+                      const int32_t* val_in, int32_t* col_out, int32_t* val_out, int col_base,
+                      int64_t ncols, cudaStream_t st);
 
 // Relative-error numerator ||Q^T X_(alpha)||_F^2 with Q = R Z^T, Z = L^{-1}
 // (kept x kept, column-major, ld ldz).  The rows of X with the most

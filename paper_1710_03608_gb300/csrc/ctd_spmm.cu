@@ -454,26 +454,71 @@ ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_
 
 // Sort each row of a row-major factor by column: one warp per row, each
 // entry placed at its rank (the number of smaller columns; columns within a
-// row are distinct).  Rows of up to SR_SMEM entries are ranked against a
-// copy of their columns in the warp's shared memory (the long rows, those
-// of the frequent mode-alpha indices, would otherwise rescan global memory
-// once per entry); longer rows rank against global memory.  In/out arrays
+// row are distinct).  When the columns lie in [col_base, col_base + ncols)
+// with ncols <= SR_BITS, a row longer than SR_SHORT marks its columns in a
+// bitmap in the warp's shared memory and takes each rank as the popcount of
+// the bits below it (a prefix over the bitmap's words, then one word), so a
+// row of n entries costs O(n + ncols/32) rather than O(n^2) (the long rows,
+// those of the frequent mode-alpha indices, used to dominate).  Otherwise
+// rows of up to SR_SMEM entries are ranked against a copy of their columns
+// in shared memory and longer ones against global memory.  In/out arrays
 // differ.
 constexpr int SR_SMEM = 512;
+constexpr int SR_SHORT = 64;
+constexpr int SR_BITS = 8192;
+constexpr int SR_WORDS = SR_BITS / 32;
 
 __global__ void __launch_bounds__(256)
     k_sort_rows(const unsigned long long* __restrict__ rowptr, int64_t n_rows,
                 const int32_t* __restrict__ col_in, const int32_t* __restrict__ val_in,
-                int32_t* __restrict__ col_out, int32_t* __restrict__ val_out) {
+                int32_t* __restrict__ col_out, int32_t* __restrict__ val_out, int col_base,
+                int ncols) {
   __shared__ int32_t keys[8][SR_SMEM];
+  __shared__ unsigned bits[8][SR_WORDS];
+  __shared__ unsigned pre[8][SR_WORDS];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int32_t* kw = keys[wib];
+  unsigned* bw = bits[wib];
+  unsigned* pw = pre[wib];
+  const bool use_bits = ncols > 0 && ncols <= SR_BITS;
+  const int nwords = (ncols + 31) >> 5;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = gw; i < n_rows; i += nw) {
     const unsigned long long a = rowptr[i], b = rowptr[i + 1];
     const int len = (int)(b - a);
-    if (len <= SR_SMEM) {
+    if (use_bits && len > SR_SHORT) {
+      for (int w = lane; w < nwords; w += 32) bw[w] = 0u;
+      __syncwarp();
+      for (int e = lane; e < len; e += 32) {
+        const int m = col_in[a + e] - col_base;
+        atomicOr(&bw[m >> 5], 1u << (m & 31));
+      }
+      __syncwarp();
+      // exclusive prefix of the words' popcounts, 32 words per pass
+      unsigned carry = 0;
+      for (int w0 = 0; w0 < nwords; w0 += 32) {
+        const int w = w0 + lane;
+        const unsigned c = w < nwords ? (unsigned)__popc(bw[w]) : 0u;
+        unsigned x = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
+          if (lane >= d) x += y;
+        }
+        if (w < nwords) pw[w] = carry + x - c;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+      }
+      __syncwarp();
+      for (int e = lane; e < len; e += 32) {
+        const int mc = col_in[a + e];
+        const int m = mc - col_base;
+        const int r = (int)pw[m >> 5] + __popc(bw[m >> 5] & ((1u << (m & 31)) - 1u));
+        col_out[a + r] = mc;
+        val_out[a + r] = val_in[a + e];
+      }
+      __syncwarp();
+    } else if (len <= SR_SMEM) {
       for (int e = lane; e < len; e += 32) kw[e] = col_in[a + e];
       __syncwarp();
       for (int e = lane; e < len; e += 32) {
@@ -569,11 +614,13 @@ void launch_sort_segments(const uint64_t* ptr, int64_t nseg, int32_t* idx, int32
 }
 
 void launch_sort_rows(const uint64_t* rowptr, int64_t n_rows, const int32_t* col_in,
-                      const int32_t* val_in, int32_t* col_out, int32_t* val_out, cudaStream_t st) {
+                      const int32_t* val_in, int32_t* col_out, int32_t* val_out, int col_base,
+                      int64_t ncols, cudaStream_t st) {
   if (n_rows <= 0) return;
+  const int nc = ncols > 0 && ncols <= SR_BITS ? (int)ncols : 0;  // 0: no bitmap
   CTD_LAUNCH(k_sort_rows, (grid_for(n_rows * 32, 256, (int64_t)num_sms() * 16)), (256), 0, st,
              reinterpret_cast<const unsigned long long*>(rowptr), n_rows, col_in, val_in, col_out,
-             val_out);
+             val_out, col_base, nc);
 }
 
 // ---------------------------------------------------------------------------

@@ -868,7 +868,8 @@ ctd_status build_csr_from_csc(const uint64_t* colptr, const int32_t* row, const 
                reinterpret_cast<const unsigned long long*>(colptr), row, val, ncols, col_base,
                reinterpret_cast<unsigned long long*>(cur), col_tmp, val_tmp);
     // rows sorted by column, so R(i, :) can be copied out in order
-    launch_sort_rows(rowptr_out, n_rows, col_tmp, val_tmp, col_out, val_out, st);
+    launch_sort_rows(rowptr_out, n_rows, col_tmp, val_tmp, col_out, val_out, col_base, ncols,
+                     st);
   }
   CTD_CUDA(cudaGetLastError());
   return CTD_OK;
