@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink every mode (and nnz by scale^3) for profiling runs")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the default launch shapes instead of the autotuned ones")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the small-tensor latency, batched and serving measurements")
     return ap.parse_args()
@@ -396,6 +398,13 @@ def ours(args):
     for _ in range(max(args.warmup, 3)):
         step(X).free()
     torch.cuda.synchronize()
+    # the launch-shape autotuner on this workload, before the timed region:
+    # the knobs change how the hot kernels are laid out, never what they
+    # compute; the timed steps run with the setting it picks
+    from paper_1710_03608_gb300 import measure
+    tune = None
+    if not args.no_autotune:
+        tune = measure.autotune_kernels(X, S, seed, save=False)
     sizes = None
     clocks = ClockSampler(local)
     ctd.profile(True)
@@ -485,7 +494,12 @@ def ours(args):
         e2e = {"value": nnz_step / dt, "unit": "nnz/s", "h2d_bytes_per_step": 16 * coo.nnz,
                "d2h_bytes_per_step": 8, "ms_per_step": dt * 1e3}
 
+    # defaults back for the other workloads
+    for k in measure.KNOB_GRID:
+        ctd.set_tuning(k, -1)
     extra = {}
+    if tune is not None:
+        extra["kernel_autotune"] = tune
     if rank == 0 and world == 1 and not args.no_extra and args.scale == 1.0:
         extra["small_tensor_latency"] = small_latency(ctd, synth, st, local)
         extra["batched"] = batched_form(ctd, synth, local)

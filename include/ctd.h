@@ -414,6 +414,22 @@ CTD_API ctd_status ctd_set_allocator(ctd_alloc_fn alloc, ctd_release_fn release)
  * hook or the pool), as it requested them. */
 CTD_API ctd_status ctd_allocated_bytes(size_t* bytes);
 
+/* Launch-shape knobs of the hot kernels (no counterpart in the paper:
+ * they change how the work is laid out on the GPU, never the arithmetic or
+ * the results), for an autotuner to set per workload.  Keys:
+ *   "qform_hot_kb"        shared memory (KB) for the rows of Q staged by the
+ *                         error's Q-form (0 to 200; default 200; at most 100
+ *                         for kept widths above 512)
+ *   "cfill_dense_kb"      shared memory (KB) per block of the C fill's
+ *                         multi-nonzero kernel: dense rows of R plus the
+ *                         warps' accumulators (64 to 220; default 220)
+ *   "copy_blocks_per_sm"  blocks per SM of the C fill's one-nonzero copy
+ *                         (1 to 32; default 8)
+ * ctd_set_tuning(key, -1) restores the default.  Process-wide; takes effect
+ * at the next call.  CTD_EINVAL: unknown key, value out of range, NULL. */
+CTD_API ctd_status ctd_set_tuning(const char* key, int64_t value);
+CTD_API ctd_status ctd_get_tuning(const char* key, int64_t* value);
+
 /* Diagnostics (no counterpart in the paper).  ctd_profile(1) clears and
  * starts per-phase device timing: each phase of a call is bracketed by a
  * CUDA event pair on the call's stream.  ctd_profile_report waits for the

@@ -190,6 +190,25 @@ ctd_status sync(cudaStream_t st) {
 }
 
 namespace {
+struct TuneSpec {
+  const char* key;
+  int64_t def, lo, hi;
+};
+constexpr TuneSpec kTune[TUNE_N] = {{"qform_hot_kb", 200, 0, 200},
+                                    {"cfill_dense_kb", 220, 64, 220},
+                                    {"copy_blocks_per_sm", 8, 1, 32}};
+std::atomic<int64_t> g_tune[TUNE_N] = {{200}, {220}, {8}};
+int tune_index(const char* key) {
+  if (!key) return -1;
+  for (int k = 0; k < TUNE_N; ++k)
+    if (std::strcmp(kTune[k].key, key) == 0) return k;
+  return -1;
+}
+}  // namespace
+
+int64_t tuning(TuneKey k) { return g_tune[k].load(std::memory_order_relaxed); }
+
+namespace {
 thread_local SideStream t_side;
 }
 
@@ -972,6 +991,23 @@ extern "C" ctd_status ctd_set_allocator(ctd_alloc_fn alloc, ctd_release_fn relea
 extern "C" ctd_status ctd_allocated_bytes(size_t* bytes) {
   if (!bytes) return fail(CTD_EINVAL, "NULL argument");
   *bytes = live_bytes();
+  return CTD_OK;
+}
+
+extern "C" ctd_status ctd_set_tuning(const char* key, int64_t value) {
+  const int k = tune_index(key);
+  if (k < 0) return fail(CTD_EINVAL, std::string("unknown tuning key: ") + (key ? key : "NULL"));
+  if (value == -1) value = kTune[k].def;
+  if (value < kTune[k].lo || value > kTune[k].hi)
+    return fail(CTD_EINVAL, std::string("tuning value out of range for ") + key);
+  g_tune[k].store(value);
+  return CTD_OK;
+}
+
+extern "C" ctd_status ctd_get_tuning(const char* key, int64_t* value) {
+  const int k = tune_index(key);
+  if (k < 0 || !value) return fail(CTD_EINVAL, "unknown tuning key or NULL");
+  *value = g_tune[k].load();
   return CTD_OK;
 }
 

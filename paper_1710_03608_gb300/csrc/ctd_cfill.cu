@@ -775,7 +775,8 @@ ctd_status cf_all(int nq, int db, bool p4, const CscDev& X, int64_t n_cols, int6
     PhaseScope ph("c_fill_copy", st);
     // four rounds of loads in flight; tighter register bounds (more warps
     // per SM) measured no faster: the copy is bound by its stores
-    CTD_LAUNCH((k_copy_flat<V, 4, 1>), (num_sms() * 8), (256), 0, st, X, rp, ip, icol, ival, P,
+    CTD_LAUNCH((k_copy_flat<V, 4, 1>), (num_sms() * (int)tuning(TUNE_COPY_BLOCKS)), (256), 0, st,
+               X, rp, ip, icol, ival, P,
                single, counts, coff, ccnt, crow, cval);
   }
   PhaseScope ph("c_fill_multi", st);
@@ -815,8 +816,9 @@ ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, in
   const int db = (R.max_abs >= 0 && R.max_abs <= 127) ? 1
                  : (R.max_abs >= 0 && R.max_abs <= 32767) ? 2 : 4;
   const size_t row_b = (size_t)W * db;
-  // one block per SM: dense rows, the warps' accumulators and row staging in ~220 KB
-  const int budget = 220 * 1024;
+  // one block per SM: dense rows, the warps' accumulators and row staging in
+  // ~220 KB (a smaller budget keeps fewer rows dense: "cfill_dense_kb")
+  const int budget = (int)tuning(TUNE_CFILL_DENSE) * 1024;
   int hmax = (int)((budget - (int64_t)(CF_THREADS / 32) * (256 + W * 4)) / (int64_t)row_b);
   hmax = std::max(0, std::min(hmax, CF_MAX_DENSE));
   const int minlen = std::max(16, 8 * nq);  // shorter rows are cheaper walked sparsely

@@ -117,6 +117,12 @@ struct Arena {
 // launch.  A higher limit does not change launches that ask for less.
 ctd_status allow_max_smem(const void* fn);
 
+// Launch-shape knobs (ctd_set_tuning): shared memory for the Q-form's
+// staged rows and for the C fill's dense rows (bytes), blocks per SM of the
+// one-nonzero copy.
+enum TuneKey { TUNE_QFORM_HOT, TUNE_CFILL_DENSE, TUNE_COPY_BLOCKS, TUNE_N };
+int64_t tuning(TuneKey k);
+
 inline int num_sms() {
   static int n = 0;
   if (!n) {

@@ -1235,8 +1235,9 @@ ctd_status launch_error_qform(const CscDev& X, int64_t n_cols, int64_t n_rows, i
   CTD_TRY(scratch.get(&slot_of, n_rows));
   CTD_TRY(scratch.get(&work, 2));
   // hot rows (one register block wide only): as many as fit in ~200 KB of
-  // shared memory (one block per SM; 100 KB each for two blocks at NK = 8)
-  const size_t budget = NK >= 8 ? 100 * 1024 : 200 * 1024;
+  // shared memory (one block per SM; 100 KB each for two blocks at NK = 8),
+  // or in the "qform_hot_kb" knob's budget when that is smaller
+  const size_t budget = (size_t)std::min<int64_t>(tuning(TUNE_QFORM_HOT), NK >= 8 ? 100 : 200) * 1024;
   int n_hot = nblk == 1 ? (int)std::min<int64_t>((int64_t)(budget / ((size_t)qs * tsz)), n_rows)
                         : 0;
   CTD_TRY(scratch.get(&hot, std::max(n_hot, 1)));

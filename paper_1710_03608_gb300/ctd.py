@@ -37,7 +37,7 @@ EXPORTED = ["ctd_static", "ctd_dynamic_create", "ctd_dynamic_step", "ctd_error",
             "ctd_server_wait", "ctd_server_result", "ctd_server_state", "ctd_server_free",
             "ctd_ddos_candidates", "ctd_dynamic_from_static", "ctd_fault_inject_alloc",
             "ctd_selftest_bounded_wait", "ctd_set_allocator", "ctd_allocated_bytes",
-            "ctd_static_nway", "ctd_get_R_f64"]
+            "ctd_static_nway", "ctd_get_R_f64", "ctd_set_tuning", "ctd_get_tuning"]
 
 
 class CtdError(RuntimeError):
@@ -118,6 +118,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ctd_set_allocator": [P, P],
         "ctd_static_nway": [C.POINTER(ctd_coon), I32, I64, D, U64, I32, C.c_uint, P, C.POINTER(P)],
         "ctd_allocated_bytes": [C.POINTER(C.c_size_t)],
+        "ctd_set_tuning": [C.c_char_p, I64],
+        "ctd_get_tuning": [C.c_char_p, C.POINTER(C.c_int64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -160,6 +162,23 @@ def use_torch_allocator(enable: bool = True) -> None:
     alloc = C.cast(_shim.ctd_torch_alloc, C.c_void_p)
     release = C.cast(_shim.ctd_torch_release, C.c_void_p)
     _check(lib.ctd_set_allocator(alloc, release))
+
+
+TUNING_KEYS = ("qform_hot_kb", "cfill_dense_kb", "copy_blocks_per_sm")
+
+
+def set_tuning(key: str, value: int) -> None:
+    """Set a launch-shape knob of the hot kernels (-1: its default)."""
+    _check(load().ctd_set_tuning(key.encode(), int(value)))
+
+
+def get_tuning(key: str = None):
+    """One knob's value, or all of them as a dict."""
+    if key is None:
+        return {k: get_tuning(k) for k in TUNING_KEYS}
+    v = C.c_int64()
+    _check(load().ctd_get_tuning(key.encode(), C.byref(v)))
+    return v.value
 
 
 def allocated_bytes() -> int:

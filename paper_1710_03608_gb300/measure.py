@@ -52,12 +52,102 @@ def memory_usage(F) -> float:
 # ---------------------------------------------------------------------------
 # autotuner: worker streams for the batched form
 # ---------------------------------------------------------------------------
-def tuned_workers(default: int = 8) -> int:
+def _tune_load() -> dict:
     try:
         with open(TUNE_FILE) as f:
-            return int(json.load(f)["batched_workers"])
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _tune_save(update: dict) -> None:
+    d = _tune_load()
+    d.update(update)
+    os.makedirs(os.path.dirname(TUNE_FILE), exist_ok=True)
+    with open(TUNE_FILE, "w") as f:
+        json.dump(d, f)
+
+
+def tuned_workers(default: int = 8) -> int:
+    try:
+        return int(_tune_load()["batched_workers"])
     except Exception:
         return default
+
+
+# ---------------------------------------------------------------------------
+# launch-shape autotuner of the hot kernels (ctd_set_tuning knobs)
+# ---------------------------------------------------------------------------
+KNOB_GRID = {"qform_hot_kb": (0, 100, 150, 200),
+             "cfill_dense_kb": (128, 176, 220),
+             "copy_blocks_per_sm": (2, 4, 8, 16)}
+
+
+def size_class(nnz: int) -> str:
+    """Workloads are tuned per decade of nonzeros."""
+    import math
+    return f"nnz_1e{int(round(math.log10(max(int(nnz), 1))))}"
+
+
+def _time_calls(X, s, seed, calls: int) -> float:
+    """Mean device time (ms) of `calls` ctd_static calls, CUDA events on the
+    current stream, after one untimed call."""
+    import torch
+    st = torch.cuda.current_stream()
+    ctd.ctd_static(X, 1, s, 1e-6, seed, ctd.CTD_FP32_BULK, 0, st).free()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(calls):
+        ctd.ctd_static(X, 1, s, 1e-6, seed, ctd.CTD_FP32_BULK, 0, st).free()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / calls
+
+
+def autotune_kernels(X, s, seed=0, calls: int = 5, save: bool = True) -> dict:
+    """One pass of coordinate descent over the knobs of KNOB_GRID on CTD-S of
+    X (FP32_BULK): each knob in turn takes the value with the shortest mean
+    call, the others held at their best so far.  The knobs change launch
+    shapes only, never results.  The best setting is kept in the tuning
+    file under the tensor's size class; the knobs are left at it."""
+    best = {k: ctd.get_tuning(k) for k in KNOB_GRID}
+    for k, v in best.items():
+        ctd.set_tuning(k, v)
+    base = _time_calls(X, s, seed, calls)
+    sweep = {}
+    for k, values in KNOB_GRID.items():
+        times = {}
+        for v in values:
+            ctd.set_tuning(k, v)
+            times[v] = min(_time_calls(X, s, seed, calls) for _ in range(2))
+        best[k] = min(times, key=times.get)
+        ctd.set_tuning(k, best[k])
+        sweep[k] = times
+    # the default and the tuned setting once more, alternately
+    tuned, default = [], []
+    for _ in range(2):
+        for key in KNOB_GRID:
+            ctd.set_tuning(key, -1)
+        default.append(_time_calls(X, s, seed, calls))
+        for key, v in best.items():
+            ctd.set_tuning(key, v)
+        tuned.append(_time_calls(X, s, seed, calls))
+    cls = size_class(X.desc.nnz)
+    if save:
+        kern = _tune_load().get("kernels", {})
+        kern[cls] = best
+        _tune_save({"kernels": kern})
+    return {"class": cls, "best": best, "default_ms": min(default), "tuned_ms": min(tuned),
+            "first_ms": base, "sweep_ms": sweep, "calls": calls}
+
+
+def apply_tuning(nnz: int) -> dict:
+    """Set the knobs the tuning file holds for nnz's size class (defaults
+    when it holds none); returns what was set."""
+    best = _tune_load().get("kernels", {}).get(size_class(nnz), {})
+    for k in KNOB_GRID:
+        ctd.set_tuning(k, best.get(k, -1))
+    return {k: ctd.get_tuning(k) for k in KNOB_GRID}
 
 
 def autotune_workers(Xs, s, seeds, candidates=(2, 4, 8, 12, 16, 24), save: bool = True) -> dict:
@@ -75,9 +165,7 @@ def autotune_workers(Xs, s, seeds, candidates=(2, 4, 8, 12, 16, 24), save: bool 
         times[w] = dt
     best = min(times, key=times.get)
     if save:
-        os.makedirs(os.path.dirname(TUNE_FILE), exist_ok=True)
-        with open(TUNE_FILE, "w") as f:
-            json.dump({"batched_workers": best, "times_s": times}, f)
+        _tune_save({"batched_workers": best, "times_s": times})
     return {"best": best, "times_s": times}
 
 

@@ -79,6 +79,18 @@ int main(void) {
   size_t held = 1;
   if (ctd_allocated_bytes(&held) != CTD_OK || held != 0) return 10;
   if (ctd_allocated_bytes(NULL) != CTD_EINVAL) return 11;
+  /* launch-shape knobs: known keys, ranges, -1 restores the default */
+  int64_t t = 0;
+  if (ctd_get_tuning("copy_blocks_per_sm", &t) != CTD_OK || t != 8) return 12;
+  if (ctd_set_tuning("copy_blocks_per_sm", 3) != CTD_OK) return 13;
+  if (ctd_get_tuning("copy_blocks_per_sm", &t) != CTD_OK || t != 3) return 14;
+  if (ctd_set_tuning("copy_blocks_per_sm", 0) != CTD_EINVAL) return 15;
+  if (ctd_set_tuning("cfill_dense_kb", 221) != CTD_EINVAL) return 16;
+  if (ctd_set_tuning("no_such_knob", 1) != CTD_EINVAL) return 17;
+  if (ctd_set_tuning(NULL, 1) != CTD_EINVAL) return 18;
+  if (ctd_set_tuning("copy_blocks_per_sm", -1) != CTD_OK) return 19;
+  if (ctd_get_tuning("copy_blocks_per_sm", &t) != CTD_OK || t != 8) return 20;
+  if (ctd_get_tuning("qform_hot_kb", NULL) != CTD_EINVAL) return 21;
   printf("%s\n", v);
   return 0;
 }
