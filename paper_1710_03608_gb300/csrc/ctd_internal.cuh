@@ -231,7 +231,9 @@ void launch_sqnorms_cdf(const uint64_t* colptr, const int32_t* val, int64_t n_co
 // total at or past 2^63 sets DEV_OVERFLOW in *status.  in == out is
 // allowed for the inclusive u64 scan (each element is read before it is
 // written, by the same thread).  cur32 (optional, u32 scan only) receives
-// the exclusive prefix of every element as u32 and may alias `in`.
+// the exclusive prefix of every element as u32 and may alias `in`.  Up to
+// 16,384 elements take one launch (one block), longer inputs three
+// (reduce, scan of the tile sums, apply).
 size_t scan_tmp_elems(int64_t n);
 // Tiling of the scans: a tile of SCAN_TILE elements is one block of
 // SCAN_WARPS warps, each warp a segment of SCAN_PER_WARP elements.

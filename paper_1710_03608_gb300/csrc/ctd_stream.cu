@@ -252,12 +252,70 @@ __global__ void k_scan_apply(const Tin* in, unsigned long long* out, int64_t n,
   if (!inclusive && blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
 }
 
+// Short inputs (at most SS_MAX elements) in one launch: one block of 32
+// warps, warp w owns elements [512 w, 512 w + 512); the warps' sums, their
+// exclusive offsets in shared memory, then each warp's running scan.  The
+// same outputs, aliasing rules and overflow flag as the three-pass form.
+constexpr int SS_WARPS = 32, SS_PER_WARP = 512, SS_MAX = SS_WARPS * SS_PER_WARP;
+
+template <typename Tin>
+__global__ void __launch_bounds__(SS_WARPS * 32)
+    k_scan_small(const Tin* in, unsigned long long* out, int64_t n, bool inclusive,
+                 uint32_t* cur32, unsigned* status) {
+  __shared__ unsigned long long ws[SS_WARPS], wsat[SS_WARPS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t base = (int64_t)warp * SS_PER_WARP;
+  unsigned long long acc = 0, accs = 0;
+#pragma unroll 4
+  for (int it = 0; it < SS_PER_WARP / 32; ++it) {
+    const int64_t e = base + it * 32 + lane;
+    if (e < n) {
+      const unsigned long long x = (unsigned long long)in[e];
+      acc += x;
+      accs = sat_add(accs, x);
+    }
+  }
+  acc = warp_sum(acc);
+  accs = warp_sat_sum(accs);
+  if (lane == 0) {
+    ws[warp] = acc;
+    wsat[warp] = accs;
+  }
+  __syncthreads();
+  unsigned long long carry = 0;
+  for (int w = 0; w < warp; ++w) carry += ws[w];
+  if (threadIdx.x == 0) {
+    // the exact total (saturating) at or past 2^63: every prefix is exact below it
+    unsigned long long t = 0;
+    for (int w = 0; w < SS_WARPS; ++w) t = sat_add(t, wsat[w]);
+    if (t >= (1ull << 63)) atomicOr(status, DEV_OVERFLOW);
+  }
+  const int shift = inclusive ? 0 : 1;
+#pragma unroll 4
+  for (int it = 0; it < SS_PER_WARP / 32; ++it) {
+    const int64_t e = base + it * 32 + lane;
+    const unsigned long long x = e < n ? (unsigned long long)in[e] : 0ull;
+    const unsigned long long inc = warp_incl_scan(x);
+    if (e < n) {
+      out[e + shift] = carry + inc;
+      if (cur32) cur32[e] = (uint32_t)(carry + inc - x);
+    }
+    carry += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  if (!inclusive && threadIdx.x == 0) out[0] = 0;
+}
+
 template <typename Tin>
 static void scan_impl(const Tin* in, uint64_t* out, int64_t n, bool inclusive, uint64_t* tmp,
                       unsigned* status, cudaStream_t st, uint32_t* cur32 = nullptr) {
   const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (n == 0) {
     if (!inclusive) cudaMemsetAsync(out, 0, sizeof(uint64_t), st);
+    return;
+  }
+  if (n <= SS_MAX) {
+    CTD_LAUNCH(k_scan_small<Tin>, (1), (SS_WARPS * 32), 0, st, in,
+               reinterpret_cast<unsigned long long*>(out), n, inclusive, cur32, status);
     return;
   }
   unsigned long long* ts = reinterpret_cast<unsigned long long*>(tmp);
