@@ -34,7 +34,7 @@ WORKLOAD = "CTD-S traffic tensor 10000x10000x1000, 1e7 nnz, Zipf(1.2) src/dst, G
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -102,6 +102,12 @@ class ClockSampler:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # nvidia-smi takes a moment to start sampling: wait for its first line
+        # (up to 3 s) so that the samples cover the whole timed region
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.005)
+        self.lines.clear()
 
     def _read(self):
         for line in self.proc.stdout:

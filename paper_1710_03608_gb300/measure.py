@@ -11,6 +11,7 @@
       one CTD-D stream of 2*10^4 x 2*10^4 slices (500K nonzeros each, planted
       block at steps 40-45); per-step nonzeros/s and d~_t.
   python -m paper_1710_03608_gb300.measure ncu-summary LAUNCHES.csv
+  python -m paper_1710_03608_gb300.measure ncu-dram DRAM.csv --peak GBS
       per-kernel launches, time and share of an ncu launch list (no GPU).
 
 All times are host wall-clock around calls that wait for their work (the
@@ -486,6 +487,48 @@ def ncu_launch_summary(csv_path: str, top: int = 30) -> str:
     return "\n".join(lines)
 
 
+def ncu_dram_summary(csv_path: str, peak_gbs: float, top: int = 40) -> str:
+    """Per kernel, from an `ncu --metrics dram__bytes_read.sum,
+    dram__bytes_write.sum,gpu__time_duration.sum --csv` launch list: launches,
+    mean duration, mean DRAM bytes moved and the rate they were moved at
+    (serialized, cold-cache launches), and that rate as a fraction of
+    `peak_gbs`."""
+    import collections
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    h = rows[hi]
+    ii, ki, mi = h.index("ID"), h.index("Kernel Name"), h.index("Metric Name")
+    vi, ui = h.index("Metric Value"), h.index("Metric Unit")
+    tscale = {"ns": 1e-9, "nsecond": 1e-9, "us": 1e-6, "usecond": 1e-6, "ms": 1e-3,
+              "msecond": 1e-3, "s": 1.0, "second": 1.0}
+    bscale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    launch = collections.defaultdict(lambda: [None, 0.0, 0.0])  # name, seconds, bytes
+    for r in rows[hi + 1:]:
+        if len(r) <= vi:
+            continue
+        rec = launch[r[ii]]
+        rec[0] = r[ki].split("(")[0].replace("void ", "")
+        v = float(r[vi].replace(",", ""))
+        if r[mi] == "gpu__time_duration.sum":
+            rec[1] += v * tscale.get(r[ui], 1e-9)
+        elif r[mi].startswith("dram__bytes_"):
+            rec[2] += v * bscale.get(r[ui], 1.0)
+    agg = collections.defaultdict(lambda: [0, 0.0, 0.0])
+    for name, sec, byt in launch.values():
+        a = agg[name]
+        a[0] += 1
+        a[1] += sec
+        a[2] += byt
+    lines = [f"{'kernel':48s} {'launches':>8s} {'us/launch':>10s} {'MB/launch':>10s} "
+             f"{'GB/s':>8s} {'of peak':>8s}"]
+    for n, (c, sec, byt) in sorted(agg.items(), key=lambda x: -x[1][1])[:top]:
+        rate = byt / sec / 1e9 if sec > 0 else 0.0
+        lines.append(f"{n:48s} {c:8d} {1e6 * sec / c:10.1f} {byt / c / 1e6:10.2f} "
+                     f"{rate:8.0f} {rate / peak_gbs:8.3f}")
+    return "\n".join(lines)
+
+
 def ncu_metrics_summary(rep_path: str, kernel_regex: str, names) -> dict:
     """Selected raw metrics of the captured launches of one kernel from an
     `ncu -o` report (read with `ncu -i ... --page raw --csv`)."""
@@ -544,6 +587,10 @@ def main():
     ns = sub.add_parser("ncu-summary")
     ns.add_argument("csv")
     ns.add_argument("--top", type=int, default=30)
+    nd = sub.add_parser("ncu-dram")
+    nd.add_argument("csv")
+    nd.add_argument("--peak", type=float, required=True, help="GB/s (the measured copy)")
+    nd.add_argument("--top", type=int, default=40)
     b = sub.add_parser("batched")
     b.add_argument("--count", type=int, default=256)
     b.add_argument("--workers", type=int, default=0)
@@ -573,6 +620,9 @@ def main():
     args = ap.parse_args()
     if args.cmd == "ncu-summary":
         print(ncu_launch_summary(args.csv, args.top))
+        return
+    if args.cmd == "ncu-dram":
+        print(ncu_dram_summary(args.csv, args.peak, args.top))
         return
     if args.cmd == "ncu-traffic":
         print(json.dumps(ncu_traffic_record(args.csv, args.kernels, args.scale, args.source)))

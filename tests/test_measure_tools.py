@@ -79,3 +79,35 @@ def test_bench_reports_traffic_only_for_the_captured_source(tmp_path, monkeypatc
     assert bench.ncu_traffic(str(src))["bytes_per_launch"] == 5.0
     src.write_text("B\n")                    # the kernels changed since the capture
     assert bench.ncu_traffic(str(src)) is None
+
+
+def test_dram_summary_groups_metrics_by_launch(tmp_path):
+    """Three metrics per launch (read, write, duration) grouped by the launch
+    ID: per kernel the mean duration, mean bytes and their rate."""
+    from paper_1710_03608_gb300 import measure
+    p = tmp_path / "dram.csv"
+    rows = [
+        (0, "void ctd::k_a(int)", "dram__bytes_read.sum", "Mbyte", "60"),
+        (0, "void ctd::k_a(int)", "dram__bytes_write.sum", "Mbyte", "40"),
+        (0, "void ctd::k_a(int)", "gpu__time_duration.sum", "usecond", "50"),
+        (1, "void ctd::k_a(int)", "dram__bytes_read.sum", "byte", "100000000"),
+        (1, "void ctd::k_a(int)", "dram__bytes_write.sum", "byte", "100000000"),
+        (1, "void ctd::k_a(int)", "gpu__time_duration.sum", "nsecond", "150000"),
+        (2, "ctd::k_b(int)", "dram__bytes_read.sum", "Kbyte", "1000"),
+        (2, "ctd::k_b(int)", "dram__bytes_write.sum", "byte", "0"),
+        (2, "ctd::k_b(int)", "gpu__time_duration.sum", "usecond", "10"),
+    ]
+    with open(p, "w", newline="") as f:
+        w = csv.writer(f, quoting=csv.QUOTE_ALL)
+        w.writerow(HEADER)
+        for lid, name, metric, unit, value in rows:
+            w.writerow([lid, 1, "python", "h", name, 1, 7, "(256, 1, 1)", "(152, 1, 1)", 0,
+                        "10.3", "Command line profiler metrics", metric, unit, value])
+    out = measure.ncu_dram_summary(str(p), peak_gbs=1000.0).splitlines()
+    a = out[1].split()
+    # k_a: 2 launches, 100 us mean, 150 MB mean, 300 MB / 200 us = 1500 GB/s
+    assert a[0] == "ctd::k_a" and a[1] == "2"
+    assert float(a[2]) == pytest.approx(100.0) and float(a[3]) == pytest.approx(150.0)
+    assert float(a[4]) == pytest.approx(1500.0) and float(a[5]) == pytest.approx(1.5)
+    b = out[2].split()
+    assert b[0] == "ctd::k_b" and float(b[4]) == pytest.approx(100.0)
