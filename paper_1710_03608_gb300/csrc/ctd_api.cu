@@ -566,7 +566,7 @@ ctd_status static_impl(const CooDev& X, int64_t s, double eps, uint64_t seed, in
                         rc_val, st);
   // rows of each gathered column in ascending order, so every floating-point
   // sum over a candidate's entries is reproducible
-  launch_sort_segments(rc_ptr, su, rc_row, rc_val, rcr_col, rcr_val, st);
+  launch_sort_segments(rc_ptr, su, rc_row, rc_val, rcr_col, rcr_val, M.n_rows, st);
   STEP(build_csr_from_csc(rc_ptr, rc_row, rc_val, su, nnz_cand, M.n_rows, 0, rcr_ptr, rcr_col,
                           rcr_val, scratch, st));
 

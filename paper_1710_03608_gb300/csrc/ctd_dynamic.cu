@@ -540,7 +540,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
                           rc_val, st);
     // rows of each gathered column in ascending order, so every floating-point
     // sum over a candidate's entries is reproducible
-    launch_sort_segments(rc_ptr, du, rc_row, rc_val, rcr_col, rcr_val, st);
+    launch_sort_segments(rc_ptr, du, rc_row, rc_val, rcr_col, rcr_val, M.n_rows, st);
     CTD_TRY(build_csr_from_csc(rc_ptr, rc_row, rc_val, du, (int64_t)nnz_cand, M.n_rows, 0,
                                rcr_ptr, rcr_col, rcr_val, scratch, st));
     // exact Gram of the candidates (once) and their squared norms

@@ -356,9 +356,12 @@ void launch_list_columns(const uint64_t* colptr, const uint64_t* coff, int64_t n
                          uint64_t minc, int64_t* list, unsigned* count, cudaStream_t st);
 // Sort each row of a row-major factor by column (col/val copied to *_out).
 // Sort every segment of (ptr, idx, val) by idx in place (tmp_* hold as many
-// entries as idx; used for segments longer than 2048).
+// entries as idx; used for segments longer than 2048).  The indices lie in
+// [0, index_range); a range of at most 65,536 lets long segments be ranked
+// through a bitmap of their indices.
 void launch_sort_segments(const uint64_t* ptr, int64_t nseg, int32_t* idx, int32_t* val,
-                          int32_t* tmp_idx, int32_t* tmp_val, cudaStream_t st);
+                          int32_t* tmp_idx, int32_t* tmp_val, int64_t index_range,
+                          cudaStream_t st);
 // Sort each row of (rowptr, col, val) by column into the out arrays; the
 // columns lie in [col_base, col_base + ncols) (ncols <= 8192 enables the
 // bitmap ranking of long rows; 0 or larger: comparisons only).

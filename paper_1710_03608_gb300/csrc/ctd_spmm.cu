@@ -542,22 +542,81 @@ __global__ void __launch_bounds__(256)
 }
 
 // Sort each segment of a compressed layout by index (values follow), in
-// place: a block per segment, bitonic in shared memory up to 2048 entries;
-// longer segments rank each entry by counting (indices within a segment are
-// distinct).  Used to give gathered columns a reproducible order.
+// place: a block per segment.  When the indices lie in [0, nbits) with nbits
+// <= SEG_BITS, a segment of more than 32 entries marks its indices in a
+// bitmap in shared memory and places each entry at its rank, the popcount
+// of the bits below it (a block-wide prefix over the bitmap's words, then
+// one word): O(n + nbits/32) per segment.  Otherwise bitonic in shared
+// memory up to 2048 entries, and longer segments rank each entry by
+// counting (indices within a segment are distinct).  Used to give gathered
+// columns a reproducible order.
 constexpr int SEG_SORT_MAX = 2048;
+constexpr int SEG_BITS = 65536;
+constexpr int SEG_WORDS = SEG_BITS / 32;
 
 __global__ void __launch_bounds__(256)
     k_sort_segments(const unsigned long long* __restrict__ ptr, int64_t nseg,
                     int32_t* __restrict__ idx, int32_t* __restrict__ val,
-                    int32_t* __restrict__ tmp_idx, int32_t* __restrict__ tmp_val) {
+                    int32_t* __restrict__ tmp_idx, int32_t* __restrict__ tmp_val, int nbits) {
   __shared__ int32_t ks[SEG_SORT_MAX];
   __shared__ int32_t vs[SEG_SORT_MAX];
+  __shared__ unsigned bits[SEG_WORDS];
+  __shared__ unsigned pre[SEG_WORDS];
+  __shared__ unsigned wtot[8];
+  const int nwords = (nbits + 31) >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t g = blockIdx.x; g < nseg; g += gridDim.x) {
     const unsigned long long a = ptr[g], b = ptr[g + 1];
     const int n = (int)(b - a);
     if (n <= 1) continue;
-    if (n <= SEG_SORT_MAX) {
+    if (nbits > 0 && n > 32) {
+      for (int w = threadIdx.x; w < nwords; w += blockDim.x) bits[w] = 0u;
+      __syncthreads();
+      for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int m = idx[a + e];
+        atomicOr(&bits[m >> 5], 1u << (m & 31));
+      }
+      __syncthreads();
+      // exclusive prefix of the words' popcounts: each thread a run of
+      // consecutive words, then the threads' totals across the block
+      const int per = (nwords + blockDim.x - 1) / blockDim.x;
+      const int w0 = threadIdx.x * per;
+      unsigned mine = 0;
+      for (int w = w0; w < min(w0 + per, nwords); ++w) mine += __popc(bits[w]);
+      unsigned inc = mine;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+      }
+      if (lane == 31) wtot[warp] = inc;
+      __syncthreads();
+      unsigned off = inc - mine;
+      for (int q = 0; q < warp; ++q) off += wtot[q];
+      for (int w = w0; w < min(w0 + per, nwords); ++w) {
+        pre[w] = off;
+        off += __popc(bits[w]);
+      }
+      __syncthreads();
+      const bool smem = n <= SEG_SORT_MAX;
+      for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int m = idx[a + e];
+        const int r = (int)pre[m >> 5] + __popc(bits[m >> 5] & ((1u << (m & 31)) - 1u));
+        if (smem) {
+          ks[r] = m;
+          vs[r] = val[a + e];
+        } else {
+          tmp_idx[a + r] = m;
+          tmp_val[a + r] = val[a + e];
+        }
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        idx[a + e] = smem ? ks[e] : tmp_idx[a + e];
+        val[a + e] = smem ? vs[e] : tmp_val[a + e];
+      }
+      __syncthreads();
+    } else if (n <= SEG_SORT_MAX) {
       int m = 1;
       while (m < n) m <<= 1;
       for (int e = threadIdx.x; e < m; e += blockDim.x) {
@@ -606,11 +665,13 @@ __global__ void __launch_bounds__(256)
 }
 
 void launch_sort_segments(const uint64_t* ptr, int64_t nseg, int32_t* idx, int32_t* val,
-                          int32_t* tmp_idx, int32_t* tmp_val, cudaStream_t st) {
+                          int32_t* tmp_idx, int32_t* tmp_val, int64_t index_range,
+                          cudaStream_t st) {
   if (nseg <= 0) return;
+  const int nbits = index_range > 0 && index_range <= SEG_BITS ? (int)index_range : 0;
   CTD_LAUNCH(k_sort_segments, ((unsigned)std::min<int64_t>(nseg, (int64_t)num_sms() * 8)), (256), 0,
              st, reinterpret_cast<const unsigned long long*>(ptr), nseg, idx, val, tmp_idx,
-             tmp_val);
+             tmp_val, nbits);
 }
 
 void launch_sort_rows(const uint64_t* rowptr, int64_t n_rows, const int32_t* col_in,
