@@ -581,7 +581,7 @@ ctd_status static_impl(const CooDev& X, int64_t s, double eps, uint64_t seed, in
     if (real)
       STEP(real_gram(rc_ptr, rc_row, rc_val, d_count, su, M.n_rows, G, scratch, st));
     else
-      STEP(launch_spmm_dense(M.csc(), F->Iu, d_count, su, Rc, G, su, st));
+      STEP(launch_spmm_dense(M.csc(), F->Iu, d_count, su, Rc, G, su, st, &scratch));
     launch_thresholds(G, su, su, 1.0, xn2, st);
   }
   FilterIn fi;

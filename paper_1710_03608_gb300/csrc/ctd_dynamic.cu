@@ -550,7 +550,7 @@ extern "C" ctd_status ctd_dynamic_step(ctd_factors* F, const ctd_coo3* dXd, int6
     {
       PhaseScope ph("d_gram", st);
       CTD_TRY(launch_spmm_dense(M.csc(), D.lastIu, d_count, du,
-                                CsrDev{rcr_ptr, rcr_col, rcr_val, du}, G0, du, st));
+                                CsrDev{rcr_ptr, rcr_col, rcr_val, du}, G0, du, st, &scratch));
       launch_thresholds(G0, du, du, 1.0, xn2, st);  // ||x_k||^2
     }
     const int64_t dt0 = dt;  // W_K of the whole step, against Q^(t), for the M chain

@@ -320,10 +320,13 @@ struct CsrDev {        // a factor by row: row i holds (col, val) pairs
 };
 
 // Dense products: out(:, c) = R^T x_{fibers[c]} for c < nf (column-major,
-// leading dimension ld), exact integer sums stored as double.
+// leading dimension ld), exact integer sums stored as double.  With a
+// scratch arena (and R at most 6,144 wide) each column's entries are spread
+// over several blocks through an int64 accumulator; without, a block per
+// column.
 ctd_status launch_spmm_dense(const CscDev& X, const int64_t* fibers, const int* nf_dev,
                              int nf_max, const CsrDev& R, double* out, int64_t ld,
-                             cudaStream_t st);
+                             cudaStream_t st, Arena* scratch = nullptr);
 
 // Sparse product C = R^T X_(alpha) over all n_cols columns.
 // bounds: ub[f] = min(width, sum of R row lengths over column f) rounded up

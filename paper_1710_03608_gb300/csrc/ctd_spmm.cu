@@ -69,10 +69,61 @@ __global__ void __launch_bounds__(SPMM_THREADS)
   }
 }
 
+// The same product with each column's entries spread over up to GS_SLICES
+// blocks (block (c, s) takes the column's 32-entry chunks s, s + GS_SLICES,
+// ... over its warps), so that the longest columns, those with the frequent
+// mode-alpha indices, do not leave one block working alone; each block adds
+// its integer partial sums into an int64 accumulator (exact in any order),
+// which a second pass converts.
+constexpr int GS_SLICES = 8;
+
+__global__ void __launch_bounds__(SPMM_THREADS)
+    k_spmm_dense_sliced(CscDev X, const int64_t* __restrict__ fibers, const int* nf_dev,
+                        int nf_max, CsrDev R, unsigned long long* __restrict__ gacc) {
+  extern __shared__ unsigned long long acc[];
+  const int nf = min(*nf_dev, nf_max);
+  const int c = blockIdx.x, sl = blockIdx.y;
+  if (c >= nf) return;
+  const int64_t f = fibers[c];
+  const unsigned long long nchunk = (X.colptr[f + 1] - X.colptr[f] + 31) / 32;
+  if ((unsigned long long)sl >= nchunk) return;  // uniform over the block
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int m = threadIdx.x; m < R.width; m += blockDim.x) acc[m] = 0;
+  __syncthreads();
+  accumulate_column(X, R, f, acc, nullptr, sl + GS_SLICES * warp, GS_SLICES * nw);
+  __syncthreads();
+  unsigned long long* g = gacc + (int64_t)c * R.width;
+  for (int m = threadIdx.x; m < R.width; m += blockDim.x)
+    if (acc[m]) atomicAdd(g + m, acc[m]);
+}
+
+__global__ void k_gram_convert(const unsigned long long* __restrict__ gacc, const int* nf_dev,
+                               int nf_max, int width, double* __restrict__ out, int64_t ld) {
+  const int nf = min(*nf_dev, nf_max);
+  const int64_t total = (int64_t)nf * width;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / width, m = e % width;
+    out[c * ld + m] = (double)(long long)gacc[e];
+  }
+}
+
 ctd_status launch_spmm_dense(const CscDev& X, const int64_t* fibers, const int* nf_dev,
                              int nf_max, const CsrDev& R, double* out, int64_t ld,
-                             cudaStream_t st) {
+                             cudaStream_t st, Arena* scratch) {
   if (nf_max <= 0 || R.width <= 0) return CTD_OK;
+  if (scratch && (size_t)R.width * sizeof(unsigned long long) <= 48 * 1024) {
+    unsigned long long* gacc;
+    CTD_TRY(scratch->get(&gacc, (size_t)nf_max * R.width));
+    CTD_CUDA(cudaMemsetAsync(gacc, 0, (size_t)nf_max * R.width * sizeof(unsigned long long), st));
+    CTD_LAUNCH(k_spmm_dense_sliced, (dim3((unsigned)nf_max, GS_SLICES)), (SPMM_THREADS),
+               (size_t)R.width * sizeof(unsigned long long), st, X, fibers, nf_dev, nf_max, R,
+               gacc);
+    CTD_LAUNCH(k_gram_convert, (grid_for((int64_t)nf_max * R.width, 256, (int64_t)num_sms() * 8)),
+               (256), 0, st, gacc, nf_dev, nf_max, R.width, out, ld);
+    CTD_CUDA(cudaGetLastError());
+    return CTD_OK;
+  }
   if (R.width > CTA_MODE_MAX_WIDTH)
     return fail(CTD_EINVAL, "factor wider than the supported maximum (24576 columns)");
   const size_t smem = (size_t)R.width * sizeof(unsigned long long);
