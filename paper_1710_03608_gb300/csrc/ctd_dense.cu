@@ -13,16 +13,18 @@
 //
 // The factorization is one cooperative launch (a block per SM), blocked by
 // 32 columns: four warps of block 0 (one per SM sub-partition) decide and
-// factor each diagonal block in order, in registers, right after their own
-// trailing tile of the previous panel (lookahead); the blocks then solve
-// the panel's rows and apply the trailing update in 32 x 32 tiles, with
-// two bounded grid barriers per panel.  All arithmetic is FP64 on the
-// CUDA cores.
+// factor each diagonal block in order, in registers, as soon as its update
+// by the previous panel is done (lookahead): that update is split by rows
+// over four blocks, which signal block 0 through a counter (a bounded
+// wait), while the other blocks apply the rest of the trailing update in
+// 32 x 32 tiles; the blocks then solve the next panel's rows.  Two bounded
+// grid barriers per panel.  All arithmetic is FP64 on the CUDA cores.
 #include "ctd_internal.cuh"
 
 namespace ctd {
 
 constexpr int NB = 32;
+constexpr int TQ = 4;  // blocks that share the update of the next diagonal block
 
 // ---------------------------------------------------------------------------
 // generic FP64 GEMM: C = alpha op(A) op(B) + beta C (column-major)
@@ -292,6 +294,7 @@ struct CholShared {
   int force_s[NB];
   double fpiv_s[NB];
   double colc[2][NB];  // the column just finished (double-buffered)
+  int okq;             // block 0: the parts of the next diagonal block arrived
 };
 
 __device__ void chol_diag_block(double* __restrict__ A, int64_t n, int64_t lda, int64_t k0,
@@ -391,6 +394,8 @@ __global__ void __launch_bounds__(256, 1)
   double* invd = sh.invd;
   int* kp = sh.kp;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned* handoff = status + 3;  // parts of the next diagonal block done
+  int panels = 0;
   // the first diagonal block; every later one is factored by block 0 right
   // after its own trailing tile (tile 0 of the previous panel, which is that
   // diagonal block), overlapping the other blocks' trailing updates
@@ -431,10 +436,46 @@ __global__ void __launch_bounds__(256, 1)
     }
     __threadfence();
     if (!grid_sync(gb)) return;
-    // --- C: trailing update of the lower triangle, 32 x 32 tiles over blocks
+    // --- C: trailing update of the lower triangle, 32 x 32 tiles.  Tile 0,
+    // the next diagonal block (which the next panel's factorization waits
+    // for), is split by rows over the first TQ blocks; block 0 then waits
+    // (bounded) for the other parts and factors it while the other blocks
+    // take the remaining tiles.  Every entry is the same fma sequence as in
+    // a whole-tile update.
     const int64_t tb = (rest + NB - 1) / NB;
     const int64_t ntiles = tb * (tb + 1) / 2;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int tq = (int)min((int64_t)TQ, (int64_t)gridDim.x);
+    if ((int)blockIdx.x < tq) {
+      constexpr int QR = NB / TQ;  // rows of a part
+      for (int qq = blockIdx.x; qq < TQ; qq += tq) {
+        const int64_t ra = k1 + (int64_t)qq * QR;
+        __syncthreads();
+        for (int e = tid; e < NB * NB; e += blockDim.x) {
+          const int rr = e % NB, q = e / NB;
+          if (rr < QR) D[rr][q] = (ra + rr < n && q < nb) ? A[(ra + rr) + (k0 + q) * lda] : 0.0;
+          Pc[rr][q] = (k1 + rr < n && q < nb) ? A[(k1 + rr) + (k0 + q) * lda] : 0.0;
+        }
+        __syncthreads();
+        const int rr = tid % QR, cc = tid / QR;
+        const int64_t r = ra + rr, c = k1 + cc;
+        if (cc < NB && r < n && c < n && r >= c) {
+          double s2 = 0.0;
+#pragma unroll
+          for (int q = 0; q < NB; ++q) s2 = fma(D[rr][q], Pc[cc][q], s2);
+          A[r + c * lda] -= s2;
+        }
+      }
+      if (blockIdx.x != 0) {
+        __syncthreads();
+        if (tid == 0) {
+          __threadfence();
+          atomicAdd(handoff, (unsigned)((TQ - 1 - (int)blockIdx.x) / tq + 1));
+        }
+      }
+    }
+    const int first = gridDim.x > 1 ? 1 : 0;  // block 0 goes on to the diagonal block
+    for (int64_t t = 1 + (int64_t)blockIdx.x - first; (int)blockIdx.x >= first && t < ntiles;
+         t += (int64_t)gridDim.x - first) {
       int64_t bi = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
       while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
       while (bi * (bi + 1) / 2 > t) --bi;
@@ -461,7 +502,28 @@ __global__ void __launch_bounds__(256, 1)
       }
     }
     if (blockIdx.x == 0) {
-      __syncthreads();  // tile 0 (the next diagonal block) is written by this block
+      // the other parts of tile 0: a counter the part blocks raise, bounded wait
+      ++panels;
+      __syncthreads();
+      if (tid == 0) {
+        sh.okq = 1;
+        const unsigned others = (unsigned)(TQ - (TQ + tq - 1) / tq);
+        const unsigned target = others * (unsigned)panels;
+        volatile unsigned* vh = handoff;
+        volatile unsigned* vstat = status;
+        long long spins = 0;
+        while (*vh < target) {
+          if ((*vstat & DEV_TIMEOUT) || ++spins > BARRIER_SPIN_LIMIT) {
+            atomicOr(status, DEV_TIMEOUT);
+            sh.okq = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+        __threadfence();
+      }
+      __syncthreads();
+      if (!sh.okq) return;
       chol_diag_block(A, n, lda, k1, thr, force, fpiv, keep, piv, status, sh);
     }
     __threadfence();
@@ -473,9 +535,10 @@ ctd_status launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr
                             cudaStream_t st, const int* force, double* piv, unsigned* status,
                             const double* fpiv) {
   if (n <= 0) return CTD_OK;
-  // barrier words live in the status array's tail: status[1] count, status[2] generation
+  // barrier words live in the status array's tail: status[1] count, status[2]
+  // generation, status[3] the parts of each next diagonal block done
   GridBar gb{status + 1, status + 2, status};
-  CTD_CUDA(cudaMemsetAsync(status + 1, 0, 2 * sizeof(unsigned), st));
+  CTD_CUDA(cudaMemsetAsync(status + 1, 0, 3 * sizeof(unsigned), st));
   int per_sm = 0;
   CTD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_coop, 256, 0));
   if (per_sm <= 0) return fail(CTD_ECUDA, "the skip-Cholesky kernel cannot be resident");

@@ -433,8 +433,9 @@ void dgemm(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, cons
 // diagonal (the explicit residual's squared norm).  piv (optional)
 // receives each column's pivot before its decision; a forced keep without a
 // positive pivot sets DEV_CAPACITY in status[0]; a grid barrier that gives
-// up sets DEV_TIMEOUT.  status must hold 3 words (status[1..2] are the grid
-// barrier's counter and generation).
+// up sets DEV_TIMEOUT.  status must hold 4 words (status[1..2] are the grid
+// barrier's counter and generation, status[3] counts the parts of each next
+// diagonal block's update).
 ctd_status launch_chol_skip(double* A, int64_t n, int64_t lda, const double* thr, int* keep,
                             cudaStream_t st, const int* force, double* piv, unsigned* status,
                             const double* fpiv = nullptr);
