@@ -452,6 +452,13 @@ CTD_API ctd_status ctd_profile_report(char* buf, size_t len);
 CTD_API ctd_status ctd_fault_inject_alloc(int64_t fail_after);
 CTD_API ctd_status ctd_selftest_bounded_wait(int64_t spin_limit, void* stream);
 
+/* Self-test of the skip-Cholesky's FP64 inverse square root (no
+ * counterpart in the paper): for the n host values d[i] > 0, out[i] = the
+ * library's 1/sqrt(d[i]) and ref[i] = CUDA's 1.0 / sqrt(d[i]), both
+ * computed on the device.  n in [0, 2^24]; CTD_EINVAL otherwise or on
+ * NULL arrays. */
+CTD_API ctd_status ctd_selftest_rsqrt(const double* d, int64_t n, double* out, double* ref);
+
 /* Message of the last failing call on this thread ("" if none). */
 CTD_API const char* ctd_last_error(void);
 

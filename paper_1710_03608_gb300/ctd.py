@@ -37,7 +37,8 @@ EXPORTED = ["ctd_static", "ctd_dynamic_create", "ctd_dynamic_step", "ctd_error",
             "ctd_server_wait", "ctd_server_result", "ctd_server_state", "ctd_server_free",
             "ctd_ddos_candidates", "ctd_dynamic_from_static", "ctd_fault_inject_alloc",
             "ctd_selftest_bounded_wait", "ctd_set_allocator", "ctd_allocated_bytes",
-            "ctd_static_nway", "ctd_get_R_f64", "ctd_set_tuning", "ctd_get_tuning"]
+            "ctd_static_nway", "ctd_get_R_f64", "ctd_set_tuning", "ctd_get_tuning",
+            "ctd_selftest_rsqrt"]
 
 
 class CtdError(RuntimeError):
@@ -119,6 +120,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ctd_static_nway": [C.POINTER(ctd_coon), I32, I64, D, U64, I32, C.c_uint, P, C.POINTER(P)],
         "ctd_allocated_bytes": [C.POINTER(C.c_size_t)],
         "ctd_set_tuning": [C.c_char_p, I64],
+        "ctd_selftest_rsqrt": [P, I64, P, P],
         "ctd_get_tuning": [C.c_char_p, C.POINTER(C.c_int64)],
     }
     for name, args in sig.items():
@@ -162,6 +164,15 @@ def use_torch_allocator(enable: bool = True) -> None:
     alloc = C.cast(_shim.ctd_torch_alloc, C.c_void_p)
     release = C.cast(_shim.ctd_torch_release, C.c_void_p)
     _check(lib.ctd_set_allocator(alloc, release))
+
+
+def selftest_rsqrt(d):
+    """(library's 1/sqrt, CUDA's 1.0/sqrt) of the FP64 array d, on the device."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    out = np.empty_like(d)
+    ref = np.empty_like(d)
+    _check(load().ctd_selftest_rsqrt(_ptr(d), int(d.size), _ptr(out), _ptr(ref)))
+    return out, ref
 
 
 TUNING_KEYS = ("qform_hot_kb", "cfill_dense_kb", "copy_blocks_per_sm")
