@@ -277,7 +277,17 @@ __device__ bool grid_sync(const GridBar& gb) {
 // takes one inverse square root per column in sequence.
 __device__ __forceinline__ double rsqrt_fp64(double d) {
   if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-  const double y = (double)rsqrtf((float)d);
+  // the FP32 estimate without FP64 <-> FP32 conversions (which would run on
+  // the FP64 pipe): d's exponent rebiased and its mantissa truncated to 23
+  // bits (relative error below 2^-23), and the estimate widened back
+  // exactly, by integer operations on the bit patterns
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned fb = ((unsigned)(((b >> 52) & 0x7FF) - 1023 + 127) << 23) |
+                      (unsigned)((b >> 29) & 0x7FFFFF);
+  const unsigned yb = __float_as_uint(rsqrtf(__uint_as_float(fb)));
+  const double y = __longlong_as_double(
+      (long long)((((unsigned long long)((yb >> 23) & 0xFF) - 127 + 1023) << 52) |
+                  ((unsigned long long)(yb & 0x7FFFFF) << 29)));
   const double t = d * y;
   const double e = fma(-t, y, 1.0);     // 1 - d y^2
   const double c = fma(e, 0.375, 0.5);  // 1/2 + 3e/8
