@@ -672,14 +672,29 @@ ctd_status static_impl(const CooDev& X, int64_t s, double eps, uint64_t seed, in
   uint64_t cap = 0, nnzR = 0;
   int rmax = -1;
   int* d_rmax = nullptr;
+  // the C fill's column lists come out of the C bounds' pass when the fill
+  // takes its dense-row path (integer values, exact int32 partial sums,
+  // at most 1024 kept fibers)
+  CfillLists lists;
+  const bool fused_lists = !real && T < (1ull << 31) && kept <= 1024;
   if (!(flags & CTD_SKIP_C)) {
     uint32_t* ub;
     STEP(scratch.get(&ub, M.n_cols));
     STEP(F->mem.get(&F->Coff, M.n_cols + 1));
     STEP(F->mem.get(&F->Ccnt, M.n_cols));
+    if (fused_lists) {
+      const int64_t list_cap = std::max<int64_t>(1, std::min<int64_t>(M.n_cols, M.nnz));
+      STEP(scratch.get(&lists.single, list_cap));
+      STEP(scratch.get(&lists.heavy, list_cap));
+      STEP(scratch.get(&lists.multi, list_cap));
+      STEP(scratch.get(&lists.counts, 3));
+    }
     {
       PhaseScope ph("c_bounds", st);
-      launch_c_bounds(M.csc(), M.n_cols, R, ub, st);
+      if (fused_lists)
+        STEP(launch_c_bounds_lists(M.csc(), M.n_cols, R, ub, minval > 0, F->Ccnt, lists, st));
+      else
+        launch_c_bounds(M.csc(), M.n_cols, R, ub, st);
       launch_scan_u32(ub, F->Coff, M.n_cols, false, M.tmp, M.status, st);
     }
     // largest |R| (the C fill stores its longest rows as int16 when they fit)
@@ -716,7 +731,8 @@ ctd_status static_impl(const CooDev& X, int64_t s, double eps, uint64_t seed, in
                        precision == CTD_FP32_BULK, st));
     else
       STEP(launch_c_fill(M.csc(), M.n_cols, M.n_rows, M.nnz, R, F->Coff, F->Ccnt, F->Crow,
-                         F->Cval, precision == CTD_FP32_BULK, minval > 0, x_int8, T, st));
+                         F->Cval, precision == CTD_FP32_BULK, minval > 0, x_int8, T, st,
+                         fused_lists ? &lists : nullptr));
   }
   uint64_t* d_nnzc;
   STEP(scratch.get(&d_nnzc, 1));

@@ -210,6 +210,84 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// The C bounds and the column lists in one pass (what k_c_bounds and
+// k_classify do separately): per column the bound ub = min(width, sum of
+// the R row lengths of its entries) rounded up to a multiple of 4, written
+// to ub; an empty bound gives ccnt = 0, else the column joins one of the
+// three lists as k_classify would put it (appends warp-aggregated into
+// shared counters, one global atomic per list per block and round).
+__global__ void __launch_bounds__(256)
+    k_bounds_classify(CscDev X, int64_t n_cols, CsrDev R, unsigned* __restrict__ ub, int positive,
+                      unsigned* __restrict__ ccnt, int64_t* __restrict__ single,
+                      int64_t* __restrict__ heavy, int64_t* __restrict__ multi,
+                      unsigned* __restrict__ counts) {
+  __shared__ unsigned cnt[3], base[3];
+  const int lane = threadIdx.x & 31;
+  const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(X.colptr);
+  const unsigned long long* rp = reinterpret_cast<const unsigned long long*>(R.rowptr);
+  const unsigned long long width = (unsigned long long)R.width;
+  const int64_t span = (int64_t)blockDim.x * CL_ITEMS;
+  for (int64_t b0 = (int64_t)blockIdx.x * span; b0 < n_cols; b0 += (int64_t)gridDim.x * span) {
+    if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int kind[CL_ITEMS];
+    unsigned off[CL_ITEMS];
+    unsigned long long xa[CL_ITEMS], xb[CL_ITEMS];
+#pragma unroll
+    for (int u = 0; u < CL_ITEMS; ++u) {
+      const int64_t f = b0 + (int64_t)u * blockDim.x + threadIdx.x;
+      xa[u] = f < n_cols ? xp[f] : 0ull;
+      xb[u] = f < n_cols ? xp[f + 1] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < CL_ITEMS; ++u) {
+      const int64_t f = b0 + (int64_t)u * blockDim.x + threadIdx.x;
+      int k = -1;  // -1 none, 0 single, 1 heavy, 2 multi
+      if (f < n_cols) {
+        unsigned long long sum = 0;
+        for (unsigned long long p = xa[u]; p < xb[u] && sum < width; ++p) {
+          const int i = __ldg(X.row + p);
+          sum += __ldg(rp + i + 1) - __ldg(rp + i);
+        }
+        const unsigned bound = ((unsigned)min(sum, width) + 3u) & ~3u;
+        ub[f] = bound;
+        const unsigned long long nx = xb[u] - xa[u];
+        if (bound == 0)
+          ccnt[f] = 0;
+        else if (nx == 1 && positive)
+          k = 0;
+        else
+          k = nx >= (unsigned long long)CF_HEAVY_COL ? 1 : 2;
+      }
+      kind[u] = k;
+      off[u] = 0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const unsigned m = __ballot_sync(0xffffffffu, k == q);
+        if (!m) continue;
+        const int leader = __ffs(m) - 1;
+        unsigned wb = 0;
+        if (lane == leader) wb = atomicAdd(&cnt[q], (unsigned)__popc(m));
+        wb = __shfl_sync(0xffffffffu, wb, leader);
+        if (k == q) off[u] = wb + __popc(m & ((1u << lane) - 1));
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3)
+      base[threadIdx.x] = cnt[threadIdx.x] ? atomicAdd(counts + threadIdx.x, cnt[threadIdx.x]) : 0;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < CL_ITEMS; ++u) {
+      const int k = kind[u];
+      if (k < 0) continue;
+      const int64_t f = b0 + (int64_t)u * blockDim.x + threadIdx.x;
+      int64_t* out = k == 0 ? single : k == 1 ? heavy : multi;
+      out[base[k] + off[u]] = f;
+    }
+    __syncthreads();
+  }
+}
+
 // four consecutive values, 16-byte aligned (float) or two 16-byte halves (double)
 template <typename V>
 __device__ __forceinline__ void store4(V* p, V a, V b, V c, V d);
@@ -737,20 +815,28 @@ template <typename V>
 ctd_status cf_all(int nq, int db, bool p4, const CscDev& X, int64_t n_cols, int64_t n_rows, const CsrDev& R,
                   const Dense& dn,
                   const unsigned long long* coff, uint32_t* ccnt, uint16_t* crow, V* cval,
-                  int positive, int64_t list_cap, Arena& a, cudaStream_t st) {
+                  int positive, int64_t list_cap, Arena& a, cudaStream_t st,
+                  const CfillLists* lists) {
   int64_t *single, *heavy, *multi;
   unsigned* counts;
   unsigned long long* work;
-  CTD_TRY(a.get(&single, list_cap));
-  CTD_TRY(a.get(&heavy, list_cap));
-  CTD_TRY(a.get(&multi, list_cap));
-  CTD_TRY(a.get(&counts, 3));
   CTD_TRY(a.get(&work, 2));
-  CTD_CUDA(cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned), st));
   CTD_CUDA(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), st));
-  CTD_LAUNCH(k_classify, (grid_for(n_cols, 256 * CL_ITEMS, (int64_t)num_sms() * 8)), (256), 0, st,
-             reinterpret_cast<const unsigned long long*>(X.colptr), coff, n_cols, positive, ccnt,
-             single, counts, heavy, counts + 1, multi, counts + 2);
+  if (lists) {  // built with the C bounds
+    single = lists->single;
+    heavy = lists->heavy;
+    multi = lists->multi;
+    counts = lists->counts;
+  } else {
+    CTD_TRY(a.get(&single, list_cap));
+    CTD_TRY(a.get(&heavy, list_cap));
+    CTD_TRY(a.get(&multi, list_cap));
+    CTD_TRY(a.get(&counts, 3));
+    CTD_CUDA(cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned), st));
+    CTD_LAUNCH(k_classify, (grid_for(n_cols, 256 * CL_ITEMS, (int64_t)num_sms() * 8)), (256), 0,
+               st, reinterpret_cast<const unsigned long long*>(X.colptr), coff, n_cols, positive,
+               ccnt, single, counts, heavy, counts + 1, multi, counts + 2);
+  }
   // row images (see k_img_sizes): P entries per image, a multiple of 4
   unsigned long long *sz, *ip, *stmp;
   unsigned* sstat;
@@ -805,7 +891,7 @@ ctd_status cf_all(int nq, int db, bool p4, const CscDev& X, int64_t n_cols, int6
 ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t nnz,
                              const CsrDev& R, const uint64_t* coff, uint32_t* ccnt,
                              uint16_t* crow, void* cval, int fp32, int positive, int x_int8,
-                             cudaStream_t st) {
+                             cudaStream_t st, const CfillLists* lists) {
   if (R.nnz < 0) return fail(CTD_EINVAL, "C fill: the entry count of R is not set");
   const int width = R.width;
   const int nq0 = (width + 127) / 128;
@@ -843,9 +929,20 @@ ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, in
   const int64_t list_cap = std::max<int64_t>(1, std::min(n_cols, nnz));
   if (fp32)
     return cf_all<float>(nq, db, x_int8 != 0, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<float*>(cval),
-                         positive, list_cap, a, st);
+                         positive, list_cap, a, st, lists);
   return cf_all<double>(nq, db, x_int8 != 0, X, n_cols, n_rows, R, dn, co, ccnt, crow, static_cast<double*>(cval),
-                        positive, list_cap, a, st);
+                        positive, list_cap, a, st, lists);
+}
+
+ctd_status launch_c_bounds_lists(const CscDev& X, int64_t n_cols, const CsrDev& R, uint32_t* ub,
+                                 int positive, uint32_t* ccnt, const CfillLists& L,
+                                 cudaStream_t st) {
+  CTD_CUDA(cudaMemsetAsync(L.counts, 0, 3 * sizeof(unsigned), st));
+  if (n_cols <= 0) return CTD_OK;
+  CTD_LAUNCH(k_bounds_classify, (grid_for(n_cols, 256 * CL_ITEMS, (int64_t)num_sms() * 8)), (256),
+             0, st, X, n_cols, R, ub, positive, ccnt, L.single, L.heavy, L.multi, L.counts);
+  CTD_CUDA(cudaGetLastError());
+  return CTD_OK;
 }
 
 }  // namespace ctd

@@ -344,16 +344,32 @@ void launch_c_bounds(const CscDev& X, int64_t n_cols, const CsrDev& R, uint32_t*
 // double.  R's rows must be sorted by column.  positive: every value of X
 // and R is > 0 (enables the one-nonzero copy path).  x_int8: every value of
 // X is in [-128, 127] (four products per instruction on int8 rows of R).
+// The C fill's column lists (built with the C bounds by
+// launch_c_bounds_lists): one-nonzero columns, columns with at least 128
+// nonzeros, the other multi-nonzero columns, and their three counts.
+struct CfillLists {
+  int64_t* single = nullptr;
+  int64_t* heavy = nullptr;
+  int64_t* multi = nullptr;
+  unsigned* counts = nullptr;
+};
 ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t nnz,
                          const CsrDev& R, const uint64_t* coff, uint32_t* ccnt, uint16_t* crow,
                          void* cval, int fp32, int positive, int x_int8, uint64_t sqnorm_X,
-                         cudaStream_t st);
+                         cudaStream_t st, const CfillLists* lists = nullptr);
 // The same with the longest rows of R dense in shared memory and register
 // accumulators (ctd_cfill.cu); requires sqnorm_X < 2^31 and width <= 1024.
 ctd_status c_fill_dense_rows(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t nnz,
                              const CsrDev& R, const uint64_t* coff, uint32_t* ccnt,
                              uint16_t* crow, void* cval, int fp32, int positive, int x_int8,
-                             cudaStream_t st);
+                             cudaStream_t st, const CfillLists* lists = nullptr);
+// The C bounds (as launch_c_bounds) and, in the same pass over the columns,
+// the C fill's column lists (list_cap entries each; counts zeroed here) and
+// ccnt = 0 for the columns C leaves empty.  positive: every value of X and R
+// is > 0 (one-nonzero columns are then copies).
+ctd_status launch_c_bounds_lists(const CscDev& X, int64_t n_cols, const CsrDev& R, uint32_t* ub,
+                                 int positive, uint32_t* ccnt, const CfillLists& L,
+                                 cudaStream_t st);
 // list[0..count) = columns with >= minc nonzeros and a nonzero C bound
 void launch_list_columns(const uint64_t* colptr, const uint64_t* coff, int64_t n_cols,
                          uint64_t minc, int64_t* list, unsigned* count, cudaStream_t st);

@@ -462,7 +462,7 @@ static ctd_status c_fill_impl(const CscDev& X, int64_t n_cols, const CsrDev& R,
 ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_t nnz,
                          const CsrDev& R, const uint64_t* coff, uint32_t* ccnt, uint16_t* crow,
                          void* cval, int fp32, int positive, int x_int8, uint64_t sqnorm_X,
-                         cudaStream_t st) {
+                         cudaStream_t st, const CfillLists* lists) {
   if (n_cols <= 0) return CTD_OK;
   if (R.width <= 0) {
     CTD_CUDA(cudaMemsetAsync(ccnt, 0, n_cols * sizeof(uint32_t), st));
@@ -473,7 +473,7 @@ ctd_status launch_c_fill(const CscDev& X, int64_t n_cols, int64_t n_rows, int64_
   // accumulators cover the width: dense long rows + registers
   if (sqnorm_X < (1ull << 31) && R.width <= 1024)
     return c_fill_dense_rows(X, n_cols, n_rows, nnz, R, coff, ccnt, crow, cval, fp32, positive,
-                             x_int8, st);
+                             x_int8, st, lists);
   unsigned long long* work;
   int64_t* heavy;
   unsigned* nheavy;
