@@ -470,12 +470,15 @@ def ncu_launch_summary(csv_path: str, top: int = 30) -> str:
     hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
     h = rows[hi]
     ki, vi, ui = h.index("Kernel Name"), h.index("Metric Value"), h.index("Metric Unit")
+    mi = h.index("Metric Name") if "Metric Name" in h else None
     scale = {"ns": 1e-6, "nsecond": 1e-6, "us": 1e-3, "usecond": 1e-3, "ms": 1.0,
              "msecond": 1.0, "s": 1e3, "second": 1e3}
     agg = collections.defaultdict(lambda: [0, 0.0])
     for r in rows[hi + 1:]:
         if len(r) <= vi:
             continue
+        if mi is not None and r[mi] != "gpu__time_duration.sum":
+            continue  # other metrics of the same launch (a DRAM capture)
         name = r[ki].split("(")[0].replace("void ", "")
         agg[name][0] += 1
         agg[name][1] += float(r[vi].replace(",", "")) * scale.get(r[ui], 1.0)

@@ -111,3 +111,23 @@ def test_dram_summary_groups_metrics_by_launch(tmp_path):
     assert float(a[4]) == pytest.approx(1500.0) and float(a[5]) == pytest.approx(1.5)
     b = out[2].split()
     assert b[0] == "ctd::k_b" and float(b[4]) == pytest.approx(100.0)
+
+
+def test_launch_summary_counts_only_durations(tmp_path):
+    """On a capture with DRAM metrics beside the duration, the launch list
+    sums the durations alone."""
+    from paper_1710_03608_gb300 import measure
+    p = tmp_path / "mixed.csv"
+    with open(p, "w", newline="") as f:
+        w = csv.writer(f, quoting=csv.QUOTE_ALL)
+        w.writerow(HEADER)
+        for lid, metric, unit, value in [(0, "dram__bytes_read.sum", "Mbyte", "500"),
+                                         (0, "gpu__time_duration.sum", "usecond", "100"),
+                                         (1, "dram__bytes_write.sum", "byte", "7"),
+                                         (1, "gpu__time_duration.sum", "usecond", "300")]:
+            w.writerow([lid, 1, "python", "h", "void ctd::k_a(int)", 1, 7, "(256, 1, 1)",
+                        "(152, 1, 1)", 0, "10.3", "Command line profiler metrics", metric, unit,
+                        value])
+    out = measure.ncu_launch_summary(str(p)).splitlines()
+    row = out[1].split()
+    assert row[0] == "ctd::k_a" and row[1] == "2" and float(row[2]) == pytest.approx(0.4)
