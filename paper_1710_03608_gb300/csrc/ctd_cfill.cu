@@ -5,16 +5,20 @@
 // traffic tensor with 10^7 nonzeros and s~ = 456, the 100 longest of 8.5K
 // nonempty rows carry 95% of the 1.5 * 10^9 products.  Walking such a row
 // costs two global loads and one shared-memory atomic per product.  Here the
-// H longest rows live densely in shared memory (int32, padded to NQ * 128
-// columns), and lane l of a warp owns output rows m = 128 q + 4 l + {0..3}
-// in registers: one dense row adds into them with NQ 128-bit shared loads
-// and 4 NQ integer multiply-adds, no atomics.  The other rows go through a
+// H longest rows live densely in shared memory (int8, int16 or int32, the
+// narrowest R's values fit, padded to NQ * 128 columns), and lane l of a
+// warp owns output rows m = 128 q + 4 l + {0..3} in registers: dense rows
+// add into them from shared loads with integer multiply-adds (with int8
+// rows and X's values in int8, four rows at a time by dp4a), no atomics.  The other rows go through a
 // sparse walk into a per-warp shared accumulator, and the emission adds the
 // two, compacts the nonzeros of each 128-row slab (ballots) through shared
 // memory and writes them in ascending row order, consecutive lanes on
 // consecutive entries.  A column with one nonzero v at row
 // i is v R(i, :): those are copied from images of R's rows laid out so that
 // every copy moves aligned 8- and 16-byte vectors (k_img_fill, k_copy_flat).
+// The columns are sorted into those kinds by k_bounds_classify, in the pass
+// that computes their capacities (or by k_classify where that pass is the
+// plain one).
 //
 // Exactness: every partial sum is an integer of magnitude at most
 // ||x_f|| ||r_m|| <= ||X||_F^2 < 2^31 (Cauchy-Schwarz); this path is taken
@@ -139,7 +143,7 @@ __device__ __forceinline__ void load_dense(const CsrDev& R, const Dense& dn, voi
 // R (`single`, count = ub); at least CF_HEAVY_COL nonzeros: `heavy`; else
 // `multi`.  Appends are warp-aggregated; the order inside a list does not
 // matter (every column writes its own output range).
-constexpr int CL_ITEMS = 8;  // columns per thread in k_classify
+constexpr int CL_ITEMS = 8;  // columns per thread in k_classify and k_bounds_classify
 
 __global__ void __launch_bounds__(256)
     k_classify(const unsigned long long* __restrict__ xp,
