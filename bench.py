@@ -258,6 +258,38 @@ def small_latency(ctd, synth, st, gpu):
             "clocks": clocks.summary()}
 
 
+def stream_form(ctd, synth, gpu, steps=6):
+    """The first `steps` of the CTD-D stream of 20,000 x 20,000 slices (5*10^5
+    Zipf(1.1) nonzeros each, Poisson(2)+1 counts, d = 400, FP32 bulk): device
+    time of each step (synchronized on both sides), slices built on the host
+    before it.  The early steps are the cheap ones: the basis is still
+    small; the whole 100-step stream is measured by `measure.py stream`."""
+    import torch
+    st = synth.traffic_stream_20k(scale=1.0, steps=100)
+    G = ctd.Dynamic(st.dims2, 1, ctd.CTD_FP32_BULK, 0, 0, ctd.CTD_KEEP_LAST_C)
+    clocks = ClockSampler(gpu)
+    per, tot_nnz, tot_s = [], 0, 0.0
+    slices = [st.slice(t) for t in range(steps)]
+    clocks.start()
+    for t, sl in enumerate(slices):
+        X = ctd.Coo.from_synth(sl)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.step_slice(X, 400, EPS)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        per.append(round(dt * 1e3, 3))
+        tot_nnz += sl.nnz
+        tot_s += dt
+    clocks.stop()
+    out = {"workload": f"first {steps} of 100 CTD-D steps, 20000x20000 slices, "
+                       f"{st.nnz} nonzeros each, d = 400, FP32 bulk",
+           "nnz_per_s": tot_nnz / tot_s, "ms_per_step": per, "d_kept": int(G.sizes().s_kept),
+           "rel_error": G.error(), "clocks": clocks.summary()}
+    G.free()
+    return out
+
+
 def batched_form(ctd, synth, gpu):
     """The 256-tensor law (I, J log-uniform in [500, 2*10^4], K in [10, 500],
     nnz log-uniform in [10^4, 2*10^6], Zipf(1.2) ids, Poisson(3)+1 counts,
@@ -508,6 +540,10 @@ def ours(args):
         extra["kernel_autotune"] = tune
     if rank == 0 and world == 1 and not args.no_extra and args.scale == 1.0:
         extra["small_tensor_latency"] = small_latency(ctd, synth, st, local)
+        try:
+            extra["stream"] = stream_form(ctd, synth, local)
+        except Exception as e:  # a sample of another config must not cost the line
+            extra["stream"] = {"error": f"{type(e).__name__}: {e}"}
         extra["batched"] = batched_form(ctd, synth, local)
         extra["serving"] = serving_form(ctd, synth, local)
 
