@@ -13,7 +13,7 @@
 // B^T U B with the explicit inverse would amplify them by kappa and keep
 // dependent fibers.  The block form takes the same decisions as the
 // sequential loop.  With Y_K = U^(t) B_K and S_K = L_S L_S^T, the rank-|K|
-// update of U is the block form of Algorithm 1's update of U applied |K| times:
+// update of U is Algorithm 1's bordered update applied |K| times, in block form:
 //     U^(t+1) = [[U + Y_K S_K^{-1} Y_K^T, -Y_K S_K^{-1}], [., S_K^{-1}]].
 // C update: the new columns R^(t+1)^T dX are computed exactly; the
 // lower-left block ((dR)^T R^(t)) U^(t) C^(t) of Eq. (C_t+1_final) is kept
