@@ -51,6 +51,10 @@ struct ctd_server {
   size_t budget = 0;   // with an allocator hook: bytes the library may hold
   int dev = 0;
   std::vector<ctd_factors*> states;
+  // per stream, the state's kept count and column count after its last
+  // finished step: submit sizes its estimate from these (under the lock)
+  // rather than reading a state that a worker may be updating
+  std::vector<int64_t> kept_seen, cols_seen;
   std::vector<std::deque<int64_t>> queue;   // tickets per stream
   std::vector<char> busy;
   std::vector<Request> req;                  // by ticket
@@ -65,11 +69,11 @@ struct ctd_server {
 
 namespace {
 
-size_t step_estimate(const ctd_factors* F, const ctd_coo3& X, int64_t d) {
-  const double dt = (double)F->s_kept + (double)d;
+size_t step_estimate(int64_t s_kept, int64_t n_cols, const ctd_coo3& X, int64_t d) {
+  const double dt = (double)s_kept + (double)d;
   // COO staging + CSC + CDF (~64 B/nnz), candidates' Gram/Schur/W (FP64),
   // U/L growth, the new-column block (bounded by nnz * d~ / 8 B on average)
-  return (size_t)(64.0 * X.nnz + 8.0 * (double)F->n_cols * 6.0 + 24.0 * dt * d +
+  return (size_t)(64.0 * X.nnz + 8.0 * (double)n_cols * 6.0 + 24.0 * dt * d +
                   16.0 * dt * dt * 0.25 + 12.0 * (double)X.nnz * 16.0);
 }
 
@@ -121,6 +125,8 @@ void worker(ctd_server* S, int w) {
     {
       std::lock_guard<std::mutex> lk(S->mu);
       r.done = true;
+      S->kept_seen[r.stream] = S->states[r.stream]->s_kept;
+      S->cols_seen[r.stream] = S->states[r.stream]->n_cols;
       S->busy[r.stream] = 0;
       S->running_bytes -= r.estimate;
       S->running -= 1;
@@ -167,6 +173,12 @@ extern "C" ctd_status ctd_server_create(int n_streams, const int64_t dims2[2], i
       return rc;
     }
   }
+  S->kept_seen.assign(n_streams, 0);
+  S->cols_seen.assign(n_streams, 0);
+  for (int k = 0; k < n_streams; ++k) {
+    S->kept_seen[k] = S->states[k]->s_kept;
+    S->cols_seen[k] = S->states[k]->n_cols;
+  }
   S->cstream.assign(workers, nullptr);
   for (int w = 0; w < workers; ++w)
     if (cudaStreamCreateWithFlags(&S->cstream[w], cudaStreamNonBlocking) != cudaSuccess) {
@@ -199,7 +211,7 @@ extern "C" ctd_status ctd_server_submit(ctd_server* S, int stream_id, const ctd_
   r.stream = stream_id;
   r.X = *dX;
   r.t_submit = Clock::now();
-  r.estimate = step_estimate(S->states[stream_id], *dX, S->d);
+  r.estimate = step_estimate(S->kept_seen[stream_id], S->cols_seen[stream_id], *dX, S->d);
   S->req.push_back(r);
   const int64_t t = (int64_t)S->req.size() - 1;
   S->queue[stream_id].push_back(t);
