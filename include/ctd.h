@@ -11,7 +11,8 @@
  * Conventions for every entry point:
  *  - Tensors are 3-way, in COO form (Section 2.1 "sparse-unordered"):
  *    int32 index vectors i, j, k (0-based) and int32 values.  Coordinates
- *    must be distinct; values may be zero or negative.
+ *    must be distinct; values may be zero or negative.  (ctd_static_nway
+ *    takes tensors of order 1 to 8 with int32 or FP32 values; see there.)
  *  - Mode alpha is 1, 2 or 3 (the paper's 1-based notation).  Column f of
  *    X_(alpha) is the little-endian index over the other two modes
  *    (alpha=1: f = j + J*k; alpha=2: f = i + I*k; alpha=3: f = i + I*j).
@@ -79,7 +80,8 @@ typedef enum {
  * sums over a column's entries (the error through Q, W = Q^T X_c of CTD-D)
  * round differently in the last bits.  With this flag every result is
  * bit-identical from run to run, at the cost of the sort: about 0.4 ms per
- * 10^7 nonzeros on GB300, 7% of a CTD-S call on the traffic tensor. */
+ * 10^7 nonzeros on GB300, about 10% of a CTD-S call on a 10^7-nonzero
+ * traffic tensor. */
 #define CTD_DETERMINISTIC 8u
 /* For ctd_static: keep the column distribution of the draws (the squared
  * column norms and their prefix sums, Eq. 1) in the factors, where
@@ -144,10 +146,11 @@ CTD_API ctd_status ctd_static(const ctd_coo3* X, int alpha, int64_t s, double ep
  *  X        order N in 1 .. CTD_MAX_ORDER, dims[0 .. N), idx[0 .. N) the index
  *           arrays (int32, 0-based), val the values: int32 counts
  *           (val_type CTD_VAL_INT32) or real values as FP32 (CTD_VAL_FP32);
- *           device or host memory.  Real values take the draws on the
- *           squares' fixed-point grid of reading A28 (each square rounded
- *           down to a multiple of 2^-32 of the largest square's power of
- *           two; exact and device-independent) and FP64 arithmetic after the
+ *           device or host memory.  Real values take the draws on a
+ *           fixed-point grid of the squares (each square rounded down to a
+ *           multiple of 2^-32 of the smallest power of two above the
+ *           largest square; exact and device-independent; the paper gives
+ *           the draws of real values no precision) and FP64 arithmetic after the
  *           draws: R, U and C hold the same values as with integers up to
  *           rounding, the error is FP64, and the dense R/C copies this path
  *           makes need I_alpha * s' < 2^31 (else CTD_ENOTSUP).  CTD-D and

@@ -41,14 +41,29 @@ Readings of points the paper leaves open (same letters everywhere):
   A9 a dynamic state may start empty; the first kept fiber then gives
      U = 1/(x^T x), as for Algorithm 1's first kept fiber.
   A10 an all-zero input yields no draws and an empty factor.
+  A12 zero and negative values are allowed; squares are summed exactly, and
+      ||X||^2 (or one column's sum) at or past 2^63 is an overflow error.
+  A14 a residual ratio within 1e-7 of eps is a near-tie; parity cases are
+      checked to have none (the decision there depends on rounding).
+  A17 U is compared within max(1e-10, 1e-15 kappa(R^T R)) relative (both
+      sides carry errors of order kappa u), and the GPU's ||U R^T R - I||
+      may be at most twice this oracle's.
+  A20 CTD-D's error: the reconstruction of earlier columns does not change
+      when R grows, so each step adds ||dX||^2 - ||P dX||^2, P the
+      projector onto range(R) after the step.
   A21 the test's residual is evaluated as x minus its orthogonal projection
       onto range(R), by Gram-Schmidt with reorthogonalization (equal to
       x - R U R^T x in exact arithmetic; stable in floating point).
+  A23 Section 5's average norm is the exact sum of the representatives'
+     norms rounded once, divided by their count (no summation order).
+  A27 an entry of U counts as a nonzero of Eq. (memoryEff) when its
+      magnitude exceeds 1e-12 of U's largest (rounding noise is not fill).
   A28 real values: each square on a fixed-point grid, floor(v^2 2^(32-E))
      with 2^E the smallest power of two above the largest square; the draws
      use those exact integers.
-  A23 Section 5's average norm is the exact sum of the representatives'
-     norms rounded once, divided by their count (no summation order).
+  A29 real values: the error's bar is the FP64 bar widened to
+      4 n u kappa(R^T R) (n rows of R, u = 2^-53), since the Gram matrix of
+      real values is rounded.
 
 Parity pinned by tests/test_oracle_pins.py (brute force, numpy/scipy
 library routines, invariants, chi-square).  The DDoS rule is pinned by a

@@ -5,11 +5,12 @@
 // destination is a candidate when its representative's 2-norm is above the
 // average norm of all representatives.
 //
-// The average is computed without a summation order (reading A23): every
-// norm is a double >= 1 (the square root of a nonzero integer), hence an
-// integer multiple of 2^-52, so the norms are added exactly as 128-bit fixed
-// point numbers and the sum is rounded to double once.  Any parallel
-// evaluation then gives the same bits as the exactly rounded sum.
+// The paper gives the average no precision; here it does not depend on a
+// summation order: every norm is a double >= 1 (the square root of a
+// nonzero integer), hence an integer multiple of 2^-52, so the norms are
+// added exactly as 128-bit fixed point numbers and the sum is rounded to
+// double once.  Any parallel evaluation then gives the same bits as the
+// exactly rounded sum.
 #include "ctd_internal.cuh"
 
 namespace ctd {

@@ -467,7 +467,7 @@ ctd_status run_filter(const FilterIn& in, FilterOut& out, Arena& scratch, cudaSt
     bool changed = false;
     for (int c = 0; c < ns && !changed; ++c) {
       const int k = sus[c];
-      const int explicit_keep = h_ratio[c] > in.eps ? 1 : 0;  // equality: dependent (A4)
+      const int explicit_keep = h_ratio[c] > in.eps ? 1 : 0;  // ||res|| = eps ||x||: dependent
       if (explicit_keep != h_keep[k]) {
         h_force[k] = explicit_keep;
         h_fpiv[k] = h_ratio[c] * h_ratio[c] * h_xn[k];

@@ -196,7 +196,7 @@ inline ModeMap make_mode_map(const int64_t dims[3], int alpha) {
 // (wshift == WSHIFT_INT): the exact square.  Real values (the 32-bit payload
 // holds an FP32 value): the square on a fixed-point grid, floor(v^2 *
 // 2^wshift), with 2^-wshift = 2^(E - 32) where 2^E bounds the largest
-// square (reading A28); v^2 is exact in FP64 and the scaling is a power of
+// square; v^2 is exact in FP64 and the scaling is a power of
 // two, so the weight is exact and the same on every device.
 constexpr int WSHIFT_INT = -0x7fffffff - 1;
 __device__ __forceinline__ unsigned long long sample_weight(int32_t bits, int wshift) {

@@ -2,8 +2,8 @@
 //
 // The integer path (ctd_api.cu) keeps every stage before U exact in
 // integer arithmetic.  With real values only the draws stay exact: the
-// sampling weight of a value is its square on a fixed-point grid (reading
-// A28, sample_weight), so the column distribution, the CDF and the draws
+// sampling weight of a value is its square on a fixed-point grid
+// (sample_weight), so the column distribution, the CDF and the draws
 // are integers again, exact and the same on every device.  Everything after
 // the draws is FP64 on the FP32 inputs (their products are exact in FP64;
 // only the order of additions differs from a plain FP64 evaluation):
@@ -182,7 +182,7 @@ ctd_status real_sqnorm(const int32_t* v, int64_t nnz, double* out, Arena& scratc
   return sum_f64(part, nb, out, scratch, st);
 }
 
-// The sampling grid of real values (reading A28): 2^-wshift = 2^(E - 32)
+// The sampling grid of real values: 2^-wshift = 2^(E - 32)
 // with 2^E the smallest power of two above the largest square (wshift = 0
 // when every value is zero); CTD_EINVAL for a value that is not finite.
 ctd_status real_weight_shift(const int32_t* v, int64_t nnz, int* wshift, Arena& scratch,
