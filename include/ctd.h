@@ -364,7 +364,7 @@ CTD_API ctd_status ctd_ddos_candidates(const ctd_factors* F, int64_t cap, int64_
  * without allocating any device memory.  The paper has no counterpart: this
  * is for callers that cannot call cudaMalloc (code running inside another
  * allocator's arena or under a hard memory cap, or latency-critical paths
- * that must not enter the driver's allocator).
+ * that must not enter the CUDA runtime's allocator).
  *  X         tensor in DEVICE memory (CTD_MEM_HOST is rejected: copying it
  *            in would need a buffer)
  *  draws     device int64[s], receives I;  unique: device int64[s],
