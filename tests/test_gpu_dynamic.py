@@ -227,6 +227,39 @@ def test_traffic_stream_full_size_sampled():
         assert 0.0 <= G.error() <= 1.0
 
 
+def test_traffic_stream_full_size_u_error_c():
+    """The same full-size stream (2*10^4 x 2*10^4 slices, 5*10^5 nonzeros,
+    d = 400, FP32 bulk), three steps against the oracle's Algorithm 2 run on
+    the whole slices: draws, unique draws, kept fibers and R bit for bit, U
+    within the U bar, the error within the FP32-bulk bar (the oracle's
+    per-step projection form), and the newest block of C, R^(t+1)^T dX
+    (exact), on 500 sampled columns per step."""
+    m = ctd()
+    S = synth.traffic_stream_20k(steps=3)
+    G = m.Dynamic(S.dims2, 1, m.CTD_FP32_BULK, 0)
+    st = O.DynamicState(S.dims2[0], S.dims2[1])
+    st.track_c = False          # the dense C of all steps is not needed here
+    rng = np.random.default_rng(11)
+    J = S.dims2[1]
+    for t in range(S.steps):
+        sl = S.slice(t)
+        G.step_slice(m.Coo.from_synth(sl), 400, 1e-6)
+        step = O.ctd_d_step(st, S.dims2, sl.i, sl.j, sl.val, 400, 1e-6, 0)
+        I, Iu = G.samples()
+        assert np.array_equal(I, step.I) and np.array_equal(Iu, step.I_unique)
+        assert tie_margin(step.ratios, 1e-6) > 1e-7, "near-tie"
+        fib, fstep = G.fibers()
+        assert [(int(a), int(b)) for a, b in zip(fstep, fib)] == st.fibers
+        R_ref = np.stack([np.rint(c).astype(np.int64) for c in st.R_cols], axis=1)
+        assert np.array_equal(G.R_dense(), R_ref)
+        assert rel_fro(G.U(), st.U) <= u_tol(R_ref)
+        e_ref = st.err_num / st.err_den
+        assert abs(G.error() - e_ref) <= error_tol(1, e_ref)
+        cols = np.sort(rng.choice(J, 500, replace=False))
+        got = G.C_columns(J * t + cols)
+        assert np.array_equal(got, step.C_new[:, cols].astype(np.float64))
+
+
 def test_planted_block_stream_scaled():
     """The same stream shape over steps 36..47 so the planted block (steps
     40-45) arrives mid-stream."""
